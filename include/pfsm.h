@@ -1,0 +1,147 @@
+/*
+ * pfsm.h -- C ABI of the B300 (sm_103a) partitioned folded spectrum method (PFSM) library.
+ *
+ * The method (Briggs, Kelley, Bernholc, arXiv:1502.07806, Section II) finds all N eigenpairs
+ * of a real symmetric N x N matrix A that is nearly diagonal in the previous SCF step's
+ * eigenbasis (the reduced subspace Hamiltonian of Eq. 3):
+ *   1. split the eigen-indices into contiguous slices (Fig. 1, m = N/P per slice);
+ *   2. for each slice, solve the overlapping diagonal submatrix B = A[s:s+M, s:s+M] that
+ *      contains it (M = gamma N);
+ *   3. zero-pad the slice's submatrix eigenvectors to length N; they start Eq. 11 with the
+ *      submatrix eigenvalues as shifts eps;
+ *   4. iterate Eq. 11, x <- x - alpha (A - eps I)^2 x, as two matrix products per iteration;
+ *   5. orthonormalise all N vectors (Gram-Schmidt, ascending index order).
+ * Outputs are Rayleigh quotients lambda_k = v_k^T A v_k and unit vectors v_k.
+ *
+ * Conventions for every call:
+ *   - All matrix/vector pointers are DEVICE pointers to FP64 data unless stated otherwise.
+ *     Matrices are dense, row-major, N x N, leading dimension N. V_out[i*N + k] is component i
+ *     of eigenvector k (column k is vector k, as in torch.linalg.eigh).
+ *   - The caller owns every buffer it passes. The handle owns its workspace (allocated once in
+ *     pfsm_init with cudaMalloc, freed in pfsm_destroy) and keeps the last solve's (lambda, V)
+ *     for pfsm_backward.
+ *   - `stream` is a cudaStream_t passed as void* (0 = legacy default stream). Every kernel of a
+ *     call is enqueued on that stream; calls return without synchronising, except
+ *     pfsm_get_status.
+ *   - Return value: PFSM_OK or a pfsm_status_t error. Argument errors and launch errors are
+ *     reported synchronously; conditions the GPU detects while running (NaN input, an
+ *     unsorted prev_eigvals, a Gram-Schmidt breakdown, ...) are recorded in a device status
+ *     word that pfsm_get_status reads. No call exits, traps or waits without bound.
+ *   - pfsm_last_error() returns a thread-local message describing the most recent failure.
+ *
+ * Readings of the paper fixed by this library (identical in the test oracle):
+ *   slices: sizes floor(N/P), the first N mod P one larger, unless slice_sizes is given;
+ *   windows: slice plus `halo` rows each side, clamped to [0, N) (Section II; default halo
+ *     ceil(0.1 N) gives gamma ~ 0.3 at m ~ 0.1 N, the working rule at the end of Section II);
+ *   cluster snap: an interior slice boundary inside a near-degenerate cluster of
+ *     prev_eigvals (gap < cluster_tol) moves to the nearest gap >= cluster_tol within a quarter
+ *     of the neighbouring nominal slices ("down" before "up" at each distance);
+ *   start vectors: the window eigenpairs at the slice indices' own ascending positions; sign
+ *     chosen so the home component is positive (largest component if the home one is < 0.1);
+ *   alpha_k = min(alpha_theta / d_k^2, 1 - 2^-20), d_k = max(hi - eps_k, eps_k - lo), [lo, hi]
+ *     the Gershgorin interval of A (keeps 1 - alpha (lambda - eps)^2 in [0, 1], Eq. 7-11);
+ *   exactly fs_iters iterations of Eq. 11, fixed shifts, no normalisation in between;
+ *   Gram-Schmidt done as Cholesky-QR (S = X^T X = R^T R, V = X R^-1), equal in exact arithmetic
+ *     to Gram-Schmidt in ascending index order; a vector whose norm after projection falls
+ *     below 1e-8 of its norm before is a breakdown (PFSM_ERR_NOT_SPD);
+ *   eigenvalue k stays tied to previous index k: outputs are not re-sorted.
+ */
+#ifndef PFSM_H
+#define PFSM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pfsm_handle_s *pfsm_handle_t;
+
+typedef enum {
+    PFSM_OK = 0,
+    PFSM_ERR_INVALID_ARG = 1,   /* bad size, null pointer, parameter out of range, prev_eigvals
+                                   not ascending (device-detected) */
+    PFSM_ERR_CUDA = 2,          /* a CUDA runtime call failed; see pfsm_last_error() */
+    PFSM_ERR_NOT_SPD = 3,       /* Gram-Schmidt breakdown: overlap matrix not positive definite */
+    PFSM_ERR_NAN_INPUT = 4,     /* A or prev_eigvals holds NaN or Inf */
+    PFSM_ERR_NOT_CONVERGED = 5, /* a submatrix eigensolve did not converge */
+    PFSM_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+    PFSM_ERR_NO_SOLVE = 7,      /* pfsm_backward called before any pfsm_solve on the handle */
+    PFSM_ERR_OUT_OF_MEMORY = 8  /* workspace allocation failed in pfsm_init */
+} pfsm_status_t;
+
+typedef enum {
+    PFSM_FP64 = 0,        /* every product in FP64 (DFMA) */
+    PFSM_TF32_SPLIT = 1,  /* Eq. 11 products on tcgen05 tensor cores in split TF32, FP32
+                             accumulation, FP64 diagonal part and FP64 residual correction */
+    PFSM_BF16_SPLIT = 2   /* as PFSM_TF32_SPLIT with three-way BF16 splitting */
+} pfsm_precision_t;
+
+typedef struct {
+    int32_t halo;          /* rows added on each side of a slice; < 0 selects ceil(0.1 N) */
+    int32_t fs_iters;      /* K >= 0 iterations of Eq. 11 (default 3) */
+    double alpha_theta;    /* theta > 0 in alpha_k = min(theta / d_k^2, 1 - 2^-20) (default 1) */
+    double cluster_tol;    /* slice-boundary snap gap, absolute (default 1e-5; 0 disables) */
+    double degen_tol;      /* backward: pairs with |lambda_i - lambda_j| < degen_tol get no
+                              eigenvector coupling term (default 1e-8) */
+    int32_t precision;     /* pfsm_precision_t (default PFSM_FP64) */
+    int32_t recompute_v;   /* backward recomputes (lambda, V) from the last A instead of
+                              using the kept copy (default 0) */
+    const int32_t *slice_sizes; /* HOST array of nblocks sizes summing to N, or NULL */
+} pfsm_params_t;
+
+/* Fills *p with the defaults listed above. */
+void pfsm_default_params(pfsm_params_t *p);
+
+/* Creates a handle for N x N problems split into nblocks slices (1 <= nblocks <= N).
+ * p may be NULL (defaults). Allocates all device workspace on the current device.
+ * Returns PFSM_ERR_INVALID_ARG for bad sizes/params, PFSM_ERR_OUT_OF_MEMORY or PFSM_ERR_CUDA. */
+int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t *out);
+
+/* One PFSM solve (Section II, steps 1-5).
+ *   A            device, N x N FP64, symmetric (the full matrix is read, not symmetrised)
+ *   prev_eigvals device, N FP64, ascending: the previous step's eigenvalues; they order the
+ *                eigen-indices and place the slice boundaries
+ *   eigvals_out  device, N FP64: Rayleigh quotient of vector k at index k (not re-sorted)
+ *   V_out        device, N x N FP64: V_out[i*N + k] = component i of vector k
+ * A and prev_eigvals must stay valid until the stream reaches the end of the call. */
+int pfsm_solve(pfsm_handle_t h, const double *A, const double *prev_eigvals,
+               double *eigvals_out, double *V_out, void *stream);
+
+/* Eigen-adjoint of the last solve on h (not in the paper): for a loss L(lambda, V),
+ *   dA = sym( V (diag(dLambda) + F o (V^T dV)) V^T ),  F_ij = 1/(lambda_j - lambda_i)
+ * for i != j with |lambda_i - lambda_j| >= degen_tol, else 0; sym(X) = (X + X^T)/2.
+ *   dLambda  device, N FP64, or NULL (treated as zeros)
+ *   dV       device, N x N FP64 in V_out's layout, or NULL (treated as zeros)
+ *   dA_out   device, N x N FP64, written in full (symmetric)
+ * With recompute_v set, (lambda, V) are recomputed from the A of the last solve, which must
+ * still be valid. Returns PFSM_ERR_NO_SOLVE if h has not solved yet. */
+int pfsm_backward(pfsm_handle_t h, const double *dLambda, const double *dV, double *dA_out,
+                  void *stream);
+
+/* Synchronises the stream of the last call on h and returns the device status word of that
+ * call (PFSM_OK or a device-detected pfsm_status_t) in *device_status (host pointer).
+ * The status word is cleared at the start of every solve. */
+int pfsm_get_status(pfsm_handle_t h, int32_t *device_status);
+
+/* Diagnostics of the last solve, copied on `stream` into caller device buffers:
+ *   which = 0: residual norms r_k = ||A v_k - lambda_k v_k||_2          (N doubles)
+ *   which = 1: vectors after the Eq. 11 iterations, before Gram-Schmidt (N x N, V layout)
+ *   which = 2: shifts eps_k                                             (N doubles)
+ *   which = 3: step sizes alpha_k                                       (N doubles)
+ *   which = 4: the partition plan as 4*nblocks int32 (k0[], m[], s[], M[]) reinterpreted
+ *              into the first 2*nblocks doubles' bytes
+ * Returns PFSM_ERR_INVALID_ARG for an unknown `which`, PFSM_ERR_NO_SOLVE before a solve. */
+int pfsm_get_diagnostic(pfsm_handle_t h, int32_t which, void *out, void *stream);
+
+/* Thread-local text of the last error raised on this thread ("" if none). */
+const char *pfsm_last_error(void);
+
+/* Frees the handle and its workspace (synchronises the device first). NULL is allowed. */
+int pfsm_destroy(pfsm_handle_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFSM_H */

@@ -1,0 +1,184 @@
+"""B300-native partitioned folded spectrum method (PFSM, arXiv:1502.07806, Section II).
+
+Thin Python binding over the C ABI in ``include/pfsm.h``: this module only marshals torch CUDA
+tensors (device pointers, sizes, the current stream) into ``libpfsm.so``. Every step of the
+method runs in the library's CUDA kernels; there is no CPU path. If the library is missing the
+calls raise ``RuntimeError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpfsm.so")
+
+OK, INVALID_ARG, CUDA_ERROR, NOT_SPD, NAN_INPUT, NOT_CONVERGED, TIMEOUT, NO_SOLVE, OUT_OF_MEMORY = range(9)
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA_ERROR", 3: "NOT_SPD", 4: "NAN_INPUT",
+                5: "NOT_CONVERGED", 6: "TIMEOUT", 7: "NO_SOLVE", 8: "OUT_OF_MEMORY"}
+FP64, TF32_SPLIT, BF16_SPLIT = 0, 1, 2
+DIAG_RESIDUALS, DIAG_XFS, DIAG_EPS, DIAG_ALPHA, DIAG_PLAN = range(5)
+
+EXPORTED = ("pfsm_default_params", "pfsm_init", "pfsm_solve", "pfsm_backward", "pfsm_get_status",
+            "pfsm_get_diagnostic", "pfsm_last_error", "pfsm_destroy")
+
+
+class PFSMError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        super().__init__(f"{where}: {STATUS_NAMES.get(code, code)}" + (f" ({detail})" if detail else ""))
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("halo", ctypes.c_int32), ("fs_iters", ctypes.c_int32),
+                ("alpha_theta", ctypes.c_double), ("cluster_tol", ctypes.c_double),
+                ("degen_tol", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("recompute_v", ctypes.c_int32), ("slice_sizes", ctypes.POINTER(ctypes.c_int32))]
+
+
+_lib = None
+
+
+def load_library():
+    """Loads libpfsm.so (raises RuntimeError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"PFSM CUDA library not built: {LIB_PATH} is missing "
+                           "(run paper_1502_07806_b300.build.build())")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.pfsm_default_params.argtypes = [ctypes.POINTER(Params)]
+    lib.pfsm_default_params.restype = None
+    lib.pfsm_init.argtypes = [i64, i32, ctypes.POINTER(Params), ctypes.POINTER(P)]
+    lib.pfsm_solve.argtypes = [P, P, P, P, P, P]
+    lib.pfsm_backward.argtypes = [P, P, P, P, P]
+    lib.pfsm_get_status.argtypes = [P, ctypes.POINTER(i32)]
+    lib.pfsm_get_diagnostic.argtypes = [P, i32, P, P]
+    lib.pfsm_last_error.argtypes = []
+    lib.pfsm_last_error.restype = ctypes.c_char_p
+    lib.pfsm_destroy.argtypes = [P]
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise PFSMError(rc, where, load_library().pfsm_last_error().decode())
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def default_params() -> Params:
+    p = Params()
+    load_library().pfsm_default_params(ctypes.byref(p))
+    return p
+
+
+class Handle:
+    """Owns one pfsm_handle_t (workspace for N x N problems split into nblocks slices)."""
+
+    def __init__(self, n: int, nblocks: int, halo: int = -1, fs_iters: int = 3,
+                 alpha_theta: float = 1.0, cluster_tol: float = 1e-5, degen_tol: float = 1e-8,
+                 precision: int = FP64, recompute_v: bool = False, slice_sizes=None):
+        lib = load_library()
+        p = default_params()
+        p.halo, p.fs_iters, p.alpha_theta = halo, fs_iters, alpha_theta
+        p.cluster_tol, p.degen_tol, p.precision = cluster_tol, degen_tol, precision
+        p.recompute_v = int(bool(recompute_v))
+        self._sizes = None
+        if slice_sizes is not None:
+            self._sizes = (ctypes.c_int32 * nblocks)(*[int(x) for x in slice_sizes])
+            p.slice_sizes = ctypes.cast(self._sizes, ctypes.POINTER(ctypes.c_int32))
+        h = ctypes.c_void_p()
+        _check(lib.pfsm_init(n, nblocks, ctypes.byref(p), ctypes.byref(h)), "pfsm_init")
+        self._h, self.n, self.nblocks = h, n, nblocks
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().pfsm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, A: torch.Tensor, prev: torch.Tensor, eigvals_out: torch.Tensor | None = None,
+              V_out: torch.Tensor | None = None):
+        n = self.n
+        if eigvals_out is None:
+            eigvals_out = torch.empty(n, dtype=torch.float64, device=A.device)
+        if V_out is None:
+            V_out = torch.empty(n, n, dtype=torch.float64, device=A.device)
+        _check(load_library().pfsm_solve(self._h, _ptr(A), _ptr(prev), _ptr(eigvals_out),
+                                         _ptr(V_out), _stream()), "pfsm_solve")
+        return eigvals_out, V_out
+
+    def backward(self, dlam: torch.Tensor | None, dV: torch.Tensor | None,
+                 dA_out: torch.Tensor | None = None):
+        n = self.n
+        if dA_out is None:
+            dA_out = torch.empty(n, n, dtype=torch.float64, device="cuda")
+        _check(load_library().pfsm_backward(self._h, _ptr(dlam), _ptr(dV), _ptr(dA_out), _stream()),
+               "pfsm_backward")
+        return dA_out
+
+    def status(self) -> int:
+        s = ctypes.c_int32(-1)
+        _check(load_library().pfsm_get_status(self._h, ctypes.byref(s)), "pfsm_get_status")
+        return s.value
+
+    def diagnostic(self, which: int) -> torch.Tensor:
+        n = self.n
+        if which == DIAG_XFS:
+            out = torch.empty(n, n, dtype=torch.float64, device="cuda")
+        elif which == DIAG_PLAN:
+            out = torch.empty(max(1, (4 * self.nblocks + 1) // 2), dtype=torch.float64, device="cuda")
+        else:
+            out = torch.empty(n, dtype=torch.float64, device="cuda")
+        _check(load_library().pfsm_get_diagnostic(self._h, which, ctypes.c_void_p(out.data_ptr()), _stream()),
+               "pfsm_get_diagnostic")
+        if which == DIAG_PLAN:
+            return out.view(torch.int32)[: 4 * self.nblocks].reshape(4, self.nblocks)
+        return out
+
+
+def solve(A: torch.Tensor, prev: torch.Tensor, nblocks: int, **kw):
+    """One-shot solve: returns (eigvals, V, status)."""
+    h = Handle(A.shape[0], nblocks, **kw)
+    lam, V = h.solve(A, prev)
+    st = h.status()
+    h.close()
+    return lam, V, st
+
+
+class PFSMFunction(torch.autograd.Function):
+    """(A, prev) -> (eigvals, V) through the PFSM kernels, with the eigen-adjoint backward."""
+
+    @staticmethod
+    def forward(ctx, A, prev, handle: Handle):
+        lam, V = handle.solve(A.contiguous(), prev.contiguous())
+        ctx.handle = handle
+        return lam, V
+
+    @staticmethod
+    def backward(ctx, dlam, dV):
+        dlam = None if dlam is None else dlam.contiguous()
+        dV = None if dV is None else dV.contiguous()
+        dA = ctx.handle.backward(dlam, dV)
+        return dA, None, None

@@ -1,0 +1,270 @@
+// C ABI of the PFSM library: argument checks, workspace ownership, and the order of kernels for
+// one solve (Section II: partition, submatrix solves, Eq. 11 iterations, Gram-Schmidt).
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "pfsm_internal.cuh"
+
+using namespace pfsm;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(PFSM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define PFSM_CUDA(expr)                                        \
+    do {                                                       \
+        cudaError_t e_ = (expr);                               \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #expr);    \
+    } while (0)
+
+template <typename T>
+cudaError_t alloc(T **p, size_t count)
+{
+    return cudaMalloc((void **)p, count * sizeof(T) + 256);
+}
+
+void free_ws(pfsm_handle_s *h)
+{
+    Workspace &w = h->ws;
+    void *ptrs[] = {w.plan, w.tile_krange, w.status, w.gersh, w.X, w.Xfs, w.Y, w.S, w.W, w.Vrm,
+                    w.sdiag, w.eps, w.alpha, w.lam, w.res, w.refl, w.tau, w.td, w.te,
+                    w.sel_val, w.sel_vec, w.iiwork, w.slices};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    w = Workspace{};
+}
+
+// Largest dynamic shared memory a CTA may use on this part.
+constexpr size_t kSmemCap = 227 * 1024;
+
+}  // namespace
+
+extern "C" {
+
+void pfsm_default_params(pfsm_params_t *p)
+{
+    if (!p) return;
+    p->halo = -1;
+    p->fs_iters = 3;
+    p->alpha_theta = 1.0;
+    p->cluster_tol = 1e-5;
+    p->degen_tol = 1e-8;
+    p->precision = PFSM_FP64;
+    p->recompute_v = 0;
+    p->slice_sizes = nullptr;
+}
+
+const char *pfsm_last_error(void) { return g_last_error.c_str(); }
+
+int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t *out)
+{
+    if (!out) return fail(PFSM_ERR_INVALID_ARG, "pfsm_init: out is NULL");
+    *out = nullptr;
+    if (N < 1 || N > 65535) return fail(PFSM_ERR_INVALID_ARG, "pfsm_init: N=%lld outside [1, 65535]", (long long)N);
+    if (nblocks < 1 || nblocks > N)
+        return fail(PFSM_ERR_INVALID_ARG, "pfsm_init: nblocks=%d outside [1, N]", nblocks);
+    pfsm_params_t prm;
+    pfsm_default_params(&prm);
+    if (p) prm = *p;
+    if (prm.fs_iters < 0 || prm.fs_iters > 1000) return fail(PFSM_ERR_INVALID_ARG, "pfsm_init: fs_iters=%d", prm.fs_iters);
+    if (!(prm.alpha_theta > 0.0) || !(prm.cluster_tol >= 0.0) || !(prm.degen_tol >= 0.0))
+        return fail(PFSM_ERR_INVALID_ARG, "pfsm_init: alpha_theta must be > 0, tolerances >= 0");
+    if (prm.precision != PFSM_FP64)
+        return fail(PFSM_ERR_INVALID_ARG, "pfsm_init: precision %d not available in this build", prm.precision);
+    int32_t mnom = (int32_t)((N + nblocks - 1) / nblocks);
+    if (prm.slice_sizes) {
+        int64_t tot = 0;
+        mnom = 0;
+        for (int32_t b = 0; b < nblocks; b++) {
+            if (prm.slice_sizes[b] < 1) return fail(PFSM_ERR_INVALID_ARG, "pfsm_init: slice %d has size %d", b, prm.slice_sizes[b]);
+            tot += prm.slice_sizes[b];
+            mnom = prm.slice_sizes[b] > mnom ? prm.slice_sizes[b] : mnom;
+        }
+        if (tot != N) return fail(PFSM_ERR_INVALID_ARG, "pfsm_init: slice sizes sum to %lld, not N", (long long)tot);
+    }
+    pfsm_handle_s *h = new pfsm_handle_s();
+    h->N = N;
+    h->nb = nblocks;
+    h->prm = prm;
+    h->halo = prm.halo < 0 ? (int32_t)((N + 9) / 10) : prm.halo;
+    // the cluster snap moves each boundary by at most a quarter of a nominal slice
+    int64_t mmax = (int64_t)mnom + 2 * (mnom / 4);
+    h->mmax = (int32_t)(mmax < N ? mmax : N);
+    int64_t Mmax = (int64_t)h->mmax + 2 * (int64_t)h->halo;
+    h->Mmax = (int32_t)(Mmax < N ? Mmax : N);
+    // cluster shape of the tridiagonalisation
+    const int Mx = h->Mmax;
+    auto smem_rows = [&](int cl) { return (size_t)((Mx + cl - 1) / cl) * Mx * 8 + (size_t)(4 * Mx + 64) * 8; };
+    if (Mx <= 128 && smem_rows(4) <= kSmemCap) { h->cl = 4; h->rows_in_smem = true; }
+    else if (smem_rows(8) <= kSmemCap) { h->cl = 8; h->rows_in_smem = true; }
+    else if (smem_rows(16) <= kSmemCap) { h->cl = 16; h->rows_in_smem = true; }
+    else { h->cl = 16; h->rows_in_smem = false; }
+
+    Workspace &w = h->ws;
+    const size_t NN = (size_t)N * N;
+    const int64_t ntiles = (N + kFsTileRows - 1) / kFsTileRows;
+    const size_t nbM = (size_t)nblocks * h->Mmax;
+    size_t ii = (size_t)nblocks * h->mmax * 5 * h->Mmax;
+    if (!h->rows_in_smem && nbM * h->Mmax > ii) ii = nbM * h->Mmax;
+    cudaError_t e = cudaSuccess;
+#define PFSM_ALLOC(ptr, cnt) if (e == cudaSuccess) e = alloc(&(ptr), (cnt))
+    PFSM_ALLOC(w.plan, 4 * (size_t)nblocks);
+    PFSM_ALLOC(w.tile_krange, 2 * (size_t)ntiles);
+    PFSM_ALLOC(w.status, 1);
+    PFSM_ALLOC(w.gersh, 2 * (size_t)N + 2);
+    PFSM_ALLOC(w.X, NN);
+    PFSM_ALLOC(w.Xfs, NN);
+    PFSM_ALLOC(w.Y, NN);
+    PFSM_ALLOC(w.S, NN);
+    PFSM_ALLOC(w.W, NN);
+    PFSM_ALLOC(w.Vrm, NN);
+    PFSM_ALLOC(w.sdiag, (size_t)N);
+    PFSM_ALLOC(w.eps, (size_t)N);
+    PFSM_ALLOC(w.alpha, (size_t)N);
+    PFSM_ALLOC(w.lam, (size_t)N);
+    PFSM_ALLOC(w.res, (size_t)N);
+    PFSM_ALLOC(w.refl, nbM * h->Mmax);
+    PFSM_ALLOC(w.tau, nbM);
+    PFSM_ALLOC(w.td, nbM);
+    PFSM_ALLOC(w.te, nbM);
+    PFSM_ALLOC(w.sel_val, (size_t)nblocks * h->mmax);
+    PFSM_ALLOC(w.sel_vec, (size_t)nblocks * h->mmax * h->Mmax);
+    PFSM_ALLOC(w.iiwork, ii);
+    if (prm.slice_sizes) PFSM_ALLOC(w.slices, (size_t)nblocks);
+#undef PFSM_ALLOC
+    if (e == cudaSuccess && prm.slice_sizes)
+        e = cudaMemcpy(w.slices, prm.slice_sizes, sizeof(int32_t) * nblocks, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = configure_kernels(h);
+    if (e != cudaSuccess) {
+        int code = (e == cudaErrorMemoryAllocation) ? PFSM_ERR_OUT_OF_MEMORY : PFSM_ERR_CUDA;
+        free_ws(h);
+        delete h;
+        cudaGetLastError();
+        return fail(code, "pfsm_init: %s", cudaGetErrorString(e));
+    }
+    h->prm.slice_sizes = nullptr;   // the host array is not kept
+    *out = h;
+    return PFSM_OK;
+}
+
+static int solve_impl(pfsm_handle_s *h, const double *A, const double *prev, double *eigvals_out,
+                      double *V_out, cudaStream_t st)
+{
+    Workspace &w = h->ws;
+    const int64_t N = h->N;
+    PFSM_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int32_t), st));
+    PFSM_CUDA(launch_validate_gersh(A, prev, N, w.gersh, w.status, st));
+    PFSM_CUDA(launch_plan(prev, N, h->nb, h->halo, h->prm.cluster_tol, w.slices, w.plan,
+                          w.tile_krange, w.gersh, w.status, st));
+    PFSM_CUDA(launch_subeig(h, A, st));
+    // Eq. 11, fs_iters times: Y = (A - eps I) X ; X <- X - alpha (A - eps I) Y
+    for (int it = 0; it < h->prm.fs_iters; it++) {
+        GemmArgs g{};
+        g.rows = N; g.cols = N; g.K = N;
+        g.P = w.X; g.ldp = N; g.Q = A; g.ldq = N; g.C = w.Y; g.ldc = N;
+        g.aux_x = w.X; g.eps = w.eps;
+        g.krange = (it == 0) ? w.tile_krange : nullptr;   // start vectors vanish outside windows
+        PFSM_CUDA(launch_gemm_f64(g, EPI_FS1, Q_KMAJOR, st));
+        GemmArgs u{};
+        u.rows = N; u.cols = N; u.K = N;
+        u.P = w.Y; u.ldp = N; u.Q = A; u.ldq = N; u.C = w.X; u.ldc = N;
+        u.aux_y = w.Y; u.eps = w.eps; u.alpha = w.alpha;
+        PFSM_CUDA(launch_gemm_f64(u, EPI_FS2, Q_KMAJOR, st));
+    }
+    PFSM_CUDA(cudaMemcpyAsync(w.Xfs, w.X, (size_t)N * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    PFSM_CUDA(launch_gram_schmidt_f64(h, st));
+    PFSM_CUDA(launch_rayleigh_f64(h, A, eigvals_out, V_out, st));
+    h->solved = true;
+    h->last_A = A;
+    h->last_prev = prev;
+    h->last_stream = st;
+    return PFSM_OK;
+}
+
+int pfsm_solve(pfsm_handle_t h, const double *A, const double *prev_eigvals, double *eigvals_out,
+               double *V_out, void *stream)
+{
+    if (!h) return fail(PFSM_ERR_INVALID_ARG, "pfsm_solve: null handle");
+    if (!A || !prev_eigvals || !eigvals_out || !V_out)
+        return fail(PFSM_ERR_INVALID_ARG, "pfsm_solve: null buffer");
+    return solve_impl(h, A, prev_eigvals, eigvals_out, V_out, (cudaStream_t)stream);
+}
+
+int pfsm_backward(pfsm_handle_t h, const double *dLambda, const double *dV, double *dA_out,
+                  void *stream)
+{
+    if (!h) return fail(PFSM_ERR_INVALID_ARG, "pfsm_backward: null handle");
+    if (!dA_out) return fail(PFSM_ERR_INVALID_ARG, "pfsm_backward: null dA_out");
+    if (!h->solved) return fail(PFSM_ERR_NO_SOLVE, "pfsm_backward: no solve on this handle yet");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (h->prm.recompute_v) {
+        // rebuild (lambda, V) from the last inputs; outputs land in the handle's own buffers
+        int rc = solve_impl(h, h->last_A, h->last_prev, h->ws.lam, h->ws.Vrm, st);
+        if (rc != PFSM_OK) return rc;
+    }
+    PFSM_CUDA(launch_backward_f64(h, dLambda, dV, dA_out, st));
+    h->last_stream = st;
+    return PFSM_OK;
+}
+
+int pfsm_get_status(pfsm_handle_t h, int32_t *device_status)
+{
+    if (!h || !device_status) return fail(PFSM_ERR_INVALID_ARG, "pfsm_get_status: null argument");
+    PFSM_CUDA(cudaStreamSynchronize(h->last_stream));
+    PFSM_CUDA(cudaMemcpy(device_status, h->ws.status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    return PFSM_OK;
+}
+
+int pfsm_get_diagnostic(pfsm_handle_t h, int32_t which, void *out, void *stream)
+{
+    if (!h || !out) return fail(PFSM_ERR_INVALID_ARG, "pfsm_get_diagnostic: null argument");
+    if (!h->solved) return fail(PFSM_ERR_NO_SOLVE, "pfsm_get_diagnostic: no solve yet");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)h->N;
+    const void *src = nullptr;
+    size_t bytes = 0;
+    switch (which) {
+    case 0: src = h->ws.res; bytes = n * 8; break;
+    case 1: {
+        cudaError_t e = launch_transpose(h->ws.Xfs, (double *)out, h->N, st);
+        if (e != cudaSuccess) return cuda_fail(e, "transpose");
+        return PFSM_OK;
+    }
+    case 2: src = h->ws.eps; bytes = n * 8; break;
+    case 3: src = h->ws.alpha; bytes = n * 8; break;
+    case 4: src = h->ws.plan; bytes = (size_t)4 * h->nb * sizeof(int32_t); break;
+    default: return fail(PFSM_ERR_INVALID_ARG, "pfsm_get_diagnostic: unknown which=%d", which);
+    }
+    PFSM_CUDA(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToDevice, st));
+    return PFSM_OK;
+}
+
+int pfsm_destroy(pfsm_handle_t h)
+{
+    if (!h) return PFSM_OK;
+    cudaDeviceSynchronize();
+    free_ws(h);
+    delete h;
+    return PFSM_OK;
+}
+
+}  // extern "C"

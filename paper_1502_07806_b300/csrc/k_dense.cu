@@ -1,0 +1,293 @@
+// Gram-Schmidt (Section II, after the Eq. 11 iterations), Rayleigh quotients / residuals, and
+// the eigen-adjoint backward, FP64.
+//
+// Gram-Schmidt is done as Cholesky-QR. With the vectors as rows of X:
+//   S = X X^T (overlap, lower triangle), S = L L^T (blocked right-looking Cholesky),
+//   V = L^-1 X (blocked forward substitution over the rows).
+// In exact arithmetic this is the QR factorisation with positive R diagonal, i.e. Gram-Schmidt
+// in ascending index order. L_jj^2 is the squared norm of vector j after projecting out vectors
+// 0..j-1 and S_jj its squared norm before, so L_jj < 1e-8 sqrt(S_jj) is the breakdown test.
+#include <cfloat>
+
+#include "pfsm_internal.cuh"
+
+namespace pfsm {
+
+constexpr int CB = 64;   // Cholesky / TRSM block
+
+__global__ void k_copy_diag(const double *__restrict__ S, int64_t N, double *__restrict__ d)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) d[i] = S[i * N + i];
+}
+
+// Unblocked Cholesky of the b x b diagonal block at (jb, jb), in shared memory, one CTA.
+__global__ void k_potrf_diag(double *__restrict__ S, int64_t N, int64_t jb, int b,
+                             const double *__restrict__ sdiag, int32_t *status)
+{
+    __shared__ double L[CB][CB + 1];
+    for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
+        int i = t / b, k = t % b;
+        L[i][k] = (k <= i) ? S[(jb + i) * N + jb + k] : 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < b; j++) {
+        if (threadIdx.x == 0) {
+            double d = L[j][j];
+            double ref = sqrt(fmax(sdiag[jb + j], 0.0));
+            double l = (d > 0.0) ? sqrt(d) : 0.0;
+            if (!(l >= 1e-8 * ref) || l == 0.0 || !isfinite(d)) {
+                set_status(status, PFSM_ERR_NOT_SPD);
+                l = 1.0;   // keep the arithmetic finite; the result is flagged as invalid
+            }
+            L[j][j] = l;
+        }
+        __syncthreads();
+        const double inv = 1.0 / L[j][j];
+        for (int i = j + 1 + threadIdx.x; i < b; i += blockDim.x) L[i][j] *= inv;
+        __syncthreads();
+        const int rem = b - j - 1;
+        for (int t = threadIdx.x; t < rem * rem; t += blockDim.x) {
+            int i = j + 1 + t / rem, k = j + 1 + t % rem;
+            if (k <= i) L[i][k] -= L[i][j] * L[k][j];
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
+        int i = t / b, k = t % b;
+        if (k <= i) S[(jb + i) * N + jb + k] = L[i][k];
+    }
+}
+
+// Panel: rows i >= jb + b solve l_i L_jj^T = s_i (columns jb .. jb+b-1), 16 rows per CTA.
+constexpr int kPanelRows = 16;
+__global__ void k_trsm_panel(double *__restrict__ S, int64_t N, int64_t jb, int b)
+{
+    __shared__ double L[CB][CB + 1];
+    __shared__ double Pn[kPanelRows][CB + 1];
+    const int64_t rbase = jb + b + (int64_t)blockIdx.x * kPanelRows;
+    for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
+        int i = t / b, k = t % b;
+        L[i][k] = (k <= i) ? S[(jb + i) * N + jb + k] : 0.0;
+    }
+    for (int t = threadIdx.x; t < kPanelRows * b; t += blockDim.x) {
+        int r = t / b, k = t % b;
+        int64_t row = rbase + r;
+        Pn[r][k] = (row < N) ? S[row * N + jb + k] : 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x < kPanelRows) {
+        const int r = threadIdx.x;
+        for (int j = 0; j < b; j++) {
+            double acc = Pn[r][j];
+            for (int l = 0; l < j; l++) acc -= Pn[r][l] * L[j][l];
+            Pn[r][j] = acc / L[j][j];
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kPanelRows * b; t += blockDim.x) {
+        int r = t / b, k = t % b;
+        int64_t row = rbase + r;
+        if (row < N) S[row * N + jb + k] = Pn[r][k];
+    }
+}
+
+// Rows jb .. jb+b-1 of X become L_jj^-1 X[jb:jb+b, :] (forward substitution, one column per
+// thread, columns coalesced across the CTA).
+__global__ void k_trsm_diag_rows(const double *__restrict__ S, double *__restrict__ X, int64_t N,
+                                 int64_t jb, int b)
+{
+    __shared__ double L[CB][CB + 1];
+    for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
+        int i = t / b, k = t % b;
+        L[i][k] = (k <= i) ? S[(jb + i) * N + jb + k] : 0.0;
+    }
+    __syncthreads();
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    double *col = X + jb * N + c;     // this thread's column; earlier rows already solved
+    for (int r = 0; r < b; r++) {
+        double acc = col[r * N];
+        for (int l = 0; l < r; l++) acc -= L[r][l] * col[l * N];
+        col[r * N] = acc / L[r][r];
+    }
+}
+
+cudaError_t launch_gram_schmidt_f64(pfsm_handle_s *h, cudaStream_t st)
+{
+    Workspace &w = h->ws;
+    const int64_t N = h->N;
+    cudaError_t e;
+    // S = X X^T (lower)
+    GemmArgs g{};
+    g.rows = N; g.cols = N; g.K = N;
+    g.P = w.X; g.ldp = N; g.Q = w.X; g.ldq = N; g.C = w.S; g.ldc = N; g.lower_only = 1;
+    if ((e = launch_gemm_f64(g, EPI_STORE, Q_KMAJOR, st)) != cudaSuccess) return e;
+    k_copy_diag<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(w.S, N, w.sdiag);
+    // Cholesky
+    for (int64_t jb = 0; jb < N; jb += CB) {
+        const int b = (int)((N - jb) < CB ? (N - jb) : CB);
+        k_potrf_diag<<<1, 256, 0, st>>>(w.S, N, jb, b, w.sdiag, w.status);
+        const int64_t rest = N - jb - b;
+        if (rest <= 0) break;
+        k_trsm_panel<<<(unsigned)((rest + kPanelRows - 1) / kPanelRows), 128, 0, st>>>(w.S, N, jb, b);
+        GemmArgs u{};
+        u.rows = rest; u.cols = rest; u.K = b;
+        u.P = w.S + (jb + b) * N + jb; u.ldp = N;
+        u.Q = w.S + (jb + b) * N + jb; u.ldq = N;
+        u.C = w.S + (jb + b) * N + jb + b; u.ldc = N; u.lower_only = 1;
+        if ((e = launch_gemm_f64(u, EPI_SUB, Q_KMAJOR, st)) != cudaSuccess) return e;
+    }
+    // V = L^-1 X (rows)
+    for (int64_t jb = 0; jb < N; jb += CB) {
+        const int b = (int)((N - jb) < CB ? (N - jb) : CB);
+        k_trsm_diag_rows<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(w.S, w.X, N, jb, b);
+        const int64_t rest = N - jb - b;
+        if (rest <= 0) break;
+        GemmArgs u{};
+        u.rows = rest; u.cols = N; u.K = b;
+        u.P = w.S + (jb + b) * N + jb; u.ldp = N;
+        u.Q = w.X + jb * N; u.ldq = N;
+        u.C = w.X + (jb + b) * N; u.ldc = N;
+        if ((e = launch_gemm_f64(u, EPI_SUB, Q_NMAJOR, st)) != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+// ---- Rayleigh quotients and residual norms (warp-shuffle row reductions) --------------------
+
+__device__ __forceinline__ double cta_sum(double v, double *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += red[i];
+    return t;
+}
+
+// One CTA per vector k: lambda_k = v_k . w_k, r_k = ||w_k - lambda_k v_k|| with W = V A (rows).
+__global__ void k_rayleigh_rows(const double *__restrict__ V, const double *__restrict__ W,
+                                int64_t N, double *__restrict__ lam, double *__restrict__ res)
+{
+    __shared__ double red[32];
+    const int64_t k = blockIdx.x;
+    const double *v = V + k * N, *w = W + k * N;
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) acc += v[i] * w[i];
+    const double l = cta_sum(acc, red);
+    double r2 = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+        double t = w[i] - l * v[i];
+        r2 += t * t;
+    }
+    r2 = cta_sum(r2, red);
+    if (threadIdx.x == 0) { lam[k] = l; res[k] = sqrt(r2); }
+}
+
+__global__ void k_transpose(const double *__restrict__ in, double *__restrict__ out, int64_t N)
+{
+    __shared__ double t[32][33];
+    const int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        int64_t r = by + j, c = bx + threadIdx.x;
+        if (r < N && c < N) t[j][threadIdx.x] = in[r * N + c];
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        int64_t r = bx + j, c = by + threadIdx.x;
+        if (r < N && c < N) out[r * N + c] = t[threadIdx.x][j];
+    }
+}
+
+cudaError_t launch_transpose(const double *in, double *out, int64_t N, cudaStream_t st)
+{
+    dim3 grid((unsigned)((N + 31) / 32), (unsigned)((N + 31) / 32));
+    k_transpose<<<grid, dim3(32, 8), 0, st>>>(in, out, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rayleigh_f64(pfsm_handle_s *h, const double *A, double *eigvals_out,
+                                double *V_out, cudaStream_t st)
+{
+    Workspace &w = h->ws;
+    const int64_t N = h->N;
+    cudaError_t e;
+    GemmArgs g{};
+    g.rows = N; g.cols = N; g.K = N;
+    g.P = w.X; g.ldp = N; g.Q = A; g.ldq = N; g.C = w.W; g.ldc = N;
+    if ((e = launch_gemm_f64(g, EPI_STORE, Q_KMAJOR, st)) != cudaSuccess) return e;
+    k_rayleigh_rows<<<(unsigned)N, 256, 0, st>>>(w.X, w.W, N, w.lam, w.res);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_transpose(w.X, w.Vrm, N, st)) != cudaSuccess) return e;
+    if (eigvals_out != w.lam &&
+        (e = cudaMemcpyAsync(eigvals_out, w.lam, (size_t)N * sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+        return e;
+    if (V_out == w.Vrm) return cudaSuccess;
+    return cudaMemcpyAsync(V_out, w.Vrm, (size_t)N * N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+}
+
+// ---- eigen-adjoint ----------------------------------------------------------------------------
+
+// In place on G = V^T dV: M_kl = sym(diag(dlam) + F o G), F_kl = 1/(lam_l - lam_k) masked.
+__global__ void k_adjoint_mix(double *__restrict__ G, int64_t N, const double *__restrict__ lam,
+                              const double *__restrict__ dlam, double tau)
+{
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t k = blockIdx.y;
+    if (l >= N || l < k) return;
+    if (l == k) { G[k * N + k] = dlam ? dlam[k] : 0.0; return; }
+    const double gap = lam[l] - lam[k];
+    const double fkl = (fabs(gap) >= tau) ? 1.0 / gap : 0.0;    // F_kl
+    const double flk = (fabs(gap) >= tau) ? -1.0 / gap : 0.0;   // F_lk
+    const double m = 0.5 * (fkl * G[k * N + l] + flk * G[l * N + k]);
+    G[k * N + l] = m;
+    G[l * N + k] = m;
+}
+
+__global__ void k_symmetrize(double *__restrict__ D, int64_t N)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = blockIdx.y;
+    if (j >= N || j <= i) return;
+    const double s = 0.5 * (D[i * N + j] + D[j * N + i]);
+    D[i * N + j] = s;
+    D[j * N + i] = s;
+}
+
+cudaError_t launch_backward_f64(pfsm_handle_s *h, const double *dLambda, const double *dV,
+                                double *dA_out, cudaStream_t st)
+{
+    Workspace &w = h->ws;
+    const int64_t N = h->N;
+    cudaError_t e;
+    // G = V^T dV : G[k, l] = sum_i Vt[k, i] dVt[l, i]; Vt = X (rows), dVt = transpose(dV)
+    if (dV) {
+        if ((e = launch_transpose(dV, w.W, N, st)) != cudaSuccess) return e;
+        GemmArgs g{};
+        g.rows = N; g.cols = N; g.K = N;
+        g.P = w.X; g.ldp = N; g.Q = w.W; g.ldq = N; g.C = w.S; g.ldc = N;
+        if ((e = launch_gemm_f64(g, EPI_STORE, Q_KMAJOR, st)) != cudaSuccess) return e;
+    } else {
+        if ((e = cudaMemsetAsync(w.S, 0, (size_t)N * N * sizeof(double), st)) != cudaSuccess) return e;
+    }
+    dim3 gm((unsigned)((N + 255) / 256), (unsigned)N);
+    k_adjoint_mix<<<gm, 256, 0, st>>>(w.S, N, w.lam, dLambda, h->prm.degen_tol);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // Ut[j, k] = sum_l V[j, l] M[k, l]
+    GemmArgs u{};
+    u.rows = N; u.cols = N; u.K = N;
+    u.P = w.Vrm; u.ldp = N; u.Q = w.S; u.ldq = N; u.C = w.Y; u.ldc = N;
+    if ((e = launch_gemm_f64(u, EPI_STORE, Q_KMAJOR, st)) != cudaSuccess) return e;
+    // dA[i, j] = sum_k V[i, k] Ut[j, k]
+    GemmArgs d{};
+    d.rows = N; d.cols = N; d.K = N;
+    d.P = w.Vrm; d.ldp = N; d.Q = w.Y; d.ldq = N; d.C = dA_out; d.ldc = N;
+    if ((e = launch_gemm_f64(d, EPI_STORE, Q_KMAJOR, st)) != cudaSuccess) return e;
+    k_symmetrize<<<gm, 256, 0, st>>>(dA_out, N);
+    return cudaGetLastError();
+}
+
+}  // namespace pfsm

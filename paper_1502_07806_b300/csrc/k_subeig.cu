@@ -1,0 +1,450 @@
+// Batched FP64 submatrix eigensolves and start vectors (Section II: "solving a sequence of
+// eigenvector problems generated from overlapping diagonal submatrices"; the eigenvectors y of
+// each submatrix B start Eq. 11 and its eigenvalues are the shifts).
+//
+// Only the m eigenpairs of each window at the slice's own ascending positions are needed, so
+// instead of a full dense eigensolver the pipeline is:
+//   1. k_tridiag      Householder reduction of every window B_b to tridiagonal T_b
+//                     (Golub & Van Loan Sec. 8.3.1). One thread-block cluster per window; rows
+//                     are spread cyclically over the cluster's CTAs (in shared memory when they
+//                     fit, else in global memory) and the Householder vector and the product
+//                     p = beta B v are exchanged through distributed shared memory.
+//   2. k_bisect       the selected eigenvalues of T_b by Sturm-count bisection, one thread each.
+//   3. k_inverse_iter their eigenvectors of T_b by inverse iteration with a pivoted tridiagonal
+//                     LU, re-orthogonalised inside clusters of (nearly) equal eigenvalues.
+//   4. k_backtransform y = H_0 ... H_{M-3} z, sign rule, zero padding to length N, shift eps and
+//                     step alpha: one warp per start vector, written straight into X.
+#include <cooperative_groups.h>
+#include <cfloat>
+
+#include "pfsm_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace pfsm {
+
+constexpr int kTriThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < nw; i++) t += red[i];   // same order in every thread and every CTA
+    return t;
+}
+
+// Grid: nb * CL CTAs, clusters of CL along x. Rows of window b are owned cyclically: CTA `rank`
+// owns rows i with i % CL == rank.
+template <bool SMEM_ROWS>
+__global__ void __launch_bounds__(kTriThreads)
+k_tridiag(const double *__restrict__ A, int64_t N, const int32_t *__restrict__ plan, int32_t nb,
+          int32_t Mmax, double *__restrict__ gwork, double *__restrict__ refl,
+          double *__restrict__ tau, double *__restrict__ td, double *__restrict__ te)
+{
+    cg::cluster_group cluster = cg::this_cluster();
+    const int CL = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int b = blockIdx.x / CL;
+    const int64_t s0 = plan[2 * nb + b];
+    const int M = plan[3 * nb + b];
+    const int R = (Mmax + CL - 1) / CL;
+    extern __shared__ double sm[];
+    double *rows = SMEM_ROWS ? sm : (gwork + (size_t)b * Mmax * Mmax);
+    double *vbuf = sm + (SMEM_ROWS ? (size_t)R * Mmax : 0);
+    double *pbuf = vbuf + Mmax;
+    double *hv = pbuf + Mmax;
+    double *wv = hv + Mmax;
+    double *red = wv + Mmax;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    auto rowp = [&](int i) -> double * {
+        return SMEM_ROWS ? rows + (size_t)(i / CL) * Mmax : rows + (size_t)i * Mmax;
+    };
+    double *brefl = refl + (size_t)b * Mmax * Mmax;
+    double *btau = tau + (size_t)b * Mmax, *btd = td + (size_t)b * Mmax, *bte = te + (size_t)b * Mmax;
+
+    // load owned rows of B = A[s0:s0+M, s0:s0+M]
+    for (int i = rank + warp * CL; i < M; i += nwarps * CL) {
+        const double *src = A + (s0 + i) * N + s0;
+        double *dst = rowp(i);
+        for (int j = lane; j < M; j += 32) dst[j] = src[j];
+    }
+    __syncthreads();
+    // broadcast column 0 (rows >= 1) into every CTA's vbuf
+    for (int i = rank + threadIdx.x * CL; i < M; i += blockDim.x * CL) {
+        if (i < 1) continue;
+        double v = rowp(i)[0];
+        for (int r = 0; r < CL; r++) cluster.map_shared_rank(vbuf, r)[i] = v;
+    }
+    cluster.sync();
+
+    for (int k = 0; k + 2 < M; k++) {
+        // (a) Householder vector of column k, computed redundantly and identically in every CTA
+        double x0 = vbuf[k + 1];
+        double t2 = 0.0;
+        for (int i = k + 2 + threadIdx.x; i < M; i += blockDim.x) t2 += vbuf[i] * vbuf[i];
+        double tail2 = block_sum(t2, red);
+        double beta = 0.0, alpha = x0;
+        if (tail2 != 0.0) {
+            double xn = sqrt(x0 * x0 + tail2);
+            alpha = (x0 >= 0.0) ? -xn : xn;
+            double v0 = x0 - alpha;
+            beta = 2.0 / (v0 * v0 + tail2);
+            for (int i = k + 1 + threadIdx.x; i < M; i += blockDim.x) hv[i] = (i == k + 1) ? v0 : vbuf[i];
+        }
+        if (rank == 0) {
+            if (threadIdx.x == 0) { bte[k] = alpha; btau[k] = beta; }
+            double *rr = brefl + (size_t)k * Mmax;
+            for (int i = k + 1 + threadIdx.x; i < M; i += blockDim.x)
+                rr[i] = (beta != 0.0) ? ((i == k + 1) ? x0 - alpha : vbuf[i]) : 0.0;
+        }
+        if (k % CL == rank && threadIdx.x == 0) btd[k] = rowp(k)[k];
+        __syncthreads();
+        // (b) p_i = beta * B22[i, :] . v for owned rows i > k, broadcast to the cluster
+        if (beta != 0.0) {
+            int first = k + 1 + ((rank - (k + 1)) % CL + CL) % CL;   // first owned row > k
+            for (int i = first + warp * CL; i < M; i += nwarps * CL) {
+                const double *ri = rowp(i);
+                double acc = 0.0;
+                for (int j = k + 1 + lane; j < M; j += 32) acc += ri[j] * hv[j];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane < CL) cluster.map_shared_rank(pbuf, lane)[i] = beta * acc;
+            }
+        }
+        cluster.sync();
+        if (beta != 0.0) {
+            // (c) w = p - (beta p.v / 2) v ; B22 -= v w^T + w v^T on owned rows
+            double pv = 0.0;
+            for (int i = k + 1 + threadIdx.x; i < M; i += blockDim.x) pv += pbuf[i] * hv[i];
+            double Kc = 0.5 * beta * block_sum(pv, red);
+            for (int i = k + 1 + threadIdx.x; i < M; i += blockDim.x) wv[i] = pbuf[i] - Kc * hv[i];
+            __syncthreads();
+            int first = k + 1 + ((rank - (k + 1)) % CL + CL) % CL;
+            for (int i = first + warp * CL; i < M; i += nwarps * CL) {
+                double *ri = rowp(i);
+                const double hi = hv[i], wi = wv[i];
+                for (int j = k + 1 + lane; j < M; j += 32) ri[j] -= hi * wv[j] + wi * hv[j];
+            }
+            __syncthreads();
+        }
+        // (d) broadcast column k+1 (rows >= k+2) for the next step
+        {
+            int first = k + 2 + ((rank - (k + 2)) % CL + CL) % CL;
+            for (int i = first + threadIdx.x * CL; i < M; i += blockDim.x * CL) {
+                double v = rowp(i)[k + 1];
+                for (int r = 0; r < CL; r++) cluster.map_shared_rank(vbuf, r)[i] = v;
+            }
+        }
+        cluster.sync();
+    }
+    // trailing 2x2 (or 1x1)
+    if (threadIdx.x == 0) {
+        if (M >= 2) {
+            if ((M - 2) % CL == rank) btd[M - 2] = rowp(M - 2)[M - 2];
+            if ((M - 1) % CL == rank) { btd[M - 1] = rowp(M - 1)[M - 1]; bte[M - 2] = rowp(M - 1)[M - 2]; }
+        } else if (rank == 0) {
+            btd[0] = rowp(0)[0];
+        }
+        if (rank == 0) { bte[M - 1] = 0.0; if (M >= 2) btau[M - 2] = 0.0; btau[M - 1] = 0.0; }
+    }
+    cluster.sync();   // keep every CTA's shared memory alive until remote writes are done
+}
+
+// ---- tridiagonal helpers -------------------------------------------------------------------
+
+__device__ __forceinline__ int sturm_count(const double *d, const double *e2, int M, double x,
+                                           double pivmin)
+{
+    double q = d[0] - x;
+    if (fabs(q) < pivmin) q = -pivmin;
+    int cnt = q < 0.0;
+    for (int i = 1; i < M; i++) {
+        q = (d[i] - x) - e2[i - 1] / q;
+        if (fabs(q) < pivmin) q = -pivmin;
+        cnt += q < 0.0;
+    }
+    return cnt;
+}
+
+// Grid (ceil(mmax / 128), nb). Eigenvalue at ascending position (k0 - s + t) of T_b, t < m_b.
+__global__ void k_bisect(const int32_t *__restrict__ plan, int32_t nb, int32_t Mmax, int32_t mmax,
+                         const double *__restrict__ td, const double *__restrict__ te,
+                         double *__restrict__ sel_val)
+{
+    const int b = blockIdx.y;
+    const int k0 = plan[b], mb = plan[nb + b], s = plan[2 * nb + b], M = plan[3 * nb + b];
+    extern __shared__ double smd[];
+    double *d = smd, *e2 = smd + Mmax;
+    __shared__ double s_lo, s_hi, s_piv, s_atol;
+    const double *bd = td + (size_t)b * Mmax, *be = te + (size_t)b * Mmax;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        d[i] = bd[i];
+        e2[i] = (i + 1 < M) ? be[i] * be[i] : 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double lo = INFINITY, hi = -INFINITY, emax2 = 0.0;
+        for (int i = 0; i < M; i++) {
+            double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < M ? fabs(be[i]) : 0.0);
+            lo = fmin(lo, d[i] - r);
+            hi = fmax(hi, d[i] + r);
+            if (i + 1 < M) emax2 = fmax(emax2, e2[i]);
+        }
+        double span = fmax(fabs(lo), fabs(hi));
+        s_lo = lo - 2.0 * DBL_EPSILON * span - DBL_MIN;
+        s_hi = hi + 2.0 * DBL_EPSILON * span + DBL_MIN;
+        s_piv = DBL_MIN * fmax(1.0, emax2);
+        s_atol = DBL_EPSILON * span;   // absolute accuracy of any backward-stable solver
+    }
+    __syncthreads();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= mb) return;
+    const int pos = k0 - s + t;
+    double lo = s_lo, hi = s_hi;
+    for (int it = 0; it < 256; it++) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + s_atol) break;
+        if (sturm_count(d, e2, M, mid, s_piv) > pos) hi = mid; else lo = mid;
+    }
+    sel_val[(size_t)b * mmax + t] = 0.5 * (lo + hi);
+}
+
+__device__ __forceinline__ double hash_unit(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint64_t z = ((uint64_t)a << 42) ^ ((uint64_t)b << 21) ^ (uint64_t)c;
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return ((double)(z >> 11) * 0x1.0p-53) * 2.0 - 1.0;   // (-1, 1)
+}
+
+// Grid (ceil(mmax / 64), nb), 64 threads. Thread t computes the unit eigenvector of T_b for the
+// selected eigenvalue t. Members of a cluster (consecutive selected eigenvalues closer than
+// gaptol) are computed one after another by the cluster's first thread and orthogonalised
+// against each other (modified Gram-Schmidt) after every solve.
+__global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int32_t Mmax,
+                               int32_t mmax, const double *__restrict__ td,
+                               const double *__restrict__ te, const double *__restrict__ sel_val,
+                               double *__restrict__ sel_vec, double *__restrict__ work)
+{
+    const int b = blockIdx.y;
+    const int mb = plan[nb + b], M = plan[3 * nb + b];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= mb) return;
+    const double *d = td + (size_t)b * Mmax, *e = te + (size_t)b * Mmax;
+    const double *lam = sel_val + (size_t)b * mmax;
+    double tnorm = 0.0;
+    for (int i = 0; i < M; i++)
+        tnorm = fmax(tnorm, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < M ? fabs(e[i]) : 0.0));
+    const double gaptol = 1e-9 * fmax(tnorm, DBL_MIN);
+    if (t > 0 && lam[t] - lam[t - 1] < gaptol) return;     // handled by the cluster's first thread
+    const size_t stride = (size_t)nb * mmax;                 // interleaved per-thread storage
+    const size_t me = (size_t)b * mmax + t;
+    double *u0 = work + me, *u1 = work + stride * Mmax + me, *u2 = work + 2 * stride * Mmax + me;
+    double *lm = work + 3 * stride * Mmax + me, *pv = work + 4 * stride * Mmax + me;
+    const double pert = DBL_EPSILON * fmax(tnorm, DBL_MIN);
+    int last = t;
+    while (last + 1 < mb && lam[last + 1] - lam[last] < gaptol) last++;
+    for (int j = t; j <= last; j++) {
+        const double x = lam[j];
+        double *z = sel_vec + ((size_t)b * mmax + j) * Mmax;
+        // pivoted LU of T - x I: rows (p, q, r) = entries at columns (i, i+1, i+2)
+        double p = d[0] - x, q = (M > 1) ? e[0] : 0.0, r = 0.0;
+        for (int i = 0; i + 1 < M; i++) {
+            double ei = e[i], an = d[i + 1] - x, en = (i + 2 < M) ? e[i + 1] : 0.0;
+            if (fabs(p) >= fabs(ei)) {
+                double l = (p != 0.0) ? ei / p : 0.0;
+                u0[i * stride] = (p != 0.0) ? p : pert; u1[i * stride] = q; u2[i * stride] = r;
+                lm[i * stride] = l; pv[i * stride] = 0.0;
+                p = an - l * q; q = en - l * r; r = 0.0;
+            } else {
+                double l = p / ei;
+                u0[i * stride] = ei; u1[i * stride] = an; u2[i * stride] = en;
+                lm[i * stride] = l; pv[i * stride] = 1.0;
+                double np = q - l * an, nq = r - l * en;
+                p = np; q = nq; r = 0.0;
+            }
+        }
+        u0[(size_t)(M - 1) * stride] = (p != 0.0) ? p : pert;
+        for (int i = 0; i < M; i++) z[i] = hash_unit(b, j, i);
+        for (int it = 0; it < 3; it++) {
+            // forward: replay the row operations on the right-hand side
+            for (int i = 0; i + 1 < M; i++) {
+                double zi = z[i], zn = z[i + 1], l = lm[i * stride];
+                if (pv[i * stride] != 0.0) { z[i] = zn; z[i + 1] = zi - l * zn; }
+                else z[i + 1] = zn - l * zi;
+            }
+            // back substitution with the three upper diagonals
+            for (int i = M - 1; i >= 0; i--) {
+                double acc = z[i];
+                if (i + 1 < M) acc -= u1[i * stride] * z[i + 1];
+                if (i + 2 < M) acc -= u2[i * stride] * z[i + 2];
+                double piv = u0[i * stride];
+                if (fabs(piv) < pert) piv = (piv < 0.0) ? -pert : pert;
+                z[i] = acc / piv;
+            }
+            // orthogonalise against earlier cluster members, then normalise
+            for (int c = t; c < j; c++) {
+                const double *zc = sel_vec + ((size_t)b * mmax + c) * Mmax;
+                double dot = 0.0;
+                for (int i = 0; i < M; i++) dot += zc[i] * z[i];
+                for (int i = 0; i < M; i++) z[i] -= dot * zc[i];
+            }
+            double mx = 0.0;
+            for (int i = 0; i < M; i++) mx = fmax(mx, fabs(z[i]));
+            if (mx == 0.0 || !isfinite(mx)) { for (int i = 0; i < M; i++) z[i] = hash_unit(b, j + 7919, i + it); continue; }
+            double nrm = 0.0;
+            for (int i = 0; i < M; i++) { z[i] /= mx; nrm += z[i] * z[i]; }
+            nrm = 1.0 / sqrt(nrm);
+            for (int i = 0; i < M; i++) z[i] *= nrm;
+        }
+    }
+}
+
+// One warp per start vector: y = H_0 H_1 ... H_{M-3} z, then the sign rule, zero padding to
+// length N, the shift eps and the step alpha. Grid (ceil(mmax / 8), nb), 256 threads.
+__global__ void k_backtransform(const int32_t *__restrict__ plan, int32_t nb, int64_t N,
+                                int32_t Mmax, int32_t mmax, const double *__restrict__ refl,
+                                const double *__restrict__ tau, const double *__restrict__ sel_val,
+                                const double *__restrict__ sel_vec, const double *__restrict__ gersh,
+                                double alpha_theta, double *__restrict__ X,
+                                double *__restrict__ eps, double *__restrict__ alpha)
+{
+    const int b = blockIdx.y;
+    const int k0 = plan[b], mb = plan[nb + b], s = plan[2 * nb + b], M = plan[3 * nb + b];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x * (blockDim.x >> 5) + warp;
+    extern __shared__ double smz[];
+    double *z = smz + (size_t)warp * Mmax;
+    if (t >= mb) return;
+    const double *src = sel_vec + ((size_t)b * mmax + t) * Mmax;
+    for (int i = lane; i < M; i += 32) z[i] = src[i];
+    __syncwarp();
+    const double *brefl = refl + (size_t)b * Mmax * Mmax;
+    const double *btau = tau + (size_t)b * Mmax;
+    for (int k = M - 3; k >= 0; k--) {
+        const double bk = btau[k];
+        if (bk == 0.0) continue;
+        const double *v = brefl + (size_t)k * Mmax;
+        double dot = 0.0;
+        for (int i = k + 1 + lane; i < M; i += 32) dot += v[i] * z[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        const double f = bk * dot;
+        for (int i = k + 1 + lane; i < M; i += 32) z[i] -= f * v[i];
+        __syncwarp();
+    }
+    // sign rule: home component positive when |y_home| >= 0.1, else the largest component
+    const int home = k0 - s + t;
+    double best = -1.0;
+    int arg = M;
+    for (int i = lane; i < M; i += 32) {
+        double a = fabs(z[i]);
+        if (a > best) { best = a; arg = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oa = __shfl_xor_sync(0xffffffffu, arg, o);
+        if (ob > best || (ob == best && oa < arg)) { best = ob; arg = oa; }
+    }
+    const double yh = z[home];
+    const double ref = (fabs(yh) >= 0.1) ? yh : z[arg];
+    const double flip = (ref < 0.0) ? -1.0 : 1.0;
+    const int64_t kg = k0 + t;
+    double *xr = X + kg * N;
+    for (int64_t j = lane; j < N; j += 32) {
+        int64_t li = j - s;
+        xr[j] = (li >= 0 && li < M) ? flip * z[li] : 0.0;
+    }
+    if (lane == 0) {
+        const double lam = sel_val[(size_t)b * mmax + t];
+        const double glo = gersh[2 * N], ghi = gersh[2 * N + 1];
+        const double dmax = fmax(ghi - lam, lam - glo);
+        const double a = alpha_theta / (dmax * dmax);
+        const double cap = 1.0 - 0x1.0p-20;
+        eps[kg] = lam;
+        alpha[kg] = (a < cap) ? a : cap;
+    }
+}
+
+cudaError_t configure_kernels(pfsm_handle_s *h)
+{
+    const int Mmax = h->Mmax, CL = h->cl;
+    const int R = (Mmax + CL - 1) / CL;
+    size_t smem = (size_t)(4 * Mmax + 64) * sizeof(double);
+    if (h->rows_in_smem) smem += (size_t)R * Mmax * sizeof(double);
+    cudaError_t e;
+    if (h->rows_in_smem) {
+        if ((e = cudaFuncSetAttribute(k_tridiag<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+        if (CL > 8 && (e = cudaFuncSetAttribute(k_tridiag<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
+    } else {
+        if ((e = cudaFuncSetAttribute(k_tridiag<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+        if (CL > 8 && (e = cudaFuncSetAttribute(k_tridiag<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
+    }
+    if ((e = cudaFuncSetAttribute(k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * Mmax * sizeof(double)))) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * Mmax * sizeof(double)));
+}
+
+cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
+{
+    Workspace &w = h->ws;
+    const int nb = h->nb, Mmax = h->Mmax, mmax = h->mmax, CL = h->cl;
+    // 1. tridiagonalisation, one cluster per window
+    {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(nb * CL));
+        cfg.blockDim = dim3(kTriThreads);
+        const int R = (Mmax + CL - 1) / CL;
+        size_t smem = (size_t)(4 * Mmax + 64) * sizeof(double);
+        if (h->rows_in_smem) smem += (size_t)R * Mmax * sizeof(double);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CL;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t e;
+        if (h->rows_in_smem)
+            e = cudaLaunchKernelEx(&cfg, k_tridiag<true>, A, h->N, (const int32_t *)w.plan, nb, Mmax,
+                                   (double *)nullptr, w.refl, w.tau, w.td, w.te);
+        else
+            e = cudaLaunchKernelEx(&cfg, k_tridiag<false>, A, h->N, (const int32_t *)w.plan, nb, Mmax,
+                                   w.iiwork, w.refl, w.tau, w.td, w.te);
+        if (e != cudaSuccess) return e;
+    }
+    // 2. bisection
+    {
+        dim3 grid((unsigned)((mmax + 127) / 128), (unsigned)nb);
+        k_bisect<<<grid, 128, (size_t)2 * Mmax * sizeof(double), st>>>(w.plan, nb, Mmax, mmax, w.td, w.te, w.sel_val);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    // 3. inverse iteration
+    {
+        dim3 grid((unsigned)((mmax + 63) / 64), (unsigned)nb);
+        k_inverse_iter<<<grid, 64, 0, st>>>(w.plan, nb, Mmax, mmax, w.td, w.te, w.sel_val, w.sel_vec, w.iiwork);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    // 4. back-transform + start vectors
+    {
+        dim3 grid((unsigned)((mmax + 7) / 8), (unsigned)nb);
+        k_backtransform<<<grid, 256, (size_t)8 * Mmax * sizeof(double), st>>>(
+            w.plan, nb, h->N, Mmax, mmax, w.refl, w.tau, w.sel_val, w.sel_vec, w.gersh,
+            h->prm.alpha_theta, w.X, w.eps, w.alpha);
+        return cudaGetLastError();
+    }
+}
+
+}  // namespace pfsm
