@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""PFSM benchmark: solves/s (and algorithmic TFLOP/s) of the partitioned folded spectrum method
+on the diamond-cell-like workload (N = 1280 = 1024 occupied + 256 unoccupied bands, 10 slices of
+128 with windows of 384, K = 3 iterations of Eq. 11, SCF step 0 of the seeded sequence).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--precision fp64]
+
+One JSON line on rank 0. The timed steps run on device-resident inputs with L2 flushed between
+steps (a 256 MiB write, outside the per-step CUDA events). `e2e` repeats the measurement through
+the C ABI with host buffers: pinned host -> device copy of A and prev, the solve, and the device ->
+host copy of eigenvalues and eigenvectors, all inside the timed region. Under torchrun every rank
+solves its own replica (the method does not shard one matrix across GPUs on this path).
+
+`--impl reference` times the FP64 CPU oracle (plain loops, OpenMP over independent units) on the
+same workload, rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PFSM solves/s & TFLOP/s vs plain FP64 GPU PFSM at equal eigen-accuracy"
+FP64_NOMINAL_TFLOPS = 1.25        # B300 FP64 (DFMA) nominal rate; tcgen05 has no FP64 kind
+# DRAM traffic of one FS-GEMM launch from an ncu capture of the current kernel (bytes), or None
+# when the kernel changed since the capture (see profiles/).
+FS_GEMM_TRAFFIC = None
+
+
+def workload(n=None, nblocks=None, halo=None):
+    """The benchmarked workload; size overrides exist for profiling captures only."""
+    import workloads as wl
+    if n is None:
+        p = wl.diamond_like(0)
+        return p, {"workload": "diamond-like N=1280 (1024 occ + 256 unocc), 10 slices of 128, "
+                               "windows of 384, K=3, SCF step 0 (sigma 5e-4)",
+                   "N": p.n, "nblocks": p.nblocks, "halo": (p.n + 9) // 10, "fs_iters": p.fs_iters}
+    occ = (4 * n) // 5
+    p = wl.diamond_like(0, n_occ=occ, n_unocc=n - occ, nblocks=nblocks or max(1, n // 128))
+    if halo is not None:
+        p.halo = halo
+    h = p.halo if p.halo >= 0 else (n + 9) // 10
+    return p, {"workload": f"diamond-like N={n} ({occ} occ + {n - occ} unocc), {p.nblocks} slices, "
+                           f"halo {h}, K=3 (profiling size)",
+               "N": p.n, "nblocks": p.nblocks, "halo": h, "fs_iters": p.fs_iters}
+
+
+def algorithmic_flops(plan, n, K):
+    """Flop convention: eig sum(4/3 M^3 + 2 M^2 m) + FS 2N sum(M m) + 2N^3 + (K-1) 4N^3
+    + overlap N^3 + Cholesky N^3/3 + triangular solve N^3 + Rayleigh 2N^3."""
+    k0, m, s, M = (list(map(float, r)) for r in plan)
+    eig = sum(4.0 / 3.0 * Mb ** 3 + 2.0 * Mb * Mb * mb for mb, Mb in zip(m, M))
+    fs_first = 2.0 * n * sum(Mb * mb for mb, Mb in zip(m, M))
+    fs = (fs_first + 2.0 * n ** 3 + (K - 1) * 4.0 * n ** 3) if K > 0 else 0.0
+    gs = n ** 3 + n ** 3 / 3.0 + n ** 3
+    ray = 2.0 * n ** 3
+    return {"total": eig + fs + gs + ray, "eig": eig, "fs": fs, "gs": gs, "rayleigh": ray}
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, max, throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if "Active" in v and "Not" not in v})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_rate(p, seconds: float):
+    """Oracle solves/s on this host, repeating full solves for at least `seconds`."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    count = 0
+    while True:
+        oracle.pfsm(p.A, p.prev, p.nblocks, halo=p.halo, fs_iters=p.fs_iters, keep_xfs=False)
+        count += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            return count / el, count, el
+
+
+def threads_used():
+    env = os.environ.get("OMP_NUM_THREADS")
+    return int(env) if env and env.isdigit() else (os.cpu_count() or 1)
+
+
+def run_reference(args, cfg, p):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.pfsm(p.A, p.prev, p.nblocks, halo=p.halo, fs_iters=p.fs_iters, keep_xfs=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.pfsm(p.A, p.prev, p.nblocks, halo=p.halo, fs_iters=p.fs_iters, keep_xfs=False)
+    el = time.perf_counter() - t0
+    v = args.steps / el
+    cores = threads_used()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(cfg, precision="fp64", l2="n/a (CPU)"),
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} full oracle solves of the workload"},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", choices=("fp64",), default="fp64")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-oracle", action="store_true", help="skip the accuracy check and CPU baseline")
+    ap.add_argument("--n", type=int, default=None, help="profiling size override")
+    ap.add_argument("--nblocks", type=int, default=None)
+    ap.add_argument("--halo", type=int, default=None)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    p, cfg = workload(args.n, args.nblocks, args.halo)
+    if args.impl == "reference":
+        return run_reference(args, cfg, p)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1502_07806_b300 as pf
+    from paper_1502_07806_b300 import build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    prec = {"fp64": pf.FP64}[args.precision]
+    h = pf.Handle(p.n, p.nblocks, halo=p.halo, fs_iters=p.fs_iters, precision=prec)
+    A = torch.from_numpy(p.A).cuda()
+    prev = torch.from_numpy(p.prev).cuda()
+    lam = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    V = torch.empty(p.n, p.n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    h.set_timing(True)
+    for _ in range(args.warmup):
+        h.solve(A, prev, lam, V)
+    st = h.status()
+    if st != 0:
+        raise RuntimeError(f"device status {pf.STATUS_NAMES.get(st, st)}")
+    plan = h.diagnostic(pf.DIAG_PLAN).cpu().numpy()
+    fl = algorithmic_flops(plan, p.n, p.fs_iters)
+
+    # ---- device-resident timed steps -------------------------------------------------------
+    step_ms, phases, launches = [], [], 0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record()
+            h.solve(A, prev, lam, V)
+            ev[i][1].record()
+            prof = h.profile()          # synchronises; outside the events
+            phases.append(prof)
+            launches += prof["launches"]
+        barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1000.0
+    if world > 1:
+        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * args.steps / total_s
+    ms_per_step = 1000.0 * total_s / args.steps
+    st = h.status()
+    if st != 0:
+        raise RuntimeError(f"device status {pf.STATUS_NAMES.get(st, st)}")
+
+    # ---- end to end through the C ABI with host buffers -----------------------------------
+    hA = torch.from_numpy(p.A).pin_memory()
+    hprev = torch.from_numpy(p.prev).pin_memory()
+    hlam = torch.empty(p.n, dtype=torch.float64).pin_memory()
+    hV = torch.empty(p.n, p.n, dtype=torch.float64).pin_memory()
+    dA = torch.empty_like(A)
+    dprev = torch.empty_like(prev)
+    h.set_timing(False)
+    e2e_ms = []
+    barrier()
+    for i in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dA.copy_(hA, non_blocking=True)
+        dprev.copy_(hprev, non_blocking=True)
+        h.solve(dA, dprev, lam, V)
+        hlam.copy_(lam, non_blocking=True)
+        hV.copy_(V, non_blocking=True)
+        e1.record()
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    barrier()
+    e2e_s = sum(e2e_ms) / 1000.0
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * args.steps / e2e_s
+    h2d = p.A.nbytes + p.prev.nbytes
+    d2h = p.n * 8 + p.n * p.n * 8
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- phase breakdown and roofline of the dominant kernel -------------------------------
+    ph = {k: statistics.mean(pr[k] for pr in phases) for k in pf.PHASES[:5]}
+    fs_ms = ph["fs_iterations"]
+    fs_launches = 2 * p.fs_iters
+    achieved = fl["fs"] / (fs_ms / 1000.0) / 1e12 if fs_ms > 0 else None
+    roofline = {"kernel": "k_gemm_f64 (Eq. 11 products, fused epilogues)", "bound": "alu",
+                "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": (achieved / FP64_NOMINAL_TFLOPS) if achieved else None,
+                "traffic": FS_GEMM_TRAFFIC,
+                "per_launch": {"flops": fl["fs"] / fs_launches, "ms": fs_ms / fs_launches},
+                "peak_source": "B300 nominal FP64 (DFMA) rate; a DFMA microbenchmark measured 1.09 TFLOP/s at 1927 MHz"}
+
+    out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": dict(cfg, precision=args.precision, l2="flushed between steps (256 MiB write)",
+                          parallelism=f"replicas x{world}"),
+           "tflops": fl["total"] * value / world / 1e12,
+           "fp64_solves_per_s": value if args.precision == "fp64" else None,
+           "phases_ms": ph, "roofline": roofline,
+           "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h},
+           "gpu_launches": launches, "clocks": clk.summary()}
+
+    if not args.no_oracle and world == 1:
+        import oracle
+        ref = oracle.pfsm(p.A, p.prev, p.nblocks, halo=p.halo, fs_iters=p.fs_iters, keep_xfs=False)
+        lam_h, V_h = lam.cpu().numpy(), V.cpu().numpy()
+        scale = float(np.max(np.abs(ref.lam)))
+        d = np.sum(V_h * ref.V, axis=0)
+        proj = np.linalg.norm(ref.V - V_h * np.where(d < 0, -1.0, 1.0), axis=0) * np.sqrt(1 + np.abs(d))
+        out["accuracy"] = {"max_abs_dlambda_over_normA": float(np.max(np.abs(lam_h - ref.lam)) / scale),
+                           "max_projector_err": float(np.max(proj)), "reference": "FP64 CPU oracle"}
+        rate, count, el = oracle_rate(p, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": rate, "unit": "solves/s", "cores": threads_used(), "kind": "oracle",
+                               "sample": f"{count} full oracle solves of the workload in {el:.1f} s"}
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

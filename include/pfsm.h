@@ -134,6 +134,23 @@ int pfsm_get_status(pfsm_handle_t h, int32_t *device_status);
  * Returns PFSM_ERR_INVALID_ARG for an unknown `which`, PFSM_ERR_NO_SOLVE before a solve. */
 int pfsm_get_diagnostic(pfsm_handle_t h, int32_t which, void *out, void *stream);
 
+/* Per-call instrumentation, for benchmarks and profiling. */
+typedef struct {
+    int32_t launches;     /* kernels enqueued by the last pfsm_solve / pfsm_backward on h */
+    int32_t timed;        /* 1 when phase_ms holds measurements (timing enabled on h) */
+    float phase_ms[8];    /* CUDA-event times on the call's stream, in milliseconds:
+                             0 validation + partition plan, 1 submatrix solves + start vectors,
+                             2 Eq. 11 iterations, 3 Gram-Schmidt (overlap, Cholesky, solve),
+                             4 Rayleigh quotients, residuals and outputs, 5 backward */
+} pfsm_profile_t;
+
+/* Enables (enable != 0) or disables CUDA-event phase timing on h. Timing adds one event record
+ * per phase boundary to the stream and nothing else. */
+int pfsm_set_timing(pfsm_handle_t h, int32_t enable);
+
+/* Synchronises the stream of the last call on h and fills *out (host pointer). */
+int pfsm_get_profile(pfsm_handle_t h, pfsm_profile_t *out);
+
 /* Thread-local text of the last error raised on this thread ("" if none). */
 const char *pfsm_last_error(void);
 

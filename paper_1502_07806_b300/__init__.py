@@ -22,7 +22,9 @@ FP64, TF32_SPLIT, BF16_SPLIT = 0, 1, 2
 DIAG_RESIDUALS, DIAG_XFS, DIAG_EPS, DIAG_ALPHA, DIAG_PLAN = range(5)
 
 EXPORTED = ("pfsm_default_params", "pfsm_init", "pfsm_solve", "pfsm_backward", "pfsm_get_status",
-            "pfsm_get_diagnostic", "pfsm_last_error", "pfsm_destroy")
+            "pfsm_get_diagnostic", "pfsm_set_timing", "pfsm_get_profile", "pfsm_last_error",
+            "pfsm_destroy")
+PHASES = ("plan", "submatrix", "fs_iterations", "gram_schmidt", "rayleigh", "backward")
 
 
 class PFSMError(RuntimeError):
@@ -36,6 +38,11 @@ class Params(ctypes.Structure):
                 ("alpha_theta", ctypes.c_double), ("cluster_tol", ctypes.c_double),
                 ("degen_tol", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("recompute_v", ctypes.c_int32), ("slice_sizes", ctypes.POINTER(ctypes.c_int32))]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int32), ("timed", ctypes.c_int32),
+                ("phase_ms", ctypes.c_float * 8)]
 
 
 _lib = None
@@ -58,6 +65,8 @@ def load_library():
     lib.pfsm_backward.argtypes = [P, P, P, P, P]
     lib.pfsm_get_status.argtypes = [P, ctypes.POINTER(i32)]
     lib.pfsm_get_diagnostic.argtypes = [P, i32, P, P]
+    lib.pfsm_set_timing.argtypes = [P, i32]
+    lib.pfsm_get_profile.argtypes = [P, ctypes.POINTER(Profile)]
     lib.pfsm_last_error.argtypes = []
     lib.pfsm_last_error.restype = ctypes.c_char_p
     lib.pfsm_destroy.argtypes = [P]
@@ -142,6 +151,18 @@ class Handle:
         s = ctypes.c_int32(-1)
         _check(load_library().pfsm_get_status(self._h, ctypes.byref(s)), "pfsm_get_status")
         return s.value
+
+    def set_timing(self, enable: bool = True):
+        _check(load_library().pfsm_set_timing(self._h, int(bool(enable))), "pfsm_set_timing")
+
+    def profile(self) -> dict:
+        """Launch count and per-phase CUDA-event times (ms) of the last call on this handle."""
+        pr = Profile()
+        _check(load_library().pfsm_get_profile(self._h, ctypes.byref(pr)), "pfsm_get_profile")
+        out = {"launches": pr.launches}
+        if pr.timed:
+            out.update({name: float(pr.phase_ms[i]) for i, name in enumerate(PHASES)})
+        return out
 
     def diagnostic(self, which: int) -> torch.Tensor:
         n = self.n

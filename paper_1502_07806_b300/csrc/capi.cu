@@ -161,6 +161,13 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
         cudaGetLastError();
         return fail(code, "pfsm_init: %s", cudaGetErrorString(e));
     }
+    for (int i = 0; i < 8 && e == cudaSuccess; i++) e = cudaEventCreate(&h->ev[i]);
+    if (e != cudaSuccess) {
+        free_ws(h);
+        delete h;
+        cudaGetLastError();
+        return fail(PFSM_ERR_CUDA, "pfsm_init: %s", cudaGetErrorString(e));
+    }
     h->prm.slice_sizes = nullptr;   // the host array is not kept
     *out = h;
     return PFSM_OK;
@@ -171,11 +178,15 @@ static int solve_impl(pfsm_handle_s *h, const double *A, const double *prev, dou
 {
     Workspace &w = h->ws;
     const int64_t N = h->N;
+    auto mark = [&](int i) -> cudaError_t { return h->timing ? cudaEventRecord(h->ev[i], st) : cudaSuccess; };
     PFSM_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int32_t), st));
+    PFSM_CUDA(mark(0));
     PFSM_CUDA(launch_validate_gersh(A, prev, N, w.gersh, w.status, st));
     PFSM_CUDA(launch_plan(prev, N, h->nb, h->halo, h->prm.cluster_tol, w.slices, w.plan,
                           w.tile_krange, w.gersh, w.status, st));
+    PFSM_CUDA(mark(1));
     PFSM_CUDA(launch_subeig(h, A, st));
+    PFSM_CUDA(mark(2));
     // Eq. 11, fs_iters times: Y = (A - eps I) X ; X <- X - alpha (A - eps I) Y
     for (int it = 0; it < h->prm.fs_iters; it++) {
         GemmArgs g{};
@@ -190,9 +201,12 @@ static int solve_impl(pfsm_handle_s *h, const double *A, const double *prev, dou
         u.aux_y = w.Y; u.eps = w.eps; u.alpha = w.alpha;
         PFSM_CUDA(launch_gemm_f64(u, EPI_FS2, Q_KMAJOR, st));
     }
+    PFSM_CUDA(mark(3));
     PFSM_CUDA(cudaMemcpyAsync(w.Xfs, w.X, (size_t)N * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
     PFSM_CUDA(launch_gram_schmidt_f64(h, st));
+    PFSM_CUDA(mark(4));
     PFSM_CUDA(launch_rayleigh_f64(h, A, eigvals_out, V_out, st));
+    PFSM_CUDA(mark(5));
     h->solved = true;
     h->last_A = A;
     h->last_prev = prev;
@@ -206,7 +220,11 @@ int pfsm_solve(pfsm_handle_t h, const double *A, const double *prev_eigvals, dou
     if (!h) return fail(PFSM_ERR_INVALID_ARG, "pfsm_solve: null handle");
     if (!A || !prev_eigvals || !eigvals_out || !V_out)
         return fail(PFSM_ERR_INVALID_ARG, "pfsm_solve: null buffer");
-    return solve_impl(h, A, prev_eigvals, eigvals_out, V_out, (cudaStream_t)stream);
+    g_launches = 0;
+    int rc = solve_impl(h, A, prev_eigvals, eigvals_out, V_out, (cudaStream_t)stream);
+    h->last_launches = (int32_t)g_launches;
+    h->last_was_backward = false;
+    return rc;
 }
 
 int pfsm_backward(pfsm_handle_t h, const double *dLambda, const double *dV, double *dA_out,
@@ -216,13 +234,18 @@ int pfsm_backward(pfsm_handle_t h, const double *dLambda, const double *dV, doub
     if (!dA_out) return fail(PFSM_ERR_INVALID_ARG, "pfsm_backward: null dA_out");
     if (!h->solved) return fail(PFSM_ERR_NO_SOLVE, "pfsm_backward: no solve on this handle yet");
     cudaStream_t st = (cudaStream_t)stream;
+    g_launches = 0;
     if (h->prm.recompute_v) {
         // rebuild (lambda, V) from the last inputs; outputs land in the handle's own buffers
         int rc = solve_impl(h, h->last_A, h->last_prev, h->ws.lam, h->ws.Vrm, st);
         if (rc != PFSM_OK) return rc;
     }
+    if (h->timing) PFSM_CUDA(cudaEventRecord(h->ev[6], st));
     PFSM_CUDA(launch_backward_f64(h, dLambda, dV, dA_out, st));
+    if (h->timing) PFSM_CUDA(cudaEventRecord(h->ev[7], st));
     h->last_stream = st;
+    h->last_launches = (int32_t)g_launches;
+    h->last_was_backward = true;
     return PFSM_OK;
 }
 
@@ -258,10 +281,35 @@ int pfsm_get_diagnostic(pfsm_handle_t h, int32_t which, void *out, void *stream)
     return PFSM_OK;
 }
 
+int pfsm_set_timing(pfsm_handle_t h, int32_t enable)
+{
+    if (!h) return fail(PFSM_ERR_INVALID_ARG, "pfsm_set_timing: null handle");
+    h->timing = enable != 0;
+    return PFSM_OK;
+}
+
+int pfsm_get_profile(pfsm_handle_t h, pfsm_profile_t *out)
+{
+    if (!h || !out) return fail(PFSM_ERR_INVALID_ARG, "pfsm_get_profile: null argument");
+    std::memset(out, 0, sizeof(*out));
+    out->launches = h->last_launches;
+    if (!h->timing || !h->solved) return PFSM_OK;
+    PFSM_CUDA(cudaStreamSynchronize(h->last_stream));
+    auto span = [&](int a, int b, float *dst) -> cudaError_t { return cudaEventElapsedTime(dst, h->ev[a], h->ev[b]); };
+    const bool fwd = !h->last_was_backward || h->prm.recompute_v;
+    if (fwd)
+        for (int i = 0; i < 5; i++) PFSM_CUDA(span(i, i + 1, &out->phase_ms[i]));
+    if (h->last_was_backward) PFSM_CUDA(span(6, 7, &out->phase_ms[5]));
+    out->timed = 1;
+    return PFSM_OK;
+}
+
 int pfsm_destroy(pfsm_handle_t h)
 {
     if (!h) return PFSM_OK;
     cudaDeviceSynchronize();
+    for (int i = 0; i < 8; i++)
+        if (h->ev[i]) cudaEventDestroy(h->ev[i]);
     free_ws(h);
     delete h;
     return PFSM_OK;

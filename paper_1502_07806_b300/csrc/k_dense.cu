@@ -123,14 +123,14 @@ cudaError_t launch_gram_schmidt_f64(pfsm_handle_s *h, cudaStream_t st)
     g.rows = N; g.cols = N; g.K = N;
     g.P = w.X; g.ldp = N; g.Q = w.X; g.ldq = N; g.C = w.S; g.ldc = N; g.lower_only = 1;
     if ((e = launch_gemm_f64(g, EPI_STORE, Q_KMAJOR, st)) != cudaSuccess) return e;
-    k_copy_diag<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(w.S, N, w.sdiag);
+    k_copy_diag<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(w.S, N, w.sdiag); g_launches++;
     // Cholesky
     for (int64_t jb = 0; jb < N; jb += CB) {
         const int b = (int)((N - jb) < CB ? (N - jb) : CB);
-        k_potrf_diag<<<1, 256, 0, st>>>(w.S, N, jb, b, w.sdiag, w.status);
+        k_potrf_diag<<<1, 256, 0, st>>>(w.S, N, jb, b, w.sdiag, w.status); g_launches++;
         const int64_t rest = N - jb - b;
         if (rest <= 0) break;
-        k_trsm_panel<<<(unsigned)((rest + kPanelRows - 1) / kPanelRows), 128, 0, st>>>(w.S, N, jb, b);
+        k_trsm_panel<<<(unsigned)((rest + kPanelRows - 1) / kPanelRows), 128, 0, st>>>(w.S, N, jb, b); g_launches++;
         GemmArgs u{};
         u.rows = rest; u.cols = rest; u.K = b;
         u.P = w.S + (jb + b) * N + jb; u.ldp = N;
@@ -141,7 +141,7 @@ cudaError_t launch_gram_schmidt_f64(pfsm_handle_s *h, cudaStream_t st)
     // V = L^-1 X (rows)
     for (int64_t jb = 0; jb < N; jb += CB) {
         const int b = (int)((N - jb) < CB ? (N - jb) : CB);
-        k_trsm_diag_rows<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(w.S, w.X, N, jb, b);
+        k_trsm_diag_rows<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(w.S, w.X, N, jb, b); g_launches++;
         const int64_t rest = N - jb - b;
         if (rest <= 0) break;
         GemmArgs u{};
@@ -205,7 +205,7 @@ __global__ void k_transpose(const double *__restrict__ in, double *__restrict__ 
 cudaError_t launch_transpose(const double *in, double *out, int64_t N, cudaStream_t st)
 {
     dim3 grid((unsigned)((N + 31) / 32), (unsigned)((N + 31) / 32));
-    k_transpose<<<grid, dim3(32, 8), 0, st>>>(in, out, N);
+    k_transpose<<<grid, dim3(32, 8), 0, st>>>(in, out, N); g_launches++;
     return cudaGetLastError();
 }
 
@@ -219,7 +219,7 @@ cudaError_t launch_rayleigh_f64(pfsm_handle_s *h, const double *A, double *eigva
     g.rows = N; g.cols = N; g.K = N;
     g.P = w.X; g.ldp = N; g.Q = A; g.ldq = N; g.C = w.W; g.ldc = N;
     if ((e = launch_gemm_f64(g, EPI_STORE, Q_KMAJOR, st)) != cudaSuccess) return e;
-    k_rayleigh_rows<<<(unsigned)N, 256, 0, st>>>(w.X, w.W, N, w.lam, w.res);
+    k_rayleigh_rows<<<(unsigned)N, 256, 0, st>>>(w.X, w.W, N, w.lam, w.res); g_launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_transpose(w.X, w.Vrm, N, st)) != cudaSuccess) return e;
     if (eigvals_out != w.lam &&
@@ -274,7 +274,7 @@ cudaError_t launch_backward_f64(pfsm_handle_s *h, const double *dLambda, const d
         if ((e = cudaMemsetAsync(w.S, 0, (size_t)N * N * sizeof(double), st)) != cudaSuccess) return e;
     }
     dim3 gm((unsigned)((N + 255) / 256), (unsigned)N);
-    k_adjoint_mix<<<gm, 256, 0, st>>>(w.S, N, w.lam, dLambda, h->prm.degen_tol);
+    k_adjoint_mix<<<gm, 256, 0, st>>>(w.S, N, w.lam, dLambda, h->prm.degen_tol); g_launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // Ut[j, k] = sum_l V[j, l] M[k, l]
     GemmArgs u{};
@@ -286,7 +286,7 @@ cudaError_t launch_backward_f64(pfsm_handle_s *h, const double *dLambda, const d
     d.rows = N; d.cols = N; d.K = N;
     d.P = w.Vrm; d.ldp = N; d.Q = w.Y; d.ldq = N; d.C = dA_out; d.ldc = N;
     if ((e = launch_gemm_f64(d, EPI_STORE, Q_KMAJOR, st)) != cudaSuccess) return e;
-    k_symmetrize<<<gm, 256, 0, st>>>(dA_out, N);
+    k_symmetrize<<<gm, 256, 0, st>>>(dA_out, N); g_launches++;
     return cudaGetLastError();
 }
 

@@ -130,7 +130,7 @@ cudaError_t launch_gemm_f64(const GemmArgs &a, int epi, int qlayout, cudaStream_
     if (a.rows <= 0 || a.cols <= 0) return cudaSuccess;
     dim3 grid((unsigned)((a.cols + BN - 1) / BN), (unsigned)((a.rows + BM - 1) / BM));
 #define PFSM_GEMM_CASE(E, Q) \
-    if (epi == E && qlayout == Q) { k_gemm_f64<E, Q><<<grid, 256, 0, st>>>(a); return cudaGetLastError(); }
+    if (epi == E && qlayout == Q) { k_gemm_f64<E, Q><<<grid, 256, 0, st>>>(a); g_launches++; return cudaGetLastError(); }
     PFSM_GEMM_CASE(EPI_STORE, Q_KMAJOR)
     PFSM_GEMM_CASE(EPI_SUB, Q_KMAJOR)
     PFSM_GEMM_CASE(EPI_FS1, Q_KMAJOR)

@@ -135,7 +135,7 @@ cudaError_t launch_validate_gersh(const double *A, const double *prev, int64_t N
 {
     const int warps = 8;
     dim3 grid((unsigned)((N + warps - 1) / warps));
-    k_validate_gersh<<<grid, warps * 32, 0, st>>>(A, prev, N, gersh, status);
+    k_validate_gersh<<<grid, warps * 32, 0, st>>>(A, prev, N, gersh, status); g_launches++;
     return cudaGetLastError();
 }
 
@@ -144,7 +144,7 @@ cudaError_t launch_plan(const double *prev, int64_t N, int32_t nb, int32_t halo,
                         double *gersh, int32_t *status, cudaStream_t st)
 {
     (void)status;
-    k_plan<<<1, 1024, 0, st>>>(prev, N, nb, halo, cluster_tol, slice_sizes_dev, plan, tile_krange, gersh);
+    k_plan<<<1, 1024, 0, st>>>(prev, N, nb, halo, cluster_tol, slice_sizes_dev, plan, tile_krange, gersh); g_launches++;
     return cudaGetLastError();
 }
 

@@ -416,24 +416,24 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
         cfg.numAttrs = 1;
         cudaError_t e;
         if (h->rows_in_smem)
-            e = cudaLaunchKernelEx(&cfg, k_tridiag<true>, A, h->N, (const int32_t *)w.plan, nb, Mmax,
-                                   (double *)nullptr, w.refl, w.tau, w.td, w.te);
+            e = counted(cudaLaunchKernelEx(&cfg, k_tridiag<true>, A, h->N, (const int32_t *)w.plan, nb, Mmax,
+                                   (double *)nullptr, w.refl, w.tau, w.td, w.te));
         else
-            e = cudaLaunchKernelEx(&cfg, k_tridiag<false>, A, h->N, (const int32_t *)w.plan, nb, Mmax,
-                                   w.iiwork, w.refl, w.tau, w.td, w.te);
+            e = counted(cudaLaunchKernelEx(&cfg, k_tridiag<false>, A, h->N, (const int32_t *)w.plan, nb, Mmax,
+                                   w.iiwork, w.refl, w.tau, w.td, w.te));
         if (e != cudaSuccess) return e;
     }
     // 2. bisection
     {
         dim3 grid((unsigned)((mmax + 127) / 128), (unsigned)nb);
-        k_bisect<<<grid, 128, (size_t)2 * Mmax * sizeof(double), st>>>(w.plan, nb, Mmax, mmax, w.td, w.te, w.sel_val);
+        k_bisect<<<grid, 128, (size_t)2 * Mmax * sizeof(double), st>>>(w.plan, nb, Mmax, mmax, w.td, w.te, w.sel_val); g_launches++;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     // 3. inverse iteration
     {
         dim3 grid((unsigned)((mmax + 63) / 64), (unsigned)nb);
-        k_inverse_iter<<<grid, 64, 0, st>>>(w.plan, nb, Mmax, mmax, w.td, w.te, w.sel_val, w.sel_vec, w.iiwork);
+        k_inverse_iter<<<grid, 64, 0, st>>>(w.plan, nb, Mmax, mmax, w.td, w.te, w.sel_val, w.sel_vec, w.iiwork); g_launches++;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -442,7 +442,7 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
         dim3 grid((unsigned)((mmax + 7) / 8), (unsigned)nb);
         k_backtransform<<<grid, 256, (size_t)8 * Mmax * sizeof(double), st>>>(
             w.plan, nb, h->N, Mmax, mmax, w.refl, w.tau, w.sel_val, w.sel_vec, w.gersh,
-            h->prm.alpha_theta, w.X, w.eps, w.alpha);
+            h->prm.alpha_theta, w.X, w.eps, w.alpha); g_launches++;
         return cudaGetLastError();
     }
 }

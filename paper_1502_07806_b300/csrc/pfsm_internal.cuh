@@ -64,11 +64,20 @@ struct pfsm_handle_s {
     bool solved = false;
     const double *last_A = nullptr;
     const double *last_prev = nullptr;
+    // instrumentation
+    bool timing = false;
+    cudaEvent_t ev[8] = {};
+    int32_t last_launches = 0;
+    bool last_was_backward = false;
 };
 
 namespace pfsm {
 
 constexpr int kFsTileRows = 64;     // row tile of the FP64 GEMM (also the K-range granularity)
+
+// Kernels enqueued by this host thread since the counter was last reset (instrumentation).
+inline thread_local int64_t g_launches = 0;
+inline cudaError_t counted(cudaError_t e) { if (e == cudaSuccess) g_launches++; return e; }
 
 // ---- launchers (each enqueues on `st`; returns cudaGetLastError()) ----
 cudaError_t launch_validate_gersh(const double *A, const double *prev, int64_t N, double *gersh,
