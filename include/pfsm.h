@@ -134,6 +134,27 @@ int pfsm_get_status(pfsm_handle_t h, int32_t *device_status);
  * Returns PFSM_ERR_INVALID_ARG for an unknown `which`, PFSM_ERR_NO_SOLVE before a solve. */
 int pfsm_get_diagnostic(pfsm_handle_t h, int32_t which, void *out, void *stream);
 
+/* Eq. 11 on caller vectors WITHOUT ANY DEVICE ALLOCATION. The paper has no counterpart; this
+ * entry point exists for callers that cannot allocate device memory when they call the
+ * library, e.g. codes that reserve all device memory up front for their own pool, or
+ * latency-critical loops where the device-wide synchronisation of cudaMalloc/cudaFree would
+ * stall other streams.
+ *   N       order of A
+ *   count   number of vectors; count * N must not exceed 1048576 (8 MiB of FP64 scratch),
+ *           otherwise the call returns PFSM_ERR_INVALID_ARG without touching the GPU
+ *   A       device, N x N FP64, symmetric
+ *   X       device, count x N FP64, ROW k = vector k (note: rows, unlike V_out); updated in
+ *           place with `iters` iterations x <- x - alpha_k (A - eps_k I)^2 x
+ *   eps, alpha  device, count FP64 shifts and steps
+ * The only scratch, (A - eps I) X between the two products of each iteration, lives in one
+ * fixed 8 MiB device array that every GPU loading this library holds until the process exits.
+ * The first call on a device looks up that array's device address (cudaGetSymbolAddress), so
+ * make the first call on each device outside any stream capture. All calls share the array:
+ * calls that may overlap on the GPU (different streams, or several host threads) race on it and
+ * must be serialised by the caller. Nothing in it needs clearing between calls. */
+int pfsm_fs_iterate_noalloc(int64_t N, int64_t count, const double *A, double *X,
+                            const double *eps, const double *alpha, int32_t iters, void *stream);
+
 /* Per-call instrumentation, for benchmarks and profiling. */
 typedef struct {
     int32_t launches;     /* kernels enqueued by the last pfsm_solve / pfsm_backward on h */

@@ -23,7 +23,7 @@ DIAG_RESIDUALS, DIAG_XFS, DIAG_EPS, DIAG_ALPHA, DIAG_PLAN = range(5)
 
 EXPORTED = ("pfsm_default_params", "pfsm_init", "pfsm_solve", "pfsm_backward", "pfsm_get_status",
             "pfsm_get_diagnostic", "pfsm_set_timing", "pfsm_get_profile", "pfsm_last_error",
-            "pfsm_destroy")
+            "pfsm_destroy", "pfsm_fs_iterate_noalloc")
 PHASES = ("plan", "submatrix", "fs_iterations", "gram_schmidt", "rayleigh", "backward")
 
 
@@ -65,6 +65,7 @@ def load_library():
     lib.pfsm_backward.argtypes = [P, P, P, P, P]
     lib.pfsm_get_status.argtypes = [P, ctypes.POINTER(i32)]
     lib.pfsm_get_diagnostic.argtypes = [P, i32, P, P]
+    lib.pfsm_fs_iterate_noalloc.argtypes = [i64, i64, P, P, P, P, i32, P]
     lib.pfsm_set_timing.argtypes = [P, i32]
     lib.pfsm_get_profile.argtypes = [P, ctypes.POINTER(Profile)]
     lib.pfsm_last_error.argtypes = []
@@ -177,6 +178,17 @@ class Handle:
         if which == DIAG_PLAN:
             return out.view(torch.int32)[: 4 * self.nblocks].reshape(4, self.nblocks)
         return out
+
+
+def fs_iterate_noalloc(A: torch.Tensor, X_rows: torch.Tensor, eps: torch.Tensor,
+                       alpha: torch.Tensor, iters: int) -> torch.Tensor:
+    """Eq. 11 in place on the rows of X_rows (count x N) with no device allocation in the
+    library (its scratch is a fixed 8 MiB device array; count * N <= 2^20)."""
+    n, count = A.shape[0], X_rows.shape[0]
+    _check(load_library().pfsm_fs_iterate_noalloc(n, count, _ptr(A), _ptr(X_rows), _ptr(eps),
+                                                  _ptr(alpha), iters, _stream()),
+           "pfsm_fs_iterate_noalloc")
+    return X_rows
 
 
 def solve(A: torch.Tensor, prev: torch.Tensor, nblocks: int, **kw):
