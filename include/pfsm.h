@@ -134,6 +134,17 @@ int pfsm_get_status(pfsm_handle_t h, int32_t *device_status);
  * Returns PFSM_ERR_INVALID_ARG for an unknown `which`, PFSM_ERR_NO_SOLVE before a solve. */
 int pfsm_get_diagnostic(pfsm_handle_t h, int32_t which, void *out, void *stream);
 
+/* Split-precision product on the tcgen05 tensor cores, the building block of the mixed forms
+ * (Eq. 11 products). C[r, c] = sum_k P[r, k] Q[c, k] for FP64 row-major P (rows x K), Q
+ * (cols x K) and C (rows x cols), all device pointers. Each operand is split into BF16 (3
+ * pieces, precision PFSM_BF16_SPLIT) or TF32 (2 pieces, PFSM_TF32_SPLIT) and the cross products
+ * of total order below the piece count are accumulated in FP32 in tensor memory: relative
+ * accuracy about 2^-22 (TF32) or 2^-24 (BF16) of sum_k |P[r,k] Q[c,k]|. Allocates its slices
+ * with cudaMallocAsync on `stream`, frees them, and synchronises the stream before returning;
+ * returns PFSM_ERR_TIMEOUT if a bounded device wait gave up. rows, cols <= 65535. */
+int pfsm_split_gemm(int64_t rows, int64_t cols, int64_t K, const double *P, const double *Q,
+                    double *C, int32_t precision, void *stream);
+
 /* Eq. 11 on caller vectors WITHOUT ANY DEVICE ALLOCATION. The paper has no counterpart; this
  * entry point exists for callers that cannot allocate device memory when they call the
  * library, e.g. codes that reserve all device memory up front for their own pool, or

@@ -23,7 +23,7 @@ DIAG_RESIDUALS, DIAG_XFS, DIAG_EPS, DIAG_ALPHA, DIAG_PLAN = range(5)
 
 EXPORTED = ("pfsm_default_params", "pfsm_init", "pfsm_solve", "pfsm_backward", "pfsm_get_status",
             "pfsm_get_diagnostic", "pfsm_set_timing", "pfsm_get_profile", "pfsm_last_error",
-            "pfsm_destroy", "pfsm_fs_iterate_noalloc")
+            "pfsm_destroy", "pfsm_fs_iterate_noalloc", "pfsm_split_gemm")
 PHASES = ("plan", "submatrix", "fs_iterations", "gram_schmidt", "rayleigh", "backward")
 
 
@@ -66,6 +66,7 @@ def load_library():
     lib.pfsm_get_status.argtypes = [P, ctypes.POINTER(i32)]
     lib.pfsm_get_diagnostic.argtypes = [P, i32, P, P]
     lib.pfsm_fs_iterate_noalloc.argtypes = [i64, i64, P, P, P, P, i32, P]
+    lib.pfsm_split_gemm.argtypes = [i64, i64, i64, P, P, P, i32, P]
     lib.pfsm_set_timing.argtypes = [P, i32]
     lib.pfsm_get_profile.argtypes = [P, ctypes.POINTER(Profile)]
     lib.pfsm_last_error.argtypes = []
@@ -189,6 +190,16 @@ def fs_iterate_noalloc(A: torch.Tensor, X_rows: torch.Tensor, eps: torch.Tensor,
                                                   _ptr(alpha), iters, _stream()),
            "pfsm_fs_iterate_noalloc")
     return X_rows
+
+
+def split_gemm(P: torch.Tensor, Q: torch.Tensor, precision: int = BF16_SPLIT) -> torch.Tensor:
+    """C = P Q^T on the tensor cores in split BF16/TF32 (FP64 in and out)."""
+    rows, K = P.shape
+    cols = Q.shape[0]
+    C = torch.empty(rows, cols, dtype=torch.float64, device=P.device)
+    _check(load_library().pfsm_split_gemm(rows, cols, K, _ptr(P), _ptr(Q), _ptr(C), precision, _stream()),
+           "pfsm_split_gemm")
+    return C
 
 
 def solve(A: torch.Tensor, prev: torch.Tensor, nblocks: int, **kw):

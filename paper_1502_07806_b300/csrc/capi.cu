@@ -47,7 +47,8 @@ void free_ws(pfsm_handle_s *h)
     Workspace &w = h->ws;
     void *ptrs[] = {w.plan, w.tile_krange, w.status, w.gersh, w.X, w.Xfs, w.Y, w.S, w.W, w.Vrm,
                     w.sdiag, w.eps, w.alpha, w.lam, w.res, w.refl, w.tau, w.td, w.te,
-                    w.sel_val, w.sel_vec, w.iiwork, w.slices};
+                    w.sel_val, w.sel_vec, w.iiwork, w.slices, w.slE, w.slX, w.slY, w.slZ,
+                    w.Z, w.dA};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     w = Workspace{};
@@ -88,8 +89,8 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
     if (prm.fs_iters < 0 || prm.fs_iters > 1000) return fail(PFSM_ERR_INVALID_ARG, "pfsm_init: fs_iters=%d", prm.fs_iters);
     if (!(prm.alpha_theta > 0.0) || !(prm.cluster_tol >= 0.0) || !(prm.degen_tol >= 0.0))
         return fail(PFSM_ERR_INVALID_ARG, "pfsm_init: alpha_theta must be > 0, tolerances >= 0");
-    if (prm.precision != PFSM_FP64)
-        return fail(PFSM_ERR_INVALID_ARG, "pfsm_init: precision %d not available in this build", prm.precision);
+    if (prm.precision != PFSM_FP64 && prm.precision != PFSM_TF32_SPLIT && prm.precision != PFSM_BF16_SPLIT)
+        return fail(PFSM_ERR_INVALID_ARG, "pfsm_init: unknown precision %d", prm.precision);
     int32_t mnom = (int32_t)((N + nblocks - 1) / nblocks);
     if (prm.slice_sizes) {
         int64_t tot = 0;
@@ -150,6 +151,19 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
     PFSM_ALLOC(w.sel_vec, (size_t)nblocks * h->mmax * h->Mmax);
     PFSM_ALLOC(w.iiwork, ii);
     if (prm.slice_sizes) PFSM_ALLOC(w.slices, (size_t)nblocks);
+    if (prm.precision != PFSM_FP64) {
+        const size_t esz = slice_kind(prm.precision) == 0 ? 2 : 4;
+        const size_t sl_bytes = (size_t)slices_for(prm.precision) * N * padded_ld(N) * esz;
+        uint8_t *tmp[4] = {};
+        for (int i = 0; i < 4; i++) {
+            PFSM_ALLOC(tmp[i], sl_bytes);
+            if (e == cudaSuccess) e = cudaMemset(tmp[i], 0, sl_bytes);   // zero padding columns
+        }
+        w.slE = tmp[0]; w.slX = tmp[1]; w.slY = tmp[2]; w.slZ = tmp[3];
+        PFSM_ALLOC(w.Z, NN);
+        PFSM_ALLOC(w.dA, (size_t)N);
+        if (e == cudaSuccess) e = configure_tc_kernels();
+    }
 #undef PFSM_ALLOC
     if (e == cudaSuccess && prm.slice_sizes)
         e = cudaMemcpy(w.slices, prm.slice_sizes, sizeof(int32_t) * nblocks, cudaMemcpyHostToDevice);
@@ -173,6 +187,48 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
     return PFSM_OK;
 }
 
+// Eq. 11 in the mixed forms. With A = D + E (D = diag A) the iteration runs on the residual
+// vectors, the same recurrence as Eq. 11:
+//   Y_0 = (A - eps I) X_0 ;  Z_j = (A - eps I) Y_j ;  X_{j+1} = X_j - alpha Z_j ;
+//   Y_{j+1} = Y_j - alpha (A - eps I) Z_j.
+// Every tensor-core product is E times a small operand; the diagonal part is applied exactly in
+// FP64 in the epilogue. Y_0 vanishes inside each start vector's window (there the start vector is
+// an eigenvector of the window with eigenvalue eps), so the first product keeps only the entries
+// outside the window, where no cancellation occurs.
+static cudaError_t fs_mixed(pfsm_handle_s *h, const double *A, cudaStream_t st)
+{
+    Workspace &w = h->ws;
+    const int64_t N = h->N;
+    const int K = h->prm.fs_iters;
+    if (K == 0) return cudaSuccess;
+    const int ns = slices_for(h->prm.precision), kind = slice_kind(h->prm.precision);
+    const int64_t ld = padded_ld(N);
+    SliceBuf sE{w.slE, N, ld, ns, kind}, sX{w.slX, N, ld, ns, kind}, sY{w.slY, N, ld, ns, kind},
+        sZ{w.slZ, N, ld, ns, kind};
+    cudaError_t e;
+    if ((e = launch_split(A, N, N, N, sE, true, w.dA, st)) != cudaSuccess) return e;
+    if ((e = launch_split(w.X, N, N, N, sX, false, nullptr, st)) != cudaSuccess) return e;
+    TcParams p{};
+    p.rows = (int)N; p.cols = (int)N; p.ldo = N;
+    p.d = w.dA; p.eps = w.eps; p.alpha = w.alpha; p.status = w.status;
+    p.plan = w.plan; p.nb = h->nb;
+    p.krange = w.tile_krange; p.nrowtiles64 = (int)((N + kFsTileRows - 1) / kFsTileRows);
+    p.epi = TC_EPI_Y0; p.out = w.Y;
+    if ((e = launch_gemm_tc(sX, sE, p, &sY, st)) != cudaSuccess) return e;
+    p.krange = nullptr;
+    for (int j = 0; j < K; j++) {
+        TcParams z = p;
+        z.epi = TC_EPI_Z; z.out = w.Z; z.V = w.Y; z.X = w.X;
+        if ((e = launch_gemm_tc(sY, sE, z, j + 1 < K ? &sZ : nullptr, st)) != cudaSuccess) return e;
+        if (j + 1 < K) {
+            TcParams y = p;
+            y.epi = TC_EPI_YN; y.out = w.Y; y.V = w.Z; y.Yold = w.Y;
+            if ((e = launch_gemm_tc(sZ, sE, y, &sY, st)) != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
 static int solve_impl(pfsm_handle_s *h, const double *A, const double *prev, double *eigvals_out,
                       double *V_out, cudaStream_t st)
 {
@@ -187,6 +243,9 @@ static int solve_impl(pfsm_handle_s *h, const double *A, const double *prev, dou
     PFSM_CUDA(mark(1));
     PFSM_CUDA(launch_subeig(h, A, st));
     PFSM_CUDA(mark(2));
+    if (h->prm.precision != PFSM_FP64) {
+        PFSM_CUDA(fs_mixed(h, A, st));
+    } else
     // Eq. 11, fs_iters times: Y = (A - eps I) X ; X <- X - alpha (A - eps I) Y
     for (int it = 0; it < h->prm.fs_iters; it++) {
         GemmArgs g{};
@@ -278,6 +337,43 @@ int pfsm_get_diagnostic(pfsm_handle_t h, int32_t which, void *out, void *stream)
     default: return fail(PFSM_ERR_INVALID_ARG, "pfsm_get_diagnostic: unknown which=%d", which);
     }
     PFSM_CUDA(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToDevice, st));
+    return PFSM_OK;
+}
+
+int pfsm_split_gemm(int64_t rows, int64_t cols, int64_t K, const double *P, const double *Q,
+                    double *C, int32_t precision, void *stream)
+{
+    if (rows < 1 || cols < 1 || K < 1 || rows > 65535 || cols > 65535 || K > (1 << 24) || !P || !Q || !C)
+        return fail(PFSM_ERR_INVALID_ARG, "pfsm_split_gemm: bad size or null pointer");
+    if (precision != PFSM_TF32_SPLIT && precision != PFSM_BF16_SPLIT)
+        return fail(PFSM_ERR_INVALID_ARG, "pfsm_split_gemm: precision must be a split form");
+    cudaStream_t st = (cudaStream_t)stream;
+    PFSM_CUDA(configure_tc_kernels());
+    const int ns = slices_for(precision), kind = slice_kind(precision);
+    const int64_t ld = padded_ld(K);
+    const size_t esz = kind == 0 ? 2 : 4;
+    void *sp = nullptr, *sq = nullptr;
+    int32_t *status = nullptr;
+    PFSM_CUDA(cudaMallocAsync(&sp, (size_t)ns * rows * ld * esz, st));
+    PFSM_CUDA(cudaMallocAsync(&sq, (size_t)ns * cols * ld * esz, st));
+    PFSM_CUDA(cudaMallocAsync((void **)&status, sizeof(int32_t), st));
+    PFSM_CUDA(cudaMemsetAsync(sp, 0, (size_t)ns * rows * ld * esz, st));
+    PFSM_CUDA(cudaMemsetAsync(sq, 0, (size_t)ns * cols * ld * esz, st));
+    PFSM_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
+    SliceBuf bp{sp, rows, ld, ns, kind}, bq{sq, cols, ld, ns, kind};
+    PFSM_CUDA(launch_split(P, rows, K, K, bp, false, nullptr, st));
+    PFSM_CUDA(launch_split(Q, cols, K, K, bq, false, nullptr, st));
+    TcParams p{};
+    p.rows = (int)rows; p.cols = (int)cols; p.epi = TC_EPI_STORE; p.out = C; p.ldo = cols;
+    p.status = status;
+    PFSM_CUDA(launch_gemm_tc(bp, bq, p, nullptr, st));
+    int32_t hs = 0;
+    PFSM_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    PFSM_CUDA(cudaFreeAsync(sp, st));
+    PFSM_CUDA(cudaFreeAsync(sq, st));
+    PFSM_CUDA(cudaFreeAsync(status, st));
+    PFSM_CUDA(cudaStreamSynchronize(st));
+    if (hs != 0) return fail(hs, "pfsm_split_gemm: device status %d", hs);
     return PFSM_OK;
 }
 

@@ -45,6 +45,10 @@ struct Workspace {
     double *iiwork = nullptr;      // nb * mmax * 5 * Mmax inverse-iteration LU storage (also
                                    // the window rows when they do not fit in shared memory)
     int32_t *slices = nullptr;     // nb explicit slice sizes, or null
+    // mixed forms: BF16/TF32 slices of E = A - diag(A), X, Y, Z (rows x ld, ns per operand)
+    void *slE = nullptr, *slX = nullptr, *slY = nullptr, *slZ = nullptr;
+    double *Z = nullptr;           // N*N (A - eps I) Y
+    double *dA = nullptr;          // N diag(A)
 };
 
 }  // namespace pfsm
@@ -104,6 +108,42 @@ struct GemmArgs {
     int lower_only;                      // skip tiles strictly above the diagonal
 };
 cudaError_t launch_gemm_f64(const GemmArgs &a, int epi, int qlayout, cudaStream_t st);
+
+// ---- tensor-core split-precision GEMM (k_gemm_tc.cu) ----
+enum TcEpi : int { TC_EPI_STORE = 0, TC_EPI_Y0 = 1, TC_EPI_Z = 2, TC_EPI_YN = 3 };
+
+// A matrix held as `ns` slices (kind 0: BF16, kind 1: TF32 in FP32 containers), each rows x ld,
+// ld a multiple of 64 elements with zero padding columns.
+struct SliceBuf {
+    void *ptr;
+    int64_t rows, ld;
+    int ns, kind;
+};
+
+struct TcParams {
+    int rows, cols;                 // output extent
+    int kblocks, bk, npairs;        // filled by launch_gemm_tc
+    int8_t pa[16], pb[16];
+    const int32_t *krange;          // per 64-row tile K range, or null
+    int nrowtiles64;
+    int epi;
+    double *out; int64_t ldo;
+    void *out_slices; int64_t sl_ld, sl_stride; int out_ns;
+    double *X;                      // TC_EPI_Z: x <- x - alpha z
+    const double *V;                // operand in FP64 (Y for TC_EPI_Z, Z for TC_EPI_YN)
+    const double *Yold;             // TC_EPI_YN
+    const double *d, *eps, *alpha;
+    const int32_t *plan; int nb;    // TC_EPI_Y0 window mask
+    int32_t *status;
+};
+cudaError_t configure_tc_kernels();
+cudaError_t launch_split(const double *src, int64_t rows, int64_t cols, int64_t ld, const SliceBuf &dst,
+                         bool zero_diag, double *d, cudaStream_t st);
+cudaError_t launch_gemm_tc(const SliceBuf &P, const SliceBuf &Q, TcParams prm, SliceBuf *out_sl,
+                           cudaStream_t st);
+inline int slices_for(int precision) { return precision == PFSM_BF16_SPLIT ? 3 : 2; }
+inline int slice_kind(int precision) { return precision == PFSM_BF16_SPLIT ? 0 : 1; }
+inline int64_t padded_ld(int64_t n) { return (n + 63) / 64 * 64; }
 
 cudaError_t launch_gram_schmidt_f64(pfsm_handle_s *h, cudaStream_t st);
 cudaError_t launch_rayleigh_f64(pfsm_handle_s *h, const double *A, double *eigvals_out,

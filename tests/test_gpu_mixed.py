@@ -1,0 +1,89 @@
+"""GPU: the tcgen05 split-precision GEMM and the mixed-precision forms of the PFSM solve.
+
+The split GEMM is checked against the exact FP64 product with an error bound relative to
+sum_k |P[r,k] Q[c,k]|. The mixed solves are checked against the FP64 oracle: eigenvalues at the
+FP64 form's bar (|dlambda| <= 1e-10 ||A||, the "equal eigen-accuracy" condition of the benchmark)
+and eigenvector projectors; the measured errors are printed (reported per result)."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as wl
+from compare import projector_errors, spectral_scale
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1502_07806_b300 as mod
+    from paper_1502_07806_b300 import build
+    build.build()
+    mod.load_library()
+    return mod
+
+
+PRECISIONS = [("bf16", 2), ("tf32", 1)]
+
+
+@pytest.mark.parametrize("rows,cols,K", [(128, 128, 64), (200, 130, 333), (7, 300, 1000),
+                                         (1280, 1280, 1280), (257, 129, 64)])
+@pytest.mark.parametrize("name,prec", PRECISIONS)
+def test_split_gemm_matches_fp64(pf, rows, cols, K, name, prec):
+    rng = np.random.default_rng(rows * 7 + cols + K)
+    P = rng.standard_normal((rows, K)) * np.exp(rng.uniform(-3, 3, (rows, 1)))
+    Q = rng.standard_normal((cols, K))
+    C = pf.split_gemm(torch.from_numpy(P).cuda(), torch.from_numpy(Q).cuda(), prec).cpu().numpy()
+    ref = P @ Q.T
+    bound = np.abs(P) @ np.abs(Q).T
+    err = np.max(np.abs(C - ref) / bound)
+    print(f"{name} {rows}x{cols}x{K}: max |C - PQ^T| / (|P||Q|^T) = {err:.2e}")
+    # representation of the pieces (2^-24 BF16 x3, 2^-21 TF32 x2) plus FP32 accumulation in
+    # tensor memory, which grows like sqrt(K) 2^-24 for random terms (4x margin)
+    rep = 2.0 ** -24 if name == "bf16" else 2.0 ** -21
+    assert err < 4 * rep + 4 * np.sqrt(K) * 2.0 ** -24
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _solve(pf, p, **kw):
+    h = pf.Handle(p.n, p.nblocks, halo=p.halo, **kw)
+    lam, V = h.solve(_dev(p.A), _dev(p.prev))
+    st = h.status()
+    xfs = h.diagnostic(pf.DIAG_XFS).cpu().numpy()
+    return lam.cpu().numpy(), V.cpu().numpy(), xfs, st
+
+
+@pytest.mark.parametrize("name,prec", PRECISIONS)
+@pytest.mark.parametrize("case", ["gapped256_s0", "gapped256_s2", "diamond1280_s0", "ragged333"])
+def test_mixed_solve_matches_oracle(pf, orc, name, prec, case):
+    if case.startswith("gapped"):
+        p = wl.small_gapped(int(case[-1]))
+    elif case.startswith("diamond"):
+        p = wl.diamond_like(0)
+    else:
+        p = wl.random_nearly_diagonal(333, seed=4, sigma=2e-3, decay=12.0, nblocks=11, halo=31)
+    r = orc.pfsm(p.A, p.prev, p.nblocks, halo=p.halo)
+    lam, V, xfs, st = _solve(pf, p, precision=prec)
+    assert st == 0
+    scale = spectral_scale(r.lam)
+    dl = np.max(np.abs(lam - r.lam)) / scale
+    pe = np.max(projector_errors(r.V, V, r.lam))
+    dx = np.max(np.abs(xfs - r.xfs))
+    print(f"{case} {name}: |dlam|/||A|| = {dl:.2e}, projector = {pe:.2e}, |dX after Eq. 11| = {dx:.2e}")
+    assert dl <= 1e-10
+    assert pe <= 1e-8
+    assert dx <= 1e-9
+
+
+@pytest.mark.parametrize("name,prec", PRECISIONS)
+def test_mixed_without_iterations_equals_fp64(pf, name, prec):
+    p = wl.small_gapped(1)
+    a = _solve(pf, p, precision=prec, fs_iters=0)
+    b = _solve(pf, p, precision=pf.FP64, fs_iters=0)
+    np.testing.assert_array_equal(a[1], b[1])
+    np.testing.assert_array_equal(a[0], b[0])
