@@ -3,7 +3,12 @@
 on the diamond-cell-like workload (N = 1280 = 1024 occupied + 256 unoccupied bands, 10 slices of
 128 with windows of 384, K = 3 iterations of Eq. 11, SCF step 0 of the seeded sequence).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--precision fp64]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision bf16|tf32|fp64]
+
+The headline is the mixed form (Eq. 11 products on tcgen05 in split BF16 by default, everything
+else FP64); the plain FP64 GPU PFSM is timed in the same run for the comparison the metric asks
+for, and both are checked against the FP64 oracle.
 
 One JSON line on rank 0. The timed steps run on device-resident inputs with L2 flushed between
 steps (a 256 MiB write, outside the per-step CUDA events). `e2e` repeats the measurement through
@@ -29,10 +34,25 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "PFSM solves/s & TFLOP/s vs plain FP64 GPU PFSM at equal eigen-accuracy"
-FP64_NOMINAL_TFLOPS = 1.25        # B300 FP64 (DFMA) nominal rate; tcgen05 has no FP64 kind
-# DRAM traffic of one FS-GEMM launch from an ncu capture of the current kernel (bytes), or None
-# when the kernel changed since the capture (see profiles/).
-FS_GEMM_TRAFFIC = None
+# FP64 on B300 runs on the DFMA pipe (tcgen05 has no FP64 kind): 148 SMs x 2 DFMA/clock x 2 flop
+# x 2.032 GHz maximum SM clock.
+FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
+FP64_PEAK_SOURCE = ("unit counts: 148 SMs x 2 DFMA/clk x 2 flop x 2032 MHz; ncu shows k_gemm_f64 at "
+                    "99.7% FP64-pipe activity")
+TF32_OVER_BF16 = 1.1 / 2.25       # nominal dense TF32 / BF16 tensor rate
+DTYPES = {"fp64": "f64", "bf16": "bf16x3-split, f32 accumulate, f64 epilogue",
+          "tf32": "tf32x2-split, f32 accumulate, f64 epilogue"}
+# DRAM traffic (bytes) of one Eq. 11 product launch from an ncu capture of the current kernel
+# build on this workload, or None when the kernel changed since the capture (see profiles/).
+FS_GEMM_TRAFFIC = {}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 def workload(n=None, nblocks=None, halo=None):
@@ -160,7 +180,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--precision", choices=("fp64",), default="fp64")
+    ap.add_argument("--precision", choices=("bf16", "tf32", "fp64"), default="bf16")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-oracle", action="store_true", help="skip the accuracy check and CPU baseline")
     ap.add_argument("--n", type=int, default=None, help="profiling size override")
@@ -196,28 +216,29 @@ def main():
         build.build()
     if world > 1:
         dist.barrier()
-    prec = {"fp64": pf.FP64}[args.precision]
-    h = pf.Handle(p.n, p.nblocks, halo=p.halo, fs_iters=p.fs_iters, precision=prec)
+    precs = {"fp64": pf.FP64, "tf32": pf.TF32_SPLIT, "bf16": pf.BF16_SPLIT}
     A = torch.from_numpy(p.A).cuda()
     prev = torch.from_numpy(p.prev).cuda()
-    lam = torch.empty(p.n, dtype=torch.float64, device="cuda")
-    V = torch.empty(p.n, p.n, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    h.set_timing(True)
-    for _ in range(args.warmup):
-        h.solve(A, prev, lam, V)
-    st = h.status()
-    if st != 0:
-        raise RuntimeError(f"device status {pf.STATUS_NAMES.get(st, st)}")
-    plan = h.diagnostic(pf.DIAG_PLAN).cpu().numpy()
-    fl = algorithmic_flops(plan, p.n, p.fs_iters)
 
-    # ---- device-resident timed steps -------------------------------------------------------
-    step_ms, phases, launches = [], [], 0
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    barrier()
-    with ClockSampler(local) as clk:
-        for i in range(args.steps):
+    def measure(precision: str, steps: int, clocks: bool):
+        """Warm-up, then `steps` device-resident solves timed with CUDA events, L2 flushed."""
+        h = pf.Handle(p.n, p.nblocks, halo=p.halo, fs_iters=p.fs_iters, precision=precs[precision])
+        lam = torch.empty(p.n, dtype=torch.float64, device="cuda")
+        V = torch.empty(p.n, p.n, dtype=torch.float64, device="cuda")
+        h.set_timing(True)
+        for _ in range(args.warmup):
+            h.solve(A, prev, lam, V)
+        st = h.status()
+        if st != 0:
+            raise RuntimeError(f"{precision}: device status {pf.STATUS_NAMES.get(st, st)}")
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        phases, launches = [], 0
+        barrier()
+        sampler = ClockSampler(local) if clocks else None
+        if sampler:
+            sampler.__enter__()
+        for i in range(steps):
             flush.zero_()
             ev[i][0].record()
             h.solve(A, prev, lam, V)
@@ -226,17 +247,27 @@ def main():
             phases.append(prof)
             launches += prof["launches"]
         barrier()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(step_ms) / 1000.0
-    if world > 1:
-        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * args.steps / total_s
-    ms_per_step = 1000.0 * total_s / args.steps
-    st = h.status()
-    if st != 0:
-        raise RuntimeError(f"device status {pf.STATUS_NAMES.get(st, st)}")
+        if sampler:
+            sampler.__exit__(None, None, None)
+        total = sum(a.elapsed_time(b) for a, b in ev) / 1000.0
+        if world > 1:
+            t = torch.tensor([total], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+        st = h.status()
+        if st != 0:
+            raise RuntimeError(f"{precision}: device status {pf.STATUS_NAMES.get(st, st)}")
+        ph = {k: statistics.mean(pr[k] for pr in phases) for k in pf.PHASES[:5]}
+        return dict(h=h, lam=lam, V=V, total=total, value=world * steps / total, phases=ph,
+                    launches=launches, clocks=sampler.summary() if sampler else None)
+
+    main_run = measure(args.precision, args.steps, clocks=True)
+    h = main_run["h"]
+    plan = h.diagnostic(pf.DIAG_PLAN).cpu().numpy()
+    fl = algorithmic_flops(plan, p.n, p.fs_iters)
+    value = main_run["value"]
+    ms_per_step = 1000.0 * main_run["total"] / args.steps
+    fp64_run = main_run if args.precision == "fp64" else measure("fp64", max(3, args.steps // 2), clocks=False)
 
     # ---- end to end through the C ABI with host buffers -----------------------------------
     hA = torch.from_numpy(p.A).pin_memory()
@@ -245,6 +276,7 @@ def main():
     hV = torch.empty(p.n, p.n, dtype=torch.float64).pin_memory()
     dA = torch.empty_like(A)
     dprev = torch.empty_like(prev)
+    lam, V = main_run["lam"], main_run["V"]
     h.set_timing(False)
     e2e_ms = []
     barrier()
@@ -275,39 +307,56 @@ def main():
             dist.destroy_process_group()
         return 0
 
-    # ---- phase breakdown and roofline of the dominant kernel -------------------------------
-    ph = {k: statistics.mean(pr[k] for pr in phases) for k in pf.PHASES[:5]}
+    # ---- roofline of the Eq. 11 product kernel ------------------------------------------------
+    ph = main_run["phases"]
     fs_ms = ph["fs_iterations"]
     fs_launches = 2 * p.fs_iters
     achieved = fl["fs"] / (fs_ms / 1000.0) / 1e12 if fs_ms > 0 else None
-    roofline = {"kernel": "k_gemm_f64 (Eq. 11 products, fused epilogues)", "bound": "alu",
-                "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": (achieved / FP64_NOMINAL_TFLOPS) if achieved else None,
-                "traffic": FS_GEMM_TRAFFIC,
+    if args.precision == "fp64":
+        peak, bound, kern = FP64_PEAK_TFLOPS, "alu", "k_gemm_f64 (FP64 DFMA, fused Eq. 11 epilogues)"
+        src = FP64_PEAK_SOURCE
+        products = 1
+    else:
+        peaks = measured_peaks()
+        bf16 = peaks.get("bf16_tflops") or 1800.0
+        peak = bf16 if args.precision == "bf16" else bf16 * TF32_OVER_BF16
+        bound, kern = "tensor", f"k_gemm_tc<{args.precision}> (tcgen05, split operands, fused FP64 epilogues)"
+        src = ("MEASURED_PEAKS.json bf16_tflops (burst)" if peaks.get("bf16_tflops") else "fallback 1.8 PFLOP/s bf16") + \
+              ("" if args.precision == "bf16" else " x nominal TF32/BF16 ratio 1.1/2.25")
+        products = 6 if args.precision == "bf16" else 3
+    roofline = {"kernel": kern, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": FS_GEMM_TRAFFIC.get(args.precision),
                 "per_launch": {"flops": fl["fs"] / fs_launches, "ms": fs_ms / fs_launches},
-                "peak_source": "B300 nominal FP64 (DFMA) rate; a DFMA microbenchmark measured 1.09 TFLOP/s at 1927 MHz"}
+                "flop_convention": "algorithmic (each N^3 term once); tensor-core work is "
+                                   f"{products}x that in split products",
+                "peak_source": src}
 
     out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
            "config": dict(cfg, precision=args.precision, l2="flushed between steps (256 MiB write)",
                           parallelism=f"replicas x{world}"),
            "tflops": fl["total"] * value / world / 1e12,
-           "fp64_solves_per_s": value if args.precision == "fp64" else None,
-           "phases_ms": ph, "roofline": roofline,
+           "fp64_solves_per_s": fp64_run["value"],
+           "speedup_vs_fp64": value / fp64_run["value"],
+           "phases_ms": ph, "fp64_phases_ms": fp64_run["phases"], "roofline": roofline,
            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h},
-           "gpu_launches": launches, "clocks": clk.summary()}
+           "gpu_launches": main_run["launches"], "clocks": main_run["clocks"]}
 
     if not args.no_oracle and world == 1:
         import oracle
         ref = oracle.pfsm(p.A, p.prev, p.nblocks, halo=p.halo, fs_iters=p.fs_iters, keep_xfs=False)
-        lam_h, V_h = lam.cpu().numpy(), V.cpu().numpy()
         scale = float(np.max(np.abs(ref.lam)))
-        d = np.sum(V_h * ref.V, axis=0)
-        proj = np.linalg.norm(ref.V - V_h * np.where(d < 0, -1.0, 1.0), axis=0) * np.sqrt(1 + np.abs(d))
-        out["accuracy"] = {"max_abs_dlambda_over_normA": float(np.max(np.abs(lam_h - ref.lam)) / scale),
-                           "max_projector_err": float(np.max(proj)), "reference": "FP64 CPU oracle"}
+
+        def accuracy(run):
+            lam_h, V_h = run["lam"].cpu().numpy(), run["V"].cpu().numpy()
+            d = np.sum(V_h * ref.V, axis=0)
+            proj = np.linalg.norm(ref.V - V_h * np.where(d < 0, -1.0, 1.0), axis=0) * np.sqrt(1 + np.abs(d))
+            return {"max_abs_dlambda_over_normA": float(np.max(np.abs(lam_h - ref.lam)) / scale),
+                    "max_projector_err": float(np.max(proj)), "reference": "FP64 CPU oracle"}
+        out["accuracy"] = accuracy(main_run)
+        out["fp64_accuracy"] = accuracy(fp64_run)
         rate, count, el = oracle_rate(p, args.cpu_seconds)
         out["cpu_baseline"] = {"value": rate, "unit": "solves/s", "cores": threads_used(), "kind": "oracle",
                                "sample": f"{count} full oracle solves of the workload in {el:.1f} s"}
