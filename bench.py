@@ -257,7 +257,7 @@ def main():
         st = h.status()
         if st != 0:
             raise RuntimeError(f"{precision}: device status {pf.STATUS_NAMES.get(st, st)}")
-        ph = {k: statistics.mean(pr[k] for pr in phases) for k in pf.PHASES[:5]}
+        ph = {k: statistics.mean(pr[k] for pr in phases) for k in pf.PHASES[:5] + pf.SUB_PHASES}
         return dict(h=h, lam=lam, V=V, total=total, value=world * steps / total, phases=ph,
                     launches=launches, clocks=sampler.summary() if sampler else None)
 

@@ -170,10 +170,12 @@ int pfsm_fs_iterate_noalloc(int64_t N, int64_t count, const double *A, double *X
 typedef struct {
     int32_t launches;     /* kernels enqueued by the last pfsm_solve / pfsm_backward on h */
     int32_t timed;        /* 1 when phase_ms holds measurements (timing enabled on h) */
-    float phase_ms[8];    /* CUDA-event times on the call's stream, in milliseconds:
+    float phase_ms[12];   /* CUDA-event times on the call's stream, in milliseconds:
                              0 validation + partition plan, 1 submatrix solves + start vectors,
                              2 Eq. 11 iterations, 3 Gram-Schmidt (overlap, Cholesky, solve),
-                             4 Rayleigh quotients, residuals and outputs, 5 backward */
+                             4 Rayleigh quotients, residuals and outputs, 5 backward;
+                             inside 1: 6 tridiagonalisation, 7 bisection, 8 inverse iteration,
+                             9 back-transformation + start vectors */
 } pfsm_profile_t;
 
 /* Enables (enable != 0) or disables CUDA-event phase timing on h. Timing adds one event record

@@ -25,6 +25,7 @@ EXPORTED = ("pfsm_default_params", "pfsm_init", "pfsm_solve", "pfsm_backward", "
             "pfsm_get_diagnostic", "pfsm_set_timing", "pfsm_get_profile", "pfsm_last_error",
             "pfsm_destroy", "pfsm_fs_iterate_noalloc", "pfsm_split_gemm")
 PHASES = ("plan", "submatrix", "fs_iterations", "gram_schmidt", "rayleigh", "backward")
+SUB_PHASES = ("tridiag", "bisect", "inverse_iter", "backtransform")
 
 
 class PFSMError(RuntimeError):
@@ -42,7 +43,7 @@ class Params(ctypes.Structure):
 
 class Profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int32), ("timed", ctypes.c_int32),
-                ("phase_ms", ctypes.c_float * 8)]
+                ("phase_ms", ctypes.c_float * 12)]
 
 
 _lib = None
@@ -164,6 +165,7 @@ class Handle:
         out = {"launches": pr.launches}
         if pr.timed:
             out.update({name: float(pr.phase_ms[i]) for i, name in enumerate(PHASES)})
+            out.update({name: float(pr.phase_ms[6 + i]) for i, name in enumerate(SUB_PHASES)})
         return out
 
     def diagnostic(self, which: int) -> torch.Tensor:

@@ -48,7 +48,7 @@ void free_ws(pfsm_handle_s *h)
     void *ptrs[] = {w.plan, w.tile_krange, w.status, w.gersh, w.X, w.Xfs, w.Y, w.S, w.W, w.Vrm,
                     w.sdiag, w.eps, w.alpha, w.lam, w.res, w.refl, w.tau, w.td, w.te,
                     w.sel_val, w.sel_vec, w.iiwork, w.slices, w.slE, w.slX, w.slY, w.slZ,
-                    w.Z, w.dA};
+                    w.Z, w.dA, w.Linv};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     w = Workspace{};
@@ -139,6 +139,7 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
     PFSM_ALLOC(w.W, NN);
     PFSM_ALLOC(w.Vrm, NN);
     PFSM_ALLOC(w.sdiag, (size_t)N);
+    PFSM_ALLOC(w.Linv, (size_t)(N + 64) * 64);
     PFSM_ALLOC(w.eps, (size_t)N);
     PFSM_ALLOC(w.alpha, (size_t)N);
     PFSM_ALLOC(w.lam, (size_t)N);
@@ -176,6 +177,7 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
         return fail(code, "pfsm_init: %s", cudaGetErrorString(e));
     }
     for (int i = 0; i < 8 && e == cudaSuccess; i++) e = cudaEventCreate(&h->ev[i]);
+    for (int i = 0; i < 4 && e == cudaSuccess; i++) e = cudaEventCreate(&h->sub_ev[i]);
     if (e != cudaSuccess) {
         free_ws(h);
         delete h;
@@ -393,8 +395,13 @@ int pfsm_get_profile(pfsm_handle_t h, pfsm_profile_t *out)
     PFSM_CUDA(cudaStreamSynchronize(h->last_stream));
     auto span = [&](int a, int b, float *dst) -> cudaError_t { return cudaEventElapsedTime(dst, h->ev[a], h->ev[b]); };
     const bool fwd = !h->last_was_backward || h->prm.recompute_v;
-    if (fwd)
+    if (fwd) {
         for (int i = 0; i < 5; i++) PFSM_CUDA(span(i, i + 1, &out->phase_ms[i]));
+        // submatrix sub-phases: ev[1] | tridiag | sub_ev[0] | bisect | sub_ev[1] | inverse
+        // iteration | sub_ev[2] | back-transform | ev[2]
+        cudaEvent_t seq[5] = {h->ev[1], h->sub_ev[0], h->sub_ev[1], h->sub_ev[2], h->ev[2]};
+        for (int i = 0; i < 4; i++) PFSM_CUDA(cudaEventElapsedTime(&out->phase_ms[6 + i], seq[i], seq[i + 1]));
+    }
     if (h->last_was_backward) PFSM_CUDA(span(6, 7, &out->phase_ms[5]));
     out->timed = 1;
     return PFSM_OK;
@@ -406,6 +413,8 @@ int pfsm_destroy(pfsm_handle_t h)
     cudaDeviceSynchronize();
     for (int i = 0; i < 8; i++)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    for (int i = 0; i < 4; i++)
+        if (h->sub_ev[i]) cudaEventDestroy(h->sub_ev[i]);
     free_ws(h);
     delete h;
     return PFSM_OK;

@@ -3,7 +3,8 @@
 //
 // Gram-Schmidt is done as Cholesky-QR. With the vectors as rows of X:
 //   S = X X^T (overlap, lower triangle), S = L L^T (blocked right-looking Cholesky),
-//   V = L^-1 X (blocked forward substitution over the rows).
+//   V = L^-1 X (blocked forward substitution over the rows, as GEMMs with the inverses of the
+//   64 x 64 diagonal blocks of L, so nearly all FP64 work runs in the FP64 GEMM kernel).
 // In exact arithmetic this is the QR factorisation with positive R diagonal, i.e. Gram-Schmidt
 // in ascending index order. L_jj^2 is the squared norm of vector j after projecting out vectors
 // 0..j-1 and S_jj its squared norm before, so L_jj < 1e-8 sqrt(S_jj) is the breakdown test.
@@ -21,9 +22,11 @@ __global__ void k_copy_diag(const double *__restrict__ S, int64_t N, double *__r
     if (i < N) d[i] = S[i * N + i];
 }
 
-// Unblocked Cholesky of the b x b diagonal block at (jb, jb), in shared memory, one CTA.
-__global__ void k_potrf_diag(double *__restrict__ S, int64_t N, int64_t jb, int b,
-                             const double *__restrict__ sdiag, int32_t *status)
+// Unblocked Cholesky of the b x b diagonal block at (jb, jb), in shared memory, one CTA; also
+// writes the block's inverse L_jj^-1 (lower triangular, b x b, leading dimension CB) to Linv.
+__global__ void k_potrf_inv(double *__restrict__ S, int64_t N, int64_t jb, int b,
+                            const double *__restrict__ sdiag, int32_t *status,
+                            double *__restrict__ Linv)
 {
     __shared__ double L[CB][CB + 1];
     for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
@@ -49,7 +52,7 @@ __global__ void k_potrf_diag(double *__restrict__ S, int64_t N, int64_t jb, int 
         const int rem = b - j - 1;
         for (int t = threadIdx.x; t < rem * rem; t += blockDim.x) {
             int i = j + 1 + t / rem, k = j + 1 + t % rem;
-            if (k <= i) L[i][k] -= L[i][j] * L[k][j];
+            if (k <= i) L[i][k] = fma(-L[i][j], L[k][j], L[i][k]);
         }
         __syncthreads();
     }
@@ -57,59 +60,20 @@ __global__ void k_potrf_diag(double *__restrict__ S, int64_t N, int64_t jb, int 
         int i = t / b, k = t % b;
         if (k <= i) S[(jb + i) * N + jb + k] = L[i][k];
     }
-}
-
-// Panel: rows i >= jb + b solve l_i L_jj^T = s_i (columns jb .. jb+b-1), 16 rows per CTA.
-constexpr int kPanelRows = 16;
-__global__ void k_trsm_panel(double *__restrict__ S, int64_t N, int64_t jb, int b)
-{
-    __shared__ double L[CB][CB + 1];
-    __shared__ double Pn[kPanelRows][CB + 1];
-    const int64_t rbase = jb + b + (int64_t)blockIdx.x * kPanelRows;
-    for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
-        int i = t / b, k = t % b;
-        L[i][k] = (k <= i) ? S[(jb + i) * N + jb + k] : 0.0;
-    }
-    for (int t = threadIdx.x; t < kPanelRows * b; t += blockDim.x) {
-        int r = t / b, k = t % b;
-        int64_t row = rbase + r;
-        Pn[r][k] = (row < N) ? S[row * N + jb + k] : 0.0;
-    }
-    __syncthreads();
-    if (threadIdx.x < kPanelRows) {
-        const int r = threadIdx.x;
-        for (int j = 0; j < b; j++) {
-            double acc = Pn[r][j];
-            for (int l = 0; l < j; l++) acc -= Pn[r][l] * L[j][l];
-            Pn[r][j] = acc / L[j][j];
+    // inverse: column c of L^-1 by forward substitution, one column per thread
+    for (int c = threadIdx.x; c < CB; c += blockDim.x) {
+        double x[CB];
+#pragma unroll
+        for (int i = 0; i < CB; i++) x[i] = 0.0;
+        if (c < b) {
+            for (int i = c; i < b; i++) {
+                double acc = (i == c) ? 1.0 : 0.0;
+                for (int k = c; k < i; k++) acc = fma(-L[i][k], x[k], acc);
+                x[i] = acc / L[i][i];
+            }
         }
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < kPanelRows * b; t += blockDim.x) {
-        int r = t / b, k = t % b;
-        int64_t row = rbase + r;
-        if (row < N) S[row * N + jb + k] = Pn[r][k];
-    }
-}
-
-// Rows jb .. jb+b-1 of X become L_jj^-1 X[jb:jb+b, :] (forward substitution, one column per
-// thread, columns coalesced across the CTA).
-__global__ void k_trsm_diag_rows(const double *__restrict__ S, double *__restrict__ X, int64_t N,
-                                 int64_t jb, int b)
-{
-    __shared__ double L[CB][CB + 1];
-    for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
-        int i = t / b, k = t % b;
-        L[i][k] = (k <= i) ? S[(jb + i) * N + jb + k] : 0.0;
-    }
-    __syncthreads();
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= N) return;
-    double *col = X + jb * N + c;     // this thread's column; earlier rows already solved
-    for (int r = 0; r < b; r++) {
-        double acc = col[r * N];
-        for (int l = 0; l < r; l++) acc -= L[r][l] * col[l * N];
-        col[r * N] = acc / L[r][r];
+#pragma unroll
+        for (int i = 0; i < CB; i++) Linv[i * CB + c] = (c < b && i < b) ? x[i] : 0.0;
     }
 }
 
@@ -124,13 +88,20 @@ cudaError_t launch_gram_schmidt_f64(pfsm_handle_s *h, cudaStream_t st)
     g.P = w.X; g.ldp = N; g.Q = w.X; g.ldq = N; g.C = w.S; g.ldc = N; g.lower_only = 1;
     if ((e = launch_gemm_f64(g, EPI_STORE, Q_KMAJOR, st)) != cudaSuccess) return e;
     k_copy_diag<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(w.S, N, w.sdiag); g_launches++;
-    // Cholesky
+    // blocked right-looking Cholesky S = L L^T; L_jj^-1 kept per block in Linv
     for (int64_t jb = 0; jb < N; jb += CB) {
         const int b = (int)((N - jb) < CB ? (N - jb) : CB);
-        k_potrf_diag<<<1, 256, 0, st>>>(w.S, N, jb, b, w.sdiag, w.status); g_launches++;
+        double *Li = w.Linv + jb * CB;
+        k_potrf_inv<<<1, 256, 0, st>>>(w.S, N, jb, b, w.sdiag, w.status, Li); g_launches++;
         const int64_t rest = N - jb - b;
         if (rest <= 0) break;
-        k_trsm_panel<<<(unsigned)((rest + kPanelRows - 1) / kPanelRows), 128, 0, st>>>(w.S, N, jb, b); g_launches++;
+        // panel: L[rest, jb] = S[rest, jb] L_jj^-T (one CTA per row tile: in place is safe)
+        GemmArgs pn{};
+        pn.rows = rest; pn.cols = b; pn.K = b;
+        pn.P = w.S + (jb + b) * N + jb; pn.ldp = N;
+        pn.Q = Li; pn.ldq = CB;
+        pn.C = w.S + (jb + b) * N + jb; pn.ldc = N;
+        if ((e = launch_gemm_f64(pn, EPI_STORE, Q_KMAJOR, st)) != cudaSuccess) return e;
         GemmArgs u{};
         u.rows = rest; u.cols = rest; u.K = b;
         u.P = w.S + (jb + b) * N + jb; u.ldp = N;
@@ -138,19 +109,28 @@ cudaError_t launch_gram_schmidt_f64(pfsm_handle_s *h, cudaStream_t st)
         u.C = w.S + (jb + b) * N + jb + b; u.ldc = N; u.lower_only = 1;
         if ((e = launch_gemm_f64(u, EPI_SUB, Q_KMAJOR, st)) != cudaSuccess) return e;
     }
-    // V = L^-1 X (rows)
+    // V = L^-1 X by blocks of rows, written to Y: V_b = L_bb^-1 X_b, then X_rest -= L_rest,b V_b
     for (int64_t jb = 0; jb < N; jb += CB) {
         const int b = (int)((N - jb) < CB ? (N - jb) : CB);
-        k_trsm_diag_rows<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(w.S, w.X, N, jb, b); g_launches++;
+        GemmArgs dg{};
+        dg.rows = b; dg.cols = N; dg.K = b;
+        dg.P = w.Linv + jb * CB; dg.ldp = CB;
+        dg.Q = w.X + jb * N; dg.ldq = N;
+        dg.C = w.Y + jb * N; dg.ldc = N;
+        if ((e = launch_gemm_f64(dg, EPI_STORE, Q_NMAJOR, st)) != cudaSuccess) return e;
         const int64_t rest = N - jb - b;
         if (rest <= 0) break;
         GemmArgs u{};
         u.rows = rest; u.cols = N; u.K = b;
         u.P = w.S + (jb + b) * N + jb; u.ldp = N;
-        u.Q = w.X + jb * N; u.ldq = N;
+        u.Q = w.Y + jb * N; u.ldq = N;
         u.C = w.X + (jb + b) * N; u.ldc = N;
         if ((e = launch_gemm_f64(u, EPI_SUB, Q_NMAJOR, st)) != cudaSuccess) return e;
     }
+    // the orthonormal vectors now live in Y: swap the buffers so X holds V
+    double *t = w.X;
+    w.X = w.Y;
+    w.Y = t;
     return cudaGetLastError();
 }
 

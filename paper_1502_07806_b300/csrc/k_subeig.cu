@@ -9,9 +9,11 @@
 //                     are spread cyclically over the cluster's CTAs (in shared memory when they
 //                     fit, else in global memory) and the Householder vector and the product
 //                     p = beta B v are exchanged through distributed shared memory.
-//   2. k_bisect       the selected eigenvalues of T_b by Sturm-count bisection, one thread each.
-//   3. k_inverse_iter their eigenvectors of T_b by inverse iteration with a pivoted tridiagonal
-//                     LU, re-orthogonalised inside clusters of (nearly) equal eigenvalues.
+//   2. k_bisect       the selected eigenvalues of T_b: FP32 Sturm bisection, FP64 Newton steps on
+//                     det(T - xI), FP64 Sturm counts certifying the index; one lane each.
+//   3. k_inverse_iter their eigenvectors of T_b by inverse iteration (two solves) with a pivoted
+//                     tridiagonal LU, re-orthogonalised inside clusters of (nearly) equal
+//                     eigenvalues.
 //   4. k_backtransform y = H_0 ... H_{M-3} z, sign rule, zero padding to length N, shift eps and
 //                     step alpha: one warp per start vector, written straight into X.
 #include <cooperative_groups.h>
@@ -128,7 +130,7 @@ k_tridiag(const double *__restrict__ A, int64_t N, const int32_t *__restrict__ p
             for (int i = first + warp * CL; i < M; i += nwarps * CL) {
                 double *ri = rowp(i);
                 const double hi = hv[i], wi = wv[i];
-                for (int j = k + 1 + lane; j < M; j += 32) ri[j] -= hi * wv[j] + wi * hv[j];
+                for (int j = k + 1 + lane; j < M; j += 32) ri[j] = fma(-hi, wv[j], fma(-wi, hv[j], ri[j]));
             }
             __syncthreads();
         }
@@ -157,62 +159,174 @@ k_tridiag(const double *__restrict__ A, int64_t N, const int32_t *__restrict__ p
 
 // ---- tridiagonal helpers -------------------------------------------------------------------
 
-__device__ __forceinline__ int sturm_count(const double *d, const double *e2, int M, double x,
-                                           double pivmin)
+// Number of eigenvalues of the tridiagonal T (diagonal d, squared off-diagonal e2) below x, as
+// the number of sign changes in the leading principal minors p_i of T - xI:
+//   p_-1 = 1, p_0 = d_0 - x, p_i = (d_i - x) p_{i-1} - e2_{i-1} p_{i-2}
+// (Sturm sequence). On B300 every warp-wide FP64 instruction costs ~64 cycles of its SM
+// sub-partition, so the step uses three (sub, mul, fma) and does signs, zero tests and the
+// power-of-two rescaling that keeps magnitudes in range on the integer bit patterns. An exact
+// zero minor takes the sign opposite to its predecessor, as the ratio form's -pivmin does.
+__device__ __forceinline__ int sturm3(const double *d, const double *e2, int M, double x)
 {
-    double q = d[0] - x;
-    if (fabs(q) < pivmin) q = -pivmin;
-    int cnt = q < 0.0;
+    double pp = 1.0, pc = d[0] - x;
+    long long bc = __double_as_longlong(pc);
+    if ((bc << 1) == 0) { pc = -0x1.0p-60; bc = __double_as_longlong(pc); }
+    int cnt = bc < 0;
     for (int i = 1; i < M; i++) {
-        q = (d[i] - x) - e2[i - 1] / q;
-        if (fabs(q) < pivmin) q = -pivmin;
-        cnt += q < 0.0;
+        double pn = fma(d[i] - x, pc, -e2[i - 1] * pp);
+        long long bn = __double_as_longlong(pn);
+        if ((bn << 1) == 0) {                       // exact zero: opposite sign, tiny magnitude
+            pn = __longlong_as_double((bc & 0x7FFFFFFFFFFFFFFFll) ^ (~bc & (1ll << 63))) * 0x1.0p-60;
+            bn = __double_as_longlong(pn);
+        }
+        cnt += (int)(((unsigned long long)(bn ^ bc)) >> 63);
+        const int ex = (int)((bn >> 52) & 0x7FF);
+        if (ex > 1023 + 512 || ex < 1023 - 512) {
+            const double sc = __longlong_as_double((long long)(2046 - ex) << 52);   // 2^(1023 - ex)
+            pn *= sc;
+            pc *= sc;
+            bn = __double_as_longlong(pn);
+        }
+        pp = pc;
+        pc = pn;
+        bc = bn;
     }
     return cnt;
 }
 
-// Grid (ceil(mmax / 128), nb). Eigenvalue at ascending position (k0 - s + t) of T_b, t < m_b.
+__device__ __forceinline__ int sturm3f(const float *d, const float *e2, int M, float x)
+{
+    float pp = 1.0f, pc = d[0] - x;
+    int bc = __float_as_int(pc);
+    if ((bc << 1) == 0) { pc = -0x1.0p-30f; bc = __float_as_int(pc); }
+    int cnt = bc < 0;
+    for (int i = 1; i < M; i++) {
+        float pn = fmaf(d[i] - x, pc, -e2[i - 1] * pp);
+        int bn = __float_as_int(pn);
+        if ((bn << 1) == 0) {
+            pn = __int_as_float((bc & 0x7FFFFFFF) ^ (~bc & (int)0x80000000)) * 0x1.0p-30f;
+            bn = __float_as_int(pn);
+        }
+        cnt += (int)(((unsigned)(bn ^ bc)) >> 31);
+        const int ex = (bn >> 23) & 0xFF;
+        if (ex > 127 + 48 || ex < 127 - 48) {
+            const float sc = __int_as_float((254 - ex) << 23);                     // 2^(127 - ex)
+            pn *= sc;
+            pc *= sc;
+            bn = __float_as_int(pn);
+        }
+        pp = pc;
+        pc = pn;
+        bc = bn;
+    }
+    return cnt;
+}
+
+// Newton correction -p_M(x) / p_M'(x) for det(T - xI), from the three-term recurrence of the
+// minors and of their derivatives p_i' = (d_i - x) p_{i-1}' - p_{i-1} - e2_{i-1} p_{i-2}', both
+// rescaled together by powers of two.
+__device__ __forceinline__ double newton_step(const double *d, const double *e2, int M, double x)
+{
+    double pp = 1.0, pc = d[0] - x, qp = 0.0, qc = -1.0;
+    for (int i = 1; i < M; i++) {
+        const double dx = d[i] - x, f = e2[i - 1];
+        const double pn = fma(dx, pc, -f * pp);
+        const double qn = fma(dx, qc, -fma(f, qp, pc));
+        const int ex = (int)((__double_as_longlong(pn) >> 52) & 0x7FF);
+        const int eq = (int)((__double_as_longlong(qn) >> 52) & 0x7FF);
+        const int em = ex > eq ? ex : eq;
+        pp = pc; qp = qc; pc = pn; qc = qn;
+        if (em > 1023 + 512 || (em < 1023 - 512 && em > 0)) {
+            const double sc = __longlong_as_double((long long)(2046 - em) << 52);
+            pp *= sc; qp *= sc; pc *= sc; qc *= sc;
+        }
+    }
+    return (qc != 0.0) ? -pc / qc : 0.0;
+}
+
+// One selected eigenvalue per lane, grid (ceil(mmax / 32), nb), 32 threads: the eigenvalue at
+// ascending position (k0 - s + t) of T_b. FP32 bisection (cheap on B300) brackets it to 8 FP32
+// ulps of ||T||; three FP64 Newton steps on det(T - xI) from the bracket's midpoint take it to
+// FP64 accuracy (quadratic convergence while |x - lambda| is far below the gap to the next
+// eigenvalue); two FP64 Sturm counts at x -/+ tol certify that the result is the eigenvalue at
+// that position to within tol = 4 ulp |x| + 2 ulp ||T||. A lane that fails the check falls back
+// to FP64 bisection (first on the widened FP32 bracket if its ends check out, else on the
+// Gershgorin interval).
 __global__ void k_bisect(const int32_t *__restrict__ plan, int32_t nb, int32_t Mmax, int32_t mmax,
                          const double *__restrict__ td, const double *__restrict__ te,
                          double *__restrict__ sel_val)
 {
     const int b = blockIdx.y;
     const int k0 = plan[b], mb = plan[nb + b], s = plan[2 * nb + b], M = plan[3 * nb + b];
+    if (blockIdx.x * blockDim.x >= mb) return;
     extern __shared__ double smd[];
     double *d = smd, *e2 = smd + Mmax;
-    __shared__ double s_lo, s_hi, s_piv, s_atol;
+    float *df = reinterpret_cast<float *>(smd + 2 * Mmax), *e2f = df + Mmax;
+    __shared__ double s_lo, s_hi, s_atol;
     const double *bd = td + (size_t)b * Mmax, *be = te + (size_t)b * Mmax;
     for (int i = threadIdx.x; i < M; i += blockDim.x) {
         d[i] = bd[i];
         e2[i] = (i + 1 < M) ? be[i] * be[i] : 0.0;
+        df[i] = (float)d[i];
+        e2f[i] = (float)e2[i];
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double lo = INFINITY, hi = -INFINITY, emax2 = 0.0;
+        double lo = INFINITY, hi = -INFINITY;
         for (int i = 0; i < M; i++) {
             double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < M ? fabs(be[i]) : 0.0);
             lo = fmin(lo, d[i] - r);
             hi = fmax(hi, d[i] + r);
-            if (i + 1 < M) emax2 = fmax(emax2, e2[i]);
         }
         double span = fmax(fabs(lo), fabs(hi));
         s_lo = lo - 2.0 * DBL_EPSILON * span - DBL_MIN;
         s_hi = hi + 2.0 * DBL_EPSILON * span + DBL_MIN;
-        s_piv = DBL_MIN * fmax(1.0, emax2);
-        s_atol = DBL_EPSILON * span;   // absolute accuracy of any backward-stable solver
+        s_atol = DBL_EPSILON * span;
     }
     __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= mb) return;
     const int pos = k0 - s + t;
-    double lo = s_lo, hi = s_hi;
-    for (int it = 0; it < 256; it++) {
-        double mid = 0.5 * (lo + hi);
-        if (mid <= lo || mid >= hi) break;
-        if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + s_atol) break;
-        if (sturm_count(d, e2, M, mid, s_piv) > pos) hi = mid; else lo = mid;
+    const double span = s_atol / DBL_EPSILON;
+    float flo = (float)s_lo, fhi = (float)s_hi;
+    const float ftol = 8.0f * FLT_EPSILON * (float)span;
+    for (int it = 0; it < 160 && fhi - flo > ftol; it++) {
+        const float mid = 0.5f * (flo + fhi);
+        if (mid <= flo || mid >= fhi) break;
+        if (sturm3f(df, e2f, M, mid) > pos) fhi = mid; else flo = mid;
     }
-    sel_val[(size_t)b * mmax + t] = 0.5 * (lo + hi);
+    const double widen = 32.0 * FLT_EPSILON * span;
+    const double blo = fmax(s_lo, (double)flo - widen), bhi = fmin(s_hi, (double)fhi + widen);
+    double x = 0.5 * ((double)flo + (double)fhi);
+    for (int it = 0; it < 3; it++) {
+        const double xn = x + newton_step(d, e2, M, x);
+        if (!(xn >= blo && xn <= bhi)) break;        // left the bracket: keep the last iterate
+        x = xn;
+    }
+    const double tol = 4.0 * DBL_EPSILON * fabs(x) + 2.0 * s_atol;
+    if (!(sturm3(d, e2, M, x - tol) <= pos && sturm3(d, e2, M, x + tol) > pos)) {
+        double lo = blo, hi = bhi;
+        if (!(sturm3(d, e2, M, lo) <= pos && sturm3(d, e2, M, hi) > pos)) { lo = s_lo; hi = s_hi; }
+        for (int it = 0; it < 256; it++) {
+            const double mid = 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi) break;
+            if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + s_atol) break;
+            if (sturm3(d, e2, M, mid) > pos) hi = mid; else lo = mid;
+        }
+        x = 0.5 * (lo + hi);
+    }
+    sel_val[(size_t)b * mmax + t] = x;
+}
+
+// Reciprocal without an IEEE FP64 division (~640 cycles dependent on B300): FP32 estimate and two
+// Newton steps y <- y (2 - p y), accurate to about 1 ulp for |p| in FP32's normal range (pivots
+// are clamped to [eps ||T||, ~||T||] by the caller).
+__device__ __forceinline__ double fast_rcp(double p)
+{
+    double y = (double)__frcp_rn((float)p);
+    y = y * fma(-p, y, 2.0);
+    y = y * fma(-p, y, 2.0);
+    return y;
 }
 
 __device__ __forceinline__ double hash_unit(uint32_t a, uint32_t b, uint32_t c)
@@ -225,10 +339,13 @@ __device__ __forceinline__ double hash_unit(uint32_t a, uint32_t b, uint32_t c)
     return ((double)(z >> 11) * 0x1.0p-53) * 2.0 - 1.0;   // (-1, 1)
 }
 
-// Grid (ceil(mmax / 64), nb), 64 threads. Thread t computes the unit eigenvector of T_b for the
-// selected eigenvalue t. Members of a cluster (consecutive selected eigenvalues closer than
-// gaptol) are computed one after another by the cluster's first thread and orthogonalised
-// against each other (modified Gram-Schmidt) after every solve.
+// Grid (ceil(mmax / 32), nb), 32 threads: lane t computes the unit eigenvector of T_b for the
+// selected eigenvalue t by two inverse-iteration solves with a pivoted tridiagonal LU of
+// T - lambda I (reciprocal pivots clamped to |pivot| >= eps ||T||). Members of a cluster
+// (consecutive selected eigenvalues closer than gaptol) are computed one after another by the
+// cluster's first lane and orthogonalised against each other (modified Gram-Schmidt) after every
+// solve. Per-lane work arrays are interleaved across lanes (element i of lane t at i * stride + t)
+// so that the sequential sweeps issue coalesced loads.
 __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int32_t Mmax,
                                int32_t mmax, const double *__restrict__ td,
                                const double *__restrict__ te, const double *__restrict__ sel_val,
@@ -238,73 +355,94 @@ __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int
     const int mb = plan[nb + b], M = plan[3 * nb + b];
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= mb) return;
-    const double *d = td + (size_t)b * Mmax, *e = te + (size_t)b * Mmax;
+    const double *__restrict__ d = td + (size_t)b * Mmax;
+    const double *__restrict__ e = te + (size_t)b * Mmax;
     const double *lam = sel_val + (size_t)b * mmax;
     double tnorm = 0.0;
     for (int i = 0; i < M; i++)
         tnorm = fmax(tnorm, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < M ? fabs(e[i]) : 0.0));
     const double gaptol = 1e-9 * fmax(tnorm, DBL_MIN);
-    if (t > 0 && lam[t] - lam[t - 1] < gaptol) return;     // handled by the cluster's first thread
-    const size_t stride = (size_t)nb * mmax;                 // interleaved per-thread storage
+    if (t > 0 && lam[t] - lam[t - 1] < gaptol) return;     // handled by the cluster's first lane
+    const size_t stride = (size_t)nb * mmax;
     const size_t me = (size_t)b * mmax + t;
-    double *u0 = work + me, *u1 = work + stride * Mmax + me, *u2 = work + 2 * stride * Mmax + me;
-    double *lm = work + 3 * stride * Mmax + me, *pv = work + 4 * stride * Mmax + me;
+    double *__restrict__ u0 = work + me;                    // reciprocal pivots
+    double *__restrict__ u1 = work + stride * Mmax + me;
+    double *__restrict__ u2 = work + 2 * stride * Mmax + me;
+    double *__restrict__ lm = work + 3 * stride * Mmax + me; // multipliers, sign bit = row swap
+    double *__restrict__ z = work + 4 * stride * Mmax + me;
     const double pert = DBL_EPSILON * fmax(tnorm, DBL_MIN);
     int last = t;
     while (last + 1 < mb && lam[last + 1] - lam[last] < gaptol) last++;
     for (int j = t; j <= last; j++) {
         const double x = lam[j];
-        double *z = sel_vec + ((size_t)b * mmax + j) * Mmax;
-        // pivoted LU of T - x I: rows (p, q, r) = entries at columns (i, i+1, i+2)
+        // pivoted LU of T - x I: rows (p, q, r) = entries at columns (i, i+1, i+2). The row-swap
+        // flag is kept in the lowest mantissa bit of the stored multiplier (a 1-ulp change).
         double p = d[0] - x, q = (M > 1) ? e[0] : 0.0, r = 0.0;
+#pragma unroll 4
         for (int i = 0; i + 1 < M; i++) {
-            double ei = e[i], an = d[i + 1] - x, en = (i + 2 < M) ? e[i + 1] : 0.0;
-            if (fabs(p) >= fabs(ei)) {
-                double l = (p != 0.0) ? ei / p : 0.0;
-                u0[i * stride] = (p != 0.0) ? p : pert; u1[i * stride] = q; u2[i * stride] = r;
-                lm[i * stride] = l; pv[i * stride] = 0.0;
-                p = an - l * q; q = en - l * r; r = 0.0;
-            } else {
-                double l = p / ei;
-                u0[i * stride] = ei; u1[i * stride] = an; u2[i * stride] = en;
-                lm[i * stride] = l; pv[i * stride] = 1.0;
-                double np = q - l * an, nq = r - l * en;
-                p = np; q = nq; r = 0.0;
-            }
+            const double ei = e[i], an = d[i + 1] - x, en = (i + 2 < M) ? e[i + 1] : 0.0;
+            const bool swp = !(fabs(p) >= fabs(ei));
+            const double piv = swp ? ei : p;
+            const double pc = fabs(piv) >= pert ? piv : (piv < 0.0 ? -pert : pert);
+            const double rp = fast_rcp(pc);
+            const double l = swp ? p * rp : ((p != 0.0) ? ei * rp : 0.0);
+            u0[i * stride] = rp;
+            u1[i * stride] = swp ? an : q;
+            u2[i * stride] = swp ? en : r;
+            const long long lb = __double_as_longlong(l);
+            lm[i * stride] = __longlong_as_double(swp ? (lb | 1ll) : (lb & ~1ll));
+            const double np = swp ? fma(-l, an, q) : fma(-l, q, an);
+            const double nq = swp ? fma(-l, en, r) : fma(-l, r, en);
+            p = np; q = nq; r = 0.0;
         }
-        u0[(size_t)(M - 1) * stride] = (p != 0.0) ? p : pert;
-        for (int i = 0; i < M; i++) z[i] = hash_unit(b, j, i);
-        for (int it = 0; it < 3; it++) {
+        u0[(size_t)(M - 1) * stride] = fast_rcp(fabs(p) >= pert ? p : (p < 0.0 ? -pert : pert));
+        u1[(size_t)(M - 1) * stride] = 0.0;      // read (times zero) by the back substitution
+        u2[(size_t)(M - 1) * stride] = 0.0;
+        for (int i = 0; i < M; i++) z[i * stride] = hash_unit(b, j, i);
+        for (int it = 0; it < 2; it++) {
             // forward: replay the row operations on the right-hand side
+            double zi = z[0];
+#pragma unroll 4
             for (int i = 0; i + 1 < M; i++) {
-                double zi = z[i], zn = z[i + 1], l = lm[i * stride];
-                if (pv[i * stride] != 0.0) { z[i] = zn; z[i + 1] = zi - l * zn; }
-                else z[i + 1] = zn - l * zi;
+                const double lraw = lm[i * stride];
+                const bool swp = (__double_as_longlong(lraw) & 1ll) != 0;
+                const double l = lraw;       // the flag bit perturbs l by at most 1 ulp
+                const double zn = z[(i + 1) * stride];
+                if (swp) { z[i * stride] = zn; zi = fma(-l, zn, zi); }
+                else { z[i * stride] = zi; zi = fma(-l, zi, zn); }
             }
+            z[(size_t)(M - 1) * stride] = zi;
             // back substitution with the three upper diagonals
+            double z1 = 0.0, z2 = 0.0;
+#pragma unroll 4
             for (int i = M - 1; i >= 0; i--) {
-                double acc = z[i];
-                if (i + 1 < M) acc -= u1[i * stride] * z[i + 1];
-                if (i + 2 < M) acc -= u2[i * stride] * z[i + 2];
-                double piv = u0[i * stride];
-                if (fabs(piv) < pert) piv = (piv < 0.0) ? -pert : pert;
-                z[i] = acc / piv;
+                const double acc = fma(-u2[i * stride], z2, fma(-u1[i * stride], z1, z[i * stride]));
+                const double zi2 = acc * u0[i * stride];
+                z[i * stride] = zi2;
+                z2 = z1;
+                z1 = zi2;
             }
             // orthogonalise against earlier cluster members, then normalise
             for (int c = t; c < j; c++) {
                 const double *zc = sel_vec + ((size_t)b * mmax + c) * Mmax;
                 double dot = 0.0;
-                for (int i = 0; i < M; i++) dot += zc[i] * z[i];
-                for (int i = 0; i < M; i++) z[i] -= dot * zc[i];
+                for (int i = 0; i < M; i++) dot = fma(zc[i], z[i * stride], dot);
+                for (int i = 0; i < M; i++) z[i * stride] = fma(-dot, zc[i], z[i * stride]);
             }
             double mx = 0.0;
-            for (int i = 0; i < M; i++) mx = fmax(mx, fabs(z[i]));
-            if (mx == 0.0 || !isfinite(mx)) { for (int i = 0; i < M; i++) z[i] = hash_unit(b, j + 7919, i + it); continue; }
+            for (int i = 0; i < M; i++) mx = fmax(mx, fabs(z[i * stride]));
+            if (mx == 0.0 || !isfinite(mx)) {
+                for (int i = 0; i < M; i++) z[i * stride] = hash_unit(b, j + 7919, i + it);
+                continue;
+            }
+            const double imx = fast_rcp(mx);
             double nrm = 0.0;
-            for (int i = 0; i < M; i++) { z[i] /= mx; nrm += z[i] * z[i]; }
-            nrm = 1.0 / sqrt(nrm);
-            for (int i = 0; i < M; i++) z[i] *= nrm;
+            for (int i = 0; i < M; i++) { const double v = z[i * stride] * imx; z[i * stride] = v; nrm = fma(v, v, nrm); }
+            const double inr = rsqrt(nrm);
+            for (int i = 0; i < M; i++) z[i * stride] *= inr;
         }
+        double *out = sel_vec + ((size_t)b * mmax + j) * Mmax;
+        for (int i = 0; i < M; i++) out[i] = z[i * stride];
     }
 }
 
@@ -389,7 +527,7 @@ cudaError_t configure_kernels(pfsm_handle_s *h)
         if ((e = cudaFuncSetAttribute(k_tridiag<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
         if (CL > 8 && (e = cudaFuncSetAttribute(k_tridiag<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
     }
-    if ((e = cudaFuncSetAttribute(k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * Mmax * sizeof(double)))) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(3 * Mmax * sizeof(double)))) != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * Mmax * sizeof(double)));
 }
 
@@ -397,6 +535,7 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
 {
     Workspace &w = h->ws;
     const int nb = h->nb, Mmax = h->Mmax, mmax = h->mmax, CL = h->cl;
+    cudaError_t e0;
     // 1. tridiagonalisation, one cluster per window
     {
         cudaLaunchConfig_t cfg = {};
@@ -423,20 +562,26 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
                                    w.iiwork, w.refl, w.tau, w.td, w.te));
         if (e != cudaSuccess) return e;
     }
-    // 2. bisection
+    // one eigenpair per lane, full warps (a warp-wide FP64 instruction costs the same with 1 or
+    // 32 active lanes)
+    const int tpb = 32;
+    if (h->timing && (e0 = cudaEventRecord(h->sub_ev[0], st)) != cudaSuccess) return e0;
+    // 2. eigenvalues
     {
-        dim3 grid((unsigned)((mmax + 127) / 128), (unsigned)nb);
-        k_bisect<<<grid, 128, (size_t)2 * Mmax * sizeof(double), st>>>(w.plan, nb, Mmax, mmax, w.td, w.te, w.sel_val); g_launches++;
+        dim3 grid((unsigned)((mmax + tpb - 1) / tpb), (unsigned)nb);
+        k_bisect<<<grid, tpb, (size_t)3 * Mmax * sizeof(double), st>>>(w.plan, nb, Mmax, mmax, w.td, w.te, w.sel_val); g_launches++;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    if (h->timing && (e0 = cudaEventRecord(h->sub_ev[1], st)) != cudaSuccess) return e0;
     // 3. inverse iteration
     {
-        dim3 grid((unsigned)((mmax + 63) / 64), (unsigned)nb);
-        k_inverse_iter<<<grid, 64, 0, st>>>(w.plan, nb, Mmax, mmax, w.td, w.te, w.sel_val, w.sel_vec, w.iiwork); g_launches++;
+        dim3 grid((unsigned)((mmax + tpb - 1) / tpb), (unsigned)nb);
+        k_inverse_iter<<<grid, tpb, 0, st>>>(w.plan, nb, Mmax, mmax, w.td, w.te, w.sel_val, w.sel_vec, w.iiwork); g_launches++;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    if (h->timing && (e0 = cudaEventRecord(h->sub_ev[2], st)) != cudaSuccess) return e0;
     // 4. back-transform + start vectors
     {
         dim3 grid((unsigned)((mmax + 7) / 8), (unsigned)nb);

@@ -35,6 +35,7 @@ struct Workspace {
     double *W = nullptr;           // N*N A V (rows), backward scratch
     double *Vrm = nullptr;         // N*N V in output layout (kept for backward)
     double *sdiag = nullptr;       // N diag(S) before factorisation
+    double *Linv = nullptr;        // N x 64 inverses of the 64 x 64 diagonal blocks of L
     double *eps = nullptr, *alpha = nullptr, *lam = nullptr, *res = nullptr; // N each
     // submatrix eigensolver
     double *refl = nullptr;        // nb * Mmax * Mmax Householder vectors (row k = v_k)
@@ -71,6 +72,7 @@ struct pfsm_handle_s {
     // instrumentation
     bool timing = false;
     cudaEvent_t ev[8] = {};
+    cudaEvent_t sub_ev[4] = {};   // inside the submatrix phase (timing only)
     int32_t last_launches = 0;
     bool last_was_backward = false;
 };
