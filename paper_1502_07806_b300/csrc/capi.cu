@@ -169,6 +169,7 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
     if (e == cudaSuccess && prm.slice_sizes)
         e = cudaMemcpy(w.slices, prm.slice_sizes, sizeof(int32_t) * nblocks, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = configure_kernels(h);
+    if (e == cudaSuccess) e = configure_dense_kernels();
     if (e != cudaSuccess) {
         int code = (e == cudaErrorMemoryAllocation) ? PFSM_ERR_OUT_OF_MEMORY : PFSM_ERR_CUDA;
         free_ws(h);

@@ -22,59 +22,112 @@ __global__ void k_copy_diag(const double *__restrict__ S, int64_t N, double *__r
     if (i < N) d[i] = S[i * N + i];
 }
 
-// Unblocked Cholesky of the b x b diagonal block at (jb, jb), in shared memory, one CTA; also
-// writes the block's inverse L_jj^-1 (lower triangular, b x b, leading dimension CB) to Linv.
-__global__ void k_potrf_inv(double *__restrict__ S, int64_t N, int64_t jb, int b,
-                            const double *__restrict__ sdiag, int32_t *status,
-                            double *__restrict__ Linv)
+// 1/sqrt(d) without FP64 sqrt/divide sequences (~10 dependent FP64 instructions, ~64 cycles each
+// on B300): FP32 estimate and two Newton steps y <- y (3 - d y^2) / 2. Needs d in FP32 range.
+__device__ __forceinline__ double fast_rsqrt(double d)
 {
-    __shared__ double L[CB][CB + 1];
-    for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
-        int i = t / b, k = t % b;
-        L[i][k] = (k <= i) ? S[(jb + i) * N + jb + k] : 0.0;
+    double y = (double)rsqrtf((float)d);
+    y = y * fma(-0.5 * d, y * y, 1.5);
+    y = y * fma(-0.5 * d, y * y, 1.5);
+    return y;
+}
+
+// Cholesky of the b x b diagonal block at (jb, jb), in shared memory, one CTA of 256 threads; also
+// writes the block's inverse L_jj^-1 (lower triangular, CB x CB, zero padded) to Linv.
+// The inverse is formed in two levels, L = [A 0; B C] -> L^-1 = [A^-1 0; -C^-1 B A^-1 C^-1]: the
+// two 32 x 32 diagonal inverses are built concurrently row by row (each row's sums split four
+// ways), then the off-diagonal block is two 32 x 32 x 32 products.
+__global__ void __launch_bounds__(256)
+k_potrf_inv(double *__restrict__ S, int64_t N, int64_t jb, int b, const double *__restrict__ sdiag,
+            int32_t *status, double *__restrict__ Linv)
+{
+    constexpr int H = CB / 2;
+    extern __shared__ double potrf_sm[];   // L and X, CB x (CB + 1) each (dynamic: > 48 KB)
+    double(*L)[CB + 1] = reinterpret_cast<double(*)[CB + 1]>(potrf_sm);
+    double(*X)[CB + 1] = reinterpret_cast<double(*)[CB + 1]>(potrf_sm + CB * (CB + 1));
+    __shared__ double R[CB];              // 1 / L_jj
+    __shared__ double part[4][2][H];
+    const int tid = threadIdx.x;
+    for (int t = tid; t < CB * CB; t += blockDim.x) {
+        const int i = t / CB, k = t % CB;
+        // pad the block to CB x CB with the identity so the fixed-size inverse stays exact
+        L[i][k] = (i < b && k < b) ? ((k <= i) ? S[(jb + i) * N + jb + k] : 0.0) : (i == k ? 1.0 : 0.0);
+        X[i][k] = 0.0;
     }
     __syncthreads();
     for (int j = 0; j < b; j++) {
-        if (threadIdx.x == 0) {
-            double d = L[j][j];
-            double ref = sqrt(fmax(sdiag[jb + j], 0.0));
-            double l = (d > 0.0) ? sqrt(d) : 0.0;
-            if (!(l >= 1e-8 * ref) || l == 0.0 || !isfinite(d)) {
+        if (tid == 0) {
+            const double d = L[j][j];
+            const double ref = sqrt(fmax(sdiag[jb + j], 0.0));
+            double y = (d > 0.0 && d < 1e300 && d > 1e-300) ? fast_rsqrt(d) : 0.0;
+            double l = d * y;
+            if (!(l >= 1e-8 * ref) || !(y > 0.0) || !isfinite(l)) {
                 set_status(status, PFSM_ERR_NOT_SPD);
                 l = 1.0;   // keep the arithmetic finite; the result is flagged as invalid
+                y = 1.0;
             }
             L[j][j] = l;
+            R[j] = y;
         }
         __syncthreads();
-        const double inv = 1.0 / L[j][j];
-        for (int i = j + 1 + threadIdx.x; i < b; i += blockDim.x) L[i][j] *= inv;
+        const double inv = R[j];
+        for (int i = j + 1 + tid; i < b; i += blockDim.x) L[i][j] *= inv;
         __syncthreads();
         const int rem = b - j - 1;
-        for (int t = threadIdx.x; t < rem * rem; t += blockDim.x) {
-            int i = j + 1 + t / rem, k = j + 1 + t % rem;
+        for (int t = tid; t < rem * rem; t += blockDim.x) {
+            const int i = j + 1 + t / rem, k = j + 1 + t % rem;
             if (k <= i) L[i][k] = fma(-L[i][j], L[k][j], L[i][k]);
         }
         __syncthreads();
     }
-    for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
-        int i = t / b, k = t % b;
+    for (int j = b + tid; j < CB; j += blockDim.x) R[j] = 1.0;
+    for (int t = tid; t < b * b; t += blockDim.x) {
+        const int i = t / b, k = t % b;
         if (k <= i) S[(jb + i) * N + jb + k] = L[i][k];
     }
-    // inverse: column c of L^-1 by forward substitution, one column per thread
-    for (int c = threadIdx.x; c < CB; c += blockDim.x) {
-        double x[CB];
-#pragma unroll
-        for (int i = 0; i < CB; i++) x[i] = 0.0;
-        if (c < b) {
-            for (int i = c; i < b; i++) {
-                double acc = (i == c) ? 1.0 : 0.0;
-                for (int k = c; k < i; k++) acc = fma(-L[i][k], x[k], acc);
-                x[i] = acc / L[i][i];
+    __syncthreads();
+    // level 1: A^-1 (rows 0..H-1) and C^-1 (rows H..CB-1), row by row
+    {
+        const int half = tid / 128, c = tid % H, pp = (tid % 128) / H;   // pp in 0..3
+        const int off = half * H;
+        for (int i = 0; i < H; i++) {
+            double sum = 0.0;
+            for (int k = c + pp; k < i; k += 4) sum = fma(L[off + i][off + k], X[off + k][off + c], sum);
+            part[pp][half][c] = sum;
+            __syncthreads();
+            if (pp == 0 && c <= i) {
+                const double t = part[0][half][c] + part[1][half][c] + part[2][half][c] + part[3][half][c];
+                X[off + i][off + c] = ((i == c) ? 1.0 - t : -t) * R[off + i];
             }
+            __syncthreads();
         }
-#pragma unroll
-        for (int i = 0; i < CB; i++) Linv[i * CB + c] = (c < b && i < b) ? x[i] : 0.0;
     }
+    // level 2: T = B A^-1 (kept in X's upper-right block, unused otherwise), then -C^-1 T
+    for (int t = tid; t < H * H; t += blockDim.x) {
+        const int i = t / H, c = t % H;
+        double acc = 0.0;
+        for (int k = c; k < H; k++) acc = fma(L[H + i][k], X[k][c], acc);
+        X[i][H + c] = acc;
+    }
+    __syncthreads();
+    for (int t = tid; t < H * H; t += blockDim.x) {
+        const int i = t / H, c = t % H;
+        double acc = 0.0;
+        for (int k = 0; k <= i; k++) acc = fma(X[H + i][H + k], X[k][H + c], acc);
+        X[H + i][c] = -acc;
+    }
+    __syncthreads();
+    for (int t = tid; t < CB * CB; t += blockDim.x) {
+        const int i = t / CB, k = t % CB;
+        Linv[i * CB + k] = (i < b && k <= i) ? X[i][k] : 0.0;
+    }
+}
+
+constexpr size_t kPotrfSmem = 2 * CB * (CB + 1) * sizeof(double);
+
+cudaError_t configure_dense_kernels()
+{
+    return cudaFuncSetAttribute(k_potrf_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPotrfSmem);
 }
 
 cudaError_t launch_gram_schmidt_f64(pfsm_handle_s *h, cudaStream_t st)
@@ -92,7 +145,7 @@ cudaError_t launch_gram_schmidt_f64(pfsm_handle_s *h, cudaStream_t st)
     for (int64_t jb = 0; jb < N; jb += CB) {
         const int b = (int)((N - jb) < CB ? (N - jb) : CB);
         double *Li = w.Linv + jb * CB;
-        k_potrf_inv<<<1, 256, 0, st>>>(w.S, N, jb, b, w.sdiag, w.status, Li); g_launches++;
+        k_potrf_inv<<<1, 256, kPotrfSmem, st>>>(w.S, N, jb, b, w.sdiag, w.status, Li); g_launches++;
         const int64_t rest = N - jb - b;
         if (rest <= 0) break;
         // panel: L[rest, jb] = S[rest, jb] L_jj^-T (one CTA per row tile: in place is safe)

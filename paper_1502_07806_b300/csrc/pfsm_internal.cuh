@@ -147,6 +147,7 @@ inline int slices_for(int precision) { return precision == PFSM_BF16_SPLIT ? 3 :
 inline int slice_kind(int precision) { return precision == PFSM_BF16_SPLIT ? 0 : 1; }
 inline int64_t padded_ld(int64_t n) { return (n + 63) / 64 * 64; }
 
+cudaError_t configure_dense_kernels();   // shared-memory attributes of k_dense.cu
 cudaError_t launch_gram_schmidt_f64(pfsm_handle_s *h, cudaStream_t st);
 cudaError_t launch_rayleigh_f64(pfsm_handle_s *h, const double *A, double *eigvals_out,
                                 double *V_out, cudaStream_t st);
