@@ -134,6 +134,34 @@ int pfsm_get_status(pfsm_handle_t h, int32_t *device_status);
  * Returns PFSM_ERR_INVALID_ARG for an unknown `which`, PFSM_ERR_NO_SOLVE before a solve. */
 int pfsm_get_diagnostic(pfsm_handle_t h, int32_t which, void *out, void *stream);
 
+/* ---- batches of independent problems (k-points / spin channels of one SCF step) ---------
+ * Not in the paper. A batch owns one workspace per problem and a set of internal streams;
+ * problems are assigned longest first (N^3) to the least-loaded stream so small problems run
+ * beside large ones. The first pfsm_solve_batched call with a given set of buffers and stream
+ * captures the fork / per-problem solves / join into a CUDA graph; later calls with the same
+ * buffers replay it with one graph launch (new buffers trigger a new capture). */
+typedef struct pfsm_batch_s *pfsm_batch_t;
+
+/* count problems; N[i], nblocks[i] (HOST arrays) as for pfsm_init; p shared by all problems
+ * (p->slice_sizes is ignored). Allocates every problem's workspace. */
+int pfsm_batch_init(int32_t count, const int64_t *N, const int32_t *nblocks, const pfsm_params_t *p,
+                    pfsm_batch_t *out);
+
+/* A, prev, eigvals_out, V_out: HOST arrays of `count` DEVICE pointers, each laid out as in
+ * pfsm_solve for its own N[i]. Ordered on `stream` (any stream, including the legacy default):
+ * the graph runs on a private stream of the batch after the caller's earlier work on `stream`,
+ * and later work on `stream` waits for it. Not synchronised. The buffers must stay valid until
+ * the stream reaches the end of the call. */
+int pfsm_solve_batched(pfsm_batch_t b, const double *const *A, const double *const *prev,
+                       double *const *eigvals_out, double *const *V_out, void *stream);
+
+/* Synchronises the batch's last stream and writes each problem's device status word to
+ * statuses[i] (HOST array of count int32). */
+int pfsm_batch_get_status(pfsm_batch_t b, int32_t *statuses);
+
+/* Frees the batch (synchronises the device first). NULL is allowed. */
+int pfsm_batch_destroy(pfsm_batch_t b);
+
 /* Split-precision product on the tcgen05 tensor cores, the building block of the mixed forms
  * (Eq. 11 products). C[r, c] = sum_k P[r, k] Q[c, k] for FP64 row-major P (rows x K), Q
  * (cols x K) and C (rows x cols), all device pointers. Each operand is split into BF16 (3

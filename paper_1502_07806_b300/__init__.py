@@ -23,7 +23,8 @@ DIAG_RESIDUALS, DIAG_XFS, DIAG_EPS, DIAG_ALPHA, DIAG_PLAN = range(5)
 
 EXPORTED = ("pfsm_default_params", "pfsm_init", "pfsm_solve", "pfsm_backward", "pfsm_get_status",
             "pfsm_get_diagnostic", "pfsm_set_timing", "pfsm_get_profile", "pfsm_last_error",
-            "pfsm_destroy", "pfsm_fs_iterate_noalloc", "pfsm_split_gemm")
+            "pfsm_destroy", "pfsm_fs_iterate_noalloc", "pfsm_split_gemm", "pfsm_batch_init",
+            "pfsm_solve_batched", "pfsm_batch_get_status", "pfsm_batch_destroy")
 PHASES = ("plan", "submatrix", "fs_iterations", "gram_schmidt", "rayleigh", "backward")
 SUB_PHASES = ("tridiag", "bisect", "inverse_iter", "backtransform")
 
@@ -68,6 +69,10 @@ def load_library():
     lib.pfsm_get_diagnostic.argtypes = [P, i32, P, P]
     lib.pfsm_fs_iterate_noalloc.argtypes = [i64, i64, P, P, P, P, i32, P]
     lib.pfsm_split_gemm.argtypes = [i64, i64, i64, P, P, P, i32, P]
+    lib.pfsm_batch_init.argtypes = [i32, P, P, ctypes.POINTER(Params), ctypes.POINTER(P)]
+    lib.pfsm_solve_batched.argtypes = [P, P, P, P, P, P]
+    lib.pfsm_batch_get_status.argtypes = [P, P]
+    lib.pfsm_batch_destroy.argtypes = [P]
     lib.pfsm_set_timing.argtypes = [P, i32]
     lib.pfsm_get_profile.argtypes = [P, ctypes.POINTER(Profile)]
     lib.pfsm_last_error.argtypes = []
@@ -192,6 +197,56 @@ def fs_iterate_noalloc(A: torch.Tensor, X_rows: torch.Tensor, eps: torch.Tensor,
                                                   _ptr(alpha), iters, _stream()),
            "pfsm_fs_iterate_noalloc")
     return X_rows
+
+
+class Batch:
+    """Many independent problems of uneven N solved by one captured CUDA graph."""
+
+    def __init__(self, sizes, nblocks, halo: int = -1, fs_iters: int = 3, precision: int = FP64,
+                 alpha_theta: float = 1.0, cluster_tol: float = 1e-5):
+        lib = load_library()
+        p = default_params()
+        p.halo, p.fs_iters, p.precision = halo, fs_iters, precision
+        p.alpha_theta, p.cluster_tol = alpha_theta, cluster_tol
+        self.sizes = [int(n) for n in sizes]
+        self.count = len(self.sizes)
+        ns = (ctypes.c_int64 * self.count)(*self.sizes)
+        nb = (ctypes.c_int32 * self.count)(*[int(x) for x in nblocks])
+        b = ctypes.c_void_p()
+        _check(lib.pfsm_batch_init(self.count, ns, nb, ctypes.byref(p), ctypes.byref(b)), "pfsm_batch_init")
+        self._b = b
+
+    @staticmethod
+    def _ptrs(ts):
+        return (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+    def solve(self, As, prevs, lams=None, Vs=None):
+        if lams is None:
+            lams = [torch.empty(n, dtype=torch.float64, device="cuda") for n in self.sizes]
+        if Vs is None:
+            Vs = [torch.empty(n, n, dtype=torch.float64, device="cuda") for n in self.sizes]
+        for t in list(As) + list(prevs) + list(lams) + list(Vs):
+            _ptr(t)   # type / device / layout checks
+        _check(load_library().pfsm_solve_batched(self._b, self._ptrs(As), self._ptrs(prevs),
+                                                 self._ptrs(lams), self._ptrs(Vs), _stream()),
+               "pfsm_solve_batched")
+        return lams, Vs
+
+    def status(self):
+        out = (ctypes.c_int32 * self.count)()
+        _check(load_library().pfsm_batch_get_status(self._b, out), "pfsm_batch_get_status")
+        return list(out)
+
+    def close(self):
+        if getattr(self, "_b", None):
+            load_library().pfsm_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def split_gemm(P: torch.Tensor, Q: torch.Tensor, precision: int = BF16_SPLIT) -> torch.Tensor:

@@ -59,6 +59,8 @@ constexpr size_t kSmemCap = 227 * 1024;
 
 }  // namespace
 
+void pfsm::set_last_error(const char *msg) { g_last_error = msg; }
+
 extern "C" {
 
 void pfsm_default_params(pfsm_params_t *p)

@@ -141,24 +141,26 @@ cudaError_t launch_gram_schmidt_f64(pfsm_handle_s *h, cudaStream_t st)
     g.P = w.X; g.ldp = N; g.Q = w.X; g.ldq = N; g.C = w.S; g.ldc = N; g.lower_only = 1;
     if ((e = launch_gemm_f64(g, EPI_STORE, Q_KMAJOR, st)) != cudaSuccess) return e;
     k_copy_diag<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(w.S, N, w.sdiag); g_launches++;
-    // blocked right-looking Cholesky S = L L^T; L_jj^-1 kept per block in Linv
+    // blocked right-looking Cholesky S = L L^T: diagonal blocks of L stay in S with their inverses in
+    // Linv, the off-diagonal panels of L go to W
     for (int64_t jb = 0; jb < N; jb += CB) {
         const int b = (int)((N - jb) < CB ? (N - jb) : CB);
         double *Li = w.Linv + jb * CB;
         k_potrf_inv<<<1, 256, kPotrfSmem, st>>>(w.S, N, jb, b, w.sdiag, w.status, Li); g_launches++;
         const int64_t rest = N - jb - b;
         if (rest <= 0) break;
-        // panel: L[rest, jb] = S[rest, jb] L_jj^-T (one CTA per row tile: in place is safe)
+        // panel: L[rest, jb] = S[rest, jb] L_jj^-T, written to W at the same position (not in
+        // place: several CTAs read each row of the operand)
         GemmArgs pn{};
         pn.rows = rest; pn.cols = b; pn.K = b;
         pn.P = w.S + (jb + b) * N + jb; pn.ldp = N;
         pn.Q = Li; pn.ldq = CB;
-        pn.C = w.S + (jb + b) * N + jb; pn.ldc = N;
+        pn.C = w.W + (jb + b) * N + jb; pn.ldc = N;
         if ((e = launch_gemm_f64(pn, EPI_STORE, Q_KMAJOR, st)) != cudaSuccess) return e;
         GemmArgs u{};
         u.rows = rest; u.cols = rest; u.K = b;
-        u.P = w.S + (jb + b) * N + jb; u.ldp = N;
-        u.Q = w.S + (jb + b) * N + jb; u.ldq = N;
+        u.P = w.W + (jb + b) * N + jb; u.ldp = N;
+        u.Q = w.W + (jb + b) * N + jb; u.ldq = N;
         u.C = w.S + (jb + b) * N + jb + b; u.ldc = N; u.lower_only = 1;
         if ((e = launch_gemm_f64(u, EPI_SUB, Q_KMAJOR, st)) != cudaSuccess) return e;
     }
@@ -175,7 +177,7 @@ cudaError_t launch_gram_schmidt_f64(pfsm_handle_s *h, cudaStream_t st)
         if (rest <= 0) break;
         GemmArgs u{};
         u.rows = rest; u.cols = N; u.K = b;
-        u.P = w.S + (jb + b) * N + jb; u.ldp = N;
+        u.P = w.W + (jb + b) * N + jb; u.ldp = N;        // off-diagonal panels of L live in W
         u.Q = w.Y + jb * N; u.ldq = N;
         u.C = w.X + (jb + b) * N; u.ldc = N;
         if ((e = launch_gemm_f64(u, EPI_SUB, Q_NMAJOR, st)) != cudaSuccess) return e;

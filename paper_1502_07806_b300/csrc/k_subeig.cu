@@ -17,6 +17,7 @@
 //   4. k_backtransform y = H_0 ... H_{M-3} z, sign rule, zero padding to length N, shift eps and
 //                     step alpha: one warp per start vector, written straight into X.
 #include <cooperative_groups.h>
+#include <algorithm>
 #include <cfloat>
 
 #include "pfsm_internal.cuh"
@@ -75,7 +76,8 @@ k_tridiag(const double *__restrict__ A, int64_t N, const int32_t *__restrict__ p
         double *dst = rowp(i);
         for (int j = lane; j < M; j += 32) dst[j] = src[j];
     }
-    __syncthreads();
+    // every CTA of the cluster must be running before any distributed-shared-memory access
+    cluster.sync();
     // broadcast column 0 (rows >= 1) into every CTA's vbuf
     for (int i = rank + threadIdx.x * CL; i < M; i += blockDim.x * CL) {
         if (i < 1) continue;
@@ -513,22 +515,28 @@ __global__ void k_backtransform(const int32_t *__restrict__ plan, int32_t nb, in
     }
 }
 
+// Function attributes are process-wide while handles differ in window size, so every attribute
+// is set to the device maximum (what a launch actually requests still sets its occupancy).
 cudaError_t configure_kernels(pfsm_handle_s *h)
 {
-    const int Mmax = h->Mmax, CL = h->cl;
-    const int R = (Mmax + CL - 1) / CL;
-    size_t smem = (size_t)(4 * Mmax + 64) * sizeof(double);
-    if (h->rows_in_smem) smem += (size_t)R * Mmax * sizeof(double);
-    cudaError_t e;
-    if (h->rows_in_smem) {
-        if ((e = cudaFuncSetAttribute(k_tridiag<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-        if (CL > 8 && (e = cudaFuncSetAttribute(k_tridiag<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
-    } else {
-        if ((e = cudaFuncSetAttribute(k_tridiag<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-        if (CL > 8 && (e = cudaFuncSetAttribute(k_tridiag<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
-    }
-    if ((e = cudaFuncSetAttribute(k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(3 * Mmax * sizeof(double)))) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * Mmax * sizeof(double)));
+    (void)h;
+    int dev = 0, cap = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    // dynamic limit = opt-in maximum minus the kernel's own static shared memory
+    auto set_max = [&](const void *fn) -> cudaError_t {
+        cudaFuncAttributes fa;
+        cudaError_t r = cudaFuncGetAttributes(&fa, fn);
+        if (r != cudaSuccess) return r;
+        return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, cap - (int)fa.sharedSizeBytes);
+    };
+    if ((e = set_max((const void *)k_tridiag<true>)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_tridiag<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
+    if ((e = set_max((const void *)k_tridiag<false>)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_tridiag<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
+    if ((e = set_max((const void *)k_bisect)) != cudaSuccess) return e;
+    return set_max((const void *)k_backtransform);
 }
 
 cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
@@ -584,8 +592,10 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
     if (h->timing && (e0 = cudaEventRecord(h->sub_ev[2], st)) != cudaSuccess) return e0;
     // 4. back-transform + start vectors
     {
-        dim3 grid((unsigned)((mmax + 7) / 8), (unsigned)nb);
-        k_backtransform<<<grid, 256, (size_t)8 * Mmax * sizeof(double), st>>>(
+        // one warp per vector, as many per CTA as shared memory holds (up to 8)
+        const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(227 * 1024) / ((size_t)Mmax * sizeof(double))));
+        dim3 grid((unsigned)((mmax + wpb - 1) / wpb), (unsigned)nb);
+        k_backtransform<<<grid, 32 * wpb, (size_t)wpb * Mmax * sizeof(double), st>>>(
             w.plan, nb, h->N, Mmax, mmax, w.refl, w.tau, w.sel_val, w.sel_vec, w.gersh,
             h->prm.alpha_theta, w.X, w.eps, w.alpha); g_launches++;
         return cudaGetLastError();

@@ -85,6 +85,9 @@ constexpr int kFsTileRows = 64;     // row tile of the FP64 GEMM (also the K-ran
 inline thread_local int64_t g_launches = 0;
 inline cudaError_t counted(cudaError_t e) { if (e == cudaSuccess) g_launches++; return e; }
 
+// Records the thread-local message returned by pfsm_last_error().
+void set_last_error(const char *msg);
+
 // ---- launchers (each enqueues on `st`; returns cudaGetLastError()) ----
 cudaError_t launch_validate_gersh(const double *A, const double *prev, int64_t N, double *gersh,
                                   int32_t *status, cudaStream_t st);
