@@ -48,7 +48,7 @@ void free_ws(pfsm_handle_s *h)
     void *ptrs[] = {w.plan, w.tile_krange, w.status, w.gersh, w.X, w.Xfs, w.Y, w.S, w.W, w.Vrm,
                     w.sdiag, w.eps, w.alpha, w.lam, w.res, w.refl, w.tau, w.td, w.te,
                     w.sel_val, w.sel_vec, w.iiwork, w.slices, w.slE, w.slX, w.slY, w.slZ,
-                    w.Z, w.dA, w.Linv};
+                    w.Z, w.dA, w.Linv, w.ozP, w.ozQ, w.ozeP, w.ozeQ};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     w = Workspace{};
@@ -165,7 +165,17 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
         w.slE = tmp[0]; w.slX = tmp[1]; w.slY = tmp[2]; w.slZ = tmp[3];
         PFSM_ALLOC(w.Z, NN);
         PFSM_ALLOC(w.dA, (size_t)N);
+        const size_t oz_bytes = (size_t)OZ_SLICES * N * padded_ld(N) * 2;
+        uint8_t *o1 = nullptr, *o2 = nullptr;
+        PFSM_ALLOC(o1, oz_bytes);
+        PFSM_ALLOC(o2, oz_bytes);
+        if (e == cudaSuccess) e = cudaMemset(o1, 0, oz_bytes);      // zero padding columns
+        if (e == cudaSuccess) e = cudaMemset(o2, 0, oz_bytes);
+        w.ozP = o1; w.ozQ = o2;
+        PFSM_ALLOC(w.ozeP, (size_t)N);
+        PFSM_ALLOC(w.ozeQ, (size_t)N);
         if (e == cudaSuccess) e = configure_tc_kernels();
+        if (e == cudaSuccess) e = configure_oz_kernels();
     }
 #undef PFSM_ALLOC
     if (e == cudaSuccess && prm.slice_sizes)
@@ -350,10 +360,41 @@ int pfsm_split_gemm(int64_t rows, int64_t cols, int64_t K, const double *P, cons
 {
     if (rows < 1 || cols < 1 || K < 1 || rows > 65535 || cols > 65535 || K > (1 << 24) || !P || !Q || !C)
         return fail(PFSM_ERR_INVALID_ARG, "pfsm_split_gemm: bad size or null pointer");
-    if (precision != PFSM_TF32_SPLIT && precision != PFSM_BF16_SPLIT)
-        return fail(PFSM_ERR_INVALID_ARG, "pfsm_split_gemm: precision must be a split form");
+    if (precision != PFSM_TF32_SPLIT && precision != PFSM_BF16_SPLIT && precision != PFSM_FP64)
+        return fail(PFSM_ERR_INVALID_ARG, "pfsm_split_gemm: unknown precision");
     cudaStream_t st = (cudaStream_t)stream;
     PFSM_CUDA(configure_tc_kernels());
+    if (precision == PFSM_FP64) {       // FP64-accurate: base-32 digits, exact level sums
+        PFSM_CUDA(configure_oz_kernels());
+        const int64_t ld = padded_ld(K);
+        void *sp = nullptr, *sq = nullptr;
+        int32_t *ep = nullptr, *eq = nullptr, *status = nullptr;
+        const size_t bp = (size_t)OZ_SLICES * rows * ld * 2, bq = (size_t)OZ_SLICES * cols * ld * 2;
+        PFSM_CUDA(cudaMallocAsync(&sp, bp, st));
+        PFSM_CUDA(cudaMallocAsync(&sq, bq, st));
+        PFSM_CUDA(cudaMallocAsync((void **)&ep, rows * sizeof(int32_t), st));
+        PFSM_CUDA(cudaMallocAsync((void **)&eq, cols * sizeof(int32_t), st));
+        PFSM_CUDA(cudaMallocAsync((void **)&status, sizeof(int32_t), st));
+        PFSM_CUDA(cudaMemsetAsync(sp, 0, bp, st));
+        PFSM_CUDA(cudaMemsetAsync(sq, 0, bq, st));
+        PFSM_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
+        SliceBuf dp{sp, rows, ld, OZ_SLICES, 0}, dq{sq, cols, ld, OZ_SLICES, 0};
+        PFSM_CUDA(launch_oz_split(P, rows, K, K, dp, ep, st));
+        PFSM_CUDA(launch_oz_split(Q, cols, K, K, dq, eq, st));
+        OzParams o{};
+        o.rows = (int)rows; o.cols = (int)cols; o.C = C; o.ldc = cols; o.status = status;
+        PFSM_CUDA(launch_gemm_oz(dp, ep, dq, eq, o, st));
+        int32_t hs = 0;
+        PFSM_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        PFSM_CUDA(cudaFreeAsync(sp, st));
+        PFSM_CUDA(cudaFreeAsync(sq, st));
+        PFSM_CUDA(cudaFreeAsync(ep, st));
+        PFSM_CUDA(cudaFreeAsync(eq, st));
+        PFSM_CUDA(cudaFreeAsync(status, st));
+        PFSM_CUDA(cudaStreamSynchronize(st));
+        if (hs != 0) return fail(hs, "pfsm_split_gemm: device status %d", hs);
+        return PFSM_OK;
+    }
     const int ns = slices_for(precision), kind = slice_kind(precision);
     const int64_t ld = padded_ld(K);
     const size_t esz = kind == 0 ? 2 : 4;

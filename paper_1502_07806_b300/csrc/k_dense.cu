@@ -135,11 +135,19 @@ cudaError_t launch_gram_schmidt_f64(pfsm_handle_s *h, cudaStream_t st)
     Workspace &w = h->ws;
     const int64_t N = h->N;
     cudaError_t e;
-    // S = X X^T (lower)
-    GemmArgs g{};
-    g.rows = N; g.cols = N; g.K = N;
-    g.P = w.X; g.ldp = N; g.Q = w.X; g.ldq = N; g.C = w.S; g.ldc = N; g.lower_only = 1;
-    if ((e = launch_gemm_f64(g, EPI_STORE, Q_KMAJOR, st)) != cudaSuccess) return e;
+    // S = X X^T (lower): DFMA in the FP64 form, FP64-accurate tensor-core digits in the mixed forms
+    if (h->prm.precision != PFSM_FP64) {
+        SliceBuf d{w.ozP, N, padded_ld(N), OZ_SLICES, 0};
+        if ((e = launch_oz_split(w.X, N, N, N, d, w.ozeP, st)) != cudaSuccess) return e;
+        OzParams o{};
+        o.rows = (int)N; o.cols = (int)N; o.C = w.S; o.ldc = N; o.lower_only = 1; o.status = w.status;
+        if ((e = launch_gemm_oz(d, w.ozeP, d, w.ozeP, o, st)) != cudaSuccess) return e;
+    } else {
+        GemmArgs g{};
+        g.rows = N; g.cols = N; g.K = N;
+        g.P = w.X; g.ldp = N; g.Q = w.X; g.ldq = N; g.C = w.S; g.ldc = N; g.lower_only = 1;
+        if ((e = launch_gemm_f64(g, EPI_STORE, Q_KMAJOR, st)) != cudaSuccess) return e;
+    }
     k_copy_diag<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(w.S, N, w.sdiag); g_launches++;
     // blocked right-looking Cholesky S = L L^T: diagonal blocks of L stay in S with their inverses in
     // Linv, the off-diagonal panels of L go to W
@@ -250,10 +258,21 @@ cudaError_t launch_rayleigh_f64(pfsm_handle_s *h, const double *A, double *eigva
     Workspace &w = h->ws;
     const int64_t N = h->N;
     cudaError_t e;
-    GemmArgs g{};
-    g.rows = N; g.cols = N; g.K = N;
-    g.P = w.X; g.ldp = N; g.Q = A; g.ldq = N; g.C = w.W; g.ldc = N;
-    if ((e = launch_gemm_f64(g, EPI_STORE, Q_KMAJOR, st)) != cudaSuccess) return e;
+    if (h->prm.precision != PFSM_FP64) {   // W = V A with FP64-accurate tensor-core digits
+        SliceBuf dv{w.ozP, N, padded_ld(N), OZ_SLICES, 0}, da{w.ozQ, N, padded_ld(N), OZ_SLICES, 0};
+        if ((e = launch_oz_split(w.X, N, N, N, dv, w.ozeP, st)) != cudaSuccess) return e;
+        // A = diag(d) + E: digits of E only, the diagonal term added exactly in FP64
+        if ((e = launch_oz_split(A, N, N, N, da, w.ozeQ, st, true, w.dA)) != cudaSuccess) return e;
+        OzParams o{};
+        o.rows = (int)N; o.cols = (int)N; o.C = w.W; o.ldc = N; o.status = w.status;
+        o.Vp = w.X; o.ldv = N; o.dcol = w.dA;
+        if ((e = launch_gemm_oz(dv, w.ozeP, da, w.ozeQ, o, st)) != cudaSuccess) return e;
+    } else {
+        GemmArgs g{};
+        g.rows = N; g.cols = N; g.K = N;
+        g.P = w.X; g.ldp = N; g.Q = A; g.ldq = N; g.C = w.W; g.ldc = N;
+        if ((e = launch_gemm_f64(g, EPI_STORE, Q_KMAJOR, st)) != cudaSuccess) return e;
+    }
     k_rayleigh_rows<<<(unsigned)N, 256, 0, st>>>(w.X, w.W, N, w.lam, w.res); g_launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_transpose(w.X, w.Vrm, N, st)) != cudaSuccess) return e;

@@ -16,10 +16,7 @@
 // tcgen05.ld (32 lanes each). Every mbarrier wait is bounded by %globaltimer: a wait that gives
 // up records PFSM_ERR_TIMEOUT in the status word, the CTA skips the rest of its work, waits
 // (bounded) for its copies in flight, frees its TMEM and exits.
-#include <cuda.h>
-#include <cuda_bf16.h>
-
-#include "pfsm_internal.cuh"
+#include "tc_common.cuh"
 
 namespace pfsm {
 
@@ -29,141 +26,6 @@ constexpr int BM = 128, BN = 128, STAGES = 6;
 constexpr int TILE_BYTES = BM * 128;                 // 128 rows x 128 bytes
 constexpr int STAGE_BYTES = 2 * TILE_BYTES;
 constexpr uint32_t TMEM_COLS = 128;
-constexpr uint64_t kWaitNs = 2000000000ull;          // 2 s per wait before giving up
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t globaltimer()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the phase of parity `parity` to complete.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = globaltimer();
-    while (!mbar_try_wait(bar, parity))
-        if (globaltimer() - t0 > kWaitNs) return false;
-    return true;
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y, int z)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Shared-memory matrix descriptor of a K-major operand tile with 128-byte swizzle: 8-row groups
-// 1024 B apart (stride byte offset), descriptor version 1.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;                 // leading byte offset (unused for this layout)
-    d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
-    d |= (uint64_t)1 << 46;                 // version
-    d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
-    return d;
-}
-
-// Instruction descriptor: FP32 accumulator, A/B element format (BF16 = 1, TF32 = 2), both
-// operands K-major, N = 128 (bits 17-22 hold N/8), M = 128 (bits 24-28 hold M/16).
-template <int KIND>
-__host__ __device__ constexpr uint32_t idesc()
-{
-    return (1u << 4) | ((KIND == 0 ? 1u : 2u) << 7) | ((KIND == 0 ? 1u : 2u) << 10) |
-           ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-}
-
-template <int KIND>
-__device__ __forceinline__ void umma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accum)
-{
-    if (KIND == 0)
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-            ::"r"(dtmem), "l"(a), "l"(b), "r"(idesc<0>()), "r"(accum));
-    else
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-            ::"r"(dtmem), "l"(a), "l"(b), "r"(idesc<1>()), "r"(accum));
-}
-
-__device__ __forceinline__ void umma_commit(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ float to_tf32(float x)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
-// Writes the `ns` KIND slices of v at slice-matrix element offset `o`.
-template <int KIND>
-__device__ __forceinline__ void store_slices(void *base, int64_t sstride, int64_t o, int ns, double v)
-{
-    double rem = v;
-    for (int s = 0; s < ns; s++) {
-        if (KIND == 0) {
-            __nv_bfloat16 b = __double2bfloat16(rem);
-            reinterpret_cast<__nv_bfloat16 *>(base)[s * sstride + o] = b;
-            rem -= (double)__bfloat162float(b);
-        } else {
-            float t = to_tf32((float)rem);
-            reinterpret_cast<float *>(base)[s * sstride + o] = t;
-            rem -= (double)t;
-        }
-    }
-}
 
 }  // namespace tc
 
@@ -382,21 +244,25 @@ EncodeTiledFn encode_fn()
     return fn;
 }
 
-// 3-D map over the slices: {ld (K), rows, ns}, box {128 bytes of K, 128 rows, 1 slice}.
-cudaError_t make_slice_map(CUtensorMap *map, const SliceBuf &b)
+}  // namespace
+
+// 3-D map over the slices: {ld (K), rows, ns}, box {128 bytes of K, box_rows rows, 1 slice}.
+cudaError_t make_slice_map(CUtensorMap *map, const SliceBuf &b, int box_rows)
 {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
     const int esz = b.kind == 0 ? 2 : 4;
     cuuint64_t dims[3] = {(cuuint64_t)b.ld, (cuuint64_t)b.rows, (cuuint64_t)b.ns};
     cuuint64_t strides[2] = {(cuuint64_t)b.ld * esz, (cuuint64_t)b.ld * b.rows * esz};
-    cuuint32_t box[3] = {(cuuint32_t)(128 / esz), 128u, 1u};
+    cuuint32_t box[3] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows, 1u};
     cuuint32_t estr[3] = {1u, 1u, 1u};
     CUresult r = fn(map, b.kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
                     b.ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
+
+namespace {
 
 size_t tc_smem_bytes() { return (size_t)tc::STAGES * tc::STAGE_BYTES + 1024 + 256; }
 
@@ -426,8 +292,8 @@ cudaError_t launch_gemm_tc(const SliceBuf &P, const SliceBuf &Q, TcParams prm, S
 {
     CUtensorMap mp, mq;
     cudaError_t e;
-    if ((e = make_slice_map(&mp, P)) != cudaSuccess) return e;
-    if ((e = make_slice_map(&mq, Q)) != cudaSuccess) return e;
+    if ((e = make_slice_map(&mp, P, tc::BM)) != cudaSuccess) return e;
+    if ((e = make_slice_map(&mq, Q, tc::BN)) != cudaSuccess) return e;
     prm.bk = P.kind == 0 ? 64 : 32;
     prm.kblocks = (int)(P.ld / prm.bk);
     int n = 0;   // slice pairs of total order below the slice count

@@ -50,6 +50,8 @@ struct Workspace {
     void *slE = nullptr, *slX = nullptr, *slY = nullptr, *slZ = nullptr;
     double *Z = nullptr;           // N*N (A - eps I) Y
     double *dA = nullptr;          // N diag(A)
+    void *ozP = nullptr, *ozQ = nullptr;   // OZ_SLICES digit matrices (BF16) of two operands
+    int32_t *ozeP = nullptr, *ozeQ = nullptr;   // their row exponents
 };
 
 }  // namespace pfsm
@@ -146,6 +148,25 @@ cudaError_t launch_split(const double *src, int64_t rows, int64_t cols, int64_t 
                          bool zero_diag, double *d, cudaStream_t st);
 cudaError_t launch_gemm_tc(const SliceBuf &P, const SliceBuf &Q, TcParams prm, SliceBuf *out_sl,
                            cudaStream_t st);
+// ---- FP64-accurate products on the BF16 tensor cores (k_gemm_oz.cu) ----
+#define OZ_SLICES 9                 // base-32 digits per entry (about 2^-45 relative accuracy)
+struct OzParams {
+    int rows, cols;                 // output extent
+    int kblocks;                    // 64-element K blocks (filled by launch_gemm_oz)
+    const int32_t *ep, *eq;         // row exponents of P and Q (filled by launch_gemm_oz)
+    double *C; int64_t ldc;
+    int sub;                        // C -= P Q^T instead of C = P Q^T
+    int lower_only;                 // only entries with c <= r
+    const double *Vp; int64_t ldv;  // with dcol: C[r, c] += Vp[r, c] dcol[c] (exact diagonal term)
+    const double *dcol;
+    int32_t *status;
+};
+cudaError_t configure_oz_kernels();
+cudaError_t launch_oz_split(const double *src, int64_t rows, int64_t cols, int64_t ld, const SliceBuf &dst,
+                            int32_t *exps, cudaStream_t st, bool zero_diag = false, double *d = nullptr);
+cudaError_t launch_gemm_oz(const SliceBuf &P, const int32_t *ep, const SliceBuf &Q, const int32_t *eq,
+                           OzParams prm, cudaStream_t st);
+
 inline int slices_for(int precision) { return precision == PFSM_BF16_SPLIT ? 3 : 2; }
 inline int slice_kind(int precision) { return precision == PFSM_BF16_SPLIT ? 0 : 1; }
 inline int64_t padded_ld(int64_t n) { return (n + 63) / 64 * 64; }

@@ -46,6 +46,25 @@ def test_split_gemm_matches_fp64(pf, rows, cols, K, name, prec):
     assert err < 4 * rep + 4 * np.sqrt(K) * 2.0 ** -24
 
 
+@pytest.mark.parametrize("rows,cols,K", [(128, 64, 64), (200, 130, 333), (1280, 1280, 1280),
+                                         (257, 65, 3000), (64, 300, 1)])
+def test_fp64_digit_gemm_is_fp64_accurate(pf, rows, cols, K):
+    """The tensor-core digit product (exact level sums) against the FP64 product: error at the
+    FP64 rounding level, far below any single-pass BF16/TF32 split."""
+    rng = np.random.default_rng(rows + 3 * cols + 7 * K)
+    P = rng.standard_normal((rows, K)) * np.exp(rng.uniform(-20, 20, (rows, 1)))
+    Q = rng.standard_normal((cols, K)) * np.exp(rng.uniform(-5, 5, (1, K)))
+    C = pf.split_gemm(torch.from_numpy(P).cuda(), torch.from_numpy(Q).cuda(), pf.FP64).cpu().numpy()
+    ref = P @ Q.T
+    # worst case: each operand rounded to 45 bits below 2^e >= its row max (2^-43 of
+    # max|P_r| max|Q_c| per term), plus the dropped levels L >= 9 (about 2^-42 per term)
+    bound = K * np.max(np.abs(P), axis=1)[:, None] * np.max(np.abs(Q), axis=1)[None, :]
+    err = np.max(np.abs(C - ref) / bound)
+    rel = np.max(np.abs(C - ref) / (np.abs(P) @ np.abs(Q).T))
+    print(f"digits {rows}x{cols}x{K}: max err / (K max|P_r| max|Q_c|) = {err:.2e}, / (|P||Q|^T) = {rel:.2e}")
+    assert err < 2.0 ** -40
+
+
 def _dev(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
@@ -81,9 +100,15 @@ def test_mixed_solve_matches_oracle(pf, orc, name, prec, case):
 
 
 @pytest.mark.parametrize("name,prec", PRECISIONS)
-def test_mixed_without_iterations_equals_fp64(pf, name, prec):
+def test_mixed_without_iterations_matches_fp64(pf, name, prec):
+    """K = 0 leaves only the FP64 stages: start vectors, Gram-Schmidt and Rayleigh quotients, with
+    the overlap and Rayleigh products done by FP64-accurate tensor-core digits in the mixed forms."""
     p = wl.small_gapped(1)
     a = _solve(pf, p, precision=prec, fs_iters=0)
     b = _solve(pf, p, precision=pf.FP64, fs_iters=0)
-    np.testing.assert_array_equal(a[1], b[1])
-    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[2], b[2])                  # identical start vectors
+    dl, dv = np.max(np.abs(a[0] - b[0])), np.max(np.abs(a[1] - b[1]))
+    print(f"K=0 {name}: |dlambda| = {dl:.2e}, |dV| = {dv:.2e}")
+    # digit products carry ~2^-46 of each row's largest entry per term: K 2^-46 ~ 4e-12 worst
+    # case for these unit-scale rows (K = 256), far below the FP64 bars (1e-10 ||A||, 1e-8)
+    assert dl < 1e-11 and dv < 1e-10
