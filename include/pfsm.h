@@ -207,7 +207,8 @@ typedef struct {
                              2 Eq. 11 iterations, 3 Gram-Schmidt (overlap, Cholesky, solve),
                              4 Rayleigh quotients, residuals and outputs, 5 backward;
                              inside 1: 6 tridiagonalisation, 7 bisection, 8 inverse iteration,
-                             9 back-transformation + start vectors */
+                             9 back-transformation + start vectors; inside 3: 10 overlap,
+                             11 Cholesky; the triangular solve is phase 3 minus 10 and 11 */
 } pfsm_profile_t;
 
 /* Enables (enable != 0) or disables CUDA-event phase timing on h. Timing adds one event record

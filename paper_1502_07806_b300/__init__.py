@@ -26,7 +26,7 @@ EXPORTED = ("pfsm_default_params", "pfsm_init", "pfsm_solve", "pfsm_backward", "
             "pfsm_destroy", "pfsm_fs_iterate_noalloc", "pfsm_split_gemm", "pfsm_batch_init",
             "pfsm_solve_batched", "pfsm_batch_get_status", "pfsm_batch_destroy")
 PHASES = ("plan", "submatrix", "fs_iterations", "gram_schmidt", "rayleigh", "backward")
-SUB_PHASES = ("tridiag", "bisect", "inverse_iter", "backtransform")
+SUB_PHASES = ("tridiag", "bisect", "inverse_iter", "backtransform", "overlap", "cholesky")
 
 
 class PFSMError(RuntimeError):

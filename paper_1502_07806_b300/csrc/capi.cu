@@ -191,6 +191,7 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
     }
     for (int i = 0; i < 8 && e == cudaSuccess; i++) e = cudaEventCreate(&h->ev[i]);
     for (int i = 0; i < 4 && e == cudaSuccess; i++) e = cudaEventCreate(&h->sub_ev[i]);
+    for (int i = 0; i < 2 && e == cudaSuccess; i++) e = cudaEventCreate(&h->gs_ev[i]);
     if (e != cudaSuccess) {
         free_ws(h);
         delete h;
@@ -445,6 +446,8 @@ int pfsm_get_profile(pfsm_handle_t h, pfsm_profile_t *out)
         // iteration | sub_ev[2] | back-transform | ev[2]
         cudaEvent_t seq[5] = {h->ev[1], h->sub_ev[0], h->sub_ev[1], h->sub_ev[2], h->ev[2]};
         for (int i = 0; i < 4; i++) PFSM_CUDA(cudaEventElapsedTime(&out->phase_ms[6 + i], seq[i], seq[i + 1]));
+        PFSM_CUDA(cudaEventElapsedTime(&out->phase_ms[10], h->ev[3], h->gs_ev[0]));
+        PFSM_CUDA(cudaEventElapsedTime(&out->phase_ms[11], h->gs_ev[0], h->gs_ev[1]));
     }
     if (h->last_was_backward) PFSM_CUDA(span(6, 7, &out->phase_ms[5]));
     out->timed = 1;
@@ -459,6 +462,8 @@ int pfsm_destroy(pfsm_handle_t h)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
     for (int i = 0; i < 4; i++)
         if (h->sub_ev[i]) cudaEventDestroy(h->sub_ev[i]);
+    for (int i = 0; i < 2; i++)
+        if (h->gs_ev[i]) cudaEventDestroy(h->gs_ev[i]);
     free_ws(h);
     delete h;
     return PFSM_OK;

@@ -54,33 +54,39 @@ k_potrf_inv(double *__restrict__ S, int64_t N, int64_t jb, int b, const double *
         L[i][k] = (i < b && k < b) ? ((k <= i) ? S[(jb + i) * N + jb + k] : 0.0) : (i == k ? 1.0 : 0.0);
         X[i][k] = 0.0;
     }
+    __shared__ double REF[CB];            // sqrt of the overlap's diagonal (norms before projection)
+    if (tid < b) REF[tid] = sqrt(fmax(sdiag[jb + tid], 0.0));
     __syncthreads();
+    // Right-looking factorisation on the unscaled columns: step j updates the trailing lower
+    // triangle with (L[i][j] L[k][j]) / d_j; column j is never read after step j, so all columns
+    // are scaled by 1/sqrt(d_j) at the end. Two barriers per column.
+    const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
     for (int j = 0; j < b; j++) {
         if (tid == 0) {
             const double d = L[j][j];
-            const double ref = sqrt(fmax(sdiag[jb + j], 0.0));
-            double y = (d > 0.0 && d < 1e300 && d > 1e-300) ? fast_rsqrt(d) : 0.0;
-            double l = d * y;
-            if (!(l >= 1e-8 * ref) || !(y > 0.0) || !isfinite(l)) {
+            double y = (d > 1e-300 && d < 1e300) ? fast_rsqrt(d) : 0.0;
+            const double l = d * y;
+            if (!(l >= 1e-8 * REF[j]) || !(y > 0.0) || !isfinite(l)) {
                 set_status(status, PFSM_ERR_NOT_SPD);
-                l = 1.0;   // keep the arithmetic finite; the result is flagged as invalid
-                y = 1.0;
+                y = 1.0;   // keep the arithmetic finite; the result is flagged as invalid
             }
-            L[j][j] = l;
             R[j] = y;
         }
         __syncthreads();
-        const double inv = R[j];
-        for (int i = j + 1 + tid; i < b; i += blockDim.x) L[i][j] *= inv;
-        __syncthreads();
-        const int rem = b - j - 1;
-        for (int t = tid; t < rem * rem; t += blockDim.x) {
-            const int i = j + 1 + t / rem, k = j + 1 + t % rem;
-            if (k <= i) L[i][k] = fma(-L[i][j], L[k][j], L[i][k]);
+        const double c = R[j] * R[j];
+        for (int i = j + 1 + warp; i < b; i += nw) {
+            const double aij = L[i][j] * c;
+            for (int k = j + 1 + lane; k <= i; k += 32) L[i][k] = fma(-aij, L[k][j], L[i][k]);
         }
         __syncthreads();
     }
+    for (int t = tid; t < b * b; t += blockDim.x) {
+        const int i = t / b, k = t % b;
+        if (k < i) L[i][k] *= R[k];
+        else if (k == i) L[i][i] = 1.0 / R[i];      // sqrt(d_i) = d_i / sqrt(d_i)
+    }
     for (int j = b + tid; j < CB; j += blockDim.x) R[j] = 1.0;
+    __syncthreads();
     for (int t = tid; t < b * b; t += blockDim.x) {
         const int i = t / b, k = t % b;
         if (k <= i) S[(jb + i) * N + jb + k] = L[i][k];
@@ -149,6 +155,7 @@ cudaError_t launch_gram_schmidt_f64(pfsm_handle_s *h, cudaStream_t st)
         if ((e = launch_gemm_f64(g, EPI_STORE, Q_KMAJOR, st)) != cudaSuccess) return e;
     }
     k_copy_diag<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(w.S, N, w.sdiag); g_launches++;
+    if (h->timing && (e = cudaEventRecord(h->gs_ev[0], st)) != cudaSuccess) return e;
     // blocked right-looking Cholesky S = L L^T: diagonal blocks of L stay in S with their inverses in
     // Linv, the off-diagonal panels of L go to W
     for (int64_t jb = 0; jb < N; jb += CB) {
@@ -172,6 +179,7 @@ cudaError_t launch_gram_schmidt_f64(pfsm_handle_s *h, cudaStream_t st)
         u.C = w.S + (jb + b) * N + jb + b; u.ldc = N; u.lower_only = 1;
         if ((e = launch_gemm_f64(u, EPI_SUB, Q_KMAJOR, st)) != cudaSuccess) return e;
     }
+    if (h->timing && (e = cudaEventRecord(h->gs_ev[1], st)) != cudaSuccess) return e;
     // V = L^-1 X by blocks of rows, written to Y: V_b = L_bb^-1 X_b, then X_rest -= L_rest,b V_b
     for (int64_t jb = 0; jb < N; jb += CB) {
         const int b = (int)((N - jb) < CB ? (N - jb) : CB);

@@ -75,6 +75,7 @@ struct pfsm_handle_s {
     bool timing = false;
     cudaEvent_t ev[8] = {};
     cudaEvent_t sub_ev[4] = {};   // inside the submatrix phase (timing only)
+    cudaEvent_t gs_ev[2] = {};    // inside Gram-Schmidt: after the overlap, after Cholesky
     int32_t last_launches = 0;
     bool last_was_backward = false;
 };
