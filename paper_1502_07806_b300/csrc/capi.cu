@@ -48,7 +48,7 @@ void free_ws(pfsm_handle_s *h)
     void *ptrs[] = {w.plan, w.tile_krange, w.status, w.gersh, w.X, w.Xfs, w.Y, w.S, w.W, w.Vrm,
                     w.sdiag, w.eps, w.alpha, w.lam, w.res, w.refl, w.tau, w.td, w.te,
                     w.sel_val, w.sel_vec, w.iiwork, w.slices, w.slE, w.slX, w.slY, w.slZ,
-                    w.Z, w.dA, w.Linv, w.ozP, w.ozQ, w.ozeP, w.ozeQ};
+                    w.Z, w.dA, w.Linv, w.ozP, w.ozQ, w.ozeP, w.ozeQ, w.L32, w.R32, w.M32, w.F};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     w = Workspace{};
@@ -174,6 +174,12 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
         w.ozP = o1; w.ozQ = o2;
         PFSM_ALLOC(w.ozeP, (size_t)N);
         PFSM_ALLOC(w.ozeQ, (size_t)N);
+        PFSM_ALLOC(w.L32, NN);
+        PFSM_ALLOC(w.R32, NN);
+        PFSM_ALLOC(w.M32, NN);
+        if (e == cudaSuccess) e = cudaMemset(w.M32, 0, NN * sizeof(float));   // stays zero above the diagonal
+        PFSM_ALLOC(w.F, NN);
+        if (e == cudaSuccess) e = configure_gs_mixed_kernels();
         if (e == cudaSuccess) e = configure_tc_kernels();
         if (e == cudaSuccess) e = configure_oz_kernels();
     }
@@ -278,7 +284,7 @@ static int solve_impl(pfsm_handle_s *h, const double *A, const double *prev, dou
     }
     PFSM_CUDA(mark(3));
     PFSM_CUDA(cudaMemcpyAsync(w.Xfs, w.X, (size_t)N * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    PFSM_CUDA(launch_gram_schmidt_f64(h, st));
+    PFSM_CUDA(h->prm.precision == PFSM_FP64 ? launch_gram_schmidt_f64(h, st) : launch_gram_schmidt_mixed(h, st));
     PFSM_CUDA(mark(4));
     PFSM_CUDA(launch_rayleigh_f64(h, A, eigvals_out, V_out, st));
     PFSM_CUDA(mark(5));

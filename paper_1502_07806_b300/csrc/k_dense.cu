@@ -1,5 +1,6 @@
-// Gram-Schmidt (Section II, after the Eq. 11 iterations), Rayleigh quotients / residuals, and
-// the eigen-adjoint backward, FP64.
+// Gram-Schmidt of the FP64 form (Section II, after the Eq. 11 iterations), Rayleigh quotients /
+// residuals, and the eigen-adjoint backward, FP64. (The mixed forms orthonormalise in
+// k_gs_mixed.cu.)
 //
 // Gram-Schmidt is done as Cholesky-QR. With the vectors as rows of X:
 //   S = X X^T (overlap, lower triangle), S = L L^T (blocked right-looking Cholesky),
@@ -141,20 +142,12 @@ cudaError_t launch_gram_schmidt_f64(pfsm_handle_s *h, cudaStream_t st)
     Workspace &w = h->ws;
     const int64_t N = h->N;
     cudaError_t e;
-    // S = X X^T (lower): DFMA in the FP64 form, FP64-accurate tensor-core digits in the mixed forms
-    if (h->prm.precision != PFSM_FP64) {
-        SliceBuf d{w.ozP, N, padded_ld(N), OZ_SLICES, 0};
-        if ((e = launch_oz_split(w.X, N, N, N, d, w.ozeP, st)) != cudaSuccess) return e;
-        OzParams o{};
-        o.rows = (int)N; o.cols = (int)N; o.C = w.S; o.ldc = N; o.lower_only = 1; o.status = w.status;
-        if ((e = launch_gemm_oz(d, w.ozeP, d, w.ozeP, o, st)) != cudaSuccess) return e;
-    } else {
-        GemmArgs g{};
-        g.rows = N; g.cols = N; g.K = N;
-        g.P = w.X; g.ldp = N; g.Q = w.X; g.ldq = N; g.C = w.S; g.ldc = N; g.lower_only = 1;
-        if ((e = launch_gemm_f64(g, EPI_STORE, Q_KMAJOR, st)) != cudaSuccess) return e;
-    }
-    k_copy_diag<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(w.S, N, w.sdiag); g_launches++;
+    // S = X X^T (lower)
+    GemmArgs g{};
+    g.rows = N; g.cols = N; g.K = N;
+    g.P = w.X; g.ldp = N; g.Q = w.X; g.ldq = N; g.C = w.S; g.ldc = N; g.lower_only = 1;
+    if ((e = launch_gemm_f64(g, EPI_STORE, Q_KMAJOR, st)) != cudaSuccess) return e;
+    if ((e = launch_copy_diag(w.S, N, w.sdiag, st)) != cudaSuccess) return e;
     if (h->timing && (e = cudaEventRecord(h->gs_ev[0], st)) != cudaSuccess) return e;
     // blocked right-looking Cholesky S = L L^T: diagonal blocks of L stay in S with their inverses in
     // Linv, the off-diagonal panels of L go to W
@@ -251,6 +244,12 @@ __global__ void k_transpose(const double *__restrict__ in, double *__restrict__ 
         int64_t r = bx + j, c = by + threadIdx.x;
         if (r < N && c < N) out[r * N + c] = t[threadIdx.x][j];
     }
+}
+
+cudaError_t launch_copy_diag(const double *S, int64_t N, double *d, cudaStream_t st)
+{
+    k_copy_diag<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(S, N, d); g_launches++;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_transpose(const double *in, double *out, int64_t N, cudaStream_t st)

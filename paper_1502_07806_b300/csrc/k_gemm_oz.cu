@@ -36,16 +36,19 @@ constexpr int BETA = 5;
 
 // One warp per row: exponent of the row's largest |entry| and the S digits of every entry.
 // zero_diag: digits of the off-diagonal part (entry (r, r) taken as 0, its value stored in d[r]).
-__global__ void k_oz_split(const double *__restrict__ src, int64_t rows, int64_t cols, int64_t ld,
+// Input in FP64 or FP32 (an FP32 operand's digits are exact: 24 bits fit in the 45-bit grid of its
+// row unless the entry is below 2^-21 of the row's largest).
+template <typename T>
+__global__ void k_oz_split(const T *__restrict__ src, int64_t rows, int64_t cols, int64_t ld,
                            __nv_bfloat16 *__restrict__ dst, int64_t sl_ld, int64_t sstride,
                            int32_t *__restrict__ exps, int zero_diag, double *__restrict__ d)
 {
     const int lane = threadIdx.x & 31;
     const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (r >= rows) return;
-    const double *x = src + r * ld;
-    auto val = [&](int64_t c) { return (zero_diag && c == r) ? 0.0 : x[c]; };
-    if (zero_diag && lane == 0 && d) d[r] = x[r];
+    const T *x = src + r * ld;
+    auto val = [&](int64_t c) { return (zero_diag && c == r) ? 0.0 : (double)x[c]; };
+    if (zero_diag && lane == 0 && d) d[r] = (double)x[r];
     double mx = 0.0;
     for (int64_t c = lane; c < cols; c += 32) mx = fmax(mx, fabs(val(c)));
 #pragma unroll
@@ -95,7 +98,8 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
     auto acce_bar = [&](int b) { return bar_base + 8u * (2 * STAGES + 2 + b); };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    const int nkb_total = prm.kblocks;                        // 64-element K blocks
+    // 64-element K blocks; a lower-triangular P has no entries beyond column row0 + BM - 1
+    const int nkb_total = prm.p_lower ? min(prm.kblocks, (row0 + BM + 63) / 64) : prm.kblocks;
     const int kb_per_chunk = KCHUNK / 64;
     const int nch = (nkb_total + kb_per_chunk - 1) / kb_per_chunk;
     const int S = OZ_SLICES;
@@ -260,8 +264,18 @@ cudaError_t launch_oz_split(const double *src, int64_t rows, int64_t cols, int64
                             int32_t *exps, cudaStream_t st, bool zero_diag, double *d)
 {
     const unsigned blocks = (unsigned)((rows + 7) / 8);
-    k_oz_split<<<blocks, 256, 0, st>>>(src, rows, cols, ld, reinterpret_cast<__nv_bfloat16 *>(dst.ptr),
-                                       dst.ld, dst.ld * dst.rows, exps, zero_diag ? 1 : 0, d);
+    k_oz_split<double><<<blocks, 256, 0, st>>>(src, rows, cols, ld, reinterpret_cast<__nv_bfloat16 *>(dst.ptr),
+                                               dst.ld, dst.ld * dst.rows, exps, zero_diag ? 1 : 0, d);
+    g_launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_oz_split_f32(const float *src, int64_t rows, int64_t cols, int64_t ld, const SliceBuf &dst,
+                                int32_t *exps, cudaStream_t st)
+{
+    const unsigned blocks = (unsigned)((rows + 7) / 8);
+    k_oz_split<float><<<blocks, 256, 0, st>>>(src, rows, cols, ld, reinterpret_cast<__nv_bfloat16 *>(dst.ptr),
+                                              dst.ld, dst.ld * dst.rows, exps, 0, nullptr);
     g_launches++;
     return cudaGetLastError();
 }

@@ -8,7 +8,8 @@
 // the slice count are accumulated into ONE FP32 accumulator in tensor memory (6 products for
 // BF16, 3 for TF32): the K loop runs over (pair, k-block). The epilogue converts to FP64 and
 // applies the Eq. 11 algebra in FP64 (TC_EPI_* modes), and can write the BF16/TF32 slices of its
-// own result, which are the operand of the next product.
+// own result, which are the operand of the next product. TC_EPI_STORE / TC_EPI_RSUB serve the
+// FP32-accurate products of the mixed-form Gram-Schmidt.
 //
 // CTA: 192 threads, one 128x128 output tile. Warp 0 issues TMA loads (SWIZZLE_128B, 128-byte K
 // rows) into a 6-stage ring; warp 1 owns the TMEM accumulator (128 columns) and issues
@@ -47,6 +48,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
+    if (prm.lower_only && col0 > row0 + BM - 1) return;           // whole tile above the diagonal
 
     // K-block range (the first product only needs the columns its rows' windows cover)
     int kb0 = 0, kb1 = prm.kblocks;
@@ -183,8 +185,10 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
                     } else if (prm.epi == TC_EPI_Z) {
                         res = acc + (prm.d[c] - er) * prm.V[o];
                         prm.X[o] -= ar * res;
-                    } else {   // TC_EPI_YN
+                    } else if (prm.epi == TC_EPI_YN) {
                         res = prm.Yold[o] - ar * (acc + (prm.d[c] - er) * prm.V[o]);
+                    } else {   // TC_EPI_RSUB
+                        res = prm.V[o] - acc;
                     }
                     prm.out[o] = res;
                     if (prm.out_ns > 0)

@@ -52,6 +52,10 @@ struct Workspace {
     double *dA = nullptr;          // N diag(A)
     void *ozP = nullptr, *ozQ = nullptr;   // OZ_SLICES digit matrices (BF16) of two operands
     int32_t *ozeP = nullptr, *ozeQ = nullptr;   // their row exponents
+    // mixed-form Gram-Schmidt: FP32 Cholesky working matrix, augmented right-hand side and the
+    // preconditioner M = L~^-1 (zero above the diagonal), and the FP64 correction factor F
+    float *L32 = nullptr, *R32 = nullptr, *M32 = nullptr;
+    double *F = nullptr;
 };
 
 }  // namespace pfsm
@@ -118,7 +122,7 @@ struct GemmArgs {
 cudaError_t launch_gemm_f64(const GemmArgs &a, int epi, int qlayout, cudaStream_t st);
 
 // ---- tensor-core split-precision GEMM (k_gemm_tc.cu) ----
-enum TcEpi : int { TC_EPI_STORE = 0, TC_EPI_Y0 = 1, TC_EPI_Z = 2, TC_EPI_YN = 3 };
+enum TcEpi : int { TC_EPI_STORE = 0, TC_EPI_Y0 = 1, TC_EPI_Z = 2, TC_EPI_YN = 3, TC_EPI_RSUB = 4 };
 
 // A matrix held as `ns` slices (kind 0: BF16, kind 1: TF32 in FP32 containers), each rows x ld,
 // ld a multiple of 64 elements with zero padding columns.
@@ -138,10 +142,12 @@ struct TcParams {
     double *out; int64_t ldo;
     void *out_slices; int64_t sl_ld, sl_stride; int out_ns;
     double *X;                      // TC_EPI_Z: x <- x - alpha z
-    const double *V;                // operand in FP64 (Y for TC_EPI_Z, Z for TC_EPI_YN)
+    const double *V;                // operand in FP64 (Y for TC_EPI_Z, Z for TC_EPI_YN, the
+                                    // minuend of TC_EPI_RSUB: out = V - P Q^T, may alias out)
     const double *Yold;             // TC_EPI_YN
     const double *d, *eps, *alpha;
     const int32_t *plan; int nb;    // TC_EPI_Y0 window mask
+    int lower_only;                 // skip output tiles strictly above the diagonal
     int32_t *status;
 };
 cudaError_t configure_tc_kernels();
@@ -158,6 +164,7 @@ struct OzParams {
     double *C; int64_t ldc;
     int sub;                        // C -= P Q^T instead of C = P Q^T
     int lower_only;                 // only entries with c <= r
+    int p_lower;                    // P is lower triangular: skip K blocks beyond the tile's rows
     const double *Vp; int64_t ldv;  // with dcol: C[r, c] += Vp[r, c] dcol[c] (exact diagonal term)
     const double *dcol;
     int32_t *status;
@@ -165,6 +172,8 @@ struct OzParams {
 cudaError_t configure_oz_kernels();
 cudaError_t launch_oz_split(const double *src, int64_t rows, int64_t cols, int64_t ld, const SliceBuf &dst,
                             int32_t *exps, cudaStream_t st, bool zero_diag = false, double *d = nullptr);
+cudaError_t launch_oz_split_f32(const float *src, int64_t rows, int64_t cols, int64_t ld, const SliceBuf &dst,
+                                int32_t *exps, cudaStream_t st);
 cudaError_t launch_gemm_oz(const SliceBuf &P, const int32_t *ep, const SliceBuf &Q, const int32_t *eq,
                            OzParams prm, cudaStream_t st);
 
@@ -177,6 +186,10 @@ cudaError_t launch_gram_schmidt_f64(pfsm_handle_s *h, cudaStream_t st);
 cudaError_t launch_rayleigh_f64(pfsm_handle_s *h, const double *A, double *eigvals_out,
                                 double *V_out, cudaStream_t st);
 cudaError_t launch_transpose(const double *in, double *out, int64_t N, cudaStream_t st);
+cudaError_t launch_copy_diag(const double *S, int64_t N, double *d, cudaStream_t st);
+// mixed-form Gram-Schmidt (k_gs_mixed.cu)
+cudaError_t configure_gs_mixed_kernels();
+cudaError_t launch_gram_schmidt_mixed(pfsm_handle_s *h, cudaStream_t st);
 cudaError_t launch_backward_f64(pfsm_handle_s *h, const double *dLambda, const double *dV,
                                 double *dA_out, cudaStream_t st);
 
