@@ -7,9 +7,14 @@
 // digits n_0 .. n_8 (n_s in [-16, 16) for s >= 1, |n_0| <= 32), each stored exactly as a BF16 value:
 //   x = 2^e_r sum_s n_s 2^-5(s+1)   (to 2^-46 of the row's largest entry).
 // Product (k_gemm_oz): C[r, c] = sum_L 2^(e_r + e_c - 5(L+2)) sum_{s+t=L} sum_k n_s[r,k] m_t[c,k].
-// Every digit product has |n m| <= 2^10, so the (L+1) products of level L summed over a K chunk of
-// at most 16384/(L+1) terms stay below 2^24 and the FP32 accumulation in tensor memory is EXACT.
-// Levels L = 0 .. S-1 are kept (about 2^-45 relative to |P||Q|^T); each (level, K chunk) group is
+// Every digit product has |n m| <= 2^10 and a level has at most S = 9 pairs, so a level summed over
+// a K chunk of 1792 terms stays below 2^24 and the FP32 accumulation in tensor memory is EXACT.
+// Levels L = 0 .. OZ_LEVELS-1 = 10 are kept. Every entry, however small, has O(1) low digits, so
+// the products of a dropped level L add up like a random walk over K: about
+// sqrt(K (pairs at L)) 2^(8 - 5(L+2)) / 3 relative to 2^(e_r + e_c). Stopping after L = 8 would
+// leave sqrt(K) 2^-46 (1e-12 at K = 9072); stopping after L = 10 leaves about 1e-15 there, below
+// the 2^-46 rounding of the operands themselves. Products that only need FP32-class accuracy
+// ask for fewer levels (about sqrt(K) 2^(3 - 5(levels+1)) / 3). Each (level, K chunk) group is
 // drained from TMEM into FP64 registers with its exact power-of-two scale while the tensor cores
 // fill the other of two TMEM buffers.
 //
@@ -103,7 +108,8 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
     const int kb_per_chunk = KCHUNK / 64;
     const int nch = (nkb_total + kb_per_chunk - 1) / kb_per_chunk;
     const int S = OZ_SLICES;
-    const int groups = S * nch;
+    const int LV = (prm.levels > 0 && prm.levels < 2 * S - 1) ? prm.levels : OZ_LEVELS;   // levels 0 .. LV-1
+    const int groups = LV * nch;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) {

@@ -1,32 +1,60 @@
 // Split-precision GEMM on the 5th-generation tensor cores (tcgen05 + TMEM, operands fed by TMA)
-// for the products of Eq. 11 in the mixed forms.
+// for the products of Eq. 11 in the mixed forms, and the FP32-accurate products of the mixed-form
+// Gram-Schmidt.
 //
 //   C[r, c] = sum over slice pairs (a, b) of sum_k P_a[r, k] * Q_b[c, k]
 //
 // P and Q are FP64 matrices held as BF16 (3 slices) or TF32 (2 slices) pieces, x = sum_s x_s with
 // each x_s the rounding of the remainder left by the earlier slices. Pairs of total order below
 // the slice count are accumulated into ONE FP32 accumulator in tensor memory (6 products for
-// BF16, 3 for TF32): the K loop runs over (pair, k-block). The epilogue converts to FP64 and
-// applies the Eq. 11 algebra in FP64 (TC_EPI_* modes), and can write the BF16/TF32 slices of its
-// own result, which are the operand of the next product. TC_EPI_STORE / TC_EPI_RSUB serve the
-// FP32-accurate products of the mixed-form Gram-Schmidt.
+// BF16, 3 for TF32). The epilogue applies the Eq. 11 algebra (TC_EPI_* modes) and can write the
+// BF16/TF32 slices of its own result, the operand of the next product.
 //
-// CTA: 192 threads, one 128x128 output tile. Warp 0 issues TMA loads (SWIZZLE_128B, 128-byte K
-// rows) into a 6-stage ring; warp 1 owns the TMEM accumulator (128 columns) and issues
-// tcgen05.mma (M=128, N=128, K=16 bf16 / 8 tf32) from one lane; warps 2-5 drain TMEM with
-// tcgen05.ld (32 lanes each). Every mbarrier wait is bounded by %globaltimer: a wait that gives
-// up records PFSM_ERR_TIMEOUT in the status word, the CTA skips the rest of its work, waits
-// (bounded) for its copies in flight, frees its TMEM and exits.
+// Persistent CTAs (one per SM, 192 threads) walk the output tiles (128 x 128). Warp 0 issues the
+// TMA loads: one pipeline stage holds every slice of P and of Q for one 128-byte K block, so each
+// slice tile is loaded once and feeds all the pairs that use it. Warp 1 owns a double-buffered
+// TMEM accumulator (2 x 128 columns) and issues tcgen05.mma from one lane, so the MMAs of tile
+// i + 1 run while warps 2-5 drain tile i. The epilogue keeps FP64 only where Eq. 11 accumulates
+// (X -= alpha Z, Y_new = Y - alpha (...)) and does the rest in FP32, which is as accurate as the
+// split product itself: B300's FP64 pipe (2 FMA/clk/SM) would otherwise outlast the MMAs.
+// Every mbarrier wait is bounded by %globaltimer: a wait that gives up records PFSM_ERR_TIMEOUT
+// in the status word; all roles then stop, the loads and MMAs in flight are waited for
+// (bounded), TMEM is freed and the CTA exits.
 #include "tc_common.cuh"
 
 namespace pfsm {
 
 namespace tc {
 
-constexpr int BM = 128, BN = 128, STAGES = 6;
+constexpr int BM = 128, BN = 128;
 constexpr int TILE_BYTES = BM * 128;                 // 128 rows x 128 bytes
-constexpr int STAGE_BYTES = 2 * TILE_BYTES;
-constexpr uint32_t TMEM_COLS = 128;
+constexpr uint32_t TMEM_COLS = 256;                  // two 128-column FP32 accumulators
+constexpr int EBP = 17;                              // epilogue staging row (16 columns + pad)
+
+template <int KIND> struct Cfg {
+    static constexpr int NS = KIND == 0 ? 3 : 2;     // slices per operand
+    static constexpr int BK = KIND == 0 ? 64 : 32;   // K elements per 128-byte row
+    static constexpr int KSTEP = KIND == 0 ? 16 : 8; // K per tcgen05.mma
+    static constexpr int STAGE_BYTES = 2 * NS * TILE_BYTES;
+    static constexpr int STAGES = KIND == 0 ? 2 : 3;
+    static constexpr int NPAIRS = NS * (NS + 1) / 2;
+};
+
+// Output tile t -> (tile row, tile column): row-major over the tile grid, or over its lower
+// triangle (column tile <= row tile) for lower-only products of square outputs.
+__device__ __forceinline__ void tile_coords(int t, int ncolt, int lower, int &tr, int &tcl)
+{
+    if (!lower) {
+        tr = t / ncolt;
+        tcl = t % ncolt;
+        return;
+    }
+    int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((r + 1) * (r + 2) / 2 <= t) r++;
+    while (r * (r + 1) / 2 > t) r--;
+    tr = r;
+    tcl = t - r * (r + 1) / 2;
+}
 
 }  // namespace tc
 
@@ -35,41 +63,54 @@ __global__ void __launch_bounds__(192, 1)
 k_gemm_tc(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUtensorMap mapQ, TcParams prm)
 {
     using namespace tc;
+    using C = Cfg<KIND>;
     extern __shared__ __align__(1024) uint8_t smraw[];
     const uint32_t raw = smem_u32(smraw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *gbase = smraw + (base - raw);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + STAGES * STAGE_BYTES);
-    // bars[0..S): full, [S..2S): empty, [2S]: accumulator ready
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 1);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + C::STAGES * C::STAGE_BYTES);
+    // bars: [0,S) full, [S,2S) empty, [2S,2S+2) accumulator full, [2S+2,2S+4) accumulator empty,
+    // [2S+4] all MMAs done
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * C::STAGES + 5);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    float *dhi = reinterpret_cast<float *>(tmem_slot + 4);     // per tile column: diag(A) split
+    float *dlo = dhi + BN;
+    double *ebuf = reinterpret_cast<double *>(dlo + BN);        // epilogue staging, 128 x EBP
     const uint32_t bar_base = smem_u32(bars);
-    const uint32_t acc_bar = bar_base + 8u * (2 * STAGES);
-
+    auto full_bar = [&](int s) { return bar_base + 8u * s; };
+    auto empty_bar = [&](int s) { return bar_base + 8u * (C::STAGES + s); };
+    auto accf_bar = [&](int b) { return bar_base + 8u * (2 * C::STAGES + b); };
+    auto acce_bar = [&](int b) { return bar_base + 8u * (2 * C::STAGES + 2 + b); };
+    const uint32_t done_bar = bar_base + 8u * (2 * C::STAGES + 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
-    if (prm.lower_only && col0 > row0 + BM - 1) return;           // whole tile above the diagonal
+    const int ncolt = (prm.cols + BN - 1) / BN, nrowt = (prm.rows + BM - 1) / BM;
+    const int ntiles = prm.lower_only ? nrowt * (nrowt + 1) / 2 : nrowt * ncolt;
 
-    // K-block range (the first product only needs the columns its rows' windows cover)
-    int kb0 = 0, kb1 = prm.kblocks;
-    if (prm.krange) {
-        const int t0 = 2 * blockIdx.y;
-        const int t1 = min(t0 + 1, prm.nrowtiles64 - 1);
-        const int kbeg = min(prm.krange[2 * t0], prm.krange[2 * t1]);
-        const int kend = max(prm.krange[2 * t0 + 1], prm.krange[2 * t1 + 1]);
-        kb0 = kbeg / prm.bk;
-        kb1 = min(prm.kblocks, (kend + prm.bk - 1) / prm.bk);
-        if (kb1 < kb0) kb1 = kb0;
-    }
-    const int nkb = kb1 - kb0;
-    const int total = nkb * prm.npairs;
+    // K-block range of a tile row (the first product only needs the columns its rows' windows cover)
+    auto krange = [&](int tr, int &kb0, int &kb1) {
+        kb0 = 0;
+        kb1 = prm.kblocks;
+        if (prm.krange) {
+            const int t0 = 2 * tr;
+            const int t1 = min(t0 + 1, prm.nrowtiles64 - 1);
+            const int kbeg = min(prm.krange[2 * t0], prm.krange[2 * t1]);
+            const int kend = max(prm.krange[2 * t0 + 1], prm.krange[2 * t1 + 1]);
+            kb0 = kbeg / C::BK;
+            kb1 = min(prm.kblocks, (kend + C::BK - 1) / C::BK);
+            if (kb1 < kb0) kb1 = kb0;
+        }
+    };
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; s++) {
-            mbar_init(bar_base + 8u * s, 1);
-            mbar_init(bar_base + 8u * (STAGES + s), 1);
+        for (int s = 0; s < C::STAGES; s++) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
         }
-        mbar_init(acc_bar, 1);
+        for (int b = 0; b < 2; b++) {
+            mbar_init(accf_bar(b), 1);
+            mbar_init(acce_bar(b), 128);
+        }
+        mbar_init(done_bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapP) : "memory");
@@ -87,112 +128,220 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
 
     if (warp == 0) {
         if (lane == 0) {
-            int issued = 0;
-            for (int it = 0; it < total; it++) {
-                const int s = it % STAGES, round = it / STAGES;
-                if (round > 0 && !mbar_wait(bar_base + 8u * (STAGES + s), (round - 1) & 1)) {
-                    set_status(prm.status, PFSM_ERR_TIMEOUT);
-                    *abort_flag = 1;
-                    break;
+            int it = 0, issued = 0;
+            bool stop = false;
+            for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+                int tr, tcl, kb0, kb1;
+                tile_coords(t, ncolt, prm.lower_only, tr, tcl);
+                krange(tr, kb0, kb1);
+                for (int kb = kb0; kb < kb1; kb++, it++) {
+                    const int s = it % C::STAGES, round = it / C::STAGES;
+                    if (round > 0 && !mbar_wait(empty_bar(s), (round - 1) & 1)) {
+                        set_status(prm.status, PFSM_ERR_TIMEOUT);
+                        *abort_flag = 1;
+                        stop = true;
+                        break;
+                    }
+                    if (*abort_flag) { stop = true; break; }
+                    const uint32_t st0 = base + s * C::STAGE_BYTES;
+                    mbar_expect_tx(full_bar(s), C::STAGE_BYTES);
+#pragma unroll
+                    for (int a = 0; a < C::NS; a++) {
+                        tma_load_3d(st0 + a * TILE_BYTES, &mapP, full_bar(s), kb * C::BK, tr * BM, a);
+                        tma_load_3d(st0 + (C::NS + a) * TILE_BYTES, &mapQ, full_bar(s), kb * C::BK, tcl * BN, a);
+                    }
+                    issued = it + 1;
                 }
-                if (*abort_flag) break;
-                const int q = it / nkb, kb = kb0 + it % nkb;
-                const uint32_t sa = base + s * STAGE_BYTES, sb = sa + TILE_BYTES;
-                mbar_expect_tx(bar_base + 8u * s, STAGE_BYTES);
-                tma_load_3d(sa, &mapP, bar_base + 8u * s, kb * prm.bk, row0, prm.pa[q]);
-                tma_load_3d(sb, &mapQ, bar_base + 8u * s, kb * prm.bk, col0, prm.pb[q]);
-                issued = it + 1;
             }
             // leave no copies in flight: wait (bounded) for the last stages filled
-            for (int it = (issued > STAGES ? issued - STAGES : 0); it < issued; it++)
-                mbar_wait(bar_base + 8u * (it % STAGES), (it / STAGES) & 1);
+            for (int i = (issued > C::STAGES ? issued - C::STAGES : 0); i < issued; i++)
+                mbar_wait(full_bar(i % C::STAGES), (i / C::STAGES) & 1);
         }
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {
+            int it = 0, lt = 0;
             bool ok = true;
-            for (int it = 0; it < total; it++) {
-                const int s = it % STAGES;
-                if (!mbar_wait(bar_base + 8u * s, (it / STAGES) & 1) || *abort_flag) {
-                    set_status(prm.status, PFSM_ERR_TIMEOUT);
-                    *abort_flag = 1;
-                    ok = false;
-                    break;
-                }
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, lt++) {
+                int tr, tcl, kb0, kb1;
+                tile_coords(t, ncolt, prm.lower_only, tr, tcl);
+                krange(tr, kb0, kb1);
+                const int buf = lt & 1;
+                if (lt >= 2 && !mbar_wait(acce_bar(buf), ((lt >> 1) - 1) & 1)) { ok = false; break; }
                 fence_after();
-                const uint32_t sa = base + s * STAGE_BYTES, sb = sa + TILE_BYTES;
-                const uint64_t da = sw128_desc(sa), db = sw128_desc(sb);
+                const uint32_t dacc = tmem_acc + 128u * buf;
+                bool first = true;
+                for (int kb = kb0; kb < kb1; kb++, it++) {
+                    const int s = it % C::STAGES;
+                    if (!mbar_wait(full_bar(s), (it / C::STAGES) & 1) || *abort_flag) { ok = false; break; }
+                    fence_after();
+                    const uint32_t st0 = base + s * C::STAGE_BYTES;
 #pragma unroll
-                for (int kk = 0; kk < 4; kk++)   // 4 x 32 bytes of K per 128-byte row
-                    umma<KIND>(tmem_acc, da + 2 * kk, db + 2 * kk, (it > 0 || kk > 0) ? 1u : 0u);
-                umma_commit(bar_base + 8u * (STAGES + s));
+                    for (int ord = 0; ord < C::NS; ord++)
+#pragma unroll
+                        for (int a = 0; a <= ord; a++) {
+                            const uint64_t da = sw128_desc(st0 + a * TILE_BYTES);
+                            const uint64_t db = sw128_desc(st0 + (C::NS + ord - a) * TILE_BYTES);
+#pragma unroll
+                            for (int kk = 0; kk < 4; kk++) {   // 4 x 32 bytes of K per 128-byte row
+                                umma<KIND>(dacc, da + 2 * kk, db + 2 * kk, first ? 0u : 1u);
+                                first = false;
+                            }
+                        }
+                    umma_commit(empty_bar(s));
+                }
+                umma_commit(accf_bar(buf));   // this tile's sum is complete when its MMAs are
             }
-            // signals the epilogue; also tracks every issued MMA before TMEM is released
-            umma_commit(acc_bar);
-            if (!ok) mbar_wait(acc_bar, 0);
+            if (!ok) {
+                set_status(prm.status, PFSM_ERR_TIMEOUT);
+                *abort_flag = 1;
+            }
+            // track every issued MMA before TMEM is released (bounded)
+            umma_commit(done_bar);
+            mbar_wait(done_bar, 0);
         }
         __syncwarp();
     } else {
         // epilogue: warp w reads TMEM lanes 32*(w % 4) .. +31, i.e. tile rows
         const int g = warp & 3;
-        const int r = row0 + 32 * g + lane;
-        const bool have_acc = total > 0;
-        bool ok = true;
-        if (have_acc) ok = mbar_wait(acc_bar, 0);
-        ok = __all_sync(0xffffffffu, ok);
-        if (!ok) {
-            set_status(prm.status, PFSM_ERR_TIMEOUT);
-            *abort_flag = 1;
-        }
-        fence_after();
-        const bool row_ok = r < prm.rows;
-        double er = 0.0, ar = 0.0;
-        int win_lo = 0, win_hi = 0;
-        if (row_ok) {
-            if (prm.eps) er = prm.eps[r];
-            if (prm.alpha) ar = prm.alpha[r];
-            if (prm.epi == TC_EPI_Y0) {
-                // window of the slice owning row r (largest b with k0[b] <= r)
-                int lo = 0, hi = prm.nb - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (prm.plan[mid] <= r) lo = mid; else hi = mid - 1;
+        const int et = threadIdx.x - 64;                 // 0 .. 127
+        int lt = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, lt++) {
+            int tr, tcl, kb0, kb1;
+            tile_coords(t, ncolt, prm.lower_only, tr, tcl);
+            krange(tr, kb0, kb1);
+            const int buf = lt & 1;
+            const int row0 = tr * BM, col0 = tcl * BN;
+            const int r = row0 + 32 * g + lane;
+            // column data of this tile (the previous tile's readers are done: named barrier)
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (prm.d) {
+                const int c = col0 + et;
+                const double dv = c < prm.cols ? prm.d[c] : 0.0;
+                const float h = (float)dv;
+                dhi[et] = h;
+                dlo[et] = (float)(dv - (double)h);
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            const bool got = mbar_wait(accf_bar(buf), (lt >> 1) & 1);
+            if (!got) {
+                set_status(prm.status, PFSM_ERR_TIMEOUT);
+                *abort_flag = 1;
+            }
+            // one decision for all four epilogue warps (they meet at named barriers)
+            int stop;
+            asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.s32 q, %1, 0;\n\t"
+                         "bar.red.or.pred p, 1, 128, q;\n\tselp.s32 %0, 1, 0, p;\n\t}"
+                         : "=r"(stop) : "r"((!got || *abort_flag) ? 1 : 0) : "memory");
+            if (stop) break;
+            fence_after();
+            const bool have_acc = kb1 > kb0;
+            const bool row_ok = r < prm.rows;
+            float ehi = 0.0f, elo = 0.0f;
+            double ar = 0.0;
+            int win_lo = 0, win_hi = 0;
+            if (row_ok) {
+                if (prm.eps) {
+                    const double ev = prm.eps[r];
+                    ehi = (float)ev;
+                    elo = (float)(ev - (double)ehi);
                 }
-                win_lo = prm.plan[2 * prm.nb + lo];
-                win_hi = win_lo + prm.plan[3 * prm.nb + lo];
-            }
-        }
-        for (int chunk = 0; chunk < BN / 32; chunk++) {
-            uint32_t v[32];
-            if (have_acc && ok) {
-                tmem_ld32(tmem_acc + ((uint32_t)(32 * g) << 16) + 32 * chunk, v);
-            } else {
-#pragma unroll
-                for (int j = 0; j < 32; j++) v[j] = 0u;
-            }
-            if (!row_ok || !ok) continue;
-#pragma unroll
-            for (int j = 0; j < 32; j++) {
-                const int c = col0 + 32 * chunk + j;
-                if (c < prm.cols) {
-                    const double acc = (double)__uint_as_float(v[j]);
-                    const int64_t o = (int64_t)r * prm.ldo + c;
-                    double res;
-                    if (prm.epi == TC_EPI_STORE) {
-                        res = acc;
-                    } else if (prm.epi == TC_EPI_Y0) {
-                        res = (c >= win_lo && c < win_hi) ? 0.0 : acc;
-                    } else if (prm.epi == TC_EPI_Z) {
-                        res = acc + (prm.d[c] - er) * prm.V[o];
-                        prm.X[o] -= ar * res;
-                    } else if (prm.epi == TC_EPI_YN) {
-                        res = prm.Yold[o] - ar * (acc + (prm.d[c] - er) * prm.V[o]);
-                    } else {   // TC_EPI_RSUB
-                        res = prm.V[o] - acc;
+                if (prm.alpha) ar = prm.alpha[r];
+                if (prm.epi == TC_EPI_Y0) {
+                    // window of the slice owning row r (largest b with k0[b] <= r)
+                    int lo = 0, hi = prm.nb - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (prm.plan[mid] <= r) lo = mid; else hi = mid - 1;
                     }
-                    prm.out[o] = res;
-                    if (prm.out_ns > 0)
-                        store_slices<KIND>(prm.out_slices, prm.sl_stride, (int64_t)r * prm.sl_ld + c, prm.out_ns, res);
+                    win_lo = prm.plan[2 * prm.nb + lo];
+                    win_hi = win_lo + prm.plan[3 * prm.nb + lo];
+                }
+            }
+            double(*eb)[EBP] = reinterpret_cast<double(*)[EBP]>(ebuf) + 32 * g;   // this warp's staging
+            const int R0 = row0 + 32 * g;
+            // coalesced access of the warp's 32 x 16 block: lanes 0-15 row 2i, lanes 16-31 row 2i+1
+            auto in_block = [&](int rr, int c) { return R0 + rr < prm.rows && c < prm.cols && !(prm.lower_only && c > R0 + rr); };
+            auto load_block = [&](const double *src, int C0) {
+#pragma unroll 4
+                for (int i = 0; i < 16; i++) {
+                    const int rr = 2 * i + (lane >> 4), cc = lane & 15, c = C0 + cc;
+                    if (in_block(rr, c)) eb[rr][cc] = src[(int64_t)(R0 + rr) * prm.ldo + c];
+                }
+                __syncwarp();
+            };
+            auto store_block = [&](double *dst, int C0, bool slices) {
+                __syncwarp();
+#pragma unroll 4
+                for (int i = 0; i < 16; i++) {
+                    const int rr = 2 * i + (lane >> 4), cc = lane & 15, c = C0 + cc;
+                    if (in_block(rr, c)) {
+                        const double x = eb[rr][cc];
+                        dst[(int64_t)(R0 + rr) * prm.ldo + c] = x;
+                        if (slices)
+                            store_slices_f32<KIND>(prm.out_slices, prm.sl_stride, (int64_t)(R0 + rr) * prm.sl_ld + c,
+                                                   prm.out_ns, (float)x);
+                    }
+                }
+                __syncwarp();
+            };
+            const bool sl = prm.out_ns > 0;
+            for (int chunk = 0; chunk < BN / 32; chunk++) {
+                uint32_t v[32];
+                if (have_acc) {
+                    tmem_ld32(tmem_acc + ((uint32_t)(32 * g) << 16) + 128u * buf + 32 * chunk, v);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; j++) v[j] = 0u;
+                }
+                if (chunk == BN / 32 - 1) {     // accumulator drained: hand it back to the MMA warp
+                    fence_before();
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce_bar(buf)) : "memory");
+                }
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const int C0 = col0 + 32 * chunk + 16 * h;
+                    if (prm.epi == TC_EPI_STORE || prm.epi == TC_EPI_Y0) {
+#pragma unroll
+                        for (int j = 0; j < 16; j++) {
+                            const int c = C0 + j;
+                            float x = __uint_as_float(v[16 * h + j]);
+                            if (prm.epi == TC_EPI_Y0 && c >= win_lo && c < win_hi) x = 0.0f;
+                            eb[lane][j] = (double)x;
+                        }
+                        store_block(prm.out, C0, sl);
+                    } else if (prm.epi == TC_EPI_RSUB) {
+                        load_block(prm.V, C0);
+#pragma unroll
+                        for (int j = 0; j < 16; j++) eb[lane][j] -= (double)__uint_as_float(v[16 * h + j]);
+                        store_block(prm.out, C0, false);
+                    } else {
+                        // (A - eps_r I) applied to the FP64 operand's diagonal part, in FP32:
+                        // (d_c - eps_r) from hi/lo pieces, times the operand rounded to FP32
+                        float t[16];
+                        load_block(prm.V, C0);
+#pragma unroll
+                        for (int j = 0; j < 16; j++) {
+                            const int cl = C0 - col0 + j;
+                            const float diff = (dhi[cl] - ehi) + (dlo[cl] - elo);
+                            t[j] = fmaf(diff, (float)eb[lane][j], __uint_as_float(v[16 * h + j]));
+                        }
+                        __syncwarp();
+                        if (prm.epi == TC_EPI_Z) {
+                            load_block(prm.X, C0);                       // X -= alpha Z in FP64
+#pragma unroll
+                            for (int j = 0; j < 16; j++) eb[lane][j] = fma(-ar, (double)t[j], eb[lane][j]);
+                            store_block(prm.X, C0, false);
+#pragma unroll
+                            for (int j = 0; j < 16; j++) eb[lane][j] = (double)t[j];
+                            store_block(prm.out, C0, sl);
+                        } else {   // TC_EPI_YN: Y - alpha (E Z + (D - eps) Z), accumulated in FP64
+                            load_block(prm.Yold, C0);
+#pragma unroll
+                            for (int j = 0; j < 16; j++) eb[lane][j] = fma(-ar, (double)t[j], eb[lane][j]);
+                            store_block(prm.out, C0, sl);
+                        }
+                    }
                 }
             }
         }
@@ -268,15 +417,30 @@ cudaError_t make_slice_map(CUtensorMap *map, const SliceBuf &b, int box_rows)
 
 namespace {
 
-size_t tc_smem_bytes() { return (size_t)tc::STAGES * tc::STAGE_BYTES + 1024 + 256; }
+template <int KIND>
+size_t tc_smem_bytes()
+{
+    return (size_t)tc::Cfg<KIND>::STAGES * tc::Cfg<KIND>::STAGE_BYTES + 1024 + 256 + 2 * tc::BN * 4 + 128 * tc::EBP * 8;
+}
+
+int sm_count()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 148;
+    }
+    return n;
+}
 
 }  // namespace
 
 cudaError_t configure_tc_kernels()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes<0>());
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
+    return cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes<1>());
 }
 
 cudaError_t launch_split(const double *src, int64_t rows, int64_t cols, int64_t ld, const SliceBuf &dst,
@@ -298,17 +462,13 @@ cudaError_t launch_gemm_tc(const SliceBuf &P, const SliceBuf &Q, TcParams prm, S
     cudaError_t e;
     if ((e = make_slice_map(&mp, P, tc::BM)) != cudaSuccess) return e;
     if ((e = make_slice_map(&mq, Q, tc::BN)) != cudaSuccess) return e;
+    if (P.kind != Q.kind || P.ns != (P.kind == 0 ? 3 : 2) || Q.ns != P.ns || P.ld != Q.ld) return cudaErrorInvalidValue;
+    if (prm.lower_only && prm.rows != prm.cols) return cudaErrorInvalidValue;
     prm.bk = P.kind == 0 ? 64 : 32;
     prm.kblocks = (int)(P.ld / prm.bk);
-    int n = 0;   // slice pairs of total order below the slice count
-    for (int ord = 0; ord < P.ns; ord++)
-        for (int a = 0; a <= ord; a++) {
-            prm.pa[n] = (int8_t)a;
-            prm.pb[n] = (int8_t)(ord - a);
-            n++;
-        }
-    prm.npairs = n;
+    prm.npairs = P.ns * (P.ns + 1) / 2;
     if (out_sl) {
+        if (out_sl->ns != P.ns || out_sl->kind != P.kind) return cudaErrorInvalidValue;
         prm.out_slices = out_sl->ptr;
         prm.sl_ld = out_sl->ld;
         prm.sl_stride = out_sl->ld * out_sl->rows;
@@ -316,11 +476,14 @@ cudaError_t launch_gemm_tc(const SliceBuf &P, const SliceBuf &Q, TcParams prm, S
     } else {
         prm.out_ns = 0;
     }
-    dim3 grid((unsigned)((prm.cols + tc::BN - 1) / tc::BN), (unsigned)((prm.rows + tc::BM - 1) / tc::BM));
+    const int nrowt = (prm.rows + tc::BM - 1) / tc::BM, ncolt = (prm.cols + tc::BN - 1) / tc::BN;
+    const int ntiles = prm.lower_only ? nrowt * (nrowt + 1) / 2 : nrowt * ncolt;
+    if (ntiles == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)(ntiles < sm_count() ? ntiles : sm_count());
     if (P.kind == 0)
-        k_gemm_tc<0><<<grid, 192, tc_smem_bytes(), st>>>(mp, mq, prm);
+        k_gemm_tc<0><<<grid, 192, tc_smem_bytes<0>(), st>>>(mp, mq, prm);
     else
-        k_gemm_tc<1><<<grid, 192, tc_smem_bytes(), st>>>(mp, mq, prm);
+        k_gemm_tc<1><<<grid, 192, tc_smem_bytes<1>(), st>>>(mp, mq, prm);
     g_launches++;
     return cudaGetLastError();
 }

@@ -7,7 +7,7 @@
 // tensor cores are fast. The steps below move all sequential work to FP32 and all FP64-accurate
 // work to dense products on the tensor cores:
 //
-//   1. S~ = X X^T to FP32 accuracy (split BF16/TF32 product).
+//   1. S~ = X X^T to about 2^-35 (digit product truncated to six levels).
 //   2. FP32 blocked Cholesky S~ = L~ L~^T and, in the same sweep, M = L~^-1 (lower triangular,
 //      positive diagonal). M is a preconditioner only: nothing below needs it to be accurate.
 //   3. V1 = M X with the FP64-accurate digit product. For ANY lower-triangular M with positive
@@ -342,15 +342,16 @@ cudaError_t launch_gram_schmidt_mixed(pfsm_handle_s *h, cudaStream_t st)
     const int64_t N = h->N;
     const int64_t ld = padded_ld(N);
     const int ns = slices_for(h->prm.precision), kind = slice_kind(h->prm.precision);
-    SliceBuf sX{w.slX, N, ld, ns, kind}, sY{w.slY, N, ld, ns, kind}, sZ{w.slZ, N, ld, ns, kind};
+    SliceBuf sY{w.slY, N, ld, ns, kind}, sZ{w.slZ, N, ld, ns, kind};
     SliceBuf dP{w.ozP, N, ld, OZ_SLICES, 0}, dQ{w.ozQ, N, ld, OZ_SLICES, 0};
     cudaError_t e;
-    // 1. S~ = X X^T (lower) to FP32 accuracy, and its diagonal for the breakdown test
-    if ((e = launch_split(w.X, N, N, N, sX, false, nullptr, st)) != cudaSuccess) return e;
-    TcParams p{};
-    p.rows = (int)N; p.cols = (int)N; p.ldo = N; p.status = w.status;
-    p.epi = TC_EPI_STORE; p.out = w.S; p.lower_only = 1;
-    if ((e = launch_gemm_tc(sX, sX, p, nullptr, st)) != cudaSuccess) return e;
+    // 1. S~ = X X^T (lower) to about 2^-35 (six digit levels: a split product accumulated in FP32
+    //    would carry sqrt(N) 2^-24, which at large N makes E, and with it F, too large for the
+    //    split products of steps 5-6), and its diagonal for the breakdown test
+    OzParams o{};
+    if ((e = launch_oz_split(w.X, N, N, N, dP, w.ozeP, st)) != cudaSuccess) return e;
+    o.rows = (int)N; o.cols = (int)N; o.C = w.S; o.ldc = N; o.lower_only = 1; o.levels = 6; o.status = w.status;
+    if ((e = launch_gemm_oz(dP, w.ozeP, dP, w.ozeP, o, st)) != cudaSuccess) return e;
     if ((e = launch_copy_diag(w.S, N, w.sdiag, st)) != cudaSuccess) return e;
     if (h->timing && (e = cudaEventRecord(h->gs_ev[0], st)) != cudaSuccess) return e;
     // 2. M = L~^-1 in FP32
@@ -360,7 +361,7 @@ cudaError_t launch_gram_schmidt_mixed(pfsm_handle_s *h, cudaStream_t st)
     if ((e = launch_transpose(w.X, w.W, N, st)) != cudaSuccess) return e;
     if ((e = launch_oz_split_f32(w.M32, N, N, N, dP, w.ozeP, st)) != cudaSuccess) return e;
     if ((e = launch_oz_split(w.W, N, N, N, dQ, w.ozeQ, st)) != cudaSuccess) return e;
-    OzParams o{};
+    o = OzParams{};
     o.rows = (int)N; o.cols = (int)N; o.C = w.Y; o.ldc = N; o.p_lower = 1; o.status = w.status;
     if ((e = launch_gemm_oz(dP, w.ozeP, dQ, w.ozeQ, o, st)) != cudaSuccess) return e;
     // 4. S2 = V1 V1^T (lower) -> S

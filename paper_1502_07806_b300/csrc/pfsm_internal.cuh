@@ -135,7 +135,6 @@ struct SliceBuf {
 struct TcParams {
     int rows, cols;                 // output extent
     int kblocks, bk, npairs;        // filled by launch_gemm_tc
-    int8_t pa[16], pb[16];
     const int32_t *krange;          // per 64-row tile K range, or null
     int nrowtiles64;
     int epi;
@@ -156,7 +155,8 @@ cudaError_t launch_split(const double *src, int64_t rows, int64_t cols, int64_t 
 cudaError_t launch_gemm_tc(const SliceBuf &P, const SliceBuf &Q, TcParams prm, SliceBuf *out_sl,
                            cudaStream_t st);
 // ---- FP64-accurate products on the BF16 tensor cores (k_gemm_oz.cu) ----
-#define OZ_SLICES 9                 // base-32 digits per entry (about 2^-45 relative accuracy)
+#define OZ_SLICES 9                 // base-32 digits per entry (2^-46 of the row's largest)
+#define OZ_LEVELS 11                // digit levels s + t kept by default (see k_gemm_oz.cu)
 struct OzParams {
     int rows, cols;                 // output extent
     int kblocks;                    // 64-element K blocks (filled by launch_gemm_oz)
@@ -165,6 +165,7 @@ struct OzParams {
     int sub;                        // C -= P Q^T instead of C = P Q^T
     int lower_only;                 // only entries with c <= r
     int p_lower;                    // P is lower triangular: skip K blocks beyond the tile's rows
+    int levels;                     // digit levels L = s + t kept (0: OZ_LEVELS)
     const double *Vp; int64_t ldv;  // with dcol: C[r, c] += Vp[r, c] dcol[c] (exact diagonal term)
     const double *dcol;
     int32_t *status;

@@ -146,6 +146,24 @@ __device__ __forceinline__ void store_slices(void *base, int64_t sstride, int64_
     }
 }
 
+// Writes the slices of an FP32 value (all arithmetic in FP32: the pieces of a 24-bit significand).
+template <int KIND>
+__device__ __forceinline__ void store_slices_f32(void *base, int64_t sstride, int64_t o, int ns, float v)
+{
+    float rem = v;
+    for (int s = 0; s < ns; s++) {
+        if (KIND == 0) {
+            const __nv_bfloat16 b = __float2bfloat16_rn(rem);
+            reinterpret_cast<__nv_bfloat16 *>(base)[s * sstride + o] = b;
+            rem -= __bfloat162float(b);
+        } else {
+            const float t = to_tf32(rem);
+            reinterpret_cast<float *>(base)[s * sstride + o] = t;
+            rem -= t;
+        }
+    }
+}
+
 }  // namespace tc
 
 // 3-D TMA map over row-major slices: {ld (K), rows, ns}, box {128 bytes of K, box_rows, 1}.
