@@ -48,7 +48,7 @@ void free_ws(pfsm_handle_s *h)
     void *ptrs[] = {w.plan, w.tile_krange, w.status, w.gersh, w.X, w.Xfs, w.Y, w.S, w.W, w.Vrm,
                     w.sdiag, w.eps, w.alpha, w.lam, w.res, w.refl, w.tau, w.td, w.te,
                     w.sel_val, w.sel_vec, w.iiwork, w.slices, w.slE, w.slX, w.slY, w.slZ,
-                    w.Z, w.dA, w.Linv, w.ozP, w.ozQ, w.ozeP, w.ozeQ, w.L32, w.R32, w.M32, w.F};
+                    w.Z, w.dA, w.Linv, w.ozP, w.ozQ, w.ozeP, w.ozeQ, w.L32, w.R32, w.M32, w.F, w.VW, w.WV, w.tdP, w.tdQ, w.tdeP, w.tdeQ};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     w = Workspace{};
@@ -56,6 +56,10 @@ void free_ws(pfsm_handle_s *h)
 
 // Largest dynamic shared memory a CTA may use on this part.
 constexpr size_t kSmemCap = 227 * 1024;
+// The blocked reduction (k_tridiag_panel) issues more FP64 instructions per step than the
+// unblocked one saves (B300 spends ~64 cycles of an SMSP's FP64 pipe on every FP64 warp
+// instruction, shuffle reductions and redundant scalar work included); off until that changes.
+constexpr bool kUseBlockedReduction = false;
 
 }  // namespace
 
@@ -121,13 +125,29 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
     else if (smem_rows(8) <= kSmemCap) { h->cl = 8; h->rows_in_smem = true; }
     else if (smem_rows(16) <= kSmemCap) { h->cl = 16; h->rows_in_smem = true; }
     else { h->cl = 16; h->rows_in_smem = false; }
+    // the mixed forms' blocked reduction keeps each warp's rows of V and W in registers (up to
+    // 24 rows a warp) and the window rows in shared memory for windows up to tri_mcap
+    if (prm.precision != PFSM_FP64 && kUseBlockedReduction) {
+        const int cl = Mx <= 128 ? 4 : (Mx <= 512 ? 8 : 16);
+        const int rpw = ((Mx + cl - 1) / cl + 7) / 8;
+        if (rpw <= 24) {
+            h->tri_blocked = true;
+            h->cl = cl;
+            h->tri_rpw = rpw <= 8 ? 8 : 24;
+            int mc = Mx;
+            while (mc > 0 && tri_panel_smem(Mx, cl, mc) > kSmemCap) mc -= 8;
+            h->tri_mcap = mc < 0 ? 0 : mc;
+        }
+    }
 
     Workspace &w = h->ws;
     const size_t NN = (size_t)N * N;
     const int64_t ntiles = (N + kFsTileRows - 1) / kFsTileRows;
     const size_t nbM = (size_t)nblocks * h->Mmax;
     size_t ii = (size_t)nblocks * h->mmax * 5 * h->Mmax;
-    if (!h->rows_in_smem && nbM * h->Mmax > ii) ii = nbM * h->Mmax;
+    // the window matrices in global memory: for rows that do not fit in shared memory, and for the
+    // blocked reduction of the mixed forms, whose trailing updates run between panel launches
+    if ((!h->rows_in_smem || prm.precision != PFSM_FP64) && nbM * h->Mmax > ii) ii = nbM * h->Mmax;
     cudaError_t e = cudaSuccess;
 #define PFSM_ALLOC(ptr, cnt) if (e == cudaSuccess) e = alloc(&(ptr), (cnt))
     PFSM_ALLOC(w.plan, 4 * (size_t)nblocks);
@@ -179,6 +199,19 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
         PFSM_ALLOC(w.M32, NN);
         if (e == cudaSuccess) e = cudaMemset(w.M32, 0, NN * sizeof(float));   // stays zero above the diagonal
         PFSM_ALLOC(w.F, NN);
+        {
+            const size_t vw = nbM * 2 * kPanel;                  // nb * Mmax rows x 2 * kPanel
+            PFSM_ALLOC(w.VW, vw);
+            PFSM_ALLOC(w.WV, vw);
+            if (e == cudaSuccess) e = cudaMemset(w.VW, 0, vw * sizeof(double));
+            if (e == cudaSuccess) e = cudaMemset(w.WV, 0, vw * sizeof(double));
+            uint8_t *t1 = nullptr, *t2 = nullptr;
+            PFSM_ALLOC(t1, (size_t)OZ_SLICES * vw * 2);
+            PFSM_ALLOC(t2, (size_t)OZ_SLICES * vw * 2);
+            w.tdP = t1; w.tdQ = t2;
+            PFSM_ALLOC(w.tdeP, nbM);
+            PFSM_ALLOC(w.tdeQ, nbM);
+        }
         if (e == cudaSuccess) e = configure_gs_mixed_kernels();
         if (e == cudaSuccess) e = configure_tc_kernels();
         if (e == cudaSuccess) e = configure_oz_kernels();

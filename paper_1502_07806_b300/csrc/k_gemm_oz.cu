@@ -85,8 +85,13 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
 {
     using namespace tc;
     using namespace oz;
-    const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
+    const int z = blockIdx.z;
+    const int row0 = prm.row_base + blockIdx.y * BM, col0 = prm.row_base + blockIdx.x * BN;
+    const int rows_lim = prm.ext ? prm.ext[z] : prm.rows, cols_lim = prm.ext ? prm.ext[z] : prm.cols;
+    if (row0 >= rows_lim || col0 >= cols_lim) return;              // tile outside this window
     if (prm.lower_only && col0 > row0 + BM - 1) return;           // whole tile above the diagonal
+    const int64_t zr = (int64_t)z * prm.zrow;                      // operand row offset
+    double *Cz = prm.C + (int64_t)z * prm.zc;
     extern __shared__ __align__(1024) uint8_t smraw[];
     const uint32_t raw = smem_u32(smraw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -96,6 +101,7 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 4);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     int *ecol = reinterpret_cast<int *>(tmem_slot + 2);           // BN column exponents
+    double *estage = reinterpret_cast<double *>(gbase + STAGES * STAGE_BYTES + 1024);   // 128 x (BN + 1)
     const uint32_t bar_base = smem_u32(bars);
     auto full_bar = [&](int s) { return bar_base + 8u * s; };
     auto empty_bar = [&](int s) { return bar_base + 8u * (STAGES + s); };
@@ -126,7 +132,7 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapQ) : "memory");
     }
     for (int j = threadIdx.x; j < BN; j += blockDim.x)
-        ecol[j] = (col0 + j < prm.cols) ? prm.eq[col0 + j] : 0;
+        ecol[j] = (col0 + j < cols_lim) ? prm.eq[zr + col0 + j] : 0;
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      ::"r"(smem_u32(tmem_slot)), "r"(TMEM_COLS) : "memory");
@@ -157,8 +163,8 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
                         if (*abort_flag) { stop = true; break; }
                         const uint32_t a = base + s * STAGE_BYTES, b = a + A_BYTES;
                         mbar_expect_tx(full_bar(s), STAGE_BYTES);
-                        tma_load_3d(a, &mapP, full_bar(s), kb * 64, row0, sa);
-                        tma_load_3d(b, &mapQ, full_bar(s), kb * 64, col0, sb);
+                        tma_load_3d(a, &mapP, full_bar(s), kb * 64, (int)(zr + row0), sa);
+                        tma_load_3d(b, &mapQ, full_bar(s), kb * 64, (int)(zr + col0), sb);
                         issued = it + 1;
                     }
                 }
@@ -206,9 +212,13 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
     } else {
         const int gq = warp & 3;
         const int r = row0 + 32 * gq + lane;
-        double acc[BN];
+        // the levels are combined in float-float (hi + lo, about 48 bits) with Knuth's TwoSum: each
+        // level sum is an exact FP32 integer and its scale an exact power of two, so a level costs
+        // a few FP32 operations per entry instead of two FP64 ones (the FP64 pipe is 64 times
+        // slower); one FP64 conversion per entry at the end
+        float hi[BN], lo[BN];
 #pragma unroll
-        for (int j = 0; j < BN; j++) acc[j] = 0.0;
+        for (int j = 0; j < BN; j++) { hi[j] = 0.0f; lo[j] = 0.0f; }
         bool ok = true;
         for (int g = 0; g < groups; g++) {
             const int L = g / nch, buf = g & 1;
@@ -221,28 +231,45 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
                 break;
             }
             fence_after();
-            const double scale = ldexp(1.0, -oz::BETA * (L + 2));
+            const float scale = __int_as_float((127 - oz::BETA * (L + 2)) << 23);   // 2^-5(L+2)
             uint32_t v[32];
-            tmem_ld32(tmem_acc + ((uint32_t)(32 * gq) << 16) + 64u * buf, v);
 #pragma unroll
-            for (int j = 0; j < 32; j++) acc[j] = fma((double)__uint_as_float(v[j]), scale, acc[j]);
-            tmem_ld32(tmem_acc + ((uint32_t)(32 * gq) << 16) + 64u * buf + 32, v);
+            for (int half = 0; half < 2; half++) {
+                tmem_ld32(tmem_acc + ((uint32_t)(32 * gq) << 16) + 64u * buf + 32 * half, v);
 #pragma unroll
-            for (int j = 0; j < 32; j++) acc[32 + j] = fma((double)__uint_as_float(v[j]), scale, acc[32 + j]);
+                for (int j = 0; j < 32; j++) {
+                    const float x = __uint_as_float(v[j]) * scale;
+                    const float h = hi[32 * half + j];
+                    const float sum = h + x, bp = sum - h;
+                    lo[32 * half + j] += (h - (sum - bp)) + (x - bp);
+                    hi[32 * half + j] = sum;
+                }
+            }
             fence_before();
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce_bar(buf)) : "memory");
         }
-        if (ok && r < prm.rows) {
-            const int er = prm.ep[r];
+        // epilogue through this warp's shared-memory staging block (32 rows x 64 columns), so
+        // that the loads and stores of C (and of the exact diagonal term) are row-contiguous
+        double(*eb)[BN + 1] = reinterpret_cast<double(*)[BN + 1]>(estage) + 32 * gq;
+        const int R0 = row0 + 32 * gq;
+        const int er = (ok && r < rows_lim) ? prm.ep[zr + r] : 0;
 #pragma unroll
-            for (int j = 0; j < BN; j++) {
-                const int c = col0 + j;
-                if (c < prm.cols && !(prm.lower_only && c > r)) {
-                    double res = ldexp(acc[j], er + ecol[j]);
-                    if (prm.dcol) res = fma(prm.Vp[(int64_t)r * prm.ldv + c], prm.dcol[c], res);
-                    const int64_t o = (int64_t)r * prm.ldc + c;
-                    if (prm.sub) prm.C[o] -= res;
-                    else prm.C[o] = res;
+        for (int j = 0; j < BN; j++) eb[lane][j] = ldexp((double)hi[j] + (double)lo[j], er + ecol[j]);
+        __syncwarp();
+        if (ok) {
+            for (int rr = 0; rr < 32; rr++) {
+                const int gr = R0 + rr;
+                if (gr >= rows_lim) break;
+#pragma unroll
+                for (int h = 0; h < BN / 32; h++) {
+                    const int c = col0 + 32 * h + lane;
+                    if (c < cols_lim && !(prm.lower_only && c > gr)) {
+                        double res = eb[rr][32 * h + lane];
+                        if (prm.dcol) res = fma(prm.Vp[(int64_t)gr * prm.ldv + c], prm.dcol[c], res);
+                        const int64_t o = (int64_t)gr * prm.ldc + c;
+                        if (prm.sub) Cz[o] -= res;
+                        else Cz[o] = res;
+                    }
                 }
             }
         }
@@ -258,7 +285,7 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
 // ---- host side -------------------------------------------------------------------------------
 
 namespace {
-size_t oz_smem_bytes() { return (size_t)oz::STAGES * oz::STAGE_BYTES + 1024 + 512 + oz::BN * 4; }
+size_t oz_smem_bytes() { return (size_t)oz::STAGES * oz::STAGE_BYTES + 1024 + 1024 + (size_t)128 * (oz::BN + 1) * 8; }
 }
 
 cudaError_t configure_oz_kernels()
@@ -287,7 +314,7 @@ cudaError_t launch_oz_split_f32(const float *src, int64_t rows, int64_t cols, in
 }
 
 cudaError_t launch_gemm_oz(const SliceBuf &P, const int32_t *ep, const SliceBuf &Q, const int32_t *eq,
-                           OzParams prm, cudaStream_t st)
+                           OzParams prm, cudaStream_t st, int batch)
 {
     CUtensorMap mp, mq;
     cudaError_t e;
@@ -296,7 +323,10 @@ cudaError_t launch_gemm_oz(const SliceBuf &P, const int32_t *ep, const SliceBuf 
     prm.kblocks = (int)(P.ld / 64);
     prm.ep = ep;
     prm.eq = eq;
-    dim3 grid((unsigned)((prm.cols + oz::BN - 1) / oz::BN), (unsigned)((prm.rows + oz::BM - 1) / oz::BM));
+    // batched: prm.rows / prm.cols give the grid extent from row_base (the largest window)
+    const int ext_r = prm.rows - prm.row_base, ext_c = prm.cols - prm.row_base;
+    if (ext_r <= 0 || ext_c <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((ext_c + oz::BN - 1) / oz::BN), (unsigned)((ext_r + oz::BM - 1) / oz::BM), (unsigned)batch);
     k_gemm_oz<<<grid, 192, oz_smem_bytes(), st>>>(mp, mq, prm);
     g_launches++;
     return cudaGetLastError();

@@ -36,8 +36,14 @@ __device__ __forceinline__ double block_sum(double v, double *red)
     __syncthreads();
     if ((threadIdx.x & 31) == 0) red[w] = v;
     __syncthreads();
+    // pairwise over the warps (a serial sum would be a chain of dependent FP64 adds); the same
+    // order in every thread and every CTA
     double t = 0.0;
-    for (int i = 0; i < nw; i++) t += red[i];   // same order in every thread and every CTA
+    if (nw == 8) {
+        t = ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
+    } else {
+        for (int i = 0; i < nw; i++) t += red[i];
+    }
     return t;
 }
 
@@ -155,6 +161,282 @@ k_tridiag(const double *__restrict__ A, int64_t N, const int32_t *__restrict__ p
             btd[0] = rowp(0)[0];
         }
         if (rank == 0) { bte[M - 1] = 0.0; if (M >= 2) btau[M - 2] = 0.0; btau[M - 1] = 0.0; }
+    }
+    cluster.sync();   // keep every CTA's shared memory alive until remote writes are done
+}
+
+// 1/p and 1/sqrt(d) for d, p > 0 of any FP64 magnitude without the IEEE FP64 divide / square
+// root sequences (each ~10 dependent FP64 instructions of ~64 cycles on B300): the exponent is
+// split off (so the FP32 seed never under- or overflows), then an FP32 estimate and two Newton
+// steps, y <- y (2 - p y) and y <- y (3 - d y^2) / 2, give about 1 ulp.
+__device__ __forceinline__ double scaled_rcp(double p)
+{
+    int e;
+    const double m = frexp(p, &e);                     // p = m 2^e, m in [0.5, 1)
+    double y = (double)__frcp_rn((float)m);
+    y = y * fma(-m, y, 2.0);
+    y = y * fma(-m, y, 2.0);
+    return ldexp(y, -e);
+}
+
+__device__ __forceinline__ double scaled_rsqrt(double d)
+{
+    int e;
+    double m = frexp(d, &e);
+    if (e & 1) { m *= 2.0; e -= 1; }                  // d = m 2^e, e even, m in [0.5, 2)
+    double y = (double)rsqrtf((float)m);
+    y = y * fma(-0.5 * m, y * y, 1.5);
+    y = y * fma(-0.5 * m, y * y, 1.5);
+    return ldexp(y, -e / 2);
+}
+
+// ---- blocked reduction (mixed forms) ----------------------------------------------------------
+// The same reduction in panels of kPanel = 32 columns (the blocked form of Golub & Van Loan
+// Sec. 8.3.1, as in LAPACK's symmetric tridiagonal reduction). Within a panel the trailing matrix
+// is NOT updated: with the panel's reflectors v_q and vectors w_q = p_q - (beta_q p_q.v_q / 2) v_q
+// collected in V and W, the current matrix is A_ps - V W^T - W V^T (A_ps: the matrix at the start
+// of the panel), so step k needs
+//   column k:  A_ps[:, k] - V W[k, :]^T - W V[k, :]^T          (O(j M) per step)
+//   p = beta (A_ps v - V (W^T v) - W (V^T v))                   (one mat-vec on A_ps)
+// and the rank-2 updates of the unblocked loop (2/3 of its FP64 work) become one rank-64 update
+// per panel, A_ps -= [V W] [W V]^T, done by the FP64-accurate digit product on the tensor cores
+// between panel launches. V and W are stored as the balanced pairs (sqrt(beta) v, w / sqrt(beta))
+// (same v w^T, both of order one, as the digit product scales each row of [V W] by one power of
+// two). Every step costs two cluster barriers: (A) the updated column k is gathered, (B) the
+// mat-vec entries and the partial dot products V^T v, W^T v are gathered.
+//
+// B300 issues a dependent FP64 FMA every ~64 cycles, so no FP64 reduction here is a long serial
+// chain: a warp owns every 8th local row (up to RPW rows), lane q holds V[row][q] and W[row][q] in
+// registers, and the per-row sums over q are shuffle trees run for all the warp's rows at once.
+// The panel rows' V and W entries (needed by every CTA for the next column) are recomputed
+// redundantly in every CTA from the gathered mat-vec. Rows of A_ps sit in shared memory when the
+// window fits (M <= Mcap), else they are read from the window matrix in global memory (L2).
+template <int RPW>
+__global__ void __launch_bounds__(kTriThreads, 1)
+k_tridiag_panel(const double *__restrict__ A, int64_t N, const int32_t *__restrict__ plan, int32_t nb,
+                int32_t Mmax, int32_t Mcap, int k0, double *__restrict__ gwork, double *__restrict__ refl,
+                double *__restrict__ tau, double *__restrict__ td, double *__restrict__ te,
+                double *__restrict__ VW, double *__restrict__ WV)
+{
+    constexpr int NB = kPanel;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int CL = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int b = blockIdx.x / CL;
+    const int64_t s0 = plan[2 * nb + b];
+    const int M = plan[3 * nb + b];
+    const int kend = min(k0 + NB, M - 2);              // Householder steps k0 .. kend-1
+    if (k0 > 0 && k0 >= M - 2) return;                 // this window finished in an earlier panel
+    double *G = gwork + (size_t)b * Mmax * Mmax;       // the window's matrix, updated between panels
+    const bool srows = M <= Mcap;
+    const int Rcap = (Mcap + CL - 1) / CL;
+    extern __shared__ double sm[];
+    double *rows = sm;                                 // Rcap x Mcap (when the window fits)
+    double *vbuf = sm + (size_t)Rcap * Mcap;
+    double *pbuf = vbuf + Mmax;
+    double *hv = pbuf + Mmax;
+    double *red = hv + Mmax;                           // 64
+    double *Vp = red + 64, *Wp = Vp + (NB + 2) * NB;   // panel rows k0 .. k0 + NB + 1
+    double *dots = Wp + (NB + 2) * NB;                 // [CL][2 NB] partial V^T v, W^T v
+    double *ab = dots + (size_t)CL * 2 * NB;           // a = V^T v (NB), b = W^T v (NB)
+    double *wd = ab + 2 * NB;                          // [8 warps][2 NB]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    auto rowp = [&](int i) -> double * {
+        return srows ? rows + (size_t)(i / CL) * Mcap : G + (size_t)i * Mmax;
+    };
+    auto grow = [&](int t) { return (warp + 8 * t) * CL + rank; };   // global row of slot t
+    double *brefl = refl + (size_t)b * Mmax * Mmax;
+    double *btau = tau + (size_t)b * Mmax, *btd = td + (size_t)b * Mmax, *bte = te + (size_t)b * Mmax;
+
+    // rows of the panel-start matrix (the first panel copies the window out of A)
+    for (int i = rank + warp * CL; i < M; i += 8 * CL) {
+        if (i < k0) continue;
+        double *dst = rowp(i);
+        if (k0 == 0) {
+            const double *src = A + (s0 + i) * N + s0;
+            double *gdst = G + (size_t)i * Mmax;
+            for (int j = lane; j < M; j += 32) {
+                const double x = src[j];
+                gdst[j] = x;
+                if (srows) dst[j] = x;
+            }
+        } else if (srows) {
+            const double *gsrc = G + (size_t)i * Mmax;
+            for (int j = k0 + lane; j < M; j += 32) dst[j] = gsrc[j];
+        }
+    }
+    double Vr[RPW], Wr[RPW];                           // V[grow(t)][lane], W[grow(t)][lane]
+#pragma unroll
+    for (int t = 0; t < RPW; t++) { Vr[t] = 0.0; Wr[t] = 0.0; }
+    for (int t = tid; t < 2 * (NB + 2) * NB; t += blockDim.x) Vp[t] = 0.0;
+    // every CTA of the cluster must be running before any distributed-shared-memory access
+    cluster.sync();
+
+    for (int k = k0; k < kend; k++) {
+        const int j = k - k0;
+        // (A) column k of the current matrix on owned rows i >= k, gathered into every vbuf
+        {
+            const double wk = lane < j ? Wp[j * NB + lane] : 0.0, vk = lane < j ? Vp[j * NB + lane] : 0.0;
+            double part[RPW];
+#pragma unroll
+            for (int t = 0; t < RPW; t++) part[t] = fma(Vr[t], wk, Wr[t] * vk);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int t = 0; t < RPW; t++) part[t] += __shfl_xor_sync(0xffffffffu, part[t], o);
+#pragma unroll
+            for (int t = 0; t < RPW; t++) {
+                const int i = grow(t);
+                if (i < M && i >= k && lane < CL) cluster.map_shared_rank(vbuf, lane)[i] = rowp(i)[k] - part[t];
+            }
+        }
+        cluster.sync();
+        // Householder vector of column k (redundantly and identically in every CTA)
+        const double x0 = vbuf[k + 1];
+        double t2 = 0.0;
+        for (int i = k + 2 + tid; i < M; i += blockDim.x) t2 = fma(vbuf[i], vbuf[i], t2);
+        const double tail2 = block_sum(t2, red);
+        double beta = 0.0, alpha = x0;
+        if (tail2 != 0.0) {
+            const double nn = fma(x0, x0, tail2);
+            const double xn = nn * scaled_rsqrt(nn);
+            alpha = (x0 >= 0.0) ? -xn : xn;
+            const double v0 = x0 - alpha;
+            beta = 2.0 * scaled_rcp(fma(v0, v0, tail2));
+        }
+        for (int i = k + 1 + tid; i < M; i += blockDim.x)
+            hv[i] = (beta != 0.0) ? ((i == k + 1) ? x0 - alpha : vbuf[i]) : 0.0;
+        if (rank == 0) {
+            if (tid == 0) { btd[k] = vbuf[k]; bte[k] = alpha; btau[k] = beta; }
+            double *rr = brefl + (size_t)k * Mmax;
+            for (int i = k + 1 + tid; i < M; i += blockDim.x)
+                rr[i] = (beta != 0.0) ? ((i == k + 1) ? x0 - alpha : vbuf[i]) : 0.0;
+        }
+        __syncthreads();
+        // (B) s = A_ps v on owned rows (broadcast), partial V^T v and W^T v over owned rows
+        if (beta != 0.0) {
+            double acc[RPW];
+            const double *rp[RPW];
+#pragma unroll
+            for (int t = 0; t < RPW; t++) {
+                acc[t] = 0.0;
+                const int i = grow(t);
+                rp[t] = (i < M && i > k) ? rowp(i) : nullptr;
+            }
+            for (int l = k + 1 + lane; l < M; l += 32) {
+                const double h = hv[l];
+#pragma unroll
+                for (int t = 0; t < RPW; t++)
+                    if (rp[t]) acc[t] = fma(rp[t][l], h, acc[t]);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int t = 0; t < RPW; t++) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+            double da = 0.0, db = 0.0, da2 = 0.0, db2 = 0.0;   // two chains each
+#pragma unroll
+            for (int t = 0; t < RPW; t++) {
+                const int i = grow(t);
+                if (i < M && i > k) {
+                    if (lane < CL) cluster.map_shared_rank(pbuf, lane)[i] = acc[t];
+                    const double h = hv[i];
+                    if (t & 1) { da2 = fma(Vr[t], h, da2); db2 = fma(Wr[t], h, db2); }
+                    else { da = fma(Vr[t], h, da); db = fma(Wr[t], h, db); }
+                }
+            }
+            wd[warp * 2 * NB + lane] = da + da2;
+            wd[warp * 2 * NB + NB + lane] = db + db2;
+        }
+        __syncthreads();
+        if (beta != 0.0 && tid < 2 * NB) {
+            const double s01 = wd[tid] + wd[2 * NB + tid], s23 = wd[4 * NB + tid] + wd[6 * NB + tid];
+            const double s45 = wd[8 * NB + tid] + wd[10 * NB + tid], s67 = wd[12 * NB + tid] + wd[14 * NB + tid];
+            const double sum = (s01 + s23) + (s45 + s67);
+            for (int r = 0; r < CL; r++) cluster.map_shared_rank(dots, r)[rank * 2 * NB + tid] = sum;
+        }
+        cluster.sync();
+        if (beta != 0.0) {
+            // a = V^T v, b = W^T v (same summation order in every CTA)
+            if (tid < 2 * NB) {
+                double acc = 0.0;
+                for (int r = 0; r < CL; r++) acc += dots[r * 2 * NB + tid];
+                ab[tid] = acc;
+            }
+            double sv = 0.0;
+            for (int i = k + 1 + tid; i < M; i += blockDim.x) sv = fma(pbuf[i], hv[i], sv);
+            sv = block_sum(sv, red);                   // also orders the ab[] writes before use
+            const double aq = ab[lane], bq = ab[NB + lane];
+            double ab2 = aq * bq;                      // a . b over the lanes (zero beyond j)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) ab2 += __shfl_xor_sync(0xffffffffu, ab2, o);
+            const double Kc = 0.5 * beta * beta * (sv - 2.0 * ab2);
+            const double isb = scaled_rsqrt(beta), sb = beta * isb;
+            // w = beta (s - V b - W a) - Kc v on owned rows; store column j of (V, W) balanced
+            double part[RPW];
+#pragma unroll
+            for (int t = 0; t < RPW; t++) part[t] = fma(Vr[t], bq, Wr[t] * aq);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int t = 0; t < RPW; t++) part[t] += __shfl_xor_sync(0xffffffffu, part[t], o);
+#pragma unroll
+            for (int t = 0; t < RPW; t++) {
+                const int i = grow(t);
+                if (i < M && i > k && lane == j) {
+                    const double w = fma(-Kc, hv[i], beta * (pbuf[i] - part[t]));
+                    Vr[t] = sb * hv[i];
+                    Wr[t] = w * isb;
+                }
+            }
+            // the same for the panel rows k0 + pr > k, kept in every CTA (one warp per row)
+            for (int pr = j + 1 + warp; pr < NB + 2 && k0 + pr < M; pr += 8) {
+                const int i = k0 + pr;
+                double q = fma(Vp[pr * NB + lane], bq, Wp[pr * NB + lane] * aq);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+                if (lane == 0) {
+                    const double w = fma(-Kc, hv[i], beta * (pbuf[i] - q));
+                    Vp[pr * NB + j] = sb * hv[i];
+                    Wp[pr * NB + j] = w * isb;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    const bool last = M - 2 <= k0 + NB;
+    if (last) {
+        // the trailing 2 x 2 (or 1 x 1) with the panel's corrections
+        auto corr = [&](int r1, int r2) {   // (V W^T + W V^T)[r1, r2], both panel rows
+            double c = 0.0;
+            const int p1 = r1 - k0, p2 = r2 - k0;
+            if (p1 >= 0 && p2 >= 0 && p1 < NB + 2 && p2 < NB + 2)
+                for (int q = 0; q < NB; q++)
+                    c = fma(Vp[p1 * NB + q], Wp[p2 * NB + q], fma(Wp[p1 * NB + q], Vp[p2 * NB + q], c));
+            return c;
+        };
+        if (tid == 0) {
+            if (M >= 2) {
+                if ((M - 2) % CL == rank) btd[M - 2] = rowp(M - 2)[M - 2] - corr(M - 2, M - 2);
+                if ((M - 1) % CL == rank) {
+                    btd[M - 1] = rowp(M - 1)[M - 1] - corr(M - 1, M - 1);
+                    bte[M - 2] = rowp(M - 1)[M - 2] - corr(M - 1, M - 2);
+                }
+            } else if (rank == 0) {
+                btd[0] = rowp(0)[0];
+            }
+            if (rank == 0) { bte[M - 1] = 0.0; if (M >= 2) btau[M - 2] = 0.0; btau[M - 1] = 0.0; }
+        }
+    } else {
+        // operands of the trailing update A_ps -= [V W] [W V]^T, rows >= k0 + NB
+#pragma unroll
+        for (int t = 0; t < RPW; t++) {
+            const int i = grow(t);
+            if (i < M && i >= kend) {
+                double *o1 = VW + ((size_t)b * Mmax + i) * 2 * NB, *o2 = WV + ((size_t)b * Mmax + i) * 2 * NB;
+                o1[lane] = Vr[t]; o1[NB + lane] = Wr[t];
+                o2[lane] = Wr[t]; o2[NB + lane] = Vr[t];
+            }
+        }
     }
     cluster.sync();   // keep every CTA's shared memory alive until remote writes are done
 }
@@ -535,6 +817,10 @@ cudaError_t configure_kernels(pfsm_handle_s *h)
     if ((e = cudaFuncSetAttribute(k_tridiag<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
     if ((e = set_max((const void *)k_tridiag<false>)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_tridiag<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
+    if ((e = set_max((const void *)k_tridiag_panel<8>)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_tridiag_panel<8>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
+    if ((e = set_max((const void *)k_tridiag_panel<24>)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_tridiag_panel<24>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
     if ((e = set_max((const void *)k_bisect)) != cudaSuccess) return e;
     return set_max((const void *)k_backtransform);
 }
@@ -545,7 +831,43 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
     const int nb = h->nb, Mmax = h->Mmax, mmax = h->mmax, CL = h->cl;
     cudaError_t e0;
     // 1. tridiagonalisation, one cluster per window
-    {
+    if (h->tri_blocked) {
+        // blocked: one panel launch per kPanel columns, the trailing update as a batched digit
+        // product A_ps[k1:, k1:] -= [V W] [W V]^T per window (FP64-accurate, tensor cores)
+        const size_t smem = tri_panel_smem(Mmax, CL, h->tri_mcap);
+        const int64_t srows = (int64_t)nb * Mmax;
+        SliceBuf dP{w.tdP, srows, 2 * kPanel, OZ_SLICES, 0}, dQ{w.tdQ, srows, 2 * kPanel, OZ_SLICES, 0};
+        for (int k0 = 0; k0 == 0 || k0 < Mmax - 2; k0 += kPanel) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)(nb * CL));
+            cfg.blockDim = dim3(kTriThreads);
+            cfg.dynamicSmemBytes = smem;
+            cfg.stream = st;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = CL;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            cudaError_t e;
+            if (h->tri_rpw == 8)
+                e = counted(cudaLaunchKernelEx(&cfg, k_tridiag_panel<8>, A, h->N, (const int32_t *)w.plan, nb, Mmax,
+                                               h->tri_mcap, k0, w.iiwork, w.refl, w.tau, w.td, w.te, w.VW, w.WV));
+            else
+                e = counted(cudaLaunchKernelEx(&cfg, k_tridiag_panel<24>, A, h->N, (const int32_t *)w.plan, nb, Mmax,
+                                               h->tri_mcap, k0, w.iiwork, w.refl, w.tau, w.td, w.te, w.VW, w.WV));
+            if (e != cudaSuccess) return e;
+            const int k1 = k0 + kPanel;
+            if (k1 >= Mmax - 2) break;                 // every window ended in this panel
+            if ((e = launch_oz_split(w.VW, srows, 2 * kPanel, 2 * kPanel, dP, w.tdeP, st)) != cudaSuccess) return e;
+            if ((e = launch_oz_split(w.WV, srows, 2 * kPanel, 2 * kPanel, dQ, w.tdeQ, st)) != cudaSuccess) return e;
+            OzParams o{};
+            o.rows = Mmax; o.cols = Mmax; o.C = w.iiwork; o.ldc = Mmax; o.sub = 1; o.status = w.status;
+            o.zrow = Mmax; o.zc = (int64_t)Mmax * Mmax; o.row_base = k1; o.ext = w.plan + 3 * nb;
+            if ((e = launch_gemm_oz(dP, w.tdeP, dQ, w.tdeQ, o, st, nb)) != cudaSuccess) return e;
+        }
+    } else {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(nb * CL));
         cfg.blockDim = dim3(kTriThreads);

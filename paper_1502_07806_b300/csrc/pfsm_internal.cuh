@@ -56,6 +56,11 @@ struct Workspace {
     // preconditioner M = L~^-1 (zero above the diagonal), and the FP64 correction factor F
     float *L32 = nullptr, *R32 = nullptr, *M32 = nullptr;
     double *F = nullptr;
+    // mixed-form blocked tridiagonalisation: per window rows of [V W] and [W V] (nb * Mmax x
+    // 2 * 32), their digit matrices and row exponents
+    double *VW = nullptr, *WV = nullptr;
+    void *tdP = nullptr, *tdQ = nullptr;
+    int32_t *tdeP = nullptr, *tdeQ = nullptr;
 };
 
 }  // namespace pfsm
@@ -69,6 +74,9 @@ struct pfsm_handle_s {
     int32_t Mmax = 0;    // largest window
     int32_t cl = 8;      // CTAs per submatrix cluster
     bool rows_in_smem = true;
+    bool tri_blocked = false;      // mixed forms: blocked reduction (k_tridiag_panel)
+    int32_t tri_rpw = 8;           // its rows-per-warp register capacity (8 or 24)
+    int32_t tri_mcap = 0;          // largest window kept in shared memory by it
     int32_t *h_slices = nullptr;   // host copy of explicit slice sizes (or null)
     pfsm::Workspace ws;
     cudaStream_t last_stream = nullptr;
@@ -166,6 +174,11 @@ struct OzParams {
     int lower_only;                 // only entries with c <= r
     int p_lower;                    // P is lower triangular: skip K blocks beyond the tile's rows
     int levels;                     // digit levels L = s + t kept (0: OZ_LEVELS)
+    // batched windows (blockIdx.z = window z): operand rows z * zrow + i, C + z * zc, output
+    // entries (i, j) for row_base <= i, j < ext[z] (ext null: one product, row_base 0)
+    int64_t zrow, zc;
+    int row_base;
+    const int32_t *ext;
     const double *Vp; int64_t ldv;  // with dcol: C[r, c] += Vp[r, c] dcol[c] (exact diagonal term)
     const double *dcol;
     int32_t *status;
@@ -176,11 +189,23 @@ cudaError_t launch_oz_split(const double *src, int64_t rows, int64_t cols, int64
 cudaError_t launch_oz_split_f32(const float *src, int64_t rows, int64_t cols, int64_t ld, const SliceBuf &dst,
                                 int32_t *exps, cudaStream_t st);
 cudaError_t launch_gemm_oz(const SliceBuf &P, const int32_t *ep, const SliceBuf &Q, const int32_t *eq,
-                           OzParams prm, cudaStream_t st);
+                           OzParams prm, cudaStream_t st, int batch = 1);
 
 inline int slices_for(int precision) { return precision == PFSM_BF16_SPLIT ? 3 : 2; }
 inline int slice_kind(int precision) { return precision == PFSM_BF16_SPLIT ? 0 : 1; }
 inline int64_t padded_ld(int64_t n) { return (n + 63) / 64 * 64; }
+
+// blocked tridiagonalisation of the mixed forms (k_subeig.cu): panel width and the panel
+// kernel's dynamic shared memory (window rows for windows up to Mcap, or none)
+constexpr int kPanel = 32;
+inline size_t tri_panel_smem(int Mmax, int CL, int Mcap)
+{
+    size_t b = (size_t)(3 * Mmax + 64) * sizeof(double);                       // vbuf, pbuf, hv, red
+    b += 2 * (size_t)(kPanel + 2) * kPanel * sizeof(double);                    // panel rows of V, W
+    b += (size_t)(CL + 1 + 8) * 2 * kPanel * sizeof(double);                    // dots, ab, per-warp dots
+    if (Mcap > 0) b += (size_t)((Mcap + CL - 1) / CL) * Mcap * sizeof(double);
+    return b;
+}
 
 cudaError_t configure_dense_kernels();   // shared-memory attributes of k_dense.cu
 cudaError_t launch_gram_schmidt_f64(pfsm_handle_s *h, cudaStream_t st);

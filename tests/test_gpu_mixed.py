@@ -106,14 +106,15 @@ def test_mixed_solve_matches_oracle(pf, orc, name, prec, case):
 
 @pytest.mark.parametrize("name,prec", PRECISIONS)
 def test_mixed_without_iterations_matches_fp64(pf, name, prec):
-    """K = 0 leaves only the FP64 stages: start vectors, Gram-Schmidt and Rayleigh quotients, with
-    the overlap and Rayleigh products done by FP64-accurate tensor-core digits in the mixed forms."""
+    """K = 0 leaves only the FP64-accurate stages: the submatrix eigensolves (blocked reduction with
+    digit-product trailing updates in the mixed forms, unblocked in the FP64 form), Gram-Schmidt
+    and Rayleigh quotients. The two forms differ by rounding only: window eigenvectors by about
+    eps ||B|| / (smallest gap in a window), here ~1e-4 for 116 uniform eigenvalues."""
     p = wl.small_gapped(1)
     a = _solve(pf, p, precision=prec, fs_iters=0)
     b = _solve(pf, p, precision=pf.FP64, fs_iters=0)
-    np.testing.assert_array_equal(a[2], b[2])                  # identical start vectors
-    dl, dv = np.max(np.abs(a[0] - b[0])), np.max(np.abs(a[1] - b[1]))
-    print(f"K=0 {name}: |dlambda| = {dl:.2e}, |dV| = {dv:.2e}")
-    # digit products carry ~2^-46 of each row's largest entry per term: K 2^-46 ~ 4e-12 worst
-    # case for these unit-scale rows (K = 256), far below the FP64 bars (1e-10 ||A||, 1e-8)
-    assert dl < 1e-11 and dv < 1e-10
+    dx = np.max(np.abs(a[2] - b[2]))                            # start vectors
+    dl = np.max(np.abs(a[0] - b[0]))
+    pe = np.max(projector_errors(b[1], a[1], b[0]))
+    print(f"K=0 {name}: |dX0| = {dx:.2e}, |dlambda| = {dl:.2e}, projector = {pe:.2e}")
+    assert dx < 1e-9 and dl < 1e-11 and pe < 1e-8
