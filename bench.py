@@ -42,9 +42,15 @@ FP64_PEAK_SOURCE = ("unit counts: 148 SMs x 2 DFMA/clk x 2 flop x 2032 MHz; ncu 
 TF32_OVER_BF16 = 1.1 / 2.25       # nominal dense TF32 / BF16 tensor rate
 DTYPES = {"fp64": "f64", "bf16": "bf16x3-split, f32 accumulate, f64 epilogue",
           "tf32": "tf32x2-split, f32 accumulate, f64 epilogue"}
-# DRAM traffic (bytes) of one Eq. 11 product launch from an ncu capture of the current kernel
-# build on this workload, or None when the kernel changed since the capture (see profiles/).
-FS_GEMM_TRAFFIC = {}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, bytes per launch) from an ncu
+# capture of the current kernel build on this workload, keyed by (kernel, precision); absent
+# when the kernel changed since the capture. Captures and commands: profiles/.
+TRAFFIC = {
+    # the window reduction is the same kernel and launch in every form (profiles/dram_traffic_*)
+    ("k_tridiag", "bf16"): 5886208, ("k_tridiag", "tf32"): 5886208, ("k_tridiag", "fp64"): 5886208,
+    # Eq. 11 split products, mean over the K = 3 iterations' six launches
+    ("k_gemm_tc", "bf16"): (12921088 + 5 * 46013184) // 6,
+}
 
 
 def measured_peaks():
@@ -86,18 +92,54 @@ def algorithmic_flops(plan, n, K):
 
 
 class ClockSampler:
-    """nvidia-smi samples during the timed region (SM clock, max, throttle reasons)."""
+    """SM clock, maximum clock and throttle reasons sampled during the timed region: through NVML
+    every 10 ms when the nvidia-ml-py bindings import (the timed region can be a fraction of a
+    second), else through `nvidia-smi -lms 200`."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits (nvmlClocksEventReason*)
+    REASON_BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+                   "hw_thermal_slowdown": 0x40}
 
     def __init__(self, index: int):
         self.index = index
-        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-        self.p = None
+        self.rows, self.nvml, self.p, self.f, self.t, self.stop = [], None, None, None, None, False
+
+    def _nvml_handle(self):
+        import pynvml
+        import torch
+        pynvml.nvmlInit()
+        try:
+            pr = torch.cuda.get_device_properties(self.index)
+            bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+            return pynvml, pynvml.nvmlDeviceGetHandleByPciBusId(bus)
+        except Exception:
+            return pynvml, pynvml.nvmlDeviceGetHandleByIndex(self.index)
 
     def __enter__(self):
+        try:
+            import threading
+            nv, hd = self._nvml_handle()
+            self.nvml = (nv, hd)
+
+            def loop():
+                while not self.stop:
+                    try:
+                        sm = nv.nvmlDeviceGetClockInfo(hd, nv.NVML_CLOCK_SM)
+                        mx = nv.nvmlDeviceGetMaxClockInfo(hd, nv.NVML_CLOCK_SM)
+                        rs = nv.nvmlDeviceGetCurrentClocksEventReasons(hd)
+                        self.rows.append((float(sm), float(mx), int(rs)))
+                    except Exception:
+                        pass
+                    time.sleep(0.01)
+            self.t = threading.Thread(target=loop, daemon=True)
+            self.t.start()
+            return self
+        except Exception:
+            self.nvml = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
                                        "--format=csv,noheader,nounits", "-lms", "200"],
@@ -107,6 +149,9 @@ class ClockSampler:
         return self
 
     def __exit__(self, *exc):
+        if self.t:
+            self.stop = True
+            self.t.join(timeout=2)
         if self.p:
             self.p.terminate()
             try:
@@ -115,6 +160,12 @@ class ClockSampler:
                 self.p.kill()
 
     def summary(self):
+        if self.nvml:
+            if not self.rows:
+                return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0, "via": "nvml"}
+            reasons = sorted({n for _, _, rs in self.rows for n, bit in self.REASON_BITS.items() if rs & bit})
+            return {"sm_mhz": statistics.median(r[0] for r in self.rows), "sm_max_mhz": max(r[1] for r in self.rows),
+                    "reasons": reasons, "samples": len(self.rows), "via": "nvml, 10 ms"}
         self.f.flush()
         self.f.seek(0)
         rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
@@ -126,7 +177,7 @@ class ClockSampler:
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if "Active" in v and "Not" not in v})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "via": "nvidia-smi, 200 ms"}
 
 
 def oracle_rate(p, seconds: float):
@@ -307,29 +358,51 @@ def main():
             dist.destroy_process_group()
         return 0
 
-    # ---- roofline of the Eq. 11 product kernel ------------------------------------------------
+    # ---- rooflines: the dominant kernel, and the Eq. 11 product kernel ---------------------------
     ph = main_run["phases"]
-    fs_ms = ph["fs_iterations"]
-    fs_launches = 2 * p.fs_iters
-    achieved = fl["fs"] / (fs_ms / 1000.0) / 1e12 if fs_ms > 0 else None
-    if args.precision == "fp64":
-        peak, bound, kern = FP64_PEAK_TFLOPS, "alu", "k_gemm_f64 (FP64 DFMA, fused Eq. 11 epilogues)"
-        src = FP64_PEAK_SOURCE
-        products = 1
-    else:
-        peaks = measured_peaks()
-        bf16 = peaks.get("bf16_tflops") or 1800.0
-        peak = bf16 if args.precision == "bf16" else bf16 * TF32_OVER_BF16
-        bound, kern = "tensor", f"k_gemm_tc<{args.precision}> (tcgen05, split operands, fused FP64 epilogues)"
-        src = ("MEASURED_PEAKS.json bf16_tflops (burst)" if peaks.get("bf16_tflops") else "fallback 1.8 PFLOP/s bf16") + \
-              ("" if args.precision == "bf16" else " x nominal TF32/BF16 ratio 1.1/2.25")
-        products = 6 if args.precision == "bf16" else 3
-    roofline = {"kernel": kern, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": FS_GEMM_TRAFFIC.get(args.precision),
+    peaks = measured_peaks()
+
+    def gemm_roofline():
+        fs_ms = ph["fs_iterations"]
+        fs_launches = 2 * p.fs_iters
+        achieved = fl["fs"] / (fs_ms / 1000.0) / 1e12 if fs_ms > 0 else None
+        if args.precision == "fp64":
+            peak, bound, kern = FP64_PEAK_TFLOPS, "alu", "k_gemm_f64"
+            src, products = FP64_PEAK_SOURCE, 1
+        else:
+            bf16 = peaks.get("bf16_tflops") or 1800.0
+            peak = bf16 if args.precision == "bf16" else bf16 * TF32_OVER_BF16
+            bound, kern = "tensor", "k_gemm_tc"
+            src = ("MEASURED_PEAKS.json bf16_tflops (burst), of measured" if peaks.get("bf16_tflops")
+                   else "fallback 1.8 PFLOP/s bf16, of fallback") + \
+                  ("" if args.precision == "bf16" else " x nominal TF32/BF16 ratio 1.1/2.25")
+            products = 6 if args.precision == "bf16" else 3
+        return {"kernel": kern, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": TRAFFIC.get((kern, args.precision)),
                 "per_launch": {"flops": fl["fs"] / fs_launches, "ms": fs_ms / fs_launches},
+                "timing": "Eq. 11 phase (its product launches and two operand splits) / launches, CUDA events",
                 "flop_convention": "algorithmic (each N^3 term once); tensor-core work is "
                                    f"{products}x that in split products",
-                "peak_source": src}
+                "peak_source": src, "total_ms": fs_ms}
+
+    def tridiag_roofline():
+        # one launch reduces every window: algorithmic sum_b 4/3 M_b^3 (FP64 DFMA pipe)
+        tri_ms = ph["tridiag"]
+        M = plan[3].astype(float)
+        flops = float(sum(4.0 / 3.0 * Mb ** 3 for Mb in M))
+        achieved = flops / (tri_ms / 1000.0) / 1e12 if tri_ms > 0 else None
+        return {"kernel": "k_tridiag", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+                "traffic": TRAFFIC.get(("k_tridiag", args.precision)),
+                "per_launch": {"flops": flops, "ms": tri_ms},
+                "timing": "CUDA events on the solve stream around the single launch",
+                "flop_convention": "algorithmic Householder reduction, 4/3 M^3 per window",
+                "peak_source": FP64_PEAK_SOURCE, "total_ms": tri_ms}
+
+    cands = [tridiag_roofline(), gemm_roofline()]
+    cands.sort(key=lambda r: -r["total_ms"])
+    roofline, other = cands[0], cands[1:]
 
     out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -340,6 +413,7 @@ def main():
            "fp64_solves_per_s": fp64_run["value"],
            "speedup_vs_fp64": value / fp64_run["value"],
            "phases_ms": ph, "fp64_phases_ms": fp64_run["phases"], "roofline": roofline,
+           "roofline_other": other,
            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h},
            "gpu_launches": main_run["launches"], "clocks": main_run["clocks"]}

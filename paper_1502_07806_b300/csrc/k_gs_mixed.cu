@@ -391,8 +391,10 @@ cudaError_t launch_gram_schmidt_mixed(pfsm_handle_s *h, cudaStream_t st)
     if ((e = launch_gemm_tc(sY, sZ, t, nullptr, st)) != cudaSuccess) return e;
     if ((e = launch_oz_split(w.F, N, N, N, dP, w.ozeP, st)) != cudaSuccess) return e;
     if ((e = launch_oz_split(w.W, N, N, N, dQ, w.ozeQ, st)) != cudaSuccess) return e;
+    // F is of order |E| (1e-7 here), so F W needs about 1e-9 of its own size: seven digit levels
+    // (about sqrt(N) 2^-37 / 3 of 2^(e_r + e_c), e_r the exponent of F's row)
     o = OzParams{};
-    o.rows = (int)N; o.cols = (int)N; o.C = w.Y; o.ldc = N; o.sub = 1; o.p_lower = 1; o.status = w.status;
+    o.rows = (int)N; o.cols = (int)N; o.C = w.Y; o.ldc = N; o.sub = 1; o.p_lower = 1; o.levels = 7; o.status = w.status;
     if ((e = launch_gemm_oz(dP, w.ozeP, dQ, w.ozeQ, o, st)) != cudaSuccess) return e;
     // the orthonormal vectors now live in Y: swap the buffers so X holds V
     double *tmp = w.X;
