@@ -94,7 +94,7 @@ def algorithmic_flops(plan, n, K):
 class ClockSampler:
     """SM clock, maximum clock and throttle reasons sampled during the timed region: through NVML
     every 10 ms when the nvidia-ml-py bindings import (the timed region can be a fraction of a
-    second), else through `nvidia-smi -lms 200`."""
+    second), else through `nvidia-smi -lms 50`."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -142,7 +142,7 @@ class ClockSampler:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -177,7 +177,7 @@ class ClockSampler:
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if "Active" in v and "Not" not in v})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows), "via": "nvidia-smi, 200 ms"}
+                "reasons": reasons, "samples": len(rows), "via": "nvidia-smi, 50 ms"}
 
 
 def oracle_rate(p, seconds: float):

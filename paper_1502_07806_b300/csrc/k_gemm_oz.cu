@@ -1,6 +1,6 @@
 // FP64-accurate products on the BF16 tensor cores (tcgen05 + TMEM, TMA-fed): the error-free
 // splitting of Ozaki, Ogita, Oishi and Rump (2012), arranged for B300, where the DFMA pipe gives
-// 1.2 TFLOP/s and the BF16 tensor cores about 1.8 PFLOP/s.
+// 1.2 TFLOP/s and the BF16 tensor cores about 1.75 PFLOP/s.
 //
 // Splitting (k_oz_split): every row r of an operand is scaled by its own power of two 2^-e_r so
 // that |x| < 1, rounded to a 45-bit fixed-point integer q, and q is cut into S = 9 balanced base-32
@@ -14,25 +14,30 @@
 // sqrt(K (pairs at L)) 2^(8 - 5(L+2)) / 3 relative to 2^(e_r + e_c). Stopping after L = 8 would
 // leave sqrt(K) 2^-46 (1e-12 at K = 9072); stopping after L = 10 leaves about 1e-15 there, below
 // the 2^-46 rounding of the operands themselves. Products that only need FP32-class accuracy
-// ask for fewer levels (about sqrt(K) 2^(3 - 5(levels+1)) / 3). Each (level, K chunk) group is
-// drained from TMEM into FP64 registers with its exact power-of-two scale while the tensor cores
-// fill the other of two TMEM buffers.
+// ask for fewer levels (about sqrt(K) 2^(3 - 5(levels+1)) / 3).
 //
-// CTA: 192 threads, a 128 x 64 output tile. Warp 0: TMA loads of digit tiles (6-stage ring).
-// Warp 1: TMEM owner and MMA issuer (M = 128, N = 64, K = 16). Warps 2-5: drain TMEM (one row each
-// thread, 64 FP64 accumulators), then apply the epilogue, which can add an exact FP64 diagonal
-// term C[r, c] += V[r, c] d[c] (for products with A = diag(d) + E whose digits cover E only, so
-// that the error scales with the small off-diagonal part). All mbarrier waits are bounded.
+// CTA: 192 threads, a 128 x 32 output tile. All levels accumulate at once, each in its own
+// 32-column FP32 accumulator in tensor memory (11 x 32 of the 512 columns), so one pipeline stage
+// holds every digit slice of P and of Q for one 32-element (64-byte, 64-byte-swizzled) K block,
+// 90 KB loaded by two TMA copies, and feeds all 60 slice-pair products (120 MMAs of 128x32x16):
+// each slice tile is read from L2 once per K block instead of once per pair. Warp 0: TMA (2
+// stages). Warp 1: TMEM owner and MMA issuer. Warps 2-5: at the end of each exact K chunk, drain
+// the level sums (one row per thread) into float-float registers with exact power-of-two scales;
+// finally one FP64 conversion per entry and row-contiguous stores through shared memory. The
+// epilogue can add an exact FP64 diagonal term C[r, c] += V[r, c] d[c] (for products with
+// A = diag(d) + E whose digits cover E only). All mbarrier waits are bounded.
 #include "tc_common.cuh"
 
 namespace pfsm {
 
 namespace oz {
 
-constexpr int BM = 128, BN = 64, STAGES = 6;
-constexpr int A_BYTES = BM * 128, B_BYTES = BN * 128, STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr uint32_t TMEM_COLS = 128;          // two 64-column FP32 accumulators
-constexpr int KCHUNK = 1792;                 // K terms per exact group: 1792 * 9 <= 16384
+constexpr int BM = 128, BN = 32, KB = 32;         // tile, K block (32 BF16 = 64 bytes)
+constexpr int P_TILE = BM * 64, Q_TILE = BN * 64;  // bytes per slice per K block
+constexpr int STAGES = 2;
+constexpr int MAX_STAGE_BYTES = OZ_SLICES * (P_TILE + Q_TILE);
+constexpr uint32_t TMEM_COLS = 512;               // level L at columns 32 L
+constexpr int KCHUNK = 1792;                      // K terms per exact level sum
 constexpr int BETA = 5;
 
 }  // namespace oz
@@ -92,40 +97,38 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
     if (prm.lower_only && col0 > row0 + BM - 1) return;           // whole tile above the diagonal
     const int64_t zr = (int64_t)z * prm.zrow;                      // operand row offset
     double *Cz = prm.C + (int64_t)z * prm.zc;
+    const int S = OZ_SLICES;
+    const int LV = (prm.levels > 0 && prm.levels < OZ_LEVELS) ? prm.levels : OZ_LEVELS;   // levels 0 .. LV-1
+    const int NSL = LV < S ? LV : S;                               // slices that take part
+    const int stage_bytes = NSL * (P_TILE + Q_TILE);
     extern __shared__ __align__(1024) uint8_t smraw[];
     const uint32_t raw = smem_u32(smraw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *gbase = smraw + (base - raw);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + STAGES * STAGE_BYTES);
-    // bars: [0,S) full, [S,2S) empty, [2S,2S+2) accumulator full, [2S+2,2S+4) accumulator empty
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 4);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + STAGES * MAX_STAGE_BYTES);
+    // bars: [0,2) full, [2,4) empty, 4 chunk summed, 5 chunk drained, 6 all MMAs done
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 3);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     int *ecol = reinterpret_cast<int *>(tmem_slot + 2);           // BN column exponents
-    double *estage = reinterpret_cast<double *>(gbase + STAGES * STAGE_BYTES + 1024);   // 128 x (BN + 1)
     const uint32_t bar_base = smem_u32(bars);
     auto full_bar = [&](int s) { return bar_base + 8u * s; };
     auto empty_bar = [&](int s) { return bar_base + 8u * (STAGES + s); };
-    auto accf_bar = [&](int b) { return bar_base + 8u * (2 * STAGES + b); };
-    auto acce_bar = [&](int b) { return bar_base + 8u * (2 * STAGES + 2 + b); };
+    const uint32_t accf_bar = bar_base + 8u * (2 * STAGES), acce_bar = accf_bar + 8u, done_bar = accf_bar + 16u;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    // 64-element K blocks; a lower-triangular P has no entries beyond column row0 + BM - 1
-    const int nkb_total = prm.p_lower ? min(prm.kblocks, (row0 + BM + 63) / 64) : prm.kblocks;
-    const int kb_per_chunk = KCHUNK / 64;
-    const int nch = (nkb_total + kb_per_chunk - 1) / kb_per_chunk;
-    const int S = OZ_SLICES;
-    const int LV = (prm.levels > 0 && prm.levels < 2 * S - 1) ? prm.levels : OZ_LEVELS;   // levels 0 .. LV-1
-    const int groups = LV * nch;
+    // 32-element K blocks; a lower-triangular P has no entries beyond column row0 + BM - 1
+    const int nkb = prm.p_lower ? min(prm.kblocks, (row0 + BM + KB - 1) / KB) : prm.kblocks;
+    const int kb_per_chunk = KCHUNK / KB;
+    const int nch = (nkb + kb_per_chunk - 1) / kb_per_chunk;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) {
             mbar_init(full_bar(s), 1);
             mbar_init(empty_bar(s), 1);
         }
-        for (int b = 0; b < 2; b++) {
-            mbar_init(accf_bar(b), 1);
-            mbar_init(acce_bar(b), 128);
-        }
+        mbar_init(accf_bar, 1);
+        mbar_init(acce_bar, 128);
+        mbar_init(done_bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapP) : "memory");
@@ -142,32 +145,24 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
     __syncthreads();
     fence_after();
     const uint32_t tmem_acc = *tmem_slot;
+    auto stageP = [&](int s, int sl) { return base + s * MAX_STAGE_BYTES + sl * P_TILE; };
+    auto stageQ = [&](int s, int sl) { return base + s * MAX_STAGE_BYTES + NSL * P_TILE + sl * Q_TILE; };
 
     if (warp == 0) {
         if (lane == 0) {
-            int it = 0, issued = 0;
-            bool stop = false;
-            for (int g = 0; g < groups && !stop; g++) {
-                const int L = g / nch, ch = g % nch;
-                const int kbA = ch * kb_per_chunk, kbB = min(nkb_total, kbA + kb_per_chunk);
-                for (int sa = (L >= S ? L - S + 1 : 0); sa <= L && sa < S && !stop; sa++) {
-                    const int sb = L - sa;
-                    for (int kb = kbA; kb < kbB; kb++, it++) {
-                        const int s = it % STAGES, round = it / STAGES;
-                        if (round > 0 && !mbar_wait(empty_bar(s), (round - 1) & 1)) {
-                            set_status(prm.status, PFSM_ERR_TIMEOUT);
-                            *abort_flag = 1;
-                            stop = true;
-                            break;
-                        }
-                        if (*abort_flag) { stop = true; break; }
-                        const uint32_t a = base + s * STAGE_BYTES, b = a + A_BYTES;
-                        mbar_expect_tx(full_bar(s), STAGE_BYTES);
-                        tma_load_3d(a, &mapP, full_bar(s), kb * 64, (int)(zr + row0), sa);
-                        tma_load_3d(b, &mapQ, full_bar(s), kb * 64, (int)(zr + col0), sb);
-                        issued = it + 1;
-                    }
+            int issued = 0;
+            for (int kb = 0; kb < nkb; kb++) {
+                const int s = kb % STAGES, round = kb / STAGES;
+                if (round > 0 && !mbar_wait(empty_bar(s), (round - 1) & 1)) {
+                    set_status(prm.status, PFSM_ERR_TIMEOUT);
+                    *abort_flag = 1;
+                    break;
                 }
+                if (*abort_flag) break;
+                mbar_expect_tx(full_bar(s), stage_bytes);
+                tma_load_3d(stageP(s, 0), &mapP, full_bar(s), kb * KB, (int)(zr + row0), 0);
+                tma_load_3d(stageQ(s, 0), &mapQ, full_bar(s), kb * KB, (int)(zr + col0), 0);
+                issued = kb + 1;
             }
             for (int i = (issued > STAGES ? issued - STAGES : 0); i < issued; i++)
                 mbar_wait(full_bar(i % STAGES), (i / STAGES) & 1);
@@ -175,54 +170,47 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {
-            int it = 0;
             bool ok = true;
-            for (int g = 0; g < groups && ok; g++) {
-                const int L = g / nch, ch = g % nch, buf = g & 1;
-                if (g >= 2 && !mbar_wait(acce_bar(buf), ((g >> 1) - 1) & 1)) { ok = false; break; }
+            for (int ch = 0; ch < nch && ok; ch++) {
+                if (ch > 0 && !mbar_wait(acce_bar, (ch - 1) & 1)) { ok = false; break; }   // drained
                 fence_after();
-                const uint32_t dacc = tmem_acc + 64u * buf;
-                const int kbA = ch * kb_per_chunk, kbB = min(nkb_total, kbA + kb_per_chunk);
-                bool first = true;
-                for (int sa = (L >= S ? L - S + 1 : 0); sa <= L && sa < S && ok; sa++) {
-                    for (int kb = kbA; kb < kbB; kb++, it++) {
-                        const int s = it % STAGES;
-                        if (!mbar_wait(full_bar(s), (it / STAGES) & 1) || *abort_flag) { ok = false; break; }
-                        fence_after();
-                        const uint32_t a = base + s * STAGE_BYTES, b = a + A_BYTES;
-                        const uint64_t da = sw128_desc(a), db = sw128_desc(b);
-#pragma unroll
-                        for (int kk = 0; kk < 4; kk++) {
-                            umma<0, BM, BN>(dacc, da + 2 * kk, db + 2 * kk, first ? 0u : 1u);
-                            first = false;
+                const int kbA = ch * kb_per_chunk, kbB = min(nkb, kbA + kb_per_chunk);
+                for (int kb = kbA; kb < kbB && ok; kb++) {
+                    const int s = kb % STAGES;
+                    if (!mbar_wait(full_bar(s), (kb / STAGES) & 1) || *abort_flag) { ok = false; break; }
+                    fence_after();
+                    for (int L = 0; L < LV; L++) {
+                        const int sa0 = L >= S ? L - S + 1 : 0, sa1 = L < S ? L : S - 1;
+                        const uint32_t dacc = tmem_acc + 32u * L;
+                        for (int sa = sa0; sa <= sa1; sa++) {
+                            const uint64_t da = sw64_desc(stageP(s, sa)), db = sw64_desc(stageQ(s, L - sa));
+                            umma<0, BM, BN>(dacc, da, db, (kb == kbA && sa == sa0) ? 0u : 1u);
+                            umma<0, BM, BN>(dacc, da + 2, db + 2, 1u);   // second 16 of the 32 K
                         }
-                        umma_commit(empty_bar(s));
                     }
+                    umma_commit(empty_bar(s));
                 }
-                umma_commit(accf_bar(buf));   // this group's sum is complete when its MMAs are
+                umma_commit(accf_bar);      // this chunk's level sums are complete with its MMAs
             }
             if (!ok) {
                 set_status(prm.status, PFSM_ERR_TIMEOUT);
                 *abort_flag = 1;
-                umma_commit(accf_bar(0));
-                mbar_wait(accf_bar(0), 0);    // fences the MMAs issued so far (bounded)
             }
+            umma_commit(done_bar);          // tracks every MMA issued before TMEM is released
+            mbar_wait(done_bar, 0);
         }
         __syncwarp();
     } else {
         const int gq = warp & 3;
         const int r = row0 + 32 * gq + lane;
-        // the levels are combined in float-float (hi + lo, about 48 bits) with Knuth's TwoSum: each
-        // level sum is an exact FP32 integer and its scale an exact power of two, so a level costs
-        // a few FP32 operations per entry instead of two FP64 ones (the FP64 pipe is 64 times
-        // slower); one FP64 conversion per entry at the end
+        // float-float (hi + lo, ~48 bits) with Knuth's TwoSum: each level sum is an exact FP32
+        // integer and its scale an exact power of two, so a level costs a few FP32 operations
         float hi[BN], lo[BN];
 #pragma unroll
         for (int j = 0; j < BN; j++) { hi[j] = 0.0f; lo[j] = 0.0f; }
         bool ok = true;
-        for (int g = 0; g < groups; g++) {
-            const int L = g / nch, buf = g & 1;
-            bool got = mbar_wait(accf_bar(buf), (g >> 1) & 1);
+        for (int ch = 0; ch < nch; ch++) {
+            bool got = mbar_wait(accf_bar, ch & 1);
             got = __all_sync(0xffffffffu, got) && !*abort_flag;
             if (!got) {
                 ok = false;
@@ -231,45 +219,41 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
                 break;
             }
             fence_after();
-            const float scale = __int_as_float((127 - oz::BETA * (L + 2)) << 23);   // 2^-5(L+2)
-            uint32_t v[32];
-#pragma unroll
-            for (int half = 0; half < 2; half++) {
-                tmem_ld32(tmem_acc + ((uint32_t)(32 * gq) << 16) + 64u * buf + 32 * half, v);
+            for (int L = 0; L < LV; L++) {
+                const float scale = __int_as_float((127 - BETA * (L + 2)) << 23);   // 2^-5(L+2)
+                uint32_t v[32];
+                tmem_ld32(tmem_acc + ((uint32_t)(32 * gq) << 16) + 32u * L, v);
 #pragma unroll
                 for (int j = 0; j < 32; j++) {
                     const float x = __uint_as_float(v[j]) * scale;
-                    const float h = hi[32 * half + j];
-                    const float sum = h + x, bp = sum - h;
-                    lo[32 * half + j] += (h - (sum - bp)) + (x - bp);
-                    hi[32 * half + j] = sum;
+                    const float sum = hi[j] + x, bp = sum - hi[j];
+                    lo[j] += (hi[j] - (sum - bp)) + (x - bp);
+                    hi[j] = sum;
                 }
             }
             fence_before();
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce_bar(buf)) : "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce_bar) : "memory");
         }
-        // epilogue through this warp's shared-memory staging block (32 rows x 64 columns), so
-        // that the loads and stores of C (and of the exact diagonal term) are row-contiguous
-        double(*eb)[BN + 1] = reinterpret_cast<double(*)[BN + 1]>(estage) + 32 * gq;
+        // every MMA has completed (last chunk waited) and every stage consumed: the stage
+        // memory now holds this warp's staging block (32 rows x 32 columns), so that the loads and
+        // stores of C (and of the exact diagonal term) are row-contiguous
+        double(*eb)[BN + 1] = reinterpret_cast<double(*)[BN + 1]>(gbase) + 32 * gq;
         const int R0 = row0 + 32 * gq;
         const int er = (ok && r < rows_lim) ? prm.ep[zr + r] : 0;
 #pragma unroll
         for (int j = 0; j < BN; j++) eb[lane][j] = ldexp((double)hi[j] + (double)lo[j], er + ecol[j]);
         __syncwarp();
         if (ok) {
+            const int c = col0 + lane;
             for (int rr = 0; rr < 32; rr++) {
                 const int gr = R0 + rr;
                 if (gr >= rows_lim) break;
-#pragma unroll
-                for (int h = 0; h < BN / 32; h++) {
-                    const int c = col0 + 32 * h + lane;
-                    if (c < cols_lim && !(prm.lower_only && c > gr)) {
-                        double res = eb[rr][32 * h + lane];
-                        if (prm.dcol) res = fma(prm.Vp[(int64_t)gr * prm.ldv + c], prm.dcol[c], res);
-                        const int64_t o = (int64_t)gr * prm.ldc + c;
-                        if (prm.sub) Cz[o] -= res;
-                        else Cz[o] = res;
-                    }
+                if (c < cols_lim && !(prm.lower_only && c > gr)) {
+                    double res = eb[rr][lane];
+                    if (prm.dcol) res = fma(prm.Vp[(int64_t)gr * prm.ldv + c], prm.dcol[c], res);
+                    const int64_t o = (int64_t)gr * prm.ldc + c;
+                    if (prm.sub) Cz[o] -= res;
+                    else Cz[o] = res;
                 }
             }
         }
@@ -285,7 +269,7 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
 // ---- host side -------------------------------------------------------------------------------
 
 namespace {
-size_t oz_smem_bytes() { return (size_t)oz::STAGES * oz::STAGE_BYTES + 1024 + 1024 + (size_t)128 * (oz::BN + 1) * 8; }
+size_t oz_smem_bytes() { return (size_t)oz::STAGES * oz::MAX_STAGE_BYTES + 1024 + 512; }
 }
 
 cudaError_t configure_oz_kernels()
@@ -318,9 +302,13 @@ cudaError_t launch_gemm_oz(const SliceBuf &P, const int32_t *ep, const SliceBuf 
 {
     CUtensorMap mp, mq;
     cudaError_t e;
-    if ((e = make_slice_map(&mp, P, oz::BM)) != cudaSuccess) return e;
-    if ((e = make_slice_map(&mq, Q, oz::BN)) != cudaSuccess) return e;
-    prm.kblocks = (int)(P.ld / 64);
+    const int lv = (prm.levels > 0 && prm.levels < OZ_LEVELS) ? prm.levels : OZ_LEVELS;
+    const int nsl = lv < OZ_SLICES ? lv : OZ_SLICES;
+    if (P.ns != OZ_SLICES || Q.ns != OZ_SLICES || P.kind != 0 || Q.kind != 0 || P.ld != Q.ld || P.ld % oz::KB)
+        return cudaErrorInvalidValue;
+    if ((e = make_slice_map64(&mp, P, oz::BM, nsl)) != cudaSuccess) return e;
+    if ((e = make_slice_map64(&mq, Q, oz::BN, nsl)) != cudaSuccess) return e;
+    prm.kblocks = (int)(P.ld / oz::KB);
     prm.ep = ep;
     prm.eq = eq;
     // batched: prm.rows / prm.cols give the grid extent from row_base (the largest window)

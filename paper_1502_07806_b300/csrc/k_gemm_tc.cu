@@ -415,6 +415,21 @@ cudaError_t make_slice_map(CUtensorMap *map, const SliceBuf &b, int box_rows)
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+cudaError_t make_slice_map64(CUtensorMap *map, const SliceBuf &b, int box_rows, int box_slices)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    const int esz = b.kind == 0 ? 2 : 4;
+    cuuint64_t dims[3] = {(cuuint64_t)b.ld, (cuuint64_t)b.rows, (cuuint64_t)b.ns};
+    cuuint64_t strides[2] = {(cuuint64_t)b.ld * esz, (cuuint64_t)b.ld * b.rows * esz};
+    cuuint32_t box[3] = {(cuuint32_t)(64 / esz), (cuuint32_t)box_rows, (cuuint32_t)box_slices};
+    cuuint32_t estr[3] = {1u, 1u, 1u};
+    CUresult r = fn(map, b.kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                    b.ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 namespace {
 
 template <int KIND>

@@ -78,6 +78,18 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
     return d;
 }
 
+// The same for 64-byte K rows with 64-byte swizzle (layout type 4): 8-row groups 512 B apart.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                 // leading byte offset (unused for this layout)
+    d |= (uint64_t)(512 >> 4) << 32;        // stride byte offset
+    d |= (uint64_t)1 << 46;                 // version
+    d |= (uint64_t)4 << 61;                 // SWIZZLE_64B
+    return d;
+}
+
 // Instruction descriptor: FP32 accumulator, A/B element format (BF16 = 1, TF32 = 2), both
 // operands K-major, N (bits 17-22 hold N/8), M (bits 24-28 hold M/16).
 template <int KIND, int M_, int N_>
@@ -168,5 +180,7 @@ __device__ __forceinline__ void store_slices_f32(void *base, int64_t sstride, in
 
 // 3-D TMA map over row-major slices: {ld (K), rows, ns}, box {128 bytes of K, box_rows, 1}.
 cudaError_t make_slice_map(CUtensorMap *map, const SliceBuf &b, int box_rows);
+// The same with 64-byte K rows, 64-byte swizzle and `box_slices` slices per copy.
+cudaError_t make_slice_map64(CUtensorMap *map, const SliceBuf &b, int box_rows, int box_slices);
 
 }  // namespace pfsm
