@@ -49,122 +49,6 @@ __device__ __forceinline__ double block_sum(double v, double *red)
 
 // Grid: nb * CL CTAs, clusters of CL along x. Rows of window b are owned cyclically: CTA `rank`
 // owns rows i with i % CL == rank.
-template <bool SMEM_ROWS>
-__global__ void __launch_bounds__(kTriThreads)
-k_tridiag(const double *__restrict__ A, int64_t N, const int32_t *__restrict__ plan, int32_t nb,
-          int32_t Mmax, double *__restrict__ gwork, double *__restrict__ refl,
-          double *__restrict__ tau, double *__restrict__ td, double *__restrict__ te)
-{
-    cg::cluster_group cluster = cg::this_cluster();
-    const int CL = (int)cluster.num_blocks();
-    const int rank = (int)cluster.block_rank();
-    const int b = blockIdx.x / CL;
-    const int64_t s0 = plan[2 * nb + b];
-    const int M = plan[3 * nb + b];
-    const int R = (Mmax + CL - 1) / CL;
-    extern __shared__ double sm[];
-    double *rows = SMEM_ROWS ? sm : (gwork + (size_t)b * Mmax * Mmax);
-    double *vbuf = sm + (SMEM_ROWS ? (size_t)R * Mmax : 0);
-    double *pbuf = vbuf + Mmax;
-    double *hv = pbuf + Mmax;
-    double *wv = hv + Mmax;
-    double *red = wv + Mmax;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    auto rowp = [&](int i) -> double * {
-        return SMEM_ROWS ? rows + (size_t)(i / CL) * Mmax : rows + (size_t)i * Mmax;
-    };
-    double *brefl = refl + (size_t)b * Mmax * Mmax;
-    double *btau = tau + (size_t)b * Mmax, *btd = td + (size_t)b * Mmax, *bte = te + (size_t)b * Mmax;
-
-    // load owned rows of B = A[s0:s0+M, s0:s0+M]
-    for (int i = rank + warp * CL; i < M; i += nwarps * CL) {
-        const double *src = A + (s0 + i) * N + s0;
-        double *dst = rowp(i);
-        for (int j = lane; j < M; j += 32) dst[j] = src[j];
-    }
-    // every CTA of the cluster must be running before any distributed-shared-memory access
-    cluster.sync();
-    // broadcast column 0 (rows >= 1) into every CTA's vbuf
-    for (int i = rank + threadIdx.x * CL; i < M; i += blockDim.x * CL) {
-        if (i < 1) continue;
-        double v = rowp(i)[0];
-        for (int r = 0; r < CL; r++) cluster.map_shared_rank(vbuf, r)[i] = v;
-    }
-    cluster.sync();
-
-    for (int k = 0; k + 2 < M; k++) {
-        // (a) Householder vector of column k, computed redundantly and identically in every CTA
-        double x0 = vbuf[k + 1];
-        double t2 = 0.0;
-        for (int i = k + 2 + threadIdx.x; i < M; i += blockDim.x) t2 += vbuf[i] * vbuf[i];
-        double tail2 = block_sum(t2, red);
-        double beta = 0.0, alpha = x0;
-        if (tail2 != 0.0) {
-            double xn = sqrt(x0 * x0 + tail2);
-            alpha = (x0 >= 0.0) ? -xn : xn;
-            double v0 = x0 - alpha;
-            beta = 2.0 / (v0 * v0 + tail2);
-            for (int i = k + 1 + threadIdx.x; i < M; i += blockDim.x) hv[i] = (i == k + 1) ? v0 : vbuf[i];
-        }
-        if (rank == 0) {
-            if (threadIdx.x == 0) { bte[k] = alpha; btau[k] = beta; }
-            double *rr = brefl + (size_t)k * Mmax;
-            for (int i = k + 1 + threadIdx.x; i < M; i += blockDim.x)
-                rr[i] = (beta != 0.0) ? ((i == k + 1) ? x0 - alpha : vbuf[i]) : 0.0;
-        }
-        if (k % CL == rank && threadIdx.x == 0) btd[k] = rowp(k)[k];
-        __syncthreads();
-        // (b) p_i = beta * B22[i, :] . v for owned rows i > k, broadcast to the cluster
-        if (beta != 0.0) {
-            int first = k + 1 + ((rank - (k + 1)) % CL + CL) % CL;   // first owned row > k
-            for (int i = first + warp * CL; i < M; i += nwarps * CL) {
-                const double *ri = rowp(i);
-                double acc = 0.0;
-                for (int j = k + 1 + lane; j < M; j += 32) acc += ri[j] * hv[j];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                if (lane < CL) cluster.map_shared_rank(pbuf, lane)[i] = beta * acc;
-            }
-        }
-        cluster.sync();
-        if (beta != 0.0) {
-            // (c) w = p - (beta p.v / 2) v ; B22 -= v w^T + w v^T on owned rows
-            double pv = 0.0;
-            for (int i = k + 1 + threadIdx.x; i < M; i += blockDim.x) pv += pbuf[i] * hv[i];
-            double Kc = 0.5 * beta * block_sum(pv, red);
-            for (int i = k + 1 + threadIdx.x; i < M; i += blockDim.x) wv[i] = pbuf[i] - Kc * hv[i];
-            __syncthreads();
-            int first = k + 1 + ((rank - (k + 1)) % CL + CL) % CL;
-            for (int i = first + warp * CL; i < M; i += nwarps * CL) {
-                double *ri = rowp(i);
-                const double hi = hv[i], wi = wv[i];
-                for (int j = k + 1 + lane; j < M; j += 32) ri[j] = fma(-hi, wv[j], fma(-wi, hv[j], ri[j]));
-            }
-            __syncthreads();
-        }
-        // (d) broadcast column k+1 (rows >= k+2) for the next step
-        {
-            int first = k + 2 + ((rank - (k + 2)) % CL + CL) % CL;
-            for (int i = first + threadIdx.x * CL; i < M; i += blockDim.x * CL) {
-                double v = rowp(i)[k + 1];
-                for (int r = 0; r < CL; r++) cluster.map_shared_rank(vbuf, r)[i] = v;
-            }
-        }
-        cluster.sync();
-    }
-    // trailing 2x2 (or 1x1)
-    if (threadIdx.x == 0) {
-        if (M >= 2) {
-            if ((M - 2) % CL == rank) btd[M - 2] = rowp(M - 2)[M - 2];
-            if ((M - 1) % CL == rank) { btd[M - 1] = rowp(M - 1)[M - 1]; bte[M - 2] = rowp(M - 1)[M - 2]; }
-        } else if (rank == 0) {
-            btd[0] = rowp(0)[0];
-        }
-        if (rank == 0) { bte[M - 1] = 0.0; if (M >= 2) btau[M - 2] = 0.0; btau[M - 1] = 0.0; }
-    }
-    cluster.sync();   // keep every CTA's shared memory alive until remote writes are done
-}
-
 // 1/p and 1/sqrt(d) for d, p > 0 of any FP64 magnitude without the IEEE FP64 divide / square
 // root sequences (each ~10 dependent FP64 instructions of ~64 cycles on B300): the exponent is
 // split off (so the FP32 seed never under- or overflows), then an FP32 estimate and two Newton
@@ -188,6 +72,153 @@ __device__ __forceinline__ double scaled_rsqrt(double d)
     y = y * fma(-0.5 * m, y * y, 1.5);
     y = y * fma(-0.5 * m, y * y, 1.5);
     return ldexp(y, -e / 2);
+}
+
+// B300 spends ~64 cycles of a sub-partition's FP64 pipe on EVERY FP64 warp instruction, so the
+// loop is arranged to issue few of them: the Householder scalars and p.v are computed by one warp
+// (not by all eight) and broadcast through shared memory, and the mat-vec runs four threads per
+// row (two shuffle rounds per row instead of five), leaving the rank-2 update (two DFMA per entry,
+// lanes along the row) as the bulk. Rows in shared memory are padded to Mmax + 2 doubles so the
+// eight rows a warp reads in the mat-vec fall in different banks.
+template <bool SMEM_ROWS>
+__global__ void __launch_bounds__(kTriThreads)
+k_tridiag(const double *__restrict__ A, int64_t N, const int32_t *__restrict__ plan, int32_t nb,
+          int32_t Mmax, double *__restrict__ gwork, double *__restrict__ refl,
+          double *__restrict__ tau, double *__restrict__ td, double *__restrict__ te)
+{
+    cg::cluster_group cluster = cg::this_cluster();
+    const int CL = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int b = blockIdx.x / CL;
+    const int64_t s0 = plan[2 * nb + b];
+    const int M = plan[3 * nb + b];
+    const int R = (Mmax + CL - 1) / CL;
+    const int ld = SMEM_ROWS ? Mmax + 2 : Mmax;
+    extern __shared__ double sm[];
+    double *rows = SMEM_ROWS ? sm : (gwork + (size_t)b * Mmax * Mmax);
+    double *vbuf = sm + (SMEM_ROWS ? (size_t)R * ld : 0);
+    double *pbuf = vbuf + Mmax;
+    double *hv = pbuf + Mmax;
+    double *wv = hv + Mmax;
+    double *sc = wv + Mmax;                            // broadcast scalars (64)
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    auto rowp = [&](int i) -> double * {
+        return SMEM_ROWS ? rows + (size_t)(i / CL) * ld : rows + (size_t)i * Mmax;
+    };
+    double *brefl = refl + (size_t)b * Mmax * Mmax;
+    double *btau = tau + (size_t)b * Mmax, *btd = td + (size_t)b * Mmax, *bte = te + (size_t)b * Mmax;
+
+    // load owned rows of B = A[s0:s0+M, s0:s0+M]
+    for (int i = rank + warp * CL; i < M; i += nwarps * CL) {
+        const double *src = A + (s0 + i) * N + s0;
+        double *dst = rowp(i);
+        for (int j = lane; j < M; j += 32) dst[j] = src[j];
+    }
+    // every CTA of the cluster must be running before any distributed-shared-memory access
+    cluster.sync();
+    // broadcast column 0 (rows >= 1) into every CTA's vbuf
+    for (int i = rank + tid * CL; i < M; i += blockDim.x * CL) {
+        if (i < 1) continue;
+        double v = rowp(i)[0];
+        for (int r = 0; r < CL; r++) cluster.map_shared_rank(vbuf, r)[i] = v;
+    }
+    cluster.sync();
+
+    for (int k = 0; k + 2 < M; k++) {
+        // (a) Householder vector of column k: scalars by warp 0 (identical in every CTA)
+        if (warp == 0) {
+            const double x0 = vbuf[k + 1];
+            double t2 = 0.0;
+            for (int i = k + 2 + lane; i < M; i += 32) t2 = fma(vbuf[i], vbuf[i], t2);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+            double beta = 0.0, alpha = x0, v0 = 0.0;
+            if (t2 != 0.0) {
+                const double nn = fma(x0, x0, t2);
+                const double xn = nn * scaled_rsqrt(nn);
+                alpha = (x0 >= 0.0) ? -xn : xn;
+                v0 = x0 - alpha;
+                beta = 2.0 * scaled_rcp(fma(v0, v0, t2));
+            }
+            if (lane == 0) { sc[0] = beta; sc[1] = alpha; sc[2] = v0; }
+        }
+        __syncthreads();
+        const double beta = sc[0], alpha = sc[1], v0 = sc[2];
+        for (int i = k + 1 + tid; i < M; i += blockDim.x) hv[i] = (beta != 0.0) ? ((i == k + 1) ? v0 : vbuf[i]) : 0.0;
+        if (rank == 0) {
+            if (tid == 0) { bte[k] = alpha; btau[k] = beta; }
+            double *rr = brefl + (size_t)k * Mmax;
+            for (int i = k + 1 + tid; i < M; i += blockDim.x)
+                rr[i] = (beta != 0.0) ? ((i == k + 1) ? v0 : vbuf[i]) : 0.0;
+        }
+        if (k % CL == rank && tid == 0) btd[k] = rowp(k)[k];
+        __syncthreads();
+        // (b) p_i = beta * B22[i, :] . v for owned rows i > k, four threads per row, broadcast
+        if (beta != 0.0) {
+            const int part = tid & 3;
+            for (int li0 = 0; li0 < R; li0 += blockDim.x >> 2) {   // same trip count in every lane
+                const int li = li0 + (tid >> 2);
+                const int i = li * CL + rank;
+                double a0 = 0.0, a1 = 0.0;
+                if (li < R && i > k && i < M) {
+                    const double *ri = rowp(i);
+                    int l = k + 1 + part;
+                    for (; l + 4 < M; l += 8) {
+                        a0 = fma(ri[l], hv[l], a0);
+                        a1 = fma(ri[l + 4], hv[l + 4], a1);
+                    }
+                    if (l < M) a0 = fma(ri[l], hv[l], a0);
+                }
+                double acc = a0 + a1;
+                acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                if (li < R && i > k && i < M)
+                    for (int r = part; r < CL; r += 4) cluster.map_shared_rank(pbuf, r)[i] = beta * acc;
+            }
+        }
+        cluster.sync();
+        if (beta != 0.0) {
+            // (c) w = p - (beta p.v / 2) v (p.v by warp 0); B22 -= v w^T + w v^T on owned rows
+            if (warp == 0) {
+                double pv = 0.0;
+                for (int i = k + 1 + lane; i < M; i += 32) pv = fma(pbuf[i], hv[i], pv);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
+                if (lane == 0) sc[3] = 0.5 * beta * pv;
+            }
+            __syncthreads();
+            const double Kc = sc[3];
+            for (int i = k + 1 + tid; i < M; i += blockDim.x) wv[i] = fma(-Kc, hv[i], pbuf[i]);
+            __syncthreads();
+            const int first = k + 1 + ((rank - (k + 1)) % CL + CL) % CL;
+            for (int i = first + warp * CL; i < M; i += nwarps * CL) {
+                double *ri = rowp(i);
+                const double hi = hv[i], wi = wv[i];
+                for (int j = k + 1 + lane; j < M; j += 32) ri[j] = fma(-hi, wv[j], fma(-wi, hv[j], ri[j]));
+            }
+            __syncthreads();
+        }
+        // (d) broadcast column k+1 (rows >= k+2) for the next step
+        {
+            const int first = k + 2 + ((rank - (k + 2)) % CL + CL) % CL;
+            for (int i = first + tid * CL; i < M; i += blockDim.x * CL) {
+                double v = rowp(i)[k + 1];
+                for (int r = 0; r < CL; r++) cluster.map_shared_rank(vbuf, r)[i] = v;
+            }
+        }
+        cluster.sync();
+    }
+    // trailing 2x2 (or 1x1)
+    if (tid == 0) {
+        if (M >= 2) {
+            if ((M - 2) % CL == rank) btd[M - 2] = rowp(M - 2)[M - 2];
+            if ((M - 1) % CL == rank) { btd[M - 1] = rowp(M - 1)[M - 1]; bte[M - 2] = rowp(M - 1)[M - 2]; }
+        } else if (rank == 0) {
+            btd[0] = rowp(0)[0];
+        }
+        if (rank == 0) { bte[M - 1] = 0.0; if (M >= 2) btau[M - 2] = 0.0; btau[M - 1] = 0.0; }
+    }
+    cluster.sync();   // keep every CTA's shared memory alive until remote writes are done
 }
 
 // ---- blocked reduction (mixed forms) ----------------------------------------------------------
@@ -873,7 +904,7 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
         cfg.blockDim = dim3(kTriThreads);
         const int R = (Mmax + CL - 1) / CL;
         size_t smem = (size_t)(4 * Mmax + 64) * sizeof(double);
-        if (h->rows_in_smem) smem += (size_t)R * Mmax * sizeof(double);
+        if (h->rows_in_smem) smem += (size_t)R * (Mmax + 2) * sizeof(double);
         cfg.dynamicSmemBytes = smem;
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
