@@ -120,11 +120,15 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
     h->Mmax = (int32_t)(Mmax < N ? Mmax : N);
     // cluster shape of the tridiagonalisation
     const int Mx = h->Mmax;
-    auto smem_rows = [&](int cl) { return (size_t)((Mx + cl - 1) / cl) * (Mx + 2) * 8 + (size_t)(4 * Mx + 64) * 8; };
-    if (Mx <= 128 && smem_rows(4) <= kSmemCap) { h->cl = 4; h->rows_in_smem = true; }
-    else if (smem_rows(8) <= kSmemCap) { h->cl = 8; h->rows_in_smem = true; }
-    else if (smem_rows(16) <= kSmemCap) { h->cl = 16; h->rows_in_smem = true; }
-    else { h->cl = 16; h->rows_in_smem = false; }
+    {
+        cudaError_t ce = configure_kernels(h);
+        if (ce == cudaSuccess) ce = select_tridiag_cluster(h, kSmemCap);
+        if (ce != cudaSuccess) {
+            delete h;
+            cudaGetLastError();
+            return fail(PFSM_ERR_CUDA, "pfsm_init: %s", cudaGetErrorString(ce));
+        }
+    }
     // the mixed forms' blocked reduction keeps each warp's rows of V and W in registers (up to
     // 24 rows a warp) and the window rows in shared memory for windows up to tri_mcap
     if (prm.precision != PFSM_FP64 && kUseBlockedReduction) {

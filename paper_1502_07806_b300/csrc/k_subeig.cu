@@ -830,6 +830,53 @@ __global__ void k_backtransform(const int32_t *__restrict__ plan, int32_t nb, in
 
 // Function attributes are process-wide while handles differ in window size, so every attribute
 // is set to the device maximum (what a launch actually requests still sets its occupancy).
+// Cluster size of the window reduction: B300 runs clusters of up to 16 CTAs (any size, 9-16 as
+// non-portable), but a cluster must fit in one GPC, so how many clusters of a given size run at
+// once depends on the GPC layout; the occupancy query answers it. Per-window time goes with the
+// rows each CTA owns (its share of the FP64 work) plus a per-step barrier cost that grows with
+// the cluster; windows beyond the co-resident count wait for a second wave. Chooses the size
+// with the least waves x (rows per CTA + 3.3 x cluster size), rows in shared memory when they
+// fit. The 3.3 is fitted to B300 timings of ten 384-row windows: 8, 9, 10 and 16 CTAs took 4.35,
+// 4.22, 4.07 and 4.61 ms in one wave; 11, 12 and 14 fit nine clusters at a time and took 7.6-8.0.
+cudaError_t select_tridiag_cluster(pfsm_handle_s *h, size_t smem_cap)
+{
+    const int Mx = h->Mmax, nb = h->nb;
+    double best = 1e300;
+    int best_cl = 16;
+    bool best_smem = false;
+    for (int cl = 16; cl >= 2; cl--) {
+        const size_t R = (size_t)((Mx + cl - 1) / cl);
+        const size_t srows = R * (size_t)(Mx + 2) * sizeof(double) + (size_t)(4 * Mx + 64) * sizeof(double);
+        const bool in_smem = srows <= smem_cap;
+        const size_t smem = in_smem ? srows : (size_t)(4 * Mx + 64) * sizeof(double);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(nb * cl));
+        cfg.blockDim = dim3(kTriThreads);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cl;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int active = 0;
+        cudaError_t e = in_smem ? cudaOccupancyMaxActiveClusters(&active, k_tridiag<true>, &cfg)
+                                : cudaOccupancyMaxActiveClusters(&active, k_tridiag<false>, &cfg);
+        if (e != cudaSuccess || active < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        const int waves = (nb + active - 1) / active;
+        const double cost = waves * ((double)R + 3.3 * cl) * (in_smem ? 1.0 : 1.5);
+        if (cost < best) { best = cost; best_cl = cl; best_smem = in_smem; }
+    }
+    if (best == 1e300) return cudaErrorInvalidConfiguration;
+    h->cl = best_cl;
+    h->rows_in_smem = best_smem;
+    return cudaSuccess;
+}
+
 cudaError_t configure_kernels(pfsm_handle_s *h)
 {
     (void)h;

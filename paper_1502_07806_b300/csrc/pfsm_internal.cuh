@@ -195,6 +195,9 @@ inline int slices_for(int precision) { return precision == PFSM_BF16_SPLIT ? 3 :
 inline int slice_kind(int precision) { return precision == PFSM_BF16_SPLIT ? 0 : 1; }
 inline int64_t padded_ld(int64_t n) { return (n + 63) / 64 * 64; }
 
+// cluster size and row placement of the window reduction (k_subeig.cu)
+cudaError_t select_tridiag_cluster(pfsm_handle_s *h, size_t smem_cap);
+
 // blocked tridiagonalisation of the mixed forms (k_subeig.cu): panel width and the panel
 // kernel's dynamic shared memory (window rows for windows up to Mcap, or none)
 constexpr int kPanel = 32;
