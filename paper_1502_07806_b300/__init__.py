@@ -237,6 +237,17 @@ class Batch:
         _check(load_library().pfsm_batch_get_status(self._b, out), "pfsm_batch_get_status")
         return list(out)
 
+    @classmethod
+    def autotuned(cls, As, prevs, halo: int = -1, fs_iters: int = 3, precision: int = FP64,
+                  cache_path: str | None = None, **kw):
+        """A batch whose block counts are measured per size class (autotune.tune on the first
+        problem of each class; later problems of the class reuse it)."""
+        from . import autotune
+        nblocks = [autotune.tune(A, prev, precision, halo=halo, fs_iters=fs_iters, cache_path=cache_path)
+                   for A, prev in zip(As, prevs)]
+        return cls([int(A.shape[0]) for A in As], nblocks, halo=halo, fs_iters=fs_iters,
+                   precision=precision, **kw)
+
     def close(self):
         if getattr(self, "_b", None):
             load_library().pfsm_batch_destroy(self._b)

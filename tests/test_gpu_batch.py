@@ -72,3 +72,31 @@ def test_batch_small_problems_match_oracle(pf, orc, problems):
         print(f"batch N={p.n}: |dlam|/||A|| = {dl:.2e}, projector = {pe:.2e}")
         assert dl <= 1e-10 and pe <= 1e-8
     b.close()
+
+
+def test_autotuned_batch(pf, problems, tmp_path):
+    """Block counts measured per size class; each problem still equals its solo solve with the
+    chosen layout and stays within the FP64 bars of the oracle-checked default."""
+    from paper_1502_07806_b300 import autotune
+    order = np.argsort([p.n for p in problems])
+    probs = [problems[i] for i in order[:3]] + [problems[order[-1]]]
+    As = [_dev(p.A) for p in probs]
+    prevs = [_dev(p.prev) for p in probs]
+    path = str(tmp_path / "tune.json")
+    nbs = []
+    for A, prev, p in zip(As, prevs, probs):
+        best, meas = autotune.tune(A, prev, pf.BF16_SPLIT, cache_path=path, return_measurements=True)
+        print(f"N={p.n}: " + ", ".join(f"{k} slices {v[0]:.2f} ms res {v[1]:.1e}" for k, v in sorted(meas.items()))
+              + f" -> {best}")
+        assert best in autotune.candidates(p.n) and best in meas
+        nbs.append(best)
+    b = pf.Batch.autotuned(As, prevs, precision=pf.BF16_SPLIT, cache_path=path)
+    lams, Vs = b.solve(As, prevs)
+    assert b.status() == [0] * len(probs)
+    for i, p in enumerate(probs):
+        h = pf.Handle(p.n, nbs[i], precision=pf.BF16_SPLIT)
+        lam, V = h.solve(As[i], prevs[i])
+        assert h.status() == 0
+        assert torch.equal(lams[i], lam) and torch.equal(Vs[i], V)
+        h.close()
+    b.close()
