@@ -168,11 +168,11 @@ int pfsm_batch_destroy(pfsm_batch_t b);
  * pieces, precision PFSM_BF16_SPLIT) or TF32 (2 pieces, PFSM_TF32_SPLIT) and the cross products
  * of total order below the piece count are accumulated in FP32 in tensor memory: relative
  * accuracy about 2^-22 (TF32) or 2^-24 (BF16) of sum_k |P[r,k] Q[c,k]|. With precision
- * PFSM_FP64 the product is FP64-accurate: each row is scaled by a power of two and cut into nine
- * base-32 digits held exactly in BF16, digit products of equal level are summed exactly in FP32
- * tensor memory (K chunks of 1792) and levels 0..10 are combined in FP64 (error about
- * 2^-46 max|P[r,:]| max|Q[c,:]| times a small multiple of 1 + sqrt(K) 2^-5; Ozaki, Ogita, Oishi,
- * Rump 2012). Allocates its slices
+ * PFSM_FP64 the product is FP64-accurate: each row is scaled by a power of two and cut into seven
+ * base-128 digits held exactly in BF16, digit products of equal level are summed exactly in FP32
+ * tensor memory (K chunks of 512) and levels 0..6 are combined in float-float, then FP64 (error
+ * about sqrt(K) 2^-49 max|P[r,:]| max|Q[c,:]| for random-sign terms, at most K 2^-46 of it;
+ * Ozaki, Ogita, Oishi, Rump 2012). Allocates its slices
  * with cudaMallocAsync on `stream`, frees them, and synchronises the stream before returning;
  * returns PFSM_ERR_TIMEOUT if a bounded device wait gave up. rows, cols <= 65535. */
 int pfsm_split_gemm(int64_t rows, int64_t cols, int64_t K, const double *P, const double *Q,

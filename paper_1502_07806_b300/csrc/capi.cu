@@ -408,7 +408,7 @@ int pfsm_split_gemm(int64_t rows, int64_t cols, int64_t K, const double *P, cons
         return fail(PFSM_ERR_INVALID_ARG, "pfsm_split_gemm: unknown precision");
     cudaStream_t st = (cudaStream_t)stream;
     PFSM_CUDA(configure_tc_kernels());
-    if (precision == PFSM_FP64) {       // FP64-accurate: base-32 digits, exact level sums
+    if (precision == PFSM_FP64) {       // FP64-accurate: base-128 digits, exact level sums
         PFSM_CUDA(configure_oz_kernels());
         const int64_t ld = padded_ld(K);
         void *sp = nullptr, *sq = nullptr;

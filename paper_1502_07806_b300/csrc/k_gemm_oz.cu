@@ -3,28 +3,32 @@
 // 1.2 TFLOP/s and the BF16 tensor cores about 1.75 PFLOP/s.
 //
 // Splitting (k_oz_split): every row r of an operand is scaled by its own power of two 2^-e_r so
-// that |x| < 1, rounded to a 45-bit fixed-point integer q, and q is cut into S = 9 balanced base-32
-// digits n_0 .. n_8 (n_s in [-16, 16) for s >= 1, |n_0| <= 32), each stored exactly as a BF16 value:
-//   x = 2^e_r sum_s n_s 2^-5(s+1)   (to 2^-46 of the row's largest entry).
-// Product (k_gemm_oz): C[r, c] = sum_L 2^(e_r + e_c - 5(L+2)) sum_{s+t=L} sum_k n_s[r,k] m_t[c,k].
-// Every digit product has |n m| <= 2^10 and a level has at most S = 9 pairs, so a level summed over
-// a K chunk of 1792 terms stays below 2^24 and the FP32 accumulation in tensor memory is EXACT.
-// Levels L = 0 .. OZ_LEVELS-1 = 10 are kept. Every entry, however small, has O(1) low digits, so
-// the products of a dropped level L add up like a random walk over K: about
-// sqrt(K (pairs at L)) 2^(8 - 5(L+2)) / 3 relative to 2^(e_r + e_c). Stopping after L = 8 would
-// leave sqrt(K) 2^-46 (1e-12 at K = 9072); stopping after L = 10 leaves about 1e-15 there, below
-// the 2^-46 rounding of the operands themselves. Products that only need FP32-class accuracy
-// ask for fewer levels (about sqrt(K) 2^(3 - 5(levels+1)) / 3).
+// that |x| < 1, rounded to a 48-bit fixed-point integer q (|q| <= 2^48), and q is cut into S = 7
+// balanced base-128 digits n_0 .. n_6 (n_s in [-64, 64) for s >= 1, |n_0| <= 64), each an integer
+// that BF16 holds exactly:
+//   x = 2^e_r sum_s n_s 2^-(6 + 7 s)   (to 2^-49 of the row's largest entry).
+// Product (k_gemm_oz): C[r, c] = sum_L 2^(e_r + e_c - 12 - 7 L) sum_{s+t=L} sum_k n_s[r,k] m_t[c,k].
+// Every digit product has |n m| <= 2^12 and level L <= 6 has L + 1 pairs, so a level summed over a
+// K chunk of 512 terms stays below 7 * 2^21 < 2^24 and the FP32 accumulation in tensor memory is
+// EXACT. Levels L = 0 .. OZ_LEVELS-1 = 6 are kept (all 28 pairs with s + t <= 6). Every entry,
+// however small, has O(1) low digits, so the products of the first dropped level L add up like a
+// random walk over K: about sqrt((L + 1) K) 2^-7L / 3 relative to 2^(e_r + e_c) -- for L = 7
+// (the default) about sqrt(K) 2^-49, the size of the operands' own rounding. Products that only
+// need FP32-class accuracy ask for fewer levels (5 levels: about sqrt(6 K) 2^-35 / 3).
 //
 // CTA: 192 threads, a 128 x 32 output tile. All levels accumulate at once, each in its own
-// 32-column FP32 accumulator in tensor memory (11 x 32 of the 512 columns), so one pipeline stage
-// holds every digit slice of P and of Q for one 32-element (64-byte, 64-byte-swizzled) K block,
-// 90 KB loaded by two TMA copies, and feeds all 60 slice-pair products (120 MMAs of 128x32x16):
-// each slice tile is read from L2 once per K block instead of once per pair. Warp 0: TMA (2
-// stages). Warp 1: TMEM owner and MMA issuer. Warps 2-5: at the end of each exact K chunk, drain
-// the level sums (one row per thread) into float-float registers with exact power-of-two scales;
-// finally one FP64 conversion per entry and row-contiguous stores through shared memory. The
-// epilogue can add an exact FP64 diagonal term C[r, c] += V[r, c] d[c] (for products with
+// 32-column FP32 accumulator in tensor memory, in one of two 256-column buffers that alternate
+// between exact K chunks (the drain of one chunk overlaps the MMAs of the next). A pipeline stage
+// (3 of them) holds every digit slice of P and of Q for one 32-element (64-byte, 64-byte-swizzled)
+// K block, 70 KB loaded by two TMA copies. Q's slice tiles sit back to back in the stage, one SW64
+// layout of 7 x 32 rows, and level L's accumulator at columns 32 L, so P slice s times Q slices
+// 0 .. LV-1-s is ONE MMA (N = 32 (LV - s)) whose output columns are exactly the accumulators of
+// levels s .. LV-1: 7 MMAs per 16 K for 28 slice pairs, each reading the 4 KB P tile once. The
+// s = 0 MMA covers every level, so it alone carries the "overwrite" flag at a chunk's start.
+// Warp 0: TMA. Warp 1: TMEM owner and MMA issuer. Warps 2-5: at the end of each exact K chunk,
+// drain the level sums (one row per thread) into float-float registers with exact power-of-two
+// scales; finally one FP64 conversion per entry and row-contiguous stores through shared memory.
+// The epilogue can add an exact FP64 diagonal term C[r, c] += V[r, c] d[c] (for products with
 // A = diag(d) + E whose digits cover E only). All mbarrier waits are bounded.
 #include "tc_common.cuh"
 
@@ -34,11 +38,17 @@ namespace oz {
 
 constexpr int BM = 128, BN = 32, KB = 32;         // tile, K block (32 BF16 = 64 bytes)
 constexpr int P_TILE = BM * 64, Q_TILE = BN * 64;  // bytes per slice per K block
-constexpr int STAGES = 2;
+constexpr int STAGES = 3;
 constexpr int MAX_STAGE_BYTES = OZ_SLICES * (P_TILE + Q_TILE);
-constexpr uint32_t TMEM_COLS = 512;               // level L at columns 32 L
-constexpr int KCHUNK = 1792;                      // K terms per exact level sum
-constexpr int BETA = 5;
+constexpr uint32_t TMEM_COLS = 512;               // two buffers of 256 columns, level L at 32 L
+constexpr uint32_t BUF_COLS = 256;
+constexpr int KCHUNK = 512;                       // K terms per exact level sum
+constexpr int BETA = 7;                           // bits per digit
+constexpr int QBITS = BETA * OZ_SLICES - 1;       // fixed-point bits of q (48)
+static_assert(OZ_LEVELS <= OZ_SLICES && OZ_LEVELS <= 8, "the s = 0 MMA must span every level");
+static_assert(OZ_LEVELS * BN <= (int)BUF_COLS, "levels of one buffer exceed its columns");
+static_assert(KCHUNK % KB == 0 && (double)KCHUNK * OZ_LEVELS * 4096.0 < 16777216.0,
+              "a level sum over one K chunk must stay exact in FP32");
 
 }  // namespace oz
 
@@ -46,8 +56,8 @@ constexpr int BETA = 5;
 
 // One warp per row: exponent of the row's largest |entry| and the S digits of every entry.
 // zero_diag: digits of the off-diagonal part (entry (r, r) taken as 0, its value stored in d[r]).
-// Input in FP64 or FP32 (an FP32 operand's digits are exact: 24 bits fit in the 45-bit grid of its
-// row unless the entry is below 2^-21 of the row's largest).
+// Input in FP64 or FP32 (an FP32 operand's digits are exact: 24 bits fit in the 48-bit grid of its
+// row unless the entry is below 2^-24 of the row's largest).
 template <typename T>
 __global__ void k_oz_split(const T *__restrict__ src, int64_t rows, int64_t cols, int64_t ld,
                            __nv_bfloat16 *__restrict__ dst, int64_t sl_ld, int64_t sstride,
@@ -66,16 +76,16 @@ __global__ void k_oz_split(const T *__restrict__ src, int64_t rows, int64_t cols
     int e = 0;
     if (mx > 0.0) frexp(mx, &e);             // mx = f 2^e, f in [0.5, 1): |x| 2^-e < 1
     if (lane == 0) exps[r] = e;
-    const double sc = ldexp(1.0, 5 * OZ_SLICES - e);
+    const double sc = ldexp(1.0, oz::QBITS - e);
     __nv_bfloat16 *out = dst + r * sl_ld;
     for (int64_t c = lane; c < cols; c += 32) {
-        long long q = __double2ll_rn(val(c) * sc);    // |q| <= 2^45
+        long long q = __double2ll_rn(val(c) * sc);    // |q| <= 2^48
         int dig[OZ_SLICES];
 #pragma unroll
-        for (int s = OZ_SLICES - 1; s >= 1; s--) {    // balanced base-32 digits, low to high
-            const int d = (int)(((q + 16) & 31) - 16);
+        for (int s = OZ_SLICES - 1; s >= 1; s--) {    // balanced base-128 digits, low to high
+            const int d = (int)(((q + 64) & 127) - 64);
             dig[s] = d;
-            q = (q - d) >> 5;
+            q = (q - d) >> oz::BETA;
         }
         dig[0] = (int)q;
 #pragma unroll
@@ -97,23 +107,25 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
     if (prm.lower_only && col0 > row0 + BM - 1) return;           // whole tile above the diagonal
     const int64_t zr = (int64_t)z * prm.zrow;                      // operand row offset
     double *Cz = prm.C + (int64_t)z * prm.zc;
-    const int S = OZ_SLICES;
     const int LV = (prm.levels > 0 && prm.levels < OZ_LEVELS) ? prm.levels : OZ_LEVELS;   // levels 0 .. LV-1
-    const int NSL = LV < S ? LV : S;                               // slices that take part
+    const int NSL = LV;                                            // slices that take part (s, t < LV)
     const int stage_bytes = NSL * (P_TILE + Q_TILE);
     extern __shared__ __align__(1024) uint8_t smraw[];
     const uint32_t raw = smem_u32(smraw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *gbase = smraw + (base - raw);
     uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + STAGES * MAX_STAGE_BYTES);
-    // bars: [0,2) full, [2,4) empty, 4 chunk summed, 5 chunk drained, 6 all MMAs done
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 3);
+    // bars: [0, S) full, [S, 2S) empty, then per TMEM buffer "chunk summed" x2, "chunk drained"
+    // x2, and "all MMAs done"
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 5);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     int *ecol = reinterpret_cast<int *>(tmem_slot + 2);           // BN column exponents
     const uint32_t bar_base = smem_u32(bars);
     auto full_bar = [&](int s) { return bar_base + 8u * s; };
     auto empty_bar = [&](int s) { return bar_base + 8u * (STAGES + s); };
-    const uint32_t accf_bar = bar_base + 8u * (2 * STAGES), acce_bar = accf_bar + 8u, done_bar = accf_bar + 16u;
+    auto accf_bar = [&](int b) { return bar_base + 8u * (2 * STAGES + b); };
+    auto acce_bar = [&](int b) { return bar_base + 8u * (2 * STAGES + 2 + b); };
+    const uint32_t done_bar = bar_base + 8u * (2 * STAGES + 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     // 32-element K blocks; a lower-triangular P has no entries beyond column row0 + BM - 1
@@ -126,8 +138,10 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
             mbar_init(full_bar(s), 1);
             mbar_init(empty_bar(s), 1);
         }
-        mbar_init(accf_bar, 1);
-        mbar_init(acce_bar, 128);
+        for (int b = 0; b < 2; b++) {
+            mbar_init(accf_bar(b), 1);
+            mbar_init(acce_bar(b), 128);
+        }
         mbar_init(done_bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -172,25 +186,26 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
         if (lane == 0) {
             bool ok = true;
             for (int ch = 0; ch < nch && ok; ch++) {
-                if (ch > 0 && !mbar_wait(acce_bar, (ch - 1) & 1)) { ok = false; break; }   // drained
+                const int buf = ch & 1;
+                // the buffer's previous chunk (ch - 2) must be drained before it is overwritten
+                if (ch >= 2 && !mbar_wait(acce_bar(buf), ((ch >> 1) - 1) & 1)) { ok = false; break; }
                 fence_after();
+                const uint32_t dbuf = tmem_acc + BUF_COLS * buf;
                 const int kbA = ch * kb_per_chunk, kbB = min(nkb, kbA + kb_per_chunk);
                 for (int kb = kbA; kb < kbB && ok; kb++) {
                     const int s = kb % STAGES;
                     if (!mbar_wait(full_bar(s), (kb / STAGES) & 1) || *abort_flag) { ok = false; break; }
                     fence_after();
-                    for (int L = 0; L < LV; L++) {
-                        const int sa0 = L >= S ? L - S + 1 : 0, sa1 = L < S ? L : S - 1;
-                        const uint32_t dacc = tmem_acc + 32u * L;
-                        for (int sa = sa0; sa <= sa1; sa++) {
-                            const uint64_t da = sw64_desc(stageP(s, sa)), db = sw64_desc(stageQ(s, L - sa));
-                            umma<0, BM, BN>(dacc, da, db, (kb == kbA && sa == sa0) ? 0u : 1u);
-                            umma<0, BM, BN>(dacc, da + 2, db + 2, 1u);   // second 16 of the 32 K
+                    for (int h = 0; h < 2; h++) {                  // the two 16-element halves
+                        for (int sa = 0; sa < NSL; sa++) {
+                            const uint32_t acc = (kb == kbA && h == 0 && sa == 0) ? 0u : 1u;
+                            umma_bf16_n(dbuf + 32u * sa, sw64_desc(stageP(s, sa)) + 2 * h,
+                                        sw64_desc(stageQ(s, 0)) + 2 * h, BN * (LV - sa), acc);
                         }
                     }
                     umma_commit(empty_bar(s));
                 }
-                umma_commit(accf_bar);      // this chunk's level sums are complete with its MMAs
+                umma_commit(accf_bar(buf));  // this chunk's level sums are complete with its MMAs
             }
             if (!ok) {
                 set_status(prm.status, PFSM_ERR_TIMEOUT);
@@ -210,7 +225,8 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
         for (int j = 0; j < BN; j++) { hi[j] = 0.0f; lo[j] = 0.0f; }
         bool ok = true;
         for (int ch = 0; ch < nch; ch++) {
-            bool got = mbar_wait(accf_bar, ch & 1);
+            const int buf = ch & 1;
+            bool got = mbar_wait(accf_bar(buf), (ch >> 1) & 1);
             got = __all_sync(0xffffffffu, got) && !*abort_flag;
             if (!got) {
                 ok = false;
@@ -220,9 +236,9 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
             }
             fence_after();
             for (int L = 0; L < LV; L++) {
-                const float scale = __int_as_float((127 - BETA * (L + 2)) << 23);   // 2^-5(L+2)
+                const float scale = __int_as_float((127 - 12 - BETA * L) << 23);   // 2^-(12 + 7 L)
                 uint32_t v[32];
-                tmem_ld32(tmem_acc + ((uint32_t)(32 * gq) << 16) + 32u * L, v);
+                tmem_ld32(tmem_acc + ((uint32_t)(32 * gq) << 16) + BUF_COLS * buf + 32u * L, v);
 #pragma unroll
                 for (int j = 0; j < 32; j++) {
                     const float x = __uint_as_float(v[j]) * scale;
@@ -232,7 +248,7 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
                 }
             }
             fence_before();
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce_bar) : "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce_bar(buf)) : "memory");
         }
         // every MMA has completed (last chunk waited) and every stage consumed: the stage
         // memory now holds this warp's staging block (32 rows x 32 columns), so that the loads and
@@ -302,8 +318,7 @@ cudaError_t launch_gemm_oz(const SliceBuf &P, const int32_t *ep, const SliceBuf 
 {
     CUtensorMap mp, mq;
     cudaError_t e;
-    const int lv = (prm.levels > 0 && prm.levels < OZ_LEVELS) ? prm.levels : OZ_LEVELS;
-    const int nsl = lv < OZ_SLICES ? lv : OZ_SLICES;
+    const int nsl = (prm.levels > 0 && prm.levels < OZ_LEVELS) ? prm.levels : OZ_LEVELS;
     if (P.ns != OZ_SLICES || Q.ns != OZ_SLICES || P.kind != 0 || Q.kind != 0 || P.ld != Q.ld || P.ld % oz::KB)
         return cudaErrorInvalidValue;
     if ((e = make_slice_map64(&mp, P, oz::BM, nsl)) != cudaSuccess) return e;

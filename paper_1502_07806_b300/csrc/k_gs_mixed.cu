@@ -7,7 +7,7 @@
 // tensor cores are fast. The steps below move all sequential work to FP32 and all FP64-accurate
 // work to dense products on the tensor cores:
 //
-//   1. S~ = X X^T to about 2^-35 (digit product truncated to six levels).
+//   1. S~ = X X^T to about 2^-35 (digit product truncated to five levels).
 //   2. FP32 blocked Cholesky S~ = L~ L~^T and, in the same sweep, M = L~^-1 (lower triangular,
 //      positive diagonal). M is a preconditioner only: nothing below needs it to be accurate.
 //   3. V1 = M X with the FP64-accurate digit product. For ANY lower-triangular M with positive
@@ -345,12 +345,12 @@ cudaError_t launch_gram_schmidt_mixed(pfsm_handle_s *h, cudaStream_t st)
     SliceBuf sY{w.slY, N, ld, ns, kind}, sZ{w.slZ, N, ld, ns, kind};
     SliceBuf dP{w.ozP, N, ld, OZ_SLICES, 0}, dQ{w.ozQ, N, ld, OZ_SLICES, 0};
     cudaError_t e;
-    // 1. S~ = X X^T (lower) to about 2^-35 (six digit levels: a split product accumulated in FP32
+    // 1. S~ = X X^T (lower) to about 2^-35 (five digit levels: a split product accumulated in FP32
     //    would carry sqrt(N) 2^-24, which at large N makes E, and with it F, too large for the
     //    split products of steps 5-6), and its diagonal for the breakdown test
     OzParams o{};
     if ((e = launch_oz_split(w.X, N, N, N, dP, w.ozeP, st)) != cudaSuccess) return e;
-    o.rows = (int)N; o.cols = (int)N; o.C = w.S; o.ldc = N; o.lower_only = 1; o.levels = 6; o.status = w.status;
+    o.rows = (int)N; o.cols = (int)N; o.C = w.S; o.ldc = N; o.lower_only = 1; o.levels = 5; o.status = w.status;
     if ((e = launch_gemm_oz(dP, w.ozeP, dP, w.ozeP, o, st)) != cudaSuccess) return e;
     if ((e = launch_copy_diag(w.S, N, w.sdiag, st)) != cudaSuccess) return e;
     if (h->timing && (e = cudaEventRecord(h->gs_ev[0], st)) != cudaSuccess) return e;
@@ -391,10 +391,10 @@ cudaError_t launch_gram_schmidt_mixed(pfsm_handle_s *h, cudaStream_t st)
     if ((e = launch_gemm_tc(sY, sZ, t, nullptr, st)) != cudaSuccess) return e;
     if ((e = launch_oz_split(w.F, N, N, N, dP, w.ozeP, st)) != cudaSuccess) return e;
     if ((e = launch_oz_split(w.W, N, N, N, dQ, w.ozeQ, st)) != cudaSuccess) return e;
-    // F is of order |E| (1e-7 here), so F W needs about 1e-9 of its own size: seven digit levels
-    // (about sqrt(N) 2^-37 / 3 of 2^(e_r + e_c), e_r the exponent of F's row)
+    // F is of order |E| (1e-7 here), so F W needs about 1e-9 of its own size: six digit levels
+    // (about sqrt(7 N) 2^-42 / 3 of 2^(e_r + e_c), e_r the exponent of F's row)
     o = OzParams{};
-    o.rows = (int)N; o.cols = (int)N; o.C = w.Y; o.ldc = N; o.sub = 1; o.p_lower = 1; o.levels = 7; o.status = w.status;
+    o.rows = (int)N; o.cols = (int)N; o.C = w.Y; o.ldc = N; o.sub = 1; o.p_lower = 1; o.levels = 6; o.status = w.status;
     if ((e = launch_gemm_oz(dP, w.ozeP, dQ, w.ozeQ, o, st)) != cudaSuccess) return e;
     // the orthonormal vectors now live in Y: swap the buffers so X holds V
     double *tmp = w.X;

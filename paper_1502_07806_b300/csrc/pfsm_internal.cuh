@@ -163,11 +163,11 @@ cudaError_t launch_split(const double *src, int64_t rows, int64_t cols, int64_t 
 cudaError_t launch_gemm_tc(const SliceBuf &P, const SliceBuf &Q, TcParams prm, SliceBuf *out_sl,
                            cudaStream_t st);
 // ---- FP64-accurate products on the BF16 tensor cores (k_gemm_oz.cu) ----
-#define OZ_SLICES 9                 // base-32 digits per entry (2^-46 of the row's largest)
-#define OZ_LEVELS 11                // digit levels s + t kept by default (see k_gemm_oz.cu)
+#define OZ_SLICES 7                 // base-128 digits per entry (2^-49 of the row's largest)
+#define OZ_LEVELS 7                 // digit levels s + t kept by default (see k_gemm_oz.cu)
 struct OzParams {
     int rows, cols;                 // output extent
-    int kblocks;                    // 64-element K blocks (filled by launch_gemm_oz)
+    int kblocks;                    // 32-element K blocks (filled by launch_gemm_oz)
     const int32_t *ep, *eq;         // row exponents of P and Q (filled by launch_gemm_oz)
     double *C; int64_t ldc;
     int sub;                        // C -= P Q^T instead of C = P Q^T

@@ -114,6 +114,17 @@ __device__ __forceinline__ void umma(uint32_t dtmem, uint64_t a, uint64_t b, uin
             ::"r"(dtmem), "l"(a), "l"(b), "r"(idesc<1, M_, N_>()), "r"(accum));
 }
 
+// kind::f16 MMA (BF16 operands) with M = 128 and N given at run time (a multiple of 16 in
+// [16, 256]): N / 8 goes into bits 17-22 of the instruction descriptor.
+__device__ __forceinline__ void umma_bf16_n(uint32_t dtmem, uint64_t a, uint64_t b, int n, uint32_t accum)
+{
+    const uint32_t id = idesc<0, 128, 0>() | ((uint32_t)(n >> 3) << 17);
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(dtmem), "l"(a), "l"(b), "r"(id), "r"(accum));
+}
+
 __device__ __forceinline__ void umma_commit(uint32_t bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");

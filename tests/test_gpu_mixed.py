@@ -56,10 +56,10 @@ def test_fp64_digit_gemm_is_fp64_accurate(pf, rows, cols, K):
     Q = rng.standard_normal((cols, K)) * np.exp(rng.uniform(-5, 5, (1, K)))
     C = pf.split_gemm(torch.from_numpy(P).cuda(), torch.from_numpy(Q).cuda(), pf.FP64).cpu().numpy()
     ref = P @ Q.T
-    # each operand is rounded to 2^-46 of 2^e >= its row max, and the dropped levels L >= 11 add
-    # about 2^-57 per term; both are sums of K terms of random sign, so the error scales with
-    # sqrt(K) max|P_r| max|Q_c| (worst case K); per term at most about 2^-43 (2^e <= 2 max, two
-    # operands), the bound for K = 1 where nothing averages
+    # each operand is rounded to 2^-49 of 2^e >= its row max, and the first dropped level (L = 7,
+    # six digit pairs) adds about 2^-49 per term; both are sums of K terms of random sign, so the
+    # error scales with sqrt(K) max|P_r| max|Q_c| (worst case K); per term at most about 2^-46
+    # (2^e <= 2 max, two operands, the dropped levels), so the bounds below keep an 8x margin
     scale = np.max(np.abs(P), axis=1)[:, None] * np.max(np.abs(Q), axis=1)[None, :]
     err = np.max(np.abs(C - ref) / (K * scale))
     err_rw = np.max(np.abs(C - ref) / (np.sqrt(K) * scale))
