@@ -26,7 +26,8 @@ namespace cg = cooperative_groups;
 
 namespace pfsm {
 
-constexpr int kTriThreads = 256;
+constexpr int kTriThreads = 256;      // blocked panel kernel
+constexpr int kTriLaThreads = 288;    // k_tridiag: warp 0 + eight warps (two per sub-partition)
 
 __device__ __forceinline__ double block_sum(double v, double *red)
 {
@@ -47,8 +48,6 @@ __device__ __forceinline__ double block_sum(double v, double *red)
     return t;
 }
 
-// Grid: nb * CL CTAs, clusters of CL along x. Rows of window b are owned cyclically: CTA `rank`
-// owns rows i with i % CL == rank.
 // 1/p and 1/sqrt(d) for d, p > 0 of any FP64 magnitude without the IEEE FP64 divide / square
 // root sequences (each ~10 dependent FP64 instructions of ~64 cycles on B300): the exponent is
 // split off (so the FP32 seed never under- or overflows), then an FP32 estimate and two Newton
@@ -74,18 +73,55 @@ __device__ __forceinline__ double scaled_rsqrt(double d)
     return ldexp(y, -e / 2);
 }
 
-// B300 spends ~64 cycles of a sub-partition's FP64 pipe on EVERY FP64 warp instruction, so the
-// loop is arranged to issue few of them: the Householder scalars and p.v are computed by one warp
-// (not by all eight) and broadcast through shared memory, and the mat-vec runs four threads per
-// row (two shuffle rounds per row instead of five), leaving the rank-2 update (two DFMA per entry,
-// lanes along the row) as the bulk. Rows in shared memory are padded to Mmax + 2 doubles so the
-// eight rows a warp reads in the mat-vec fall in different banks.
+// Householder scalars of the column c (entries kk+1 .. M-1) that step kk reduces, by one warp:
+// x0 = c[kk+1], alpha = -sign(x0) ||c||, v0 = x0 - alpha, beta = 2 / (v0^2 + sum_{i > kk+1} c_i^2)
+// (beta = 0 and alpha = x0 when the tail is already zero).
+__device__ __forceinline__ void householder_scalars(const double *c, int kk, int M, int lane, double *sc)
+{
+    const double x0 = c[kk + 1];
+    double t2 = 0.0;
+    for (int i = kk + 2 + lane; i < M; i += 32) t2 = fma(c[i], c[i], t2);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+    double beta = 0.0, alpha = x0, v0 = 0.0;
+    if (t2 != 0.0) {
+        const double nn = fma(x0, x0, t2);
+        const double xn = nn * scaled_rsqrt(nn);
+        alpha = (x0 >= 0.0) ? -xn : xn;
+        v0 = x0 - alpha;
+        beta = 2.0 * scaled_rcp(fma(v0, v0, t2));
+    }
+    if (lane == 0) { sc[0] = beta; sc[1] = alpha; sc[2] = v0; }
+}
+
+// Householder reduction of every window to tridiagonal form, one thread-block cluster per window.
+// Grid: nb * CL CTAs, clusters of CL along x; CTA `rank` owns the rows i with i % CL == rank (in
+// shared memory when they fit, else in the window's global work matrix).
+//
+// B300 spends ~64 cycles of a sub-partition's FP64 pipe on every FP64 warp instruction and a
+// dependent FP64 chain runs at about that pace, so the step is arranged around ONE cluster barrier
+// with the serial work hidden behind the rank-2 update (a look-ahead form of Golub & Van Loan
+// Sec. 8.3.1). Step k, with x = column k (entries > k, in every CTA), its scalars (alpha, beta)
+// and u = B x on the owned rows already known:
+//   S1  v = x with v_{k+1} = x_{k+1} - alpha;  p_i = beta (u_i - alpha B_{i,k+1}) = beta (B v)_i for
+//       the owned rows, pushed into every CTA with the CTA's partial p.v; the owner of row k+1
+//       pushes that row (= column k+1, by symmetry) into every CTA.
+//   --  cluster barrier
+//   S2  w = p - (beta p.v / 2) v, and the next column x' = (row k+1) - v_{k+1} w - w_{k+1} v,
+//       i.e. column k+1 after this step's update, in every CTA without a second exchange.
+//   S3  warp 0: the scalars of step k+1 from x'. Warps 1-8 (two per SM sub-partition): the
+//       rank-2 update B -= v w^T + w v^T of the owned rows, fused with the next step's product
+//       u' = B x' on the freshly updated entries (lanes along the row, eight rows per warp, the
+//       per-row sums by one transpose-reduce: 9 shuffle adds per 8 rows).
+// Buffers written by other CTAs (p, the p.v partials, row k+1) alternate with the step's parity:
+// a CTA can run at most one step ahead of another, since it cannot pass the next barrier first.
 template <bool SMEM_ROWS>
-__global__ void __launch_bounds__(kTriThreads)
+__global__ void __launch_bounds__(kTriLaThreads)
 k_tridiag(const double *__restrict__ A, int64_t N, const int32_t *__restrict__ plan, int32_t nb,
           int32_t Mmax, double *__restrict__ gwork, double *__restrict__ refl,
           double *__restrict__ tau, double *__restrict__ td, double *__restrict__ te)
 {
+    constexpr int G = 8;                               // rows per warp group in the fused loop
     cg::cluster_group cluster = cg::this_cluster();
     const int CL = (int)cluster.num_blocks();
     const int rank = (int)cluster.block_rank();
@@ -93,20 +129,85 @@ k_tridiag(const double *__restrict__ A, int64_t N, const int32_t *__restrict__ p
     const int64_t s0 = plan[2 * nb + b];
     const int M = plan[3 * nb + b];
     const int R = (Mmax + CL - 1) / CL;
-    const int ld = SMEM_ROWS ? Mmax + 2 : Mmax;
     extern __shared__ double sm[];
     double *rows = SMEM_ROWS ? sm : (gwork + (size_t)b * Mmax * Mmax);
-    double *vbuf = sm + (SMEM_ROWS ? (size_t)R * ld : 0);
-    double *pbuf = vbuf + Mmax;
-    double *hv = pbuf + Mmax;
-    double *wv = hv + Mmax;
-    double *sc = wv + Mmax;                            // broadcast scalars (64)
+    double *vec = sm + (SMEM_ROWS ? (size_t)R * Mmax : 0);
+    double *cbuf = vec;                    // x: column k, entries > k
+    double *nbuf = vec + Mmax;             // x': column k+1 after step k, entries > k+1
+    double *hv = vec + 2 * Mmax;           // v
+    double *wv = vec + 3 * Mmax;           // w
+    double *pbuf = vec + 4 * Mmax;         // [2][Mmax] p (written by every CTA)
+    double *rowbuf = vec + 6 * Mmax;       // [2][Mmax] row k+1 (written by its owner)
+    double *uu = vec + 8 * Mmax;           // [R] (B x)_i of the owned rows
+    double *pvp = uu + R;                  // [2][32] partial p.v of every CTA
+    double *sc = pvp + 64;                 // scalars of the next step
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     auto rowp = [&](int i) -> double * {
-        return SMEM_ROWS ? rows + (size_t)(i / CL) * ld : rows + (size_t)i * Mmax;
+        return SMEM_ROWS ? rows + (size_t)(i / CL) * Mmax : rows + (size_t)i * Mmax;
     };
     double *brefl = refl + (size_t)b * Mmax * Mmax;
     double *btau = tau + (size_t)b * Mmax, *btd = td + (size_t)b * Mmax, *bte = te + (size_t)b * Mmax;
+    const int nown = (M - rank + CL - 1) / CL;         // owned rows li * CL + rank < M
+
+    // rows i >= rmin: B_ij -= v_i w_j + w_i v_j for j >= rmin (when upd), and
+    // uu = sum_{j >= rmin} B_ij c_j on the updated entries (c_rmin must be 0 or part of the sum)
+    auto fused = [&](int rmin, const double *cv, bool upd) {
+        const int wq = warp - 1, nwq = nwarps - 1;
+        const int lfirst = (rmin - rank + CL - 1) / CL;
+        for (int t0 = lfirst + wq; t0 < nown; t0 += nwq * G) {
+            double *rp[G];
+            double vi[G], wi[G], acc[G];
+            int cnt = 0;
+#pragma unroll
+            for (int g = 0; g < G; g++) {
+                const int li = t0 + nwq * g;
+                const bool ok = li < nown;
+                const int i = ok ? li * CL + rank : rank;
+                rp[g] = rowp(i);
+                vi[g] = ok ? hv[i] : 0.0;
+                wi[g] = ok ? wv[i] : 0.0;
+                acc[g] = 0.0;
+                cnt += ok ? 1 : 0;
+            }
+            for (int j = rmin + lane; j < M; j += 32) {
+                const double vj = hv[j], wj = wv[j], cj = cv[j];
+#pragma unroll
+                for (int g = 0; g < G; g++) {
+                    if (g < cnt) {
+                        double bb = rp[g][j];
+                        if (upd) {
+                            bb = fma(-vi[g], wj, fma(-wi[g], vj, bb));
+                            rp[g][j] = bb;
+                        }
+                        acc[g] = fma(bb, cj, acc[g]);
+                    }
+                }
+            }
+            // sums over the 32 lanes: halve the rows held per lane at offsets 16, 8, 4 (lane
+            // ends with row (lane >> 2) & 7), then plain butterflies over the last two lane bits
+#pragma unroll
+            for (int h = 0; h < 4; h++) {
+                const bool up = (lane & 16) != 0;
+                const double send = up ? acc[h] : acc[h + 4], keep = up ? acc[h + 4] : acc[h];
+                acc[h] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+            }
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const bool up = (lane & 8) != 0;
+                const double send = up ? acc[h] : acc[h + 2], keep = up ? acc[h + 2] : acc[h];
+                acc[h] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+            }
+            {
+                const bool up = (lane & 4) != 0;
+                const double send = up ? acc[0] : acc[1], keep = up ? acc[1] : acc[0];
+                acc[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+            }
+            acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 2);
+            acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
+            const int g = (lane >> 2) & 7;
+            if ((lane & 3) == 0 && g < cnt) uu[t0 + nwq * g] = acc[0];
+        }
+    };
 
     // load owned rows of B = A[s0:s0+M, s0:s0+M]
     for (int i = rank + warp * CL; i < M; i += nwarps * CL) {
@@ -114,99 +215,81 @@ k_tridiag(const double *__restrict__ A, int64_t N, const int32_t *__restrict__ p
         double *dst = rowp(i);
         for (int j = lane; j < M; j += 32) dst[j] = src[j];
     }
+    for (int j = tid; j < Mmax; j += blockDim.x) { hv[j] = 0.0; wv[j] = 0.0; }
     // every CTA of the cluster must be running before any distributed-shared-memory access
     cluster.sync();
-    // broadcast column 0 (rows >= 1) into every CTA's vbuf
+    // column 0 (entries >= 1) into every CTA
     for (int i = rank + tid * CL; i < M; i += blockDim.x * CL) {
         if (i < 1) continue;
-        double v = rowp(i)[0];
-        for (int r = 0; r < CL; r++) cluster.map_shared_rank(vbuf, r)[i] = v;
+        const double v = rowp(i)[0];
+        for (int r = 0; r < CL; r++) cluster.map_shared_rank(cbuf, r)[i] = v;
     }
     cluster.sync();
+    // u = B x for step 0 and its scalars
+    if (warp == 0) {
+        if (M >= 3) householder_scalars(cbuf, 0, M, lane, sc);
+    } else {
+        fused(1, cbuf, false);
+    }
+    __syncthreads();
 
     for (int k = 0; k + 2 < M; k++) {
-        // (a) Householder vector of column k: scalars by warp 0 (identical in every CTA)
-        if (warp == 0) {
-            const double x0 = vbuf[k + 1];
-            double t2 = 0.0;
-            for (int i = k + 2 + lane; i < M; i += 32) t2 = fma(vbuf[i], vbuf[i], t2);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) t2 += __shfl_xor_sync(0xffffffffu, t2, o);
-            double beta = 0.0, alpha = x0, v0 = 0.0;
-            if (t2 != 0.0) {
-                const double nn = fma(x0, x0, t2);
-                const double xn = nn * scaled_rsqrt(nn);
-                alpha = (x0 >= 0.0) ? -xn : xn;
-                v0 = x0 - alpha;
-                beta = 2.0 * scaled_rcp(fma(v0, v0, t2));
-            }
-            if (lane == 0) { sc[0] = beta; sc[1] = alpha; sc[2] = v0; }
-        }
-        __syncthreads();
+        const int par = k & 1, n1 = k + 1;
         const double beta = sc[0], alpha = sc[1], v0 = sc[2];
-        for (int i = k + 1 + tid; i < M; i += blockDim.x) hv[i] = (beta != 0.0) ? ((i == k + 1) ? v0 : vbuf[i]) : 0.0;
+        double *pb = pbuf + par * Mmax, *rb = rowbuf + par * Mmax, *pp = pvp + par * 32;
+        // S1
+        for (int j = n1 + tid; j < M; j += blockDim.x) hv[j] = (beta != 0.0) ? ((j == n1) ? v0 : cbuf[j]) : 0.0;
         if (rank == 0) {
             if (tid == 0) { bte[k] = alpha; btau[k] = beta; }
             double *rr = brefl + (size_t)k * Mmax;
-            for (int i = k + 1 + tid; i < M; i += blockDim.x)
-                rr[i] = (beta != 0.0) ? ((i == k + 1) ? v0 : vbuf[i]) : 0.0;
+            for (int j = n1 + tid; j < M; j += blockDim.x) rr[j] = (beta != 0.0) ? ((j == n1) ? v0 : cbuf[j]) : 0.0;
         }
         if (k % CL == rank && tid == 0) btd[k] = rowp(k)[k];
-        __syncthreads();
-        // (b) p_i = beta * B22[i, :] . v for owned rows i > k, four threads per row, broadcast
-        if (beta != 0.0) {
-            const int part = tid & 3;
-            for (int li0 = 0; li0 < R; li0 += blockDim.x >> 2) {   // same trip count in every lane
-                const int li = li0 + (tid >> 2);
+        if (n1 % CL == rank) {                          // row k+1 (entries > k+1) to every CTA
+            const double *rr = rowp(n1);
+            for (int j = n1 + 1 + tid; j < M; j += blockDim.x) {
+                const double x = rr[j];
+                for (int r = 0; r < CL; r++) cluster.map_shared_rank(rb, r)[j] = x;
+            }
+        }
+        if (warp == 0) {
+            double part = 0.0;
+            for (int li = (n1 - rank + CL - 1) / CL + lane; li < nown; li += 32) {
                 const int i = li * CL + rank;
-                double a0 = 0.0, a1 = 0.0;
-                if (li < R && i > k && i < M) {
-                    const double *ri = rowp(i);
-                    int l = k + 1 + part;
-                    for (; l + 4 < M; l += 8) {
-                        a0 = fma(ri[l], hv[l], a0);
-                        a1 = fma(ri[l + 4], hv[l + 4], a1);
-                    }
-                    if (l < M) a0 = fma(ri[l], hv[l], a0);
-                }
-                double acc = a0 + a1;
-                acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-                acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-                if (li < R && i > k && i < M)
-                    for (int r = part; r < CL; r += 4) cluster.map_shared_rank(pbuf, r)[i] = beta * acc;
+                const double p = beta * fma(-alpha, rowp(i)[n1], uu[li]);
+                const double vi = (beta != 0.0) ? ((i == n1) ? v0 : cbuf[i]) : 0.0;
+                part = fma(p, vi, part);
+                for (int r = 0; r < CL; r++) cluster.map_shared_rank(pb, r)[i] = p;
             }
-        }
-        cluster.sync();
-        if (beta != 0.0) {
-            // (c) w = p - (beta p.v / 2) v (p.v by warp 0); B22 -= v w^T + w v^T on owned rows
-            if (warp == 0) {
-                double pv = 0.0;
-                for (int i = k + 1 + lane; i < M; i += 32) pv = fma(pbuf[i], hv[i], pv);
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
-                if (lane == 0) sc[3] = 0.5 * beta * pv;
-            }
-            __syncthreads();
-            const double Kc = sc[3];
-            for (int i = k + 1 + tid; i < M; i += blockDim.x) wv[i] = fma(-Kc, hv[i], pbuf[i]);
-            __syncthreads();
-            const int first = k + 1 + ((rank - (k + 1)) % CL + CL) % CL;
-            for (int i = first + warp * CL; i < M; i += nwarps * CL) {
-                double *ri = rowp(i);
-                const double hi = hv[i], wi = wv[i];
-                for (int j = k + 1 + lane; j < M; j += 32) ri[j] = fma(-hi, wv[j], fma(-wi, hv[j], ri[j]));
-            }
-            __syncthreads();
-        }
-        // (d) broadcast column k+1 (rows >= k+2) for the next step
-        {
-            const int first = k + 2 + ((rank - (k + 2)) % CL + CL) % CL;
-            for (int i = first + tid * CL; i < M; i += blockDim.x * CL) {
-                double v = rowp(i)[k + 1];
-                for (int r = 0; r < CL; r++) cluster.map_shared_rank(vbuf, r)[i] = v;
-            }
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            if (lane < CL) cluster.map_shared_rank(pp, lane)[rank] = part;
         }
         cluster.sync();
+        // S2 (the partial sums are added in the same order in every thread of every CTA)
+        double pv = (lane < CL) ? pp[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
+        const double Kc = 0.5 * beta * pv;
+        const double vk1 = hv[n1];
+        const double wk1 = fma(-Kc, vk1, pb[n1]);
+        for (int j = n1 + tid; j < M; j += blockDim.x) {
+            const double vj = hv[j];
+            const double wj = fma(-Kc, vj, pb[j]);
+            wv[j] = wj;
+            nbuf[j] = (j == n1) ? 0.0 : fma(-vk1, wj, fma(-wk1, vj, rb[j]));
+        }
+        __syncthreads();
+        // S3
+        if (warp == 0) {
+            if (k + 3 < M) householder_scalars(nbuf, n1, M, lane, sc);
+        } else {
+            fused(n1, nbuf, true);
+        }
+        __syncthreads();
+        double *t = cbuf;
+        cbuf = nbuf;
+        nbuf = t;
     }
     // trailing 2x2 (or 1x1)
     if (tid == 0) {
@@ -218,7 +301,15 @@ k_tridiag(const double *__restrict__ A, int64_t N, const int32_t *__restrict__ p
         }
         if (rank == 0) { bte[M - 1] = 0.0; if (M >= 2) btau[M - 2] = 0.0; btau[M - 1] = 0.0; }
     }
-    cluster.sync();   // keep every CTA's shared memory alive until remote writes are done
+    cluster.sync();   // no CTA leaves while another may still address its shared memory
+}
+
+size_t tri_smem_bytes(int Mmax, int CL, bool rows_in_smem)
+{
+    const size_t R = (size_t)((Mmax + CL - 1) / CL);
+    size_t d = (size_t)8 * Mmax + R + 64 + 16;
+    if (rows_in_smem) d += R * (size_t)Mmax;
+    return d * sizeof(double);
 }
 
 // ---- blocked reduction (mixed forms) ----------------------------------------------------------
@@ -846,12 +937,11 @@ cudaError_t select_tridiag_cluster(pfsm_handle_s *h, size_t smem_cap)
     bool best_smem = false;
     for (int cl = 16; cl >= 2; cl--) {
         const size_t R = (size_t)((Mx + cl - 1) / cl);
-        const size_t srows = R * (size_t)(Mx + 2) * sizeof(double) + (size_t)(4 * Mx + 64) * sizeof(double);
-        const bool in_smem = srows <= smem_cap;
-        const size_t smem = in_smem ? srows : (size_t)(4 * Mx + 64) * sizeof(double);
+        const bool in_smem = tri_smem_bytes(Mx, cl, true) <= smem_cap;
+        const size_t smem = tri_smem_bytes(Mx, cl, in_smem);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(nb * cl));
-        cfg.blockDim = dim3(kTriThreads);
+        cfg.blockDim = dim3(kTriLaThreads);
         cfg.dynamicSmemBytes = smem;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -948,11 +1038,8 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
     } else {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(nb * CL));
-        cfg.blockDim = dim3(kTriThreads);
-        const int R = (Mmax + CL - 1) / CL;
-        size_t smem = (size_t)(4 * Mmax + 64) * sizeof(double);
-        if (h->rows_in_smem) smem += (size_t)R * (Mmax + 2) * sizeof(double);
-        cfg.dynamicSmemBytes = smem;
+        cfg.blockDim = dim3(kTriLaThreads);
+        cfg.dynamicSmemBytes = tri_smem_bytes(Mmax, CL, h->rows_in_smem);
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
