@@ -438,6 +438,8 @@ size_t tc_smem_bytes()
     return (size_t)tc::Cfg<KIND>::STAGES * tc::Cfg<KIND>::STAGE_BYTES + 1024 + 256 + 2 * tc::BN * 4 + 128 * tc::EBP * 8;
 }
 
+}  // namespace
+
 int sm_count()
 {
     static int n = 0;
@@ -448,8 +450,6 @@ int sm_count()
     }
     return n;
 }
-
-}  // namespace
 
 cudaError_t configure_tc_kernels()
 {

@@ -28,6 +28,7 @@ namespace pfsm {
 
 constexpr int kTriThreads = 256;      // blocked panel kernel
 constexpr int kTriLaThreads = 288;    // k_tridiag: warp 0 + eight warps (two per sub-partition)
+constexpr size_t kInvSmemCap = 200 * 1024;  // k_inverse_iter: shared memory for the lanes' vectors
 
 __device__ __forceinline__ double block_sum(double v, double *red)
 {
@@ -745,13 +746,16 @@ __device__ __forceinline__ double hash_unit(uint32_t a, uint32_t b, uint32_t c)
     return ((double)(z >> 11) * 0x1.0p-53) * 2.0 - 1.0;   // (-1, 1)
 }
 
-// Grid (ceil(mmax / 32), nb), 32 threads: lane t computes the unit eigenvector of T_b for the
-// selected eigenvalue t by two inverse-iteration solves with a pivoted tridiagonal LU of
-// T - lambda I (reciprocal pivots clamped to |pivot| >= eps ||T||). Members of a cluster
-// (consecutive selected eigenvalues closer than gaptol) are computed one after another by the
-// cluster's first lane and orthogonalised against each other (modified Gram-Schmidt) after every
-// solve. Per-lane work arrays are interleaved across lanes (element i of lane t at i * stride + t)
-// so that the sequential sweeps issue coalesced loads.
+// Grid (ceil(mmax / L), nb), L threads (L = 32, fewer for windows whose vectors would not fit in
+// shared memory): lane t computes the unit eigenvector of T_b for the selected eigenvalue t by two
+// inverse-iteration solves with a pivoted tridiagonal LU of T - lambda I (reciprocal pivots clamped
+// to |pivot| >= eps ||T||). Members of a cluster (consecutive selected eigenvalues closer than
+// gaptol) are computed one after another by the cluster's first lane and orthogonalised against
+// each other (modified Gram-Schmidt) after every solve. The LU factors are written once per shift
+// into global work arrays interleaved across lanes (element i of lane t at i * stride + t:
+// coalesced), and only read by the solves; the vector z, which every sweep reads and rewrites,
+// lives in shared memory (element i of lane t at i * L + t), so no load of z waits behind an L2
+// round trip of the store before it.
 __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int32_t Mmax,
                                int32_t mmax, const double *__restrict__ td,
                                const double *__restrict__ te, const double *__restrict__ sel_val,
@@ -775,7 +779,9 @@ __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int
     double *__restrict__ u1 = work + stride * Mmax + me;
     double *__restrict__ u2 = work + 2 * stride * Mmax + me;
     double *__restrict__ lm = work + 3 * stride * Mmax + me; // multipliers, sign bit = row swap
-    double *__restrict__ z = work + 4 * stride * Mmax + me;
+    extern __shared__ double zsm[];
+    const int zst = blockDim.x;
+    double *z = zsm + threadIdx.x;                          // element i at z[i * zst]
     const double pert = DBL_EPSILON * fmax(tnorm, DBL_MIN);
     int last = t;
     while (last + 1 < mb && lam[last + 1] - lam[last] < gaptol) last++;
@@ -804,7 +810,7 @@ __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int
         u0[(size_t)(M - 1) * stride] = fast_rcp(fabs(p) >= pert ? p : (p < 0.0 ? -pert : pert));
         u1[(size_t)(M - 1) * stride] = 0.0;      // read (times zero) by the back substitution
         u2[(size_t)(M - 1) * stride] = 0.0;
-        for (int i = 0; i < M; i++) z[i * stride] = hash_unit(b, j, i);
+        for (int i = 0; i < M; i++) z[i * zst] = hash_unit(b, j, i);
         for (int it = 0; it < 2; it++) {
             // forward: replay the row operations on the right-hand side
             double zi = z[0];
@@ -813,18 +819,18 @@ __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int
                 const double lraw = lm[i * stride];
                 const bool swp = (__double_as_longlong(lraw) & 1ll) != 0;
                 const double l = lraw;       // the flag bit perturbs l by at most 1 ulp
-                const double zn = z[(i + 1) * stride];
-                if (swp) { z[i * stride] = zn; zi = fma(-l, zn, zi); }
-                else { z[i * stride] = zi; zi = fma(-l, zi, zn); }
+                const double zn = z[(i + 1) * zst];
+                if (swp) { z[i * zst] = zn; zi = fma(-l, zn, zi); }
+                else { z[i * zst] = zi; zi = fma(-l, zi, zn); }
             }
-            z[(size_t)(M - 1) * stride] = zi;
+            z[(size_t)(M - 1) * zst] = zi;
             // back substitution with the three upper diagonals
             double z1 = 0.0, z2 = 0.0;
 #pragma unroll 4
             for (int i = M - 1; i >= 0; i--) {
-                const double acc = fma(-u2[i * stride], z2, fma(-u1[i * stride], z1, z[i * stride]));
+                const double acc = fma(-u2[i * stride], z2, fma(-u1[i * stride], z1, z[i * zst]));
                 const double zi2 = acc * u0[i * stride];
-                z[i * stride] = zi2;
+                z[i * zst] = zi2;
                 z2 = z1;
                 z1 = zi2;
             }
@@ -832,91 +838,195 @@ __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int
             for (int c = t; c < j; c++) {
                 const double *zc = sel_vec + ((size_t)b * mmax + c) * Mmax;
                 double dot = 0.0;
-                for (int i = 0; i < M; i++) dot = fma(zc[i], z[i * stride], dot);
-                for (int i = 0; i < M; i++) z[i * stride] = fma(-dot, zc[i], z[i * stride]);
+                for (int i = 0; i < M; i++) dot = fma(zc[i], z[i * zst], dot);
+                for (int i = 0; i < M; i++) z[i * zst] = fma(-dot, zc[i], z[i * zst]);
             }
-            double mx = 0.0;
-            for (int i = 0; i < M; i++) mx = fmax(mx, fabs(z[i * stride]));
+            // four independent chains: a dependent FP64 instruction waits ~64 cycles on B300
+            double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+            int i4 = 0;
+            for (; i4 + 3 < M; i4 += 4) {
+                m0 = fmax(m0, fabs(z[i4 * zst]));
+                m1 = fmax(m1, fabs(z[(i4 + 1) * zst]));
+                m2 = fmax(m2, fabs(z[(i4 + 2) * zst]));
+                m3 = fmax(m3, fabs(z[(i4 + 3) * zst]));
+            }
+            for (; i4 < M; i4++) m0 = fmax(m0, fabs(z[i4 * zst]));
+            const double mx = fmax(fmax(m0, m1), fmax(m2, m3));
             if (mx == 0.0 || !isfinite(mx)) {
-                for (int i = 0; i < M; i++) z[i * stride] = hash_unit(b, j + 7919, i + it);
+                for (int i = 0; i < M; i++) z[i * zst] = hash_unit(b, j + 7919, i + it);
                 continue;
             }
             const double imx = fast_rcp(mx);
-            double nrm = 0.0;
-            for (int i = 0; i < M; i++) { const double v = z[i * stride] * imx; z[i * stride] = v; nrm = fma(v, v, nrm); }
-            const double inr = rsqrt(nrm);
-            for (int i = 0; i < M; i++) z[i * stride] *= inr;
+            double n0 = 0.0, n1 = 0.0, n2 = 0.0, n3 = 0.0;
+            for (i4 = 0; i4 + 3 < M; i4 += 4) {
+                const double v0 = z[i4 * zst] * imx, v1 = z[(i4 + 1) * zst] * imx;
+                const double v2 = z[(i4 + 2) * zst] * imx, v3 = z[(i4 + 3) * zst] * imx;
+                z[i4 * zst] = v0; z[(i4 + 1) * zst] = v1; z[(i4 + 2) * zst] = v2; z[(i4 + 3) * zst] = v3;
+                n0 = fma(v0, v0, n0); n1 = fma(v1, v1, n1); n2 = fma(v2, v2, n2); n3 = fma(v3, v3, n3);
+            }
+            for (; i4 < M; i4++) { const double v = z[i4 * zst] * imx; z[i4 * zst] = v; n0 = fma(v, v, n0); }
+            const double inr = rsqrt((n0 + n1) + (n2 + n3));
+            for (int i = 0; i < M; i++) z[i * zst] *= inr;
         }
         double *out = sel_vec + ((size_t)b * mmax + j) * Mmax;
-        for (int i = 0; i < M; i++) out[i] = z[i * stride];
+        for (int i = 0; i < M; i++) out[i] = z[i * zst];
     }
 }
 
-// One warp per start vector: y = H_0 H_1 ... H_{M-3} z, then the sign rule, zero padding to
-// length N, the shift eps and the step alpha. Grid (ceil(mmax / 8), nb), 256 threads.
-__global__ void k_backtransform(const int32_t *__restrict__ plan, int32_t nb, int64_t N,
-                                int32_t Mmax, int32_t mmax, const double *__restrict__ refl,
-                                const double *__restrict__ tau, const double *__restrict__ sel_val,
-                                const double *__restrict__ sel_vec, const double *__restrict__ gersh,
-                                double alpha_theta, double *__restrict__ X,
-                                double *__restrict__ eps, double *__restrict__ alpha)
+__device__ __forceinline__ void cp_async8(double *dst, const double *src)
 {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+
+// Back-transform y = H_0 H_1 ... H_{M-3} z of the selected eigenvectors z of T_b, then the sign
+// rule, zero padding to length N, the shift eps and the step alpha, written straight into X.
+// Grid (CTAs per window, nb), 128 threads: a CTA takes VPC = 4 NV (or fewer) consecutive vectors
+// of one window, warp w the vectors w, w+4, ... (NV per warp, lanes along the rows). The work is
+// the FP64 pipe's (2 (M - k) FMAs per reflector and vector), so the launch gives every SM at most
+// one CTA and every sub-partition at most NV vectors. The reflectors pass through shared memory in
+// double-buffered chunks of KC rows (cp.async, shared by the CTA's four warps), and the NV dot
+// products of a reflector are summed over the lanes by one transpose-reduce (6 FP64 adds for up to
+// four vectors instead of 5 per vector). Unused vector slots hold zeros and are computed but not
+// stored.
+template <int NV>
+__global__ void __launch_bounds__(128, 1)
+k_backtransform(const int32_t *__restrict__ plan, int32_t nb, int64_t N, int32_t Mmax, int32_t mmax,
+                const double *__restrict__ refl, const double *__restrict__ tau,
+                const double *__restrict__ sel_val, const double *__restrict__ sel_vec,
+                const double *__restrict__ gersh, double alpha_theta, int vpc, int kc,
+                double *__restrict__ X, double *__restrict__ eps, double *__restrict__ alpha)
+{
+    static_assert(NV >= 1 && NV <= 4, "at most four vectors per warp");
     const int b = blockIdx.y;
     const int k0 = plan[b], mb = plan[nb + b], s = plan[2 * nb + b], M = plan[3 * nb + b];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t = blockIdx.x * (blockDim.x >> 5) + warp;
-    extern __shared__ double smz[];
-    double *z = smz + (size_t)warp * Mmax;
-    if (t >= mb) return;
-    const double *src = sel_vec + ((size_t)b * mmax + t) * Mmax;
-    for (int i = lane; i < M; i += 32) z[i] = src[i];
-    __syncwarp();
+    const int tbeg = blockIdx.x * vpc;
+    if (tbeg >= mb) return;                               // whole CTA
+    const int nvc = min(vpc, mb - tbeg);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    extern __shared__ double smb[];
+    double *zs = smb;                                     // [4 NV][Mmax] vector slots (slot w + 4 j)
+    double *ts = zs + (size_t)4 * NV * Mmax;              // [Mmax] tau
+    double *rs = ts + Mmax;                               // [2][kc][Mmax] reflector chunks
     const double *brefl = refl + (size_t)b * Mmax * Mmax;
-    const double *btau = tau + (size_t)b * Mmax;
-    for (int k = M - 3; k >= 0; k--) {
-        const double bk = btau[k];
-        if (bk == 0.0) continue;
-        const double *v = brefl + (size_t)k * Mmax;
-        double dot = 0.0;
-        for (int i = k + 1 + lane; i < M; i += 32) dot += v[i] * z[i];
+    for (int q = 0; q < 4 * NV; q++) {
+        const double *src = sel_vec + ((size_t)b * mmax + tbeg + q) * Mmax;
+        for (int i = tid; i < M; i += blockDim.x) zs[(size_t)q * Mmax + i] = (q < nvc) ? src[i] : 0.0;
+    }
+    for (int i = tid; i < M; i += blockDim.x) ts[i] = tau[(size_t)b * Mmax + i];
+    double *z[NV];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-        const double f = bk * dot;
-        for (int i = k + 1 + lane; i < M; i += 32) z[i] -= f * v[i];
-        __syncwarp();
+    for (int j = 0; j < NV; j++) z[j] = zs + (size_t)(warp + 4 * j) * Mmax;
+    const int nk = M - 2;                                 // reflectors k = M-3 .. 0
+    const int nch = nk > 0 ? (nk + kc - 1) / kc : 0;
+    auto issue = [&](int c) {
+        double *dst = rs + (size_t)(c & 1) * kc * Mmax;
+        const int khi = M - 3 - c * kc;
+        for (int r = 0; r < kc; r++) {
+            const int k = khi - r;
+            if (k < 0) break;
+            for (int i = k + 1 + tid; i < M; i += blockDim.x) cp_async8(dst + (size_t)r * Mmax + i, brefl + (size_t)k * Mmax + i);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if (nch > 0) issue(0);
+    for (int c = 0; c < nch; c++) {
+        if (c + 1 < nch) {
+            issue(c + 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();
+        const double *cb = rs + (size_t)(c & 1) * kc * Mmax;
+        const int khi = M - 3 - c * kc;
+        for (int r = 0; r < kc; r++) {
+            const int k = khi - r;
+            if (k < 0) break;
+            const double bk = ts[k];
+            if (bk == 0.0) continue;
+            const double *v = cb + (size_t)r * Mmax;
+            double a[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int i = k + 1 + lane; i < M; i += 32) {
+                const double vi = v[i];
+#pragma unroll
+                for (int j = 0; j < NV; j++) a[j] = fma(vi, z[j][i], a[j]);
+            }
+            // lanes end with the sum of vector (lane >> 3) & 3: halve at offsets 16 and 8, then
+            // butterflies over the lower three lane bits
+            {
+                const bool up = (lane & 16) != 0;
+                const double s0 = up ? a[0] : a[2], s1 = up ? a[1] : a[3];
+                const double k0v = up ? a[2] : a[0], k1v = up ? a[3] : a[1];
+                a[0] = k0v + __shfl_xor_sync(0xffffffffu, s0, 16);
+                a[1] = k1v + __shfl_xor_sync(0xffffffffu, s1, 16);
+            }
+            {
+                const bool up = (lane & 8) != 0;
+                const double s0 = up ? a[0] : a[1], k0v = up ? a[1] : a[0];
+                a[0] = k0v + __shfl_xor_sync(0xffffffffu, s0, 8);
+            }
+            a[0] += __shfl_xor_sync(0xffffffffu, a[0], 4);
+            a[0] += __shfl_xor_sync(0xffffffffu, a[0], 2);
+            a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
+            const double f = bk * a[0];
+            double fj[NV];
+#pragma unroll
+            for (int j = 0; j < NV; j++) fj[j] = __shfl_sync(0xffffffffu, f, 8 * j);
+            for (int i = k + 1 + lane; i < M; i += 32) {
+                const double vi = v[i];
+#pragma unroll
+                for (int j = 0; j < NV; j++) z[j][i] = fma(-fj[j], vi, z[j][i]);
+            }
+            __syncwarp();
+        }
+        __syncthreads();                                  // chunk c's buffer is reloaded next
     }
     // sign rule: home component positive when |y_home| >= 0.1, else the largest component
-    const int home = k0 - s + t;
-    double best = -1.0;
-    int arg = M;
-    for (int i = lane; i < M; i += 32) {
-        double a = fabs(z[i]);
-        if (a > best) { best = a; arg = i; }
-    }
+    const double glo = gersh[2 * N], ghi = gersh[2 * N + 1];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        double ob = __shfl_xor_sync(0xffffffffu, best, o);
-        int oa = __shfl_xor_sync(0xffffffffu, arg, o);
-        if (ob > best || (ob == best && oa < arg)) { best = ob; arg = oa; }
+    for (int j = 0; j < NV; j++) {
+        const int lt = warp + 4 * j;
+        if (lt >= nvc) break;                             // warp-uniform
+        const int t = tbeg + lt;
+        const double *zz = z[j];
+        const int home = k0 - s + t;
+        double best = -1.0;
+        int arg = M;
+        for (int i = lane; i < M; i += 32) {
+            const double av = fabs(zz[i]);
+            if (av > best) { best = av; arg = i; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
+            if (ob > best || (ob == best && oa < arg)) { best = ob; arg = oa; }
+        }
+        const double yh = zz[home];
+        const double ref = (fabs(yh) >= 0.1) ? yh : zz[arg];
+        const double flip = (ref < 0.0) ? -1.0 : 1.0;
+        const int64_t kg = k0 + t;
+        double *xr = X + kg * N;
+        for (int64_t jj = lane; jj < N; jj += 32) {
+            const int64_t li = jj - s;
+            xr[jj] = (li >= 0 && li < M) ? flip * zz[li] : 0.0;
+        }
+        if (lane == 0) {
+            const double lam = sel_val[(size_t)b * mmax + t];
+            const double dmax = fmax(ghi - lam, lam - glo);
+            const double av = alpha_theta / (dmax * dmax);
+            const double cap = 1.0 - 0x1.0p-20;
+            eps[kg] = lam;
+            alpha[kg] = (av < cap) ? av : cap;
+        }
     }
-    const double yh = z[home];
-    const double ref = (fabs(yh) >= 0.1) ? yh : z[arg];
-    const double flip = (ref < 0.0) ? -1.0 : 1.0;
-    const int64_t kg = k0 + t;
-    double *xr = X + kg * N;
-    for (int64_t j = lane; j < N; j += 32) {
-        int64_t li = j - s;
-        xr[j] = (li >= 0 && li < M) ? flip * z[li] : 0.0;
-    }
-    if (lane == 0) {
-        const double lam = sel_val[(size_t)b * mmax + t];
-        const double glo = gersh[2 * N], ghi = gersh[2 * N + 1];
-        const double dmax = fmax(ghi - lam, lam - glo);
-        const double a = alpha_theta / (dmax * dmax);
-        const double cap = 1.0 - 0x1.0p-20;
-        eps[kg] = lam;
-        alpha[kg] = (a < cap) ? a : cap;
-    }
+}
+
+// Shared memory of k_backtransform<NV> with chunks of kc reflectors.
+size_t backtransform_smem(int Mmax, int nv, int kc)
+{
+    return ((size_t)4 * nv * Mmax + Mmax + (size_t)2 * kc * Mmax) * sizeof(double);
 }
 
 // Function attributes are process-wide while handles differ in window size, so every attribute
@@ -990,7 +1100,10 @@ cudaError_t configure_kernels(pfsm_handle_s *h)
     if ((e = set_max((const void *)k_tridiag_panel<24>)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_tridiag_panel<24>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
     if ((e = set_max((const void *)k_bisect)) != cudaSuccess) return e;
-    return set_max((const void *)k_backtransform);
+    if ((e = set_max((const void *)k_inverse_iter)) != cudaSuccess) return e;
+    if ((e = set_max((const void *)k_backtransform<1>)) != cudaSuccess) return e;
+    if ((e = set_max((const void *)k_backtransform<2>)) != cudaSuccess) return e;
+    return set_max((const void *)k_backtransform<3>);
 }
 
 cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
@@ -1071,20 +1184,40 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
     if (h->timing && (e0 = cudaEventRecord(h->sub_ev[1], st)) != cudaSuccess) return e0;
     // 3. inverse iteration
     {
-        dim3 grid((unsigned)((mmax + tpb - 1) / tpb), (unsigned)nb);
-        k_inverse_iter<<<grid, tpb, 0, st>>>(w.plan, nb, Mmax, mmax, w.td, w.te, w.sel_val, w.sel_vec, w.iiwork); g_launches++;
+        int lanes = tpb;
+        while (lanes > 1 && (size_t)lanes * Mmax * sizeof(double) > kInvSmemCap) lanes >>= 1;
+        dim3 grid((unsigned)((mmax + lanes - 1) / lanes), (unsigned)nb);
+        k_inverse_iter<<<grid, lanes, (size_t)lanes * Mmax * sizeof(double), st>>>(w.plan, nb, Mmax, mmax, w.td, w.te,
+                                                                                 w.sel_val, w.sel_vec, w.iiwork);
+        g_launches++;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     if (h->timing && (e0 = cudaEventRecord(h->sub_ev[2], st)) != cudaSuccess) return e0;
     // 4. back-transform + start vectors
     {
-        // one warp per vector, as many per CTA as shared memory holds (up to 8)
-        const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(227 * 1024) / ((size_t)Mmax * sizeof(double))));
-        dim3 grid((unsigned)((mmax + wpb - 1) / wpb), (unsigned)nb);
-        k_backtransform<<<grid, 32 * wpb, (size_t)wpb * Mmax * sizeof(double), st>>>(
-            w.plan, nb, h->N, Mmax, mmax, w.refl, w.tau, w.sel_val, w.sel_vec, w.gersh,
-            h->prm.alpha_theta, w.X, w.eps, w.alpha); g_launches++;
+        // CTAs per window: the SMs shared out over the windows (one CTA per SM), more when a
+        // window's vectors exceed what 4 warps x NV vectors take; NV and the reflector chunk KC
+        // as large as shared memory allows (NV <= 3, KC <= 16)
+        const size_t cap = kInvSmemCap;
+        int nv = 3, kc = 16;
+        while (nv > 1 && backtransform_smem(Mmax, nv, 1) > cap) nv--;
+        while (kc > 1 && backtransform_smem(Mmax, nv, kc) > cap) kc >>= 1;
+        const int per_win = std::max(1, sm_count() / nb);
+        int vpc = (mmax + per_win - 1) / per_win;
+        vpc = std::max(1, std::min(vpc, 4 * nv));
+        dim3 grid((unsigned)((mmax + vpc - 1) / vpc), (unsigned)nb);
+        const size_t smem = backtransform_smem(Mmax, nv, kc);
+        if (nv == 3)
+            k_backtransform<3><<<grid, 128, smem, st>>>(w.plan, nb, h->N, Mmax, mmax, w.refl, w.tau, w.sel_val, w.sel_vec,
+                                                     w.gersh, h->prm.alpha_theta, vpc, kc, w.X, w.eps, w.alpha);
+        else if (nv == 2)
+            k_backtransform<2><<<grid, 128, smem, st>>>(w.plan, nb, h->N, Mmax, mmax, w.refl, w.tau, w.sel_val, w.sel_vec,
+                                                     w.gersh, h->prm.alpha_theta, vpc, kc, w.X, w.eps, w.alpha);
+        else
+            k_backtransform<1><<<grid, 128, smem, st>>>(w.plan, nb, h->N, Mmax, mmax, w.refl, w.tau, w.sel_val, w.sel_vec,
+                                                     w.gersh, h->prm.alpha_theta, vpc, kc, w.X, w.eps, w.alpha);
+        g_launches++;
         return cudaGetLastError();
     }
 }

@@ -184,6 +184,7 @@ struct OzParams {
     int32_t *status;
 };
 cudaError_t configure_oz_kernels();
+int sm_count();                     // multiprocessors of the current device (cached)
 cudaError_t launch_oz_split(const double *src, int64_t rows, int64_t cols, int64_t ld, const SliceBuf &dst,
                             int32_t *exps, cudaStream_t st, bool zero_diag = false, double *d = nullptr);
 cudaError_t launch_oz_split_f32(const float *src, int64_t rows, int64_t cols, int64_t ld, const SliceBuf &dst,
