@@ -46,8 +46,9 @@ DTYPES = {"fp64": "f64", "bf16": "bf16x3-split, f32 accumulate, f64 epilogue",
 # capture of the current kernel build on this workload, keyed by (kernel, precision); absent
 # when the kernel changed since the capture. Captures and commands: profiles/.
 TRAFFIC = {
-    # the window reduction is the same kernel and launch in every form (profiles/dram_traffic_*)
-    ("k_tridiag", "bf16"): 5886208, ("k_tridiag", "tf32"): 5886208, ("k_tridiag", "fp64"): 5886208,
+    # the window reduction is the same kernel and launch in every form (one cluster barrier per
+    # step; profiles/window_eigensolve_diamond1280_full.md)
+    ("k_tridiag", "bf16"): 5901312, ("k_tridiag", "tf32"): 5901312, ("k_tridiag", "fp64"): 5901312,
     # Eq. 11 split products, mean over the K = 3 iterations' six launches
     ("k_gemm_tc", "bf16"): (12921088 + 5 * 46013184) // 6,
 }

@@ -881,10 +881,10 @@ __device__ __forceinline__ void cp_async8(double *dst, const double *src)
 
 // Back-transform y = H_0 H_1 ... H_{M-3} z of the selected eigenvectors z of T_b, then the sign
 // rule, zero padding to length N, the shift eps and the step alpha, written straight into X.
-// Grid (CTAs per window, nb), 128 threads: a CTA takes VPC = 4 NV (or fewer) consecutive vectors
-// of one window, warp w the vectors w, w+4, ... (NV per warp, lanes along the rows). The work is
-// the FP64 pipe's (2 (M - k) FMAs per reflector and vector), so the launch gives every SM at most
-// one CTA and every sub-partition at most NV vectors. The reflectors pass through shared memory in
+// One-dimensional grid, 128 threads: window b owns ceil(m_b / vpc) consecutive CTAs, each taking
+// up to vpc <= 4 NV consecutive vectors of the window, warp w the vectors w, w+4, ... (NV per warp,
+// lanes along the rows). The work is the FP64 pipe's (2 (M - k) FMAs per reflector and vector),
+// so the launch gives every SM at most one CTA and every sub-partition at most NV vectors. The reflectors pass through shared memory in
 // double-buffered chunks of KC rows (cp.async, shared by the CTA's four warps), and the NV dot
 // products of a reflector are summed over the lanes by one transpose-reduce (6 FP64 adds for up to
 // four vectors instead of 5 per vector). Unused vector slots hold zeros and are computed but not
@@ -898,10 +898,15 @@ k_backtransform(const int32_t *__restrict__ plan, int32_t nb, int64_t N, int32_t
                 double *__restrict__ X, double *__restrict__ eps, double *__restrict__ alpha)
 {
     static_assert(NV >= 1 && NV <= 4, "at most four vectors per warp");
-    const int b = blockIdx.y;
+    // CTA c takes chunk c - first_b of window b, where window b owns ceil(m_b / vpc) chunks
+    int b = -1, tbeg = 0;
+    for (int q = 0, first = 0; q < nb; q++) {
+        const int cnt = (plan[nb + q] + vpc - 1) / vpc;
+        if ((int)blockIdx.x < first + cnt) { b = q; tbeg = ((int)blockIdx.x - first) * vpc; break; }
+        first += cnt;
+    }
+    if (b < 0) return;                                    // whole CTA: beyond the last chunk
     const int k0 = plan[b], mb = plan[nb + b], s = plan[2 * nb + b], M = plan[3 * nb + b];
-    const int tbeg = blockIdx.x * vpc;
-    if (tbeg >= mb) return;                               // whole CTA
     const int nvc = min(vpc, mb - tbeg);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     extern __shared__ double smb[];
@@ -1196,17 +1201,16 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
     if (h->timing && (e0 = cudaEventRecord(h->sub_ev[2], st)) != cudaSuccess) return e0;
     // 4. back-transform + start vectors
     {
-        // CTAs per window: the SMs shared out over the windows (one CTA per SM), more when a
-        // window's vectors exceed what 4 warps x NV vectors take; NV and the reflector chunk KC
-        // as large as shared memory allows (NV <= 3, KC <= 16)
+        // vectors per CTA: the fewest for which sum_b ceil(m_b / vpc) <= N / vpc + nb CTAs fit
+        // one per SM, capped at what 4 warps x NV vectors take; NV and the reflector chunk KC as
+        // large as shared memory allows (NV <= 3, KC <= 16)
         const size_t cap = kInvSmemCap;
         int nv = 3, kc = 16;
         while (nv > 1 && backtransform_smem(Mmax, nv, 1) > cap) nv--;
         while (kc > 1 && backtransform_smem(Mmax, nv, kc) > cap) kc >>= 1;
-        const int per_win = std::max(1, sm_count() / nb);
-        int vpc = (mmax + per_win - 1) / per_win;
-        vpc = std::max(1, std::min(vpc, 4 * nv));
-        dim3 grid((unsigned)((mmax + vpc - 1) / vpc), (unsigned)nb);
+        const int64_t slots = std::max<int64_t>(1, (int64_t)sm_count() - nb);
+        int vpc = (int)std::min<int64_t>(4 * nv, std::max<int64_t>(1, (h->N + slots - 1) / slots));
+        dim3 grid((unsigned)((h->N + vpc - 1) / vpc + nb));
         const size_t smem = backtransform_smem(Mmax, nv, kc);
         if (nv == 3)
             k_backtransform<3><<<grid, 128, smem, st>>>(w.plan, nb, h->N, Mmax, mmax, w.refl, w.tau, w.sel_val, w.sel_vec,
