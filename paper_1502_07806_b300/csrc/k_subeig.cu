@@ -566,39 +566,62 @@ k_tridiag_panel(const double *__restrict__ A, int64_t N, const int32_t *__restri
 
 // ---- tridiagonal helpers -------------------------------------------------------------------
 
-// Number of eigenvalues of the tridiagonal T (diagonal d, squared off-diagonal e2) below x, as
-// the number of sign changes in the leading principal minors p_i of T - xI:
-//   p_-1 = 1, p_0 = d_0 - x, p_i = (d_i - x) p_{i-1} - e2_{i-1} p_{i-2}
-// (Sturm sequence). On B300 every warp-wide FP64 instruction costs ~64 cycles of its SM
-// sub-partition, so the step uses three (sub, mul, fma) and does signs, zero tests and the
-// power-of-two rescaling that keeps magnitudes in range on the integer bit patterns. An exact
-// zero minor takes the sign opposite to its predecessor, as the ratio form's -pivmin does.
-__device__ __forceinline__ int sturm3(const double *d, const double *e2, int M, double x)
+// ---- Sturm counts and Newton steps on a tridiagonal scaled to |d_i| <= 1, e2_i <= 1 -------------
+//
+// Number of eigenvalues of T (diagonal d, squared off-diagonal e2) below x, as the number of sign
+// changes in the leading principal minors p_i of T - xI:
+//   p_-1 = 1, p_0 = d_0 - x, p_i = (d_i - x) p_{i-1} - e2_{i-1} p_{i-2}   (Sturm sequence).
+// A dependent FP64 instruction takes ~64 cycles on B300, so only the DFMA is on the step's
+// dependent path: signs, the exact-zero rule (a zero minor takes the sign opposite to its
+// predecessor, as the ratio form's -pivmin does) and the exponents are 32-bit integer work on the
+// high words. |d_i - x| is clamped below at 2^-60 (a perturbation of T far below its rounding),
+// which bounds how fast the minors can shrink (2^-113 per step, cancellation included); with the
+// growth bounded by 4x per step, a renormalisation every four steps (both minors times the power
+// of two that brings the larger to 2^0 once it leaves [2^-400, 2^400]) keeps every value normal.
+__device__ __forceinline__ double clamp_dx(double dx)
 {
-    double pp = 1.0, pc = d[0] - x;
-    long long bc = __double_as_longlong(pc);
-    if ((bc << 1) == 0) { pc = -0x1.0p-60; bc = __double_as_longlong(pc); }
-    int cnt = bc < 0;
-    for (int i = 1; i < M; i++) {
-        double pn = fma(d[i] - x, pc, -e2[i - 1] * pp);
-        long long bn = __double_as_longlong(pn);
-        if ((bn << 1) == 0) {                       // exact zero: opposite sign, tiny magnitude
-            pn = __longlong_as_double((bc & 0x7FFFFFFFFFFFFFFFll) ^ (~bc & (1ll << 63))) * 0x1.0p-60;
-            bn = __double_as_longlong(pn);
-        }
-        cnt += (int)(((unsigned long long)(bn ^ bc)) >> 63);
-        const int ex = (int)((bn >> 52) & 0x7FF);
-        if (ex > 1023 + 512 || ex < 1023 - 512) {
-            const double sc = __longlong_as_double((long long)(2046 - ex) << 52);   // 2^(1023 - ex)
-            pn *= sc;
-            pc *= sc;
-            bn = __double_as_longlong(pn);
-        }
-        pp = pc;
-        pc = pn;
-        bc = bn;
+    const int hi = __double2hiint(dx);
+    return (((hi >> 20) & 0x7FF) < 1023 - 60) ? ((hi < 0) ? -0x1.0p-60 : 0x1.0p-60) : dx;
+}
+
+__device__ __forceinline__ int exp_of(double v) { return (__double2hiint(v) >> 20) & 0x7FF; }
+
+template <int NP>
+__device__ __forceinline__ void sturm_counts(const double *d, const double *e2, int M, const double (&x)[NP],
+                                             int (&cnt)[NP])
+{
+    double pp[NP], pc[NP];
+#pragma unroll
+    for (int j = 0; j < NP; j++) {
+        pp[j] = 1.0;
+        pc[j] = clamp_dx(d[0] - x[j]);
+        cnt[j] = __double2hiint(pc[j]) < 0;
     }
-    return cnt;
+    for (int i = 1; i < M; i++) {
+        const double di = d[i], fi = e2[i - 1];
+#pragma unroll
+        for (int j = 0; j < NP; j++) {
+            const double dx = clamp_dx(di - x[j]);
+            double pn = fma(dx, pc[j], -fi * pp[j]);
+            const double alt = pc[j] * -0x1.0p-60;          // used when pn is exactly zero
+            const int hn = __double2hiint(pn);
+            pn = (((hn & 0x7FFFFFFF) | __double2loint(pn)) == 0) ? alt : pn;
+            cnt[j] += (int)((unsigned)(__double2hiint(pn) ^ __double2hiint(pc[j])) >> 31);
+            pp[j] = pc[j];
+            pc[j] = pn;
+        }
+        if ((i & 3) == 0) {
+#pragma unroll
+            for (int j = 0; j < NP; j++) {
+                const int em = max(exp_of(pc[j]), exp_of(pp[j]));
+                if (em > 1023 + 400 || em < 1023 - 400) {
+                    const double sc = __hiloint2double((2046 - em) << 20, 0);   // 2^(1023 - em)
+                    pc[j] *= sc;
+                    pp[j] *= sc;
+                }
+            }
+        }
+    }
 }
 
 __device__ __forceinline__ int sturm3f(const float *d, const float *e2, int M, float x)
@@ -629,80 +652,120 @@ __device__ __forceinline__ int sturm3f(const float *d, const float *e2, int M, f
     return cnt;
 }
 
-// Newton correction -p_M(x) / p_M'(x) for det(T - xI), from the three-term recurrence of the
-// minors and of their derivatives p_i' = (d_i - x) p_{i-1}' - p_{i-1} - e2_{i-1} p_{i-2}', both
-// rescaled together by powers of two.
+// Newton correction -p_M(x) / p_M'(x) for det(T - xI) (scaled T), from the three-term recurrence
+// of the minors and of their derivatives p_i' = (d_i - x) p_{i-1}' - p_{i-1} - e2_{i-1} p_{i-2}',
+// both renormalised together every four steps (same bounds as sturm_counts); one DFMA per chain
+// and step on the dependent path.
 __device__ __forceinline__ double newton_step(const double *d, const double *e2, int M, double x)
 {
-    double pp = 1.0, pc = d[0] - x, qp = 0.0, qc = -1.0;
+    double pp = 1.0, pc = clamp_dx(d[0] - x), qp = 0.0, qc = -1.0;
     for (int i = 1; i < M; i++) {
-        const double dx = d[i] - x, f = e2[i - 1];
+        const double dx = clamp_dx(d[i] - x), f = e2[i - 1];
         const double pn = fma(dx, pc, -f * pp);
         const double qn = fma(dx, qc, -fma(f, qp, pc));
-        const int ex = (int)((__double_as_longlong(pn) >> 52) & 0x7FF);
-        const int eq = (int)((__double_as_longlong(qn) >> 52) & 0x7FF);
-        const int em = ex > eq ? ex : eq;
         pp = pc; qp = qc; pc = pn; qc = qn;
-        if (em > 1023 + 512 || (em < 1023 - 512 && em > 0)) {
-            const double sc = __longlong_as_double((long long)(2046 - em) << 52);
-            pp *= sc; qp *= sc; pc *= sc; qc *= sc;
+        if ((i & 3) == 0) {
+            const int em = max(max(exp_of(pc), exp_of(pp)), max(exp_of(qc), exp_of(qp)));
+            if (em > 1023 + 400 || em < 1023 - 400) {
+                const double sc = __hiloint2double((2046 - em) << 20, 0);
+                pp *= sc; qp *= sc; pc *= sc; qc *= sc;
+            }
         }
     }
     return (qc != 0.0) ? -pc / qc : 0.0;
 }
 
-// One selected eigenvalue per lane, grid (ceil(mmax / 32), nb), 32 threads: the eigenvalue at
-// ascending position (k0 - s + t) of T_b. FP32 bisection (cheap on B300) brackets it to 8 FP32
-// ulps of ||T||; three FP64 Newton steps on det(T - xI) from the bracket's midpoint take it to
-// FP64 accuracy (quadratic convergence while |x - lambda| is far below the gap to the next
-// eigenvalue); two FP64 Sturm counts at x -/+ tol certify that the result is the eigenvalue at
-// that position to within tol = 4 ulp |x| + 2 ulp ||T||. A lane that fails the check falls back
-// to FP64 bisection (first on the widened FP32 bracket if its ends check out, else on the
-// Gershgorin interval).
-__global__ void k_bisect(const int32_t *__restrict__ plan, int32_t nb, int32_t Mmax, int32_t mmax,
-                         const double *__restrict__ td, const double *__restrict__ te,
-                         double *__restrict__ sel_val)
+// The selected eigenvalues of T_b, the one at ascending position (k0 - s + t) for slice vector t.
+// Grid (ceil(mmax / 32), nb), 1024 threads (32 warps), 32 eigenvalues per CTA:
+//   1. T is scaled by the power of two that brings its Gershgorin span into [1/2, 1) (exact).
+//   2. Warp w brackets eigenvalue w of the CTA by FP32 multisection: the 32 lanes count the
+//      eigenvalues below 32 interior points of the bracket (33 subintervals), and the bracket
+//      becomes the subinterval where the count passes the position; five rounds reach 8 FP32 ulps
+//      of the span (a bisection needs twenty counts one after another).
+//   3. Warp 0, one eigenvalue per lane: three FP64 Newton steps on det(T - xI) from the bracket's
+//      midpoint (quadratic convergence while |x - lambda| is far below the gap), then two FP64
+//      Sturm counts at x -/+ tol (one pass) certify the position to within tol = 4 ulp |x| + 2 ulp
+//      of the span. A lane that fails falls back to FP64 bisection (on the widened FP32 bracket if
+//      its ends check out, else on the Gershgorin interval).
+__global__ void __launch_bounds__(1024)
+k_bisect(const int32_t *__restrict__ plan, int32_t nb, int32_t Mmax, int32_t mmax,
+         const double *__restrict__ td, const double *__restrict__ te, double *__restrict__ sel_val)
 {
     const int b = blockIdx.y;
     const int k0 = plan[b], mb = plan[nb + b], s = plan[2 * nb + b], M = plan[3 * nb + b];
-    if (blockIdx.x * blockDim.x >= mb) return;
+    if (blockIdx.x * 32 >= mb) return;                    // whole CTA
     extern __shared__ double smd[];
     double *d = smd, *e2 = smd + Mmax;
     float *df = reinterpret_cast<float *>(smd + 2 * Mmax), *e2f = df + Mmax;
-    __shared__ double s_lo, s_hi, s_atol;
+    __shared__ double s_lo, s_hi, s_sc, s_isc;
+    __shared__ float brlo[32], brhi[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double *bd = td + (size_t)b * Mmax, *be = te + (size_t)b * Mmax;
-    for (int i = threadIdx.x; i < M; i += blockDim.x) {
-        d[i] = bd[i];
-        e2[i] = (i + 1 < M) ? be[i] * be[i] : 0.0;
-        df[i] = (float)d[i];
-        e2f[i] = (float)e2[i];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    if (warp == 0) {
         double lo = INFINITY, hi = -INFINITY;
-        for (int i = 0; i < M; i++) {
-            double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < M ? fabs(be[i]) : 0.0);
-            lo = fmin(lo, d[i] - r);
-            hi = fmax(hi, d[i] + r);
+        for (int i = lane; i < M; i += 32) {
+            const double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < M ? fabs(be[i]) : 0.0);
+            lo = fmin(lo, bd[i] - r);
+            hi = fmax(hi, bd[i] + r);
         }
-        double span = fmax(fabs(lo), fabs(hi));
-        s_lo = lo - 2.0 * DBL_EPSILON * span - DBL_MIN;
-        s_hi = hi + 2.0 * DBL_EPSILON * span + DBL_MIN;
-        s_atol = DBL_EPSILON * span;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0) {
+            const double span = fmax(fabs(lo), fabs(hi));
+            int e = 0;
+            if (span > 0.0) frexp(span, &e);                // span = f 2^e, f in [1/2, 1)
+            const double sc = ldexp(1.0, -e);
+            s_sc = sc;
+            s_isc = ldexp(1.0, e);
+            const double sspan = span * sc;
+            s_lo = lo * sc - 2.0 * DBL_EPSILON * sspan - DBL_MIN;
+            s_hi = hi * sc + 2.0 * DBL_EPSILON * sspan + DBL_MIN;
+        }
     }
     __syncthreads();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const double sc = s_sc;
+    for (int i = tid; i < M; i += blockDim.x) {
+        const double di = bd[i] * sc, ei = (i + 1 < M) ? be[i] * sc : 0.0;
+        d[i] = di;
+        e2[i] = ei * ei;
+        df[i] = (float)di;
+        e2f[i] = (float)(ei * ei);
+    }
+    __syncthreads();
+    const double sspan = fmax(fabs(s_lo), fabs(s_hi));
+    // 2. FP32 multisection, warp w -> eigenvalue blockIdx.x * 32 + w
+    {
+        const int tw = blockIdx.x * 32 + warp;
+        if (tw < mb) {
+            const int pos = k0 - s + tw;
+            float flo = (float)s_lo, fhi = (float)s_hi;
+            const float ftol = 8.0f * FLT_EPSILON * (float)sspan;
+            for (int r = 0; r < 8 && fhi - flo > ftol; r++) {
+                const float w = (fhi - flo) * (1.0f / 33.0f);
+                const float xl = fminf(fmaf(w, (float)(lane + 1), flo), fhi);
+                const int cnt = sturm3f(df, e2f, M, xl);
+                const unsigned above = __ballot_sync(0xffffffffu, cnt > pos);
+                const int f = above ? __ffs(above) - 1 : 32;         // first point above the position
+                const float xlo = __shfl_sync(0xffffffffu, xl, f > 0 ? f - 1 : 0);
+                const float xhi = __shfl_sync(0xffffffffu, xl, f < 32 ? f : 31);
+                if (f > 0) flo = xlo;
+                if (f < 32) fhi = xhi;
+            }
+            if (lane == 0) { brlo[warp] = flo; brhi[warp] = fhi; }
+        }
+    }
+    __syncthreads();
+    if (warp != 0) return;
+    // 3. FP64 refinement and certification, lane -> eigenvalue blockIdx.x * 32 + lane
+    const int t = blockIdx.x * 32 + lane;
     if (t >= mb) return;
     const int pos = k0 - s + t;
-    const double span = s_atol / DBL_EPSILON;
-    float flo = (float)s_lo, fhi = (float)s_hi;
-    const float ftol = 8.0f * FLT_EPSILON * (float)span;
-    for (int it = 0; it < 160 && fhi - flo > ftol; it++) {
-        const float mid = 0.5f * (flo + fhi);
-        if (mid <= flo || mid >= fhi) break;
-        if (sturm3f(df, e2f, M, mid) > pos) fhi = mid; else flo = mid;
-    }
-    const double widen = 32.0 * FLT_EPSILON * span;
+    const double satol = DBL_EPSILON * sspan;
+    const float flo = brlo[lane], fhi = brhi[lane];
+    const double widen = 32.0 * FLT_EPSILON * sspan;
     const double blo = fmax(s_lo, (double)flo - widen), bhi = fmin(s_hi, (double)fhi + widen);
     double x = 0.5 * ((double)flo + (double)fhi);
     for (int it = 0; it < 3; it++) {
@@ -710,19 +773,27 @@ __global__ void k_bisect(const int32_t *__restrict__ plan, int32_t nb, int32_t M
         if (!(xn >= blo && xn <= bhi)) break;        // left the bracket: keep the last iterate
         x = xn;
     }
-    const double tol = 4.0 * DBL_EPSILON * fabs(x) + 2.0 * s_atol;
-    if (!(sturm3(d, e2, M, x - tol) <= pos && sturm3(d, e2, M, x + tol) > pos)) {
+    const double tol = 4.0 * DBL_EPSILON * fabs(x) + 2.0 * satol;
+    const double xs[2] = {x - tol, x + tol};
+    int cs[2];
+    sturm_counts<2>(d, e2, M, xs, cs);
+    if (!(cs[0] <= pos && cs[1] > pos)) {
         double lo = blo, hi = bhi;
-        if (!(sturm3(d, e2, M, lo) <= pos && sturm3(d, e2, M, hi) > pos)) { lo = s_lo; hi = s_hi; }
+        const double xb[2] = {lo, hi};
+        sturm_counts<2>(d, e2, M, xb, cs);
+        if (!(cs[0] <= pos && cs[1] > pos)) { lo = s_lo; hi = s_hi; }
         for (int it = 0; it < 256; it++) {
             const double mid = 0.5 * (lo + hi);
             if (mid <= lo || mid >= hi) break;
-            if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + s_atol) break;
-            if (sturm3(d, e2, M, mid) > pos) hi = mid; else lo = mid;
+            if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + satol) break;
+            const double xm[1] = {mid};
+            int cm[1];
+            sturm_counts<1>(d, e2, M, xm, cm);
+            if (cm[0] > pos) hi = mid; else lo = mid;
         }
         x = 0.5 * (lo + hi);
     }
-    sel_val[(size_t)b * mmax + t] = x;
+    sel_val[(size_t)b * mmax + t] = x * s_isc;
 }
 
 // Reciprocal without an IEEE FP64 division (~640 cycles dependent on B300): FP32 estimate and two
@@ -761,16 +832,32 @@ __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int
                                const double *__restrict__ te, const double *__restrict__ sel_val,
                                double *__restrict__ sel_vec, double *__restrict__ work)
 {
+    constexpr int PB = 8;                                   // prefetch block of the solves
     const int b = blockIdx.y;
     const int mb = plan[nb + b], M = plan[3 * nb + b];
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= mb) return;
-    const double *__restrict__ d = td + (size_t)b * Mmax;
-    const double *__restrict__ e = te + (size_t)b * Mmax;
-    const double *lam = sel_val + (size_t)b * mmax;
+    extern __shared__ double zsm[];
+    const int zst = blockDim.x;
+    double *z = zsm + threadIdx.x;                          // element i at z[i * zst]
+    double *d = zsm + (size_t)zst * Mmax;                   // the window's T, shared by the lanes
+    double *e = d + Mmax;
+    __shared__ double tn_part[32];
+    {
+        const double *gd = td + (size_t)b * Mmax, *ge = te + (size_t)b * Mmax;
+        double part = 0.0;
+        for (int i = threadIdx.x; i < M; i += blockDim.x) {
+            const double di = gd[i], ei = ge[i], em = (i > 0) ? ge[i - 1] : 0.0;
+            d[i] = di;
+            e[i] = ei;
+            part = fmax(part, fabs(di) + fabs(em) + (i + 1 < M ? fabs(ei) : 0.0));
+        }
+        tn_part[threadIdx.x] = part;
+    }
+    __syncthreads();
     double tnorm = 0.0;
-    for (int i = 0; i < M; i++)
-        tnorm = fmax(tnorm, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < M ? fabs(e[i]) : 0.0));
+    for (int q = 0; q < (int)blockDim.x; q++) tnorm = fmax(tnorm, tn_part[q]);
+    if (t >= mb) return;
+    const double *lam = sel_val + (size_t)b * mmax;
     const double gaptol = 1e-9 * fmax(tnorm, DBL_MIN);
     if (t > 0 && lam[t] - lam[t - 1] < gaptol) return;     // handled by the cluster's first lane
     const size_t stride = (size_t)nb * mmax;
@@ -779,9 +866,6 @@ __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int
     double *__restrict__ u1 = work + stride * Mmax + me;
     double *__restrict__ u2 = work + 2 * stride * Mmax + me;
     double *__restrict__ lm = work + 3 * stride * Mmax + me; // multipliers, sign bit = row swap
-    extern __shared__ double zsm[];
-    const int zst = blockDim.x;
-    double *z = zsm + threadIdx.x;                          // element i at z[i * zst]
     const double pert = DBL_EPSILON * fmax(tnorm, DBL_MIN);
     int last = t;
     while (last + 1 < mb && lam[last + 1] - lam[last] < gaptol) last++;
@@ -812,27 +896,50 @@ __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int
         u2[(size_t)(M - 1) * stride] = 0.0;
         for (int i = 0; i < M; i++) z[i * zst] = hash_unit(b, j, i);
         for (int it = 0; it < 2; it++) {
-            // forward: replay the row operations on the right-hand side
+            // forward: replay the row operations on the right-hand side; the multipliers of a
+            // block of PB rows are loaded together (one L2 round trip per block)
             double zi = z[0];
-#pragma unroll 4
-            for (int i = 0; i + 1 < M; i++) {
-                const double lraw = lm[i * stride];
-                const bool swp = (__double_as_longlong(lraw) & 1ll) != 0;
-                const double l = lraw;       // the flag bit perturbs l by at most 1 ulp
-                const double zn = z[(i + 1) * zst];
-                if (swp) { z[i * zst] = zn; zi = fma(-l, zn, zi); }
-                else { z[i * zst] = zi; zi = fma(-l, zi, zn); }
+            for (int i0 = 0; i0 + 1 < M; i0 += PB) {
+                double lr[PB];
+#pragma unroll
+                for (int q2 = 0; q2 < PB; q2++) lr[q2] = (i0 + q2 + 1 < M) ? lm[(size_t)(i0 + q2) * stride] : 0.0;
+#pragma unroll
+                for (int q2 = 0; q2 < PB; q2++) {
+                    const int i = i0 + q2;
+                    if (i + 1 < M) {
+                        const double lraw = lr[q2];
+                        const bool swp = (__double_as_longlong(lraw) & 1ll) != 0;
+                        const double l = lraw;       // the flag bit perturbs l by at most 1 ulp
+                        const double zn = z[(i + 1) * zst];
+                        if (swp) { z[i * zst] = zn; zi = fma(-l, zn, zi); }
+                        else { z[i * zst] = zi; zi = fma(-l, zi, zn); }
+                    }
+                }
             }
             z[(size_t)(M - 1) * zst] = zi;
-            // back substitution with the three upper diagonals
+            // back substitution with the three upper diagonals, factors loaded a block at a time
             double z1 = 0.0, z2 = 0.0;
-#pragma unroll 4
-            for (int i = M - 1; i >= 0; i--) {
-                const double acc = fma(-u2[i * stride], z2, fma(-u1[i * stride], z1, z[i * zst]));
-                const double zi2 = acc * u0[i * stride];
-                z[i * zst] = zi2;
-                z2 = z1;
-                z1 = zi2;
+            for (int i0 = M - 1; i0 >= 0; i0 -= PB) {
+                double a0[PB], a1[PB], a2[PB];
+#pragma unroll
+                for (int q2 = 0; q2 < PB; q2++) {
+                    const int i = i0 - q2;
+                    const bool ok = i >= 0;
+                    a0[q2] = ok ? u0[(size_t)i * stride] : 0.0;
+                    a1[q2] = ok ? u1[(size_t)i * stride] : 0.0;
+                    a2[q2] = ok ? u2[(size_t)i * stride] : 0.0;
+                }
+#pragma unroll
+                for (int q2 = 0; q2 < PB; q2++) {
+                    const int i = i0 - q2;
+                    if (i >= 0) {
+                        const double acc = fma(-a2[q2], z2, fma(-a1[q2], z1, z[i * zst]));
+                        const double zi2 = acc * a0[q2];
+                        z[i * zst] = zi2;
+                        z2 = z1;
+                        z1 = zi2;
+                    }
+                }
             }
             // orthogonalise against earlier cluster members, then normalise
             for (int c = t; c < j; c++) {
@@ -1182,7 +1289,7 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
     // 2. eigenvalues
     {
         dim3 grid((unsigned)((mmax + tpb - 1) / tpb), (unsigned)nb);
-        k_bisect<<<grid, tpb, (size_t)3 * Mmax * sizeof(double), st>>>(w.plan, nb, Mmax, mmax, w.td, w.te, w.sel_val); g_launches++;
+        k_bisect<<<grid, 1024, (size_t)3 * Mmax * sizeof(double), st>>>(w.plan, nb, Mmax, mmax, w.td, w.te, w.sel_val); g_launches++;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -1190,10 +1297,11 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
     // 3. inverse iteration
     {
         int lanes = tpb;
-        while (lanes > 1 && (size_t)lanes * Mmax * sizeof(double) > kInvSmemCap) lanes >>= 1;
+        while (lanes > 1 && (size_t)(lanes + 2) * Mmax * sizeof(double) > kInvSmemCap) lanes >>= 1;
         dim3 grid((unsigned)((mmax + lanes - 1) / lanes), (unsigned)nb);
-        k_inverse_iter<<<grid, lanes, (size_t)lanes * Mmax * sizeof(double), st>>>(w.plan, nb, Mmax, mmax, w.td, w.te,
-                                                                                 w.sel_val, w.sel_vec, w.iiwork);
+        k_inverse_iter<<<grid, lanes, (size_t)(lanes + 2) * Mmax * sizeof(double), st>>>(w.plan, nb, Mmax, mmax, w.td,
+                                                                                       w.te, w.sel_val, w.sel_vec,
+                                                                                       w.iiwork);
         g_launches++;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
