@@ -597,30 +597,43 @@ __device__ __forceinline__ void sturm_counts(const double *d, const double *e2, 
         pc[j] = clamp_dx(d[0] - x[j]);
         cnt[j] = __double2hiint(pc[j]) < 0;
     }
-    for (int i = 1; i < M; i++) {
-        const double di = d[i], fi = e2[i - 1];
+    // one step: the exact-zero substitute -2^-60 pc is built on the bit pattern (pc is normal)
+    auto step = [&](int j, double dx, double fi) {
+        double pn = fma(dx, pc[j], -fi * pp[j]);
+        const int hc = __double2hiint(pc[j]), hn = __double2hiint(pn);
+        const double alt = __hiloint2double((hc ^ (int)0x80000000) - (60 << 20), __double2loint(pc[j]));
+        pn = (((hn & 0x7FFFFFFF) | __double2loint(pn)) == 0) ? alt : pn;
+        cnt[j] += (int)((unsigned)(__double2hiint(pn) ^ hc) >> 31);
+        pp[j] = pc[j];
+        pc[j] = pn;
+    };
+    int i = 1;
+    for (; i + 3 < M; i += 4) {                 // blocks of four: d - x and the loads go first
+        double dx[4][NP], f[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            f[u] = e2[i + u - 1];
+#pragma unroll
+            for (int j = 0; j < NP; j++) dx[u][j] = clamp_dx(d[i + u] - x[j]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+#pragma unroll
+            for (int j = 0; j < NP; j++) step(j, dx[u][j], f[u]);
+        }
 #pragma unroll
         for (int j = 0; j < NP; j++) {
-            const double dx = clamp_dx(di - x[j]);
-            double pn = fma(dx, pc[j], -fi * pp[j]);
-            const double alt = pc[j] * -0x1.0p-60;          // used when pn is exactly zero
-            const int hn = __double2hiint(pn);
-            pn = (((hn & 0x7FFFFFFF) | __double2loint(pn)) == 0) ? alt : pn;
-            cnt[j] += (int)((unsigned)(__double2hiint(pn) ^ __double2hiint(pc[j])) >> 31);
-            pp[j] = pc[j];
-            pc[j] = pn;
-        }
-        if ((i & 3) == 0) {
-#pragma unroll
-            for (int j = 0; j < NP; j++) {
-                const int em = max(exp_of(pc[j]), exp_of(pp[j]));
-                if (em > 1023 + 400 || em < 1023 - 400) {
-                    const double sc = __hiloint2double((2046 - em) << 20, 0);   // 2^(1023 - em)
-                    pc[j] *= sc;
-                    pp[j] *= sc;
-                }
+            const int em = max(exp_of(pc[j]), exp_of(pp[j]));
+            if (em > 1023 + 400 || em < 1023 - 400) {
+                const double sc = __hiloint2double((2046 - em) << 20, 0);   // 2^(1023 - em)
+                pc[j] *= sc;
+                pp[j] *= sc;
             }
         }
+    }
+    for (; i < M; i++) {                        // at most three steps after the last renormalisation
+#pragma unroll
+        for (int j = 0; j < NP; j++) step(j, clamp_dx(d[i] - x[j]), e2[i - 1]);
     }
 }
 
@@ -659,46 +672,58 @@ __device__ __forceinline__ int sturm3f(const float *d, const float *e2, int M, f
 __device__ __forceinline__ double newton_step(const double *d, const double *e2, int M, double x)
 {
     double pp = 1.0, pc = clamp_dx(d[0] - x), qp = 0.0, qc = -1.0;
-    for (int i = 1; i < M; i++) {
+    int i = 1;
+    for (; i + 3 < M; i += 4) {                 // blocks of four: d - x and the loads go first
+        double dx[4], f[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) { dx[u] = clamp_dx(d[i + u] - x); f[u] = e2[i + u - 1]; }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const double pn = fma(dx[u], pc, -f[u] * pp);
+            const double qn = fma(dx[u], qc, -fma(f[u], qp, pc));
+            pp = pc; qp = qc; pc = pn; qc = qn;
+        }
+        const int em = max(max(exp_of(pc), exp_of(pp)), max(exp_of(qc), exp_of(qp)));
+        if (em > 1023 + 400 || em < 1023 - 400) {
+            const double sc = __hiloint2double((2046 - em) << 20, 0);
+            pp *= sc; qp *= sc; pc *= sc; qc *= sc;
+        }
+    }
+    for (; i < M; i++) {                        // at most three steps after the last renormalisation
         const double dx = clamp_dx(d[i] - x), f = e2[i - 1];
         const double pn = fma(dx, pc, -f * pp);
         const double qn = fma(dx, qc, -fma(f, qp, pc));
         pp = pc; qp = qc; pc = pn; qc = qn;
-        if ((i & 3) == 0) {
-            const int em = max(max(exp_of(pc), exp_of(pp)), max(exp_of(qc), exp_of(qp)));
-            if (em > 1023 + 400 || em < 1023 - 400) {
-                const double sc = __hiloint2double((2046 - em) << 20, 0);
-                pp *= sc; qp *= sc; pc *= sc; qc *= sc;
-            }
-        }
     }
     return (qc != 0.0) ? -pc / qc : 0.0;
 }
 
 // The selected eigenvalues of T_b, the one at ascending position (k0 - s + t) for slice vector t.
-// Grid (ceil(mmax / 32), nb), 1024 threads (32 warps), 32 eigenvalues per CTA:
+// Grid (ceil(mmax / 8), nb), 256 threads (8 warps), 8 eigenvalues per CTA (so that the FP32
+// multisection, the bulk of the instructions, spreads over every SM):
 //   1. T is scaled by the power of two that brings its Gershgorin span into [1/2, 1) (exact).
 //   2. Warp w brackets eigenvalue w of the CTA by FP32 multisection: the 32 lanes count the
 //      eigenvalues below 32 interior points of the bracket (33 subintervals), and the bracket
 //      becomes the subinterval where the count passes the position; five rounds reach 8 FP32 ulps
 //      of the span (a bisection needs twenty counts one after another).
-//   3. Warp 0, one eigenvalue per lane: three FP64 Newton steps on det(T - xI) from the bracket's
+//   3. Warp 0, one eigenvalue per lane (8 lanes): three FP64 Newton steps on det(T - xI) from the bracket's
 //      midpoint (quadratic convergence while |x - lambda| is far below the gap), then two FP64
 //      Sturm counts at x -/+ tol (one pass) certify the position to within tol = 4 ulp |x| + 2 ulp
 //      of the span. A lane that fails falls back to FP64 bisection (on the widened FP32 bracket if
 //      its ends check out, else on the Gershgorin interval).
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(256)
 k_bisect(const int32_t *__restrict__ plan, int32_t nb, int32_t Mmax, int32_t mmax,
          const double *__restrict__ td, const double *__restrict__ te, double *__restrict__ sel_val)
 {
     const int b = blockIdx.y;
     const int k0 = plan[b], mb = plan[nb + b], s = plan[2 * nb + b], M = plan[3 * nb + b];
-    if (blockIdx.x * 32 >= mb) return;                    // whole CTA
+    constexpr int EPC = 8;                                // eigenvalues per CTA
+    if (blockIdx.x * EPC >= mb) return;                   // whole CTA
     extern __shared__ double smd[];
     double *d = smd, *e2 = smd + Mmax;
     float *df = reinterpret_cast<float *>(smd + 2 * Mmax), *e2f = df + Mmax;
     __shared__ double s_lo, s_hi, s_sc, s_isc;
-    __shared__ float brlo[32], brhi[32];
+    __shared__ float brlo[EPC], brhi[EPC];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double *bd = td + (size_t)b * Mmax, *be = te + (size_t)b * Mmax;
     if (warp == 0) {
@@ -736,9 +761,9 @@ k_bisect(const int32_t *__restrict__ plan, int32_t nb, int32_t Mmax, int32_t mma
     }
     __syncthreads();
     const double sspan = fmax(fabs(s_lo), fabs(s_hi));
-    // 2. FP32 multisection, warp w -> eigenvalue blockIdx.x * 32 + w
+    // 2. FP32 multisection, warp w -> eigenvalue blockIdx.x * EPC + w
     {
-        const int tw = blockIdx.x * 32 + warp;
+        const int tw = blockIdx.x * EPC + warp;
         if (tw < mb) {
             const int pos = k0 - s + tw;
             float flo = (float)s_lo, fhi = (float)s_hi;
@@ -759,8 +784,9 @@ k_bisect(const int32_t *__restrict__ plan, int32_t nb, int32_t Mmax, int32_t mma
     }
     __syncthreads();
     if (warp != 0) return;
-    // 3. FP64 refinement and certification, lane -> eigenvalue blockIdx.x * 32 + lane
-    const int t = blockIdx.x * 32 + lane;
+    // 3. FP64 refinement and certification, lane -> eigenvalue blockIdx.x * EPC + lane
+    if (lane >= EPC) return;
+    const int t = blockIdx.x * EPC + lane;
     if (t >= mb) return;
     const int pos = k0 - s + t;
     const double satol = DBL_EPSILON * sspan;
@@ -911,8 +937,9 @@ __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int
                         const bool swp = (__double_as_longlong(lraw) & 1ll) != 0;
                         const double l = lraw;       // the flag bit perturbs l by at most 1 ulp
                         const double zn = z[(i + 1) * zst];
-                        if (swp) { z[i * zst] = zn; zi = fma(-l, zn, zi); }
-                        else { z[i * zst] = zi; zi = fma(-l, zi, zn); }
+                        const double ts = fma(-l, zn, zi), tn = fma(-l, zi, zn);   // both, no divergence
+                        z[i * zst] = swp ? zn : zi;
+                        zi = swp ? ts : tn;
                     }
                 }
             }
@@ -1288,8 +1315,8 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
     if (h->timing && (e0 = cudaEventRecord(h->sub_ev[0], st)) != cudaSuccess) return e0;
     // 2. eigenvalues
     {
-        dim3 grid((unsigned)((mmax + tpb - 1) / tpb), (unsigned)nb);
-        k_bisect<<<grid, 1024, (size_t)3 * Mmax * sizeof(double), st>>>(w.plan, nb, Mmax, mmax, w.td, w.te, w.sel_val); g_launches++;
+        dim3 grid((unsigned)((mmax + 7) / 8), (unsigned)nb);
+        k_bisect<<<grid, 256, (size_t)3 * Mmax * sizeof(double), st>>>(w.plan, nb, Mmax, mmax, w.td, w.te, w.sel_val); g_launches++;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
