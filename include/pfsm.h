@@ -178,6 +178,14 @@ int pfsm_batch_destroy(pfsm_batch_t b);
 int pfsm_split_gemm(int64_t rows, int64_t cols, int64_t K, const double *P, const double *Q,
                     double *C, int32_t precision, void *stream);
 
+/* pfsm_split_gemm with the split products' output-tile width given: tile_n = 64, 96 or 128
+ * columns (rows are always 128), or 0 for the autotuned width (every candidate timed once per
+ * device, slice kind and shape class, the fastest kept; the same tuner picks the width of a
+ * handle's Eq. 11 products at pfsm_init). Ignored for PFSM_FP64. Returns PFSM_ERR_INVALID_ARG
+ * for any other tile_n. */
+int pfsm_split_gemm_ex(int64_t rows, int64_t cols, int64_t K, const double *P, const double *Q,
+                       double *C, int32_t precision, int32_t tile_n, void *stream);
+
 /* Eq. 11 on caller vectors WITHOUT ANY DEVICE ALLOCATION. The paper has no counterpart; this
  * entry point exists for callers that cannot allocate device memory when they call the
  * library, e.g. codes that reserve all device memory up front for their own pool, or
@@ -210,6 +218,8 @@ typedef struct {
                              inside 1: 6 tridiagonalisation, 7 bisection, 8 inverse iteration,
                              9 back-transformation + start vectors; inside 3: 10 overlap,
                              11 Cholesky; the triangular solve is phase 3 minus 10 and 11 */
+    int32_t gemm_tile_n;  /* output-tile width (64, 96 or 128 columns) of the handle's split
+                             products, measured at pfsm_init; 0 for PFSM_FP64 handles */
 } pfsm_profile_t;
 
 /* Enables (enable != 0) or disables CUDA-event phase timing on h. Timing adds one event record

@@ -23,7 +23,7 @@ DIAG_RESIDUALS, DIAG_XFS, DIAG_EPS, DIAG_ALPHA, DIAG_PLAN = range(5)
 
 EXPORTED = ("pfsm_default_params", "pfsm_init", "pfsm_solve", "pfsm_backward", "pfsm_get_status",
             "pfsm_get_diagnostic", "pfsm_set_timing", "pfsm_get_profile", "pfsm_last_error",
-            "pfsm_destroy", "pfsm_fs_iterate_noalloc", "pfsm_split_gemm", "pfsm_batch_init",
+            "pfsm_destroy", "pfsm_fs_iterate_noalloc", "pfsm_split_gemm", "pfsm_split_gemm_ex", "pfsm_batch_init",
             "pfsm_solve_batched", "pfsm_batch_get_status", "pfsm_batch_destroy")
 PHASES = ("plan", "submatrix", "fs_iterations", "gram_schmidt", "rayleigh", "backward")
 SUB_PHASES = ("tridiag", "bisect", "inverse_iter", "backtransform", "overlap", "cholesky")
@@ -44,7 +44,7 @@ class Params(ctypes.Structure):
 
 class Profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int32), ("timed", ctypes.c_int32),
-                ("phase_ms", ctypes.c_float * 12)]
+                ("phase_ms", ctypes.c_float * 12), ("gemm_tile_n", ctypes.c_int32)]
 
 
 _lib = None
@@ -69,6 +69,7 @@ def load_library():
     lib.pfsm_get_diagnostic.argtypes = [P, i32, P, P]
     lib.pfsm_fs_iterate_noalloc.argtypes = [i64, i64, P, P, P, P, i32, P]
     lib.pfsm_split_gemm.argtypes = [i64, i64, i64, P, P, P, i32, P]
+    lib.pfsm_split_gemm_ex.argtypes = [i64, i64, i64, P, P, P, i32, i32, P]
     lib.pfsm_batch_init.argtypes = [i32, P, P, ctypes.POINTER(Params), ctypes.POINTER(P)]
     lib.pfsm_solve_batched.argtypes = [P, P, P, P, P, P]
     lib.pfsm_batch_get_status.argtypes = [P, P]
@@ -167,7 +168,7 @@ class Handle:
         """Launch count and per-phase CUDA-event times (ms) of the last call on this handle."""
         pr = Profile()
         _check(load_library().pfsm_get_profile(self._h, ctypes.byref(pr)), "pfsm_get_profile")
-        out = {"launches": pr.launches}
+        out = {"launches": pr.launches, "gemm_tile_n": pr.gemm_tile_n}
         if pr.timed:
             out.update({name: float(pr.phase_ms[i]) for i, name in enumerate(PHASES)})
             out.update({name: float(pr.phase_ms[6 + i]) for i, name in enumerate(SUB_PHASES)})
@@ -260,13 +261,14 @@ class Batch:
             pass
 
 
-def split_gemm(P: torch.Tensor, Q: torch.Tensor, precision: int = BF16_SPLIT) -> torch.Tensor:
-    """C = P Q^T on the tensor cores in split BF16/TF32 (FP64 in and out)."""
+def split_gemm(P: torch.Tensor, Q: torch.Tensor, precision: int = BF16_SPLIT, tile_n: int = 0) -> torch.Tensor:
+    """C = P Q^T on the tensor cores in split BF16/TF32 or FP64-accurate digits (FP64 in and out);
+    tile_n: output-tile width of the split products (64, 96, 128; 0 = autotuned)."""
     rows, K = P.shape
     cols = Q.shape[0]
     C = torch.empty(rows, cols, dtype=torch.float64, device=P.device)
-    _check(load_library().pfsm_split_gemm(rows, cols, K, _ptr(P), _ptr(Q), _ptr(C), precision, _stream()),
-           "pfsm_split_gemm")
+    _check(load_library().pfsm_split_gemm_ex(rows, cols, K, _ptr(P), _ptr(Q), _ptr(C), precision, tile_n,
+                                             _stream()), "pfsm_split_gemm_ex")
     return C
 
 

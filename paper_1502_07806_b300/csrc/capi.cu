@@ -242,6 +242,11 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
         return fail(PFSM_ERR_CUDA, "pfsm_init: %s", cudaGetErrorString(e));
     }
     h->prm.slice_sizes = nullptr;   // the host array is not kept
+    if (prm.precision != PFSM_FP64) {
+        // tile width of the Eq. 11 products: measured on this shape (cached per shape class)
+        SliceBuf sE{w.slE, N, padded_ld(N), slices_for(prm.precision), slice_kind(prm.precision)};
+        h->tc_bn = tune_tc_tile(sE, sE, (int)N, (int)N, w.Z);
+    }
     *out = h;
     return PFSM_OK;
 }
@@ -268,7 +273,7 @@ static cudaError_t fs_mixed(pfsm_handle_s *h, const double *A, cudaStream_t st)
     if ((e = launch_split(A, N, N, N, sE, true, w.dA, st)) != cudaSuccess) return e;
     if ((e = launch_split(w.X, N, N, N, sX, false, nullptr, st)) != cudaSuccess) return e;
     TcParams p{};
-    p.rows = (int)N; p.cols = (int)N; p.ldo = N;
+    p.rows = (int)N; p.cols = (int)N; p.ldo = N; p.bn = h->tc_bn;
     p.d = w.dA; p.eps = w.eps; p.alpha = w.alpha; p.status = w.status;
     p.plan = w.plan; p.nb = h->nb;
     p.krange = w.tile_krange; p.nrowtiles64 = (int)((N + kFsTileRows - 1) / kFsTileRows);
@@ -402,6 +407,14 @@ int pfsm_get_diagnostic(pfsm_handle_t h, int32_t which, void *out, void *stream)
 int pfsm_split_gemm(int64_t rows, int64_t cols, int64_t K, const double *P, const double *Q,
                     double *C, int32_t precision, void *stream)
 {
+    return pfsm_split_gemm_ex(rows, cols, K, P, Q, C, precision, 0, stream);
+}
+
+int pfsm_split_gemm_ex(int64_t rows, int64_t cols, int64_t K, const double *P, const double *Q,
+                       double *C, int32_t precision, int32_t tile_n, void *stream)
+{
+    if (tile_n != 0 && tile_n != 64 && tile_n != 96 && tile_n != 128)
+        return fail(PFSM_ERR_INVALID_ARG, "pfsm_split_gemm_ex: tile_n must be 0, 64, 96 or 128");
     if (rows < 1 || cols < 1 || K < 1 || rows > 65535 || cols > 65535 || K > (1 << 24) || !P || !Q || !C)
         return fail(PFSM_ERR_INVALID_ARG, "pfsm_split_gemm: bad size or null pointer");
     if (precision != PFSM_TF32_SPLIT && precision != PFSM_BF16_SPLIT && precision != PFSM_FP64)
@@ -455,7 +468,11 @@ int pfsm_split_gemm(int64_t rows, int64_t cols, int64_t K, const double *P, cons
     PFSM_CUDA(launch_split(Q, cols, K, K, bq, false, nullptr, st));
     TcParams p{};
     p.rows = (int)rows; p.cols = (int)cols; p.epi = TC_EPI_STORE; p.out = C; p.ldo = cols;
-    p.status = status;
+    p.status = status; p.bn = tile_n;
+    if (tile_n == 0) {                  // tuned (C serves as the tuner's scratch output)
+        PFSM_CUDA(cudaStreamSynchronize(st));
+        p.bn = tune_tc_tile(bp, bq, (int)rows, (int)cols, C);
+    }
     PFSM_CUDA(launch_gemm_tc(bp, bq, p, nullptr, st));
     int32_t hs = 0;
     PFSM_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -479,6 +496,7 @@ int pfsm_get_profile(pfsm_handle_t h, pfsm_profile_t *out)
     if (!h || !out) return fail(PFSM_ERR_INVALID_ARG, "pfsm_get_profile: null argument");
     std::memset(out, 0, sizeof(*out));
     out->launches = h->last_launches;
+    out->gemm_tile_n = h->prm.precision != PFSM_FP64 ? h->tc_bn : 0;
     if (!h->timing || !h->solved) return PFSM_OK;
     PFSM_CUDA(cudaStreamSynchronize(h->last_stream));
     auto span = [&](int a, int b, float *dst) -> cudaError_t { return cudaEventElapsedTime(dst, h->ev[a], h->ev[b]); };

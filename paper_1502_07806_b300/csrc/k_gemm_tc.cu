@@ -10,32 +10,39 @@
 // BF16, 3 for TF32). The epilogue applies the Eq. 11 algebra (TC_EPI_* modes) and can write the
 // BF16/TF32 slices of its own result, the operand of the next product.
 //
-// Persistent CTAs (one per SM, 192 threads) walk the output tiles (128 x 128). Warp 0 issues the
-// TMA loads: one pipeline stage holds every slice of P and of Q for one 128-byte K block, so each
-// slice tile is loaded once and feeds all the pairs that use it. Warp 1 owns a double-buffered
-// TMEM accumulator (2 x 128 columns) and issues tcgen05.mma from one lane, so the MMAs of tile
-// i + 1 run while warps 2-5 drain tile i. The epilogue keeps FP64 only where Eq. 11 accumulates
+// Persistent CTAs (one per SM, 192 threads) walk the output tiles (128 x BN, BN = 64, 96 or 128:
+// the width that fills the SMs best for the product's shape is measured once per shape class by
+// tune_tc_tile). Warp 0 issues the TMA loads: one pipeline stage holds every slice of P and of Q
+// for one 128-byte K block, so each slice tile is loaded once and feeds all the pairs that use
+// it. Warp 1 owns a double-buffered TMEM accumulator (2 x 128 columns) and issues tcgen05.mma
+// from one lane, so the MMAs of tile i + 1 run while warps 2-5 drain tile i. The epilogue keeps FP64 only where Eq. 11 accumulates
 // (X -= alpha Z, Y_new = Y - alpha (...)) and does the rest in FP32, which is as accurate as the
 // split product itself: B300's FP64 pipe (2 FMA/clk/SM) would otherwise outlast the MMAs.
 // Every mbarrier wait is bounded by %globaltimer: a wait that gives up records PFSM_ERR_TIMEOUT
 // in the status word; all roles then stop, the loads and MMAs in flight are waited for
 // (bounded), TMEM is freed and the CTA exits.
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "tc_common.cuh"
 
 namespace pfsm {
 
 namespace tc {
 
-constexpr int BM = 128, BN = 128;
-constexpr int TILE_BYTES = BM * 128;                 // 128 rows x 128 bytes
-constexpr uint32_t TMEM_COLS = 256;                  // two 128-column FP32 accumulators
+constexpr int BM = 128;
+constexpr int TILE_BYTES = BM * 128;                 // P tile: 128 rows x 128 bytes
+constexpr uint32_t TMEM_COLS = 256;                  // two accumulators, 128 columns apart
 constexpr int EBP = 17;                              // epilogue staging row (16 columns + pad)
 
-template <int KIND> struct Cfg {
+template <int KIND, int BN> struct Cfg {
+    static_assert(BN % 32 == 0 && BN >= 64 && BN <= 128, "tile width");
     static constexpr int NS = KIND == 0 ? 3 : 2;     // slices per operand
     static constexpr int BK = KIND == 0 ? 64 : 32;   // K elements per 128-byte row
     static constexpr int KSTEP = KIND == 0 ? 16 : 8; // K per tcgen05.mma
-    static constexpr int STAGE_BYTES = 2 * NS * TILE_BYTES;
+    static constexpr int Q_TILE = BN * 128;          // Q tile: BN rows x 128 bytes
+    static constexpr int STAGE_BYTES = NS * (TILE_BYTES + Q_TILE);
     static constexpr int STAGES = KIND == 0 ? 2 : 3;
     static constexpr int NPAIRS = NS * (NS + 1) / 2;
 };
@@ -58,12 +65,12 @@ __device__ __forceinline__ void tile_coords(int t, int ncolt, int lower, int &tr
 
 }  // namespace tc
 
-template <int KIND>
+template <int KIND, int BN>
 __global__ void __launch_bounds__(192, 1)
 k_gemm_tc(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUtensorMap mapQ, TcParams prm)
 {
     using namespace tc;
-    using C = Cfg<KIND>;
+    using C = Cfg<KIND, BN>;
     extern __shared__ __align__(1024) uint8_t smraw[];
     const uint32_t raw = smem_u32(smraw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -148,7 +155,8 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
 #pragma unroll
                     for (int a = 0; a < C::NS; a++) {
                         tma_load_3d(st0 + a * TILE_BYTES, &mapP, full_bar(s), kb * C::BK, tr * BM, a);
-                        tma_load_3d(st0 + (C::NS + a) * TILE_BYTES, &mapQ, full_bar(s), kb * C::BK, tcl * BN, a);
+                        tma_load_3d(st0 + C::NS * TILE_BYTES + a * C::Q_TILE, &mapQ, full_bar(s), kb * C::BK,
+                                    tcl * BN, a);
                     }
                     issued = it + 1;
                 }
@@ -181,10 +189,10 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
 #pragma unroll
                         for (int a = 0; a <= ord; a++) {
                             const uint64_t da = sw128_desc(st0 + a * TILE_BYTES);
-                            const uint64_t db = sw128_desc(st0 + (C::NS + ord - a) * TILE_BYTES);
+                            const uint64_t db = sw128_desc(st0 + C::NS * TILE_BYTES + (ord - a) * C::Q_TILE);
 #pragma unroll
                             for (int kk = 0; kk < 4; kk++) {   // 4 x 32 bytes of K per 128-byte row
-                                umma<KIND>(dacc, da + 2 * kk, db + 2 * kk, first ? 0u : 1u);
+                                umma<KIND, BM, BN>(dacc, da + 2 * kk, db + 2 * kk, first ? 0u : 1u);
                                 first = false;
                             }
                         }
@@ -215,7 +223,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
             const int r = row0 + 32 * g + lane;
             // column data of this tile (the previous tile's readers are done: named barrier)
             asm volatile("bar.sync 1, 128;" ::: "memory");
-            if (prm.d) {
+            if (prm.d && et < BN) {
                 const int c = col0 + et;
                 const double dv = c < prm.cols ? prm.d[c] : 0.0;
                 const float h = (float)dv;
@@ -432,10 +440,11 @@ cudaError_t make_slice_map64(CUtensorMap *map, const SliceBuf &b, int box_rows, 
 
 namespace {
 
-template <int KIND>
+template <int KIND, int BN>
 size_t tc_smem_bytes()
 {
-    return (size_t)tc::Cfg<KIND>::STAGES * tc::Cfg<KIND>::STAGE_BYTES + 1024 + 256 + 2 * tc::BN * 4 + 128 * tc::EBP * 8;
+    return (size_t)tc::Cfg<KIND, BN>::STAGES * tc::Cfg<KIND, BN>::STAGE_BYTES + 1024 + 256 + 2 * BN * 4 +
+           128 * tc::EBP * 8;
 }
 
 }  // namespace
@@ -453,9 +462,17 @@ int sm_count()
 
 cudaError_t configure_tc_kernels()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes<0>());
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes<1>());
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void *fn, size_t bytes) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    };
+    set((const void *)k_gemm_tc<0, 64>, tc_smem_bytes<0, 64>());
+    set((const void *)k_gemm_tc<0, 96>, tc_smem_bytes<0, 96>());
+    set((const void *)k_gemm_tc<0, 128>, tc_smem_bytes<0, 128>());
+    set((const void *)k_gemm_tc<1, 64>, tc_smem_bytes<1, 64>());
+    set((const void *)k_gemm_tc<1, 96>, tc_smem_bytes<1, 96>());
+    set((const void *)k_gemm_tc<1, 128>, tc_smem_bytes<1, 128>());
+    return e;
 }
 
 cudaError_t launch_split(const double *src, int64_t rows, int64_t cols, int64_t ld, const SliceBuf &dst,
@@ -475,8 +492,10 @@ cudaError_t launch_gemm_tc(const SliceBuf &P, const SliceBuf &Q, TcParams prm, S
 {
     CUtensorMap mp, mq;
     cudaError_t e;
+    // tile width: the caller's (tuned) choice, 128 for lower-triangle products (square tiles)
+    const int bn = (prm.lower_only || (prm.bn != 64 && prm.bn != 96)) ? 128 : prm.bn;
     if ((e = make_slice_map(&mp, P, tc::BM)) != cudaSuccess) return e;
-    if ((e = make_slice_map(&mq, Q, tc::BN)) != cudaSuccess) return e;
+    if ((e = make_slice_map(&mq, Q, bn)) != cudaSuccess) return e;
     if (P.kind != Q.kind || P.ns != (P.kind == 0 ? 3 : 2) || Q.ns != P.ns || P.ld != Q.ld) return cudaErrorInvalidValue;
     if (prm.lower_only && prm.rows != prm.cols) return cudaErrorInvalidValue;
     prm.bk = P.kind == 0 ? 64 : 32;
@@ -491,16 +510,80 @@ cudaError_t launch_gemm_tc(const SliceBuf &P, const SliceBuf &Q, TcParams prm, S
     } else {
         prm.out_ns = 0;
     }
-    const int nrowt = (prm.rows + tc::BM - 1) / tc::BM, ncolt = (prm.cols + tc::BN - 1) / tc::BN;
+    const int nrowt = (prm.rows + tc::BM - 1) / tc::BM, ncolt = (prm.cols + bn - 1) / bn;
     const int ntiles = prm.lower_only ? nrowt * (nrowt + 1) / 2 : nrowt * ncolt;
     if (ntiles == 0) return cudaSuccess;
     const unsigned grid = (unsigned)(ntiles < sm_count() ? ntiles : sm_count());
-    if (P.kind == 0)
-        k_gemm_tc<0><<<grid, 192, tc_smem_bytes<0>(), st>>>(mp, mq, prm);
-    else
-        k_gemm_tc<1><<<grid, 192, tc_smem_bytes<1>(), st>>>(mp, mq, prm);
+#define PFSM_TC_LAUNCH(K_, B_) k_gemm_tc<K_, B_><<<grid, 192, tc_smem_bytes<K_, B_>(), st>>>(mp, mq, prm)
+    if (P.kind == 0) {
+        if (bn == 64) PFSM_TC_LAUNCH(0, 64);
+        else if (bn == 96) PFSM_TC_LAUNCH(0, 96);
+        else PFSM_TC_LAUNCH(0, 128);
+    } else {
+        if (bn == 64) PFSM_TC_LAUNCH(1, 64);
+        else if (bn == 96) PFSM_TC_LAUNCH(1, 96);
+        else PFSM_TC_LAUNCH(1, 128);
+    }
+#undef PFSM_TC_LAUNCH
     g_launches++;
     return cudaGetLastError();
+}
+
+// Tile-width autotuner: every candidate width is timed (CUDA events, private stream, after one
+// warm-up launch, best of three) on a plain product C = P Q^T of the caller's shape, with the
+// caller's slice buffers as operands and `scratch` (rows x cols doubles) as output, and the
+// fastest width is kept per (device, slice kind, shape class). The operands' contents do not
+// matter for the timing. Runs synchronously; returns 128 if a candidate fails to launch.
+int tune_tc_tile(const SliceBuf &P, const SliceBuf &Q, int rows, int cols, double *scratch)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int, int64_t>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, P.kind, (rows + 63) / 64, (cols + 63) / 64, (P.ld + 63) / 64);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int best = 128;
+    float best_ms = 1e30f;
+    int32_t *status = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess && cudaEventCreate(&e0) == cudaSuccess &&
+        cudaEventCreate(&e1) == cudaSuccess && cudaMalloc((void **)&status, sizeof(int32_t)) == cudaSuccess &&
+        cudaMemsetAsync(status, 0, sizeof(int32_t), st) == cudaSuccess) {
+        const int cands[3] = {128, 96, 64};
+        for (int bn : cands) {
+            TcParams p{};
+            p.rows = rows; p.cols = cols; p.epi = TC_EPI_STORE; p.out = scratch; p.ldo = cols;
+            p.status = status; p.bn = bn;
+            if (launch_gemm_tc(P, Q, p, nullptr, st) != cudaSuccess) continue;
+            float ms = 1e30f;
+            bool ok = true;
+            for (int r = 0; r < 3 && ok; r++) {
+                float t = 0.0f;
+                ok = cudaEventRecord(e0, st) == cudaSuccess && launch_gemm_tc(P, Q, p, nullptr, st) == cudaSuccess &&
+                     cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                     cudaEventElapsedTime(&t, e0, e1) == cudaSuccess;
+                if (ok && t < ms) ms = t;
+            }
+            if (ok && ms < best_ms) { best_ms = ms; best = bn; }
+        }
+        int32_t hs = 0;
+        cudaMemcpyAsync(&hs, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        if (hs != 0) best = 128;
+    }
+    cudaGetLastError();
+    if (status) cudaFree(status);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = best;
+    return best;
 }
 
 }  // namespace pfsm

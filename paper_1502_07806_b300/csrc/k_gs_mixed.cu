@@ -386,7 +386,7 @@ cudaError_t launch_gram_schmidt_mixed(pfsm_handle_s *h, cudaStream_t st)
     if ((e = launch_split(w.W, N, N, N, sY, false, nullptr, st)) != cudaSuccess) return e;
     if ((e = launch_split(w.F, N, N, N, sZ, false, nullptr, st)) != cudaSuccess) return e;
     TcParams t{};
-    t.rows = (int)N; t.cols = (int)N; t.ldo = N; t.status = w.status;
+    t.rows = (int)N; t.cols = (int)N; t.ldo = N; t.status = w.status; t.bn = h->tc_bn;
     t.epi = TC_EPI_RSUB; t.out = w.W; t.V = w.W;
     if ((e = launch_gemm_tc(sY, sZ, t, nullptr, st)) != cudaSuccess) return e;
     if ((e = launch_oz_split(w.F, N, N, N, dP, w.ozeP, st)) != cudaSuccess) return e;

@@ -73,6 +73,7 @@ struct pfsm_handle_s {
     int32_t mmax = 0;    // largest slice after cluster snap
     int32_t Mmax = 0;    // largest window
     int32_t cl = 8;      // CTAs per submatrix cluster
+    int32_t tc_bn = 128; // tile width of the split products (tuned at init for the handle's N)
     bool rows_in_smem = true;
     bool tri_blocked = false;      // mixed forms: blocked reduction (k_tridiag_panel)
     int32_t tri_rpw = 8;           // its rows-per-warp register capacity (8 or 24)
@@ -155,9 +156,11 @@ struct TcParams {
     const double *d, *eps, *alpha;
     const int32_t *plan; int nb;    // TC_EPI_Y0 window mask
     int lower_only;                 // skip output tiles strictly above the diagonal
+    int bn;                         // tile width 64, 96 or 128 (0: 128; lower-only products: 128)
     int32_t *status;
 };
 cudaError_t configure_tc_kernels();
+int tune_tc_tile(const SliceBuf &P, const SliceBuf &Q, int rows, int cols, double *scratch);
 cudaError_t launch_split(const double *src, int64_t rows, int64_t cols, int64_t ld, const SliceBuf &dst,
                          bool zero_diag, double *d, cudaStream_t st);
 cudaError_t launch_gemm_tc(const SliceBuf &P, const SliceBuf &Q, TcParams prm, SliceBuf *out_sl,

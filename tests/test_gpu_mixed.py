@@ -28,18 +28,21 @@ def pf():
 PRECISIONS = [("bf16", 2), ("tf32", 1)]
 
 
+@pytest.mark.parametrize("tile_n", [0, 64, 96, 128])
 @pytest.mark.parametrize("rows,cols,K", [(128, 128, 64), (200, 130, 333), (7, 300, 1000),
                                          (1280, 1280, 1280), (257, 129, 64)])
 @pytest.mark.parametrize("name,prec", PRECISIONS)
-def test_split_gemm_matches_fp64(pf, rows, cols, K, name, prec):
+def test_split_gemm_matches_fp64(pf, rows, cols, K, name, prec, tile_n):
+    """Every output-tile width (and the autotuned one, tile_n = 0) against the exact product,
+    including ragged tiles (cols 130, 300, 129 leave partial 64-, 96- and 128-column tiles)."""
     rng = np.random.default_rng(rows * 7 + cols + K)
     P = rng.standard_normal((rows, K)) * np.exp(rng.uniform(-3, 3, (rows, 1)))
     Q = rng.standard_normal((cols, K))
-    C = pf.split_gemm(torch.from_numpy(P).cuda(), torch.from_numpy(Q).cuda(), prec).cpu().numpy()
+    C = pf.split_gemm(torch.from_numpy(P).cuda(), torch.from_numpy(Q).cuda(), prec, tile_n).cpu().numpy()
     ref = P @ Q.T
     bound = np.abs(P) @ np.abs(Q).T
     err = np.max(np.abs(C - ref) / bound)
-    print(f"{name} {rows}x{cols}x{K}: max |C - PQ^T| / (|P||Q|^T) = {err:.2e}")
+    print(f"{name} {rows}x{cols}x{K} tile {tile_n}: max |C - PQ^T| / (|P||Q|^T) = {err:.2e}")
     # representation of the pieces (2^-24 BF16 x3, 2^-21 TF32 x2) plus FP32 accumulation in
     # tensor memory, which grows like sqrt(K) 2^-24 for random terms (4x margin)
     rep = 2.0 ** -24 if name == "bf16" else 2.0 ** -21
@@ -118,3 +121,16 @@ def test_mixed_without_iterations_matches_fp64(pf, name, prec):
     pe = np.max(projector_errors(b[1], a[1], b[0]))
     print(f"K=0 {name}: |dX0| = {dx:.2e}, |dlambda| = {dl:.2e}, projector = {pe:.2e}")
     assert dx < 1e-9 and dl < 1e-11 and pe < 1e-8
+
+
+def test_handles_report_the_tuned_tile_width(pf):
+    """A mixed handle picks its split products' tile width at init (one of the candidates); an
+    FP64 handle has none. The same shape class reuses the cached choice."""
+    p = wl.small_gapped(0)
+    widths = []
+    for prec in (2, 2, 0):
+        h = pf.Handle(p.n, p.nblocks, halo=p.halo, precision=prec)
+        h.solve(_dev(p.A), _dev(p.prev))
+        widths.append(h.profile()["gemm_tile_n"])
+        h.close()
+    assert widths[0] in (64, 96, 128) and widths[1] == widths[0] and widths[2] == 0
