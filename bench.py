@@ -311,7 +311,8 @@ def main():
             raise RuntimeError(f"{precision}: device status {pf.STATUS_NAMES.get(st, st)}")
         ph = {k: statistics.mean(pr[k] for pr in phases) for k in pf.PHASES[:5] + pf.SUB_PHASES}
         return dict(h=h, lam=lam, V=V, total=total, value=world * steps / total, phases=ph,
-                    launches=launches, clocks=sampler.summary() if sampler else None)
+                    launches=launches, clocks=sampler.summary() if sampler else None,
+                    gemm_tile_n=phases[-1].get("gemm_tile_n") if phases else None)
 
     main_run = measure(args.precision, args.steps, clocks=True)
     h = main_run["h"]
@@ -378,13 +379,16 @@ def main():
                    else "fallback 1.8 PFLOP/s bf16, of fallback") + \
                   ("" if args.precision == "bf16" else " x nominal TF32/BF16 ratio 1.1/2.25")
             products = 6 if args.precision == "bf16" else 3
+        eff = achieved * products if achieved else None
         return {"kernel": kern, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None,
+                "effective": eff, "effective_frac": (eff / peak) if eff else None,
                 "traffic": TRAFFIC.get((kern, args.precision)),
                 "per_launch": {"flops": fl["fs"] / fs_launches, "ms": fs_ms / fs_launches},
                 "timing": "Eq. 11 phase (its product launches and two operand splits) / launches, CUDA events",
-                "flop_convention": "algorithmic (each N^3 term once); tensor-core work is "
-                                   f"{products}x that in split products",
+                "flop_convention": "achieved: algorithmic (each N^3 term once); effective: the tensor-core "
+                                   f"work actually issued, {products}x that in split products",
+                "tile_n": main_run.get("gemm_tile_n"),
                 "peak_source": src, "total_ms": fs_ms}
 
     def tridiag_roofline():
