@@ -1015,16 +1015,17 @@ __device__ __forceinline__ void cp_async8(double *dst, const double *src)
 
 // Back-transform y = H_0 H_1 ... H_{M-3} z of the selected eigenvectors z of T_b, then the sign
 // rule, zero padding to length N, the shift eps and the step alpha, written straight into X.
-// One-dimensional grid, 128 threads: window b owns ceil(m_b / vpc) consecutive CTAs, each taking
-// up to vpc <= 4 NV consecutive vectors of the window, warp w the vectors w, w+4, ... (NV per warp,
-// lanes along the rows). The work is the FP64 pipe's (2 (M - k) FMAs per reflector and vector),
-// so the launch gives every SM at most one CTA and every sub-partition at most NV vectors. The reflectors pass through shared memory in
-// double-buffered chunks of KC rows (cp.async, shared by the CTA's four warps), and the NV dot
-// products of a reflector are summed over the lanes by one transpose-reduce (6 FP64 adds for up to
-// four vectors instead of 5 per vector). Unused vector slots hold zeros and are computed but not
-// stored.
-template <int NV>
-__global__ void __launch_bounds__(128, 1)
+// One-dimensional grid, 32 NW threads: window b owns ceil(m_b / vpc) consecutive CTAs, each taking
+// up to vpc <= NW NV consecutive vectors of the window, warp w the vectors w, w+NW, ... (NV per
+// warp, lanes along the rows). The work is the FP64 pipe's (2 (M - k) FMAs per reflector and
+// vector), so the launch gives every SM at most one CTA; with NW = 8 two warps share each
+// sub-partition (one's dot-reduce-update chain hides behind the other's FMAs) and a
+// sub-partition holds at most three vectors (vpc <= 10). The reflectors pass through shared memory
+// in double-buffered chunks of KC rows (cp.async, shared by the CTA's warps), and the NV dot
+// products of a reflector are summed over the lanes by one transpose-reduce. Unused vector slots
+// hold zeros and are computed but not stored.
+template <int NV, int NW>
+__global__ void __launch_bounds__(32 * NW, 1)
 k_backtransform(const int32_t *__restrict__ plan, int32_t nb, int64_t N, int32_t Mmax, int32_t mmax,
                 const double *__restrict__ refl, const double *__restrict__ tau,
                 const double *__restrict__ sel_val, const double *__restrict__ sel_vec,
@@ -1044,18 +1045,18 @@ k_backtransform(const int32_t *__restrict__ plan, int32_t nb, int64_t N, int32_t
     const int nvc = min(vpc, mb - tbeg);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     extern __shared__ double smb[];
-    double *zs = smb;                                     // [4 NV][Mmax] vector slots (slot w + 4 j)
-    double *ts = zs + (size_t)4 * NV * Mmax;              // [Mmax] tau
+    double *zs = smb;                                     // [NW NV][Mmax] vector slots (slot w + NW j)
+    double *ts = zs + (size_t)NW * NV * Mmax;             // [Mmax] tau
     double *rs = ts + Mmax;                               // [2][kc][Mmax] reflector chunks
     const double *brefl = refl + (size_t)b * Mmax * Mmax;
-    for (int q = 0; q < 4 * NV; q++) {
+    for (int q = 0; q < NW * NV; q++) {
         const double *src = sel_vec + ((size_t)b * mmax + tbeg + q) * Mmax;
         for (int i = tid; i < M; i += blockDim.x) zs[(size_t)q * Mmax + i] = (q < nvc) ? src[i] : 0.0;
     }
     for (int i = tid; i < M; i += blockDim.x) ts[i] = tau[(size_t)b * Mmax + i];
     double *z[NV];
 #pragma unroll
-    for (int j = 0; j < NV; j++) z[j] = zs + (size_t)(warp + 4 * j) * Mmax;
+    for (int j = 0; j < NV; j++) z[j] = zs + (size_t)(warp + NW * j) * Mmax;
     const int nk = M - 2;                                 // reflectors k = M-3 .. 0
     const int nch = nk > 0 ? (nk + kc - 1) / kc : 0;
     auto issue = [&](int c) {
@@ -1125,7 +1126,7 @@ k_backtransform(const int32_t *__restrict__ plan, int32_t nb, int64_t N, int32_t
     const double glo = gersh[2 * N], ghi = gersh[2 * N + 1];
 #pragma unroll
     for (int j = 0; j < NV; j++) {
-        const int lt = warp + 4 * j;
+        const int lt = warp + NW * j;
         if (lt >= nvc) break;                             // warp-uniform
         const int t = tbeg + lt;
         const double *zz = z[j];
@@ -1162,10 +1163,10 @@ k_backtransform(const int32_t *__restrict__ plan, int32_t nb, int64_t N, int32_t
     }
 }
 
-// Shared memory of k_backtransform<NV> with chunks of kc reflectors.
-size_t backtransform_smem(int Mmax, int nv, int kc)
+// Shared memory of k_backtransform<NV, NW> with chunks of kc reflectors.
+size_t backtransform_smem(int Mmax, int nv, int nw, int kc)
 {
-    return ((size_t)4 * nv * Mmax + Mmax + (size_t)2 * kc * Mmax) * sizeof(double);
+    return ((size_t)nw * nv * Mmax + Mmax + (size_t)2 * kc * Mmax) * sizeof(double);
 }
 
 // Function attributes are process-wide while handles differ in window size, so every attribute
@@ -1240,9 +1241,9 @@ cudaError_t configure_kernels(pfsm_handle_s *h)
     if ((e = cudaFuncSetAttribute(k_tridiag_panel<24>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
     if ((e = set_max((const void *)k_bisect)) != cudaSuccess) return e;
     if ((e = set_max((const void *)k_inverse_iter)) != cudaSuccess) return e;
-    if ((e = set_max((const void *)k_backtransform<1>)) != cudaSuccess) return e;
-    if ((e = set_max((const void *)k_backtransform<2>)) != cudaSuccess) return e;
-    return set_max((const void *)k_backtransform<3>);
+    if ((e = set_max((const void *)k_backtransform<1, 4>)) != cudaSuccess) return e;
+    if ((e = set_max((const void *)k_backtransform<2, 4>)) != cudaSuccess) return e;
+    return set_max((const void *)k_backtransform<2, 8>);
 }
 
 cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
@@ -1337,25 +1338,34 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
     // 4. back-transform + start vectors
     {
         // vectors per CTA: the fewest for which sum_b ceil(m_b / vpc) <= N / vpc + nb CTAs fit
-        // one per SM, capped at what 4 warps x NV vectors take; NV and the reflector chunk KC as
-        // large as shared memory allows (NV <= 3, KC <= 16)
+        // one per SM; eight warps of up to two vectors (<= 3 per sub-partition for vpc <= 10) when
+        // shared memory holds them, else four warps of NV <= 2; the reflector chunk KC as large as
+        // shared memory allows (<= 16)
         const size_t cap = kInvSmemCap;
-        int nv = 3, kc = 16;
-        while (nv > 1 && backtransform_smem(Mmax, nv, 1) > cap) nv--;
-        while (kc > 1 && backtransform_smem(Mmax, nv, kc) > cap) kc >>= 1;
         const int64_t slots = std::max<int64_t>(1, (int64_t)sm_count() - nb);
-        int vpc = (int)std::min<int64_t>(4 * nv, std::max<int64_t>(1, (h->N + slots - 1) / slots));
+        const int want = (int)std::max<int64_t>(1, (h->N + slots - 1) / slots);
+        int nw = 8, nv = 2;
+        if (want > 10 || backtransform_smem(Mmax, 2, 8, 1) > cap) {
+            nw = 4;
+            nv = backtransform_smem(Mmax, 2, 4, 1) <= cap ? 2 : 1;
+        }
+        int kc = 16;
+        while (kc > 1 && backtransform_smem(Mmax, nv, nw, kc) > cap) kc >>= 1;
+        const int vpc = std::min(want, nw == 8 ? 10 : nw * nv);
         dim3 grid((unsigned)((h->N + vpc - 1) / vpc + nb));
-        const size_t smem = backtransform_smem(Mmax, nv, kc);
-        if (nv == 3)
-            k_backtransform<3><<<grid, 128, smem, st>>>(w.plan, nb, h->N, Mmax, mmax, w.refl, w.tau, w.sel_val, w.sel_vec,
-                                                     w.gersh, h->prm.alpha_theta, vpc, kc, w.X, w.eps, w.alpha);
+        const size_t smem = backtransform_smem(Mmax, nv, nw, kc);
+        if (nw == 8)
+            k_backtransform<2, 8><<<grid, 256, smem, st>>>(w.plan, nb, h->N, Mmax, mmax, w.refl, w.tau, w.sel_val,
+                                                        w.sel_vec, w.gersh, h->prm.alpha_theta, vpc, kc, w.X, w.eps,
+                                                        w.alpha);
         else if (nv == 2)
-            k_backtransform<2><<<grid, 128, smem, st>>>(w.plan, nb, h->N, Mmax, mmax, w.refl, w.tau, w.sel_val, w.sel_vec,
-                                                     w.gersh, h->prm.alpha_theta, vpc, kc, w.X, w.eps, w.alpha);
+            k_backtransform<2, 4><<<grid, 128, smem, st>>>(w.plan, nb, h->N, Mmax, mmax, w.refl, w.tau, w.sel_val,
+                                                        w.sel_vec, w.gersh, h->prm.alpha_theta, vpc, kc, w.X, w.eps,
+                                                        w.alpha);
         else
-            k_backtransform<1><<<grid, 128, smem, st>>>(w.plan, nb, h->N, Mmax, mmax, w.refl, w.tau, w.sel_val, w.sel_vec,
-                                                     w.gersh, h->prm.alpha_theta, vpc, kc, w.X, w.eps, w.alpha);
+            k_backtransform<1, 4><<<grid, 128, smem, st>>>(w.plan, nb, h->N, Mmax, mmax, w.refl, w.tau, w.sel_val,
+                                                        w.sel_vec, w.gersh, h->prm.alpha_theta, vpc, kc, w.X, w.eps,
+                                                        w.alpha);
         g_launches++;
         return cudaGetLastError();
     }
