@@ -18,6 +18,11 @@ Parity status per function (what pins it; see ``tests/test_oracle_pins.py``):
                monotone error over an SCF-like sequence
   backward     pinned: sum(lambda) -> identity, occupied sum -> projector, central finite
                differences of the exact eigen-map
+  gen_to_std   pinned: LAPACK solve(B, A) at convergence, the closed-form Neumann sum of the
+               iteration after a fixed count, diagonal B exact in one update, divergence of a
+               non-dominant B reported
+  gen_to_std_sym pinned: eigendecomposition-based B^{-1/2}, LAPACK generalized eigenvalues
+               (sygvd via scipy) of (A, B), B-orthonormal generalized eigenvectors x = S y
 """
 from __future__ import annotations
 
@@ -70,6 +75,8 @@ def _load():
         lib.oracle_pfsm.argtypes = [i64, i32, P, P, P, P, P, P, P, P, P, P]
         lib.oracle_backward.argtypes = [i64, P, P, P, P, f64, P]
         lib.oracle_backward.restype = None
+        lib.oracle_gen_to_std.argtypes = [i64, P, P, P, i32, f64, P, P]
+        lib.oracle_gen_to_std_sym.argtypes = [i64, P, P, P, P, i32, f64, P, P]
         _lib = lib
     return _lib
 
@@ -205,3 +212,30 @@ def backward(V, lam, dlam, dV, tau: float = 1e-8):
     dA = np.zeros((n, n))
     _load().oracle_backward(n, _p(V), _p(lam), _p(dlam), _p(dV), tau, _p(dA))
     return dA
+
+
+def gen_to_std(A, B, max_iters: int = 50, tol: float = 1e-14):
+    """Z = B^{-1} A by the Jacobi iteration of Eq. 14 (from Z_0 = 0). Returns (Z, iters, resid,
+    status): status OK or NOT_CONVERGED (Z is then the last iterate)."""
+    A, B = _f64(A), _f64(B)
+    n = A.shape[0]
+    Z = np.zeros((n, n))
+    it, r = ctypes.c_int32(), ctypes.c_double()
+    st = _load().oracle_gen_to_std(n, _p(A), _p(B), _p(Z), max_iters, tol, ctypes.byref(it), ctypes.byref(r))
+    if st not in (OK, NOT_CONVERGED):
+        raise OracleError(st, "gen_to_std")
+    return Z, it.value, r.value, st
+
+
+def gen_to_std_sym(A, B, max_iters: int = 50, tol: float = 1e-14):
+    """Symmetric conversion C = B^{-1/2} A B^{-1/2} with S = B^{-1/2} by Newton-Schulz.
+    Returns (C, S, iters, resid, status)."""
+    A, B = _f64(A), _f64(B)
+    n = A.shape[0]
+    C, S = np.zeros((n, n)), np.zeros((n, n))
+    it, r = ctypes.c_int32(), ctypes.c_double()
+    st = _load().oracle_gen_to_std_sym(n, _p(A), _p(B), _p(C), _p(S), max_iters, tol, ctypes.byref(it),
+                                       ctypes.byref(r))
+    if st not in (OK, NOT_CONVERGED):
+        raise OracleError(st, "gen_to_std_sym")
+    return C, S, it.value, r.value, st

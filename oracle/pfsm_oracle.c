@@ -494,3 +494,122 @@ void oracle_backward(int64_t n, const double *V, const double *lam, const double
     free(G);
     free(T);
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Generalized -> standard conversion, Eq. 14-15 (not on the eigensolver's hot path: the step */
+/* before it). A x = lambda B x with B diagonally dominant; Z = B^{-1} A by the Jacobi        */
+/* iteration of Eq. 14,  Z_{n+1} = (I - D^{-1} B) Z_n + D^{-1} A,  D = diag(B), written as     */
+/* Z_{n+1} = Z_n + D^{-1} (A - B Z_n), from Z_0 = 0 (so Z_1 = D^{-1} A: the identity-like     */
+/* first approximation of B^{-1} the paper describes). Before each update the residual        */
+/* R_n = A - B Z_n is measured; the iteration stops when max|R_n| <= tol max|A| or after       */
+/* max_iters updates. A, B, Z: n x n row-major. *iters = updates done, *resid = max|R| /       */
+/* max|A| of the returned Z. Returns OR_OK, OR_NOT_CONVERGED (Z = last iterate) or             */
+/* OR_INVALID_ARG (a zero diagonal entry of B).                                               */
+/* ------------------------------------------------------------------------------------------ */
+int oracle_gen_to_std(int64_t n, const double *A, const double *B, double *Z, int32_t max_iters,
+                      double tol, int32_t *iters, double *resid)
+{
+    for (int64_t i = 0; i < n; i++)
+        if (B[i * n + i] == 0.0) return OR_INVALID_ARG;
+    double amax = 0.0;
+    for (int64_t i = 0; i < n * n; i++) amax = fmax(amax, fabs(A[i]));
+    if (amax == 0.0) amax = 1.0;
+    double *R = (double *)malloc(sizeof(double) * (size_t)(n * n));
+    for (int64_t i = 0; i < n * n; i++) Z[i] = 0.0;
+    int status = OR_NOT_CONVERGED;
+    int32_t it = 0;
+    double r = 0.0;
+    for (;;) {
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; i++)              /* R = A - B Z */
+            for (int64_t j = 0; j < n; j++) {
+                double acc = 0.0;
+                for (int64_t k = 0; k < n; k++) acc += B[i * n + k] * Z[k * n + j];
+                R[i * n + j] = A[i * n + j] - acc;
+            }
+        r = 0.0;
+        for (int64_t i = 0; i < n * n; i++) r = fmax(r, fabs(R[i]));
+        r /= amax;
+        if (r <= tol) { status = OR_OK; break; }
+        if (it >= max_iters) break;
+        for (int64_t i = 0; i < n; i++)              /* Z += D^{-1} R */
+            for (int64_t j = 0; j < n; j++) Z[i * n + j] += R[i * n + j] / B[i * n + i];
+        it++;
+    }
+    free(R);
+    *iters = it;
+    *resid = r;
+    return status;
+}
+
+/* C = X Y for n x n row-major matrices (plain loops). */
+static void or_matmul(int64_t n, const double *X, const double *Y, double *C)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++)
+        for (int64_t j = 0; j < n; j++) {
+            double acc = 0.0;
+            for (int64_t k = 0; k < n; k++) acc += X[i * n + k] * Y[k * n + j];
+            C[i * n + j] = acc;
+        }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Symmetric form of the conversion (a deviation from Eq. 14-15: the eigensolver needs a      */
+/* symmetric matrix and B^{-1} A is not one): C = B^{-1/2} A B^{-1/2}, whose eigenvalues are   */
+/* those of B^{-1} A and whose eigenvectors y give the generalized ones as x = B^{-1/2} y      */
+/* (B-orthonormal). S = B^{-1/2} by the coupled Newton-Schulz iteration for the matrix square */
+/* root and its inverse (Higham, Functions of Matrices, 2008): with c = the largest Gershgorin */
+/* row bound of B (so the eigenvalues of B / c lie in (0, 1]),                               */
+/*   Y_0 = B / c, Q_0 = I;  P_k = Q_k Y_k;  T_k = (3 I - P_k) / 2;  Y_{k+1} = Y_k T_k;          */
+/*   Q_{k+1} = T_k Q_k,                                                                        */
+/* Y_k -> (B/c)^{1/2}, Q_k -> (B/c)^{-1/2}; it stops when max|I - P_k| <= tol (checked before  */
+/* each update) or after max_iters updates; then S = Q / sqrt(c) and C = S A S. A, B, C, S:    */
+/* n x n row-major. *iters = updates done, *resid = max|I - P| at the stop. Returns OR_OK,     */
+/* OR_NOT_CONVERGED or OR_NOT_SPD (a row bound c <= 0).                                       */
+/* ------------------------------------------------------------------------------------------ */
+int oracle_gen_to_std_sym(int64_t n, const double *A, const double *B, double *C, double *S,
+                          int32_t max_iters, double tol, int32_t *iters, double *resid)
+{
+    double c = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        double row = 0.0;
+        for (int64_t j = 0; j < n; j++) row += fabs(B[i * n + j]);
+        c = fmax(c, row);
+    }
+    if (!(c > 0.0)) return OR_NOT_SPD;
+    const size_t sz = sizeof(double) * (size_t)(n * n);
+    double *Y = (double *)malloc(sz), *Q = (double *)malloc(sz), *P = (double *)malloc(sz);
+    double *T = (double *)malloc(sz), *W = (double *)malloc(sz);
+    for (int64_t i = 0; i < n; i++)
+        for (int64_t j = 0; j < n; j++) {
+            Y[i * n + j] = B[i * n + j] / c;
+            Q[i * n + j] = (i == j) ? 1.0 : 0.0;
+        }
+    int status = OR_NOT_CONVERGED;
+    int32_t it = 0;
+    double r = 0.0;
+    for (;;) {
+        or_matmul(n, Q, Y, P);                       /* P = Q Y */
+        r = 0.0;
+        for (int64_t i = 0; i < n; i++)
+            for (int64_t j = 0; j < n; j++) r = fmax(r, fabs(((i == j) ? 1.0 : 0.0) - P[i * n + j]));
+        if (r <= tol) { status = OR_OK; break; }
+        if (it >= max_iters) break;
+        for (int64_t i = 0; i < n; i++)              /* T = (3 I - P) / 2 */
+            for (int64_t j = 0; j < n; j++) T[i * n + j] = 0.5 * (((i == j) ? 3.0 : 0.0) - P[i * n + j]);
+        or_matmul(n, Y, T, W);                       /* Y = Y T */
+        memcpy(Y, W, sz);
+        or_matmul(n, T, Q, W);                       /* Q = T Q */
+        memcpy(Q, W, sz);
+        it++;
+    }
+    const double isc = 1.0 / sqrt(c);
+    for (int64_t i = 0; i < n * n; i++) S[i] = Q[i] * isc;
+    or_matmul(n, S, A, W);                           /* C = S A S */
+    or_matmul(n, W, S, C);
+    free(Y); free(Q); free(P); free(T); free(W);
+    *iters = it;
+    *resid = r;
+    return status;
+}

@@ -38,6 +38,15 @@ MUTANTS = {
     "backward_transposed_operand": ("acc += V[r * n + i] * dV[r * n + j];",
                                     "acc += V[i * n + r] * dV[r * n + j];"),
     "sign_rule_dropped": ("flip = (yh < 0.0) ? -1.0 : 1.0;", "flip = 1.0;"),
+    "jacobi_drops_dinv": ("Z[i * n + j] += R[i * n + j] / B[i * n + i];", "Z[i * n + j] += R[i * n + j];"),
+    "jacobi_update_sign": ("Z[i * n + j] += R[i * n + j] / B[i * n + i];",
+                           "Z[i * n + j] -= R[i * n + j] / B[i * n + i];"),
+    "jacobi_transposed_product": ("for (int64_t k = 0; k < n; k++) acc += B[i * n + k] * Z[k * n + j];",
+                                  "for (int64_t k = 0; k < n; k++) acc += B[k * n + i] * Z[j * n + k];"),
+    "newton_schulz_sign": ("T[i * n + j] = 0.5 * (((i == j) ? 3.0 : 0.0) - P[i * n + j]);",
+                           "T[i * n + j] = 0.5 * (((i == j) ? 3.0 : 0.0) + P[i * n + j]);"),
+    "newton_schulz_no_rescale": ("for (int64_t i = 0; i < n * n; i++) S[i] = Q[i] * isc;",
+                                 "for (int64_t i = 0; i < n * n; i++) S[i] = Q[i];"),
 }
 
 

@@ -451,3 +451,79 @@ def test_backward_masks_degenerate_pairs(orc):
     assert dA[1, 2] == 0.0 and dA[2, 1] == 0.0
     assert dA[0, 1] == pytest.approx(0.5 * (1.0 / (1.0 - 0.0) + 1.0 / (0.0 - 1.0)))
     assert np.all(np.diag(dA) == 0.0)
+
+
+# ---- generalized -> standard conversion (Eq. 14-15) ---------------------------------------
+
+def test_gen_to_std_reaches_lapack_solve(orc):
+    """At convergence the Jacobi iterate is B^{-1} A, checked against LAPACK's LU solve."""
+    for n, seed in ((12, 1), (57, 2), (96, 3)):
+        A, B = wl.generalized_pair(n, seed)
+        Z, it, r, st = orc.gen_to_std(A, B, max_iters=200, tol=1e-15)
+        assert st == 0 and r <= 1e-15 and 3 <= it < 200
+        ref = np.linalg.solve(B, A)
+        assert np.max(np.abs(Z - ref)) <= 1e-14 * np.max(np.abs(ref))
+
+
+def test_gen_to_std_fixed_count_is_the_neumann_sum(orc):
+    """After k updates from Z_0 = 0: Z_k = sum_{j<k} (I - D^-1 B)^j D^-1 A (closed form of Eq. 14)."""
+    n = 20
+    A, B = wl.generalized_pair(n, 4, sigma_b=3e-2)
+    for k in (1, 2, 5):
+        Z, it, r, st = orc.gen_to_std(A, B, max_iters=k, tol=0.0)
+        assert it == k and st == 5 and r > 0.0
+        Dinv = np.diag(1.0 / np.diag(B))
+        G = np.eye(n) - Dinv @ B
+        ref, term = np.zeros((n, n)), Dinv @ A
+        for _ in range(k):
+            ref += term
+            term = G @ term
+        assert np.max(np.abs(Z - ref)) <= 1e-14 * np.max(np.abs(ref))
+        assert r == pytest.approx(np.max(np.abs(A - B @ ref)) / np.max(np.abs(A)), rel=1e-9, abs=1e-17)
+
+
+def test_gen_to_std_diagonal_b_is_exact_in_one_update(orc):
+    n = 9
+    A = wl.random_nearly_diagonal(n, seed=5, sigma=0.1, decay=None).A
+    d = 0.5 + np.arange(n) / n
+    Z, it, r, st = orc.gen_to_std(A, np.diag(d), max_iters=10, tol=1e-15)
+    assert st == 0 and it == 1
+    assert np.array_equal(Z, A / d[:, None])
+
+
+def test_gen_to_std_reports_divergence_and_bad_input(orc):
+    n = 8
+    A = np.eye(n)
+    B = np.full((n, n), 0.5) + 0.1 * np.eye(n)             # not diagonally dominant
+    Z, it, r, st = orc.gen_to_std(A, B, max_iters=30, tol=1e-14)
+    assert st == 5 and it == 30 and r > 1.0
+    with pytest.raises(orc.OracleError):
+        orc.gen_to_std(A, B - np.diag(np.diag(B)))            # zero diagonal
+
+
+def test_gen_to_std_sym_matches_eigendecomposition(orc):
+    """S = B^{-1/2} against the eigendecomposition of B; C's eigenvalues against LAPACK's
+    generalized eigensolver (sygvd); x = S y are B-orthonormal generalized eigenvectors."""
+    import scipy.linalg as sla
+    for n, seed in ((10, 6), (48, 7)):
+        A, B = wl.generalized_pair(n, seed, sigma_b=2e-2)
+        C, S, it, r, st = orc.gen_to_std_sym(A, B, max_iters=60, tol=1e-14)
+        assert st == 0 and r <= 1e-14
+        w, U = np.linalg.eigh(B)
+        Sref = (U * w ** -0.5) @ U.T
+        assert np.max(np.abs(S - Sref)) <= 1e-13
+        assert np.max(np.abs(C - C.T)) <= 1e-13
+        lam_g = sla.eigh(A, B, eigvals_only=True)
+        lam, Y = np.linalg.eigh(C)
+        assert np.max(np.abs(lam - lam_g)) <= 1e-13 * np.max(np.abs(lam_g))
+        X = S @ Y
+        assert np.max(np.abs(X.T @ B @ X - np.eye(n))) <= 1e-12
+        assert np.max(np.abs(A @ X - (B @ X) * lam)) <= 1e-12
+
+
+def test_gen_to_std_sym_identity_b_is_exact(orc):
+    n = 7
+    A = wl.random_nearly_diagonal(n, seed=8, sigma=0.2, decay=None).A
+    C, S, it, r, st = orc.gen_to_std_sym(A, np.eye(n), max_iters=5, tol=0.0)
+    # B = I: c = 1, Y_0 = Q_0 = I, T = I, the iterates never move and C = A exactly
+    assert np.array_equal(S, np.eye(n)) and np.array_equal(C, A) and r == 0.0

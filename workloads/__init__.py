@@ -205,6 +205,19 @@ def random_nearly_diagonal(n: int, seed: int, sigma: float = 1e-3, decay: float 
     return Problem(f"rnd{n}_{seed}", _assemble(lam, E), lam, nblocks, halo=halo)
 
 
+def generalized_pair(n: int, seed: int, sigma_a: float = 1e-3, sigma_b: float = 5e-3,
+                     decay: float | None = 16.0, b_spread: float = 0.1):
+    """Inputs A x = lambda B x of the generalized -> standard conversion (Eq. 14-15): A nearly
+    diagonal like the reduced Hamiltonian (lam sorted U[-1, 1], coupling sigma_a), B an overlap
+    matrix close to the identity (ultrasoft pseudopotentials): diagonal 1 + U[0, b_spread],
+    off-diagonal sigma_b N(0,1) exp(-|i-j|/decay), diagonally dominant. Returns (A, B)."""
+    A = random_nearly_diagonal(n, seed, sigma=sigma_a, decay=decay).A
+    st = _Stream(seed + 11)
+    d = 1.0 + b_spread * st.uniform(n)
+    B = _assemble(d, coupling(n, sigma_b, decay, _Stream(seed + 13)))
+    return A, B
+
+
 def symmetric_direction(n: int, seed: int) -> np.ndarray:
     """Random symmetric perturbation direction with unit Frobenius norm."""
     iu, ju = np.triu_indices(n)
