@@ -64,7 +64,8 @@ typedef enum {
     PFSM_ERR_CUDA = 2,          /* a CUDA runtime call failed; see pfsm_last_error() */
     PFSM_ERR_NOT_SPD = 3,       /* Gram-Schmidt breakdown: overlap matrix not positive definite */
     PFSM_ERR_NAN_INPUT = 4,     /* A or prev_eigvals holds NaN or Inf */
-    PFSM_ERR_NOT_CONVERGED = 5, /* a submatrix eigensolve did not converge */
+    PFSM_ERR_NOT_CONVERGED = 5, /* a submatrix eigensolve did not converge, or an iterative
+                                   conversion missed its tolerance */
     PFSM_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
     PFSM_ERR_NO_SOLVE = 7,      /* pfsm_backward called before any pfsm_solve on the handle */
     PFSM_ERR_OUT_OF_MEMORY = 8  /* workspace allocation failed in pfsm_init */
@@ -206,6 +207,35 @@ int pfsm_split_gemm_ex(int64_t rows, int64_t cols, int64_t K, const double *P, c
  * must be serialised by the caller. Nothing in it needs clearing between calls. */
 int pfsm_fs_iterate_noalloc(int64_t N, int64_t count, const double *A, double *X,
                             const double *eps, const double *alpha, int32_t iters, void *stream);
+
+/* ---- generalized -> standard conversion (Eq. 14-15), the step before the eigensolve ----------
+ * A x = lambda B x with A symmetric and B the symmetric, diagonally dominant overlap matrix; all
+ * matrices N x N row-major FP64 on the device (N <= 65535), A and B read only. Both run on
+ * `stream`, allocate their temporaries with cudaMallocAsync, read one residual per iteration back
+ * to the host (so they synchronise the stream) and write *iters_out (updates done) and
+ * *resid_out (the stopping residual) when those host pointers are non-null. Products are the
+ * FP64-accurate digit products of pfsm_split_gemm(..., PFSM_FP64); the residuals they measure
+ * have a floor of a few sqrt(N) 2^-46 (6.5e-13 for the Jacobi residual at N = 1280, 1.6e-12
+ * for max|I - Q Y| at N = 200), so tol should stay above it (1e-12 and 1e-11).
+ *
+ * pfsm_gen_to_std: Z = B^{-1} A by the Jacobi iteration of Eq. 14,
+ *   Z_{n+1} = (I - D^{-1} B) Z_n + D^{-1} A,  D = diag(B),  Z_0 = 0,
+ * stopped before an update when max|A - B Z_n| <= tol max|A| or after max_iters updates.
+ * Returns PFSM_OK, PFSM_ERR_NOT_CONVERGED (Z holds the last iterate), PFSM_ERR_INVALID_ARG
+ * (bad arguments, or a zero diagonal entry of B: Z untouched), PFSM_ERR_CUDA. */
+int pfsm_gen_to_std(int64_t N, const double *A, const double *B, double *Z, int32_t max_iters, double tol,
+                    int32_t *iters_out, double *resid_out, void *stream);
+
+/* Symmetric form of the conversion (not in the paper, which leaves B^{-1} A non-symmetric; the
+ * eigensolver needs a symmetric matrix): C = B^{-1/2} A B^{-1/2} and S = B^{-1/2}, so that C has
+ * the eigenvalues of A x = lambda B x and its eigenvectors y give x = S y (B-orthonormal).
+ * S by the coupled Newton-Schulz iteration for the inverse square root (c = the largest
+ * Gershgorin row bound of B; Y_0 = B / c, Q_0 = I; T = (3 I - Q Y) / 2; Y <- Y T; Q <- T Q),
+ * stopped before an update when max|I - Q Y| <= tol or after max_iters updates; S = Q / sqrt(c),
+ * C = S A S. Returns PFSM_OK, PFSM_ERR_NOT_CONVERGED (C, S from the last iterate),
+ * PFSM_ERR_NOT_SPD (no positive row bound), PFSM_ERR_INVALID_ARG, PFSM_ERR_CUDA. */
+int pfsm_gen_to_std_sym(int64_t N, const double *A, const double *B, double *C, double *S, int32_t max_iters,
+                        double tol, int32_t *iters_out, double *resid_out, void *stream);
 
 /* Per-call instrumentation, for benchmarks and profiling. */
 typedef struct {

@@ -24,7 +24,8 @@ DIAG_RESIDUALS, DIAG_XFS, DIAG_EPS, DIAG_ALPHA, DIAG_PLAN = range(5)
 EXPORTED = ("pfsm_default_params", "pfsm_init", "pfsm_solve", "pfsm_backward", "pfsm_get_status",
             "pfsm_get_diagnostic", "pfsm_set_timing", "pfsm_get_profile", "pfsm_last_error",
             "pfsm_destroy", "pfsm_fs_iterate_noalloc", "pfsm_split_gemm", "pfsm_split_gemm_ex", "pfsm_batch_init",
-            "pfsm_solve_batched", "pfsm_batch_get_status", "pfsm_batch_destroy")
+            "pfsm_solve_batched", "pfsm_batch_get_status", "pfsm_batch_destroy", "pfsm_gen_to_std",
+            "pfsm_gen_to_std_sym")
 PHASES = ("plan", "submatrix", "fs_iterations", "gram_schmidt", "rayleigh", "backward")
 SUB_PHASES = ("tridiag", "bisect", "inverse_iter", "backtransform", "overlap", "cholesky")
 
@@ -70,6 +71,8 @@ def load_library():
     lib.pfsm_fs_iterate_noalloc.argtypes = [i64, i64, P, P, P, P, i32, P]
     lib.pfsm_split_gemm.argtypes = [i64, i64, i64, P, P, P, i32, P]
     lib.pfsm_split_gemm_ex.argtypes = [i64, i64, i64, P, P, P, i32, i32, P]
+    lib.pfsm_gen_to_std.argtypes = [i64, P, P, P, i32, ctypes.c_double, P, P, P]
+    lib.pfsm_gen_to_std_sym.argtypes = [i64, P, P, P, P, i32, ctypes.c_double, P, P, P]
     lib.pfsm_batch_init.argtypes = [i32, P, P, ctypes.POINTER(Params), ctypes.POINTER(P)]
     lib.pfsm_solve_batched.argtypes = [P, P, P, P, P, P]
     lib.pfsm_batch_get_status.argtypes = [P, P]
@@ -270,6 +273,37 @@ def split_gemm(P: torch.Tensor, Q: torch.Tensor, precision: int = BF16_SPLIT, ti
     _check(load_library().pfsm_split_gemm_ex(rows, cols, K, _ptr(P), _ptr(Q), _ptr(C), precision, tile_n,
                                              _stream()), "pfsm_split_gemm_ex")
     return C
+
+
+def gen_to_std(A: torch.Tensor, B: torch.Tensor, max_iters: int = 50, tol: float = 1e-12,
+               check: bool = True):
+    """Z = B^-1 A by the Jacobi iteration of Eq. 14 on the device. Returns (Z, iters, resid);
+    with check=False a PFSM_ERR_NOT_CONVERGED result is returned instead of raised. The
+    residual is itself a digit product, with a floor of about sqrt(N) 2^-46: tol should stay
+    above it."""
+    n = A.shape[0]
+    Z = torch.empty(n, n, dtype=torch.float64, device=A.device)
+    it, r = ctypes.c_int32(), ctypes.c_double()
+    rc = load_library().pfsm_gen_to_std(n, _ptr(A), _ptr(B), _ptr(Z), max_iters, tol, ctypes.byref(it),
+                                        ctypes.byref(r), _stream())
+    if check or rc != 5:
+        _check(rc, "pfsm_gen_to_std")
+    return Z, it.value, r.value
+
+
+def gen_to_std_sym(A: torch.Tensor, B: torch.Tensor, max_iters: int = 50, tol: float = 1e-11,
+                   check: bool = True):
+    """C = B^-1/2 A B^-1/2 and S = B^-1/2 (Newton-Schulz) on the device. Returns (C, S, iters, resid).
+    The residual max|I - Q Y| has a floor of a few sqrt(N) 2^-46 (1.6e-12 at N = 200)."""
+    n = A.shape[0]
+    C = torch.empty(n, n, dtype=torch.float64, device=A.device)
+    S = torch.empty(n, n, dtype=torch.float64, device=A.device)
+    it, r = ctypes.c_int32(), ctypes.c_double()
+    rc = load_library().pfsm_gen_to_std_sym(n, _ptr(A), _ptr(B), _ptr(C), _ptr(S), max_iters, tol,
+                                            ctypes.byref(it), ctypes.byref(r), _stream())
+    if check or rc != 5:
+        _check(rc, "pfsm_gen_to_std_sym")
+    return C, S, it.value, r.value
 
 
 def solve(A: torch.Tensor, prev: torch.Tensor, nblocks: int, **kw):

@@ -484,6 +484,42 @@ int pfsm_split_gemm_ex(int64_t rows, int64_t cols, int64_t K, const double *P, c
     return PFSM_OK;
 }
 
+static int gen2std_result(const Gen2StdResult &r, int32_t *iters_out, double *resid_out, const char *who)
+{
+    if (iters_out) *iters_out = r.iters;
+    if (resid_out) *resid_out = r.resid;
+    switch (r.status) {
+    case PFSM_OK: return PFSM_OK;
+    case PFSM_ERR_INVALID_ARG: return fail(PFSM_ERR_INVALID_ARG, "%s: B has a zero diagonal entry", who);
+    case PFSM_ERR_NOT_SPD: return fail(PFSM_ERR_NOT_SPD, "%s: B has no positive row bound", who);
+    case PFSM_ERR_NOT_CONVERGED:
+        return fail(PFSM_ERR_NOT_CONVERGED, "%s: residual %.3e after %d updates", who, r.resid, r.iters);
+    default: return fail(r.status, "%s: device status %d", who, r.status);
+    }
+}
+
+int pfsm_gen_to_std(int64_t N, const double *A, const double *B, double *Z, int32_t max_iters, double tol,
+                    int32_t *iters_out, double *resid_out, void *stream)
+{
+    if (N < 1 || N > 65535 || !A || !B || !Z || max_iters < 0 || !(tol >= 0.0))
+        return fail(PFSM_ERR_INVALID_ARG, "pfsm_gen_to_std: bad size, pointer, max_iters or tol");
+    PFSM_CUDA(configure_oz_kernels());
+    Gen2StdResult r;
+    PFSM_CUDA(run_gen_to_std(N, A, B, Z, max_iters, tol, (cudaStream_t)stream, r));
+    return gen2std_result(r, iters_out, resid_out, "pfsm_gen_to_std");
+}
+
+int pfsm_gen_to_std_sym(int64_t N, const double *A, const double *B, double *C, double *S, int32_t max_iters,
+                        double tol, int32_t *iters_out, double *resid_out, void *stream)
+{
+    if (N < 1 || N > 65535 || !A || !B || !C || !S || max_iters < 0 || !(tol >= 0.0))
+        return fail(PFSM_ERR_INVALID_ARG, "pfsm_gen_to_std_sym: bad size, pointer, max_iters or tol");
+    PFSM_CUDA(configure_oz_kernels());
+    Gen2StdResult r;
+    PFSM_CUDA(run_gen_to_std_sym(N, A, B, C, S, max_iters, tol, (cudaStream_t)stream, r));
+    return gen2std_result(r, iters_out, resid_out, "pfsm_gen_to_std_sym");
+}
+
 int pfsm_set_timing(pfsm_handle_t h, int32_t enable)
 {
     if (!h) return fail(PFSM_ERR_INVALID_ARG, "pfsm_set_timing: null handle");

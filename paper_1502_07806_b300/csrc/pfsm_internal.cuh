@@ -188,6 +188,17 @@ struct OzParams {
 };
 cudaError_t configure_oz_kernels();
 int sm_count();                     // multiprocessors of the current device (cached)
+// ---- generalized -> standard conversion (k_gen2std.cu) ----
+struct Gen2StdResult {
+    int iters = 0;                  // updates done
+    double resid = 0.0;             // stopping residual of the returned result
+    int status = 0;                 // PFSM_OK, PFSM_ERR_NOT_CONVERGED, PFSM_ERR_INVALID_ARG (zero
+                                    // diagonal of B), PFSM_ERR_NOT_SPD, or a device status
+};
+cudaError_t run_gen_to_std(int64_t N, const double *A, const double *B, double *Z, int max_iters, double tol,
+                           cudaStream_t st, Gen2StdResult &res);
+cudaError_t run_gen_to_std_sym(int64_t N, const double *A, const double *B, double *C, double *S, int max_iters,
+                               double tol, cudaStream_t st, Gen2StdResult &res);
 cudaError_t launch_oz_split(const double *src, int64_t rows, int64_t cols, int64_t ld, const SliceBuf &dst,
                             int32_t *exps, cudaStream_t st, bool zero_diag = false, double *d = nullptr);
 cudaError_t launch_oz_split_f32(const float *src, int64_t rows, int64_t cols, int64_t ld, const SliceBuf &dst,
