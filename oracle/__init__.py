@@ -23,6 +23,11 @@ Parity status per function (what pins it; see ``tests/test_oracle_pins.py``):
                non-dominant B reported
   gen_to_std_sym pinned: eigendecomposition-based B^{-1/2}, LAPACK generalized eigenvalues
                (sygvd via scipy) of (A, B), B-orthonormal generalized eigenvectors x = S y
+  guard        pinned: diagonal input 0, 2x2 closed form |b| / |a - d|, hand-worked 3x3, the
+               paper's mixed-eigenvector counterexample far above the workloads' values
+  full         pinned: LAPACK (numpy) eigenvalues and eigenvectors up to the sign rule, the sign
+               rule itself, equality with the method for one block and no Eq. 11 iterations
+  pfsm_guarded pinned through guard, full and pfsm
 """
 from __future__ import annotations
 
@@ -77,6 +82,9 @@ def _load():
         lib.oracle_backward.restype = None
         lib.oracle_gen_to_std.argtypes = [i64, P, P, P, i32, f64, P, P]
         lib.oracle_gen_to_std_sym.argtypes = [i64, P, P, P, P, i32, f64, P, P]
+        lib.oracle_guard.argtypes = [i64, P, P]
+        lib.oracle_guard.restype = None
+        lib.oracle_full.argtypes = [i64, P, P, P, P]
         _lib = lib
     return _lib
 
@@ -239,3 +247,37 @@ def gen_to_std_sym(A, B, max_iters: int = 50, tol: float = 1e-14):
     if st not in (OK, NOT_CONVERGED):
         raise OracleError(st, "gen_to_std_sym")
     return C, S, it.value, r.value, st
+
+
+def guard(A) -> float:
+    """Diagonal-dominance value g of A (largest l2 off-diagonal row norm / diagonal spread)."""
+    A = _f64(A)
+    g = ctypes.c_double()
+    _load().oracle_guard(A.shape[0], _p(A), ctypes.byref(g))
+    return g.value
+
+
+def full(A):
+    """Full diagonalization with the start-vector sign rule: (lam, V, res), V[:, k] vector k."""
+    A = _f64(A)
+    n = A.shape[0]
+    lam, V, res = np.zeros(n), np.zeros((n, n)), np.zeros(n)
+    st = _load().oracle_full(n, _p(A), _p(lam), _p(V), _p(res))
+    if st:
+        raise OracleError(st, "full")
+    return lam, V, res
+
+
+def pfsm_guarded(A, prev, nblocks: int, solve_index: int = 0, full_steps: int = 0, guard_max: float = 0.0,
+                 **kw):
+    """The method with the conventional first steps and the guard: solves with index below
+    full_steps, and solves of an A whose guard value exceeds guard_max (> 0), are full
+    diagonalizations. Returns (path, lam, V): path 0 method, 1 first-steps rule, 2 guard."""
+    if solve_index < full_steps:
+        lam, V, _ = full(A)
+        return 1, lam, V
+    if guard_max > 0.0 and guard(A) > guard_max:
+        lam, V, _ = full(A)
+        return 2, lam, V
+    r = pfsm(A, prev, nblocks, **kw)
+    return 0, r.lam, r.V

@@ -613,3 +613,65 @@ int oracle_gen_to_std_sym(int64_t n, const double *A, const double *B, double *C
     *resid = r;
     return status;
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Diagonal-dominance guard (Section II: the method needs A diagonally dominant, and the      */
+/* paper diagonalizes conventionally for the first SCF steps). The paper gives no formula;    */
+/* the reading used here: g = max_i sqrt(sum_{j != i} A_ij^2) / (max_i A_ii - min_i A_ii),    */
+/* the largest l2 coupling of a basis state relative to the spread of the diagonal (zero      */
+/* spread: g = 0 if A is diagonal, else +inf).                                                */
+/* ------------------------------------------------------------------------------------------ */
+void oracle_guard(int64_t n, const double *A, double *g)
+{
+    double cmax = 0.0, dmin = INFINITY, dmax = -INFINITY;
+    for (int64_t i = 0; i < n; i++) {
+        double s = 0.0;
+        for (int64_t j = 0; j < n; j++)
+            if (j != i) s += A[i * n + j] * A[i * n + j];
+        cmax = fmax(cmax, sqrt(s));
+        dmin = fmin(dmin, A[i * n + i]);
+        dmax = fmax(dmax, A[i * n + i]);
+    }
+    const double spread = dmax - dmin;
+    *g = (spread > 0.0) ? cmax / spread : ((cmax > 0.0) ? INFINITY : 0.0);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Full diagonalization, the conventional step the paper uses instead of the method for the   */
+/* first SCF steps: every eigenpair of A (oracle_symeig), each vector signed by the start-     */
+/* vector rule with the whole matrix as its window (home component k positive when            */
+/* |y_k| >= 0.1, else the largest component positive), then the Rayleigh quotients and        */
+/* residuals of oracle_rayleigh. Outputs as oracle_pfsm: lam[N], V N x N with V[:, k] vector  */
+/* k, res[N]. Equivalent to the method with one block covering A and no Eq. 11 iterations.    */
+/* ------------------------------------------------------------------------------------------ */
+int oracle_full(int64_t n, const double *A, double *lam, double *V, double *res)
+{
+    double *mu = (double *)malloc(sizeof(double) * (size_t)n);
+    double *Y = (double *)malloc(sizeof(double) * (size_t)(n * n));
+    double *X = (double *)malloc(sizeof(double) * (size_t)(n * n));
+    double *r = (double *)malloc(sizeof(double) * (size_t)n);
+    int st = oracle_symeig(n, A, mu, Y);
+    if (st == OR_OK) {
+        for (int64_t k = 0; k < n; k++) {
+            double flip, yh = Y[k * n + k];
+            if (fabs(yh) >= 0.1) {
+                flip = (yh < 0.0) ? -1.0 : 1.0;
+            } else {
+                int64_t arg = 0;
+                double best = -1.0;
+                for (int64_t i = 0; i < n; i++) {
+                    double av = fabs(Y[i * n + k]);
+                    if (av > best) { best = av; arg = i; }
+                }
+                flip = (Y[arg * n + k] < 0.0) ? -1.0 : 1.0;
+            }
+            for (int64_t i = 0; i < n; i++) X[k * n + i] = flip * Y[i * n + k];
+        }
+        oracle_rayleigh(n, n, A, X, lam, r);
+        if (res) memcpy(res, r, sizeof(double) * (size_t)n);
+        for (int64_t i = 0; i < n; i++)
+            for (int64_t k = 0; k < n; k++) V[i * n + k] = X[k * n + i];
+    }
+    free(mu); free(Y); free(X); free(r);
+    return st;
+}

@@ -47,6 +47,9 @@ MUTANTS = {
                            "T[i * n + j] = 0.5 * (((i == j) ? 3.0 : 0.0) + P[i * n + j]);"),
     "newton_schulz_no_rescale": ("for (int64_t i = 0; i < n * n; i++) S[i] = Q[i] * isc;",
                                  "for (int64_t i = 0; i < n * n; i++) S[i] = Q[i];"),
+    "guard_l1_not_l2": ("if (j != i) s += A[i * n + j] * A[i * n + j];", "if (j != i) s += fabs(A[i * n + j]);"),
+    "guard_counts_diagonal": ("if (j != i) s += A[i * n + j] * A[i * n + j];", "s += A[i * n + j] * A[i * n + j];"),
+    "full_home_index_swapped": ("double flip, yh = Y[k * n + k];", "double flip, yh = Y[k * n + 0];"),
 }
 
 

@@ -527,3 +527,64 @@ def test_gen_to_std_sym_identity_b_is_exact(orc):
     C, S, it, r, st = orc.gen_to_std_sym(A, np.eye(n), max_iters=5, tol=0.0)
     # B = I: c = 1, Y_0 = Q_0 = I, T = I, the iterates never move and C = A exactly
     assert np.array_equal(S, np.eye(n)) and np.array_equal(C, A) and r == 0.0
+
+
+# ---- diagonal-dominance guard and the conventional first steps --------------------------------
+
+def test_guard_closed_forms(orc):
+    assert orc.guard(np.diag([3.0, -1.0, 2.0])) == 0.0
+    for a, b, d in ((1.0, 0.25, -1.0), (0.3, -0.02, 0.5), (-2.0, 1e-6, 7.0)):
+        assert orc.guard(np.array([[a, b], [b, d]])) == pytest.approx(abs(b) / abs(a - d), rel=1e-15)
+    A = np.array([[1.0, 0.1, 0.2], [0.1, 0.0, -0.3], [0.2, -0.3, 2.0]])
+    # rows: sqrt(0.01 + 0.04), sqrt(0.01 + 0.09), sqrt(0.04 + 0.09); spread 2
+    assert orc.guard(A) == pytest.approx(np.sqrt(0.13) / 2.0, rel=1e-15)
+    assert orc.guard(np.ones((3, 3)) - np.eye(3) + 5 * np.eye(3)) == float("inf")
+
+
+def test_guard_separates_the_papers_counterexample(orc):
+    """Randomly mixed eigenvectors (the paper's failure example) against the workloads."""
+    n = 96
+    lam = np.linspace(-1.0, 1.5, n)
+    Q, _ = np.linalg.qr(wl.gaussian((n, n), seed=31))
+    mixed = (Q * lam) @ Q.T
+    assert orc.guard(mixed) > 0.1
+    assert orc.guard(wl.small_gapped(0).A) < 0.01
+    assert orc.guard(wl.diamond_like(0).A) < 0.01
+
+
+def test_full_diagonalization_matches_lapack_and_sign_rule(orc):
+    for n, seed in ((1, 1), (9, 2), (64, 3)):
+        A = wl.random_nearly_diagonal(n, seed=seed, sigma=0.05, decay=None).A
+        lam, V, res = orc.full(A)
+        w, U = np.linalg.eigh(A)
+        assert np.max(np.abs(lam - w)) <= 1e-13 * max(1.0, np.max(np.abs(w)))
+        d = np.sign(np.sum(U * V, axis=0))
+        assert np.max(np.abs(V - U * d)) <= 1e-12
+        assert np.max(res) <= 1e-12
+        for k in range(n):
+            v = V[:, k]
+            if abs(v[k]) >= 0.1:
+                assert v[k] > 0
+            else:
+                assert v[np.argmax(np.abs(v))] > 0
+
+
+def test_full_equals_one_block_without_iterations(orc):
+    n = 40
+    p = wl.random_nearly_diagonal(n, seed=4, sigma=0.01)
+    lam, V, _ = orc.full(p.A)
+    r = orc.pfsm(p.A, p.prev, 1, halo=n, fs_iters=0)
+    assert np.max(np.abs(lam - r.lam)) <= 1e-13
+    assert np.max(np.abs(V - r.V)) <= 1e-12
+
+
+def test_guarded_paths(orc):
+    p = wl.small_gapped(0)
+    assert orc.pfsm_guarded(p.A, p.prev, p.nblocks, solve_index=0, full_steps=2)[0] == 1
+    assert orc.pfsm_guarded(p.A, p.prev, p.nblocks, solve_index=2, full_steps=2)[0] == 0
+    n = 64
+    Q, _ = np.linalg.qr(wl.gaussian((n, n), seed=32))
+    lam = np.linspace(-1.0, 1.0, n)
+    mixed = (Q * lam) @ Q.T
+    path, l2, V2 = orc.pfsm_guarded(mixed, lam, 4, guard_max=0.05)
+    assert path == 2 and np.max(np.abs(l2 - lam)) <= 1e-13
