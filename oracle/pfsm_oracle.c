@@ -655,7 +655,7 @@ int oracle_full(int64_t n, const double *A, double *lam, double *V, double *res)
         for (int64_t k = 0; k < n; k++) {
             double flip, yh = Y[k * n + k];
             if (fabs(yh) >= 0.1) {
-                flip = (yh < 0.0) ? -1.0 : 1.0;
+                flip = (yh >= 0.0) ? 1.0 : -1.0;
             } else {
                 int64_t arg = 0;
                 double best = -1.0;

@@ -50,6 +50,7 @@ MUTANTS = {
     "guard_l1_not_l2": ("if (j != i) s += A[i * n + j] * A[i * n + j];", "if (j != i) s += fabs(A[i * n + j]);"),
     "guard_counts_diagonal": ("if (j != i) s += A[i * n + j] * A[i * n + j];", "s += A[i * n + j] * A[i * n + j];"),
     "full_home_index_swapped": ("double flip, yh = Y[k * n + k];", "double flip, yh = Y[k * n + 0];"),
+    "full_sign_rule_dropped": ("flip = (yh >= 0.0) ? 1.0 : -1.0;", "flip = 1.0;"),
 }
 
 
