@@ -89,6 +89,16 @@ typedef struct {
     int32_t recompute_v;   /* backward recomputes (lambda, V) from the last A instead of
                               using the kept copy (default 0) */
     const int32_t *slice_sizes; /* HOST array of nblocks sizes summing to N, or NULL */
+    double guard_max;      /* diagonal-dominance guard (Section II: the method needs A
+                              diagonally dominant): a solve whose A has
+                              g = max_i ||A_{i,:} without A_ii||_2 / (max_i A_ii - min_i A_ii)
+                              above guard_max is a full diagonalization instead; <= 0 disables
+                              (default 0). Measuring g synchronises the solve's stream. */
+    int32_t full_steps;    /* the first full_steps solves on the handle are full
+                              diagonalizations (the paper's conventional first SCF steps;
+                              default 0). A full diagonalization (cuSOLVER syevd) gives the same
+                              outputs as the method: vectors signed by the start-vector rule,
+                              Rayleigh quotients, residuals, V; pfsm_backward works after it. */
 } pfsm_params_t;
 
 /* Fills *p with the defaults listed above. */
@@ -250,6 +260,9 @@ typedef struct {
                              11 Cholesky; the triangular solve is phase 3 minus 10 and 11 */
     int32_t gemm_tile_n;  /* output-tile width (64, 96 or 128 columns) of the handle's split
                              products, measured at pfsm_init; 0 for PFSM_FP64 handles */
+    int32_t path;         /* last pfsm_solve: 0 the method, 1 full diagonalization by the
+                             first-steps rule, 2 full diagonalization by the guard */
+    double guard_value;   /* its guard value g (0 when not measured) */
 } pfsm_profile_t;
 
 /* Enables (enable != 0) or disables CUDA-event phase timing on h. Timing adds one event record

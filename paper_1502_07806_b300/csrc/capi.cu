@@ -78,6 +78,8 @@ void pfsm_default_params(pfsm_params_t *p)
     p->precision = PFSM_FP64;
     p->recompute_v = 0;
     p->slice_sizes = nullptr;
+    p->guard_max = 0.0;
+    p->full_steps = 0;
 }
 
 const char *pfsm_last_error(void) { return g_last_error.c_str(); }
@@ -93,6 +95,8 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
     pfsm_default_params(&prm);
     if (p) prm = *p;
     if (prm.fs_iters < 0 || prm.fs_iters > 1000) return fail(PFSM_ERR_INVALID_ARG, "pfsm_init: fs_iters=%d", prm.fs_iters);
+    if (prm.full_steps < 0 || prm.guard_max != prm.guard_max)
+        return fail(PFSM_ERR_INVALID_ARG, "pfsm_init: full_steps must be >= 0 and guard_max a number");
     if (!(prm.alpha_theta > 0.0) || !(prm.cluster_tol >= 0.0) || !(prm.degen_tol >= 0.0))
         return fail(PFSM_ERR_INVALID_ARG, "pfsm_init: alpha_theta must be > 0, tolerances >= 0");
     if (prm.precision != PFSM_FP64 && prm.precision != PFSM_TF32_SPLIT && prm.precision != PFSM_BF16_SPLIT)
@@ -242,6 +246,16 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
         return fail(PFSM_ERR_CUDA, "pfsm_init: %s", cudaGetErrorString(e));
     }
     h->prm.slice_sizes = nullptr;   // the host array is not kept
+    if (prm.full_steps > 0 || prm.guard_max > 0.0) {
+        const cudaError_t fe = fallback_init(h);
+        if (fe != cudaSuccess) {
+            fallback_free(h);
+            free_ws(h);
+            delete h;
+            cudaGetLastError();
+            return fail(PFSM_ERR_CUDA, "pfsm_init: full-diagonalization setup: %s", cudaGetErrorString(fe));
+        }
+    }
     if (prm.precision != PFSM_FP64) {
         // tile width of the Eq. 11 products: measured on this shape (cached per shape class)
         SliceBuf sE{w.slE, N, padded_ld(N), slices_for(prm.precision), slice_kind(prm.precision)};
@@ -302,6 +316,34 @@ static int solve_impl(pfsm_handle_s *h, const double *A, const double *prev, dou
     PFSM_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int32_t), st));
     PFSM_CUDA(mark(0));
     PFSM_CUDA(launch_validate_gersh(A, prev, N, w.gersh, w.status, st));
+    // the conventional path: first-steps rule, then the guard (Section II)
+    int path = 0;
+    double g = 0.0;
+    if (h->nsolves < h->prm.full_steps) {
+        path = 1;
+    } else if (h->prm.guard_max > 0.0) {
+        PFSM_CUDA(measure_guard(h, A, st, g));
+        if (!(g <= h->prm.guard_max)) path = 2;
+    }
+    h->nsolves++;
+    h->last_path = path;
+    h->last_guard = g;
+    if (path != 0) {
+        PFSM_CUDA(mark(1));
+        PFSM_CUDA(run_full_diag(h, A, st));
+        for (int i = 2; i <= 4; i++) PFSM_CUDA(mark(i));
+        if (h->timing)
+            for (int i = 0; i < 3; i++) PFSM_CUDA(cudaEventRecord(h->sub_ev[i], st));
+        if (h->timing)
+            for (int i = 0; i < 2; i++) PFSM_CUDA(cudaEventRecord(h->gs_ev[i], st));
+        PFSM_CUDA(launch_rayleigh_f64(h, A, eigvals_out, V_out, st));
+        PFSM_CUDA(mark(5));
+        h->solved = true;
+        h->last_A = A;
+        h->last_prev = prev;
+        h->last_stream = st;
+        return PFSM_OK;
+    }
     PFSM_CUDA(launch_plan(prev, N, h->nb, h->halo, h->prm.cluster_tol, w.slices, w.plan,
                           w.tile_krange, w.gersh, w.status, st));
     PFSM_CUDA(mark(1));
@@ -533,6 +575,8 @@ int pfsm_get_profile(pfsm_handle_t h, pfsm_profile_t *out)
     std::memset(out, 0, sizeof(*out));
     out->launches = h->last_launches;
     out->gemm_tile_n = h->prm.precision != PFSM_FP64 ? h->tc_bn : 0;
+    out->path = h->last_path;
+    out->guard_value = h->last_guard;
     if (!h->timing || !h->solved) return PFSM_OK;
     PFSM_CUDA(cudaStreamSynchronize(h->last_stream));
     auto span = [&](int a, int b, float *dst) -> cudaError_t { return cudaEventElapsedTime(dst, h->ev[a], h->ev[b]); };
@@ -561,6 +605,7 @@ int pfsm_destroy(pfsm_handle_t h)
         if (h->sub_ev[i]) cudaEventDestroy(h->sub_ev[i]);
     for (int i = 0; i < 2; i++)
         if (h->gs_ev[i]) cudaEventDestroy(h->gs_ev[i]);
+    fallback_free(h);
     free_ws(h);
     delete h;
     return PFSM_OK;

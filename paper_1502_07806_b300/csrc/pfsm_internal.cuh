@@ -74,6 +74,15 @@ struct pfsm_handle_s {
     int32_t Mmax = 0;    // largest window
     int32_t cl = 8;      // CTAs per submatrix cluster
     int32_t tc_bn = 128; // tile width of the split products (tuned at init for the handle's N)
+    // conventional path (k_fallback.cu): first-steps rule and diagonal-dominance guard
+    int64_t nsolves = 0;           // solves done on the handle
+    int32_t last_path = 0;         // 0 the method, 1 first-steps rule, 2 guard
+    double last_guard = 0.0;       // guard value of the last solve (0 when not measured)
+    void *cusolver = nullptr;      // cusolverDnHandle_t, created when the path can be taken
+    double *syevd_work = nullptr;
+    int syevd_lwork = 0;
+    int *syevd_info = nullptr;
+    unsigned long long *guard_buf = nullptr;
     bool rows_in_smem = true;
     bool tri_blocked = false;      // mixed forms: blocked reduction (k_tridiag_panel)
     int32_t tri_rpw = 8;           // its rows-per-warp register capacity (8 or 24)
@@ -188,6 +197,11 @@ struct OzParams {
 };
 cudaError_t configure_oz_kernels();
 int sm_count();                     // multiprocessors of the current device (cached)
+// ---- conventional path: guard and full diagonalization (k_fallback.cu) ----
+cudaError_t fallback_init(pfsm_handle_s *h);
+void fallback_free(pfsm_handle_s *h);
+cudaError_t measure_guard(pfsm_handle_s *h, const double *A, cudaStream_t st, double &g);
+cudaError_t run_full_diag(pfsm_handle_s *h, const double *A, cudaStream_t st);
 // ---- generalized -> standard conversion (k_gen2std.cu) ----
 struct Gen2StdResult {
     int iters = 0;                  // updates done
