@@ -28,6 +28,9 @@ Parity status per function (what pins it; see ``tests/test_oracle_pins.py``):
   full         pinned: LAPACK (numpy) eigenvalues and eigenvectors up to the sign rule, the sign
                rule itself, equality with the method for one block and no Eq. 11 iterations
   pfsm_guarded pinned through guard, full and pfsm
+  scf_step     pinned: exact eigenbasis in gives back the basis (A diagonal), the chained
+               eigenvalues and projectors against LAPACK's eigendecomposition of each H_j,
+               orthonormality of the carried basis
 """
 from __future__ import annotations
 
@@ -281,3 +284,17 @@ def pfsm_guarded(A, prev, nblocks: int, solve_index: int = 0, full_steps: int = 
         return 2, lam, V
     r = pfsm(A, prev, nblocks, **kw)
     return 0, r.lam, r.V
+
+
+def scf_step(H, Vb, lam_prev, nblocks: int, solve_index: int = 1, full_steps: int = 0, guard_max: float = 0.0,
+             **kw):
+    """One step of the SCF loop the method assumes (the input "similar to the previous
+    iteration"): A = sym(Vb^T H Vb) is the new Hamiltonian in the previous eigenbasis Vb (columns),
+    solved with the previous eigenvalues as prev; the new basis is Vb V. Returns
+    (path, lam, Vb_new). The products are library matrix products (numpy), the solve the oracle's."""
+    H, Vb = _f64(H), _f64(Vb)
+    A = Vb.T @ H @ Vb
+    A = 0.5 * (A + A.T)
+    path, lam, V = pfsm_guarded(A, lam_prev, nblocks, solve_index=solve_index, full_steps=full_steps,
+                                guard_max=guard_max, **kw)
+    return path, lam, Vb @ V

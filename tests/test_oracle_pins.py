@@ -588,3 +588,38 @@ def test_guarded_paths(orc):
     mixed = (Q * lam) @ Q.T
     path, l2, V2 = orc.pfsm_guarded(mixed, lam, 4, guard_max=0.05)
     assert path == 2 and np.max(np.abs(l2 - lam)) <= 1e-13
+
+
+# ---- the chained SCF loop -------------------------------------------------------------------
+
+def test_scf_step_keeps_an_exact_eigenbasis(orc):
+    n = 48
+    H = wl.scf_sequence(n, 1, seed=51)[0]
+    w, U = np.linalg.eigh(H)
+    path, lam, Vb = orc.scf_step(H, U, w, 4)
+    assert path == 0
+    assert np.max(np.abs(lam - w)) <= 1e-13
+    assert np.max(np.abs(np.abs(np.sum(Vb * U, axis=0)) - 1.0)) <= 1e-12
+
+
+def test_scf_chain_tracks_each_hamiltonian(orc):
+    """Step 0 conventionally (H_0 is dense), then the method in the previous eigenbasis. Every
+    step: the basis stays orthonormal, and each eigenvalue lies within Kahan's bound
+    ||H V - V Lambda||_2 of LAPACK's (sorted pairing, V orthonormal); the method's own
+    approximation error does not grow along the chain."""
+    n, steps = 96, 5
+    Hs = wl.scf_sequence(n, steps, seed=52)
+    Vb, lam = np.eye(n), np.zeros(n)
+    errs = []
+    for j, H in enumerate(Hs):
+        path, lam, Vb = orc.scf_step(H, Vb, lam, 4, solve_index=j, full_steps=1)
+        assert path == (1 if j == 0 else 0)
+        w = np.linalg.eigvalsh(H)
+        assert np.max(np.abs(Vb.T @ Vb - np.eye(n))) <= 1e-12
+        R = H @ Vb - Vb * lam
+        bound = np.linalg.norm(R, 2) + 1e-14
+        err = np.max(np.abs(lam - w))
+        assert err <= bound
+        errs.append(err)
+    assert errs[0] <= 1e-13                      # the conventional step is exact
+    assert max(errs[2:]) <= 2.0 * errs[1]        # no growth along the chain

@@ -218,6 +218,25 @@ def generalized_pair(n: int, seed: int, sigma_a: float = 1e-3, sigma_b: float = 
     return A, B
 
 
+def scf_sequence(n: int, steps: int, seed: int, sigma0: float = 3e-3, decay_per_step: float = 0.3,
+                 lo: float = -1.0, hi: float = 1.5):
+    """A chained SCF-like sequence of Hamiltonians in a fixed (non-eigen) basis: H_j = Q diag(lam) Q^T
+    + sigma_j S_j with Q a seeded random orthogonal matrix (so H_0 is dense, not diagonally dominant),
+    lam sorted U[lo, hi], S_j symmetric N(0,1) / sqrt(n) and sigma_j = sigma0 decay^j (the SCF
+    changes shrinking). Returns the list [H_0, ..., H_{steps-1}]."""
+    Qg = _Stream(seed).normal(n * n).reshape(n, n)
+    Q, R = np.linalg.qr(Qg)
+    Q = Q * np.sign(np.diag(R))
+    lam = np.sort(lo + (hi - lo) * _Stream(seed + 1).uniform(n))
+    H0 = (Q * lam) @ Q.T
+    out = []
+    for j in range(steps):
+        S = symmetric_direction(n, seed + 100 + j) * np.sqrt(n)   # unit-Frobenius direction, rescaled
+        out.append(0.5 * ((H0 + sigma0 * decay_per_step ** j * S / np.sqrt(n)) +
+                          (H0 + sigma0 * decay_per_step ** j * S / np.sqrt(n)).T))
+    return out
+
+
 def symmetric_direction(n: int, seed: int) -> np.ndarray:
     """Random symmetric perturbation direction with unit Frobenius norm."""
     iu, ju = np.triu_indices(n)
