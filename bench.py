@@ -446,6 +446,37 @@ def main():
 
     conv = conversion()
 
+    # ---- one step of the chained SCF loop (rotation into the previous eigenbasis, solve, update) ---
+    def scf_chain(steps: int = 4):
+        import workloads as wl
+        Hs = wl.scf_sequence(p.n, steps, seed=0x5CF)
+        hs = pf.Handle(p.n, p.nblocks, halo=p.halo, fs_iters=p.fs_iters, precision=precs[args.precision],
+                       full_steps=1)
+        Vb = torch.eye(p.n, dtype=torch.float64, device="cuda")
+        lam_c = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+        ms, paths = [], []
+        for H in Hs:
+            dH = torch.from_numpy(H).cuda()
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            lam_c = hs.scf_step(dH, Vb, lam_c.clone())
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            paths.append(hs.profile()["path"])
+        w = np.linalg.eigvalsh(Hs[-1])
+        err = float(np.max(np.abs(lam_c.cpu().numpy() - w)) / np.max(np.abs(w)))
+        hs.close()
+        return {"workload": f"H_j = Q diag(lam) Q^T + 3e-3 * 0.3^j S_j, N = {p.n}, {steps} steps, "
+                            f"{p.nblocks} slices; step 0 conventional (full_steps = 1)",
+                "paths": paths, "ms_per_step": ms, "ms_method_steps_mean": float(np.mean(ms[1:])),
+                "last_step_max_abs_dlambda_over_norm_vs_lapack": err,
+                "timing": "CUDA events around pfsm_scf_step (two rotation products, the solve, the basis "
+                          "product), L2 flushed"}
+
+    scf = scf_chain()
+
     cands = [tridiag_roofline(), gemm_roofline()]
     cands.sort(key=lambda r: -r["total_ms"])
     roofline, other = cands[0], cands[1:]
@@ -463,7 +494,7 @@ def main():
            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h},
            "gpu_launches": main_run["launches"], "clocks": main_run["clocks"],
-           "gen_to_std": conv}
+           "gen_to_std": conv, "scf_chain": scf}
 
     if not args.no_oracle and world == 1:
         import oracle

@@ -135,6 +135,18 @@ int pfsm_backward(pfsm_handle_t h, const double *dLambda, const double *dV, doub
  * The status word is cleared at the start of every solve. */
 int pfsm_get_status(pfsm_handle_t h, int32_t *device_status);
 
+/* One step of the SCF loop the method assumes (its input "similar to the previous iteration",
+ * Sec. I): the Hamiltonian H (N x N symmetric, any fixed basis) is rotated into the previous
+ * eigenbasis, A = sym(Vb^T H Vb) with Vb (N x N row-major, columns = basis vectors), A is solved
+ * on h exactly as pfsm_solve does (its precision, first-steps rule and guard apply; lam_prev is
+ * prev_eigvals, ascending), and then Vb <- Vb V (in place) and lam_out <- the eigenvalues, so
+ * Vb's columns are the eigenvector estimates of H in its own basis. The rotation and update are
+ * FP64-accurate digit products; temporaries come from cudaMallocAsync on `stream`. Start a loop
+ * with Vb = I, lam_prev = 0 and full_steps >= 1 (H_0 is generally not diagonally dominant).
+ * Diagnostics afterwards describe the solve of A; pfsm_backward needs recompute_v = 0 after it. */
+int pfsm_scf_step(pfsm_handle_t h, const double *H, double *Vb, const double *lam_prev, double *lam_out,
+                  void *stream);
+
 /* Diagnostics of the last solve, copied on `stream` into caller device buffers:
  *   which = 0: residual norms r_k = ||A v_k - lambda_k v_k||_2          (N doubles)
  *   which = 1: vectors after the Eq. 11 iterations, before Gram-Schmidt (N x N, V layout)

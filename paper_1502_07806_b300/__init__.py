@@ -25,7 +25,7 @@ EXPORTED = ("pfsm_default_params", "pfsm_init", "pfsm_solve", "pfsm_backward", "
             "pfsm_get_diagnostic", "pfsm_set_timing", "pfsm_get_profile", "pfsm_last_error",
             "pfsm_destroy", "pfsm_fs_iterate_noalloc", "pfsm_split_gemm", "pfsm_split_gemm_ex", "pfsm_batch_init",
             "pfsm_solve_batched", "pfsm_batch_get_status", "pfsm_batch_destroy", "pfsm_gen_to_std",
-            "pfsm_gen_to_std_sym")
+            "pfsm_gen_to_std_sym", "pfsm_scf_step")
 PHASES = ("plan", "submatrix", "fs_iterations", "gram_schmidt", "rayleigh", "backward")
 SUB_PHASES = ("tridiag", "bisect", "inverse_iter", "backtransform", "overlap", "cholesky")
 
@@ -75,6 +75,7 @@ def load_library():
     lib.pfsm_split_gemm_ex.argtypes = [i64, i64, i64, P, P, P, i32, i32, P]
     lib.pfsm_gen_to_std.argtypes = [i64, P, P, P, i32, ctypes.c_double, P, P, P]
     lib.pfsm_gen_to_std_sym.argtypes = [i64, P, P, P, P, i32, ctypes.c_double, P, P, P]
+    lib.pfsm_scf_step.argtypes = [P, P, P, P, P, P]
     lib.pfsm_batch_init.argtypes = [i32, P, P, ctypes.POINTER(Params), ctypes.POINTER(P)]
     lib.pfsm_solve_batched.argtypes = [P, P, P, P, P, P]
     lib.pfsm_batch_get_status.argtypes = [P, P]
@@ -162,6 +163,16 @@ class Handle:
         _check(load_library().pfsm_backward(self._h, _ptr(dlam), _ptr(dV), _ptr(dA_out), _stream()),
                "pfsm_backward")
         return dA_out
+
+    def scf_step(self, H: torch.Tensor, Vb: torch.Tensor, lam_prev: torch.Tensor,
+                 lam_out: torch.Tensor | None = None) -> torch.Tensor:
+        """One chained SCF step: solve sym(Vb^T H Vb) with lam_prev, Vb <- Vb V in place.
+        Returns the eigenvalues."""
+        if lam_out is None:
+            lam_out = torch.empty(self.n, dtype=torch.float64, device=H.device)
+        _check(load_library().pfsm_scf_step(self._h, _ptr(H), _ptr(Vb), _ptr(lam_prev), _ptr(lam_out),
+                                            _stream()), "pfsm_scf_step")
+        return lam_out
 
     def status(self) -> int:
         s = ctypes.c_int32(-1)

@@ -392,12 +392,63 @@ int pfsm_solve(pfsm_handle_t h, const double *A, const double *prev_eigvals, dou
     return rc;
 }
 
+int pfsm_scf_step(pfsm_handle_t h, const double *H, double *Vb, const double *lam_prev, double *lam_out,
+                  void *stream)
+{
+    if (!h) return fail(PFSM_ERR_INVALID_ARG, "pfsm_scf_step: null handle");
+    if (!H || !Vb || !lam_prev || !lam_out) return fail(PFSM_ERR_INVALID_ARG, "pfsm_scf_step: null buffer");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t N = h->N;
+    const size_t n2b = (size_t)N * N * sizeof(double);
+    PFSM_CUDA(configure_oz_kernels());
+    g_launches = 0;
+    double *VbT = nullptr, *T = nullptr, *A = nullptr, *Vp = nullptr;
+    Digits d1, d2;
+    cudaError_t e = cudaSuccess;
+    auto step = [&](cudaError_t x) { if (e == cudaSuccess) e = x; return e == cudaSuccess; };
+    for (double **p : {&VbT, &T, &A, &Vp}) step(cudaMallocAsync((void **)p, n2b, st));
+    step(make_digits(d1, N, st));
+    step(make_digits(d2, N, st));
+    int rc = PFSM_OK;
+    if (e == cudaSuccess) {
+        // A = sym(Vb^T H Vb): T = Vb^T H (H symmetric: its rows are its columns), A = T Vb
+        step(launch_transpose(Vb, VbT, N, st));
+        step(dense_product(VbT, H, T, N, d1, d2, h->ws.status, st));
+        step(dense_product(T, VbT, A, N, d1, d2, h->ws.status, st));
+        step(launch_symmetrize(A, T, N, st));
+    }
+    if (e == cudaSuccess) {
+        const int launches_rot = (int)g_launches;
+        rc = solve_impl(h, T, lam_prev, lam_out, Vp, st);
+        if (rc == PFSM_OK) {
+            // Vb <- Vb V: the solve leaves V's columns as the rows of its vector matrix X
+            step(dense_product(Vb, h->ws.X, A, N, d1, d2, h->ws.status, st));
+            step(cudaMemcpyAsync(Vb, A, n2b, cudaMemcpyDeviceToDevice, st));
+        }
+        (void)launches_rot;
+    }
+    free_digits(d1, st);
+    free_digits(d2, st);
+    for (double *p : {VbT, T, A, Vp})
+        if (p) cudaFreeAsync(p, st);
+    h->last_launches = (int32_t)g_launches;
+    h->last_was_backward = false;
+    if (e != cudaSuccess) return cuda_fail(e, "pfsm_scf_step");
+    // the solve kept pointers to its inputs for pfsm_backward with recompute_v; they were temporaries
+    h->last_A = nullptr;
+    h->last_prev = nullptr;
+    return rc;
+}
+
 int pfsm_backward(pfsm_handle_t h, const double *dLambda, const double *dV, double *dA_out,
                   void *stream)
 {
     if (!h) return fail(PFSM_ERR_INVALID_ARG, "pfsm_backward: null handle");
     if (!dA_out) return fail(PFSM_ERR_INVALID_ARG, "pfsm_backward: null dA_out");
     if (!h->solved) return fail(PFSM_ERR_NO_SOLVE, "pfsm_backward: no solve on this handle yet");
+    if (h->prm.recompute_v && !h->last_A)
+        return fail(PFSM_ERR_INVALID_ARG, "pfsm_backward: recompute_v needs the last solve's input (none after "
+                                          "pfsm_scf_step)");
     cudaStream_t st = (cudaStream_t)stream;
     g_launches = 0;
     if (h->prm.recompute_v) {

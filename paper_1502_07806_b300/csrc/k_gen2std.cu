@@ -101,12 +101,19 @@ __global__ void k_ns_t(const double *__restrict__ P, double *__restrict__ T, int
     if ((threadIdx.x & 31) == 0) atomicMax(rmax, (unsigned long long)__double_as_longlong(m));
 }
 
-// digit operands of an N x N product, allocated on the stream
-struct Digits {
-    void *sl = nullptr;
-    int32_t *ex = nullptr;
-    SliceBuf buf{};
-};
+unsigned grid_for(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8); }
+
+cudaError_t read_max(unsigned long long *dev, double &out, cudaStream_t st)
+{
+    unsigned long long h = 0;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(&h, dev, sizeof(h), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    std::memcpy(&out, &h, sizeof(out));
+    return cudaSuccess;
+}
+
+}  // namespace
 
 cudaError_t make_digits(Digits &d, int64_t N, cudaStream_t st)
 {
@@ -127,7 +134,6 @@ void free_digits(Digits &d, cudaStream_t st)
     d = Digits{};
 }
 
-// C (=, or -= when sub) X Y^T with X's digits in dx (already split) and Y's in dy
 cudaError_t digit_product(const Digits &dx, const Digits &dy, double *C, int64_t N, bool sub, int32_t *status,
                           cudaStream_t st)
 {
@@ -136,19 +142,33 @@ cudaError_t digit_product(const Digits &dx, const Digits &dy, double *C, int64_t
     return launch_gemm_oz(dx.buf, dx.ex, dy.buf, dy.ex, o, st);
 }
 
-unsigned grid_for(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8); }
-
-cudaError_t read_max(unsigned long long *dev, double &out, cudaStream_t st)
+cudaError_t dense_product(const double *X, const double *Yrows, double *C, int64_t N, Digits &dx, Digits &dy,
+                          int32_t *status, cudaStream_t st)
 {
-    unsigned long long h = 0;
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(&h, dev, sizeof(h), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
-    std::memcpy(&out, &h, sizeof(out));
-    return cudaSuccess;
+    if ((e = launch_oz_split(X, N, N, N, dx.buf, dx.ex, st)) != cudaSuccess) return e;
+    if ((e = launch_oz_split(Yrows, N, N, N, dy.buf, dy.ex, st)) != cudaSuccess) return e;
+    return digit_product(dx, dy, C, N, false, status, st);
 }
 
+namespace {
+__global__ void k_symmetrize(const double *__restrict__ T, double *__restrict__ S, int64_t N)
+{
+    const int64_t n2 = N * N;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / N, c = i % N;
+        S[i] = 0.5 * (T[i] + T[c * N + r]);
+    }
+}
 }  // namespace
+
+cudaError_t launch_symmetrize(const double *T, double *S, int64_t N, cudaStream_t st)
+{
+    const unsigned grid = (unsigned)std::min<int64_t>((N * N + 255) / 256, (int64_t)sm_count() * 8);
+    k_symmetrize<<<grid, 256, 0, st>>>(T, S, N);
+    g_launches++;
+    return cudaGetLastError();
+}
 
 cudaError_t run_gen_to_std(int64_t N, const double *A, const double *B, double *Z, int max_iters, double tol,
                            cudaStream_t st, Gen2StdResult &res)

@@ -202,6 +202,20 @@ cudaError_t fallback_init(pfsm_handle_s *h);
 void fallback_free(pfsm_handle_s *h);
 cudaError_t measure_guard(pfsm_handle_s *h, const double *A, cudaStream_t st, double &g);
 cudaError_t run_full_diag(pfsm_handle_s *h, const double *A, cudaStream_t st);
+// ---- dense FP64-accurate N x N products with scratch digits (k_gen2std.cu) ----
+struct Digits {                     // digit operand of an N x N product, allocated on a stream
+    void *sl = nullptr;
+    int32_t *ex = nullptr;
+    SliceBuf buf{};
+};
+cudaError_t make_digits(Digits &d, int64_t N, cudaStream_t st);
+void free_digits(Digits &d, cudaStream_t st);
+cudaError_t digit_product(const Digits &dx, const Digits &dy, double *C, int64_t N, bool sub, int32_t *status,
+                          cudaStream_t st);
+// C = X Yrows^T (split both, then the digit product)
+cudaError_t dense_product(const double *X, const double *Yrows, double *C, int64_t N, Digits &dx, Digits &dy,
+                          int32_t *status, cudaStream_t st);
+cudaError_t launch_symmetrize(const double *T, double *S, int64_t N, cudaStream_t st);   // S = (T + T^T) / 2
 // ---- generalized -> standard conversion (k_gen2std.cu) ----
 struct Gen2StdResult {
     int iters = 0;                  // updates done
