@@ -28,6 +28,9 @@ Parity status per function (what pins it; see ``tests/test_oracle_pins.py``):
   full         pinned: LAPACK (numpy) eigenvalues and eigenvectors up to the sign rule, the sign
                rule itself, equality with the method for one block and no Eq. 11 iterations
   pfsm_guarded pinned through guard, full and pfsm
+  fs_adaptive  pinned: an exact eigenbasis stops at once, zero steps give one exact Rayleigh
+               quotient, a perturbed eigenvector converges to LAPACK's eigenvalue in a few steps,
+               the method with it against LAPACK
   scf_step     pinned: exact eigenbasis in gives back the basis (A diagonal), the chained
                eigenvalues and projectors against LAPACK's eigendecomposition of each H_j,
                orthonormality of the carried basis
@@ -77,6 +80,7 @@ def _load():
         lib.oracle_symeig.argtypes = [i64, P, P, P]
         lib.oracle_fs_iterate.argtypes = [i64, i64, P, P, P, P, i32]
         lib.oracle_fs_iterate.restype = None
+        lib.oracle_fs_iterate_adaptive.argtypes = [i64, i64, P, P, P, P, i32, f64, f64, f64, f64, P, P]
         lib.oracle_mgs.argtypes = [i64, i64, P, P]
         lib.oracle_rayleigh.argtypes = [i64, i64, P, P, P, P]
         lib.oracle_rayleigh.restype = None
@@ -109,7 +113,7 @@ def _p(a: np.ndarray | None):
 class _Params(ctypes.Structure):
     _fields_ = [("halo", ctypes.c_int32), ("fs_iters", ctypes.c_int32),
                 ("alpha_theta", ctypes.c_double), ("cluster_tol", ctypes.c_double),
-                ("slice_sizes", ctypes.c_void_p)]
+                ("slice_sizes", ctypes.c_void_p), ("fs_adaptive", ctypes.c_int32), ("fs_tol", ctypes.c_double)]
 
 
 def set_threads(n: int) -> None:
@@ -197,12 +201,14 @@ class Result:
 
 
 def pfsm(A, prev, nblocks: int, halo: int = -1, fs_iters: int = 3, alpha_theta: float = 1.0,
-         cluster_tol: float = 1e-5, slice_sizes=None, keep_xfs: bool = True) -> Result:
-    """The whole method on one matrix (Section II)."""
+         cluster_tol: float = 1e-5, slice_sizes=None, keep_xfs: bool = True, fs_adaptive: bool = False,
+         fs_tol: float = 0.0) -> Result:
+    """The whole method on one matrix (Section II); fs_adaptive selects the Rayleigh-quotient
+    variant of Eq. 11 with residual stopping (fs_iters is then the cap)."""
     A, prev = _f64(A), _f64(prev)
     n = A.shape[0]
     ss = None if slice_sizes is None else np.ascontiguousarray(slice_sizes, dtype=np.int32)
-    prm = _Params(halo, fs_iters, alpha_theta, cluster_tol, _p(ss))
+    prm = _Params(halo, fs_iters, alpha_theta, cluster_tol, _p(ss), int(bool(fs_adaptive)), fs_tol)
     r = Result(n, nblocks)
     xfs = r.xfs if keep_xfs else None
     st = _load().oracle_pfsm(n, nblocks, ctypes.byref(prm), _p(A), _p(prev), _p(r.lam), _p(r.V),
@@ -298,3 +304,16 @@ def scf_step(H, Vb, lam_prev, nblocks: int, solve_index: int = 1, full_steps: in
     path, lam, V = pfsm_guarded(A, lam_prev, nblocks, solve_index=solve_index, full_steps=full_steps,
                                 guard_max=guard_max, **kw)
     return path, lam, Vb @ V
+
+
+def fs_iterate_adaptive(A, X, eps, alpha, max_iters: int, tol_abs: float, theta: float = 1.0):
+    """Rayleigh-quotient variant of Eq. 11 on the rows of X (copies). Returns (X, eps, alpha, iters,
+    resid, status)."""
+    A = _f64(A)
+    X, eps, alpha = _f64(X).copy(), _f64(eps).copy(), _f64(alpha).copy()
+    n = A.shape[0]
+    lo, hi = gershgorin(A)
+    it, r = ctypes.c_int32(), ctypes.c_double()
+    st = _load().oracle_fs_iterate_adaptive(n, X.shape[0], _p(A), _p(X), _p(eps), _p(alpha), max_iters, tol_abs,
+                                            theta, lo, hi, ctypes.byref(it), ctypes.byref(r))
+    return X, eps, alpha, it.value, r.value, st

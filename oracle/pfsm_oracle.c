@@ -287,6 +287,77 @@ void oracle_fs_iterate(int64_t n, int64_t cnt, const double *A, double *X, const
     }
 }
 
+/* ------------------------------------------------------------------------------------------ */
+/* Adaptive variant of Eq. 11 (not in the paper, which fixes the shift and the count): each    */
+/* iteration first moves every shift to the Rayleigh quotient of its vector and measures the   */
+/* residual, then takes the Eq. 11 step with the new shift:                                     */
+/*   y = (A - eps I) x;  delta = x.y / x.x;  eps += delta;  y -= delta x   (y = (A - eps I) x); */
+/*   r = ||y|| / ||x||;  stop when max_k r_k <= tol_abs (before the step) or after max_iters   */
+/*   steps;  alpha = min(theta / d^2, 1 - 2^-20), d = max(ghi - eps, eps - glo);               */
+/*   x -= alpha (A - eps I) y.                                                                  */
+/* X: cnt x n rows; eps, alpha updated in place. *iters = steps done, *resid = the last        */
+/* max_k r_k. Returns OR_OK (tolerance met) or OR_NOT_CONVERGED (max_iters reached).          */
+/* ------------------------------------------------------------------------------------------ */
+int oracle_fs_iterate_adaptive(int64_t n, int64_t cnt, const double *A, double *X, double *eps, double *alpha,
+                               int32_t max_iters, double tol_abs, double theta, double glo, double ghi,
+                               int32_t *iters, double *resid)
+{
+    double *Y = (double *)malloc(sizeof(double) * (size_t)(cnt * n));
+    double *r = (double *)malloc(sizeof(double) * (size_t)cnt);
+    int status = OR_NOT_CONVERGED;
+    int32_t it = 0;
+    double rmax = 0.0;
+    for (;;) {
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int64_t k = 0; k < cnt; k++) {
+            const double *x = X + k * n;
+            double *y = Y + k * n;
+            for (int64_t i = 0; i < n; i++) {                /* y = (A - eps I) x */
+                double acc = 0.0;
+                for (int64_t j = 0; j < n; j++) acc += A[i * n + j] * x[j];
+                y[i] = acc - eps[k] * x[i];
+            }
+            double xy = 0.0, xx = 0.0;
+            for (int64_t i = 0; i < n; i++) { xy += x[i] * y[i]; xx += x[i] * x[i]; }
+            const double delta = xy / xx;                    /* Rayleigh quotient - eps */
+            eps[k] += delta;
+            double yy = 0.0;
+            for (int64_t i = 0; i < n; i++) { y[i] -= delta * x[i]; yy += y[i] * y[i]; }
+            r[k] = sqrt(yy / xx);
+        }
+        rmax = 0.0;
+        for (int64_t k = 0; k < cnt; k++) rmax = fmax(rmax, r[k]);
+        if (rmax <= tol_abs) { status = OR_OK; break; }
+        if (it >= max_iters) break;
+#pragma omp parallel
+        {
+            double *z = (double *)malloc(sizeof(double) * (size_t)n);
+#pragma omp for schedule(dynamic, 4)
+            for (int64_t k = 0; k < cnt; k++) {
+                double *x = X + k * n;
+                const double *y = Y + k * n;
+                double dmax = ghi - eps[k];
+                if (eps[k] - glo > dmax) dmax = eps[k] - glo;
+                const double a = theta / (dmax * dmax), cap = 1.0 - ldexp(1.0, -20);
+                alpha[k] = (a < cap) ? a : cap;
+                for (int64_t i = 0; i < n; i++) {            /* z = (A - eps I) y */
+                    double acc = 0.0;
+                    for (int64_t j = 0; j < n; j++) acc += A[i * n + j] * y[j];
+                    z[i] = acc - eps[k] * y[i];
+                }
+                for (int64_t i = 0; i < n; i++) x[i] -= alpha[k] * z[i];
+            }
+            free(z);
+        }
+        it++;
+    }
+    free(Y);
+    free(r);
+    *iters = it;
+    *resid = rmax;
+    return status;
+}
+
 /* Modified Gram-Schmidt over the rows of X (cnt x n), ascending index order (reading R8).     */
 /* The right-looking form below performs, for every vector, the same ordered sequence of       */
 /* projections as the textbook left-looking loop, so it is the same arithmetic.               */
@@ -356,10 +427,12 @@ void oracle_rayleigh(int64_t n, int64_t cnt, const double *A, const double *Q, d
 /* ------------------------------------------------------------------------------------------ */
 typedef struct {
     int32_t halo;
-    int32_t fs_iters;
+    int32_t fs_iters;            /* Eq. 11 iterations (the cap with fs_adaptive) */
     double alpha_theta;
     double cluster_tol;
     const int32_t *slice_sizes;
+    int32_t fs_adaptive;         /* 0: Eq. 11 as printed; 1: oracle_fs_iterate_adaptive */
+    double fs_tol;               /* its residual tolerance, relative to max(|glo|, |ghi|) */
 } oracle_params_t;
 
 int oracle_pfsm(int64_t n, int32_t nb, const oracle_params_t *prm, const double *A,
@@ -423,11 +496,18 @@ int oracle_pfsm(int64_t n, int32_t nb, const oracle_params_t *prm, const double 
         free(sub); free(mu); free(Y);
     }
     if (bad != OR_OK) { st = bad; goto done; }
+
+    /* Eq. 11, K times (or the adaptive variant, at most K steps) */
+    if (prm->fs_adaptive) {
+        int32_t fit;
+        double fres;
+        oracle_fs_iterate_adaptive(n, n, A, X, ep, al, prm->fs_iters, prm->fs_tol * fmax(fabs(glo), fabs(ghi)),
+                                   prm->alpha_theta, glo, ghi, &fit, &fres);
+    } else {
+        oracle_fs_iterate(n, n, A, X, ep, al, prm->fs_iters);
+    }
     if (eps_out) memcpy(eps_out, ep, sizeof(double) * (size_t)n);
     if (alpha_out) memcpy(alpha_out, al, sizeof(double) * (size_t)n);
-
-    /* Eq. 11, K times */
-    oracle_fs_iterate(n, n, A, X, ep, al, prm->fs_iters);
     if (xfs)
         for (int64_t i = 0; i < n; i++)
             for (int64_t k = 0; k < n; k++) xfs[i * n + k] = X[k * n + i];

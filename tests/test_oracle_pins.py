@@ -623,3 +623,68 @@ def test_scf_chain_tracks_each_hamiltonian(orc):
         errs.append(err)
     assert errs[0] <= 1e-13                      # the conventional step is exact
     assert max(errs[2:]) <= 2.0 * errs[1]        # no growth along the chain
+
+
+# ---- adaptive variant of Eq. 11 (Rayleigh-quotient shifts, residual stopping) -------------------
+
+def test_adaptive_stops_at_once_on_an_exact_eigenbasis(orc):
+    n = 30
+    A = wl.random_nearly_diagonal(n, seed=61, sigma=0.05).A
+    w, U = np.linalg.eigh(A)
+    X, eps, alpha, it, r, st = orc.fs_iterate_adaptive(A, U.T, w, np.full(n, 0.5), 10, 1e-13)
+    assert st == 0 and it == 0 and r <= 1e-13
+    assert np.array_equal(X, U.T)
+
+
+def test_adaptive_zero_steps_is_one_rayleigh_quotient(orc):
+    n = 20
+    A = wl.random_nearly_diagonal(n, seed=62, sigma=0.1, decay=None).A
+    X0 = wl.gaussian((3, n), seed=63)
+    eps0 = np.array([0.1, -0.2, 0.3])
+    X, eps, alpha, it, r, st = orc.fs_iterate_adaptive(A, X0, eps0, np.full(3, 0.5), 0, 0.0)
+    rq = np.einsum("ki,ij,kj->k", X0, A, X0) / np.einsum("ki,ki->k", X0, X0)
+    assert it == 0 and st == 5 and np.array_equal(X, X0)
+    assert np.max(np.abs(eps - rq)) <= 1e-15
+    res = [np.linalg.norm(A @ x - q * x) / np.linalg.norm(x) for x, q in zip(X0, rq)]
+    assert r == pytest.approx(max(res), rel=1e-12)
+
+
+def test_adaptive_residual_decreases_and_bounds_the_shift_error(orc):
+    """Folded-spectrum steps contract slowly (1 - alpha (lambda - eps)^2 per neighbour), so the
+    pin is the theory's: the residual decreases step by step, and each Rayleigh-quotient shift is
+    within ||r||^2 / gap of its eigenvalue (gap to the rest of the spectrum)."""
+    n = 40
+    A = wl.random_nearly_diagonal(n, seed=64, sigma=0.02).A
+    w, U = np.linalg.eigh(A)
+    ks = [3, 17, 30]
+    X0 = U[:, ks].T + 1e-3 * wl.gaussian((3, n), seed=65)
+    prev = None
+    for steps in (0, 1, 2, 4, 8, 16):
+        X, eps, alpha, it, r, st = orc.fs_iterate_adaptive(A, X0, w[ks] + 1e-4, np.full(3, 0.3), steps, 0.0)
+        assert it == steps
+        if prev is not None:
+            assert r < prev
+        prev = r
+        for k, e in zip(ks, eps):
+            x = X[list(ks).index(k)]
+            x = x / np.linalg.norm(x)
+            res = np.linalg.norm(A @ x - (x @ A @ x) * x)
+            gap = min(abs(w[j] - e) for j in range(n) if j != k)
+            assert abs(e - w[k]) <= res ** 2 / gap * 1.01 + 1e-15
+
+
+def test_method_with_adaptive_iterations_against_lapack(orc):
+    """More capped steps lower the eigenvalue error; every result is within Kahan's residual
+    bound; with the same count the adaptive variant is no worse than the fixed shifts."""
+    p = wl.small_gapped(0)
+    w = np.linalg.eigvalsh(p.A)
+    fixed = orc.pfsm(p.A, p.prev, p.nblocks, halo=p.halo, fs_iters=3)
+    errs = []
+    for k in (3, 10, 20):
+        r = orc.pfsm(p.A, p.prev, p.nblocks, halo=p.halo, fs_iters=k, fs_adaptive=True, fs_tol=0.0)
+        err = np.max(np.abs(r.lam - w))
+        R = p.A @ r.V - r.V * r.lam
+        assert err <= np.linalg.norm(R, 2)
+        errs.append(err)
+    assert errs[1] < errs[0] and errs[2] < errs[1]
+    assert errs[0] <= 1.01 * np.max(np.abs(fixed.lam - w))
