@@ -310,19 +310,19 @@ int oracle_fs_iterate_adaptive(int64_t n, int64_t cnt, const double *A, double *
     for (;;) {
 #pragma omp parallel for schedule(dynamic, 4)
         for (int64_t k = 0; k < cnt; k++) {
-            const double *x = X + k * n;
-            double *y = Y + k * n;
+            const double *xr = X + k * n;
+            double *yr = Y + k * n;
             for (int64_t i = 0; i < n; i++) {                /* y = (A - eps I) x */
                 double acc = 0.0;
-                for (int64_t j = 0; j < n; j++) acc += A[i * n + j] * x[j];
-                y[i] = acc - eps[k] * x[i];
+                for (int64_t c = 0; c < n; c++) acc += A[i * n + c] * xr[c];
+                yr[i] = acc - eps[k] * xr[i];
             }
             double xy = 0.0, xx = 0.0;
-            for (int64_t i = 0; i < n; i++) { xy += x[i] * y[i]; xx += x[i] * x[i]; }
+            for (int64_t i = 0; i < n; i++) { xy += xr[i] * yr[i]; xx += xr[i] * xr[i]; }
             const double delta = xy / xx;                    /* Rayleigh quotient - eps */
             eps[k] += delta;
             double yy = 0.0;
-            for (int64_t i = 0; i < n; i++) { y[i] -= delta * x[i]; yy += y[i] * y[i]; }
+            for (int64_t i = 0; i < n; i++) { yr[i] -= delta * xr[i]; yy += yr[i] * yr[i]; }
             r[k] = sqrt(yy / xx);
         }
         rmax = 0.0;
@@ -334,18 +334,18 @@ int oracle_fs_iterate_adaptive(int64_t n, int64_t cnt, const double *A, double *
             double *z = (double *)malloc(sizeof(double) * (size_t)n);
 #pragma omp for schedule(dynamic, 4)
             for (int64_t k = 0; k < cnt; k++) {
-                double *x = X + k * n;
-                const double *y = Y + k * n;
+                double *xr = X + k * n;
+                const double *yr = Y + k * n;
                 double dmax = ghi - eps[k];
                 if (eps[k] - glo > dmax) dmax = eps[k] - glo;
                 const double a = theta / (dmax * dmax), cap = 1.0 - ldexp(1.0, -20);
                 alpha[k] = (a < cap) ? a : cap;
                 for (int64_t i = 0; i < n; i++) {            /* z = (A - eps I) y */
                     double acc = 0.0;
-                    for (int64_t j = 0; j < n; j++) acc += A[i * n + j] * y[j];
-                    z[i] = acc - eps[k] * y[i];
+                    for (int64_t c = 0; c < n; c++) acc += A[i * n + c] * yr[c];
+                    z[i] = acc - eps[k] * yr[i];
                 }
-                for (int64_t i = 0; i < n; i++) x[i] -= alpha[k] * z[i];
+                for (int64_t i = 0; i < n; i++) xr[i] -= alpha[k] * z[i];
             }
             free(z);
         }

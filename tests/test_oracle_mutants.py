@@ -52,8 +52,8 @@ MUTANTS = {
     "full_home_index_swapped": ("double flip, yh = Y[k * n + k];", "double flip, yh = Y[k * n + 0];"),
     "full_sign_rule_dropped": ("flip = (yh >= 0.0) ? 1.0 : -1.0;", "flip = 1.0;"),
     "adaptive_shift_sign": ("eps[k] += delta;", "eps[k] -= delta;"),
-    "adaptive_no_y_correction": ("for (int64_t i = 0; i < n; i++) { y[i] -= delta * x[i]; yy += y[i] * y[i]; }",
-                                 "for (int64_t i = 0; i < n; i++) { yy += y[i] * y[i]; }"),
+    "adaptive_no_y_correction": ("for (int64_t i = 0; i < n; i++) { yr[i] -= delta * xr[i]; yy += yr[i] * yr[i]; }",
+                                 "for (int64_t i = 0; i < n; i++) { yy += yr[i] * yr[i]; }"),
     "adaptive_residual_unnormalised": ("r[k] = sqrt(yy / xx);", "r[k] = sqrt(yy);"),
 }
 
