@@ -99,6 +99,13 @@ typedef struct {
                               default 0). A full diagonalization (cuSOLVER syevd) gives the same
                               outputs as the method: vectors signed by the start-vector rule,
                               Rayleigh quotients, residuals, V; pfsm_backward works after it. */
+    int32_t fs_adaptive;   /* not in the paper: 1 replaces the fixed Eq. 11 count by steps that
+                              first move every shift to its vector's Rayleigh quotient (and the
+                              step size alpha with it) and stop once max_k ||(A - eps_k) x_k|| /
+                              ||x_k|| <= fs_tol * ||A||_Gershgorin, fs_iters steps at most; runs
+                              its products in FP64 in every precision; one residual read-back (a
+                              stream synchronisation) per step (default 0) */
+    double fs_tol;         /* its tolerance (default 0: the cap decides) */
 } pfsm_params_t;
 
 /* Fills *p with the defaults listed above. */
@@ -275,6 +282,8 @@ typedef struct {
     int32_t path;         /* last pfsm_solve: 0 the method, 1 full diagonalization by the
                              first-steps rule, 2 full diagonalization by the guard */
     double guard_value;   /* its guard value g (0 when not measured) */
+    int32_t fs_steps;     /* Eq. 11 steps taken by the last solve */
+    double fs_residual;   /* with fs_adaptive: the last max_k residual measured (else 0) */
 } pfsm_profile_t;
 
 /* Enables (enable != 0) or disables CUDA-event phase timing on h. Timing adds one event record

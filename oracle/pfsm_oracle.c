@@ -292,8 +292,8 @@ void oracle_fs_iterate(int64_t n, int64_t cnt, const double *A, double *X, const
 /* iteration first moves every shift to the Rayleigh quotient of its vector and measures the   */
 /* residual, then takes the Eq. 11 step with the new shift:                                     */
 /*   y = (A - eps I) x;  delta = x.y / x.x;  eps += delta;  y -= delta x   (y = (A - eps I) x); */
-/*   r = ||y|| / ||x||;  stop when max_k r_k <= tol_abs (before the step) or after max_iters   */
-/*   steps;  alpha = min(theta / d^2, 1 - 2^-20), d = max(ghi - eps, eps - glo);               */
+/*   alpha = min(theta / d^2, 1 - 2^-20), d = max(ghi - eps, eps - glo);  r = ||y|| / ||x||;   */
+/*   stop when max_k r_k <= tol_abs (before the step) or after max_iters steps;                */
 /*   x -= alpha (A - eps I) y.                                                                  */
 /* X: cnt x n rows; eps, alpha updated in place. *iters = steps done, *resid = the last        */
 /* max_k r_k. Returns OR_OK (tolerance met) or OR_NOT_CONVERGED (max_iters reached).          */
@@ -321,6 +321,10 @@ int oracle_fs_iterate_adaptive(int64_t n, int64_t cnt, const double *A, double *
             for (int64_t i = 0; i < n; i++) { xy += xr[i] * yr[i]; xx += xr[i] * xr[i]; }
             const double delta = xy / xx;                    /* Rayleigh quotient - eps */
             eps[k] += delta;
+            double dmax = ghi - eps[k];                      /* the step size follows the shift */
+            if (eps[k] - glo > dmax) dmax = eps[k] - glo;
+            const double a = theta / (dmax * dmax), cap = 1.0 - ldexp(1.0, -20);
+            alpha[k] = (a < cap) ? a : cap;
             double yy = 0.0;
             for (int64_t i = 0; i < n; i++) { yr[i] -= delta * xr[i]; yy += yr[i] * yr[i]; }
             r[k] = sqrt(yy / xx);
@@ -336,10 +340,6 @@ int oracle_fs_iterate_adaptive(int64_t n, int64_t cnt, const double *A, double *
             for (int64_t k = 0; k < cnt; k++) {
                 double *xr = X + k * n;
                 const double *yr = Y + k * n;
-                double dmax = ghi - eps[k];
-                if (eps[k] - glo > dmax) dmax = eps[k] - glo;
-                const double a = theta / (dmax * dmax), cap = 1.0 - ldexp(1.0, -20);
-                alpha[k] = (a < cap) ? a : cap;
                 for (int64_t i = 0; i < n; i++) {            /* z = (A - eps I) y */
                     double acc = 0.0;
                     for (int64_t c = 0; c < n; c++) acc += A[i * n + c] * yr[c];

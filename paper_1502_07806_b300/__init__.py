@@ -41,13 +41,15 @@ class Params(ctypes.Structure):
                 ("alpha_theta", ctypes.c_double), ("cluster_tol", ctypes.c_double),
                 ("degen_tol", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("recompute_v", ctypes.c_int32), ("slice_sizes", ctypes.POINTER(ctypes.c_int32)),
-                ("guard_max", ctypes.c_double), ("full_steps", ctypes.c_int32)]
+                ("guard_max", ctypes.c_double), ("full_steps", ctypes.c_int32),
+                ("fs_adaptive", ctypes.c_int32), ("fs_tol", ctypes.c_double)]
 
 
 class Profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int32), ("timed", ctypes.c_int32),
                 ("phase_ms", ctypes.c_float * 12), ("gemm_tile_n", ctypes.c_int32),
-                ("path", ctypes.c_int32), ("guard_value", ctypes.c_double)]
+                ("path", ctypes.c_int32), ("guard_value", ctypes.c_double),
+                ("fs_steps", ctypes.c_int32), ("fs_residual", ctypes.c_double)]
 
 
 _lib = None
@@ -118,13 +120,14 @@ class Handle:
     def __init__(self, n: int, nblocks: int, halo: int = -1, fs_iters: int = 3,
                  alpha_theta: float = 1.0, cluster_tol: float = 1e-5, degen_tol: float = 1e-8,
                  precision: int = FP64, recompute_v: bool = False, slice_sizes=None,
-                 guard_max: float = 0.0, full_steps: int = 0):
+                 guard_max: float = 0.0, full_steps: int = 0, fs_adaptive: bool = False, fs_tol: float = 0.0):
         lib = load_library()
         p = default_params()
         p.halo, p.fs_iters, p.alpha_theta = halo, fs_iters, alpha_theta
         p.cluster_tol, p.degen_tol, p.precision = cluster_tol, degen_tol, precision
         p.recompute_v = int(bool(recompute_v))
         p.guard_max, p.full_steps = guard_max, full_steps
+        p.fs_adaptive, p.fs_tol = int(bool(fs_adaptive)), fs_tol
         self._sizes = None
         if slice_sizes is not None:
             self._sizes = (ctypes.c_int32 * nblocks)(*[int(x) for x in slice_sizes])
@@ -187,7 +190,7 @@ class Handle:
         pr = Profile()
         _check(load_library().pfsm_get_profile(self._h, ctypes.byref(pr)), "pfsm_get_profile")
         out = {"launches": pr.launches, "gemm_tile_n": pr.gemm_tile_n, "path": pr.path,
-               "guard_value": pr.guard_value}
+               "guard_value": pr.guard_value, "fs_steps": pr.fs_steps, "fs_residual": pr.fs_residual}
         if pr.timed:
             out.update({name: float(pr.phase_ms[i]) for i, name in enumerate(PHASES)})
             out.update({name: float(pr.phase_ms[6 + i]) for i, name in enumerate(SUB_PHASES)})

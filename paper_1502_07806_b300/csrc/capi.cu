@@ -1,5 +1,7 @@
 // C ABI of the PFSM library: argument checks, workspace ownership, and the order of kernels for
 // one solve (Section II: partition, submatrix solves, Eq. 11 iterations, Gram-Schmidt).
+#include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -80,6 +82,8 @@ void pfsm_default_params(pfsm_params_t *p)
     p->slice_sizes = nullptr;
     p->guard_max = 0.0;
     p->full_steps = 0;
+    p->fs_adaptive = 0;
+    p->fs_tol = 0.0;
 }
 
 const char *pfsm_last_error(void) { return g_last_error.c_str(); }
@@ -95,6 +99,8 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
     pfsm_default_params(&prm);
     if (p) prm = *p;
     if (prm.fs_iters < 0 || prm.fs_iters > 1000) return fail(PFSM_ERR_INVALID_ARG, "pfsm_init: fs_iters=%d", prm.fs_iters);
+    if (!(prm.fs_tol >= 0.0) || (prm.fs_adaptive != 0 && prm.fs_adaptive != 1))
+        return fail(PFSM_ERR_INVALID_ARG, "pfsm_init: fs_adaptive must be 0 or 1 and fs_tol >= 0");
     if (prm.full_steps < 0 || prm.guard_max != prm.guard_max)
         return fail(PFSM_ERR_INVALID_ARG, "pfsm_init: full_steps must be >= 0 and guard_max a number");
     if (!(prm.alpha_theta > 0.0) || !(prm.cluster_tol >= 0.0) || !(prm.degen_tol >= 0.0))
@@ -246,6 +252,12 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
         return fail(PFSM_ERR_CUDA, "pfsm_init: %s", cudaGetErrorString(e));
     }
     h->prm.slice_sizes = nullptr;   // the host array is not kept
+    if (prm.fs_adaptive && cudaMalloc((void **)&h->fs_rmax, sizeof(unsigned long long)) != cudaSuccess) {
+        free_ws(h);
+        delete h;
+        cudaGetLastError();
+        return fail(PFSM_ERR_OUT_OF_MEMORY, "pfsm_init: residual buffer");
+    }
     if (prm.full_steps > 0 || prm.guard_max > 0.0) {
         const cudaError_t fe = fallback_init(h);
         if (fe != cudaSuccess) {
@@ -349,7 +361,41 @@ static int solve_impl(pfsm_handle_s *h, const double *A, const double *prev, dou
     PFSM_CUDA(mark(1));
     PFSM_CUDA(launch_subeig(h, A, st));
     PFSM_CUDA(mark(2));
-    if (h->prm.precision != PFSM_FP64) {
+    h->last_fs_steps = h->prm.fs_iters;
+    h->last_fs_resid = 0.0;
+    if (h->prm.fs_adaptive) {
+        // Rayleigh-quotient shifts and residual stopping (FP64 products in every precision); the
+        // Gershgorin ends (for the tolerance) come back with the first residual
+        double gb[2] = {0.0, 0.0};
+        PFSM_CUDA(cudaMemcpyAsync(gb, w.gersh + 2 * N, sizeof(gb), cudaMemcpyDeviceToHost, st));
+        unsigned long long *rmax = h->fs_rmax;
+        int steps = 0;
+        double r = 0.0;
+        for (;;) {
+            GemmArgs g{};
+            g.rows = N; g.cols = N; g.K = N;
+            g.P = w.X; g.ldp = N; g.Q = A; g.ldq = N; g.C = w.Y; g.ldc = N;
+            g.aux_x = w.X; g.eps = w.eps;
+            g.krange = (steps == 0) ? w.tile_krange : nullptr;   // start vectors vanish outside windows
+            PFSM_CUDA(launch_gemm_f64(g, EPI_FS1, Q_KMAJOR, st));
+            PFSM_CUDA(cudaMemsetAsync(rmax, 0, sizeof(unsigned long long), st));
+            PFSM_CUDA(launch_rq_shift(w.X, w.Y, w.eps, w.alpha, w.gersh, h->prm.alpha_theta, N, rmax, st));
+            unsigned long long rb = 0;
+            PFSM_CUDA(cudaMemcpyAsync(&rb, rmax, sizeof(rb), cudaMemcpyDeviceToHost, st));
+            PFSM_CUDA(cudaStreamSynchronize(st));
+            std::memcpy(&r, &rb, sizeof(r));
+            const double tol_abs = h->prm.fs_tol * std::max(std::fabs(gb[0]), std::fabs(gb[1]));
+            if (r <= tol_abs || steps >= h->prm.fs_iters) break;
+            GemmArgs u{};
+            u.rows = N; u.cols = N; u.K = N;
+            u.P = w.Y; u.ldp = N; u.Q = A; u.ldq = N; u.C = w.X; u.ldc = N;
+            u.aux_y = w.Y; u.eps = w.eps; u.alpha = w.alpha;
+            PFSM_CUDA(launch_gemm_f64(u, EPI_FS2, Q_KMAJOR, st));
+            steps++;
+        }
+        h->last_fs_steps = steps;
+        h->last_fs_resid = r;
+    } else if (h->prm.precision != PFSM_FP64) {
         PFSM_CUDA(fs_mixed(h, A, st));
     } else
     // Eq. 11, fs_iters times: Y = (A - eps I) X ; X <- X - alpha (A - eps I) Y
@@ -628,6 +674,8 @@ int pfsm_get_profile(pfsm_handle_t h, pfsm_profile_t *out)
     out->gemm_tile_n = h->prm.precision != PFSM_FP64 ? h->tc_bn : 0;
     out->path = h->last_path;
     out->guard_value = h->last_guard;
+    out->fs_steps = h->last_path ? 0 : h->last_fs_steps;
+    out->fs_residual = h->last_path ? 0.0 : h->last_fs_resid;
     if (!h->timing || !h->solved) return PFSM_OK;
     PFSM_CUDA(cudaStreamSynchronize(h->last_stream));
     auto span = [&](int a, int b, float *dst) -> cudaError_t { return cudaEventElapsedTime(dst, h->ev[a], h->ev[b]); };
@@ -657,6 +705,7 @@ int pfsm_destroy(pfsm_handle_t h)
     for (int i = 0; i < 2; i++)
         if (h->gs_ev[i]) cudaEventDestroy(h->gs_ev[i]);
     fallback_free(h);
+    if (h->fs_rmax) cudaFree(h->fs_rmax);
     free_ws(h);
     delete h;
     return PFSM_OK;

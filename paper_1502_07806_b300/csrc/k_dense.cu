@@ -290,6 +290,55 @@ cudaError_t launch_rayleigh_f64(pfsm_handle_s *h, const double *A, double *eigva
     return cudaMemcpyAsync(V_out, w.Vrm, (size_t)N * N * sizeof(double), cudaMemcpyDeviceToDevice, st);
 }
 
+// ---- adaptive variant of Eq. 11: Rayleigh-quotient shifts and the residual ----------------------
+
+// One warp per vector k (rows of X and Y = (A - eps I) X): delta = x.y / x.x; eps += delta;
+// y -= delta x; alpha from the new shift (min(theta / d^2, 1 - 2^-20), d the larger distance to
+// the Gershgorin ends); the residual ||y|| / ||x|| into *rmax (atomic max on non-negative bits).
+__global__ void k_rq_shift(const double *__restrict__ X, double *__restrict__ Y, double *__restrict__ eps,
+                           double *__restrict__ alpha, const double *__restrict__ gersh, double theta, int64_t N,
+                           unsigned long long *__restrict__ rmax)
+{
+    const int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (k >= N) return;
+    const double *x = X + k * N;
+    double *y = Y + k * N;
+    double xy = 0.0, xx = 0.0;
+    for (int64_t i = lane; i < N; i += 32) { xy = fma(x[i], y[i], xy); xx = fma(x[i], x[i], xx); }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        xy += __shfl_xor_sync(0xffffffffu, xy, o);
+        xx += __shfl_xor_sync(0xffffffffu, xx, o);
+    }
+    const double delta = xy / xx;
+    double yy = 0.0;
+    for (int64_t i = lane; i < N; i += 32) {
+        const double v = fma(-delta, x[i], y[i]);
+        y[i] = v;
+        yy = fma(v, v, yy);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) yy += __shfl_xor_sync(0xffffffffu, yy, o);
+    if (lane == 0) {
+        const double e = eps[k] + delta;
+        eps[k] = e;
+        const double glo = gersh[2 * N], ghi = gersh[2 * N + 1];
+        const double dmax = fmax(ghi - e, e - glo);
+        const double a = theta / (dmax * dmax), cap = 1.0 - 0x1.0p-20;
+        alpha[k] = (a < cap) ? a : cap;
+        atomicMax(rmax, (unsigned long long)__double_as_longlong(sqrt(yy / xx)));
+    }
+}
+
+cudaError_t launch_rq_shift(double *X, double *Y, double *eps, double *alpha, const double *gersh, double theta,
+                            int64_t N, unsigned long long *rmax, cudaStream_t st)
+{
+    k_rq_shift<<<(unsigned)((N + 7) / 8), 256, 0, st>>>(X, Y, eps, alpha, gersh, theta, N, rmax);
+    g_launches++;
+    return cudaGetLastError();
+}
+
 // ---- eigen-adjoint ----------------------------------------------------------------------------
 
 // In place on G = V^T dV: M_kl = sym(diag(dlam) + F o G), F_kl = 1/(lam_l - lam_k) masked.

@@ -83,6 +83,9 @@ struct pfsm_handle_s {
     int syevd_lwork = 0;
     int *syevd_info = nullptr;
     unsigned long long *guard_buf = nullptr;
+    int32_t last_fs_steps = 0;     // Eq. 11 steps of the last solve
+    double last_fs_resid = 0.0;    // adaptive variant: its last measured residual
+    unsigned long long *fs_rmax = nullptr;   // adaptive variant: residual read-back (device)
     bool rows_in_smem = true;
     bool tri_blocked = false;      // mixed forms: blocked reduction (k_tridiag_panel)
     int32_t tri_rpw = 8;           // its rows-per-warp register capacity (8 or 24)
@@ -216,6 +219,10 @@ cudaError_t digit_product(const Digits &dx, const Digits &dy, double *C, int64_t
 cudaError_t dense_product(const double *X, const double *Yrows, double *C, int64_t N, Digits &dx, Digits &dy,
                           int32_t *status, cudaStream_t st);
 cudaError_t launch_symmetrize(const double *T, double *S, int64_t N, cudaStream_t st);   // S = (T + T^T) / 2
+// adaptive Eq. 11 (k_dense.cu): per row k, eps_k += x.y / x.x, y -= that x, alpha_k from the new
+// shift, *rmax (bits, zeroed by the caller) = max_k ||y_k|| / ||x_k||
+cudaError_t launch_rq_shift(double *X, double *Y, double *eps, double *alpha, const double *gersh, double theta,
+                            int64_t N, unsigned long long *rmax, cudaStream_t st);
 // ---- generalized -> standard conversion (k_gen2std.cu) ----
 struct Gen2StdResult {
     int iters = 0;                  // updates done
