@@ -30,6 +30,17 @@ constexpr int kTriThreads = 256;      // blocked panel kernel
 constexpr int kTriLaThreads = 288;    // k_tridiag: warp 0 + eight warps (two per sub-partition)
 constexpr size_t kInvSmemCap = 200 * 1024;  // k_inverse_iter: shared memory for the lanes' vectors
 
+// named barrier `id` over n threads: bar.sync waits for all n, bar.arrive counts this warp
+// without waiting (the arriving threads' earlier shared-memory writes are visible to the waiters)
+__device__ __forceinline__ void named_sync(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int n)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
 __device__ __forceinline__ double block_sum(double v, double *red)
 {
 #pragma unroll
@@ -95,34 +106,64 @@ __device__ __forceinline__ void householder_scalars(const double *c, int kk, int
     if (lane == 0) { sc[0] = beta; sc[1] = alpha; sc[2] = v0; }
 }
 
+// The fused loop of k_tridiag for NG rows (entries j >= rmin, lanes along the row): with UPD the
+// rank-2 update B_ij -= v_i w_j + w_i v_j, and acc_g += B_ij c_j on the (updated) entries.
+template <int NG, bool UPD>
+__device__ __forceinline__ void tri_rows(double *const *rp, const double *vi, const double *wi,
+                                         const double *__restrict__ hv, const double *__restrict__ wv,
+                                         const double *__restrict__ cv, int rmin, int M, int lane,
+                                         double *acc)
+{
+    for (int j = rmin + lane; j < M; j += 32) {
+        const double vj = hv[j], wj = wv[j], cj = cv[j];
+#pragma unroll
+        for (int g = 0; g < NG; g++) {
+            double bb = rp[g][j];
+            if (UPD) {
+                bb = fma(-vi[g], wj, fma(-wi[g], vj, bb));
+                rp[g][j] = bb;
+            }
+            acc[g] = fma(bb, cj, acc[g]);
+        }
+    }
+}
+
 // Householder reduction of every window to tridiagonal form, one thread-block cluster per window.
 // Grid: nb * CL CTAs, clusters of CL along x; CTA `rank` owns the rows i with i % CL == rank (in
 // shared memory when they fit, else in the window's global work matrix).
 //
 // B300 spends ~64 cycles of a sub-partition's FP64 pipe on every FP64 warp instruction and a
 // dependent FP64 chain runs at about that pace, so the step is arranged around ONE cluster barrier
-// with the serial work hidden behind the rank-2 update (a look-ahead form of Golub & Van Loan
-// Sec. 8.3.1). Step k, with x = column k (entries > k, in every CTA), its scalars (alpha, beta)
-// and u = B x on the owned rows already known:
-//   S1  v = x with v_{k+1} = x_{k+1} - alpha;  p_i = beta (u_i - alpha B_{i,k+1}) = beta (B v)_i for
-//       the owned rows, pushed into every CTA with the CTA's partial p.v; the owner of row k+1
-//       pushes that row (= column k+1, by symmetry) into every CTA.
+// with all of its serial work hidden behind the rank-2 update (a look-ahead form of Golub & Van
+// Loan Sec. 8.3.1). Step k starts with, in every CTA: the Householder vector v of column k
+// (entries > k) and its scalars (alpha, beta), p_i = beta (B v)_i for every row i > k, the
+// partial sums of p.v and row k+1 (entries > k+1), all sent during the previous step.
 //   --  cluster barrier
 //   S2  w = p - (beta p.v / 2) v, and the next column x' = (row k+1) - v_{k+1} w - w_{k+1} v,
 //       i.e. column k+1 after this step's update, in every CTA without a second exchange.
-//   S3  warp 0: the scalars of step k+1 from x'. Warps 1-8 (two per SM sub-partition): the
-//       rank-2 update B -= v w^T + w v^T of the owned rows, fused with the next step's product
-//       u' = B x' on the freshly updated entries (lanes along the row, eight rows per warp, the
-//       per-row sums by one transpose-reduce: 9 shuffle adds per 8 rows).
-// Buffers written by other CTAs (p, the p.v partials, row k+1) alternate with the step's parity:
-// a CTA can run at most one step ahead of another, since it cannot pass the next barrier first.
+//   S3  warp 0: the scalars of step k+1 from x' and its Householder vector v' (CTA 0 also stores
+//       the reflector). Warps 1-8 (two per SM sub-partition): the rank-2 update B -= v w^T + w v^T
+//       of the owned rows fused with u = B x' on the freshly updated entries (lanes along the
+//       row, up to eight rows per warp in a loop compiled for the exact row count, the per-row
+//       sums by one transpose-reduce); then, once warp 0 has published v' (named barrier 1),
+//       p'_i = beta' (u_i - alpha' B_{i,k+2}) = beta' (B v')_i and p'_i v'_i for the owned rows;
+//       after named barrier 2 the fused warps copy the CTA's p' values as one contiguous block
+//       into every CTA (coalesced remote stores), warp 0 sums the CTA's partial p'.v' and sends
+//       it, and the owner of row k+2 sends that row.
+// B300's SM retires about one FP64 warp instruction per 16 cycles whatever its active lanes, so
+// the work outside the fused loop is kept to few FP64 warp instructions (one warp reduces where a
+// reduction in every warp would queue eight times the instructions on the same pipe).
+// Buffers written by other CTAs (p, the p.v partials, row k+1) and the vector v alternate with
+// the step's parity: a CTA can run at most one step ahead of another, since it cannot pass the
+// next barrier first.
 template <bool SMEM_ROWS>
-__global__ void __launch_bounds__(kTriLaThreads)
+__global__ void __launch_bounds__(kTriLaThreads, 1)
 k_tridiag(const double *__restrict__ A, int64_t N, const int32_t *__restrict__ plan, int32_t nb,
           int32_t Mmax, double *__restrict__ gwork, double *__restrict__ refl,
           double *__restrict__ tau, double *__restrict__ td, double *__restrict__ te)
 {
     constexpr int G = 8;                               // rows per warp group in the fused loop
+    constexpr int NWQ = kTriLaThreads / 32 - 1;        // warps of the fused loop
     cg::cluster_group cluster = cg::this_cluster();
     const int CL = (int)cluster.num_blocks();
     const int rank = (int)cluster.block_rank();
@@ -133,16 +174,19 @@ k_tridiag(const double *__restrict__ A, int64_t N, const int32_t *__restrict__ p
     extern __shared__ double sm[];
     double *rows = SMEM_ROWS ? sm : (gwork + (size_t)b * Mmax * Mmax);
     double *vec = sm + (SMEM_ROWS ? (size_t)R * Mmax : 0);
-    double *cbuf = vec;                    // x: column k, entries > k
-    double *nbuf = vec + Mmax;             // x': column k+1 after step k, entries > k+1
-    double *hv = vec + 2 * Mmax;           // v
+    double *xcol = vec;                    // column to reduce next: column 0, then each step's x'
+    double *hvb = vec + Mmax;              // [2][Mmax] v of the step of that parity
     double *wv = vec + 3 * Mmax;           // w
-    double *pbuf = vec + 4 * Mmax;         // [2][Mmax] p (written by every CTA)
-    double *rowbuf = vec + 6 * Mmax;       // [2][Mmax] row k+1 (written by its owner)
-    double *uu = vec + 8 * Mmax;           // [R] (B x)_i of the owned rows
-    double *pvp = uu + R;                  // [2][32] partial p.v of every CTA
-    double *sc = pvp + 64;                 // scalars of the next step
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int PS = Mmax + 16;              // >= CL R
+    double *pbuf = vec + 4 * Mmax;         // [2][PS] p: block [CL][R], row li * CL + r at r R + li
+    double *rowbuf = pbuf + 2 * PS;        // [2][Mmax] row k+1 (written by its owner)
+    double *uu = rowbuf + 2 * Mmax;        // [R] (B x')_i of the owned rows
+    double *prod = uu + R;                 // [R] p_i v_i of the owned rows
+    double *pst = prod + R;                // [R] p_i of the owned rows (staging for the push)
+    double *pvp = pst + R;                 // [2][32] partial p.v of every CTA
+    double *scb = pvp + 64;                // [2][4] beta, alpha, v0 of the step of that parity
+    double *kcs = scb + 8;                 // beta p.v / 2 of the current step
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     auto rowp = [&](int i) -> double * {
         return SMEM_ROWS ? rows + (size_t)(i / CL) * Mmax : rows + (size_t)i * Mmax;
     };
@@ -151,17 +195,19 @@ k_tridiag(const double *__restrict__ A, int64_t N, const int32_t *__restrict__ p
     const int nown = (M - rank + CL - 1) / CL;         // owned rows li * CL + rank < M
 
     // rows i >= rmin: B_ij -= v_i w_j + w_i v_j for j >= rmin (when upd), and
-    // uu = sum_{j >= rmin} B_ij c_j on the updated entries (c_rmin must be 0 or part of the sum)
-    auto fused = [&](int rmin, const double *cv, bool upd) {
-        const int wq = warp - 1, nwq = nwarps - 1;
+    // uu = sum_{j >= rmin} B_ij c_j on the updated entries (c_rmin must be 0 or part of the sum).
+    // Fused warp wq takes the owned rows li = lfirst + wq + NWQ m, up to G at a time; each group
+    // runs a loop compiled for its exact row count (no FP64 work issued for absent rows).
+    auto fused = [&](int rmin, const double *cv, const double *hv, bool upd) {
+        const int wq = warp - 1;
         const int lfirst = (rmin - rank + CL - 1) / CL;
-        for (int t0 = lfirst + wq; t0 < nown; t0 += nwq * G) {
+        for (int t0 = lfirst + wq; t0 < nown; t0 += NWQ * G) {
             double *rp[G];
             double vi[G], wi[G], acc[G];
             int cnt = 0;
 #pragma unroll
             for (int g = 0; g < G; g++) {
-                const int li = t0 + nwq * g;
+                const int li = t0 + NWQ * g;
                 const bool ok = li < nown;
                 const int i = ok ? li * CL + rank : rank;
                 rp[g] = rowp(i);
@@ -170,20 +216,22 @@ k_tridiag(const double *__restrict__ A, int64_t N, const int32_t *__restrict__ p
                 acc[g] = 0.0;
                 cnt += ok ? 1 : 0;
             }
-            for (int j = rmin + lane; j < M; j += 32) {
-                const double vj = hv[j], wj = wv[j], cj = cv[j];
-#pragma unroll
-                for (int g = 0; g < G; g++) {
-                    if (g < cnt) {
-                        double bb = rp[g][j];
-                        if (upd) {
-                            bb = fma(-vi[g], wj, fma(-wi[g], vj, bb));
-                            rp[g][j] = bb;
-                        }
-                        acc[g] = fma(bb, cj, acc[g]);
-                    }
-                }
+#define PFSM_TRI_ROWS(NG)                                                                          \
+    case NG:                                                                                       \
+        if (upd) tri_rows<NG, true>(rp, vi, wi, hv, wv, cv, rmin, M, lane, acc);                 \
+        else tri_rows<NG, false>(rp, vi, wi, hv, wv, cv, rmin, M, lane, acc);                    \
+        break;
+            switch (cnt) {
+                PFSM_TRI_ROWS(1)
+                PFSM_TRI_ROWS(2)
+                PFSM_TRI_ROWS(3)
+                PFSM_TRI_ROWS(4)
+                PFSM_TRI_ROWS(5)
+                PFSM_TRI_ROWS(6)
+                PFSM_TRI_ROWS(7)
+                default: PFSM_TRI_ROWS(8)
             }
+#undef PFSM_TRI_ROWS
             // sums over the 32 lanes: halve the rows held per lane at offsets 16, 8, 4 (lane
             // ends with row (lane >> 2) & 7), then plain butterflies over the last two lane bits
 #pragma unroll
@@ -206,92 +254,154 @@ k_tridiag(const double *__restrict__ A, int64_t N, const int32_t *__restrict__ p
             acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 2);
             acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
             const int g = (lane >> 2) & 7;
-            if ((lane & 3) == 0 && g < cnt) uu[t0 + nwq * g] = acc[0];
+            if ((lane & 3) == 0 && g < cnt) uu[t0 + NWQ * g] = acc[0];
         }
     };
 
+    // warp 0: scalars of step kn from the column in xcol (entries > kn), its Householder vector
+    // into hv[parn] and, in CTA 0, the reflector, alpha and beta into the window's outputs
+    auto next_vector = [&](int kn, int parn) {
+        const int n1n = kn + 1;
+        double *scn = scb + 4 * parn, *hvn = hvb + (size_t)parn * Mmax;
+        householder_scalars(xcol, kn, M, lane, scn);
+        __syncwarp();
+        const double beta = scn[0], alpha = scn[1], v0 = scn[2];
+        double *rr = brefl + (size_t)kn * Mmax;
+        for (int j = n1n + lane; j < M; j += 32) {
+            const double v = (beta != 0.0) ? ((j == n1n) ? v0 : xcol[j]) : 0.0;
+            hvn[j] = v;
+            if (rank == 0) rr[j] = v;
+        }
+        if (rank == 0 && lane == 0) { bte[kn] = alpha; btau[kn] = beta; }
+    };
+
+    // fused warps, after the fused loop over rows >= rmin and warp 0's next_vector for the step
+    // whose first row is n1n: p_i (zero for i < n1n) and p_i v_i of the warp's own rows into pst
+    // and prod; after named barrier 2 (with warp 0) the owned rows' p values go to block `rank` of
+    // every CTA's p buffer as contiguous runs (coalesced remote stores), and the owner of row n1n
+    // sends that row (entries > n1n)
+    auto publish = [&](int rmin, int n1n, int parn) {
+        const int wq = warp - 1;
+        const double *scn = scb + 4 * parn, *hvn = hvb + (size_t)parn * Mmax;
+        const double beta = scn[0], alpha = scn[1];
+        const int lfirst = (rmin - rank + CL - 1) / CL;
+        for (int li = lfirst + wq + NWQ * lane; li < nown; li += NWQ * 32) {
+            const int i = li * CL + rank;
+            double p = 0.0, pr = 0.0;
+            if (i >= n1n) {
+                p = beta * fma(-alpha, rowp(i)[n1n], uu[li]);
+                pr = p * hvn[i];
+            }
+            pst[li] = p;
+            prod[li] = pr;
+        }
+        named_sync(2, kTriLaThreads);
+        const int cntp = nown - lfirst;
+        if (cntp > 0) {
+            double *pbn = pbuf + (size_t)parn * PS + (size_t)rank * R;
+            for (int idx = tid - 32; idx < CL * cntp; idx += NWQ * 32) {
+                const int r = idx / cntp, li = lfirst + idx - r * cntp;
+                cluster.map_shared_rank(pbn, r)[li] = pst[li];
+            }
+        }
+        if (n1n % CL == rank) {
+            double *rbn = rowbuf + (size_t)parn * Mmax;
+            const double *rr = rowp(n1n);
+            for (int j = n1n + 1 + (tid - 32); j < M; j += NWQ * 32) {
+                const double x = rr[j];
+                for (int r = 0; r < CL; r++) cluster.map_shared_rank(rbn, r)[j] = x;
+            }
+        }
+    };
+
+    // warp 0, after named barrier 2: the CTA's partial p.v over its rows >= rmin into every CTA
+    // (Every FP64 warp instruction holds the SM's FP64 pipe for ~16 cycles whatever its active
+    // lanes, so the sum is one warp's, not a reduction in every warp.)
+    auto partial_pv = [&](int rmin, int parn) {
+        const int lfirst = (rmin - rank + CL - 1) / CL;
+        double t = 0.0;
+        for (int q = lfirst + lane; q < nown; q += 32) t += prod[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane < CL) cluster.map_shared_rank(pvp + 32 * parn, lane)[rank] = t;
+    };
+
     // load owned rows of B = A[s0:s0+M, s0:s0+M]
-    for (int i = rank + warp * CL; i < M; i += nwarps * CL) {
+    for (int i = rank + warp * CL; i < M; i += (kTriLaThreads / 32) * CL) {
         const double *src = A + (s0 + i) * N + s0;
         double *dst = rowp(i);
         for (int j = lane; j < M; j += 32) dst[j] = src[j];
     }
-    for (int j = tid; j < Mmax; j += blockDim.x) { hv[j] = 0.0; wv[j] = 0.0; }
+    for (int j = tid; j < 2 * Mmax; j += blockDim.x) hvb[j] = 0.0;
+    for (int j = tid; j < Mmax; j += blockDim.x) wv[j] = 0.0;
     // every CTA of the cluster must be running before any distributed-shared-memory access
     cluster.sync();
     // column 0 (entries >= 1) into every CTA
     for (int i = rank + tid * CL; i < M; i += blockDim.x * CL) {
         if (i < 1) continue;
         const double v = rowp(i)[0];
-        for (int r = 0; r < CL; r++) cluster.map_shared_rank(cbuf, r)[i] = v;
+        for (int r = 0; r < CL; r++) cluster.map_shared_rank(xcol, r)[i] = v;
     }
     cluster.sync();
-    // u = B x for step 0 and its scalars
+    // step 0's vector, u = B x and p
     if (warp == 0) {
-        if (M >= 3) householder_scalars(cbuf, 0, M, lane, sc);
+        if (M >= 3) {
+            next_vector(0, 0);
+            named_arrive(1, kTriLaThreads);
+            named_sync(2, kTriLaThreads);
+            partial_pv(1, 0);
+        }
     } else {
-        fused(1, cbuf, false);
+        fused(1, xcol, hvb, false);
+        if (M >= 3) {
+            named_sync(1, kTriLaThreads);
+            publish(1, 1, 0);
+        }
     }
-    __syncthreads();
 
     for (int k = 0; k + 2 < M; k++) {
         const int par = k & 1, n1 = k + 1;
-        const double beta = sc[0], alpha = sc[1], v0 = sc[2];
-        double *pb = pbuf + par * Mmax, *rb = rowbuf + par * Mmax, *pp = pvp + par * 32;
-        // S1
-        for (int j = n1 + tid; j < M; j += blockDim.x) hv[j] = (beta != 0.0) ? ((j == n1) ? v0 : cbuf[j]) : 0.0;
-        if (rank == 0) {
-            if (tid == 0) { bte[k] = alpha; btau[k] = beta; }
-            double *rr = brefl + (size_t)k * Mmax;
-            for (int j = n1 + tid; j < M; j += blockDim.x) rr[j] = (beta != 0.0) ? ((j == n1) ? v0 : cbuf[j]) : 0.0;
-        }
-        if (k % CL == rank && tid == 0) btd[k] = rowp(k)[k];
-        if (n1 % CL == rank) {                          // row k+1 (entries > k+1) to every CTA
-            const double *rr = rowp(n1);
-            for (int j = n1 + 1 + tid; j < M; j += blockDim.x) {
-                const double x = rr[j];
-                for (int r = 0; r < CL; r++) cluster.map_shared_rank(rb, r)[j] = x;
-            }
-        }
-        if (warp == 0) {
-            double part = 0.0;
-            for (int li = (n1 - rank + CL - 1) / CL + lane; li < nown; li += 32) {
-                const int i = li * CL + rank;
-                const double p = beta * fma(-alpha, rowp(i)[n1], uu[li]);
-                const double vi = (beta != 0.0) ? ((i == n1) ? v0 : cbuf[i]) : 0.0;
-                part = fma(p, vi, part);
-                for (int r = 0; r < CL; r++) cluster.map_shared_rank(pb, r)[i] = p;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-            if (lane < CL) cluster.map_shared_rank(pp, lane)[rank] = part;
-        }
+        const bool more = k + 3 < M;
         cluster.sync();
-        // S2 (the partial sums are added in the same order in every thread of every CTA)
-        double pv = (lane < CL) ? pp[lane] : 0.0;
+        if (k % CL == rank && tid == 0) btd[k] = rowp(k)[k];
+        const double *hv = hvb + (size_t)par * Mmax;
+        const double *pb = pbuf + (size_t)par * PS, *rb = rowbuf + (size_t)par * Mmax;
+        // S2: p.v from the CTAs' partials (in the same order in every CTA) by warp 0
+        if (warp == 0) {
+            double pv = (lane < CL) ? pvp[32 * par + lane] : 0.0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
-        const double Kc = 0.5 * beta * pv;
+            for (int o = 8; o > 0; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
+            if (lane == 0) kcs[0] = 0.5 * scb[4 * par] * pv;
+        }
+        __syncthreads();
+        const double Kc = kcs[0];
         const double vk1 = hv[n1];
-        const double wk1 = fma(-Kc, vk1, pb[n1]);
+        const double wk1 = fma(-Kc, vk1, pb[(n1 % CL) * R + n1 / CL]);
         for (int j = n1 + tid; j < M; j += blockDim.x) {
             const double vj = hv[j];
-            const double wj = fma(-Kc, vj, pb[j]);
+            const int jq = j / CL;
+            const double wj = fma(-Kc, vj, pb[(j - jq * CL) * R + jq]);
             wv[j] = wj;
-            nbuf[j] = (j == n1) ? 0.0 : fma(-vk1, wj, fma(-wk1, vj, rb[j]));
+            xcol[j] = (j == n1) ? 0.0 : fma(-vk1, wj, fma(-wk1, vj, rb[j]));
         }
         __syncthreads();
         // S3
         if (warp == 0) {
-            if (k + 3 < M) householder_scalars(nbuf, n1, M, lane, sc);
+            if (more) {
+                next_vector(n1, par ^ 1);
+                named_arrive(1, kTriLaThreads);
+                named_sync(2, kTriLaThreads);
+                partial_pv(n1, par ^ 1);
+            }
         } else {
-            fused(n1, nbuf, true);
+            fused(n1, xcol, hv, true);
+            if (more) {
+                named_sync(1, kTriLaThreads);
+                publish(n1, n1 + 1, par ^ 1);
+            }
         }
-        __syncthreads();
-        double *t = cbuf;
-        cbuf = nbuf;
-        nbuf = t;
     }
+    __syncthreads();
     // trailing 2x2 (or 1x1)
     if (tid == 0) {
         if (M >= 2) {
@@ -308,7 +418,7 @@ k_tridiag(const double *__restrict__ A, int64_t N, const int32_t *__restrict__ p
 size_t tri_smem_bytes(int Mmax, int CL, bool rows_in_smem)
 {
     const size_t R = (size_t)((Mmax + CL - 1) / CL);
-    size_t d = (size_t)8 * Mmax + R + 64 + 16;
+    size_t d = (size_t)8 * Mmax + 32 + 3 * R + 64 + 16;
     if (rows_in_smem) d += R * (size_t)Mmax;
     return d * sizeof(double);
 }
@@ -1013,6 +1123,68 @@ __device__ __forceinline__ void cp_async8(double *dst, const double *src)
                  : "memory");
 }
 
+// z_j -= bk (v . z_j) v (entries k+1 .. M-1) for a warp's NVW vectors, lanes along the rows; the
+// NVW dot products are summed over the lanes by one transpose-reduce (halving the values held per
+// lane while the lane groups shrink), then broadcast from a lane holding each sum.
+template <int NVW>
+__device__ __forceinline__ void reflect(const double *__restrict__ v, double bk, double *const *z, int k, int M,
+                                        int lane)
+{
+    double a[NVW];
+#pragma unroll
+    for (int j = 0; j < NVW; j++) a[j] = 0.0;
+    for (int i = k + 1 + lane; i < M; i += 32) {
+        const double vi = v[i];
+#pragma unroll
+        for (int j = 0; j < NVW; j++) a[j] = fma(vi, z[j][i], a[j]);
+    }
+    double f[NVW];
+    if constexpr (NVW == 1) {
+        double t = a[0];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        f[0] = bk * t;
+    } else if constexpr (NVW == 2) {
+        // lanes 0-15 end with the sum of vector 0, lanes 16-31 with that of vector 1
+        const bool up = (lane & 16) != 0;
+        double t = (up ? a[1] : a[0]) + __shfl_xor_sync(0xffffffffu, up ? a[0] : a[1], 16);
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        const double fl = bk * t;
+        f[0] = __shfl_sync(0xffffffffu, fl, 0);
+        f[1] = __shfl_sync(0xffffffffu, fl, 16);
+    } else {
+        // lanes end with the sum of vector (lane >> 3) & 3: halve at offsets 16 and 8, then
+        // butterflies over the lower three lane bits
+        double b[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) b[j] = (j < NVW) ? a[j < NVW ? j : 0] : 0.0;
+        {
+            const bool up = (lane & 16) != 0;
+            const double s0 = up ? b[0] : b[2], s1 = up ? b[1] : b[3];
+            const double k0v = up ? b[2] : b[0], k1v = up ? b[3] : b[1];
+            b[0] = k0v + __shfl_xor_sync(0xffffffffu, s0, 16);
+            b[1] = k1v + __shfl_xor_sync(0xffffffffu, s1, 16);
+        }
+        {
+            const bool up = (lane & 8) != 0;
+            const double s0 = up ? b[0] : b[1], k0v = up ? b[1] : b[0];
+            b[0] = k0v + __shfl_xor_sync(0xffffffffu, s0, 8);
+        }
+        b[0] += __shfl_xor_sync(0xffffffffu, b[0], 4);
+        b[0] += __shfl_xor_sync(0xffffffffu, b[0], 2);
+        b[0] += __shfl_xor_sync(0xffffffffu, b[0], 1);
+        const double fl = bk * b[0];
+#pragma unroll
+        for (int j = 0; j < NVW; j++) f[j] = __shfl_sync(0xffffffffu, fl, 8 * j);
+    }
+    for (int i = k + 1 + lane; i < M; i += 32) {
+        const double vi = v[i];
+#pragma unroll
+        for (int j = 0; j < NVW; j++) z[j][i] = fma(-f[j], vi, z[j][i]);
+    }
+}
+
 // Back-transform y = H_0 H_1 ... H_{M-3} z of the selected eigenvectors z of T_b, then the sign
 // rule, zero padding to length N, the shift eps and the step alpha, written straight into X.
 // One-dimensional grid, 32 NW threads: window b owns ceil(m_b / vpc) consecutive CTAs, each taking
@@ -1022,8 +1194,8 @@ __device__ __forceinline__ void cp_async8(double *dst, const double *src)
 // sub-partition (one's dot-reduce-update chain hides behind the other's FMAs) and a
 // sub-partition holds at most three vectors (vpc <= 10). The reflectors pass through shared memory
 // in double-buffered chunks of KC rows (cp.async, shared by the CTA's warps), and the NV dot
-// products of a reflector are summed over the lanes by one transpose-reduce. Unused vector slots
-// hold zeros and are computed but not stored.
+// products of a reflector are summed over the lanes by one transpose-reduce. A warp applies the
+// reflectors to its real vectors only (the FP64 pipe is the bound: unused slots cost nothing).
 template <int NV, int NW>
 __global__ void __launch_bounds__(32 * NW, 1)
 k_backtransform(const int32_t *__restrict__ plan, int32_t nb, int64_t N, int32_t Mmax, int32_t mmax,
@@ -1055,8 +1227,12 @@ k_backtransform(const int32_t *__restrict__ plan, int32_t nb, int64_t N, int32_t
     }
     for (int i = tid; i < M; i += blockDim.x) ts[i] = tau[(size_t)b * Mmax + i];
     double *z[NV];
+    int nvw = 0;                                          // the warp's vectors: slots 0 .. nvw-1
 #pragma unroll
-    for (int j = 0; j < NV; j++) z[j] = zs + (size_t)(warp + NW * j) * Mmax;
+    for (int j = 0; j < NV; j++) {
+        z[j] = zs + (size_t)(warp + NW * j) * Mmax;
+        nvw += (warp + NW * j < nvc) ? 1 : 0;
+    }
     const int nk = M - 2;                                 // reflectors k = M-3 .. 0
     const int nch = nk > 0 ? (nk + kc - 1) / kc : 0;
     auto issue = [&](int c) {
@@ -1086,38 +1262,10 @@ k_backtransform(const int32_t *__restrict__ plan, int32_t nb, int64_t N, int32_t
             const double bk = ts[k];
             if (bk == 0.0) continue;
             const double *v = cb + (size_t)r * Mmax;
-            double a[4] = {0.0, 0.0, 0.0, 0.0};
-            for (int i = k + 1 + lane; i < M; i += 32) {
-                const double vi = v[i];
-#pragma unroll
-                for (int j = 0; j < NV; j++) a[j] = fma(vi, z[j][i], a[j]);
-            }
-            // lanes end with the sum of vector (lane >> 3) & 3: halve at offsets 16 and 8, then
-            // butterflies over the lower three lane bits
-            {
-                const bool up = (lane & 16) != 0;
-                const double s0 = up ? a[0] : a[2], s1 = up ? a[1] : a[3];
-                const double k0v = up ? a[2] : a[0], k1v = up ? a[3] : a[1];
-                a[0] = k0v + __shfl_xor_sync(0xffffffffu, s0, 16);
-                a[1] = k1v + __shfl_xor_sync(0xffffffffu, s1, 16);
-            }
-            {
-                const bool up = (lane & 8) != 0;
-                const double s0 = up ? a[0] : a[1], k0v = up ? a[1] : a[0];
-                a[0] = k0v + __shfl_xor_sync(0xffffffffu, s0, 8);
-            }
-            a[0] += __shfl_xor_sync(0xffffffffu, a[0], 4);
-            a[0] += __shfl_xor_sync(0xffffffffu, a[0], 2);
-            a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
-            const double f = bk * a[0];
-            double fj[NV];
-#pragma unroll
-            for (int j = 0; j < NV; j++) fj[j] = __shfl_sync(0xffffffffu, f, 8 * j);
-            for (int i = k + 1 + lane; i < M; i += 32) {
-                const double vi = v[i];
-#pragma unroll
-                for (int j = 0; j < NV; j++) z[j][i] = fma(-fj[j], vi, z[j][i]);
-            }
+            if (nvw == NV) reflect<NV>(v, bk, z, k, M, lane);
+            else if (NV > 1 && nvw == 1) reflect<1>(v, bk, z, k, M, lane);
+            else if (NV > 2 && nvw == 2) reflect<(NV > 2 ? 2 : 1)>(v, bk, z, k, M, lane);
+            else if (NV > 3 && nvw == 3) reflect<(NV > 3 ? 3 : 1)>(v, bk, z, k, M, lane);
             __syncwarp();
         }
         __syncthreads();                                  // chunk c's buffer is reloaded next
