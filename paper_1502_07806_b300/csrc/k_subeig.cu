@@ -953,6 +953,22 @@ __device__ __forceinline__ double hash_unit(uint32_t a, uint32_t b, uint32_t c)
     return ((double)(z >> 11) * 0x1.0p-53) * 2.0 - 1.0;   // (-1, 1)
 }
 
+// Bits of |x| and their comparison: for doubles of one sign the IEEE order is the integer order of
+// the bit patterns, so pivot tests need no FP64 instruction (each costs a sub-partition's FP64
+// pipe ~64 cycles on B300, the pace of a lane's whole dependent chain here).
+__device__ __forceinline__ unsigned long long abs_bits(double x)
+{
+    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// Largest |z_i| exponent field of a lane's vector (element i at z[i * zst]), by integer max.
+__device__ __forceinline__ int max_exponent(const double *z, int zst, int M)
+{
+    unsigned long long m = 0ull;
+    for (int i = 0; i < M; i++) m = max(m, abs_bits(z[i * zst]));
+    return (int)(m >> 52);
+}
+
 // Grid (ceil(mmax / L), nb), L threads (L = 32, fewer for windows whose vectors would not fit in
 // shared memory): lane t computes the unit eigenvector of T_b for the selected eigenvalue t by two
 // inverse-iteration solves with a pivoted tridiagonal LU of T - lambda I (reciprocal pivots clamped
@@ -963,6 +979,11 @@ __device__ __forceinline__ double hash_unit(uint32_t a, uint32_t b, uint32_t c)
 // coalesced), and only read by the solves; the vector z, which every sweep reads and rewrites,
 // lives in shared memory (element i of lane t at i * L + t), so no load of z waits behind an L2
 // round trip of the store before it.
+// A lane's time is its count of FP64 instructions (~64 cycles each on its sub-partition), so: the
+// first solve's forward elimination runs inside the factorisation, pivot tests compare bit
+// patterns, a step computes only the taken branch, every lane starts from one random vector of the
+// window (cluster members after the first from their own), and the vector is normalised once,
+// after the second solve, with power-of-two rescaling by integer exponent tests guarding the range.
 __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int32_t Mmax,
                                int32_t mmax, const double *__restrict__ td,
                                const double *__restrict__ te, const double *__restrict__ sel_val,
@@ -977,6 +998,7 @@ __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int
     double *z = zsm + threadIdx.x;                          // element i at z[i * zst]
     double *d = zsm + (size_t)zst * Mmax;                   // the window's T, shared by the lanes
     double *e = d + Mmax;
+    double *rv = e + Mmax;                                  // the window's start vector
     __shared__ double tn_part[32];
     {
         const double *gd = td + (size_t)b * Mmax, *ge = te + (size_t)b * Mmax;
@@ -985,6 +1007,7 @@ __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int
             const double di = gd[i], ei = ge[i], em = (i > 0) ? ge[i - 1] : 0.0;
             d[i] = di;
             e[i] = ei;
+            rv[i] = hash_unit(b, 0x5EED, i);
             part = fmax(part, fabs(di) + fabs(em) + (i + 1 < M ? fabs(ei) : 0.0));
         }
         tn_part[threadIdx.x] = part;
@@ -1003,57 +1026,80 @@ __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int
     double *__restrict__ u2 = work + 2 * stride * Mmax + me;
     double *__restrict__ lm = work + 3 * stride * Mmax + me; // multipliers, sign bit = row swap
     const double pert = DBL_EPSILON * fmax(tnorm, DBL_MIN);
+    const unsigned long long pert_bits = abs_bits(pert);
+    // pivot clamped to |pivot| >= pert with its sign kept, by bit operations
+    auto clamp_pivot = [&](double piv) {
+        const unsigned long long pb = (unsigned long long)__double_as_longlong(piv);
+        return ((pb & 0x7FFFFFFFFFFFFFFFull) >= pert_bits) ? piv
+               : __longlong_as_double((long long)((pb & 0x8000000000000000ull) | pert_bits));
+    };
+    // z *= 2^-s when the largest exponent is far from 1 (keeps |z|^2 sums inside the FP64 range)
+    auto rescale = [&]() {
+        const int ex = max_exponent(z, zst, M) - 1023;
+        if (ex > 400 || (ex < -400 && ex > -1023)) {
+            const double f = ldexp(1.0, -ex);
+            for (int i = 0; i < M; i++) z[i * zst] *= f;
+        }
+    };
     int last = t;
     while (last + 1 < mb && lam[last + 1] - lam[last] < gaptol) last++;
     for (int j = t; j <= last; j++) {
         const double x = lam[j];
-        // pivoted LU of T - x I: rows (p, q, r) = entries at columns (i, i+1, i+2). The row-swap
-        // flag is kept in the lowest mantissa bit of the stored multiplier (a 1-ulp change).
-        double p = d[0] - x, q = (M > 1) ? e[0] : 0.0, r = 0.0;
+        // start vector: the window's, or a cluster member's own
+        if (j == t) {
+            for (int i = 0; i < M; i++) z[i * zst] = rv[i];
+        } else {
+            for (int i = 0; i < M; i++) z[i * zst] = hash_unit(b, j, i);
+        }
+        // pivoted LU of T - x I with the first solve's forward elimination: rows (p, q) = entries
+        // at columns (i, i+1) of the pivot candidate, zi its right-hand side. The row-swap flag is
+        // kept in the lowest mantissa bit of the stored multiplier (a 1-ulp change).
+        double p = d[0] - x, q = (M > 1) ? e[0] : 0.0, zi = z[0];
 #pragma unroll 4
         for (int i = 0; i + 1 < M; i++) {
             const double ei = e[i], an = d[i + 1] - x, en = (i + 2 < M) ? e[i + 1] : 0.0;
-            const bool swp = !(fabs(p) >= fabs(ei));
-            const double piv = swp ? ei : p;
-            const double pc = fabs(piv) >= pert ? piv : (piv < 0.0 ? -pert : pert);
-            const double rp = fast_rcp(pc);
-            const double l = swp ? p * rp : ((p != 0.0) ? ei * rp : 0.0);
+            const double zn = z[(i + 1) * zst];
+            const bool swp = abs_bits(p) < abs_bits(ei);
+            const double rp = fast_rcp(clamp_pivot(swp ? ei : p));
+            const double l = (swp ? p : ei) * rp;
             u0[i * stride] = rp;
             u1[i * stride] = swp ? an : q;
-            u2[i * stride] = swp ? en : r;
+            u2[i * stride] = swp ? en : 0.0;
             const long long lb = __double_as_longlong(l);
             lm[i * stride] = __longlong_as_double(swp ? (lb | 1ll) : (lb & ~1ll));
-            const double np = swp ? fma(-l, an, q) : fma(-l, q, an);
-            const double nq = swp ? fma(-l, en, r) : fma(-l, r, en);
-            p = np; q = nq; r = 0.0;
+            const double np = fma(-l, swp ? an : q, swp ? q : an);
+            q = swp ? -l * en : en;
+            p = np;
+            z[i * zst] = swp ? zn : zi;
+            zi = fma(-l, swp ? zn : zi, swp ? zi : zn);
         }
-        u0[(size_t)(M - 1) * stride] = fast_rcp(fabs(p) >= pert ? p : (p < 0.0 ? -pert : pert));
+        u0[(size_t)(M - 1) * stride] = fast_rcp(clamp_pivot(p));
         u1[(size_t)(M - 1) * stride] = 0.0;      // read (times zero) by the back substitution
         u2[(size_t)(M - 1) * stride] = 0.0;
-        for (int i = 0; i < M; i++) z[i * zst] = hash_unit(b, j, i);
+        z[(size_t)(M - 1) * zst] = zi;
         for (int it = 0; it < 2; it++) {
-            // forward: replay the row operations on the right-hand side; the multipliers of a
-            // block of PB rows are loaded together (one L2 round trip per block)
-            double zi = z[0];
-            for (int i0 = 0; i0 + 1 < M; i0 += PB) {
-                double lr[PB];
+            if (it > 0) {
+                // forward: replay the row operations on the right-hand side; the multipliers of a
+                // block of PB rows are loaded together (one L2 round trip per block)
+                double zf = z[0];
+                for (int i0 = 0; i0 + 1 < M; i0 += PB) {
+                    double lr[PB];
 #pragma unroll
-                for (int q2 = 0; q2 < PB; q2++) lr[q2] = (i0 + q2 + 1 < M) ? lm[(size_t)(i0 + q2) * stride] : 0.0;
+                    for (int q2 = 0; q2 < PB; q2++) lr[q2] = (i0 + q2 + 1 < M) ? lm[(size_t)(i0 + q2) * stride] : 0.0;
 #pragma unroll
-                for (int q2 = 0; q2 < PB; q2++) {
-                    const int i = i0 + q2;
-                    if (i + 1 < M) {
-                        const double lraw = lr[q2];
-                        const bool swp = (__double_as_longlong(lraw) & 1ll) != 0;
-                        const double l = lraw;       // the flag bit perturbs l by at most 1 ulp
-                        const double zn = z[(i + 1) * zst];
-                        const double ts = fma(-l, zn, zi), tn = fma(-l, zi, zn);   // both, no divergence
-                        z[i * zst] = swp ? zn : zi;
-                        zi = swp ? ts : tn;
+                    for (int q2 = 0; q2 < PB; q2++) {
+                        const int i = i0 + q2;
+                        if (i + 1 < M) {
+                            const double lraw = lr[q2];
+                            const bool swp = (__double_as_longlong(lraw) & 1ll) != 0;
+                            const double zn = z[(i + 1) * zst];
+                            z[i * zst] = swp ? zn : zf;
+                            zf = fma(-lraw, swp ? zn : zf, swp ? zf : zn);   // flag bit: <= 1 ulp of l
+                        }
                     }
                 }
+                z[(size_t)(M - 1) * zst] = zf;
             }
-            z[(size_t)(M - 1) * zst] = zi;
             // back substitution with the three upper diagonals, factors loaded a block at a time
             double z1 = 0.0, z2 = 0.0;
             for (int i0 = M - 1; i0 >= 0; i0 -= PB) {
@@ -1078,6 +1124,9 @@ __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int
                     }
                 }
             }
+            rescale();
+            const bool member = j > t;
+            if (!member && it == 0) continue;            // one normalisation, after the second solve
             // orthogonalise against earlier cluster members, then normalise
             for (int c = t; c < j; c++) {
                 const double *zc = sel_vec + ((size_t)b * mmax + c) * Mmax;
@@ -1085,31 +1134,22 @@ __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int
                 for (int i = 0; i < M; i++) dot = fma(zc[i], z[i * zst], dot);
                 for (int i = 0; i < M; i++) z[i * zst] = fma(-dot, zc[i], z[i * zst]);
             }
+            if (member) rescale();
             // four independent chains: a dependent FP64 instruction waits ~64 cycles on B300
-            double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+            double n0 = 0.0, n1 = 0.0, n2 = 0.0, n3 = 0.0;
             int i4 = 0;
             for (; i4 + 3 < M; i4 += 4) {
-                m0 = fmax(m0, fabs(z[i4 * zst]));
-                m1 = fmax(m1, fabs(z[(i4 + 1) * zst]));
-                m2 = fmax(m2, fabs(z[(i4 + 2) * zst]));
-                m3 = fmax(m3, fabs(z[(i4 + 3) * zst]));
+                const double v0 = z[i4 * zst], v1 = z[(i4 + 1) * zst];
+                const double v2 = z[(i4 + 2) * zst], v3 = z[(i4 + 3) * zst];
+                n0 = fma(v0, v0, n0); n1 = fma(v1, v1, n1); n2 = fma(v2, v2, n2); n3 = fma(v3, v3, n3);
             }
-            for (; i4 < M; i4++) m0 = fmax(m0, fabs(z[i4 * zst]));
-            const double mx = fmax(fmax(m0, m1), fmax(m2, m3));
-            if (mx == 0.0 || !isfinite(mx)) {
+            for (; i4 < M; i4++) { const double v = z[i4 * zst]; n0 = fma(v, v, n0); }
+            const double nn = (n0 + n1) + (n2 + n3);
+            if (!(nn > 0.0) || !(nn < INFINITY)) {
                 for (int i = 0; i < M; i++) z[i * zst] = hash_unit(b, j + 7919, i + it);
                 continue;
             }
-            const double imx = fast_rcp(mx);
-            double n0 = 0.0, n1 = 0.0, n2 = 0.0, n3 = 0.0;
-            for (i4 = 0; i4 + 3 < M; i4 += 4) {
-                const double v0 = z[i4 * zst] * imx, v1 = z[(i4 + 1) * zst] * imx;
-                const double v2 = z[(i4 + 2) * zst] * imx, v3 = z[(i4 + 3) * zst] * imx;
-                z[i4 * zst] = v0; z[(i4 + 1) * zst] = v1; z[(i4 + 2) * zst] = v2; z[(i4 + 3) * zst] = v3;
-                n0 = fma(v0, v0, n0); n1 = fma(v1, v1, n1); n2 = fma(v2, v2, n2); n3 = fma(v3, v3, n3);
-            }
-            for (; i4 < M; i4++) { const double v = z[i4 * zst] * imx; z[i4 * zst] = v; n0 = fma(v, v, n0); }
-            const double inr = rsqrt((n0 + n1) + (n2 + n3));
+            const double inr = rsqrt(nn);
             for (int i = 0; i < M; i++) z[i * zst] *= inr;
         }
         double *out = sel_vec + ((size_t)b * mmax + j) * Mmax;
@@ -1473,9 +1513,9 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
     // 3. inverse iteration
     {
         int lanes = tpb;
-        while (lanes > 1 && (size_t)(lanes + 2) * Mmax * sizeof(double) > kInvSmemCap) lanes >>= 1;
+        while (lanes > 1 && (size_t)(lanes + 3) * Mmax * sizeof(double) > kInvSmemCap) lanes >>= 1;
         dim3 grid((unsigned)((mmax + lanes - 1) / lanes), (unsigned)nb);
-        k_inverse_iter<<<grid, lanes, (size_t)(lanes + 2) * Mmax * sizeof(double), st>>>(w.plan, nb, Mmax, mmax, w.td,
+        k_inverse_iter<<<grid, lanes, (size_t)(lanes + 3) * Mmax * sizeof(double), st>>>(w.plan, nb, Mmax, mmax, w.td,
                                                                                        w.te, w.sel_val, w.sel_vec,
                                                                                        w.iiwork);
         g_launches++;
