@@ -809,31 +809,33 @@ __device__ __forceinline__ double newton_step(const double *d, const double *e2,
 }
 
 // The selected eigenvalues of T_b, the one at ascending position (k0 - s + t) for slice vector t.
-// Grid (ceil(mmax / 8), nb), 256 threads (8 warps), 8 eigenvalues per CTA (so that the FP32
-// multisection, the bulk of the instructions, spreads over every SM):
+// Grid (ceil(mmax / EPC), nb), 32 EPC threads (EPC warps, 8 <= EPC <= 32), EPC eigenvalues per CTA;
+// the launch takes the smallest EPC that gives every CTA its own SM (the FP64 phase of step 3 is
+// one warp's dependent chain, and two such warps on one sub-partition share its FP64 pipe):
 //   1. T is scaled by the power of two that brings its Gershgorin span into [1/2, 1) (exact).
 //   2. Warp w brackets eigenvalue w of the CTA by FP32 multisection: the 32 lanes count the
 //      eigenvalues below 32 interior points of the bracket (33 subintervals), and the bracket
 //      becomes the subinterval where the count passes the position; five rounds reach 8 FP32 ulps
 //      of the span (a bisection needs twenty counts one after another).
-//   3. Warp 0, one eigenvalue per lane (8 lanes): three FP64 Newton steps on det(T - xI) from the bracket's
-//      midpoint (quadratic convergence while |x - lambda| is far below the gap), then two FP64
-//      Sturm counts at x -/+ tol (one pass) certify the position to within tol = 4 ulp |x| + 2 ulp
-//      of the span. A lane that fails falls back to FP64 bisection (on the widened FP32 bracket if
+//   3. Warp 0, one eigenvalue per lane (EPC lanes): up to three FP64 Newton steps on det(T - xI)
+//      from the bracket's midpoint (quadratic convergence while |x - lambda| is far below the gap;
+//      the warp stops once every lane's correction is below tol), then two FP64 Sturm counts at
+//      x -/+ tol (one pass) certify the position to within tol = 4 ulp |x| + 2 ulp of the span.
+//      A lane that fails falls back to FP64 bisection (on the widened FP32 bracket if
 //      its ends check out, else on the Gershgorin interval).
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(1024)
 k_bisect(const int32_t *__restrict__ plan, int32_t nb, int32_t Mmax, int32_t mmax,
          const double *__restrict__ td, const double *__restrict__ te, double *__restrict__ sel_val)
 {
     const int b = blockIdx.y;
     const int k0 = plan[b], mb = plan[nb + b], s = plan[2 * nb + b], M = plan[3 * nb + b];
-    constexpr int EPC = 8;                                // eigenvalues per CTA
+    const int EPC = blockDim.x >> 5;                      // eigenvalues per CTA
     if (blockIdx.x * EPC >= mb) return;                   // whole CTA
     extern __shared__ double smd[];
     double *d = smd, *e2 = smd + Mmax;
     float *df = reinterpret_cast<float *>(smd + 2 * Mmax), *e2f = df + Mmax;
     __shared__ double s_lo, s_hi, s_sc, s_isc;
-    __shared__ float brlo[EPC], brhi[EPC];
+    __shared__ float brlo[32], brhi[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double *bd = td + (size_t)b * Mmax, *be = te + (size_t)b * Mmax;
     if (warp == 0) {
@@ -904,10 +906,13 @@ k_bisect(const int32_t *__restrict__ plan, int32_t nb, int32_t Mmax, int32_t mma
     const double widen = 32.0 * FLT_EPSILON * sspan;
     const double blo = fmax(s_lo, (double)flo - widen), bhi = fmin(s_hi, (double)fhi + widen);
     double x = 0.5 * ((double)flo + (double)fhi);
+    const unsigned act = __activemask();
     for (int it = 0; it < 3; it++) {
         const double xn = x + newton_step(d, e2, M, x);
-        if (!(xn >= blo && xn <= bhi)) break;        // left the bracket: keep the last iterate
-        x = xn;
+        const bool inside = xn >= blo && xn <= bhi;  // else keep the last iterate
+        const bool settled = !inside || fabs(xn - x) <= 4.0 * DBL_EPSILON * fabs(xn) + 2.0 * satol;
+        if (inside) x = xn;
+        if (__all_sync(act, settled)) break;
     }
     const double tol = 4.0 * DBL_EPSILON * fabs(x) + 2.0 * satol;
     const double xs[2] = {x - tol, x + tol};
@@ -1504,8 +1509,13 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
     if (h->timing && (e0 = cudaEventRecord(h->sub_ev[0], st)) != cudaSuccess) return e0;
     // 2. eigenvalues
     {
-        dim3 grid((unsigned)((mmax + 7) / 8), (unsigned)nb);
-        k_bisect<<<grid, 256, (size_t)3 * Mmax * sizeof(double), st>>>(w.plan, nb, Mmax, mmax, w.td, w.te, w.sel_val); g_launches++;
+        // eigenvalues per CTA: the fewest (>= 8) that keep the CTAs within one per SM
+        int epc = 8;
+        while (epc < 32 && (int64_t)nb * ((mmax + epc - 1) / epc) > (int64_t)sm_count()) epc++;
+        dim3 grid((unsigned)((mmax + epc - 1) / epc), (unsigned)nb);
+        k_bisect<<<grid, 32 * epc, (size_t)3 * Mmax * sizeof(double), st>>>(w.plan, nb, Mmax, mmax, w.td, w.te,
+                                                                           w.sel_val);
+        g_launches++;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
