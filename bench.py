@@ -46,11 +46,12 @@ DTYPES = {"fp64": "f64", "bf16": "bf16x3-split, f32 accumulate, f64 epilogue",
 # capture of the current kernel build on this workload, keyed by (kernel, precision); absent
 # when the kernel changed since the capture. Captures and commands: profiles/.
 TRAFFIC = {
-    # the window reduction is the same kernel and launch in every form (one cluster barrier per
-    # step; profiles/window_eigensolve_diamond1280_full.md)
-    ("k_tridiag", "bf16"): 5901312, ("k_tridiag", "tf32"): 5901312, ("k_tridiag", "fp64"): 5901312,
+    # dram__bytes_read.sum + dram__bytes_write.sum of one launch, N = 1280 workload
+    # (profiles/dram_traffic_diamond1280.md). The window reduction is the same kernel and launch in
+    # every form.
+    ("k_tridiag", "bf16"): 5948928, ("k_tridiag", "tf32"): 5948928, ("k_tridiag", "fp64"): 5948928,
     # Eq. 11 split products, mean over the K = 3 iterations' six launches
-    ("k_gemm_tc", "bf16"): (12921088 + 5 * 46013184) // 6,
+    ("k_gemm_tc", "bf16"): 40503893,
 }
 
 

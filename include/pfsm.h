@@ -276,7 +276,8 @@ typedef struct {
                              4 Rayleigh quotients, residuals and outputs, 5 backward;
                              inside 1: 6 tridiagonalisation, 7 bisection, 8 inverse iteration,
                              9 back-transformation + start vectors; inside 3: 10 overlap,
-                             11 Cholesky; the triangular solve is phase 3 minus 10 and 11 */
+                             11 Cholesky or, in the mixed forms, the preconditioner; the
+                             triangular solve is phase 3 minus 10 and 11 */
     int32_t gemm_tile_n;  /* output-tile width (64, 96 or 128 columns) of the handle's split
                              products, measured at pfsm_init; 0 for PFSM_FP64 handles */
     int32_t path;         /* last pfsm_solve: 0 the method, 1 full diagonalization by the
@@ -284,6 +285,12 @@ typedef struct {
     double guard_value;   /* its guard value g (0 when not measured) */
     int32_t fs_steps;     /* Eq. 11 steps taken by the last solve */
     double fs_residual;   /* with fs_adaptive: the last max_k residual measured (else 0) */
+    int32_t gs_precond;   /* mixed forms, last pfsm_solve by the method: Gram-Schmidt
+                             preconditioner 2 second-order series, 3 the series followed by the
+                             FP32 Cholesky factorisation (series residual too large; eager solves
+                             only); 0 otherwise */
+    double gs_precond_residual; /* max |M S M^T - I| after the series, measured by eager solves
+                                   (0 for solves captured into a CUDA graph) */
 } pfsm_profile_t;
 
 /* Enables (enable != 0) or disables CUDA-event phase timing on h. Timing adds one event record

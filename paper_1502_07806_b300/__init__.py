@@ -49,7 +49,8 @@ class Profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int32), ("timed", ctypes.c_int32),
                 ("phase_ms", ctypes.c_float * 12), ("gemm_tile_n", ctypes.c_int32),
                 ("path", ctypes.c_int32), ("guard_value", ctypes.c_double),
-                ("fs_steps", ctypes.c_int32), ("fs_residual", ctypes.c_double)]
+                ("fs_steps", ctypes.c_int32), ("fs_residual", ctypes.c_double),
+                ("gs_precond", ctypes.c_int32), ("gs_precond_residual", ctypes.c_double)]
 
 
 _lib = None
@@ -190,7 +191,8 @@ class Handle:
         pr = Profile()
         _check(load_library().pfsm_get_profile(self._h, ctypes.byref(pr)), "pfsm_get_profile")
         out = {"launches": pr.launches, "gemm_tile_n": pr.gemm_tile_n, "path": pr.path,
-               "guard_value": pr.guard_value, "fs_steps": pr.fs_steps, "fs_residual": pr.fs_residual}
+               "guard_value": pr.guard_value, "fs_steps": pr.fs_steps, "fs_residual": pr.fs_residual,
+               "gs_precond": pr.gs_precond, "gs_precond_residual": pr.gs_precond_residual}
         if pr.timed:
             out.update({name: float(pr.phase_ms[i]) for i, name in enumerate(PHASES)})
             out.update({name: float(pr.phase_ms[6 + i]) for i, name in enumerate(SUB_PHASES)})

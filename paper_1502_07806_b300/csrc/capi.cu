@@ -252,7 +252,8 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
         return fail(PFSM_ERR_CUDA, "pfsm_init: %s", cudaGetErrorString(e));
     }
     h->prm.slice_sizes = nullptr;   // the host array is not kept
-    if (prm.fs_adaptive && cudaMalloc((void **)&h->fs_rmax, sizeof(unsigned long long)) != cudaSuccess) {
+    if ((prm.fs_adaptive || prm.precision != PFSM_FP64) &&
+        cudaMalloc((void **)&h->fs_rmax, sizeof(unsigned long long)) != cudaSuccess) {
         free_ws(h);
         delete h;
         cudaGetLastError();
@@ -676,6 +677,9 @@ int pfsm_get_profile(pfsm_handle_t h, pfsm_profile_t *out)
     out->guard_value = h->last_guard;
     out->fs_steps = h->last_path ? 0 : h->last_fs_steps;
     out->fs_residual = h->last_path ? 0.0 : h->last_fs_resid;
+    const bool gs_mixed = !h->last_path && h->prm.precision != PFSM_FP64;
+    out->gs_precond = gs_mixed ? h->gs_precond : 0;
+    out->gs_precond_residual = gs_mixed ? h->gs_precond_resid : 0.0;
     if (!h->timing || !h->solved) return PFSM_OK;
     PFSM_CUDA(cudaStreamSynchronize(h->last_stream));
     auto span = [&](int a, int b, float *dst) -> cudaError_t { return cudaEventElapsedTime(dst, h->ev[a], h->ev[b]); };

@@ -58,38 +58,80 @@ static_assert(KCHUNK % KB == 0 && (double)KCHUNK * OZ_LEVELS * 4096.0 < 16777216
 // zero_diag: digits of the off-diagonal part (entry (r, r) taken as 0, its value stored in d[r]).
 // Input in FP64 or FP32 (an FP32 operand's digits are exact: 24 bits fit in the 48-bit grid of its
 // row unless the entry is below 2^-24 of the row's largest).
+// B300 retires one FP64 warp instruction per 16 cycles per SM, and the integer pipe two per cycle,
+// so each entry costs one FP64 instruction: the row maximum compares bit patterns (IEEE order of
+// magnitudes is the integer order of non-negative bit patterns), q = rn(x 2^(QBITS - e)) comes
+// from one FMA with 1.5 2^52 (the sum's low significand bits are q, rounded to nearest even: the
+// same integer as the product and conversion), and with q' = q + sum_i 64 128^i the balanced
+// digits are the 7-bit fields of q' minus 64 (bit-field extracts on 32-bit halves), whose BF16
+// values come from FP32 adds.
+__device__ __forceinline__ unsigned long long oz_bits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+// BF16 bits of (field - 64) for a 7-bit field: 1.5 2^23 + field is exact, and so is the BF16 of
+// the (<= 7 significant bits) difference
+__device__ __forceinline__ unsigned short oz_digit_bf16(uint32_t field)
+{
+    const float f = __int_as_float(0x4B400000 | (int)field) - 12582976.0f;   // 1.5 2^23 + 64
+    return (unsigned short)(__float_as_uint(f) >> 16);
+}
+
 template <typename T>
 __global__ void k_oz_split(const T *__restrict__ src, int64_t rows, int64_t cols, int64_t ld,
                            __nv_bfloat16 *__restrict__ dst, int64_t sl_ld, int64_t sstride,
                            int32_t *__restrict__ exps, int zero_diag, double *__restrict__ d)
 {
+    static_assert(OZ_SLICES == 7 && oz::BETA == 7, "digit fields are laid out for seven 7-bit digits");
     const int lane = threadIdx.x & 31;
     const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (r >= rows) return;
     const T *x = src + r * ld;
-    auto val = [&](int64_t c) { return (zero_diag && c == r) ? 0.0 : (double)x[c]; };
+    auto val = [&](int64_t c) -> double { return (zero_diag && c == r) ? 0.0 : (double)x[c]; };
     if (zero_diag && lane == 0 && d) d[r] = (double)x[r];
-    double mx = 0.0;
-    for (int64_t c = lane; c < cols; c += 32) mx = fmax(mx, fabs(val(c)));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    int e = 0;
-    if (mx > 0.0) frexp(mx, &e);             // mx = f 2^e, f in [0.5, 1): |x| 2^-e < 1
-    if (lane == 0) exps[r] = e;
-    const double sc = ldexp(1.0, oz::QBITS - e);
-    __nv_bfloat16 *out = dst + r * sl_ld;
+    unsigned long long mb = 0ull;
     for (int64_t c = lane; c < cols; c += 32) {
-        long long q = __double2ll_rn(val(c) * sc);    // |q| <= 2^48
-        int dig[OZ_SLICES];
+        unsigned long long b;
+        if (sizeof(T) == 8) b = oz_bits((double)x[c]) & 0x7FFFFFFFFFFFFFFFull;
+        else b = (unsigned long long)(__float_as_uint((float)x[c]) & 0x7FFFFFFFu);
+        mb = max(mb, (zero_diag && c == r) ? 0ull : b);
+    }
 #pragma unroll
-        for (int s = OZ_SLICES - 1; s >= 1; s--) {    // balanced base-128 digits, low to high
-            const int d = (int)(((q + 64) & 127) - 64);
-            dig[s] = d;
-            q = (q - d) >> oz::BETA;
-        }
-        dig[0] = (int)q;
-#pragma unroll
-        for (int s = 0; s < OZ_SLICES; s++) out[s * sstride + c] = __int2bfloat16_rn(dig[s]);
+    for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    // e with max|x| = f 2^e, f in [1/2, 1) (frexp); e = 0 for a zero row
+    int e = 0;
+    if (sizeof(T) == 8) {
+        const int ex = (int)(mb >> 52);
+        if (ex > 0) e = ex - 1022;
+        else if (mb != 0ull) e = -1010 - __clzll((long long)mb);                // subnormal
+    } else {
+        const int ex = (int)(mb >> 23);
+        if (ex > 0) e = ex - 126;
+        else if (mb != 0ull) e = -117 - __clz((int)mb);
+    }
+    if (lane == 0) exps[r] = e;
+    // one digit row: q from t = x 2^(QBITS - e) + 1.5 2^52 (|x 2^(QBITS - e)| < 2^QBITS <= 2^51, so
+    // the sum is rounded to an integer held in the low significand bits)
+    constexpr double kMagic = 6755399441055744.0;                     // 1.5 2^52
+    constexpr long long kBias = 64ll * (((1ll << 42) - 1) / 127);     // sum_{i < 6} 64 128^i
+    unsigned short *out = reinterpret_cast<unsigned short *>(dst + r * sl_ld);
+    auto emit = [&](int64_t c, double t) {
+        const long long q = (long long)(oz_bits(t) - oz_bits(kMagic)) + kBias;
+        const uint32_t lo = (uint32_t)q, hi = (uint32_t)((unsigned long long)q >> 32);
+        unsigned short *o = out + c;
+        o[6 * sstride] = oz_digit_bf16(lo & 127u);
+        o[5 * sstride] = oz_digit_bf16((lo >> 7) & 127u);
+        o[4 * sstride] = oz_digit_bf16((lo >> 14) & 127u);
+        o[3 * sstride] = oz_digit_bf16((lo >> 21) & 127u);
+        o[2 * sstride] = oz_digit_bf16(__funnelshift_r(lo, hi, 28) & 127u);
+        o[1 * sstride] = oz_digit_bf16((hi >> 3) & 127u);
+        o[0] = oz_digit_bf16((uint32_t)(((int)hi >> 10) + 64));      // top digit q' >> 42, |n_0| <= 64
+    };
+    const int sh = oz::QBITS - e;
+    if (sh <= 1000) {                                                 // 2^sh is a double: one FMA
+        const double sc = ldexp(1.0, sh);
+        for (int64_t c = lane; c < cols; c += 32) emit(c, fma(val(c), sc, kMagic));
+    } else {                                                          // rows below 2^-952: two factors
+        const double sc1 = ldexp(1.0, sh / 2), sc2 = ldexp(1.0, sh - sh / 2);
+        for (int64_t c = lane; c < cols; c += 32) emit(c, fma(val(c) * sc1, sc2, kMagic));
     }
 }
 
@@ -296,8 +338,8 @@ cudaError_t configure_oz_kernels()
 cudaError_t launch_oz_split(const double *src, int64_t rows, int64_t cols, int64_t ld, const SliceBuf &dst,
                             int32_t *exps, cudaStream_t st, bool zero_diag, double *d)
 {
-    const unsigned blocks = (unsigned)((rows + 7) / 8);
-    k_oz_split<double><<<blocks, 256, 0, st>>>(src, rows, cols, ld, reinterpret_cast<__nv_bfloat16 *>(dst.ptr),
+    const unsigned blocks = (unsigned)((rows + 1) / 2);   // two rows per CTA: small CTAs balance the SMs
+    k_oz_split<double><<<blocks, 64, 0, st>>>(src, rows, cols, ld, reinterpret_cast<__nv_bfloat16 *>(dst.ptr),
                                                dst.ld, dst.ld * dst.rows, exps, zero_diag ? 1 : 0, d);
     g_launches++;
     return cudaGetLastError();
@@ -306,8 +348,8 @@ cudaError_t launch_oz_split(const double *src, int64_t rows, int64_t cols, int64
 cudaError_t launch_oz_split_f32(const float *src, int64_t rows, int64_t cols, int64_t ld, const SliceBuf &dst,
                                 int32_t *exps, cudaStream_t st)
 {
-    const unsigned blocks = (unsigned)((rows + 7) / 8);
-    k_oz_split<float><<<blocks, 256, 0, st>>>(src, rows, cols, ld, reinterpret_cast<__nv_bfloat16 *>(dst.ptr),
+    const unsigned blocks = (unsigned)((rows + 1) / 2);
+    k_oz_split<float><<<blocks, 64, 0, st>>>(src, rows, cols, ld, reinterpret_cast<__nv_bfloat16 *>(dst.ptr),
                                               dst.ld, dst.ld * dst.rows, exps, 0, nullptr);
     g_launches++;
     return cudaGetLastError();

@@ -8,8 +8,19 @@
 // work to dense products on the tensor cores:
 //
 //   1. S~ = X X^T to about 2^-35 (digit product truncated to five levels).
-//   2. FP32 blocked Cholesky S~ = L~ L~^T and, in the same sweep, M = L~^-1 (lower triangular,
-//      positive diagonal). M is a preconditioner only: nothing below needs it to be accurate.
+//   2. A lower-triangular M with positive diagonal and M S M^T close to I. M is a preconditioner
+//      only: nothing below needs it to be accurate. Two forms:
+//      a. the second-order series of L^-1 for S~ = I + E: with G = Phi(E) the first
+//         order of chol(I + E) = I + G_exact, G_exact = Phi(E - G_exact G_exact^T), so
+//         L^-1 = I - G + G^2 + Phi(G G^T) + O(E^3), and since G + G^T = E,
+//         G^2 + Phi(G G^T) = Phi(G E) + diag(G_ii^2) / 2: M = I - G + Phi(G E) + diag(G_ii^2) / 2,
+//         one split product. The vectors entering Gram-Schmidt are nearly orthonormal (window
+//         eigenvectors after Eq. 11; |E| ~ 1e-2), so M S M^T - I is O(|E|^3) ~ 1e-7, what the FP32
+//         factorisation below reaches. An eager solve measures it after step 4 (one 8-byte
+//         read-back); above kSeriesMaxResidual the FP32 factorisation of V1 V1^T follows and V1 is
+//         preconditioned again. A solve captured into a CUDA graph cannot read back: it relies on
+//         the checks of step 5, which report a residual too large for the fixed point.
+//      b. FP32 blocked Cholesky S~ = L~ L~^T and, in the same sweep, M = L~^-1 (the fallback of a).
 //   3. V1 = M X with the FP64-accurate digit product. For ANY lower-triangular M with positive
 //      diagonal, chol(M S M^T) = M L, so Gram-Schmidt of V1 equals Gram-Schmidt of X.
 //   4. E = V1 V1^T - I (digit product). |E| is of the order of cond(S) times the FP32 unit.
@@ -22,6 +33,7 @@
 // contraction) or a last sweep that still moves F by more than 1e-13 reports PFSM_ERR_NOT_SPD:
 // the overlap matrix is then too ill-conditioned for this scheme (the FP64 form handles it).
 #include <cfloat>
+#include <cstring>
 
 #include "pfsm_internal.cuh"
 
@@ -33,6 +45,10 @@ constexpr int GB = 64;                  // FP32 Cholesky block
 constexpr int LDT = GB + 4;             // shared-memory row: 16-byte aligned for float4 reads
 constexpr int kFixedPointSweeps = 2;    // sweeps after F0 = Phi(E): error ~ (2|E|)^3 |E|
 constexpr size_t kStepSmem = 2 * GB * LDT * sizeof(float) + 6 * GB * sizeof(float);
+// largest max|V1 V1^T - I| after the series preconditioner handed to the fixed point of step 5:
+// emulated with exact products on perturbed N = 256 vectors, its second sweep still moved F by
+// 6e-17 at 1.3e-6 and 4e-14 at 1.2e-5 (the check below is 1e-13), and by 2e-11 at 8e-5
+constexpr double kSeriesMaxResidual = 4e-6;
 
 __device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ float el(const float4 &v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
@@ -287,21 +303,77 @@ k_chol32_update(float *__restrict__ L, float *__restrict__ R, const float *__res
 // F = Phi(S2 - I - G): strict lower part, half the diagonal, zero above (G may be null). With
 // last set, a change of F by more than 1e-13 in this sweep means the fixed point has not settled
 // to FP64 accuracy (the overlap matrix is too ill-conditioned for the FP32 preconditioner).
-__global__ void k_phi(const double *__restrict__ S2, const double *__restrict__ G, double *__restrict__ F,
-                      int64_t N, int last, int32_t *status)
+// check: |S2 - I - G| >= 1/4 (no contraction) reports PFSM_ERR_NOT_SPD. emax (may be null): the
+// largest |S2 - I - G| of the lower triangle, as FP64 bits (the integer order of non-negative
+// doubles is their order), by one atomicMax per CTA.
+__global__ void __launch_bounds__(256)
+k_phi(const double *__restrict__ S2, const double *__restrict__ G, double *__restrict__ F, int64_t N, int last,
+      int check, unsigned long long *__restrict__ emax, int32_t *status)
 {
     const int64_t r = blockIdx.y;
+    unsigned long long m = 0ull;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = r * N + c;
         double v = 0.0;
         if (c <= r) {
             v = S2[o] - (c == r ? 1.0 : 0.0);
             if (G) v -= G[o];
-            if (!(fabs(v) < 0.25)) set_status(status, PFSM_ERR_NOT_SPD);   // no contraction (or NaN)
+            m = max(m, (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull);
+            if (check && !(fabs(v) < 0.25)) set_status(status, PFSM_ERR_NOT_SPD);   // no contraction (or NaN)
             if (c == r) v *= 0.5;
             if (last && !(fabs(v - F[o]) <= 1e-13)) set_status(status, PFSM_ERR_NOT_SPD);
         }
         F[o] = v;
+    }
+    if (emax) {
+        __shared__ unsigned long long wm[8];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < (int)(blockDim.x >> 5); w++) m = max(m, wm[w]);
+            if (m) atomicMax(emax, m);
+        }
+    }
+}
+
+// Series preconditioner, first part: from the overlap S~ (lower triangle stored; the tiles above
+// the diagonal are stale) write E = S~ - I in full (symmetric) and G = Phi(E) (zero above the
+// diagonal). 32 x 32 tiles; a tile above the diagonal reads the mirrored tile through shared
+// memory, so every global access is row-contiguous.
+__global__ void __launch_bounds__(256)
+k_series_inputs(const double *__restrict__ S, double *__restrict__ E, double *__restrict__ G, int64_t N)
+{
+    __shared__ double t[32][33];
+    const int bi = blockIdx.y, bj = blockIdx.x;                  // output tile (rows bi, cols bj)
+    const int bs = max(bi, bj), bt = min(bi, bj);                // source tile in the lower part
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // 32 x 8 threads
+    for (int q = ty; q < 32; q += 8) {
+        const int64_t r = (int64_t)bs * 32 + q, c = (int64_t)bt * 32 + tx;
+        t[q][tx] = (r < N && c < N && c <= r) ? S[r * N + c] : 0.0;
+    }
+    __syncthreads();
+    for (int q = ty; q < 32; q += 8) {
+        const int64_t r = (int64_t)bi * 32 + q, c = (int64_t)bj * 32 + tx;
+        if (r >= N || c >= N) continue;
+        // element (r, c) of the symmetric matrix, from the stored lower triangle
+        const double v = (c <= r) ? t[q][tx] : t[tx][q];
+        const double e = v - (r == c ? 1.0 : 0.0);
+        E[r * N + c] = e;
+        G[r * N + c] = (c < r) ? e : (c == r ? 0.5 * e : 0.0);
+    }
+}
+
+// Series preconditioner, second part, in place over G: M = I - G + Phi(C) + diag(G_ii^2) / 2 with
+// C = G E (lower triangle read); zero above the diagonal stays zero.
+__global__ void k_series_assemble(double *__restrict__ GM, const double *__restrict__ C, int64_t N)
+{
+    const int64_t r = blockIdx.y;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= r; c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = r * N + c;
+        const double g = GM[o];
+        GM[o] = (c < r) ? C[o] - g : fma(0.5 * g, g, fma(0.5, C[o], 1.0 - g));
     }
 }
 
@@ -336,6 +408,62 @@ static cudaError_t fp32_cholesky_inverse(pfsm_handle_s *h, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// M = I - G + Phi(G E) + diag(G_ii^2) / 2 from the overlap in w.S (lower triangle), into w.F
+// (zero above the diagonal); w.Z and w.Y are scratch.
+static cudaError_t series_preconditioner(pfsm_handle_s *h, cudaStream_t st)
+{
+    Workspace &w = h->ws;
+    const int64_t N = h->N;
+    const int64_t ld = padded_ld(N);
+    const int ns = slices_for(h->prm.precision), kind = slice_kind(h->prm.precision);
+    SliceBuf sG{w.slY, N, ld, ns, kind}, sE{w.slZ, N, ld, ns, kind};
+    cudaError_t e;
+    const unsigned nt = (unsigned)((N + 31) / 32);
+    k_series_inputs<<<dim3(nt, nt), 256, 0, st>>>(w.S, w.Z, w.F, N); g_launches++;
+    if ((e = launch_split(w.F, N, N, N, sG, false, nullptr, st)) != cudaSuccess) return e;
+    if ((e = launch_split(w.Z, N, N, N, sE, false, nullptr, st)) != cudaSuccess) return e;
+    TcParams g{};                                        // C = G E^T = G E (lower triangle) -> Y
+    g.rows = (int)N; g.cols = (int)N; g.ldo = N; g.status = w.status;
+    g.epi = TC_EPI_STORE; g.out = w.Y; g.lower_only = 1;
+    if ((e = launch_gemm_tc(sG, sE, g, nullptr, st)) != cudaSuccess) return e;
+    const int64_t bx = (N + 255) / 256;
+    k_series_assemble<<<dim3((unsigned)(bx < 8 ? bx : 8), (unsigned)N), 256, 0, st>>>(w.F, w.Y, N); g_launches++;
+    return cudaGetLastError();
+}
+
+// V1 = M X -> w.Y, the digits of M (rows; FP64 in w.F or FP32 in w.M32) against those of X^T
+// (rows = basis index, K = vector index); M is lower triangular.
+static cudaError_t precondition(pfsm_handle_s *h, const double *M64, const double *X, double *out, cudaStream_t st)
+{
+    Workspace &w = h->ws;
+    const int64_t N = h->N;
+    const int64_t ld = padded_ld(N);
+    SliceBuf dP{w.ozP, N, ld, OZ_SLICES, 0}, dQ{w.ozQ, N, ld, OZ_SLICES, 0};
+    cudaError_t e;
+    if ((e = launch_transpose(X, w.W, N, st)) != cudaSuccess) return e;
+    if (M64) e = launch_oz_split(M64, N, N, N, dP, w.ozeP, st);
+    else e = launch_oz_split_f32(w.M32, N, N, N, dP, w.ozeP, st);
+    if (e != cudaSuccess) return e;
+    if ((e = launch_oz_split(w.W, N, N, N, dQ, w.ozeQ, st)) != cudaSuccess) return e;
+    OzParams o{};
+    o.rows = (int)N; o.cols = (int)N; o.C = out; o.ldc = N; o.p_lower = 1; o.status = w.status;
+    return launch_gemm_oz(dP, w.ozeP, dQ, w.ozeQ, o, st);
+}
+
+// S2 = V1 V1^T (lower, all digit levels) -> w.S
+static cudaError_t overlap_full(pfsm_handle_s *h, const double *V1, cudaStream_t st)
+{
+    Workspace &w = h->ws;
+    const int64_t N = h->N;
+    const int64_t ld = padded_ld(N);
+    SliceBuf dP{w.ozP, N, ld, OZ_SLICES, 0};
+    cudaError_t e;
+    if ((e = launch_oz_split(V1, N, N, N, dP, w.ozeP, st)) != cudaSuccess) return e;
+    OzParams o{};
+    o.rows = (int)N; o.cols = (int)N; o.C = w.S; o.ldc = N; o.lower_only = 1; o.status = w.status;
+    return launch_gemm_oz(dP, w.ozeP, dP, w.ozeP, o, st);
+}
+
 cudaError_t launch_gram_schmidt_mixed(pfsm_handle_s *h, cudaStream_t st)
 {
     Workspace &w = h->ws;
@@ -354,32 +482,52 @@ cudaError_t launch_gram_schmidt_mixed(pfsm_handle_s *h, cudaStream_t st)
     if ((e = launch_gemm_oz(dP, w.ozeP, dP, w.ozeP, o, st)) != cudaSuccess) return e;
     if ((e = launch_copy_diag(w.S, N, w.sdiag, st)) != cudaSuccess) return e;
     if (h->timing && (e = cudaEventRecord(h->gs_ev[0], st)) != cudaSuccess) return e;
-    // 2. M = L~^-1 in FP32
-    if ((e = fp32_cholesky_inverse(h, st)) != cudaSuccess) return e;
+    // 2.-3. the series preconditioner M and V1 = M X -> Y
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(st, &cap)) != cudaSuccess) return e;
+    const bool readback = cap == cudaStreamCaptureStatusNone && h->fs_rmax;
+    h->gs_precond = 2;
+    h->gs_precond_resid = 0.0;
+    if ((e = series_preconditioner(h, st)) != cudaSuccess) return e;
     if (h->timing && (e = cudaEventRecord(h->gs_ev[1], st)) != cudaSuccess) return e;
-    // 3. V1 = M X -> Y: digits of M (rows) and of X^T (rows = basis index, K = vector index)
-    if ((e = launch_transpose(w.X, w.W, N, st)) != cudaSuccess) return e;
-    if ((e = launch_oz_split_f32(w.M32, N, N, N, dP, w.ozeP, st)) != cudaSuccess) return e;
-    if ((e = launch_oz_split(w.W, N, N, N, dQ, w.ozeQ, st)) != cudaSuccess) return e;
-    o = OzParams{};
-    o.rows = (int)N; o.cols = (int)N; o.C = w.Y; o.ldc = N; o.p_lower = 1; o.status = w.status;
-    if ((e = launch_gemm_oz(dP, w.ozeP, dQ, w.ozeQ, o, st)) != cudaSuccess) return e;
+    if ((e = precondition(h, w.F, w.X, w.Y, st)) != cudaSuccess) return e;
     // 4. S2 = V1 V1^T (lower) -> S
-    if ((e = launch_oz_split(w.Y, N, N, N, dP, w.ozeP, st)) != cudaSuccess) return e;
-    o = OzParams{};
-    o.rows = (int)N; o.cols = (int)N; o.C = w.S; o.ldc = N; o.lower_only = 1; o.status = w.status;
-    if ((e = launch_gemm_oz(dP, w.ozeP, dP, w.ozeP, o, st)) != cudaSuccess) return e;
+    if ((e = overlap_full(h, w.Y, st)) != cudaSuccess) return e;
     // 5. F = Phi(E - F F^T), E = S2 - I
     const int64_t bx = (N + 255) / 256;
     const dim3 egrid((unsigned)(bx < 8 ? bx : 8), (unsigned)N);
-    k_phi<<<egrid, 256, 0, st>>>(w.S, nullptr, w.F, N, 0, w.status); g_launches++;
+    if (readback) {
+        // measure max|E| (one read-back); too large for the fixed point: FP32 factorisation of S2,
+        // V1 <- M' V1 (still Gram-Schmidt of X), S2 again
+        if ((e = cudaMemsetAsync(h->fs_rmax, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+        k_phi<<<egrid, 256, 0, st>>>(w.S, nullptr, w.F, N, 0, 0, h->fs_rmax, w.status); g_launches++;
+        unsigned long long eb = 0ull;
+        if ((e = cudaMemcpyAsync(&eb, h->fs_rmax, sizeof(eb), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+        double emax;
+        std::memcpy(&emax, &eb, sizeof(emax));
+        h->gs_precond_resid = emax;
+        if (!(emax <= kSeriesMaxResidual)) {
+            h->gs_precond = 3;
+            if ((e = launch_copy_diag(w.S, N, w.sdiag, st)) != cudaSuccess) return e;
+            if ((e = fp32_cholesky_inverse(h, st)) != cudaSuccess) return e;
+            if ((e = precondition(h, nullptr, w.Y, w.X, st)) != cudaSuccess) return e;
+            double *tmp = w.X;                           // V1 in Y, X free again
+            w.X = w.Y;
+            w.Y = tmp;
+            if ((e = overlap_full(h, w.Y, st)) != cudaSuccess) return e;
+            k_phi<<<egrid, 256, 0, st>>>(w.S, nullptr, w.F, N, 0, 1, nullptr, w.status); g_launches++;
+        }
+    } else {
+        k_phi<<<egrid, 256, 0, st>>>(w.S, nullptr, w.F, N, 0, 1, nullptr, w.status); g_launches++;
+    }
     for (int it = 0; it < kFixedPointSweeps; it++) {
         if ((e = launch_split(w.F, N, N, N, sZ, false, nullptr, st)) != cudaSuccess) return e;
         TcParams g{};
         g.rows = (int)N; g.cols = (int)N; g.ldo = N; g.status = w.status;
         g.epi = TC_EPI_STORE; g.out = w.Z; g.lower_only = 1;
         if ((e = launch_gemm_tc(sZ, sZ, g, nullptr, st)) != cudaSuccess) return e;
-        k_phi<<<egrid, 256, 0, st>>>(w.S, w.Z, w.F, N, it + 1 == kFixedPointSweeps, w.status); g_launches++;
+        k_phi<<<egrid, 256, 0, st>>>(w.S, w.Z, w.F, N, it + 1 == kFixedPointSweeps, 1, nullptr, w.status); g_launches++;
     }
     // 6. W^T = V1^T - V1^T F^T (split product, in place on V1^T), then V = V1 - F W (digits)
     if ((e = launch_transpose(w.Y, w.W, N, st)) != cudaSuccess) return e;

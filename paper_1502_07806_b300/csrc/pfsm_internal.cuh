@@ -85,7 +85,11 @@ struct pfsm_handle_s {
     unsigned long long *guard_buf = nullptr;
     int32_t last_fs_steps = 0;     // Eq. 11 steps of the last solve
     double last_fs_resid = 0.0;    // adaptive variant: its last measured residual
-    unsigned long long *fs_rmax = nullptr;   // adaptive variant: residual read-back (device)
+    unsigned long long *fs_rmax = nullptr;   // 8-byte read-back word (device): the adaptive
+                                             // variant's residual, the mixed Gram-Schmidt's
+                                             // preconditioner residual
+    int32_t gs_precond = 0;        // mixed Gram-Schmidt preconditioner of the last solve (profile)
+    double gs_precond_resid = 0.0; // its measured residual
     bool rows_in_smem = true;
     bool tri_blocked = false;      // mixed forms: blocked reduction (k_tridiag_panel)
     int32_t tri_rpw = 8;           // its rows-per-warp register capacity (8 or 24)

@@ -151,20 +151,78 @@ __device__ __forceinline__ float to_tf32(float x)
     return __uint_as_float(r);
 }
 
-// Writes the `ns` KIND slices of v at slice-matrix element offset `o`.
+// FP64 bit pattern u rounded to 53 - DROP significant bits by integer operations: ties to even
+// (RNA false) or away from zero (RNA true). A carry out of the significand moves into the
+// exponent, which is the correctly rounded result; +-0 stay +-0.
+template <int DROP, bool RNA>
+__device__ __forceinline__ unsigned long long round_sig(unsigned long long u)
+{
+    const unsigned long long half = RNA ? (1ull << (DROP - 1)) : ((1ull << (DROP - 1)) - 1ull + ((u >> DROP) & 1ull));
+    return (u + half) & ~((1ull << DROP) - 1ull);
+}
+
+// The slices of v by the conversion instructions (FP64 pipe), for values whose slices leave the
+// normal FP32 exponent range. Not inlined, so that the compiler cannot predicate it into the
+// common path.
 template <int KIND>
-__device__ __forceinline__ void store_slices(void *base, int64_t sstride, int64_t o, int ns, double v)
+__device__ __noinline__ void store_slices_exact(void *base, int64_t sstride, int64_t o, int ns, double v)
 {
     double rem = v;
     for (int s = 0; s < ns; s++) {
         if (KIND == 0) {
-            __nv_bfloat16 b = __double2bfloat16(rem);
+            const __nv_bfloat16 b = __double2bfloat16(rem);
             reinterpret_cast<__nv_bfloat16 *>(base)[s * sstride + o] = b;
             rem -= (double)__bfloat162float(b);
         } else {
-            float t = to_tf32((float)rem);
+            const float t = to_tf32((float)rem);
             reinterpret_cast<float *>(base)[s * sstride + o] = t;
             rem -= (double)t;
+        }
+    }
+}
+
+// Writes the `ns` KIND slices of v at slice-matrix element offset `o`: slice s is the BF16 (KIND 0)
+// or TF32 (KIND 1, via FP32) rounding of v minus the slices before it. B300 retires one FP64 warp
+// instruction per 16 cycles per SM, and the conversions to and from FP64 run on that pipe, so
+// the roundings are done on the FP64 bit pattern with integer operations (the same round-to-
+// nearest-even, and for TF32 the FP32 rounding followed by ties-away, as the conversion
+// instructions) and only the exact residual v - slice is an FP64 instruction. An element with a
+// slice outside the normal FP32 exponent range takes store_slices_exact instead.
+template <int KIND>
+__device__ __forceinline__ void store_slices(void *base, int64_t sstride, int64_t o, int ns, double v)
+{
+    constexpr int MAXS = 3;
+    uint32_t bits[MAXS] = {0u, 0u, 0u};
+    bool ok = true;
+    double rem = v;
+#pragma unroll
+    for (int s = 0; s < MAXS; s++) {
+        if (s < ns) {
+            const unsigned long long u = (unsigned long long)__double_as_longlong(rem);
+            const int ex = (int)((u >> 52) & 0x7FF);
+            ok = ok && ((ex >= 897 && ex <= 1149) || (u << 1) == 0ull);   // 2^-126 <= |rem| < 2^127, or 0
+            const unsigned long long r = (KIND == 0) ? round_sig<45, false>(u)           // 8 bits
+                                                     : round_sig<42, true>(round_sig<29, false>(u));   // FP32, 11 bits
+            const unsigned int re = (unsigned int)((r >> 52) & 0x7FF);
+            if (KIND == 0) {
+                const unsigned int sg = (unsigned int)(r >> 48) & 0x8000u;
+                bits[s] = re ? (sg | ((re - 896u) << 7) | (unsigned int)((r >> 45) & 0x7F)) : sg;
+            } else {
+                const unsigned int sg = (unsigned int)(r >> 32) & 0x80000000u;
+                bits[s] = re ? (sg | ((re - 896u) << 23) | (unsigned int)((r >> 29) & 0x7FFFFF)) : sg;
+            }
+            if (s + 1 < ns) rem -= __longlong_as_double((long long)r);
+        }
+    }
+    if (!ok) {
+        store_slices_exact<KIND>(base, sstride, o, ns, v);
+        return;
+    }
+#pragma unroll
+    for (int s = 0; s < MAXS; s++) {
+        if (s < ns) {
+            if (KIND == 0) reinterpret_cast<unsigned short *>(base)[s * sstride + o] = (unsigned short)bits[s];
+            else reinterpret_cast<uint32_t *>(base)[s * sstride + o] = bits[s];
         }
     }
 }
