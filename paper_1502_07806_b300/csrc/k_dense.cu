@@ -200,35 +200,35 @@ cudaError_t launch_gram_schmidt_f64(pfsm_handle_s *h, cudaStream_t st)
 
 // ---- Rayleigh quotients and residual norms (warp-shuffle row reductions) --------------------
 
-__device__ __forceinline__ double cta_sum(double v, double *red)
+// One warp per vector k: lambda_k = v_k . w_k, r_k = ||w_k - lambda_k v_k|| with W = V A (rows).
+// A warp's shuffle tree is five FP64 adds; a CTA-wide sum per vector (shared memory, a barrier and
+// a second tree) issued about as many FP64 instructions as the dot products themselves.
+__global__ void __launch_bounds__(256)
+k_rayleigh_rows(const double *__restrict__ V, const double *__restrict__ W, int64_t N, double *__restrict__ lam,
+                double *__restrict__ res)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double t = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += red[i];
-    return t;
-}
-
-// One CTA per vector k: lambda_k = v_k . w_k, r_k = ||w_k - lambda_k v_k|| with W = V A (rows).
-__global__ void k_rayleigh_rows(const double *__restrict__ V, const double *__restrict__ W,
-                                int64_t N, double *__restrict__ lam, double *__restrict__ res)
-{
-    __shared__ double red[32];
-    const int64_t k = blockIdx.x;
+    const int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (k >= N) return;
     const double *v = V + k * N, *w = W + k * N;
-    double acc = 0.0;
-    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) acc += v[i] * w[i];
-    const double l = cta_sum(acc, red);
-    double r2 = 0.0;
-    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
-        double t = w[i] - l * v[i];
-        r2 += t * t;
+    double a0 = 0.0, a1 = 0.0;
+    int64_t i = lane;
+    for (; i + 32 < N; i += 64) { a0 = fma(v[i], w[i], a0); a1 = fma(v[i + 32], w[i + 32], a1); }
+    if (i < N) a0 = fma(v[i], w[i], a0);
+    double l = a0 + a1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    double r0 = 0.0, r1 = 0.0;
+    for (i = lane; i + 32 < N; i += 64) {
+        const double t0 = fma(-l, v[i], w[i]), t1 = fma(-l, v[i + 32], w[i + 32]);
+        r0 = fma(t0, t0, r0);
+        r1 = fma(t1, t1, r1);
     }
-    r2 = cta_sum(r2, red);
-    if (threadIdx.x == 0) { lam[k] = l; res[k] = sqrt(r2); }
+    if (i < N) { const double t0 = fma(-l, v[i], w[i]); r0 = fma(t0, t0, r0); }
+    double r2 = r0 + r1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+    if (lane == 0) { lam[k] = l; res[k] = sqrt(r2); }
 }
 
 __global__ void k_transpose(const double *__restrict__ in, double *__restrict__ out, int64_t N)
@@ -280,7 +280,7 @@ cudaError_t launch_rayleigh_f64(pfsm_handle_s *h, const double *A, double *eigva
         g.P = w.X; g.ldp = N; g.Q = A; g.ldq = N; g.C = w.W; g.ldc = N;
         if ((e = launch_gemm_f64(g, EPI_STORE, Q_KMAJOR, st)) != cudaSuccess) return e;
     }
-    k_rayleigh_rows<<<(unsigned)N, 256, 0, st>>>(w.X, w.W, N, w.lam, w.res); g_launches++;
+    k_rayleigh_rows<<<(unsigned)((N + 7) / 8), 256, 0, st>>>(w.X, w.W, N, w.lam, w.res); g_launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_transpose(w.X, w.Vrm, N, st)) != cudaSuccess) return e;
     if (eigvals_out != w.lam &&
