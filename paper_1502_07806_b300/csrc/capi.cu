@@ -50,7 +50,8 @@ void free_ws(pfsm_handle_s *h)
     void *ptrs[] = {w.plan, w.tile_krange, w.status, w.gersh, w.X, w.Xfs, w.Y, w.S, w.W, w.Vrm,
                     w.sdiag, w.eps, w.alpha, w.lam, w.res, w.refl, w.tau, w.td, w.te,
                     w.sel_val, w.sel_vec, w.iiwork, w.slices, w.slE, w.slX, w.slY, w.slZ,
-                    w.Z, w.dA, w.Linv, w.ozP, w.ozQ, w.ozeP, w.ozeQ, w.L32, w.R32, w.M32, w.F, w.VW, w.WV, w.tdP, w.tdQ, w.tdeP, w.tdeQ};
+                    w.Z, w.dA, w.Linv, w.ozP, w.ozQ, w.ozeP, w.ozeQ, w.L32, w.R32, w.M32, w.F, w.VW, w.WV, w.tdP, w.tdQ, w.tdeP, w.tdeQ,
+                    w.btG, w.btRT, w.btW1, w.btW2T, w.btY, w.btDA, w.btDB, w.btEA, w.btEB, w.btExt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     w = Workspace{};
@@ -225,6 +226,25 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
             w.tdP = t1; w.tdQ = t2;
             PFSM_ALLOC(w.tdeP, nbM);
             PFSM_ALLOC(w.tdeQ, nbM);
+        }
+        if (backtransform_wy_fits(h->Mmax)) {
+            const size_t Mx = (size_t)h->Mmax, mx = (size_t)h->mmax, nbx = (size_t)nblocks;
+            const size_t ldk = (size_t)padded_ld(h->Mmax);
+            PFSM_ALLOC(w.btG, nbx * Mx * Mx);
+            PFSM_ALLOC(w.btRT, nbx * Mx * Mx);
+            PFSM_ALLOC(w.btW1, nbx * Mx * mx);
+            PFSM_ALLOC(w.btW2T, nbx * mx * Mx);
+            PFSM_ALLOC(w.btY, nbx * mx * Mx);
+            uint8_t *da = nullptr, *db = nullptr;
+            PFSM_ALLOC(da, (size_t)OZ_SLICES * nbx * Mx * ldk * 2);
+            PFSM_ALLOC(db, (size_t)OZ_SLICES * nbx * mx * ldk * 2);
+            if (e == cudaSuccess) e = cudaMemset(da, 0, (size_t)OZ_SLICES * nbx * Mx * ldk * 2);   // padding
+            if (e == cudaSuccess) e = cudaMemset(db, 0, (size_t)OZ_SLICES * nbx * mx * ldk * 2);
+            w.btDA = da; w.btDB = db;
+            PFSM_ALLOC(w.btEA, nbx * Mx);
+            PFSM_ALLOC(w.btEB, nbx * mx);
+            PFSM_ALLOC(w.btExt, 3 * nbx);
+            if (e == cudaSuccess) e = configure_bt_wy_kernels();
         }
         if (e == cudaSuccess) e = configure_gs_mixed_kernels();
         if (e == cudaSuccess) e = configure_tc_kernels();

@@ -1,0 +1,313 @@
+// Back-transformation of the selected window eigenvectors in the mixed forms (Section II: the
+// eigenvectors y of each submatrix start Eq. 11), y = H_0 H_1 ... H_{M-3} z for the m selected
+// eigenvectors z of the window's tridiagonal T, followed by the start-vector rules (sign, zero
+// padding to length N, shift eps and step alpha).
+//
+// With H_k = I - beta_k v_k v_k^T, the product of the reflectors has the compact-WY form
+//   H_0 ... H_{M-3} = I - V S^-1 V^T,   S = diag(1 / beta_k) + striu(V^T V)
+// (V = [v_0 ... v_{M-3}], striu the strictly upper triangle; Schreiber and Van Loan 1989, in the
+// form of Joffrain, Low, Quintana-Orti, van de Geijn and Van Zee 2006: for two reflectors
+// S^-1 = [[b0, -b0 b1 v0.v1], [0, b1]] reproduces I - b0 v0 v0^T - b1 v1 v1^T + b0 b1 (v0.v1) v0 v1^T).
+// A reflector with beta = 0 (column already reduced) has v = 0 and contributes nothing. The
+// reflectors' lengths differ (|v_k|^2 = 2 / beta_k), and the digit products are accurate relative
+// to the largest entry of each operand row, so every v_k is first scaled by a power of two
+// 2^p_k ~ 1 / |v_k| and beta_k by 2^-2p_k: the same H_k exactly, with |2^p_k v_k| in [1/2, 2]. So
+//   Y = Z - V W2,  S W2 = W1,  W1 = V^T Z
+// and three of the four stages are dense products, done by the FP64-accurate digit product on the
+// tensor cores, batched over the windows: G = V^T V (lower triangle), W1 = V^T Z and
+// Y = Z - W2^T V^T (rows = vectors). Only the triangular solve with S stays on the FP64 pipe:
+// M^2 m / 2 FMAs per window against the 2 M^2 m of applying the reflectors one by one.
+//   k_bt_prep    zero the unused entries of the reflector rows (j <= k, j >= M, k >= M - 2) and
+//                of the eigenvector rows, write V^T, and the per-window extents
+//   k_bt_trsm    W2 = S^-1 W1 by columns of the right-hand side: one CTA per (window, chunk of
+//                columns) holds its columns of the residual in shared memory and runs the
+//                right-looking back substitution (rows of G staged by cp.async)
+//   k_bt_finish  the start-vector rules of the FP64 back-transformation, one warp per vector
+#include "pfsm_internal.cuh"
+
+namespace pfsm {
+
+namespace {
+
+constexpr int kTrsmThreads = 256;
+constexpr int kTrsmMaxCols = 64;                 // columns per CTA (W2 staging)
+constexpr size_t kTrsmSmemCap = 160 * 1024;      // shared memory of one k_bt_trsm CTA
+constexpr size_t kTrsmGBytes = 80 * 1024;        // of it, the double-buffered rows of G
+
+__device__ __forceinline__ void cp_async8(double *dst, const double *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+
+// rows of G per staged chunk: the largest power of two <= 8 whose double buffer fits kTrsmGBytes
+int trsm_chunk_rows(int Mmax)
+{
+    int kc = 8;
+    while (kc > 1 && (size_t)2 * kc * Mmax * sizeof(double) > kTrsmGBytes) kc >>= 1;
+    return kc;
+}
+
+size_t trsm_smem(int Mmax, int cw, int kc) { return ((size_t)Mmax * cw + (size_t)2 * kc * Mmax) * sizeof(double); }
+
+// p_k of the exact power-of-two rescaling of reflector k: 2^(2 p_k) within a factor 4 of
+// beta_k / 2 = 1 / |v_k|^2 (0 for beta = 0, whose v is zero)
+__device__ __forceinline__ int wy_scale_exp(double beta)
+{
+    return beta > 0.0 ? ilogb(0.5 * beta) / 2 : 0;
+}
+
+}  // namespace
+
+bool backtransform_wy_fits(int Mmax)
+{
+    return Mmax >= 1 && trsm_smem(Mmax, 1, trsm_chunk_rows(Mmax)) <= kTrsmSmemCap;
+}
+
+// Grid (ceil(Mmax / 32), ceil(Mmax / 32), nb), 256 threads: tile (ti, tj) of window b's reflector
+// rows (row k = v_k, entries j; valid for k < M - 2, k < j < M) is scaled by 2^p_k and cleaned in
+// place and written transposed into RT; the tiles with ti * 32 < mmax also clean the eigenvector
+// rows t (entries j >= M and rows t >= m_b set to zero). ext = {M - 2, m_b, M} per window.
+__global__ void __launch_bounds__(256)
+k_bt_prep(const int32_t *__restrict__ plan, int nb, int Mmax, int mmax, const double *__restrict__ tau,
+          double *__restrict__ refl, double *__restrict__ RT, double *__restrict__ sel_vec,
+          int32_t *__restrict__ ext)
+{
+    __shared__ double t[32][33];
+    const int b = blockIdx.z;
+    const int mb = plan[nb + b], M = plan[3 * nb + b];
+    const int nk = M > 2 ? M - 2 : 0;
+    const int ti = blockIdx.y, tj = blockIdx.x;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    double *br = refl + (size_t)b * Mmax * Mmax;
+    for (int q = ty; q < 32; q += 8) {
+        const int k = ti * 32 + q, j = tj * 32 + tx;
+        double v = 0.0;
+        if (k < Mmax && j < Mmax) {
+            v = (k < nk && j > k && j < M) ? ldexp(br[(size_t)k * Mmax + j], wy_scale_exp(tau[(size_t)b * Mmax + k])) : 0.0;
+            br[(size_t)k * Mmax + j] = v;
+        }
+        t[q][tx] = v;
+    }
+    __syncthreads();
+    double *bt = RT + (size_t)b * Mmax * Mmax;
+    for (int q = ty; q < 32; q += 8) {
+        const int j = tj * 32 + q, k = ti * 32 + tx;            // RT[j][k] = refl[k][j]
+        if (j < Mmax && k < Mmax) bt[(size_t)j * Mmax + k] = t[tx][q];
+    }
+    if (ti * 32 < mmax) {
+        double *bs = sel_vec + (size_t)b * mmax * Mmax;
+        for (int q = ty; q < 32; q += 8) {
+            const int tt = ti * 32 + q, j = tj * 32 + tx;
+            if (tt < mmax && j < Mmax && (tt >= mb || j >= M)) bs[(size_t)tt * Mmax + j] = 0.0;
+        }
+    }
+    if (ti == 0 && tj == 0 && threadIdx.x == 0) {
+        ext[b] = nk;
+        ext[nb + b] = mb;
+        ext[2 * nb + b] = M;
+    }
+}
+
+// Grid (ceil(mmax / cw), nb), 256 threads: W2 = S^-1 W1 for the columns t in [c0, c0 + cw) of window
+// b, S = diag(1 / beta) + striu(G) with G = V^T V (its lower triangle read: G[k][l], l < k, is row k).
+// Right-looking back substitution: for k = nk - 1 .. 0, w_k = beta_k R_k, then R_l -= G[k][l] w_k
+// for l < k. Thread (rg, c) owns column c's rows l = rg (mod nrg) of R (shared memory); the owner
+// of row k - 1 computes w_{k-1} right after its update of that row in step k, so a step costs one
+// barrier. Rows of G pass through shared memory in double-buffered chunks of kc rows (cp.async).
+// The reflectors are the scaled ones of k_bt_prep: beta_k 2^-2p_k on the diagonal of S^-1.
+// Writes W2^T (row t, entries k; zero for k >= nk and for t >= m_b).
+__global__ void __launch_bounds__(kTrsmThreads)
+k_bt_trsm(const int32_t *__restrict__ ext, int nb, int Mmax, int mmax, int cw, int kc,
+          const double *__restrict__ G, const double *__restrict__ tau, const double *__restrict__ W1,
+          double *__restrict__ W2T)
+{
+    extern __shared__ double sm_trsm[];
+    double *R = sm_trsm;                                  // [Mmax][cw]
+    double *Gs = R + (size_t)Mmax * cw;                   // [2][kc][Mmax]
+    __shared__ double W2s[2][kTrsmMaxCols];
+    const int b = blockIdx.y;
+    const int nk = ext[b], mb = ext[nb + b];
+    const int c0 = blockIdx.x * cw;
+    const int nc = max(0, min(cw, mb - c0));
+    double *W2Tb = W2T + ((size_t)b * mmax + c0) * Mmax;
+    // zero the parts of this CTA's rows that the solve does not write
+    for (int i = threadIdx.x; i < cw * Mmax; i += blockDim.x) {
+        const int c = i / Mmax, k = i - c * Mmax;
+        if (c0 + c < mmax && (c >= nc || k >= nk)) W2Tb[(size_t)c * Mmax + k] = 0.0;
+    }
+    if (nc == 0 || nk == 0) return;
+    const double *Gb = G + (size_t)b * Mmax * Mmax;
+    const double *tb = tau + (size_t)b * Mmax;
+    const double *W1b = W1 + (size_t)b * Mmax * mmax + c0;
+    for (int i = threadIdx.x; i < nk * nc; i += blockDim.x) {
+        const int k = i / nc, c = i - k * nc;
+        R[(size_t)k * cw + c] = W1b[(size_t)k * mmax + c];
+    }
+    auto scaled_beta = [&](int k) { const double bk = tb[k]; return ldexp(bk, -2 * wy_scale_exp(bk)); };
+    const int nrg = (int)blockDim.x / nc;
+    const int c = (int)threadIdx.x % nc, rg = (int)threadIdx.x / nc;
+    const bool act = rg < nrg;
+    const int nch = (nk + kc - 1) / kc;
+    auto issue = [&](int ch) {                            // rows k = khi, khi - 1, ... of G, entries l < k
+        double *dst = Gs + (size_t)(ch & 1) * kc * Mmax;
+        const int khi = nk - 1 - ch * kc;
+        for (int r = 0; r < kc; r++) {
+            const int k = khi - r;
+            if (k < 0) break;
+            for (int l = threadIdx.x; l < k; l += blockDim.x) cp_async8(dst + (size_t)r * Mmax + l, Gb + (size_t)k * Mmax + l);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    issue(0);
+    __syncthreads();                                      // R loaded
+    if (act && (nk - 1) % nrg == rg) {                    // w of the last row
+        const double wv = scaled_beta(nk - 1) * R[(size_t)(nk - 1) * cw + c];
+        W2s[(nk - 1) & 1][c] = wv;
+        W2Tb[(size_t)c * Mmax + nk - 1] = wv;
+    }
+    for (int ch = 0; ch < nch; ch++) {
+        if (ch + 1 < nch) {
+            issue(ch + 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();                                  // chunk ch of G and the last w visible
+        const double *gch = Gs + (size_t)(ch & 1) * kc * Mmax;
+        const int khi = nk - 1 - ch * kc;
+        for (int r = 0; r < kc; r++) {
+            const int k = khi - r;
+            if (k < 0) break;
+            if (act) {
+                const double wk = W2s[k & 1][c];
+                const double *grow = gch + (size_t)r * Mmax;
+                for (int l = rg; l < k; l += nrg) R[(size_t)l * cw + c] = fma(-grow[l], wk, R[(size_t)l * cw + c]);
+                if (k >= 1 && (k - 1) % nrg == rg) {      // row k - 1 is final: its w
+                    const double wv = scaled_beta(k - 1) * R[(size_t)(k - 1) * cw + c];
+                    W2s[(k - 1) & 1][c] = wv;
+                    W2Tb[(size_t)c * Mmax + k - 1] = wv;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// One warp per selected vector (window b = warp / mmax, vector t): y = row t of Y, then the
+// start-vector rules of the FP64 back-transformation: the home component positive when
+// |y_home| >= 0.1, else the largest component (lowest index on ties); y zero-padded into row
+// k0 + t of X at columns s .. s + M - 1; eps = the window eigenvalue, alpha = min(theta / d^2,
+// 1 - 2^-20) with d the larger distance to the Gershgorin ends.
+__global__ void __launch_bounds__(256)
+k_bt_finish(const int32_t *__restrict__ plan, int nb, int64_t N, int Mmax, int mmax, const double *__restrict__ Y,
+            const double *__restrict__ sel_val, const double *__restrict__ gersh, double alpha_theta,
+            double *__restrict__ X, double *__restrict__ eps, double *__restrict__ alpha)
+{
+    const int gw = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+    const int lane = threadIdx.x & 31;
+    const int b = gw / mmax, t = gw - b * mmax;
+    if (b >= nb) return;
+    const int k0 = plan[b], mb = plan[nb + b], s = plan[2 * nb + b], M = plan[3 * nb + b];
+    if (t >= mb) return;
+    const double *zz = Y + ((size_t)b * mmax + t) * Mmax;
+    const int home = k0 - s + t;
+    double best = -1.0;
+    int arg = M;
+    for (int i = lane; i < M; i += 32) {
+        const double av = fabs(zz[i]);
+        if (av > best) { best = av; arg = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
+        if (ob > best || (ob == best && oa < arg)) { best = ob; arg = oa; }
+    }
+    const double yh = zz[home];
+    const double ref = (fabs(yh) >= 0.1) ? yh : zz[arg];
+    const double flip = (ref < 0.0) ? -1.0 : 1.0;
+    const int64_t kg = k0 + t;
+    double *xr = X + kg * N;
+    for (int64_t jj = lane; jj < N; jj += 32) {
+        const int64_t li = jj - s;
+        xr[jj] = (li >= 0 && li < M) ? flip * zz[li] : 0.0;
+    }
+    if (lane == 0) {
+        const double glo = gersh[2 * N], ghi = gersh[2 * N + 1];
+        const double lam = sel_val[(size_t)b * mmax + t];
+        const double dmax = fmax(ghi - lam, lam - glo);
+        const double av = alpha_theta / (dmax * dmax);
+        const double cap = 1.0 - 0x1.0p-20;
+        eps[kg] = lam;
+        alpha[kg] = (av < cap) ? av : cap;
+    }
+}
+
+cudaError_t launch_backtransform_wy(pfsm_handle_s *h, cudaStream_t st)
+{
+    Workspace &w = h->ws;
+    const int nb = h->nb, Mmax = h->Mmax, mmax = h->mmax;
+    const int64_t ldk = padded_ld(Mmax);
+    const int64_t nbM = (int64_t)nb * Mmax, nbm = (int64_t)nb * mmax;
+    SliceBuf dA{w.btDA, nbM, ldk, OZ_SLICES, 0}, dB{w.btDB, nbm, ldk, OZ_SLICES, 0};
+    int32_t *ext_k = w.btExt, *ext_m = w.btExt + nb, *ext_M = w.btExt + 2 * nb;
+    cudaError_t e;
+    // 1. clean reflector and eigenvector rows, V^T, extents
+    const unsigned nt = (unsigned)((Mmax + 31) / 32);
+    k_bt_prep<<<dim3(nt, nt, (unsigned)nb), 256, 0, st>>>(w.plan, nb, Mmax, mmax, w.tau, w.refl, w.btRT, w.sel_vec,
+                                                           w.btExt);
+    g_launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // 2. digits of V^T's rows (v_k, entries j) and of the eigenvectors (z_t, entries j)
+    if ((e = launch_oz_split(w.refl, nbM, Mmax, Mmax, dA, w.btEA, st)) != cudaSuccess) return e;
+    if ((e = launch_oz_split(w.sel_vec, nbm, Mmax, Mmax, dB, w.btEB, st)) != cudaSuccess) return e;
+    // 3. G = V^T V (lower triangle), per window
+    OzParams o{};
+    o.rows = Mmax; o.cols = Mmax; o.C = w.btG; o.ldc = Mmax; o.lower_only = 1; o.status = w.status;
+    o.zrow = Mmax; o.zc = (int64_t)Mmax * Mmax; o.ext = ext_k;
+    if ((e = launch_gemm_oz(dA, w.btEA, dA, w.btEA, o, st, nb)) != cudaSuccess) return e;
+    // 4. W1 = V^T Z (rows k, columns t), per window
+    o = OzParams{};
+    o.rows = Mmax; o.cols = mmax; o.C = w.btW1; o.ldc = mmax; o.status = w.status;
+    o.zrow = Mmax; o.zrow_q = mmax; o.zc = (int64_t)Mmax * mmax; o.ext = ext_k; o.ext_c = ext_m;
+    if ((e = launch_gemm_oz(dA, w.btEA, dB, w.btEB, o, st, nb)) != cudaSuccess) return e;
+    // 5. W2 = S^-1 W1 -> W2^T: columns per CTA so that the CTAs fill the SMs once, within shared memory
+    {
+        const int kc = trsm_chunk_rows(Mmax);
+        int cw = 1;
+        while (cw < kTrsmMaxCols && (int64_t)nb * ((mmax + cw - 1) / cw) > (int64_t)sm_count()) cw++;
+        while (cw > 1 && trsm_smem(Mmax, cw, kc) > kTrsmSmemCap) cw--;
+        const dim3 grid((unsigned)((mmax + cw - 1) / cw), (unsigned)nb);
+        k_bt_trsm<<<grid, kTrsmThreads, trsm_smem(Mmax, cw, kc), st>>>(w.btExt, nb, Mmax, mmax, cw, kc, w.btG, w.tau,
+                                                                      w.btW1, w.btW2T);
+        g_launches++;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    // 6. digits of W2^T (rows t, entries k) and of V (rows j, entries k)
+    if ((e = launch_oz_split(w.btW2T, nbm, Mmax, Mmax, dB, w.btEB, st)) != cudaSuccess) return e;
+    if ((e = launch_oz_split(w.btRT, nbM, Mmax, Mmax, dA, w.btEA, st)) != cudaSuccess) return e;
+    // 7. Y = Z - W2^T V^T (rows t, entries j), per window
+    if ((e = cudaMemcpyAsync(w.btY, w.sel_vec, (size_t)nbm * Mmax * sizeof(double), cudaMemcpyDeviceToDevice, st)) !=
+        cudaSuccess)
+        return e;
+    o = OzParams{};
+    o.rows = mmax; o.cols = Mmax; o.C = w.btY; o.ldc = Mmax; o.sub = 1; o.status = w.status;
+    o.zrow = mmax; o.zrow_q = Mmax; o.zc = (int64_t)mmax * Mmax; o.ext = ext_m; o.ext_c = ext_M;
+    if ((e = launch_gemm_oz(dB, w.btEB, dA, w.btEA, o, st, nb)) != cudaSuccess) return e;
+    // 8. start vectors
+    {
+        const int64_t warps = nbm;
+        k_bt_finish<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(w.plan, nb, h->N, Mmax, mmax, w.btY, w.sel_val,
+                                                                 w.gersh, h->prm.alpha_theta, w.X, w.eps, w.alpha);
+        g_launches++;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t configure_bt_wy_kernels()
+{
+    return cudaFuncSetAttribute(k_bt_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrsmSmemCap);
+}
+
+}  // namespace pfsm

@@ -144,10 +144,12 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
     using namespace oz;
     const int z = blockIdx.z;
     const int row0 = prm.row_base + blockIdx.y * BM, col0 = prm.row_base + blockIdx.x * BN;
-    const int rows_lim = prm.ext ? prm.ext[z] : prm.rows, cols_lim = prm.ext ? prm.ext[z] : prm.cols;
+    const int rows_lim = prm.ext ? prm.ext[z] : prm.rows;
+    const int cols_lim = prm.ext_c ? prm.ext_c[z] : (prm.ext ? prm.ext[z] : prm.cols);
     if (row0 >= rows_lim || col0 >= cols_lim) return;              // tile outside this window
     if (prm.lower_only && col0 > row0 + BM - 1) return;           // whole tile above the diagonal
-    const int64_t zr = (int64_t)z * prm.zrow;                      // operand row offset
+    const int64_t zr = (int64_t)z * prm.zrow;                      // operand row offsets
+    const int64_t zq = (int64_t)z * (prm.zrow_q ? prm.zrow_q : prm.zrow);
     double *Cz = prm.C + (int64_t)z * prm.zc;
     const int LV = (prm.levels > 0 && prm.levels < OZ_LEVELS) ? prm.levels : OZ_LEVELS;   // levels 0 .. LV-1
     const int NSL = LV;                                            // slices that take part (s, t < LV)
@@ -191,7 +193,7 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapQ) : "memory");
     }
     for (int j = threadIdx.x; j < BN; j += blockDim.x)
-        ecol[j] = (col0 + j < cols_lim) ? prm.eq[zr + col0 + j] : 0;
+        ecol[j] = (col0 + j < cols_lim) ? prm.eq[zq + col0 + j] : 0;
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      ::"r"(smem_u32(tmem_slot)), "r"(TMEM_COLS) : "memory");
@@ -217,7 +219,7 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
                 if (*abort_flag) break;
                 mbar_expect_tx(full_bar(s), stage_bytes);
                 tma_load_3d(stageP(s, 0), &mapP, full_bar(s), kb * KB, (int)(zr + row0), 0);
-                tma_load_3d(stageQ(s, 0), &mapQ, full_bar(s), kb * KB, (int)(zr + col0), 0);
+                tma_load_3d(stageQ(s, 0), &mapQ, full_bar(s), kb * KB, (int)(zq + col0), 0);
                 issued = kb + 1;
             }
             for (int i = (issued > STAGES ? issued - STAGES : 0); i < issued; i++)

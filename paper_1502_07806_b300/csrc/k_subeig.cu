@@ -1533,7 +1533,10 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
         if (e != cudaSuccess) return e;
     }
     if (h->timing && (e0 = cudaEventRecord(h->sub_ev[2], st)) != cudaSuccess) return e0;
-    // 4. back-transform + start vectors
+    // 4. back-transform + start vectors: the mixed forms apply the reflectors in compact-WY form
+    //    with digit products on the tensor cores (k_bt_wy.cu); the FP64 form one by one on the FP64
+    //    pipe
+    if (h->prm.precision != PFSM_FP64 && w.btG) return launch_backtransform_wy(h, st);
     {
         // vectors per CTA: the fewest for which sum_b ceil(m_b / vpc) <= N / vpc + nb CTAs fit
         // one per SM; eight warps of up to two vectors (<= 3 per sub-partition for vpc <= 10) when

@@ -61,6 +61,13 @@ struct Workspace {
     double *VW = nullptr, *WV = nullptr;
     void *tdP = nullptr, *tdQ = nullptr;
     int32_t *tdeP = nullptr, *tdeQ = nullptr;
+    // mixed-form back-transformation in compact-WY form (k_bt_wy.cu), per window: G = V^T V
+    // (Mmax x Mmax, lower), V^T (Mmax x Mmax), W1 = V^T Z (Mmax x mmax), W2^T (mmax x Mmax), Y
+    // (mmax x Mmax); the digit matrices of the Mmax-row and the mmax-row operands and their row
+    // exponents; per-window extents (reflectors, vectors, rows)
+    double *btG = nullptr, *btRT = nullptr, *btW1 = nullptr, *btW2T = nullptr, *btY = nullptr;
+    void *btDA = nullptr, *btDB = nullptr;
+    int32_t *btEA = nullptr, *btEB = nullptr, *btExt = nullptr;
 };
 
 }  // namespace pfsm
@@ -128,6 +135,11 @@ cudaError_t launch_plan(const double *prev, int64_t N, int32_t nb, int32_t halo,
                         double *gersh, int32_t *status, cudaStream_t st);
 
 cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st);
+// mixed forms: y = H_0 ... H_{M-3} z and the start vectors by the compact-WY form (k_bt_wy.cu);
+// false when the solve's shared memory cannot hold a column chunk (the FP64 kernel is used)
+bool backtransform_wy_fits(int Mmax);
+cudaError_t launch_backtransform_wy(pfsm_handle_s *h, cudaStream_t st);
+cudaError_t configure_bt_wy_kernels();
 cudaError_t configure_kernels(pfsm_handle_s *h);   // shared-memory / cluster attributes
 
 enum Epi : int { EPI_STORE = 0, EPI_SUB = 1, EPI_FS1 = 2, EPI_FS2 = 3 };
@@ -198,6 +210,8 @@ struct OzParams {
     int64_t zrow, zc;
     int row_base;
     const int32_t *ext;
+    int64_t zrow_q;                 // Q's operand rows per window (0: zrow)
+    const int32_t *ext_c;           // output column extents per window (null: ext)
     const double *Vp; int64_t ldv;  // with dcol: C[r, c] += Vp[r, c] dcol[c] (exact diagonal term)
     const double *dcol;
     int32_t *status;
