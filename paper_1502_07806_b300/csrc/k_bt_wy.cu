@@ -23,6 +23,8 @@
 //                columns) holds its columns of the residual in shared memory and runs the
 //                right-looking back substitution (rows of G staged by cp.async)
 //   k_bt_finish  the start-vector rules of the FP64 back-transformation, one warp per vector
+#include <algorithm>
+
 #include "pfsm_internal.cuh"
 
 namespace pfsm {
@@ -48,13 +50,26 @@ int trsm_chunk_rows(int Mmax)
     return kc;
 }
 
-size_t trsm_smem(int Mmax, int cw, int kc) { return ((size_t)Mmax * cw + (size_t)2 * kc * Mmax) * sizeof(double); }
+size_t trsm_smem(int Mmax, int cw, int kc)
+{
+    return ((size_t)Mmax * cw + (size_t)2 * kc * Mmax + (size_t)Mmax) * sizeof(double);
+}
 
 // p_k of the exact power-of-two rescaling of reflector k: 2^(2 p_k) within a factor 4 of
 // beta_k / 2 = 1 / |v_k|^2 (0 for beta = 0, whose v is zero)
 __device__ __forceinline__ int wy_scale_exp(double beta)
 {
     return beta > 0.0 ? ilogb(0.5 * beta) / 2 : 0;
+}
+
+// x 2^p: the exponent field moved by integer addition (no FP64 instruction; B300 retires one FP64
+// warp instruction per 16 cycles per SM) when x is normal and stays normal, else ldexp; 0 stays 0
+__device__ __forceinline__ double scale_pow2(double x, int p)
+{
+    const long long u = __double_as_longlong(x);
+    const int ex = (int)((u >> 52) & 0x7FF);
+    if (ex > 0 && ex + p > 0 && ex + p < 2047) return __longlong_as_double(u + ((long long)p << 52));
+    return ldexp(x, p);
 }
 
 }  // namespace
@@ -79,12 +94,18 @@ k_bt_prep(const int32_t *__restrict__ plan, int nb, int Mmax, int mmax, const do
     const int nk = M > 2 ? M - 2 : 0;
     const int ti = blockIdx.y, tj = blockIdx.x;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    __shared__ int pk[32];
     double *br = refl + (size_t)b * Mmax * Mmax;
+    if (threadIdx.x < 32) {
+        const int k = ti * 32 + threadIdx.x;
+        pk[threadIdx.x] = (k < nk) ? wy_scale_exp(tau[(size_t)b * Mmax + k]) : 0;
+    }
+    __syncthreads();
     for (int q = ty; q < 32; q += 8) {
         const int k = ti * 32 + q, j = tj * 32 + tx;
         double v = 0.0;
         if (k < Mmax && j < Mmax) {
-            v = (k < nk && j > k && j < M) ? ldexp(br[(size_t)k * Mmax + j], wy_scale_exp(tau[(size_t)b * Mmax + k])) : 0.0;
+            if (k < nk && j > k && j < M) v = scale_pow2(br[(size_t)k * Mmax + j], pk[q]);
             br[(size_t)k * Mmax + j] = v;
         }
         t[q][tx] = v;
@@ -125,6 +146,7 @@ k_bt_trsm(const int32_t *__restrict__ ext, int nb, int Mmax, int mmax, int cw, i
     extern __shared__ double sm_trsm[];
     double *R = sm_trsm;                                  // [Mmax][cw]
     double *Gs = R + (size_t)Mmax * cw;                   // [2][kc][Mmax]
+    double *bs = Gs + (size_t)2 * kc * Mmax;              // [Mmax] scaled beta
     __shared__ double W2s[2][kTrsmMaxCols];
     const int b = blockIdx.y;
     const int nk = ext[b], mb = ext[nb + b];
@@ -144,7 +166,11 @@ k_bt_trsm(const int32_t *__restrict__ ext, int nb, int Mmax, int mmax, int cw, i
         const int k = i / nc, c = i - k * nc;
         R[(size_t)k * cw + c] = W1b[(size_t)k * mmax + c];
     }
-    auto scaled_beta = [&](int k) { const double bk = tb[k]; return ldexp(bk, -2 * wy_scale_exp(bk)); };
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+        const double bk = tb[k];
+        bs[k] = scale_pow2(bk, -2 * wy_scale_exp(bk));
+    }
+    auto scaled_beta = [&](int k) { return bs[k]; };
     const int nrg = (int)blockDim.x / nc;
     const int c = (int)threadIdx.x % nc, rg = (int)threadIdx.x / nc;
     const bool act = rg < nrg;
@@ -182,12 +208,15 @@ k_bt_trsm(const int32_t *__restrict__ ext, int nb, int Mmax, int mmax, int cw, i
             if (act) {
                 const double wk = W2s[k & 1][c];
                 const double *grow = gch + (size_t)r * Mmax;
-                for (int l = rg; l < k; l += nrg) R[(size_t)l * cw + c] = fma(-grow[l], wk, R[(size_t)l * cw + c]);
-                if (k >= 1 && (k - 1) % nrg == rg) {      // row k - 1 is final: its w
-                    const double wv = scaled_beta(k - 1) * R[(size_t)(k - 1) * cw + c];
+                // row k - 1 receives its last update in this step: its owner applies that first and
+                // publishes w_{k-1}, overlapping the other rows' updates (rows l < k - 1)
+                if (k >= 1 && (k - 1) % nrg == rg) {
+                    const double wv = scaled_beta(k - 1) * fma(-grow[k - 1], wk, R[(size_t)(k - 1) * cw + c]);
                     W2s[(k - 1) & 1][c] = wv;
                     W2Tb[(size_t)c * Mmax + k - 1] = wv;
                 }
+#pragma unroll 4
+                for (int l = rg; l < k - 1; l += nrg) R[(size_t)l * cw + c] = fma(-grow[l], wk, R[(size_t)l * cw + c]);
             }
             __syncthreads();
         }
@@ -212,26 +241,34 @@ k_bt_finish(const int32_t *__restrict__ plan, int nb, int64_t N, int Mmax, int m
     if (t >= mb) return;
     const double *zz = Y + ((size_t)b * mmax + t) * Mmax;
     const int home = k0 - s + t;
-    double best = -1.0;
+    // |y_i| compared as bit patterns (the IEEE order of magnitudes); a NaN is never the largest
+    auto mag = [](double x) -> long long {
+        const long long a = __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll;
+        return a > 0x7FF0000000000000ll ? -1ll : a;
+    };
+    long long best = -1;
     int arg = M;
     for (int i = lane; i < M; i += 32) {
-        const double av = fabs(zz[i]);
+        const long long av = mag(zz[i]);
         if (av > best) { best = av; arg = i; }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
         if (ob > best || (ob == best && oa < arg)) { best = ob; arg = oa; }
     }
+    if (arg >= M) arg = home;                             // every entry NaN
     const double yh = zz[home];
-    const double ref = (fabs(yh) >= 0.1) ? yh : zz[arg];
-    const double flip = (ref < 0.0) ? -1.0 : 1.0;
+    const long long tenth = __double_as_longlong(0.1);
+    const double ref = (mag(yh) >= tenth) ? yh : zz[arg];
+    const unsigned long long flip = (__double_as_longlong(ref) < 0) ? 0x8000000000000000ull : 0ull;   // sign bit
     const int64_t kg = k0 + t;
     double *xr = X + kg * N;
     for (int64_t jj = lane; jj < N; jj += 32) {
         const int64_t li = jj - s;
-        xr[jj] = (li >= 0 && li < M) ? flip * zz[li] : 0.0;
+        xr[jj] = (li >= 0 && li < M) ? __longlong_as_double((long long)((unsigned long long)__double_as_longlong(zz[li]) ^ flip))
+                                     : 0.0;
     }
     if (lane == 0) {
         const double glo = gersh[2 * N], ghi = gersh[2 * N + 1];
