@@ -265,6 +265,11 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
     for (int i = 0; i < 8 && e == cudaSuccess; i++) e = cudaEventCreate(&h->ev[i]);
     for (int i = 0; i < 4 && e == cudaSuccess; i++) e = cudaEventCreate(&h->sub_ev[i]);
     for (int i = 0; i < 2 && e == cudaSuccess; i++) e = cudaEventCreate(&h->gs_ev[i]);
+    if (prm.precision != PFSM_FP64) {
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         free_ws(h);
         delete h;
@@ -317,7 +322,10 @@ static cudaError_t fs_mixed(pfsm_handle_s *h, const double *A, cudaStream_t st)
     SliceBuf sE{w.slE, N, ld, ns, kind}, sX{w.slX, N, ld, ns, kind}, sY{w.slY, N, ld, ns, kind},
         sZ{w.slZ, N, ld, ns, kind};
     cudaError_t e;
-    if ((e = launch_split(A, N, N, N, sE, true, w.dA, st)) != cudaSuccess) return e;
+    // the slices of E = A - diag(A) (and diag(A)) were split on the side stream during the window
+    // eigensolves when the handle has one (launch_subeig)
+    if (!h->side && (e = launch_split(A, N, N, N, sE, true, w.dA, st)) != cudaSuccess) return e;
+    if ((e = join_side(h, st)) != cudaSuccess) return e;
     if ((e = launch_split(w.X, N, N, N, sX, false, nullptr, st)) != cudaSuccess) return e;
     TcParams p{};
     p.rows = (int)N; p.cols = (int)N; p.ldo = N; p.bn = h->tc_bn;
@@ -381,6 +389,7 @@ static int solve_impl(pfsm_handle_s *h, const double *A, const double *prev, dou
                           w.tile_krange, w.gersh, w.status, st));
     PFSM_CUDA(mark(1));
     PFSM_CUDA(launch_subeig(h, A, st));
+    PFSM_CUDA(join_side(h, st));
     PFSM_CUDA(mark(2));
     h->last_fs_steps = h->prm.fs_iters;
     h->last_fs_resid = 0.0;
@@ -728,6 +737,9 @@ int pfsm_destroy(pfsm_handle_t h)
         if (h->sub_ev[i]) cudaEventDestroy(h->sub_ev[i]);
     for (int i = 0; i < 2; i++)
         if (h->gs_ev[i]) cudaEventDestroy(h->gs_ev[i]);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    if (h->join_ev) cudaEventDestroy(h->join_ev);
     fallback_free(h);
     if (h->fs_rmax) cudaFree(h->fs_rmax);
     free_ws(h);

@@ -23,8 +23,6 @@
 //                columns) holds its columns of the residual in shared memory and runs the
 //                right-looking back substitution (rows of G staged by cp.async)
 //   k_bt_finish  the start-vector rules of the FP64 back-transformation, one warp per vector
-#include <algorithm>
-
 #include "pfsm_internal.cuh"
 
 namespace pfsm {
@@ -79,14 +77,15 @@ bool backtransform_wy_fits(int Mmax)
     return Mmax >= 1 && trsm_smem(Mmax, 1, trsm_chunk_rows(Mmax)) <= kTrsmSmemCap;
 }
 
-// Grid (ceil(Mmax / 32), ceil(Mmax / 32), nb), 256 threads: tile (ti, tj) of window b's reflector
-// rows (row k = v_k, entries j; valid for k < M - 2, k < j < M) is scaled by 2^p_k and cleaned in
-// place and written transposed into RT; the tiles with ti * 32 < mmax also clean the eigenvector
-// rows t (entries j >= M and rows t >= m_b set to zero). ext = {M - 2, m_b, M} per window.
+// Grid (ceil(Mmax / 32), ceil(rows / 32), nb), 256 threads. Reflector part (vectors = false, rows
+// = Mmax): tile (ti, tj) of window b's reflector rows (row k = v_k, entries j; valid for k < M - 2,
+// k < j < M) is scaled by 2^p_k and cleaned in place and written transposed into RT;
+// ext = {M - 2, m_b, M} per window. Vector part (vectors = true, rows = mmax): the eigenvector rows
+// t are cleaned (entries j >= M and rows t >= m_b set to zero).
 __global__ void __launch_bounds__(256)
-k_bt_prep(const int32_t *__restrict__ plan, int nb, int Mmax, int mmax, const double *__restrict__ tau,
-          double *__restrict__ refl, double *__restrict__ RT, double *__restrict__ sel_vec,
-          int32_t *__restrict__ ext)
+k_bt_prep(const int32_t *__restrict__ plan, int nb, int Mmax, int mmax, bool vectors,
+          const double *__restrict__ tau, double *__restrict__ refl, double *__restrict__ RT,
+          double *__restrict__ sel_vec, int32_t *__restrict__ ext)
 {
     __shared__ double t[32][33];
     const int b = blockIdx.z;
@@ -94,6 +93,14 @@ k_bt_prep(const int32_t *__restrict__ plan, int nb, int Mmax, int mmax, const do
     const int nk = M > 2 ? M - 2 : 0;
     const int ti = blockIdx.y, tj = blockIdx.x;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    if (vectors) {
+        double *bs = sel_vec + (size_t)b * mmax * Mmax;
+        for (int q = ty; q < 32; q += 8) {
+            const int tt = ti * 32 + q, j = tj * 32 + tx;
+            if (tt < mmax && j < Mmax && (tt >= mb || j >= M)) bs[(size_t)tt * Mmax + j] = 0.0;
+        }
+        return;
+    }
     __shared__ int pk[32];
     double *br = refl + (size_t)b * Mmax * Mmax;
     if (threadIdx.x < 32) {
@@ -115,13 +122,6 @@ k_bt_prep(const int32_t *__restrict__ plan, int nb, int Mmax, int mmax, const do
     for (int q = ty; q < 32; q += 8) {
         const int j = tj * 32 + q, k = ti * 32 + tx;            // RT[j][k] = refl[k][j]
         if (j < Mmax && k < Mmax) bt[(size_t)j * Mmax + k] = t[tx][q];
-    }
-    if (ti * 32 < mmax) {
-        double *bs = sel_vec + (size_t)b * mmax * Mmax;
-        for (int q = ty; q < 32; q += 8) {
-            const int tt = ti * 32 + q, j = tj * 32 + tx;
-            if (tt < mmax && j < Mmax && (tt >= mb || j >= M)) bs[(size_t)tt * Mmax + j] = 0.0;
-        }
     }
     if (ti == 0 && tj == 0 && threadIdx.x == 0) {
         ext[b] = nk;
@@ -281,7 +281,31 @@ k_bt_finish(const int32_t *__restrict__ plan, int nb, int64_t N, int Mmax, int m
     }
 }
 
-cudaError_t launch_backtransform_wy(pfsm_handle_s *h, cudaStream_t st)
+// Steps that need only the window reduction's reflectors: clean and scale them, V^T, the extents,
+// the digits of V^T's rows and G = V^T V (lower triangle), per window.
+cudaError_t launch_backtransform_wy_reflectors(pfsm_handle_s *h, cudaStream_t st)
+{
+    Workspace &w = h->ws;
+    const int nb = h->nb, Mmax = h->Mmax, mmax = h->mmax;
+    const int64_t ldk = padded_ld(Mmax);
+    const int64_t nbM = (int64_t)nb * Mmax;
+    SliceBuf dA{w.btDA, nbM, ldk, OZ_SLICES, 0};
+    cudaError_t e;
+    const unsigned nt = (unsigned)((Mmax + 31) / 32);
+    k_bt_prep<<<dim3(nt, nt, (unsigned)nb), 256, 0, st>>>(w.plan, nb, Mmax, mmax, false, w.tau, w.refl, w.btRT,
+                                                           w.sel_vec, w.btExt);
+    g_launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_oz_split(w.refl, nbM, Mmax, Mmax, dA, w.btEA, st)) != cudaSuccess) return e;
+    OzParams o{};
+    o.rows = Mmax; o.cols = Mmax; o.C = w.btG; o.ldc = Mmax; o.lower_only = 1; o.status = w.status;
+    o.zrow = Mmax; o.zc = (int64_t)Mmax * Mmax; o.ext = w.btExt;
+    return launch_gemm_oz(dA, w.btEA, dA, w.btEA, o, st, nb);
+}
+
+// The rest, after the tridiagonal eigenvectors: reflector steps on this stream unless the side
+// stream ran them (joined before W1).
+cudaError_t launch_backtransform_wy(pfsm_handle_s *h, cudaStream_t st, bool reflectors_done)
 {
     Workspace &w = h->ws;
     const int nb = h->nb, Mmax = h->Mmax, mmax = h->mmax;
@@ -290,26 +314,21 @@ cudaError_t launch_backtransform_wy(pfsm_handle_s *h, cudaStream_t st)
     SliceBuf dA{w.btDA, nbM, ldk, OZ_SLICES, 0}, dB{w.btDB, nbm, ldk, OZ_SLICES, 0};
     int32_t *ext_k = w.btExt, *ext_m = w.btExt + nb, *ext_M = w.btExt + 2 * nb;
     cudaError_t e;
-    // 1. clean reflector and eigenvector rows, V^T, extents
+    if (!reflectors_done && (e = launch_backtransform_wy_reflectors(h, st)) != cudaSuccess) return e;
+    // 1. clean the eigenvector rows; their digits (z_t, entries j)
     const unsigned nt = (unsigned)((Mmax + 31) / 32);
-    k_bt_prep<<<dim3(nt, nt, (unsigned)nb), 256, 0, st>>>(w.plan, nb, Mmax, mmax, w.tau, w.refl, w.btRT, w.sel_vec,
-                                                           w.btExt);
+    k_bt_prep<<<dim3(nt, (unsigned)((mmax + 31) / 32), (unsigned)nb), 256, 0, st>>>(w.plan, nb, Mmax, mmax, true, w.tau,
+                                                                                      w.refl, w.btRT, w.sel_vec, w.btExt);
     g_launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // 2. digits of V^T's rows (v_k, entries j) and of the eigenvectors (z_t, entries j)
-    if ((e = launch_oz_split(w.refl, nbM, Mmax, Mmax, dA, w.btEA, st)) != cudaSuccess) return e;
     if ((e = launch_oz_split(w.sel_vec, nbm, Mmax, Mmax, dB, w.btEB, st)) != cudaSuccess) return e;
-    // 3. G = V^T V (lower triangle), per window
+    if ((e = join_side(h, st)) != cudaSuccess) return e;
+    // 2. W1 = V^T Z (rows k, columns t), per window
     OzParams o{};
-    o.rows = Mmax; o.cols = Mmax; o.C = w.btG; o.ldc = Mmax; o.lower_only = 1; o.status = w.status;
-    o.zrow = Mmax; o.zc = (int64_t)Mmax * Mmax; o.ext = ext_k;
-    if ((e = launch_gemm_oz(dA, w.btEA, dA, w.btEA, o, st, nb)) != cudaSuccess) return e;
-    // 4. W1 = V^T Z (rows k, columns t), per window
-    o = OzParams{};
     o.rows = Mmax; o.cols = mmax; o.C = w.btW1; o.ldc = mmax; o.status = w.status;
     o.zrow = Mmax; o.zrow_q = mmax; o.zc = (int64_t)Mmax * mmax; o.ext = ext_k; o.ext_c = ext_m;
     if ((e = launch_gemm_oz(dA, w.btEA, dB, w.btEB, o, st, nb)) != cudaSuccess) return e;
-    // 5. W2 = S^-1 W1 -> W2^T: columns per CTA so that the CTAs fill the SMs once, within shared memory
+    // 3. W2 = S^-1 W1 -> W2^T: columns per CTA so that the CTAs fill the SMs once, within shared memory
     {
         const int kc = trsm_chunk_rows(Mmax);
         int cw = 1;
@@ -321,10 +340,10 @@ cudaError_t launch_backtransform_wy(pfsm_handle_s *h, cudaStream_t st)
         g_launches++;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    // 6. digits of W2^T (rows t, entries k) and of V (rows j, entries k)
+    // 4. digits of W2^T (rows t, entries k) and of V (rows j, entries k)
     if ((e = launch_oz_split(w.btW2T, nbm, Mmax, Mmax, dB, w.btEB, st)) != cudaSuccess) return e;
     if ((e = launch_oz_split(w.btRT, nbM, Mmax, Mmax, dA, w.btEA, st)) != cudaSuccess) return e;
-    // 7. Y = Z - W2^T V^T (rows t, entries j), per window
+    // 5. Y = Z - W2^T V^T (rows t, entries j), per window
     if ((e = cudaMemcpyAsync(w.btY, w.sel_vec, (size_t)nbm * Mmax * sizeof(double), cudaMemcpyDeviceToDevice, st)) !=
         cudaSuccess)
         return e;
@@ -332,7 +351,7 @@ cudaError_t launch_backtransform_wy(pfsm_handle_s *h, cudaStream_t st)
     o.rows = mmax; o.cols = Mmax; o.C = w.btY; o.ldc = Mmax; o.sub = 1; o.status = w.status;
     o.zrow = mmax; o.zrow_q = Mmax; o.zc = (int64_t)mmax * Mmax; o.ext = ext_m; o.ext_c = ext_M;
     if ((e = launch_gemm_oz(dB, w.btEB, dA, w.btEA, o, st, nb)) != cudaSuccess) return e;
-    // 8. start vectors
+    // 6. start vectors
     {
         const int64_t warps = nbm;
         k_bt_finish<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(w.plan, nb, h->N, Mmax, mmax, w.btY, w.sel_val,
@@ -340,6 +359,13 @@ cudaError_t launch_backtransform_wy(pfsm_handle_s *h, cudaStream_t st)
         g_launches++;
     }
     return cudaGetLastError();
+}
+
+cudaError_t join_side(pfsm_handle_s *h, cudaStream_t st)
+{
+    if (!h->side_pending) return cudaSuccess;
+    h->side_pending = false;
+    return cudaStreamWaitEvent(st, h->join_ev, 0);
 }
 
 cudaError_t configure_bt_wy_kernels()

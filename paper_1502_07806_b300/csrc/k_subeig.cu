@@ -1444,6 +1444,11 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
     Workspace &w = h->ws;
     const int nb = h->nb, Mmax = h->Mmax, mmax = h->mmax, CL = h->cl;
     cudaError_t e0;
+    // mixed forms: work that needs only A (the Eq. 11 operand split) joins the side stream from here
+    // and runs beside the window reduction, which leaves SMs idle; it is enqueued after the
+    // reduction's launch so that the reduction's clusters are placed first
+    const bool side_e = h->side && h->prm.precision != PFSM_FP64 && !h->prm.fs_adaptive && h->prm.fs_iters > 0;
+    if (side_e && (e0 = cudaEventRecord(h->fork_ev, st)) != cudaSuccess) return e0;
     // 1. tridiagonalisation, one cluster per window
     if (h->tri_blocked) {
         // blocked: one panel launch per kPanel columns, the trailing update as a batched digit
@@ -1503,6 +1508,24 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
                                    w.iiwork, w.refl, w.tau, w.td, w.te));
         if (e != cudaSuccess) return e;
     }
+    if (side_e) {
+        const int64_t ld = padded_ld(h->N);
+        const SliceBuf sE{w.slE, h->N, ld, slices_for(h->prm.precision), slice_kind(h->prm.precision)};
+        if ((e0 = cudaStreamWaitEvent(h->side, h->fork_ev, 0)) != cudaSuccess) return e0;
+        if ((e0 = launch_split(A, h->N, h->N, h->N, sE, true, w.dA, h->side)) != cudaSuccess) return e0;
+        if ((e0 = cudaEventRecord(h->join_ev, h->side)) != cudaSuccess) return e0;
+        h->side_pending = true;
+    }
+    // mixed forms: the back-transform's steps that need only the reflectors run on the side
+    // stream beside the eigenvalue and inverse-iteration kernels (one warp per SM)
+    const bool side_bt = h->prm.precision != PFSM_FP64 && w.btG && h->side;
+    if (side_bt) {
+        if ((e0 = cudaEventRecord(h->fork_ev, st)) != cudaSuccess) return e0;
+        if ((e0 = cudaStreamWaitEvent(h->side, h->fork_ev, 0)) != cudaSuccess) return e0;
+        if ((e0 = launch_backtransform_wy_reflectors(h, h->side)) != cudaSuccess) return e0;
+        if ((e0 = cudaEventRecord(h->join_ev, h->side)) != cudaSuccess) return e0;
+        h->side_pending = true;
+    }
     // one eigenpair per lane, full warps (a warp-wide FP64 instruction costs the same with 1 or
     // 32 active lanes)
     const int tpb = 32;
@@ -1536,7 +1559,7 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
     // 4. back-transform + start vectors: the mixed forms apply the reflectors in compact-WY form
     //    with digit products on the tensor cores (k_bt_wy.cu); the FP64 form one by one on the FP64
     //    pipe
-    if (h->prm.precision != PFSM_FP64 && w.btG) return launch_backtransform_wy(h, st);
+    if (h->prm.precision != PFSM_FP64 && w.btG) return launch_backtransform_wy(h, st, side_bt);
     {
         // vectors per CTA: the fewest for which sum_b ceil(m_b / vpc) <= N / vpc + nb CTAs fit
         // one per SM; eight warps of up to two vectors (<= 3 per sub-partition for vpc <= 10) when

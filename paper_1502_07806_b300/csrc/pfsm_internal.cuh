@@ -112,6 +112,12 @@ struct pfsm_handle_s {
     cudaEvent_t ev[8] = {};
     cudaEvent_t sub_ev[4] = {};   // inside the submatrix phase (timing only)
     cudaEvent_t gs_ev[2] = {};    // inside Gram-Schmidt: after the overlap, after Cholesky
+    // mixed forms: a second stream for work that depends only on A or on the window reduction
+    // (the Eq. 11 operand split of A, the back-transform's reflector preparation and V^T V), run
+    // beside the window kernels that leave SMs idle; forked and joined through events
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    bool side_pending = false;     // side work enqueued and not yet waited for on the solve stream
     int32_t last_launches = 0;
     bool last_was_backward = false;
 };
@@ -136,9 +142,14 @@ cudaError_t launch_plan(const double *prev, int64_t N, int32_t nb, int32_t halo,
 
 cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st);
 // mixed forms: y = H_0 ... H_{M-3} z and the start vectors by the compact-WY form (k_bt_wy.cu);
-// false when the solve's shared memory cannot hold a column chunk (the FP64 kernel is used)
+// false when the solve's shared memory cannot hold a column chunk (the FP64 kernel is used).
+// reflectors_done: launch_backtransform_wy_reflectors already ran on the side stream.
 bool backtransform_wy_fits(int Mmax);
-cudaError_t launch_backtransform_wy(pfsm_handle_s *h, cudaStream_t st);
+cudaError_t launch_backtransform_wy(pfsm_handle_s *h, cudaStream_t st, bool reflectors_done);
+// the part of it that needs only the reduction's reflectors (on the handle's side stream)
+cudaError_t launch_backtransform_wy_reflectors(pfsm_handle_s *h, cudaStream_t st);
+// the solve stream waits for the side stream's work, if any is pending
+cudaError_t join_side(pfsm_handle_s *h, cudaStream_t st);
 cudaError_t configure_bt_wy_kernels();
 cudaError_t configure_kernels(pfsm_handle_s *h);   // shared-memory / cluster attributes
 
