@@ -270,8 +270,9 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
             const int R0 = row0 + 32 * g;
             // coalesced access of the warp's 32 x 16 block: lanes 0-15 row 2i, lanes 16-31 row 2i+1
             auto in_block = [&](int rr, int c) { return R0 + rr < prm.rows && c < prm.cols && !(prm.lower_only && c > R0 + rr); };
+            // all 16 loads of a lane in flight at once (one L2 round trip per block)
             auto load_block = [&](const double *src, int C0) {
-#pragma unroll 4
+#pragma unroll
                 for (int i = 0; i < 16; i++) {
                     const int rr = 2 * i + (lane >> 4), cc = lane & 15, c = C0 + cc;
                     if (in_block(rr, c)) eb[rr][cc] = src[(int64_t)(R0 + rr) * prm.ldo + c];
@@ -324,6 +325,17 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
                         for (int j = 0; j < 16; j++) eb[lane][j] -= (double)__uint_as_float(v[16 * h + j]);
                         store_block(prm.out, C0, false);
                     } else {
+                        // the accumulated operand (X for Z, Y_old for Y_new): each lane's own row,
+                        // 16 contiguous doubles straight into registers, in flight together with
+                        // the staged loads of V below (one L2 round trip for both)
+                        double xo[16];
+                        {
+                            const double *xs = (prm.epi == TC_EPI_Z) ? prm.X : prm.Yold;
+                            const int rw = R0 + lane;
+#pragma unroll
+                            for (int j = 0; j < 16; j++)
+                                xo[j] = in_block(lane, C0 + j) ? xs[(int64_t)rw * prm.ldo + C0 + j] : 0.0;
+                        }
                         // (A - eps_r I) applied to the FP64 operand's diagonal part, in FP32:
                         // (d_c - eps_r) from hi/lo pieces, times the operand rounded to FP32
                         float t[16];
@@ -335,18 +347,14 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
                             t[j] = fmaf(diff, (float)eb[lane][j], __uint_as_float(v[16 * h + j]));
                         }
                         __syncwarp();
-                        if (prm.epi == TC_EPI_Z) {
-                            load_block(prm.X, C0);                       // X -= alpha Z in FP64
 #pragma unroll
-                            for (int j = 0; j < 16; j++) eb[lane][j] = fma(-ar, (double)t[j], eb[lane][j]);
+                        for (int j = 0; j < 16; j++) eb[lane][j] = fma(-ar, (double)t[j], xo[j]);
+                        if (prm.epi == TC_EPI_Z) {                       // X -= alpha Z in FP64
                             store_block(prm.X, C0, false);
 #pragma unroll
                             for (int j = 0; j < 16; j++) eb[lane][j] = (double)t[j];
                             store_block(prm.out, C0, sl);
                         } else {   // TC_EPI_YN: Y - alpha (E Z + (D - eps) Z), accumulated in FP64
-                            load_block(prm.Yold, C0);
-#pragma unroll
-                            for (int j = 0; j < 16; j++) eb[lane][j] = fma(-ar, (double)t[j], eb[lane][j]);
                             store_block(prm.out, C0, sl);
                         }
                     }
