@@ -23,6 +23,8 @@
 //                columns) holds its columns of the residual in shared memory and runs the
 //                right-looking back substitution (rows of G staged by cp.async)
 //   k_bt_finish  the start-vector rules of the FP64 back-transformation, one warp per vector
+#include <algorithm>
+
 #include "pfsm_internal.cuh"
 
 namespace pfsm {
@@ -150,75 +152,80 @@ k_bt_trsm(const int32_t *__restrict__ ext, int nb, int Mmax, int mmax, int cw, i
     __shared__ double W2s[2][kTrsmMaxCols];
     const int b = blockIdx.y;
     const int nk = ext[b], mb = ext[nb + b];
-    const int c0 = blockIdx.x * cw;
-    const int nc = max(0, min(cw, mb - c0));
-    double *W2Tb = W2T + ((size_t)b * mmax + c0) * Mmax;
-    // zero the parts of this CTA's rows that the solve does not write
-    for (int i = threadIdx.x; i < cw * Mmax; i += blockDim.x) {
-        const int c = i / Mmax, k = i - c * Mmax;
-        if (c0 + c < mmax && (c >= nc || k >= nk)) W2Tb[(size_t)c * Mmax + k] = 0.0;
-    }
-    if (nc == 0 || nk == 0) return;
     const double *Gb = G + (size_t)b * Mmax * Mmax;
     const double *tb = tau + (size_t)b * Mmax;
-    const double *W1b = W1 + (size_t)b * Mmax * mmax + c0;
-    for (int i = threadIdx.x; i < nk * nc; i += blockDim.x) {
-        const int k = i / nc, c = i - k * nc;
-        R[(size_t)k * cw + c] = W1b[(size_t)k * mmax + c];
-    }
     for (int k = threadIdx.x; k < nk; k += blockDim.x) {
         const double bk = tb[k];
         bs[k] = scale_pow2(bk, -2 * wy_scale_exp(bk));
     }
-    auto scaled_beta = [&](int k) { return bs[k]; };
-    const int nrg = (int)blockDim.x / nc;
-    const int c = (int)threadIdx.x % nc, rg = (int)threadIdx.x / nc;
-    const bool act = rg < nrg;
-    const int nch = (nk + kc - 1) / kc;
-    auto issue = [&](int ch) {                            // rows k = khi, khi - 1, ... of G, entries l < k
-        double *dst = Gs + (size_t)(ch & 1) * kc * Mmax;
-        const int khi = nk - 1 - ch * kc;
-        for (int r = 0; r < kc; r++) {
-            const int k = khi - r;
-            if (k < 0) break;
-            for (int l = threadIdx.x; l < k; l += blockDim.x) cp_async8(dst + (size_t)r * Mmax + l, Gb + (size_t)k * Mmax + l);
+    // the grid is sized by the nominal slice width; a CTA takes chunks blockIdx.x, + gridDim.x, ...
+    // of the window's mmax columns (chunks beyond m_b only get their rows zeroed)
+    for (int ci = blockIdx.x; ci * cw < mmax; ci += gridDim.x) {
+        const int c0 = ci * cw;
+        const int nc = max(0, min(cw, mb - c0));
+        double *W2Tb = W2T + ((size_t)b * mmax + c0) * Mmax;
+        // zero the parts of this chunk's rows that the solve does not write
+        for (int i = threadIdx.x; i < cw * Mmax; i += blockDim.x) {
+            const int c = i / Mmax, k = i - c * Mmax;
+            if (c0 + c < mmax && (c >= nc || k >= nk)) W2Tb[(size_t)c * Mmax + k] = 0.0;
         }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    issue(0);
-    __syncthreads();                                      // R loaded
-    if (act && (nk - 1) % nrg == rg) {                    // w of the last row
-        const double wv = scaled_beta(nk - 1) * R[(size_t)(nk - 1) * cw + c];
-        W2s[(nk - 1) & 1][c] = wv;
-        W2Tb[(size_t)c * Mmax + nk - 1] = wv;
-    }
-    for (int ch = 0; ch < nch; ch++) {
-        if (ch + 1 < nch) {
-            issue(ch + 1);
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        if (nc == 0 || nk == 0) continue;                 // uniform over the CTA
+        const double *W1b = W1 + (size_t)b * Mmax * mmax + c0;
+        __syncthreads();                                  // the previous chunk is done with R, Gs, W2s
+        for (int i = threadIdx.x; i < nk * nc; i += blockDim.x) {
+            const int k = i / nc, c = i - k * nc;
+            R[(size_t)k * cw + c] = W1b[(size_t)k * mmax + c];
         }
-        __syncthreads();                                  // chunk ch of G and the last w visible
-        const double *gch = Gs + (size_t)(ch & 1) * kc * Mmax;
-        const int khi = nk - 1 - ch * kc;
-        for (int r = 0; r < kc; r++) {
-            const int k = khi - r;
-            if (k < 0) break;
-            if (act) {
-                const double wk = W2s[k & 1][c];
-                const double *grow = gch + (size_t)r * Mmax;
-                // row k - 1 receives its last update in this step: its owner applies that first and
-                // publishes w_{k-1}, overlapping the other rows' updates (rows l < k - 1)
-                if (k >= 1 && (k - 1) % nrg == rg) {
-                    const double wv = scaled_beta(k - 1) * fma(-grow[k - 1], wk, R[(size_t)(k - 1) * cw + c]);
-                    W2s[(k - 1) & 1][c] = wv;
-                    W2Tb[(size_t)c * Mmax + k - 1] = wv;
-                }
-#pragma unroll 4
-                for (int l = rg; l < k - 1; l += nrg) R[(size_t)l * cw + c] = fma(-grow[l], wk, R[(size_t)l * cw + c]);
+        const int nrg = (int)blockDim.x / nc;
+        const int c = (int)threadIdx.x % nc, rg = (int)threadIdx.x / nc;
+        const bool act = rg < nrg;
+        const int nch = (nk + kc - 1) / kc;
+        auto issue = [&](int ch) {                        // rows k = khi, khi - 1, ... of G, entries l < k
+            double *dst = Gs + (size_t)(ch & 1) * kc * Mmax;
+            const int khi = nk - 1 - ch * kc;
+            for (int r = 0; r < kc; r++) {
+                const int k = khi - r;
+                if (k < 0) break;
+                for (int l = threadIdx.x; l < k; l += blockDim.x)
+                    cp_async8(dst + (size_t)r * Mmax + l, Gb + (size_t)k * Mmax + l);
             }
-            __syncthreads();
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        issue(0);
+        __syncthreads();                                  // R and the scaled betas loaded
+        if (act && (nk - 1) % nrg == rg) {                // w of the last row
+            const double wv = bs[nk - 1] * R[(size_t)(nk - 1) * cw + c];
+            W2s[(nk - 1) & 1][c] = wv;
+            W2Tb[(size_t)c * Mmax + nk - 1] = wv;
+        }
+        for (int ch = 0; ch < nch; ch++) {
+            if (ch + 1 < nch) {
+                issue(ch + 1);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+            } else {
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            }
+            __syncthreads();                              // chunk ch of G and the last w visible
+            const double *gch = Gs + (size_t)(ch & 1) * kc * Mmax;
+            const int khi = nk - 1 - ch * kc;
+            for (int r = 0; r < kc; r++) {
+                const int k = khi - r;
+                if (k < 0) break;
+                if (act) {
+                    const double wk = W2s[k & 1][c];
+                    const double *grow = gch + (size_t)r * Mmax;
+                    // row k - 1 receives its last update in this step: its owner applies that first
+                    // and publishes w_{k-1}, overlapping the other rows' updates (rows l < k - 1)
+                    if (k >= 1 && (k - 1) % nrg == rg) {
+                        const double wv = bs[k - 1] * fma(-grow[k - 1], wk, R[(size_t)(k - 1) * cw + c]);
+                        W2s[(k - 1) & 1][c] = wv;
+                        W2Tb[(size_t)c * Mmax + k - 1] = wv;
+                    }
+#pragma unroll 4
+                    for (int l = rg; l < k - 1; l += nrg) R[(size_t)l * cw + c] = fma(-grow[l], wk, R[(size_t)l * cw + c]);
+                }
+                __syncthreads();
+            }
         }
     }
 }
@@ -330,11 +337,14 @@ cudaError_t launch_backtransform_wy(pfsm_handle_s *h, cudaStream_t st, bool refl
     if ((e = launch_gemm_oz(dA, w.btEA, dB, w.btEB, o, st, nb)) != cudaSuccess) return e;
     // 3. W2 = S^-1 W1 -> W2^T: columns per CTA so that the CTAs fill the SMs once, within shared memory
     {
+        // sized by the nominal slice width ceil(N / nb): mmax is the widest a slice can become after
+        // cluster snapping, usually far from what the plan gives
+        const int mnom = (int)std::min<int64_t>(mmax, (h->N + nb - 1) / nb);
         const int kc = trsm_chunk_rows(Mmax);
         int cw = 1;
-        while (cw < kTrsmMaxCols && (int64_t)nb * ((mmax + cw - 1) / cw) > (int64_t)sm_count()) cw++;
+        while (cw < kTrsmMaxCols && (int64_t)nb * ((mnom + cw - 1) / cw) > (int64_t)sm_count()) cw++;
         while (cw > 1 && trsm_smem(Mmax, cw, kc) > kTrsmSmemCap) cw--;
-        const dim3 grid((unsigned)((mmax + cw - 1) / cw), (unsigned)nb);
+        const dim3 grid((unsigned)((mnom + cw - 1) / cw), (unsigned)nb);
         k_bt_trsm<<<grid, kTrsmThreads, trsm_smem(Mmax, cw, kc), st>>>(w.btExt, nb, Mmax, mmax, cw, kc, w.btG, w.tau,
                                                                       w.btW1, w.btW2T);
         g_launches++;

@@ -186,24 +186,29 @@ def test_gram_schmidt_preconditioner_paths(pf, orc, name, prec, case):
 
 
 @pytest.mark.parametrize("name,prec", PRECISIONS)
-@pytest.mark.parametrize("case", ["gapped256", "ragged333", "diamond1280", "one_window"])
+@pytest.mark.parametrize("case", ["gapped256", "ragged333", "diamond1280", "one_window", "uneven_slices"])
 def test_compact_wy_backtransform_matches_reflector_by_reflector(pf, name, prec, case):
     """The mixed forms back-transform the window eigenvectors as Y = Z - V S^-1 (V^T Z) with digit
     products and an FP64 triangular solve; the FP64 form applies the reflectors one by one. Both
     share the reduction, the eigenvalues and the tridiagonal eigenvectors, so with K = 0 the start
     vectors (the Eq. 11 diagnostic) and the shifts agree to rounding. Windows of uneven sizes
-    (ragged333: slices of 30 and 31, edge windows clamped) and a single window covering A."""
+    (ragged333: slices of 30 and 31, edge windows clamped; uneven_slices: a slice of 90 where the
+    nominal width, which sizes the triangular solve's grid, is 64) and a single window covering A."""
+    kw = {}
     if case == "gapped256":
         p = wl.small_gapped(2)
     elif case == "ragged333":
         p = wl.random_nearly_diagonal(333, seed=4, sigma=2e-3, decay=12.0, nblocks=11, halo=31)
     elif case == "diamond1280":
         p = wl.diamond_like(0)
-    else:
+    elif case == "one_window":
         p = wl.random_nearly_diagonal(200, seed=9, sigma=1e-3, decay=16.0, nblocks=1, halo=0)
-    hm = pf.Handle(p.n, p.nblocks, halo=p.halo, precision=prec, fs_iters=0)
+    else:
+        p = wl.small_gapped(1)
+        kw = {"slice_sizes": [40, 90, 60, 66]}
+    hm = pf.Handle(p.n, p.nblocks, halo=p.halo, precision=prec, fs_iters=0, **kw)
     hm.solve(_dev(p.A), _dev(p.prev))
-    h64 = pf.Handle(p.n, p.nblocks, halo=p.halo, precision=pf.FP64, fs_iters=0)
+    h64 = pf.Handle(p.n, p.nblocks, halo=p.halo, precision=pf.FP64, fs_iters=0, **kw)
     h64.solve(_dev(p.A), _dev(p.prev))
     assert hm.status() == 0 and h64.status() == 0
     xm = hm.diagnostic(pf.DIAG_XFS).cpu().numpy()
