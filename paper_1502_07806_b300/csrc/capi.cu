@@ -51,7 +51,8 @@ void free_ws(pfsm_handle_s *h)
                     w.sdiag, w.eps, w.alpha, w.lam, w.res, w.refl, w.tau, w.td, w.te,
                     w.sel_val, w.sel_vec, w.iiwork, w.slices, w.slE, w.slX, w.slY, w.slZ,
                     w.Z, w.dA, w.Linv, w.ozP, w.ozQ, w.ozeP, w.ozeQ, w.L32, w.R32, w.M32, w.F, w.VW, w.WV, w.tdP, w.tdQ, w.tdeP, w.tdeQ,
-                    w.btG, w.btRT, w.btW1, w.btW2T, w.btY, w.btDA, w.btDB, w.btEA, w.btEB, w.btExt};
+                    w.btG, w.btRT, w.btW1, w.btW2T, w.btY, w.btDA, w.btDB, w.btEA, w.btEB, w.btExt,
+                    w.ozA, w.ozeA};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     w = Workspace{};
@@ -207,6 +208,11 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
         if (e == cudaSuccess) e = cudaMemset(o1, 0, oz_bytes);      // zero padding columns
         if (e == cudaSuccess) e = cudaMemset(o2, 0, oz_bytes);
         w.ozP = o1; w.ozQ = o2;
+        uint8_t *o3 = nullptr;
+        PFSM_ALLOC(o3, oz_bytes);
+        if (e == cudaSuccess) e = cudaMemset(o3, 0, oz_bytes);
+        w.ozA = o3;
+        PFSM_ALLOC(w.ozeA, (size_t)N);
         PFSM_ALLOC(w.ozeP, (size_t)N);
         PFSM_ALLOC(w.ozeQ, (size_t)N);
         PFSM_ALLOC(w.L32, NN);
@@ -355,6 +361,7 @@ static int solve_impl(pfsm_handle_s *h, const double *A, const double *prev, dou
     const int64_t N = h->N;
     auto mark = [&](int i) -> cudaError_t { return h->timing ? cudaEventRecord(h->ev[i], st) : cudaSuccess; };
     PFSM_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int32_t), st));
+    h->a_split = false;
     PFSM_CUDA(mark(0));
     PFSM_CUDA(launch_validate_gersh(A, prev, N, w.gersh, w.status, st));
     // the conventional path: first-steps rule, then the guard (Section II)

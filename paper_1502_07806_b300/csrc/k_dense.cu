@@ -266,14 +266,21 @@ cudaError_t launch_rayleigh_f64(pfsm_handle_s *h, const double *A, double *eigva
     const int64_t N = h->N;
     cudaError_t e;
     if (h->prm.precision != PFSM_FP64) {   // W = V A with FP64-accurate tensor-core digits
-        SliceBuf dv{w.ozP, N, padded_ld(N), OZ_SLICES, 0}, da{w.ozQ, N, padded_ld(N), OZ_SLICES, 0};
+        SliceBuf dv{w.ozP, N, padded_ld(N), OZ_SLICES, 0};
         if ((e = launch_oz_split(w.X, N, N, N, dv, w.ozeP, st)) != cudaSuccess) return e;
-        // A = diag(d) + E: digits of E only, the diagonal term added exactly in FP64
-        if ((e = launch_oz_split(A, N, N, N, da, w.ozeQ, st, true, w.dA)) != cudaSuccess) return e;
+        // A = diag(d) + E: digits of E only (split during the window eigensolves on the side stream
+        // when the handle has one), the diagonal term added exactly in FP64
+        const bool presplit = h->a_split;
+        SliceBuf da{presplit ? w.ozA : w.ozQ, N, padded_ld(N), OZ_SLICES, 0};
+        int32_t *ea = presplit ? w.ozeA : w.ozeQ;
+        if (!presplit && (e = launch_oz_split(A, N, N, N, da, ea, st, true, w.dA)) != cudaSuccess) return e;
         OzParams o{};
         o.rows = (int)N; o.cols = (int)N; o.C = w.W; o.ldc = N; o.status = w.status;
         o.Vp = w.X; o.ldv = N; o.dcol = w.dA;
-        if ((e = launch_gemm_oz(dv, w.ozeP, da, w.ozeQ, o, st)) != cudaSuccess) return e;
+        // six digit levels: E's entries are small against A's diagonal, so the first dropped level
+        // (about sqrt(7 N) 2^-42 / 3 of max|V_r| max|E_c|) stays far below FP64 rounding of A V
+        o.levels = 6;
+        if ((e = launch_gemm_oz(dv, w.ozeP, da, ea, o, st)) != cudaSuccess) return e;
     } else {
         GemmArgs g{};
         g.rows = N; g.cols = N; g.K = N;

@@ -1513,6 +1513,9 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
         const SliceBuf sE{w.slE, h->N, ld, slices_for(h->prm.precision), slice_kind(h->prm.precision)};
         if ((e0 = cudaStreamWaitEvent(h->side, h->fork_ev, 0)) != cudaSuccess) return e0;
         if ((e0 = launch_split(A, h->N, h->N, h->N, sE, true, w.dA, h->side)) != cudaSuccess) return e0;
+        const SliceBuf da{w.ozA, h->N, ld, OZ_SLICES, 0};      // A' digits for the Rayleigh product
+        if ((e0 = launch_oz_split(A, h->N, h->N, h->N, da, w.ozeA, h->side, true, w.dA)) != cudaSuccess) return e0;
+        h->a_split = true;
         if ((e0 = cudaEventRecord(h->join_ev, h->side)) != cudaSuccess) return e0;
         h->side_pending = true;
     }

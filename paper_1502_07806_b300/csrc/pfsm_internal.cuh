@@ -65,6 +65,9 @@ struct Workspace {
     // (Mmax x Mmax, lower), V^T (Mmax x Mmax), W1 = V^T Z (Mmax x mmax), W2^T (mmax x Mmax), Y
     // (mmax x Mmax); the digit matrices of the Mmax-row and the mmax-row operands and their row
     // exponents; per-window extents (reflectors, vectors, rows)
+    // mixed forms: digits of A' = A - diag(A) for the Rayleigh product, split on the side stream
+    void *ozA = nullptr;
+    int32_t *ozeA = nullptr;
     double *btG = nullptr, *btRT = nullptr, *btW1 = nullptr, *btW2T = nullptr, *btY = nullptr;
     void *btDA = nullptr, *btDB = nullptr;
     int32_t *btEA = nullptr, *btEB = nullptr, *btExt = nullptr;
@@ -118,6 +121,7 @@ struct pfsm_handle_s {
     cudaStream_t side = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     bool side_pending = false;     // side work enqueued and not yet waited for on the solve stream
+    bool a_split = false;          // this solve split A' into ws.ozA on the side stream
     int32_t last_launches = 0;
     bool last_was_backward = false;
 };
