@@ -31,8 +31,8 @@ namespace pfsm {
 
 namespace {
 
-constexpr int kTrsmThreads = 256;
-constexpr int kTrsmMaxCols = 64;                 // columns per CTA (W2 staging)
+constexpr int kTrsmThreads = 256;                // update threads of k_bt_trsm (plus one warp for w)
+constexpr int kTrsmMaxCols = 32;                 // columns per CTA (one lane of the w warp each)
 constexpr size_t kTrsmSmemCap = 160 * 1024;      // shared memory of one k_bt_trsm CTA
 constexpr size_t kTrsmGBytes = 80 * 1024;        // of it, the double-buffered rows of G
 
@@ -132,15 +132,16 @@ k_bt_prep(const int32_t *__restrict__ plan, int nb, int Mmax, int mmax, bool vec
     }
 }
 
-// Grid (ceil(mmax / cw), nb), 256 threads: W2 = S^-1 W1 for the columns t in [c0, c0 + cw) of window
+// Grid (ceil(m / cw), nb), 288 threads: W2 = S^-1 W1 for the columns t in [c0, c0 + cw) of window
 // b, S = diag(1 / beta) + striu(G) with G = V^T V (its lower triangle read: G[k][l], l < k, is row k).
 // Right-looking back substitution: for k = nk - 1 .. 0, w_k = beta_k R_k, then R_l -= G[k][l] w_k
-// for l < k. Thread (rg, c) owns column c's rows l = rg (mod nrg) of R (shared memory); the owner
-// of row k - 1 computes w_{k-1} right after its update of that row in step k, so a step costs one
+// for l < k. Update thread (rg, c) owns column c's rows l = rg (mod nrg) of R (shared memory) and
+// applies each step to its rows below k - 1; a dedicated warp (lane = column) applies step k to
+// row k - 1 and publishes w_{k-1}, so the w chain overlaps the updates and a step costs one
 // barrier. Rows of G pass through shared memory in double-buffered chunks of kc rows (cp.async).
 // The reflectors are the scaled ones of k_bt_prep: beta_k 2^-2p_k on the diagonal of S^-1.
 // Writes W2^T (row t, entries k; zero for k >= nk and for t >= m_b).
-__global__ void __launch_bounds__(kTrsmThreads)
+__global__ void __launch_bounds__(kTrsmThreads + 32)
 k_bt_trsm(const int32_t *__restrict__ ext, int nb, int Mmax, int mmax, int cw, int kc,
           const double *__restrict__ G, const double *__restrict__ tau, const double *__restrict__ W1,
           double *__restrict__ W2T)
@@ -176,9 +177,12 @@ k_bt_trsm(const int32_t *__restrict__ ext, int nb, int Mmax, int mmax, int cw, i
             const int k = i / nc, c = i - k * nc;
             R[(size_t)k * cw + c] = W1b[(size_t)k * mmax + c];
         }
-        const int nrg = (int)blockDim.x / nc;
+        // threads [0, kTrsmThreads) update rows; the last warp computes and publishes the next w
+        const bool wwarp = (int)threadIdx.x >= kTrsmThreads;
+        const int wl = (int)threadIdx.x - kTrsmThreads;   // its lane: column wl
+        const int nrg = kTrsmThreads / nc;
         const int c = (int)threadIdx.x % nc, rg = (int)threadIdx.x / nc;
-        const bool act = rg < nrg;
+        const bool act = !wwarp && rg < nrg;
         const int nch = (nk + kc - 1) / kc;
         auto issue = [&](int ch) {                        // rows k = khi, khi - 1, ... of G, entries l < k
             double *dst = Gs + (size_t)(ch & 1) * kc * Mmax;
@@ -193,10 +197,10 @@ k_bt_trsm(const int32_t *__restrict__ ext, int nb, int Mmax, int mmax, int cw, i
         };
         issue(0);
         __syncthreads();                                  // R and the scaled betas loaded
-        if (act && (nk - 1) % nrg == rg) {                // w of the last row
-            const double wv = bs[nk - 1] * R[(size_t)(nk - 1) * cw + c];
-            W2s[(nk - 1) & 1][c] = wv;
-            W2Tb[(size_t)c * Mmax + nk - 1] = wv;
+        if (wwarp && wl < nc) {                           // w of the last row
+            const double wv = bs[nk - 1] * R[(size_t)(nk - 1) * cw + wl];
+            W2s[(nk - 1) & 1][wl] = wv;
+            W2Tb[(size_t)wl * Mmax + nk - 1] = wv;
         }
         for (int ch = 0; ch < nch; ch++) {
             if (ch + 1 < nch) {
@@ -211,16 +215,17 @@ k_bt_trsm(const int32_t *__restrict__ ext, int nb, int Mmax, int mmax, int cw, i
             for (int r = 0; r < kc; r++) {
                 const int k = khi - r;
                 if (k < 0) break;
-                if (act) {
-                    const double wk = W2s[k & 1][c];
-                    const double *grow = gch + (size_t)r * Mmax;
-                    // row k - 1 receives its last update in this step: its owner applies that first
-                    // and publishes w_{k-1}, overlapping the other rows' updates (rows l < k - 1)
-                    if (k >= 1 && (k - 1) % nrg == rg) {
-                        const double wv = bs[k - 1] * fma(-grow[k - 1], wk, R[(size_t)(k - 1) * cw + c]);
-                        W2s[(k - 1) & 1][c] = wv;
-                        W2Tb[(size_t)c * Mmax + k - 1] = wv;
+                const double *grow = gch + (size_t)r * Mmax;
+                if (wwarp) {
+                    // row k - 1 receives its last update in this step: the w warp applies it and
+                    // publishes w_{k-1} while the update threads work on rows l < k - 1
+                    if (k >= 1 && wl < nc) {
+                        const double wv = bs[k - 1] * fma(-grow[k - 1], W2s[k & 1][wl], R[(size_t)(k - 1) * cw + wl]);
+                        W2s[(k - 1) & 1][wl] = wv;
+                        W2Tb[(size_t)wl * Mmax + k - 1] = wv;
                     }
+                } else if (act) {
+                    const double wk = W2s[k & 1][c];
 #pragma unroll 4
                     for (int l = rg; l < k - 1; l += nrg) R[(size_t)l * cw + c] = fma(-grow[l], wk, R[(size_t)l * cw + c]);
                 }
@@ -345,8 +350,8 @@ cudaError_t launch_backtransform_wy(pfsm_handle_s *h, cudaStream_t st, bool refl
         while (cw < kTrsmMaxCols && (int64_t)nb * ((mnom + cw - 1) / cw) > (int64_t)sm_count()) cw++;
         while (cw > 1 && trsm_smem(Mmax, cw, kc) > kTrsmSmemCap) cw--;
         const dim3 grid((unsigned)((mnom + cw - 1) / cw), (unsigned)nb);
-        k_bt_trsm<<<grid, kTrsmThreads, trsm_smem(Mmax, cw, kc), st>>>(w.btExt, nb, Mmax, mmax, cw, kc, w.btG, w.tau,
-                                                                      w.btW1, w.btW2T);
+        k_bt_trsm<<<grid, kTrsmThreads + 32, trsm_smem(Mmax, cw, kc), st>>>(w.btExt, nb, Mmax, mmax, cw, kc, w.btG,
+                                                                           w.tau, w.btW1, w.btW2T);
         g_launches++;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

@@ -220,3 +220,32 @@ def test_compact_wy_backtransform_matches_reflector_by_reflector(pf, name, prec,
     print(f"{case} {name}: |X0 WY - X0 reflectors| = {dx:.2e}, |Gram difference| = {orth:.2e}")
     assert np.array_equal(em, e64)                      # the same window eigenvalues
     assert dx <= 1e-12 and orth <= 1e-12
+
+
+def test_concurrent_handles_on_two_streams_match_sequential_solves(pf):
+    """Each mixed handle forks work to its own side stream (the Eq. 11 split of A beside the window
+    reduction, the back-transform's reflector steps beside the eigenvalue kernels) and joins it
+    back through events. Two handles solving different problems at the same time on two streams
+    give bit for bit what each gives alone."""
+    pa, pb = wl.small_gapped(0), wl.diamond_like(1)
+    ha = pf.Handle(pa.n, pa.nblocks, halo=pa.halo, precision=pf.BF16_SPLIT)
+    hb = pf.Handle(pb.n, pb.nblocks, halo=pb.halo, precision=pf.BF16_SPLIT)
+    Aa, Pa, Ab, Pb = _dev(pa.A), _dev(pa.prev), _dev(pb.A), _dev(pb.prev)
+    la0, Va0 = (x.clone() for x in ha.solve(Aa, Pa))
+    lb0, Vb0 = (x.clone() for x in hb.solve(Ab, Pb))
+    torch.cuda.synchronize()
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = []
+    for _ in range(3):
+        with torch.cuda.stream(sa):
+            ra = ha.solve(Aa, Pa)
+        with torch.cuda.stream(sb):
+            rb = hb.solve(Ab, Pb)
+        torch.cuda.synchronize()
+        outs.append((ra[0].clone(), ra[1].clone(), rb[0].clone(), rb[1].clone()))
+    assert ha.status() == 0 and hb.status() == 0
+    for la, Va, lb, Vb in outs:
+        assert torch.equal(la, la0) and torch.equal(Va, Va0)
+        assert torch.equal(lb, lb0) and torch.equal(Vb, Vb0)
+    ha.close()
+    hb.close()
