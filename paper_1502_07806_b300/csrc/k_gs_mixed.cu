@@ -310,21 +310,30 @@ __global__ void __launch_bounds__(256)
 k_phi(const double *__restrict__ S2, const double *__restrict__ G, double *__restrict__ F, int64_t N, int last,
       int check, unsigned long long *__restrict__ emax, int32_t *status)
 {
+    // magnitudes compared as bit patterns (a NaN's exceeds every bound): no FP64 compare, one or
+    // two FP64 subtractions per entry (B300 retires one FP64 warp instruction per 16 cycles per SM)
+    constexpr unsigned long long kQuarter = 0x3FD0000000000000ull, kTiny = 0x3D3C25C268497682ull;   // 0.25, 1e-13
     const int64_t r = blockIdx.y;
     unsigned long long m = 0ull;
+    bool bad = false;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = r * N + c;
         double v = 0.0;
         if (c <= r) {
-            v = S2[o] - (c == r ? 1.0 : 0.0);
+            v = (c == r) ? S2[o] - 1.0 : S2[o];
             if (G) v -= G[o];
-            m = max(m, (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull);
-            if (check && !(fabs(v) < 0.25)) set_status(status, PFSM_ERR_NOT_SPD);   // no contraction (or NaN)
+            const unsigned long long a = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+            m = max(m, a);
+            bad |= check && !(a < kQuarter);               // no contraction (or NaN)
             if (c == r) v *= 0.5;
-            if (last && !(fabs(v - F[o]) <= 1e-13)) set_status(status, PFSM_ERR_NOT_SPD);
+            if (last) {
+                const unsigned long long d = (unsigned long long)__double_as_longlong(v - F[o]) & 0x7FFFFFFFFFFFFFFFull;
+                bad |= !(d <= kTiny);
+            }
         }
         F[o] = v;
     }
+    if (bad) set_status(status, PFSM_ERR_NOT_SPD);
     if (emax) {
         __shared__ unsigned long long wm[8];
 #pragma unroll
