@@ -112,7 +112,10 @@ typedef struct {
 void pfsm_default_params(pfsm_params_t *p);
 
 /* Creates a handle for N x N problems split into nblocks slices (1 <= nblocks <= N).
- * p may be NULL (defaults). Allocates all device workspace on the current device.
+ * p may be NULL (defaults). Allocates all device workspace on the current device. A handle of
+ * the mixed forms also creates one internal stream: a solve forks work that needs only A or only
+ * the window reduction onto it and joins it back before the call's later work, so callers see
+ * ordinary stream order (and a solve captured into a CUDA graph captures both streams).
  * Returns PFSM_ERR_INVALID_ARG for bad sizes/params, PFSM_ERR_OUT_OF_MEMORY or PFSM_ERR_CUDA. */
 int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t *out);
 
@@ -122,7 +125,9 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
  *                eigen-indices and place the slice boundaries
  *   eigvals_out  device, N FP64: Rayleigh quotient of vector k at index k (not re-sorted)
  *   V_out        device, N x N FP64: V_out[i*N + k] = component i of vector k
- * A and prev_eigvals must stay valid until the stream reaches the end of the call. */
+ * A and prev_eigvals must stay valid until the stream reaches the end of the call. In the mixed
+ * forms an eager solve (not being captured into a CUDA graph) reads one 8-byte value back in its
+ * Gram-Schmidt phase (a stream synchronisation) to choose the preconditioner's path. */
 int pfsm_solve(pfsm_handle_t h, const double *A, const double *prev_eigvals,
                double *eigvals_out, double *V_out, void *stream);
 

@@ -240,3 +240,43 @@ def test_autograd_function(pf):
     loss.backward()
     Vn = V.detach().cpu().numpy()
     np.testing.assert_allclose(A.grad.cpu().numpy(), Vn[:, :100] @ Vn[:, :100].T, rtol=0, atol=1e-12)
+
+
+# ----------------------------------------------------------------------- mixed forms, edges --
+
+@pytest.mark.parametrize("prec", [2, 1], ids=["bf16", "tf32"])
+@pytest.mark.parametrize("n,nb,halo,K", [
+    (1, 1, -1, 3), (2, 1, -1, 3), (2, 2, 0, 2), (8, 3, 1, 3), (17, 4, 2, 1), (64, 5, -1, 3),
+    (130, 7, 9, 4), (130, 1, -1, 3), (97, 6, 200, 3), (200, 9, 13, 0),
+])
+def test_mixed_ragged_and_edge_sizes(pf, orc, n, nb, halo, K, prec):
+    """The mixed forms on the same edge cases: windows of one or two rows (no reflectors), a single
+    slice, halo >= N, K = 0, products far smaller than one tensor-core tile. Same FP64 bars."""
+    p = wl.random_nearly_diagonal(n, seed=1000 + n + nb, sigma=2e-3, decay=12.0, nblocks=nb, halo=halo)
+    r = orc.pfsm(p.A, p.prev, nb, halo=halo, fs_iters=K)
+    g = _run(pf, p, fs_iters=K, precision=prec)
+    _check(r, g)
+
+
+@pytest.mark.parametrize("prec", [2, 1], ids=["bf16", "tf32"])
+def test_mixed_explicit_slices_cluster_snap_and_zero_coupling(pf, orc, prec):
+    """Explicit uneven slices, near-degenerate previous eigenvalues on slice boundaries (the plan
+    moves them), and a diagonal A (start vectors are unit vectors, V = I) in the mixed forms."""
+    p = wl.random_nearly_diagonal(150, seed=77, sigma=1e-3, nblocks=4, halo=10)
+    sizes = [10, 70, 33, 37]
+    _check(orc.pfsm(p.A, p.prev, 4, halo=10, slice_sizes=sizes), _run(pf, p, slice_sizes=sizes, precision=prec))
+    q = wl.random_nearly_diagonal(256, seed=91, sigma=1e-3, nblocks=4)
+    prev = q.prev.copy()
+    for k in (64, 128, 129, 192):
+        prev[k] = prev[k - 1] + 1e-7
+    prev = np.maximum.accumulate(prev)
+    A = q.A.copy()
+    A[np.diag_indices(256)] = prev
+    q.A, q.prev = A, prev
+    _check(orc.pfsm(A, prev, 4), _run(pf, q, precision=prec), cluster_tol=1e-6)
+    lam = np.sort(np.random.default_rng(9).uniform(-1, 1, 96))
+    d = wl.Problem("diag", np.diag(lam), lam, 4)
+    g = _run(pf, d, precision=prec)
+    assert g["status"] == 0
+    np.testing.assert_allclose(g["V"], np.eye(96), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(g["lam"], lam, rtol=0, atol=1e-15)
