@@ -82,6 +82,25 @@ def workload(n=None, nblocks=None, halo=None):
                "N": p.n, "nblocks": p.nblocks, "halo": h, "fs_iters": p.fs_iters}
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest x over the ranks of the default process group (x itself on one rank): a
+    replicated step's whole-job time is its slowest rank's. Any backend: the tensor lives on
+    `device` (CUDA for NCCL, CPU for gloo)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, world: int, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas that each processed `units_per_rank` units in
+    (at most) `seconds`: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def algorithmic_flops(plan, n, K):
     """Flop convention: eig sum(4/3 M^3 + 2 M^2 m) + FS 2N sum(M m) + 2N^3 + (K-1) 4N^3
     + overlap N^3 + Cholesky N^3/3 + triangular solve N^3 + Rayleigh 2N^3."""
@@ -306,16 +325,12 @@ def main():
         barrier()
         if sampler:
             sampler.__exit__(None, None, None)
-        total = sum(a.elapsed_time(b) for a, b in ev) / 1000.0
-        if world > 1:
-            t = torch.tensor([total], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
+        total = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / 1000.0, world)
         st = h.status()
         if st != 0:
             raise RuntimeError(f"{precision}: device status {pf.STATUS_NAMES.get(st, st)}")
         ph = {k: statistics.mean(pr[k] for pr in phases) for k in pf.PHASES[:5] + pf.SUB_PHASES}
-        return dict(h=h, lam=lam, V=V, total=total, value=world * steps / total, phases=ph,
+        return dict(h=h, lam=lam, V=V, total=total, value=job_rate(steps, world, total), phases=ph,
                     launches=launches, clocks=sampler.summary() if sampler else None,
                     gemm_tile_n=phases[-1].get("gemm_tile_n") if phases else None)
 
@@ -351,12 +366,8 @@ def main():
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
     barrier()
-    e2e_s = sum(e2e_ms) / 1000.0
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * args.steps / e2e_s
+    e2e_s = max_over_ranks(sum(e2e_ms) / 1000.0, world)
+    e2e_value = job_rate(args.steps, world, e2e_s)
     h2d = p.A.nbytes + p.prev.nbytes
     d2h = p.n * 8 + p.n * p.n * 8
 
