@@ -808,6 +808,117 @@ __device__ __forceinline__ double newton_step(const double *d, const double *e2,
     return (qc != 0.0) ? -pc / qc : 0.0;
 }
 
+// One Newton correction -p_M(x) / p_M'(x) for det(T - xI) (the recurrences of newton_step) split
+// over two warps, i.e. over two sub-partitions' FP64 pipes: warp 0 runs the p chain (three FP64
+// instructions per step) and hands d_i - x and p_i to warp 1 through shared memory in chunks of
+// kNewtonChunk steps; warp 1 runs the p' chain (two per step). Chunks are double-buffered; named
+// barriers 1/2 mark a buffer full, 3/4 empty, and 5 ends the pass, after which both warps hold p_M
+// and p_M' and return the same correction. Renormalisation (every fourth step, when the exponent of
+// the larger of p_i, p_{i-1} leaves 2^(+-400)) is decided from the p values alone, which both warps
+// see, and applied to both chains: exact powers of two, so the result is that of the unscaled
+// recurrences. Every lane of both warps must call it the same number of times with the same M.
+constexpr int kNewtonChunk = 16;
+
+struct NewtonShared {
+    double dx[2][kNewtonChunk][32];
+    double p[2][kNewtonChunk][32];
+    double pm[2][32], qm[2][32];                 // p_M and p_M' by pass parity
+};
+
+template <int ID> __device__ __forceinline__ void named_sync64() { asm volatile("bar.sync %0, 64;" ::"n"(ID) : "memory"); }
+template <int ID> __device__ __forceinline__ void named_arrive64() { asm volatile("bar.arrive %0, 64;" ::"n"(ID) : "memory"); }
+
+__device__ __forceinline__ double newton_step_split(const double *d, const double *e2, int M, double x, int warp,
+                                                    int lane, int parity, NewtonShared &sh)
+{
+    const int nch = (M - 1 + kNewtonChunk - 1) / kNewtonChunk;   // steps i = 1 .. M-1
+    double pc = clamp_dx(d[0] - x);
+    // exponent field of the larger of two values, and whether it left 1023 +- 400 (integer tests)
+    auto renorm_em = [](double a, double b, int &em) {
+        em = max(exp_of(a), exp_of(b));
+        return em > 1023 + 400 || em < 1023 - 400;
+    };
+    if (warp == 0) {
+        double pp = 1.0;
+        // step i from dx = d_i - x and f = e2_{i-1}; i = 0 mod 4 closes a block of four
+        auto step = [&](int buf, int j, int i, double dx, double f) {
+            const double pn = fma(dx, pc, -f * pp);
+            sh.dx[buf][j][lane] = dx;
+            sh.p[buf][j][lane] = pn;
+            pp = pc;
+            pc = pn;
+            int em;
+            if ((i & 3) == 0 && renorm_em(pc, pp, em)) {
+                const double sc = __hiloint2double((2046 - em) << 20, 0);   // 2^(1023 - em)
+                pc *= sc;
+                pp *= sc;
+            }
+        };
+        for (int c = 0; c < nch; c++) {
+            const int buf = c & 1, i0 = 1 + c * kNewtonChunk, cnt = min(kNewtonChunk, M - i0);
+            if (c >= 2) buf ? named_sync64<4>() : named_sync64<3>();   // warp 1 is done with chunk c - 2
+            if (cnt == kNewtonChunk) {
+#pragma unroll
+                for (int g = 0; g < kNewtonChunk; g += 4) {          // loads and d - x of four steps first
+                    double dx[4], f[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        dx[u] = clamp_dx(d[i0 + g + u] - x);
+                        f[u] = e2[i0 + g + u - 1];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; u++) step(buf, g + u, i0 + g + u, dx[u], f[u]);
+                }
+            } else {
+                for (int j = 0; j < cnt; j++) step(buf, j, i0 + j, clamp_dx(d[i0 + j] - x), e2[i0 + j - 1]);
+            }
+            buf ? named_arrive64<2>() : named_arrive64<1>();
+        }
+        sh.pm[parity][lane] = pc;
+    } else {
+        double qp = 0.0, qc = -1.0;
+        auto step = [&](int i, double dx, double pn, double f) {
+            const double qn = fma(dx, qc, -fma(f, qp, pc));
+            qp = qc;
+            qc = qn;
+            const double pprev = pc;
+            pc = pn;
+            int em;
+            if ((i & 3) == 0 && renorm_em(pc, pprev, em)) {
+                const double sc = __hiloint2double((2046 - em) << 20, 0);
+                pc *= sc;
+                qc *= sc;
+                qp *= sc;
+            }
+        };
+        for (int c = 0; c < nch; c++) {
+            const int buf = c & 1, i0 = 1 + c * kNewtonChunk, cnt = min(kNewtonChunk, M - i0);
+            buf ? named_sync64<2>() : named_sync64<1>();        // chunk c is in shared memory
+            if (cnt == kNewtonChunk) {
+#pragma unroll
+                for (int g = 0; g < kNewtonChunk; g += 4) {
+                    double dx[4], pn[4], f[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        dx[u] = sh.dx[buf][g + u][lane];
+                        pn[u] = sh.p[buf][g + u][lane];
+                        f[u] = e2[i0 + g + u - 1];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; u++) step(i0 + g + u, dx[u], pn[u], f[u]);
+                }
+            } else {
+                for (int j = 0; j < cnt; j++) step(i0 + j, sh.dx[buf][j][lane], sh.p[buf][j][lane], e2[i0 + j - 1]);
+            }
+            if (c < nch - 2) buf ? named_arrive64<4>() : named_arrive64<3>();   // warp 0 waits for chunks 2 .. nch-1
+        }
+        sh.qm[parity][lane] = qc;
+    }
+    named_sync64<5>();
+    const double p = sh.pm[parity][lane], q = sh.qm[parity][lane];
+    return (q != 0.0) ? -p / q : 0.0;
+}
+
 // The selected eigenvalues of T_b, the one at ascending position (k0 - s + t) for slice vector t.
 // Grid (ceil(mmax / EPC), nb), 32 EPC threads (EPC warps, 8 <= EPC <= 32), EPC eigenvalues per CTA;
 // the launch takes the smallest EPC that gives every CTA its own SM (the FP64 phase of step 3 is
@@ -817,12 +928,14 @@ __device__ __forceinline__ double newton_step(const double *d, const double *e2,
 //      eigenvalues below 32 interior points of the bracket (33 subintervals), and the bracket
 //      becomes the subinterval where the count passes the position; five rounds reach 8 FP32 ulps
 //      of the span (a bisection needs twenty counts one after another).
-//   3. Warp 0, one eigenvalue per lane (EPC lanes): up to three FP64 Newton steps on det(T - xI)
-//      from the bracket's midpoint (quadratic convergence while |x - lambda| is far below the gap;
-//      the warp stops once every lane's correction is below tol), then two FP64 Sturm counts at
-//      x -/+ tol (one pass) certify the position to within tol = 4 ulp |x| + 2 ulp of the span.
-//      A lane that fails falls back to FP64 bisection (on the widened FP32 bracket if
-//      its ends check out, else on the Gershgorin interval).
+//   3. Warps 0 and 1, one eigenvalue per lane (EPC lanes; the others repeat lane 0's): up to
+//      three FP64 Newton steps on det(T - xI) from the bracket's midpoint (quadratic convergence
+//      while |x - lambda| is far below the gap; the warps stop once every lane's correction is
+//      below tol), each step's p and p' chains on the two warps (newton_step_split); then one
+//      certifying FP64 Sturm count each, warp 0 at x - tol and warp 1 at x + tol, which place the
+//      eigenvalue within tol = 4 ulp |x| + 2 ulp of the span. A lane that fails runs up to three
+//      more Newton steps and both counts again, then FP64 bisection (on the widened FP32 bracket
+//      if its ends check out, else on the Gershgorin interval).
 __global__ void __launch_bounds__(1024)
 k_bisect(const int32_t *__restrict__ plan, int32_t nb, int32_t Mmax, int32_t mmax,
          const double *__restrict__ td, const double *__restrict__ te, double *__restrict__ sel_val)
@@ -836,6 +949,8 @@ k_bisect(const int32_t *__restrict__ plan, int32_t nb, int32_t Mmax, int32_t mma
     float *df = reinterpret_cast<float *>(smd + 2 * Mmax), *e2f = df + Mmax;
     __shared__ double s_lo, s_hi, s_sc, s_isc;
     __shared__ float brlo[32], brhi[32];
+    __shared__ int s_cnt_hi[32];
+    __shared__ NewtonShared s_newton;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double *bd = td + (size_t)b * Mmax, *be = te + (size_t)b * Mmax;
     if (warp == 0) {
@@ -895,28 +1010,49 @@ k_bisect(const int32_t *__restrict__ plan, int32_t nb, int32_t Mmax, int32_t mma
         }
     }
     __syncthreads();
-    if (warp != 0) return;
-    // 3. FP64 refinement and certification, lane -> eigenvalue blockIdx.x * EPC + lane
-    if (lane >= EPC) return;
-    const int t = blockIdx.x * EPC + lane;
-    if (t >= mb) return;
+    if (warp > 1) return;
+    // 3. FP64 refinement and certification, lane -> eigenvalue blockIdx.x * EPC + lane in both warps
+    //    (every lane of both warps reaches the named barrier below: lanes without an eigenvalue
+    //    repeat lane 0's)
+    const bool valid = lane < EPC && blockIdx.x * EPC + lane < mb;
+    const int ln = valid ? lane : 0;
+    const int t = blockIdx.x * EPC + ln;
     const int pos = k0 - s + t;
     const double satol = DBL_EPSILON * sspan;
-    const float flo = brlo[lane], fhi = brhi[lane];
+    const float flo = brlo[ln], fhi = brhi[ln];
     const double widen = 32.0 * FLT_EPSILON * sspan;
     const double blo = fmax(s_lo, (double)flo - widen), bhi = fmin(s_hi, (double)fhi + widen);
     double x = 0.5 * ((double)flo + (double)fhi);
-    const unsigned act = __activemask();
     for (int it = 0; it < 3; it++) {
-        const double xn = x + newton_step(d, e2, M, x);
+        const double xn = x + newton_step_split(d, e2, M, x, warp, lane, it & 1, s_newton);
         const bool inside = xn >= blo && xn <= bhi;  // else keep the last iterate
         const bool settled = !inside || fabs(xn - x) <= 4.0 * DBL_EPSILON * fabs(xn) + 2.0 * satol;
         if (inside) x = xn;
-        if (__all_sync(act, settled)) break;
+        if (__all_sync(0xffffffffu, settled)) break;
     }
-    const double tol = 4.0 * DBL_EPSILON * fabs(x) + 2.0 * satol;
-    const double xs[2] = {x - tol, x + tol};
+    double tol = 4.0 * DBL_EPSILON * fabs(x) + 2.0 * satol;
+    {
+        const double xs[1] = {warp == 0 ? x - tol : x + tol};
+        int cs[1];
+        sturm_counts<1>(d, e2, M, xs, cs);
+        if (warp == 1) s_cnt_hi[lane] = cs[0];
+        named_sync64<6>();                                        // warps 0 and 1, all lanes
+        if (warp == 1 || !valid) return;
+        if (cs[0] <= pos && s_cnt_hi[lane] > pos) {
+            sel_val[(size_t)b * mmax + t] = x * s_isc;
+            return;
+        }
+    }
     int cs[2];
+    for (int it = 0; it < 3; it++) {                             // FP64 Newton steps, p' in FP64
+        const double xn = x + newton_step(d, e2, M, x);
+        if (!(xn >= blo && xn <= bhi)) break;
+        const bool settled = fabs(xn - x) <= 4.0 * DBL_EPSILON * fabs(xn) + 2.0 * satol;
+        x = xn;
+        if (settled) break;
+    }
+    tol = 4.0 * DBL_EPSILON * fabs(x) + 2.0 * satol;
+    const double xs[2] = {x - tol, x + tol};
     sturm_counts<2>(d, e2, M, xs, cs);
     if (!(cs[0] <= pos && cs[1] > pos)) {
         double lo = blo, hi = bhi;
