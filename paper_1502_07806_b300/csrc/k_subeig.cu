@@ -1073,12 +1073,25 @@ k_bisect(const int32_t *__restrict__ plan, int32_t nb, int32_t Mmax, int32_t mma
     sel_val[(size_t)b * mmax + t] = x * s_isc;
 }
 
-// Reciprocal without an IEEE FP64 division (~640 cycles dependent on B300): FP32 estimate and two
-// Newton steps y <- y (2 - p y), accurate to about 1 ulp for |p| in FP32's normal range (pivots
-// are clamped to [eps ||T||, ~||T||] by the caller).
+// Reciprocal without an IEEE FP64 division (~640 cycles dependent on B300) and without F2F
+// conversions (they run on the FP64 pipe): the FP32 approximate reciprocal of p's leading 24 bits,
+// both conversions done by integer operations on the bit patterns, then two Newton steps
+// y <- y (2 - p y) (relative error 2^-22 -> 2^-44 -> rounding), about 1 ulp. |p| outside
+// [2^-125, 2^126) takes the FP64 division.
 __device__ __forceinline__ double fast_rcp(double p)
 {
-    double y = (double)__frcp_rn((float)p);
+    const int hi = __double2hiint(p);
+    const unsigned lo = (unsigned)__double2loint(p);
+    const int ev = (hi >> 20) & 0x7FF;
+    if ((unsigned)(ev - 898) > 250u) return 1.0 / p;
+    const float pf = __uint_as_float(((unsigned)hi & 0x80000000u) | ((unsigned)(ev - 896) << 23) |
+                                     ((unsigned)(hi & 0xFFFFF) << 3) | (lo >> 29));
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(pf));
+    const unsigned rb = __float_as_uint(rf);
+    double y = __hiloint2double((int)((rb & 0x80000000u) | ((((rb >> 23) & 0xFFu) + 896u) << 20) |
+                                      ((rb & 0x7FFFFFu) >> 3)),
+                                (int)(rb << 29));
     y = y * fma(-p, y, 2.0);
     y = y * fma(-p, y, 2.0);
     return y;
