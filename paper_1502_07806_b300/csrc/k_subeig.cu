@@ -933,10 +933,11 @@ __device__ __forceinline__ double newton_step_split(const double *d, const doubl
 //      while |x - lambda| is far below the gap; the warps stop once every lane's correction is
 //      below tol), each step's p and p' chains on the two warps (newton_step_split); then one
 //      certifying FP64 Sturm count each, warp 0 at x - tol and warp 1 at x + tol, which place the
-//      eigenvalue within tol = 4 ulp |x| + 2 ulp of the span. A lane that fails runs up to three
-//      more Newton steps and both counts again, then FP64 bisection (on the widened FP32 bracket
-//      if its ends check out, else on the Gershgorin interval).
-__global__ void __launch_bounds__(1024)
+//      eigenvalue within tol = 4 ulp |x| + 2 ulp of the span. While a lane fails, both warps run
+//      one more Newton step for it and count again (twice at most); a lane that still fails is
+//      resolved by warp 0 with an FP64 multisection over its 32 lanes (on the widened FP32
+//      bracket if its end counts enclose the position, else on the Gershgorin interval).
+__global__ void __launch_bounds__(1024, 1)
 k_bisect(const int32_t *__restrict__ plan, int32_t nb, int32_t Mmax, int32_t mmax,
          const double *__restrict__ td, const double *__restrict__ te, double *__restrict__ sel_val)
 {
@@ -949,7 +950,7 @@ k_bisect(const int32_t *__restrict__ plan, int32_t nb, int32_t Mmax, int32_t mma
     float *df = reinterpret_cast<float *>(smd + 2 * Mmax), *e2f = df + Mmax;
     __shared__ double s_lo, s_hi, s_sc, s_isc;
     __shared__ float brlo[32], brhi[32];
-    __shared__ int s_cnt_hi[32];
+    __shared__ int s_cnt[2][32];
     __shared__ NewtonShared s_newton;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double *bd = td + (size_t)b * Mmax, *be = te + (size_t)b * Mmax;
@@ -1023,54 +1024,66 @@ k_bisect(const int32_t *__restrict__ plan, int32_t nb, int32_t Mmax, int32_t mma
     const double widen = 32.0 * FLT_EPSILON * sspan;
     const double blo = fmax(s_lo, (double)flo - widen), bhi = fmin(s_hi, (double)fhi + widen);
     double x = 0.5 * ((double)flo + (double)fhi);
+    int npass = 0;
     for (int it = 0; it < 3; it++) {
-        const double xn = x + newton_step_split(d, e2, M, x, warp, lane, it & 1, s_newton);
+        const double xn = x + newton_step_split(d, e2, M, x, warp, lane, npass++ & 1, s_newton);
         const bool inside = xn >= blo && xn <= bhi;  // else keep the last iterate
         const bool settled = !inside || fabs(xn - x) <= 4.0 * DBL_EPSILON * fabs(xn) + 2.0 * satol;
         if (inside) x = xn;
         if (__all_sync(0xffffffffu, settled)) break;
     }
-    double tol = 4.0 * DBL_EPSILON * fabs(x) + 2.0 * satol;
-    {
+    // certification: warp 0 counts at x - tol, warp 1 at x + tol, and both warps read both
+    // counts, so they take the same decisions. While a lane fails (at most twice), both warps run
+    // one more Newton step for the failing lanes and count again. (Barrier 6 is reused only
+    // after a Newton step, whose barriers both warps pass after reading the counts.)
+    double tol = 0.0;
+    bool ok = false;
+    for (int round = 0; round < 3; round++) {
+        tol = 4.0 * DBL_EPSILON * fabs(x) + 2.0 * satol;
         const double xs[1] = {warp == 0 ? x - tol : x + tol};
-        int cs[1];
-        sturm_counts<1>(d, e2, M, xs, cs);
-        if (warp == 1) s_cnt_hi[lane] = cs[0];
+        int cs1[1];
+        sturm_counts<1>(d, e2, M, xs, cs1);
+        s_cnt[warp][lane] = cs1[0];
         named_sync64<6>();                                        // warps 0 and 1, all lanes
-        if (warp == 1 || !valid) return;
-        if (cs[0] <= pos && s_cnt_hi[lane] > pos) {
-            sel_val[(size_t)b * mmax + t] = x * s_isc;
-            return;
-        }
+        ok = s_cnt[0][lane] <= pos && s_cnt[1][lane] > pos;
+        if (__all_sync(0xffffffffu, ok) || round == 2) break;
+        const double xn = x + newton_step_split(d, e2, M, x, warp, lane, npass++ & 1, s_newton);
+        if (!ok && xn >= blo && xn <= bhi) x = xn;
     }
-    int cs[2];
-    for (int it = 0; it < 3; it++) {                             // FP64 Newton steps, p' in FP64
-        const double xn = x + newton_step(d, e2, M, x);
-        if (!(xn >= blo && xn <= bhi)) break;
-        const bool settled = fabs(xn - x) <= 4.0 * DBL_EPSILON * fabs(xn) + 2.0 * satol;
-        x = xn;
-        if (settled) break;
-    }
-    tol = 4.0 * DBL_EPSILON * fabs(x) + 2.0 * satol;
-    const double xs[2] = {x - tol, x + tol};
-    sturm_counts<2>(d, e2, M, xs, cs);
-    if (!(cs[0] <= pos && cs[1] > pos)) {
-        double lo = blo, hi = bhi;
-        const double xb[2] = {lo, hi};
-        sturm_counts<2>(d, e2, M, xb, cs);
-        if (!(cs[0] <= pos && cs[1] > pos)) { lo = s_lo; hi = s_hi; }
-        for (int it = 0; it < 256; it++) {
-            const double mid = 0.5 * (lo + hi);
-            if (mid <= lo || mid >= hi) break;
-            if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + satol) break;
-            const double xm[1] = {mid};
+    if (warp == 1) return;
+    // lanes still uncertified: warp 0 resolves them one at a time by FP64 multisection over its
+    // 32 lanes (31 subintervals per Sturm pass, about five bits, instead of one bit per pass of a
+    // lane's bisection), on the widened FP32 bracket while its end counts enclose the position,
+    // else on the Gershgorin interval
+    unsigned fail = __ballot_sync(0xffffffffu, valid && !ok);
+    while (fail) {
+        const int src = __ffs(fail) - 1;
+        fail &= fail - 1;
+        const int ps = __shfl_sync(0xffffffffu, pos, src);
+        double lo = __shfl_sync(0xffffffffu, blo, src), hi = __shfl_sync(0xffffffffu, bhi, src);
+        bool gersh = false;
+        for (int r = 0; r < 32; r++) {
+            const double w = (hi - lo) * (1.0 / 31.0);
+            const double xm[1] = {(lane == 31) ? hi : fma(w, (double)lane, lo)};
             int cm[1];
             sturm_counts<1>(d, e2, M, xm, cm);
-            if (cm[0] > pos) hi = mid; else lo = mid;
+            const unsigned above = __ballot_sync(0xffffffffu, cm[0] > ps);
+            if ((above & 1u) || !(above >> 31)) {                // the ends do not enclose it
+                if (gersh) break;
+                lo = s_lo;
+                hi = s_hi;
+                gersh = true;
+                continue;
+            }
+            const int f = __ffs(above) - 1;                       // first point above, >= 1
+            const double nlo = __shfl_sync(0xffffffffu, xm[0], f - 1), nhi = __shfl_sync(0xffffffffu, xm[0], f);
+            lo = nlo;
+            hi = nhi;
+            if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + satol) break;
         }
-        x = 0.5 * (lo + hi);
+        if (lane == src) x = 0.5 * (lo + hi);
     }
-    sel_val[(size_t)b * mmax + t] = x * s_isc;
+    if (valid) sel_val[(size_t)b * mmax + t] = x * s_isc;
 }
 
 // Reciprocal without an IEEE FP64 division (~640 cycles dependent on B300) and without F2F
