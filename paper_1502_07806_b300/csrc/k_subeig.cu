@@ -921,8 +921,8 @@ __device__ __forceinline__ double newton_step_split(const double *d, const doubl
 
 // The selected eigenvalues of T_b, the one at ascending position (k0 - s + t) for slice vector t.
 // Grid (ceil(mmax / EPC), nb), 32 EPC threads (EPC warps, 8 <= EPC <= 32), EPC eigenvalues per CTA;
-// the launch takes the smallest EPC that gives every CTA its own SM (the FP64 phase of step 3 is
-// one warp's dependent chain, and two such warps on one sub-partition share its FP64 pipe):
+// the launch takes the smallest EPC that gives every CTA its own SM (step 3 runs on warps 0 and 1,
+// one per sub-partition, and a second CTA's warps would share those sub-partitions' FP64 pipes):
 //   1. T is scaled by the power of two that brings its Gershgorin span into [1/2, 1) (exact).
 //   2. Warp w brackets eigenvalue w of the CTA by FP32 multisection: the 32 lanes count the
 //      eigenvalues below 32 interior points of the bracket (33 subintervals), and the bracket
