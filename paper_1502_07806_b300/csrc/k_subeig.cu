@@ -775,40 +775,10 @@ __device__ __forceinline__ int sturm3f(const float *d, const float *e2, int M, f
     return cnt;
 }
 
-// Newton correction -p_M(x) / p_M'(x) for det(T - xI) (scaled T), from the three-term recurrence
-// of the minors and of their derivatives p_i' = (d_i - x) p_{i-1}' - p_{i-1} - e2_{i-1} p_{i-2}',
-// both renormalised together every four steps (same bounds as sturm_counts); one DFMA per chain
-// and step on the dependent path.
-__device__ __forceinline__ double newton_step(const double *d, const double *e2, int M, double x)
-{
-    double pp = 1.0, pc = clamp_dx(d[0] - x), qp = 0.0, qc = -1.0;
-    int i = 1;
-    for (; i + 3 < M; i += 4) {                 // blocks of four: d - x and the loads go first
-        double dx[4], f[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) { dx[u] = clamp_dx(d[i + u] - x); f[u] = e2[i + u - 1]; }
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const double pn = fma(dx[u], pc, -f[u] * pp);
-            const double qn = fma(dx[u], qc, -fma(f[u], qp, pc));
-            pp = pc; qp = qc; pc = pn; qc = qn;
-        }
-        const int em = max(max(exp_of(pc), exp_of(pp)), max(exp_of(qc), exp_of(qp)));
-        if (em > 1023 + 400 || em < 1023 - 400) {
-            const double sc = __hiloint2double((2046 - em) << 20, 0);
-            pp *= sc; qp *= sc; pc *= sc; qc *= sc;
-        }
-    }
-    for (; i < M; i++) {                        // at most three steps after the last renormalisation
-        const double dx = clamp_dx(d[i] - x), f = e2[i - 1];
-        const double pn = fma(dx, pc, -f * pp);
-        const double qn = fma(dx, qc, -fma(f, qp, pc));
-        pp = pc; qp = qc; pc = pn; qc = qn;
-    }
-    return (qc != 0.0) ? -pc / qc : 0.0;
-}
-
-// One Newton correction -p_M(x) / p_M'(x) for det(T - xI) (the recurrences of newton_step) split
+// One Newton correction -p_M(x) / p_M'(x) for det(T - xI) (scaled T), from the three-term
+// recurrence of the leading minors p_i = (d_i - x) p_{i-1} - e2_{i-1} p_{i-2} and of their
+// derivatives p_i' = (d_i - x) p_{i-1}' - p_{i-1} - e2_{i-1} p_{i-2}' (d - x clamped as in
+// sturm_counts), one DFMA per chain and step on the dependent path. The two chains are split
 // over two warps, i.e. over two sub-partitions' FP64 pipes: warp 0 runs the p chain (three FP64
 // instructions per step) and hands d_i - x and p_i to warp 1 through shared memory in chunks of
 // kNewtonChunk steps; warp 1 runs the p' chain (two per step). Chunks are double-buffered; named
