@@ -6,7 +6,7 @@ window eigensolves (P windows of M = m + 2h rows, ~P M^3 work, one thread-block 
 against the start-vector quality the halo h sets, and its best value on a B300 depends on how
 the windows pack into the GPU's clusters, so it is measured rather than modelled:
 
-  * candidates: slice widths `WIDTHS` (64 .. 256, SURVEY config 4's range), as block counts
+  * candidates: slice widths `WIDTHS` (64 .. 256, the batch workload's range), as block counts
     round(N / m) clipped to [1, N];
   * each candidate is timed on the caller's own matrix (CUDA events around `pfsm_solve`, after a
     warm-up solve), and rejected when its largest residual ||A v - lambda v|| exceeds the default
@@ -32,7 +32,7 @@ _memory: dict[str, int] = {}
 
 
 def default_nblocks(n: int) -> int:
-    """The untuned layout: slices clamp(N/10, 64, 256) wide (SURVEY config 4's default)."""
+    """The untuned layout: slices clamp(N/10, 64, 256) wide (the batch workload's default)."""
     m = min(256, max(64, n // 10))
     return max(1, n // m)
 
