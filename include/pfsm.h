@@ -138,7 +138,10 @@ int pfsm_solve(pfsm_handle_t h, const double *A, const double *prev_eigvals,
  *   dV       device, N x N FP64 in V_out's layout, or NULL (treated as zeros)
  *   dA_out   device, N x N FP64, written in full (symmetric)
  * With recompute_v set, (lambda, V) are recomputed from the A of the last solve, which must
- * still be valid. Returns PFSM_ERR_NO_SOLVE if h has not solved yet. */
+ * still be valid. The FP64 form computes the three N x N products on the FP64 pipe; the mixed
+ * forms (PFSM_TF32_SPLIT, PFSM_BF16_SPLIT) compute them as FP64-accurate digit products on the
+ * tensor cores (each about sqrt(N) 2^-49 of its operand rows' largest entries, the rounding of
+ * an FP64 product). Returns PFSM_ERR_NO_SOLVE if h has not solved yet. */
 int pfsm_backward(pfsm_handle_t h, const double *dLambda, const double *dV, double *dA_out,
                   void *stream);
 
@@ -234,11 +237,15 @@ int pfsm_split_gemm_ex(int64_t rows, int64_t cols, int64_t K, const double *P, c
  *           place with `iters` iterations x <- x - alpha_k (A - eps_k I)^2 x
  *   eps, alpha  device, count FP64 shifts and steps
  * The only scratch, (A - eps I) X between the two products of each iteration, lives in one
- * fixed 8 MiB device array that every GPU loading this library holds until the process exits.
- * The first call on a device looks up that array's device address (cudaGetSymbolAddress), so
- * make the first call on each device outside any stream capture. All calls share the array:
- * calls that may overlap on the GPU (different streams, or several host threads) race on it and
- * must be serialised by the caller. Nothing in it needs clearing between calls. */
+ * fixed 8 MiB device array of the library. CUDA loads the array's module into a context
+ * lazily (the default module loading since CUDA 12.2), so the FIRST call on each device (and
+ * the first in any new context, e.g. after cudaDeviceReset) loads it and allocates those
+ * 8 MiB, then looks up the array's device address (cudaGetSymbolAddress) and caches it for
+ * that context. Make that first call before reserving the device's memory for a pool, and
+ * outside any stream capture; from then on the device holds the array until the process exits
+ * (or the context is destroyed) and no call allocates. All calls share the array: calls that
+ * may overlap on the GPU (different streams, or several host threads) race on it and must be
+ * serialised by the caller. Nothing in it needs clearing between calls. */
 int pfsm_fs_iterate_noalloc(int64_t N, int64_t count, const double *A, double *X,
                             const double *eps, const double *alpha, int32_t iters, void *stream);
 

@@ -540,7 +540,11 @@ int pfsm_backward(pfsm_handle_t h, const double *dLambda, const double *dV, doub
         if (rc != PFSM_OK) return rc;
     }
     if (h->timing) PFSM_CUDA(cudaEventRecord(h->ev[6], st));
-    PFSM_CUDA(launch_backward_f64(h, dLambda, dV, dA_out, st));
+    // FP64 form: the products on the FP64 pipe; mixed forms: FP64-accurate digit products
+    if (h->prm.precision == PFSM_FP64)
+        PFSM_CUDA(launch_backward_f64(h, dLambda, dV, dA_out, st));
+    else
+        PFSM_CUDA(launch_backward_mixed(h, dLambda, dV, dA_out, st));
     if (h->timing) PFSM_CUDA(cudaEventRecord(h->ev[7], st));
     h->last_stream = st;
     h->last_launches = (int32_t)g_launches;

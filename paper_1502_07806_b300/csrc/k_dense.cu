@@ -407,4 +407,47 @@ cudaError_t launch_backward_f64(pfsm_handle_s *h, const double *dLambda, const d
     return cudaGetLastError();
 }
 
+
+// The same adjoint with its three N^3 products as FP64-accurate digit products on the tensor
+// cores (the mixed forms' backward): each operand row is scaled by a power of two and cut into
+// seven base-128 digits, digit products of equal level are summed exactly in FP32 and the levels
+// combined to FP64 (k_gemm_oz.cu), so every product carries about sqrt(K) 2^-49 of its rows'
+// largest entries -- the rounding of the FP64 products it replaces. The elementwise steps
+// (F o G with the degenerate-pair mask, the final symmetrisation) are the FP64 kernels above.
+cudaError_t launch_backward_mixed(pfsm_handle_s *h, const double *dLambda, const double *dV,
+                                  double *dA_out, cudaStream_t st)
+{
+    Workspace &w = h->ws;
+    const int64_t N = h->N;
+    const int64_t ld = padded_ld(N);
+    SliceBuf dP{w.ozP, N, ld, OZ_SLICES, 0}, dQ{w.ozQ, N, ld, OZ_SLICES, 0};
+    cudaError_t e;
+    OzParams o{};
+    o.rows = (int)N; o.cols = (int)N; o.ldc = N; o.status = w.status;
+    // G = V^T dV: rows of X (vector k) against rows of dV^T (column l of dV)
+    if (dV) {
+        if ((e = launch_transpose(dV, w.W, N, st)) != cudaSuccess) return e;
+        if ((e = launch_oz_split(w.X, N, N, N, dP, w.ozeP, st)) != cudaSuccess) return e;
+        if ((e = launch_oz_split(w.W, N, N, N, dQ, w.ozeQ, st)) != cudaSuccess) return e;
+        o.C = w.S;
+        if ((e = launch_gemm_oz(dP, w.ozeP, dQ, w.ozeQ, o, st)) != cudaSuccess) return e;
+    } else {
+        if ((e = cudaMemsetAsync(w.S, 0, (size_t)N * N * sizeof(double), st)) != cudaSuccess) return e;
+    }
+    dim3 gm((unsigned)((N + 255) / 256), (unsigned)N);
+    k_adjoint_mix<<<gm, 256, 0, st>>>(w.S, N, w.lam, dLambda, h->prm.degen_tol); g_launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // Ut = V M^T (M symmetric): rows of V (output layout) against rows of M
+    if ((e = launch_oz_split(w.Vrm, N, N, N, dP, w.ozeP, st)) != cudaSuccess) return e;
+    if ((e = launch_oz_split(w.S, N, N, N, dQ, w.ozeQ, st)) != cudaSuccess) return e;
+    o.C = w.Y;
+    if ((e = launch_gemm_oz(dP, w.ozeP, dQ, w.ozeQ, o, st)) != cudaSuccess) return e;
+    // dA = V Ut^T: V's digits are still in dP
+    if ((e = launch_oz_split(w.Y, N, N, N, dQ, w.ozeQ, st)) != cudaSuccess) return e;
+    o.C = dA_out;
+    if ((e = launch_gemm_oz(dP, w.ozeP, dQ, w.ozeQ, o, st)) != cudaSuccess) return e;
+    k_symmetrize<<<gm, 256, 0, st>>>(dA_out, N); g_launches++;
+    return cudaGetLastError();
+}
+
 }  // namespace pfsm

@@ -5,9 +5,13 @@
 // device-wide synchronisation of cudaMalloc/cudaFree would stall work on other streams. For them
 // this file offers one entry point whose only scratch buffer -- the intermediate
 // Y = (A - eps I) X between the two products of each iteration -- lives in a fixed, file-scope
-// device array instead of handle workspace. Every GPU that loads the library holds that array
-// (kNoAllocMaxElems doubles, 8 MiB) until the process exits.
+// device array instead of handle workspace (kNoAllocMaxElems doubles, 8 MiB). The array belongs
+// to this file's module, which CUDA loads into a context lazily, at the first lookup of the
+// array's address: from the first call on a device (in a given context) until the process exits
+// (or that context is destroyed), that device holds the array.
 #include <mutex>
+
+#include <cuda.h>
 
 #include "pfsm_internal.cuh"
 
@@ -21,9 +25,48 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxElems];
 
 std::mutex g_setup_mutex;
-double *g_scratch_addr[kMaxDevices] = {};
 
-// Looks up (once per device, with that device current) the device address of the scratch array.
+// Per device: the context the address was looked up in (by its process-unique ID, so a context
+// created after cudaDeviceReset, or a caller's own driver-API context, is never mistaken for the
+// earlier one) and the array's device address in that context.
+struct ScratchEntry {
+    unsigned long long ctx_id;
+    double *addr;
+};
+ScratchEntry g_scratch[kMaxDevices] = {};
+
+// cuCtxGetCurrent and cuCtxGetId through the runtime's driver entry points, so that the library
+// keeps no link-time dependency on the driver library (it loads on machines without a GPU)
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+cudaError_t current_context_id(unsigned long long *id)
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *p1 = nullptr, *p2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &p2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q2 != cudaDriverEntryPointSuccess)
+            return cudaErrorInitializationError;
+        get_current = (CtxGetCurrentFn)p1;
+        get_id = (CtxGetIdFn)p2;
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS) return cudaErrorInitializationError;
+    if (!ctx) {
+        *id = 0;
+        return cudaSuccess;
+    }
+    return get_id(ctx, id) == CUDA_SUCCESS ? cudaSuccess : cudaErrorInitializationError;
+}
+
+// The device address of the scratch array in the current device's current context, looked up
+// with that device current the first time a context is seen and cached for later calls. The
+// lookup loads this module into the context (allocating the array) if it is not loaded yet.
 cudaError_t scratch_for_current_device(double **out)
 {
     int dev = 0;
@@ -31,13 +74,19 @@ cudaError_t scratch_for_current_device(double **out)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        double *p = nullptr;
-        e = cudaGetSymbolAddress((void **)&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
+    unsigned long long id = 0;
+    if ((e = current_context_id(&id)) != cudaSuccess) return e;
+    if (id != 0 && g_scratch[dev].addr && g_scratch[dev].ctx_id == id) {
+        *out = g_scratch[dev].addr;
+        return cudaSuccess;
     }
-    *out = g_scratch_addr[dev];
+    double *p = nullptr;
+    e = cudaGetSymbolAddress((void **)&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    // the lookup makes the runtime's primary context current if no context was
+    if ((e = current_context_id(&id)) != cudaSuccess) return e;
+    g_scratch[dev] = {id, p};
+    *out = p;
     return cudaSuccess;
 }
 

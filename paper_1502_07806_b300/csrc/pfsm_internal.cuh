@@ -304,5 +304,7 @@ cudaError_t configure_gs_mixed_kernels();
 cudaError_t launch_gram_schmidt_mixed(pfsm_handle_s *h, cudaStream_t st);
 cudaError_t launch_backward_f64(pfsm_handle_s *h, const double *dLambda, const double *dV,
                                 double *dA_out, cudaStream_t st);
+cudaError_t launch_backward_mixed(pfsm_handle_s *h, const double *dLambda, const double *dV,
+                                  double *dA_out, cudaStream_t st);
 
 }  // namespace pfsm

@@ -245,6 +245,39 @@ def test_backward_recompute_matches_kept(pf):
     np.testing.assert_array_equal(outs[0], outs[1])
 
 
+@pytest.mark.parametrize("prec", [2, 1], ids=["bf16", "tf32"])
+def test_mixed_backward_matches_oracle(pf, orc, prec):
+    """The mixed forms' backward (its three N^3 products as FP64-accurate digit products): against
+    the oracle's adjoint evaluated at the GPU's own (lambda, V), which isolates the backward's
+    arithmetic, and against the oracle's gradient from its own forward (the FP64 form's bar)."""
+    p = wl.small_gapped(1)
+    n = p.n
+    W = wl.gaussian((n, n), seed=17)
+    dlam = np.r_[np.ones(200), np.zeros(n - 200)]
+    h = pf.Handle(n, p.nblocks, precision=prec)
+    lam, V = h.solve(_dev(p.A), _dev(p.prev))
+    dA = h.backward(_dev(dlam), _dev(W)).cpu().numpy()
+    assert h.status() == 0
+    assert np.array_equal(dA, dA.T)
+    same = orc.backward(V.cpu().numpy(), lam.cpu().numpy(), dlam, W, tau=1e-8)
+    err_same = np.max(np.abs(dA - same)) / np.max(np.abs(same))
+    r = orc.pfsm(p.A, p.prev, p.nblocks)
+    ref = orc.backward(r.V, r.lam, dlam, W, tau=1e-8)
+    err = np.max(np.abs(dA - ref)) / np.max(np.abs(ref))
+    print(f"mixed backward: vs oracle adjoint at the same (lambda, V) {err_same:.2e}, vs oracle gradient {err:.2e}")
+    assert err_same < 1e-12, err_same
+    assert err < 1e-7, err
+    # sum of all eigenvalues: dA = I exactly up to the products' rounding
+    dI = h.backward(_dev(np.ones(n)), None).cpu().numpy()
+    np.testing.assert_allclose(dI, np.eye(n), rtol=0, atol=1e-12)
+    # recomputing (lambda, V) inside the backward gives the kept result bit for bit (the last
+    # solve's A and prev must stay valid for it)
+    h2 = pf.Handle(n, p.nblocks, precision=prec, recompute_v=True)
+    A2, prev2 = _dev(p.A), _dev(p.prev)
+    h2.solve(A2, prev2)
+    np.testing.assert_array_equal(h2.backward(_dev(dlam), _dev(W)).cpu().numpy(), dA)
+
+
 def test_autograd_function(pf):
     p = wl.small_gapped(3)
     h = pf.Handle(p.n, p.nblocks)
