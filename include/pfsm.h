@@ -106,6 +106,13 @@ typedef struct {
                               its products in FP64 in every precision; one residual read-back (a
                               stream synchronisation) per step (default 0) */
     double fs_tol;         /* its tolerance (default 0: the cap decides) */
+    int32_t reduction;     /* how the mixed forms reduce each window to tridiagonal form before
+                              its eigenpairs (Section II's submatrix eigensolves; same result up
+                              to rounding): 0 automatic (two-stage for windows of 1024 rows or
+                              more), 1 one-stage Householder on the FP64 pipe, 2 two-stage: dense
+                              to band (half-width 32) with FP64-accurate digit products on the
+                              tensor cores, band to tridiagonal by FP64 bulge chasing. The FP64
+                              form always reduces in one stage (default 0) */
 } pfsm_params_t;
 
 /* Fills *p with the defaults listed above. */

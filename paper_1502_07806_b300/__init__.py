@@ -42,7 +42,7 @@ class Params(ctypes.Structure):
                 ("degen_tol", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("recompute_v", ctypes.c_int32), ("slice_sizes", ctypes.POINTER(ctypes.c_int32)),
                 ("guard_max", ctypes.c_double), ("full_steps", ctypes.c_int32),
-                ("fs_adaptive", ctypes.c_int32), ("fs_tol", ctypes.c_double)]
+                ("fs_adaptive", ctypes.c_int32), ("fs_tol", ctypes.c_double), ("reduction", ctypes.c_int32)]
 
 
 class Profile(ctypes.Structure):
@@ -121,7 +121,8 @@ class Handle:
     def __init__(self, n: int, nblocks: int, halo: int = -1, fs_iters: int = 3,
                  alpha_theta: float = 1.0, cluster_tol: float = 1e-5, degen_tol: float = 1e-8,
                  precision: int = FP64, recompute_v: bool = False, slice_sizes=None,
-                 guard_max: float = 0.0, full_steps: int = 0, fs_adaptive: bool = False, fs_tol: float = 0.0):
+                 guard_max: float = 0.0, full_steps: int = 0, fs_adaptive: bool = False, fs_tol: float = 0.0,
+                 reduction: int = 0):
         lib = load_library()
         p = default_params()
         p.halo, p.fs_iters, p.alpha_theta = halo, fs_iters, alpha_theta
@@ -129,6 +130,7 @@ class Handle:
         p.recompute_v = int(bool(recompute_v))
         p.guard_max, p.full_steps = guard_max, full_steps
         p.fs_adaptive, p.fs_tol = int(bool(fs_adaptive)), fs_tol
+        p.reduction = reduction
         self._sizes = None
         if slice_sizes is not None:
             self._sizes = (ctypes.c_int32 * nblocks)(*[int(x) for x in slice_sizes])

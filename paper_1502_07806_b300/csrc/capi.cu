@@ -52,7 +52,8 @@ void free_ws(pfsm_handle_s *h)
                     w.sel_val, w.sel_vec, w.iiwork, w.slices, w.slE, w.slX, w.slY, w.slZ,
                     w.Z, w.dA, w.Linv, w.ozP, w.ozQ, w.ozeP, w.ozeQ, w.L32, w.R32, w.M32, w.F, w.VW, w.WV, w.tdP, w.tdQ, w.tdeP, w.tdeQ,
                     w.btG, w.btRT, w.btW1, w.btW2T, w.btY, w.btDA, w.btDB, w.btEA, w.btEB, w.btExt,
-                    w.ozA, w.ozeA};
+                    w.ozA, w.ozeA, w.bdA, w.bdV, w.bdeA, w.bdeV, w.bExt, w.bY, w.bT, w.bU, w.bXp, w.bBw,
+                    w.bR2, w.bT2};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     w = Workspace{};
@@ -64,6 +65,9 @@ constexpr size_t kSmemCap = 227 * 1024;
 // unblocked one saves (B300 spends ~64 cycles of an SMSP's FP64 pipe on every FP64 warp
 // instruction, shuffle reductions and redundant scalar work included); off until that changes.
 constexpr bool kUseBlockedReduction = false;
+// Window width from which the mixed forms reduce in two stages by default (the one-stage
+// reduction keeps windows up to a few hundred rows in a cluster's shared memory).
+constexpr int kTwoStageMinWidth = 1024;
 
 }  // namespace
 
@@ -86,6 +90,7 @@ void pfsm_default_params(pfsm_params_t *p)
     p->full_steps = 0;
     p->fs_adaptive = 0;
     p->fs_tol = 0.0;
+    p->reduction = 0;
 }
 
 const char *pfsm_last_error(void) { return g_last_error.c_str(); }
@@ -109,6 +114,8 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
         return fail(PFSM_ERR_INVALID_ARG, "pfsm_init: alpha_theta must be > 0, tolerances >= 0");
     if (prm.precision != PFSM_FP64 && prm.precision != PFSM_TF32_SPLIT && prm.precision != PFSM_BF16_SPLIT)
         return fail(PFSM_ERR_INVALID_ARG, "pfsm_init: unknown precision %d", prm.precision);
+    if (prm.reduction < 0 || prm.reduction > 2)
+        return fail(PFSM_ERR_INVALID_ARG, "pfsm_init: reduction must be 0, 1 or 2");
     int32_t mnom = (int32_t)((N + nblocks - 1) / nblocks);
     if (prm.slice_sizes) {
         int64_t tot = 0;
@@ -154,6 +161,14 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
             while (mc > 0 && tri_panel_smem(Mx, cl, mc) > kSmemCap) mc -= 8;
             h->tri_mcap = mc < 0 ? 0 : mc;
         }
+    }
+
+    // the mixed forms' two-stage reduction: chosen for wide windows (automatic) or on request,
+    // when its kernels' shared memory and schedule allow the window width
+    if (prm.precision != PFSM_FP64 && prm.reduction != 1 && band_reduction_fits(Mx, kSmemCap) &&
+        backtransform_wy_fits(Mx) && (prm.reduction == 2 || Mx >= kTwoStageMinWidth)) {
+        h->tri_two_stage = true;
+        h->tri_blocked = false;
     }
 
     Workspace &w = h->ws;
@@ -251,6 +266,26 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
             PFSM_ALLOC(w.btEB, nbx * mx);
             PFSM_ALLOC(w.btExt, 3 * nbx);
             if (e == cudaSuccess) e = configure_bt_wy_kernels();
+        }
+        if (h->tri_two_stage) {
+            const size_t Mx = (size_t)h->Mmax, nbx = (size_t)nblocks, KBx = (size_t)kBand;
+            const size_t ldk = (size_t)padded_ld(h->Mmax);
+            const size_t nt = (size_t)band_tasks_per_sweep(h->Mmax), nch = (Mx + 63) / 64;
+            uint8_t *d1 = nullptr, *d2 = nullptr;
+            PFSM_ALLOC(d1, (size_t)OZ_SLICES * nbx * Mx * ldk * 2);
+            PFSM_ALLOC(d2, (size_t)OZ_SLICES * nbx * KBx * ldk * 2);
+            w.bdA = d1; w.bdV = d2;
+            PFSM_ALLOC(w.bdeA, nbx * Mx);
+            PFSM_ALLOC(w.bdeV, nbx * KBx);
+            PFSM_ALLOC(w.bExt, nbx);
+            PFSM_ALLOC(w.bY, nbx * Mx * KBx);
+            PFSM_ALLOC(w.bT, nbx * KBx * KBx);
+            PFSM_ALLOC(w.bU, nbx * KBx * KBx);
+            PFSM_ALLOC(w.bXp, nbx * nch * KBx * KBx);
+            PFSM_ALLOC(w.bBw, nbx * (Mx + 2 * KBx) * 2 * KBx);
+            PFSM_ALLOC(w.bR2, nbx * Mx * nt * KBx);
+            PFSM_ALLOC(w.bT2, nbx * Mx * nt);
+            if (e == cudaSuccess) e = configure_band_kernels();
         }
         if (e == cudaSuccess) e = configure_gs_mixed_kernels();
         if (e == cudaSuccess) e = configure_tc_kernels();

@@ -1,0 +1,714 @@
+// Two-stage reduction of large windows to tridiagonal form (mixed forms; Section II's submatrix
+// eigensolves, whose cost the paper puts at the cube of the window width).
+//
+// A window of width M (2068 for the silicon-vacancy-like matrix, 1440 for the metal) does not fit
+// a thread-block cluster's shared memory, and the one-stage Householder reduction then streams the
+// whole trailing matrix through the FP64 pipe at every one of its M steps (2 M^3 FP64 operations,
+// about 2 s for 36 such windows). Here the reduction is split as in the two-stage symmetric
+// eigensolvers (Bischof, Lang and Sun's successive band reduction; the dense-to-band stage as in
+// LAPACK's blocked reduction, Golub & Van Loan Sec. 5.1.7 and 8.3.1):
+//
+//  1. dense -> band of half-width KB = 32, one panel of KB columns at a time:
+//       k_band_panel   Householder QR of the panel B[r0:M, c:c+KB] (r0 = c + KB) in a cluster of
+//                      CTAs (rows in shared memory, partial sums exchanged through distributed
+//                      shared memory), unit reflectors v_t (beta = 2) with T of the compact-WY
+//                      form I - V T V^T (LAPACK's larft recurrence), R written into the band;
+//       Y = A22 V      FP64-accurate digit product on the tensor cores (k_gemm_oz.cu);
+//       k_band_w/u/z   W = Y T, U = T^T (V^T W), Z = W - V U / 2 on the FP64 pipe;
+//       A22 -= V Z^T + Z V^T   digit product, subtracted into the window.
+//     The O(M^3) work of this stage runs on the tensor cores at FP64 accuracy.
+//  2. band -> tridiagonal by bulge chasing (k_band_chase, FP64): sweep s annihilates column s below
+//     its subdiagonal with one reflector on rows s+1 .. s+KB and then chases the bulge down the
+//     band, each task (s, i) annihilating the first column of the bulge the previous one created
+//     with a reflector on rows s+1+i KB .. s+(i+1) KB; the rest of each bulge is removed by the
+//     following sweeps. Tasks (s, i) run at time 3 s + i, so every time step's tasks touch disjoint
+//     band columns; one cluster per window, one warp per task, a cluster barrier per time step.
+//  3. the tridiagonal's eigenpairs as before (k_bisect, k_inverse_iter);
+//  4. y = Q1 Q2 z: Q2's reflectors applied to the eigenvectors z on the FP64 pipe (k_band_bt2),
+//     Q1's through the compact-WY back-transformation of k_bt_wy.cu (stage 1 stores its
+//     reflectors in the same row layout as the one-stage reduction: row k = c + t holds v_t on
+//     rows r0 + t .. M-1, tau[k] = beta_t).
+// The FP64 form keeps the one-stage reduction (no tensor cores).
+#include <cooperative_groups.h>
+#include <algorithm>
+
+#include "fp64_util.cuh"
+#include "pfsm_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace pfsm {
+
+namespace {
+
+constexpr int KB = kBand;
+constexpr int kPanelThreads = 256;
+constexpr int kChunk = 64;                 // rows per CTA of the W / Z kernels
+constexpr int kBtWarps = 8;                // k_band_bt2: warps per CTA (32 vectors per CTA)
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// CTA-wide sum in a fixed order (the same result in every CTA of a cluster)
+__device__ __forceinline__ double cta_sum(double v, double *red)
+{
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < nw; i++) t += red[i];
+    return t;
+}
+
+}  // namespace
+
+// Stage-1 panels of a window of width M: panel p (columns p KB .. p KB + KB - 1) exists while its
+// trailing rows r0 = (p + 1) KB leave at least two rows, r0 <= M - 2.
+__host__ __device__ int band_panels(int M) { return M >= KB + 2 ? (M - 2 - KB) / KB + 1 : 0; }
+
+// ---- set-up: the windows into their work matrices -------------------------------------------
+// Grid (ceil(Mmax / 8), nb), 256 threads: warp per row i of window b, G[i][j] = A[s + i][s + j].
+// The reflector rows no panel writes (k in [panels * KB, M - 2)) are zeroed with tau = 0.
+__global__ void __launch_bounds__(256)
+k_band_copy(const double *__restrict__ A, int64_t N, const int32_t *__restrict__ plan, int nb, int Mmax,
+            double *__restrict__ G, double *__restrict__ refl, double *__restrict__ tau)
+{
+    const int b = blockIdx.y;
+    const int64_t s0 = plan[2 * nb + b];
+    const int M = plan[3 * nb + b];
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (i < M) {
+        const double *src = A + (s0 + i) * N + s0;
+        double *dst = G + ((size_t)b * Mmax + i) * Mmax;
+        for (int j = lane; j < M; j += 32) dst[j] = src[j];
+    }
+    const int k = band_panels(M) * KB + i;      // one uncovered reflector row per warp
+    if (i < KB + 2 && k < M - 2) {
+        double *rr = refl + ((size_t)b * Mmax + k) * Mmax;
+        for (int j = k + 1 + lane; j < M; j += 32) rr[j] = 0.0;
+        if (lane == 0) tau[(size_t)b * Mmax + k] = 0.0;
+    }
+}
+
+// ---- stage 1: panel QR --------------------------------------------------------------------------
+// Cluster of CL CTAs per window (grid nb * CL), 256 threads. The panel's n = M - r0 rows are split
+// into CL contiguous chunks held in shared memory (rows x (KB + 1) doubles). Per column t: (A)
+// partial sums of the column's tail and its head entry, pulled by every CTA after a cluster
+// barrier; (B) partial dot products of the unit reflector with the later columns, pulled after a
+// second barrier, then the rank-1 update of the owned rows. Every CTA forms the same scalars from
+// the same partial sums in the same order. Outputs: reflector rows refl[c + t] (zero outside
+// rows r0 + t .. M-1), tau = 2 (0 for a column whose tail is already zero), T (KB x KB, upper),
+// R into the band of G (rows r0 .. r0 + KB - 1, columns c .. c + KB - 1), and extp[b] = M when the
+// window has this panel, else 0 (the later kernels of this panel read their extent from it).
+__global__ void __launch_bounds__(kPanelThreads, 1)
+k_band_panel(const int32_t *__restrict__ plan, int nb, int Mmax, int c, int rpc_cap, double *__restrict__ G,
+             double *__restrict__ refl, double *__restrict__ tau, double *__restrict__ Tb, int32_t *__restrict__ extp)
+{
+    cg::cluster_group cluster = cg::this_cluster();
+    const int CL = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int b = blockIdx.x / CL;
+    const int M = plan[3 * nb + b];
+    const int r0 = c + KB;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (r0 > M - 2) {                                  // no panel here (uniform over the cluster)
+        if (rank == 0 && tid == 0) extp[b] = 0;
+        return;
+    }
+    const int n = M - r0;
+    const int rpc = (n + CL - 1) / CL;
+    const int i0 = rank * rpc, i1 = min(n, i0 + rpc), nown = max(0, i1 - i0);
+    constexpr int LD = KB + 1;
+    extern __shared__ double sm[];
+    double *P = sm;                                    // rpc_cap x LD: owned rows of the panel
+    double *red = P + (size_t)rpc_cap * LD;            // 32: cta_sum scratch
+    double *hx = red + 32;                             // [0] partial tail^2, [1] head entry (owner)
+    double *wp = hx + 2;                               // KB partial dots of the current column step
+    double *wr = wp + KB;                              // 8 x KB per-warp partial dots
+    double *alph = wr + 8 * KB;                        // KB: R's diagonal (alpha_t)
+    double *bet = alph + KB;                           // KB: beta_t (2 or 0)
+    double *Gp = bet + KB;                             // KB x KB partial V^T V (own rows)
+    double *Tm = Gp + KB * KB;                         // KB x KB: T (rank 0)
+    double *Gs = Tm + KB * KB;                         // KB x KB: V^T V (rank 0)
+    double *Gb = G + (size_t)b * Mmax * Mmax;
+
+    for (int il = warp; il < nown; il += 8) P[il * LD + lane] = Gb[(size_t)(r0 + i0 + il) * Mmax + c + lane];
+    const int tmax = min(KB, n);
+    for (int t = tid; t < KB; t += blockDim.x) { alph[t] = 0.0; bet[t] = 0.0; }
+    __syncthreads();
+    cluster.sync();                                    // every CTA is running before remote access
+
+    for (int t = 0; t < tmax; t++) {
+        // (A) tail of column t (rows t+1 .. n-1) and its head entry (row t)
+        double part = 0.0;
+        for (int il = tid; il < nown; il += blockDim.x)
+            if (i0 + il > t) part = fma(P[il * LD + t], P[il * LD + t], part);
+        part = cta_sum(part, red);
+        const int owner = t / rpc;
+        if (tid == 0) {
+            hx[0] = part;
+            hx[1] = (owner == rank) ? P[(t - i0) * LD + t] : 0.0;
+        }
+        cluster.sync();
+        double tail2 = 0.0;
+        for (int r = 0; r < CL; r++) tail2 += cluster.map_shared_rank(hx, r)[0];
+        const double x0 = cluster.map_shared_rank(hx, owner)[1];
+        double inv = 0.0, v0 = 0.0, alpha = x0, beta = 0.0;
+        if (tail2 != 0.0) {
+            const double nn = fma(x0, x0, tail2);
+            const double xn = nn * scaled_rsqrt(nn);
+            alpha = (x0 >= 0.0) ? -xn : xn;
+            v0 = x0 - alpha;
+            inv = scaled_rsqrt(fma(v0, v0, tail2));
+            beta = 2.0;
+        }
+        // the unit reflector into column t of the owned rows >= t (all zero when beta = 0)
+        for (int il = tid; il < nown; il += blockDim.x) {
+            const int i = i0 + il;
+            if (i == t) P[il * LD + t] = v0 * inv;
+            else if (i > t) P[il * LD + t] *= inv;
+        }
+        if (tid == 0) { alph[t] = alpha; bet[t] = beta; }
+        __syncthreads();
+        // (B) partial w_j = v . column j over the owned rows >= t, j > t (lane j, rows by warp)
+        if (beta != 0.0) {
+            double acc = 0.0;
+            if (lane > t)
+                for (int il = warp; il < nown; il += 8)
+                    if (i0 + il >= t) acc = fma(P[il * LD + t], P[il * LD + lane], acc);
+            wr[warp * KB + lane] = acc;
+            __syncthreads();
+            if (warp == 0) {
+                double s = 0.0;
+                for (int q = 0; q < 8; q++) s += wr[q * KB + lane];
+                wp[lane] = s;
+            }
+        }
+        cluster.sync();
+        if (beta != 0.0) {
+            double wj = 0.0;
+            if (lane > t)
+                for (int r = 0; r < CL; r++) wj += cluster.map_shared_rank(wp, r)[lane];
+            if (lane > t)
+                for (int il = warp; il < nown; il += 8)
+                    if (i0 + il >= t) P[il * LD + lane] = fma(-2.0 * wj, P[il * LD + t], P[il * LD + lane]);
+        }
+        __syncthreads();
+    }
+    // reflector columns: V[i][t] = P[i][t] for i >= t (the entries above are R's)
+    auto vij = [&](int il, int t) -> double { return (t < tmax && i0 + il >= t) ? P[il * LD + t] : 0.0; };
+    // partial V^T V over the owned rows: thread (warp, lane) -> entries (p = warp + 8 q, lane)
+    {
+        double g[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int il = 0; il < nown; il++) {
+            const double vq = vij(il, lane);
+#pragma unroll
+            for (int q = 0; q < 4; q++) g[q] = fma(vij(il, warp + 8 * q), vq, g[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) Gp[(warp + 8 * q) * KB + lane] = g[q];
+    }
+    // outputs that need only this CTA's rows: reflector rows (zero above row t), R's rows
+    double *bref = refl + (size_t)b * Mmax * Mmax;
+    for (int t = 0; t < KB; t++)
+        for (int il = tid; il < nown; il += blockDim.x)
+            bref[(size_t)(c + t) * Mmax + r0 + i0 + il] = vij(il, t);
+    for (int il = warp; il < nown; il += 8) {
+        const int i = i0 + il;                         // R row i < KB: entries j >= i of row r0 + i
+        if (i < KB && lane >= i) Gb[(size_t)(r0 + i) * Mmax + c + lane] = (lane == i) ? alph[i] : P[il * LD + lane];
+    }
+    cluster.sync();
+    if (rank == 0) {
+        for (int e = tid; e < KB * KB; e += blockDim.x) {
+            double s = 0.0;
+            for (int r = 0; r < CL; r++) s += cluster.map_shared_rank(Gp, r)[e];
+            Gs[e] = s;
+        }
+        // reflector rows' entries between the row index and the reflector's first row are zero
+        for (int t = warp; t < KB; t += 8) {
+            double *rr = bref + (size_t)(c + t) * Mmax;
+            for (int j = c + t + 1 + lane; j < r0; j += 32) rr[j] = 0.0;
+            if (lane == 0) tau[(size_t)b * Mmax + c + t] = bet[t];
+        }
+        if (tid == 0) extp[b] = M;
+        __syncthreads();
+        // T (larft, forward, columnwise): T[t][t] = beta_t, T[0:t, t] = -beta_t T[0:t, 0:t] G[0:t, t]
+        if (warp == 0) {
+            for (int q = 0; q < KB; q++) Tm[q * KB + lane] = 0.0;
+            __syncwarp();
+            for (int t = 0; t < KB; t++) {
+                double s = 0.0;
+                if (lane < t)
+                    for (int p = lane; p < t; p++) s = fma(Tm[lane * KB + p], Gs[p * KB + t], s);
+                __syncwarp();
+                if (lane < t) Tm[lane * KB + t] = -bet[t] * s;
+                if (lane == t) Tm[t * KB + t] = bet[t];
+                __syncwarp();
+            }
+            double *Tbb = Tb + (size_t)b * KB * KB;
+            for (int q = 0; q < KB; q++) Tbb[q * KB + lane] = Tm[q * KB + lane];
+        }
+    }
+    cluster.sync();                                    // remote reads done before any CTA exits
+}
+
+// ---- stage 1: W = Y T (in place) and the chunk partials of V^T W ---------------------------------
+// Grid (ceil((Mmax - r0) / kChunk), nb), 256 threads. Rows r0 + bx kChunk .. of window b.
+__global__ void __launch_bounds__(256)
+k_band_w(const int32_t *__restrict__ extp, int Mmax, int c, const double *__restrict__ refl,
+         const double *__restrict__ Tb, double *__restrict__ Y, double *__restrict__ Xp, int nchunk)
+{
+    const int b = blockIdx.y, bx = blockIdx.x;
+    const int r0 = c + KB;
+    const int n = max(0, extp[b] - r0);
+    const int ib = bx * kChunk;
+    if (ib >= n) return;
+    const int rows = min(kChunk, n - ib);
+    __shared__ double T[KB][KB + 1], Ys[kChunk][KB + 1], Vs[kChunk][KB + 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const double *Tbb = Tb + (size_t)b * KB * KB;
+    for (int e = tid; e < KB * KB; e += 256) T[e / KB][e % KB] = Tbb[e];
+    double *Yb = Y + ((size_t)b * Mmax + r0 + ib) * KB;
+    for (int e = tid; e < kChunk * KB; e += 256) {
+        const int il = e / KB, q = e % KB;
+        Ys[il][q] = (il < rows) ? Yb[(size_t)il * KB + q] : 0.0;
+    }
+    const double *bref = refl + (size_t)b * Mmax * Mmax;
+    for (int p = warp; p < KB; p += 8)
+        for (int il = lane; il < kChunk; il += 32)
+            Vs[il][p] = (il < rows) ? bref[(size_t)(c + p) * Mmax + r0 + ib + il] : 0.0;
+    __syncthreads();
+    // W[il][q] = sum_{p <= q} Y[il][p] T[p][q]: thread -> row il = tid / 4, columns q = (tid % 4) + 4 j
+    {
+        const int il = tid >> 2, q0 = tid & 3;
+        double w[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int q = q0 + 4 * j;
+            double s = 0.0;
+            for (int p = 0; p <= q; p++) s = fma(Ys[il][p], T[p][q], s);
+            w[j] = s;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 8; j++) Ys[il][q0 + 4 * j] = w[j];
+    }
+    __syncthreads();
+    for (int e = tid; e < rows * KB; e += 256) Yb[e] = Ys[e / KB][e % KB];
+    // partial X[p][q] = sum_il V[il][p] W[il][q]: thread -> p = tid / 8, q = (tid % 8) + 8 j
+    {
+        const int p = tid >> 3, q0 = tid & 7;
+        double x[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int il = 0; il < rows; il++) {
+            const double v = Vs[il][p];
+#pragma unroll
+            for (int j = 0; j < 4; j++) x[j] = fma(v, Ys[il][q0 + 8 * j], x[j]);
+        }
+        double *xo = Xp + ((size_t)b * nchunk + bx) * KB * KB;
+#pragma unroll
+        for (int j = 0; j < 4; j++) xo[p * KB + q0 + 8 * j] = x[j];
+    }
+}
+
+// U = T^T X with X = sum over the window's chunks of the partials (fixed order). Grid nb, 256.
+__global__ void __launch_bounds__(256)
+k_band_u(const int32_t *__restrict__ extp, int c, const double *__restrict__ Tb, const double *__restrict__ Xp,
+         int nchunk, double *__restrict__ U)
+{
+    const int b = blockIdx.x;
+    const int n = max(0, extp[b] - (c + KB));
+    if (n == 0) return;
+    const int nch = (n + kChunk - 1) / kChunk;
+    __shared__ double X[KB][KB + 1], T[KB][KB + 1];
+    const double *Tbb = Tb + (size_t)b * KB * KB;
+    for (int e = threadIdx.x; e < KB * KB; e += 256) {
+        double s = 0.0;
+        for (int ch = 0; ch < nch; ch++) s += Xp[((size_t)b * nchunk + ch) * KB * KB + e];
+        X[e / KB][e % KB] = s;
+        T[e / KB][e % KB] = Tbb[e];
+    }
+    __syncthreads();
+    double *Ub = U + (size_t)b * KB * KB;
+    for (int e = threadIdx.x; e < KB * KB; e += 256) {
+        const int p = e / KB, q = e % KB;
+        double s = 0.0;
+        for (int r = 0; r <= p; r++) s = fma(T[r][p], X[r][q], s);
+        Ub[e] = s;
+    }
+}
+
+// Z = W - V U / 2 and the operands of the trailing update: row r0 + i of window b in VW = [v z],
+// WV = [z v] (rows b * Mmax + r0 + i, 2 KB entries). Grid (ceil((Mmax - r0) / kChunk), nb), 256.
+__global__ void __launch_bounds__(256)
+k_band_z(const int32_t *__restrict__ extp, int Mmax, int c, const double *__restrict__ refl,
+         const double *__restrict__ Y, const double *__restrict__ U, double *__restrict__ VW, double *__restrict__ WV)
+{
+    const int b = blockIdx.y, bx = blockIdx.x;
+    const int r0 = c + KB;
+    const int n = max(0, extp[b] - r0);
+    const int ib = bx * kChunk;
+    if (ib >= n) return;
+    const int rows = min(kChunk, n - ib);
+    __shared__ double Us[KB][KB + 1], Vs[kChunk][KB + 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const double *Ub = U + (size_t)b * KB * KB;
+    for (int e = tid; e < KB * KB; e += 256) Us[e / KB][e % KB] = Ub[e];
+    const double *bref = refl + (size_t)b * Mmax * Mmax;
+    for (int p = warp; p < KB; p += 8)
+        for (int il = lane; il < kChunk; il += 32)
+            Vs[il][p] = (il < rows) ? bref[(size_t)(c + p) * Mmax + r0 + ib + il] : 0.0;
+    __syncthreads();
+    const double *Wb = Y + ((size_t)b * Mmax + r0 + ib) * KB;
+    for (int e = tid; e < rows * KB; e += 256) {
+        const int il = e / KB, q = e % KB;
+        double s = 0.0;
+        for (int p = 0; p < KB; p++) s = fma(Vs[il][p], Us[p][q], s);
+        const double z = fma(-0.5, s, Wb[e]);
+        const size_t row = (size_t)b * Mmax + r0 + ib + il;
+        VW[row * 2 * KB + q] = Vs[il][q];
+        VW[row * 2 * KB + KB + q] = z;
+        WV[row * 2 * KB + q] = z;
+        WV[row * 2 * KB + KB + q] = Vs[il][q];
+    }
+}
+
+// ---- stage 2: the band into band storage --------------------------------------------------------
+// Bw[b] holds (Mmax + 2 KB) columns of 2 KB entries: Bw[b][j][d] = B[j + d][j] (lower band of
+// half-width 2 KB - 1, room for the bulges). Grid (ceil((Mmax + 2 KB) / 8), nb), 256 threads.
+__global__ void __launch_bounds__(256)
+k_band_extract(const int32_t *__restrict__ plan, int nb, int Mmax, const double *__restrict__ G,
+               double *__restrict__ Bw)
+{
+    const int b = blockIdx.y;
+    const int M = plan[3 * nb + b];
+    const int j = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (j >= Mmax + 2 * KB) return;
+    const double *Gb = G + (size_t)b * Mmax * Mmax;
+    double *col = Bw + ((size_t)b * (Mmax + 2 * KB) + j) * 2 * KB;
+    for (int d = lane; d < 2 * KB; d += 32)
+        col[d] = (j < M && d <= KB && j + d < M) ? Gb[(size_t)(j + d) * Mmax + j] : 0.0;
+}
+
+// ---- stage 2: bulge chasing -----------------------------------------------------------------------
+// One task (s, i) by one warp (see the file comment). Rows R = [a, a + L), a = s + 1 + i KB,
+// L = min(KB, M - a); the column it annihilates, col = s (i = 0) or a - KB; the blocks it touches:
+// left (rows R, columns col+1 .. a-1, only for i >= 1), diagonal (R x R, lower triangle stored) and
+// below (rows a + L .. a + L + KB - 1, columns R). Lane l: entry l of the reflector, column
+// col + 1 + l of the left block, column a + l of the diagonal block, row a + L + l of the block
+// below. The reflector goes to refl2 (KB entries, zero past L) and tau2.
+__device__ __forceinline__ void chase_task(double *__restrict__ B, int M, int s, int i, double *__restrict__ r2,
+                                           double *__restrict__ t2, double *vsh, double *wsh, int lane)
+{
+    auto at = [&](int r, int cc) -> double & { return B[(size_t)cc * (2 * KB) + (r - cc)]; };
+    const int a = s + 1 + i * KB;
+    const int L = min(KB, M - a);
+    const int col = (i == 0) ? s : a - KB;
+    const double x = (lane < L) ? at(a + lane, col) : 0.0;
+    const double tail2 = warp_sum(lane >= 1 ? x * x : 0.0);
+    const double x0 = __shfl_sync(0xffffffffu, x, 0);
+    double beta = 0.0, alpha = x0, v = 0.0;
+    if (tail2 != 0.0) {
+        const double nn = fma(x0, x0, tail2);
+        const double xn = nn * scaled_rsqrt(nn);
+        alpha = (x0 >= 0.0) ? -xn : xn;
+        const double v0 = x0 - alpha;
+        beta = 2.0 * scaled_rcp(fma(v0, v0, tail2));
+        v = (lane == 0) ? v0 : x;
+    }
+    r2[lane] = v;
+    if (lane == 0) *t2 = beta;
+    if (beta == 0.0) return;
+    if (lane < L) at(a + lane, col) = (lane == 0) ? alpha : 0.0;
+    vsh[lane] = v;
+    __syncwarp();
+    // left block: H from the left on columns col+1 .. a-1 (the rest of the previous bulge)
+    if (i >= 1 && lane < KB - 1) {
+        const int cc = col + 1 + lane;
+        double w = 0.0;
+        for (int r = 0; r < L; r++) w = fma(vsh[r], at(a + r, cc), w);
+        w *= beta;
+        for (int r = 0; r < L; r++) at(a + r, cc) = fma(-w, vsh[r], at(a + r, cc));
+    }
+    // diagonal block: D <- H D H = D - v w^T - w v^T, p = beta D v, w = p - (beta / 2)(v.p) v
+    double p = 0.0;
+    if (lane < L) {
+        for (int q = 0; q < L; q++) {
+            const double d = (q <= lane) ? at(a + lane, a + q) : at(a + q, a + lane);
+            p = fma(d, vsh[q], p);
+        }
+        p *= beta;
+    }
+    const double vp = warp_sum(v * p);
+    const double w = fma(-0.5 * beta * vp, v, p);
+    wsh[lane] = w;
+    __syncwarp();
+    if (lane < L)
+        for (int r = lane; r < L; r++)
+            at(a + r, a + lane) = fma(-vsh[r], w, fma(-wsh[r], v, at(a + r, a + lane)));
+    // below: rows e .. e + LB - 1, H from the right (this creates the next bulge)
+    const int e = a + L;
+    const int LB = min(KB, M - e);
+    if (lane < LB) {
+        double u = 0.0;
+        for (int q = 0; q < L; q++) u = fma(at(e + lane, a + q), vsh[q], u);
+        u *= beta;
+        for (int q = 0; q < L; q++) at(e + lane, a + q) = fma(-u, vsh[q], at(e + lane, a + q));
+    }
+    __syncwarp();
+}
+
+// Cluster of CL CTAs per window (grid nb * CL), NW warps each; warp g of the window runs the
+// sweeps s = g (mod CL NW), task (s, i) at time step 3 s + i; a cluster barrier (with a fence for
+// the band's global-memory writes) ends every time step. Needs 3 CL NW > the tasks of sweep 0 so
+// that a warp's consecutive sweeps never overlap in time. Finally td/te of the tridiagonal.
+__global__ void __launch_bounds__(32 * kChaseWarps, 1)
+k_band_chase(const int32_t *__restrict__ plan, int nb, int Mmax, int NT, double *__restrict__ Bw,
+             double *__restrict__ refl2, double *__restrict__ tau2, double *__restrict__ td, double *__restrict__ te)
+{
+    cg::cluster_group cluster = cg::this_cluster();
+    const int CL = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int b = blockIdx.x / CL;
+    const int M = plan[3 * nb + b];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int W = CL * kChaseWarps, g = rank * kChaseWarps + warp;
+    __shared__ double vsh[kChaseWarps][KB], wsh[kChaseWarps][KB];
+    double *B = Bw + (size_t)b * (Mmax + 2 * KB) * 2 * KB;
+    const int S = M - 2;                               // sweeps 0 .. M-3
+    if (S > 0) {
+        const int nt0 = (M - 2 + KB - 1) / KB;         // tasks of sweep 0
+        const int tend = 3 * (S - 1) + nt0;
+        for (int t = 0; t < tend; t++) {
+            const int smax = t / 3;
+            if (smax >= g) {
+                const int s = g + ((smax - g) / W) * W;
+                const int i = t - 3 * s;
+                if (s < S && i < (M - 2 - s + KB - 1) / KB) {
+                    const size_t slot = ((size_t)b * Mmax + s) * NT + i;
+                    chase_task(B, M, s, i, refl2 + slot * KB, tau2 + slot, vsh[warp], wsh[warp], lane);
+                }
+            }
+            __threadfence();
+            cluster.sync();
+        }
+    }
+    double *btd = td + (size_t)b * Mmax, *bte = te + (size_t)b * Mmax;
+    for (int j = rank * blockDim.x + threadIdx.x; j < M; j += CL * blockDim.x) {
+        btd[j] = B[(size_t)j * 2 * KB];
+        bte[j] = (j + 1 < M) ? B[(size_t)j * 2 * KB + 1] : 0.0;
+    }
+}
+
+// ---- back-transformation of stage 2: y = Q2 z ----------------------------------------------------
+// Yt[b] holds the window's eigenvectors transposed (row j, column t; ld = mmax). Grid
+// (ceil(mmax / 32), nb), 256 threads: lane = vector t0 + lane, the reflectors of a sweep (disjoint
+// rows) spread over the 8 warps, sweeps in reverse order with a CTA barrier between them.
+__global__ void __launch_bounds__(32 * kBtWarps)
+k_band_bt2(const int32_t *__restrict__ plan, int nb, int Mmax, int mmax, int NT, const double *__restrict__ refl2,
+           const double *__restrict__ tau2, double *__restrict__ Yt)
+{
+    const int b = blockIdx.y;
+    const int mb = plan[nb + b], M = plan[3 * nb + b];
+    const int t0 = blockIdx.x * 32;
+    if (t0 >= mb) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double *Y = Yt + (size_t)b * Mmax * mmax + t0 + lane;
+    const bool act = t0 + lane < mb;
+    for (int s = M - 3; s >= 0; s--) {
+        const int ntask = (M - 2 - s + KB - 1) / KB;
+        for (int i = warp; i < ntask; i += kBtWarps) {
+            const size_t slot = ((size_t)b * Mmax + s) * NT + i;
+            const double beta = tau2[slot];
+            if (beta == 0.0) continue;
+            const double vl = refl2[slot * KB + lane];
+            const int a = s + 1 + i * KB;
+            const int L = min(KB, M - a);
+            double d = 0.0;
+            for (int r = 0; r < L; r++) {
+                const double vr = __shfl_sync(0xffffffffu, vl, r);
+                if (act) d = fma(vr, Y[(size_t)(a + r) * mmax], d);
+            }
+            d *= beta;
+            for (int r = 0; r < L; r++) {
+                const double vr = __shfl_sync(0xffffffffu, vl, r);
+                if (act) Y[(size_t)(a + r) * mmax] = fma(-d, vr, Y[(size_t)(a + r) * mmax]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// sel_vec (rows t, entries j) <-> Yt (rows j, columns t), 32 x 32 tiles. Grid
+// (ceil(Mmax / 32), ceil(mmax / 32), nb), 256 threads.
+__global__ void __launch_bounds__(256)
+k_band_transpose(const int32_t *__restrict__ plan, int nb, int Mmax, int mmax, bool to_rows,
+                 double *__restrict__ sel_vec, double *__restrict__ Yt)
+{
+    __shared__ double tile[32][33];
+    const int b = blockIdx.z;
+    const int mb = plan[nb + b], M = plan[3 * nb + b];
+    const int j0 = blockIdx.x * 32, t0 = blockIdx.y * 32;
+    if (j0 >= M || t0 >= mb) return;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    double *sv = sel_vec + (size_t)b * mmax * Mmax;
+    double *yt = Yt + (size_t)b * Mmax * mmax;
+    if (!to_rows) {
+        for (int q = ty; q < 32; q += 8) {
+            const int t = t0 + q, j = j0 + tx;
+            tile[q][tx] = (t < mb && j < M) ? sv[(size_t)t * Mmax + j] : 0.0;
+        }
+        __syncthreads();
+        for (int q = ty; q < 32; q += 8) {
+            const int j = j0 + q, t = t0 + tx;
+            if (j < M && t < mb) yt[(size_t)j * mmax + t] = tile[tx][q];
+        }
+    } else {
+        for (int q = ty; q < 32; q += 8) {
+            const int j = j0 + q, t = t0 + tx;
+            tile[q][tx] = (j < M && t < mb) ? yt[(size_t)j * mmax + t] : 0.0;
+        }
+        __syncthreads();
+        for (int q = ty; q < 32; q += 8) {
+            const int t = t0 + q, j = j0 + tx;
+            if (t < mb && j < M) sv[(size_t)t * Mmax + j] = tile[tx][q];
+        }
+    }
+}
+
+// ---- host side ------------------------------------------------------------------------------------
+
+size_t band_panel_smem(int Mmax)
+{
+    const int rpc = (Mmax - KB + kPanelCL - 1) / kPanelCL;
+    return ((size_t)rpc * (KB + 1) + 32 + 2 + KB + 8 * KB + 2 * KB + 3 * KB * KB) * sizeof(double);
+}
+
+bool band_reduction_fits(int Mmax, size_t smem_cap)
+{
+    if (Mmax < 2 * KB + 2) return false;
+    const int nt0 = (Mmax - 2 + KB - 1) / KB;
+    return band_panel_smem(Mmax) <= smem_cap && nt0 < 3 * kChaseCL * kChaseWarps;
+}
+
+int band_tasks_per_sweep(int Mmax) { return (Mmax + KB - 1) / KB; }
+
+cudaError_t configure_band_kernels()
+{
+    int dev = 0, cap = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_band_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+}
+
+cudaError_t launch_band_reduction(pfsm_handle_s *h, const double *A, cudaStream_t st)
+{
+    Workspace &w = h->ws;
+    const int nb = h->nb, Mmax = h->Mmax;
+    const int32_t *plan = w.plan;
+    const int64_t MM = (int64_t)Mmax * Mmax;
+    cudaError_t e;
+    k_band_copy<<<dim3((unsigned)((Mmax + 7) / 8), (unsigned)nb), 256, 0, st>>>(A, h->N, plan, nb, Mmax, w.iiwork,
+                                                                                 w.refl, w.tau);
+    g_launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int np = band_panels(Mmax);
+    const int nchunk = (Mmax + kChunk - 1) / kChunk;
+    const int rpc_cap = (Mmax - KB + kPanelCL - 1) / kPanelCL;
+    const size_t psmem = band_panel_smem(Mmax);
+    for (int p = 0; p < np; p++) {
+        const int c = p * KB, r0 = c + KB;
+        {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)(nb * kPanelCL));
+            cfg.blockDim = dim3(kPanelThreads);
+            cfg.dynamicSmemBytes = psmem;
+            cfg.stream = st;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = kPanelCL;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            if ((e = counted(cudaLaunchKernelEx(&cfg, k_band_panel, plan, nb, Mmax, c, rpc_cap, w.iiwork, w.refl,
+                                                w.tau, w.bT, w.bExt))) != cudaSuccess)
+                return e;
+        }
+        // Y = A22 V: digits of A22 (rows r0 .. M-1, entries r0 .. M-1) and of V^T (reflector rows)
+        const int64_t ldk = padded_ld(Mmax - r0);
+        const SliceBuf dA{w.bdA, (int64_t)nb * Mmax, ldk, OZ_SLICES, 0};
+        const SliceBuf dV{w.bdV, (int64_t)nb * KB, ldk, OZ_SLICES, 0};
+        if ((e = launch_oz_split_win(w.iiwork, MM, Mmax, r0, r0, w.bExt, r0, 0, Mmax - r0, nb, dA, Mmax, r0, w.bdeA,
+                                     st)) != cudaSuccess)
+            return e;
+        if ((e = launch_oz_split_win(w.refl, MM, Mmax, c, r0, w.bExt, r0, KB, KB, nb, dV, KB, 0, w.bdeV, st)) !=
+            cudaSuccess)
+            return e;
+        OzParams o{};
+        o.rows = Mmax; o.cols = KB; o.cols_from_zero = 1; o.C = w.bY; o.ldc = KB; o.status = w.status;
+        o.zrow = Mmax; o.zrow_q = KB; o.zc = (int64_t)Mmax * KB; o.row_base = r0; o.ext = w.bExt;
+        if ((e = launch_gemm_oz(dA, w.bdeA, dV, w.bdeV, o, st, nb)) != cudaSuccess) return e;
+        // W = Y T, U = T^T V^T W, Z = W - V U / 2 -> [V Z], [Z V]
+        const dim3 gch((unsigned)((Mmax - r0 + kChunk - 1) / kChunk), (unsigned)nb);
+        k_band_w<<<gch, 256, 0, st>>>(w.bExt, Mmax, c, w.refl, w.bT, w.bY, w.bXp, nchunk);
+        g_launches++;
+        k_band_u<<<nb, 256, 0, st>>>(w.bExt, c, w.bT, w.bXp, nchunk, w.bU);
+        g_launches++;
+        k_band_z<<<gch, 256, 0, st>>>(w.bExt, Mmax, c, w.refl, w.bY, w.bU, w.VW, w.WV);
+        g_launches++;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // A22 -= [V Z] [Z V]^T (rows and columns r0 .. M-1 of every window that had this panel)
+        const int64_t srows = (int64_t)nb * Mmax;
+        const SliceBuf dP{w.tdP, srows, 2 * KB, OZ_SLICES, 0}, dQ{w.tdQ, srows, 2 * KB, OZ_SLICES, 0};
+        if ((e = launch_oz_split(w.VW, srows, 2 * KB, 2 * KB, dP, w.tdeP, st)) != cudaSuccess) return e;
+        if ((e = launch_oz_split(w.WV, srows, 2 * KB, 2 * KB, dQ, w.tdeQ, st)) != cudaSuccess) return e;
+        OzParams u{};
+        u.rows = Mmax; u.cols = Mmax; u.C = w.iiwork; u.ldc = Mmax; u.sub = 1; u.status = w.status;
+        u.zrow = Mmax; u.zc = MM; u.row_base = r0; u.ext = w.bExt;
+        if ((e = launch_gemm_oz(dP, w.tdeP, dQ, w.tdeQ, u, st, nb)) != cudaSuccess) return e;
+    }
+    k_band_extract<<<dim3((unsigned)((Mmax + 2 * KB + 7) / 8), (unsigned)nb), 256, 0, st>>>(plan, nb, Mmax, w.iiwork,
+                                                                                         w.bBw);
+    g_launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nb * kChaseCL));
+    cfg.blockDim = dim3(32 * kChaseWarps);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kChaseCL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return counted(cudaLaunchKernelEx(&cfg, k_band_chase, plan, nb, Mmax, band_tasks_per_sweep(Mmax), w.bBw, w.bR2,
+                                      w.bT2, w.td, w.te));
+}
+
+cudaError_t launch_band_backtransform(pfsm_handle_s *h, cudaStream_t st)
+{
+    Workspace &w = h->ws;
+    const int nb = h->nb, Mmax = h->Mmax, mmax = h->mmax;
+    double *Yt = w.iiwork;                             // free again after the inverse iteration
+    const dim3 gt((unsigned)((Mmax + 31) / 32), (unsigned)((mmax + 31) / 32), (unsigned)nb);
+    k_band_transpose<<<gt, 256, 0, st>>>(w.plan, nb, Mmax, mmax, false, w.sel_vec, Yt);
+    g_launches++;
+    k_band_bt2<<<dim3((unsigned)((mmax + 31) / 32), (unsigned)nb), 32 * kBtWarps, 0, st>>>(
+        w.plan, nb, Mmax, mmax, band_tasks_per_sweep(Mmax), w.bR2, w.bT2, Yt);
+    g_launches++;
+    k_band_transpose<<<gt, 256, 0, st>>>(w.plan, nb, Mmax, mmax, true, w.sel_vec, Yt);
+    g_launches++;
+    return cudaGetLastError();
+}
+
+}  // namespace pfsm

@@ -75,24 +75,25 @@ __device__ __forceinline__ unsigned short oz_digit_bf16(uint32_t field)
     return (unsigned short)(__float_as_uint(f) >> 16);
 }
 
+// The digits of one row of `cols` entries (lane `lane` of one warp): exponent e of the row's
+// largest |entry| into *eout and the S digit slices of entry c at out[c + s * sstride]; columns
+// cols .. fill_to - 1 get zero digits. diag_col >= 0: that entry is taken as 0 (its value stored
+// in *dval when dval is given).
 template <typename T>
-__global__ void k_oz_split(const T *__restrict__ src, int64_t rows, int64_t cols, int64_t ld,
-                           __nv_bfloat16 *__restrict__ dst, int64_t sl_ld, int64_t sstride,
-                           int32_t *__restrict__ exps, int zero_diag, double *__restrict__ d)
+__device__ __forceinline__ void oz_split_row(const T *__restrict__ x, int64_t cols, int64_t fill_to, int64_t diag_col,
+                                             double *dval, unsigned short *__restrict__ out, int64_t sstride,
+                                             int32_t *eout, int lane)
 {
     static_assert(OZ_SLICES == 7 && oz::BETA == 7, "digit fields are laid out for seven 7-bit digits");
-    const int lane = threadIdx.x & 31;
-    const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (r >= rows) return;
-    const T *x = src + r * ld;
-    auto val = [&](int64_t c) -> double { return (zero_diag && c == r) ? 0.0 : (double)x[c]; };
-    if (zero_diag && lane == 0 && d) d[r] = (double)x[r];
+    const bool zero_diag = diag_col >= 0;
+    auto val = [&](int64_t c) -> double { return (zero_diag && c == diag_col) ? 0.0 : (double)x[c]; };
+    if (zero_diag && lane == 0 && dval) *dval = (double)x[diag_col];
     unsigned long long mb = 0ull;
     for (int64_t c = lane; c < cols; c += 32) {
         unsigned long long b;
         if (sizeof(T) == 8) b = oz_bits((double)x[c]) & 0x7FFFFFFFFFFFFFFFull;
         else b = (unsigned long long)(__float_as_uint((float)x[c]) & 0x7FFFFFFFu);
-        mb = max(mb, (zero_diag && c == r) ? 0ull : b);
+        mb = max(mb, (zero_diag && c == diag_col) ? 0ull : b);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
@@ -107,12 +108,11 @@ __global__ void k_oz_split(const T *__restrict__ src, int64_t rows, int64_t cols
         if (ex > 0) e = ex - 126;
         else if (mb != 0ull) e = -117 - __clz((int)mb);
     }
-    if (lane == 0) exps[r] = e;
+    if (lane == 0) *eout = e;
     // one digit row: q from t = x 2^(QBITS - e) + 1.5 2^52 (|x 2^(QBITS - e)| < 2^QBITS <= 2^51, so
     // the sum is rounded to an integer held in the low significand bits)
     constexpr double kMagic = 6755399441055744.0;                     // 1.5 2^52
     constexpr long long kBias = 64ll * (((1ll << 42) - 1) / 127);     // sum_{i < 6} 64 128^i
-    unsigned short *out = reinterpret_cast<unsigned short *>(dst + r * sl_ld);
     auto emit = [&](int64_t c, double t) {
         const long long q = (long long)(oz_bits(t) - oz_bits(kMagic)) + kBias;
         const uint32_t lo = (uint32_t)q, hi = (uint32_t)((unsigned long long)q >> 32);
@@ -133,6 +133,43 @@ __global__ void k_oz_split(const T *__restrict__ src, int64_t rows, int64_t cols
         const double sc1 = ldexp(1.0, sh / 2), sc2 = ldexp(1.0, sh - sh / 2);
         for (int64_t c = lane; c < cols; c += 32) emit(c, fma(val(c) * sc1, sc2, kMagic));
     }
+    for (int64_t c = cols + lane; c < fill_to; c += 32)
+#pragma unroll
+        for (int s = 0; s < OZ_SLICES; s++) out[c + s * sstride] = 0;
+}
+
+template <typename T>
+__global__ void k_oz_split(const T *__restrict__ src, int64_t rows, int64_t cols, int64_t ld,
+                           __nv_bfloat16 *__restrict__ dst, int64_t sl_ld, int64_t sstride,
+                           int32_t *__restrict__ exps, int zero_diag, double *__restrict__ d)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= rows) return;
+    oz_split_row<T>(src + r * ld, cols, cols, zero_diag ? r : -1, d ? d + r : nullptr,
+                    reinterpret_cast<unsigned short *>(dst + r * sl_ld), sstride, exps + r, lane);
+}
+
+// Batched over windows (blockIdx.y = window z): with n = ext[z] - ext_off, rows i in [0, n) (or
+// [0, rows_fixed) when rows_fixed > 0) of the n-column block whose first entry is
+// src + z * src_z + row0 * ld + col0 (ld the row stride), into digit rows
+// z * dst_zrow + dst_row0 + i with K index = column - col0; columns n .. fill_to - 1 of each row
+// get zero digits (the K padding the products read).
+__global__ void k_oz_split_win(const double *__restrict__ src, int64_t src_z, int64_t ld, int64_t row0, int64_t col0,
+                               const int32_t *__restrict__ ext, int ext_off, int rows_fixed, int64_t fill_to,
+                               __nv_bfloat16 *__restrict__ dst, int64_t dst_zrow, int64_t dst_row0, int64_t sl_ld,
+                               int64_t sstride, int32_t *__restrict__ exps)
+{
+    const int z = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t n = max(0, ext[z] - ext_off);                      // the window's extent
+    const int64_t nrows = rows_fixed > 0 ? rows_fixed : n;
+    if (i >= nrows) return;
+    const double *x = src + (int64_t)z * src_z + (row0 + i) * ld + col0;
+    const int64_t drow = (int64_t)z * dst_zrow + dst_row0 + i;
+    oz_split_row<double>(x, n, fill_to, -1, nullptr, reinterpret_cast<unsigned short *>(dst + drow * sl_ld), sstride,
+                         exps + drow, lane);
 }
 
 // ---- product ---------------------------------------------------------------------------------
@@ -143,7 +180,8 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
     using namespace tc;
     using namespace oz;
     const int z = blockIdx.z;
-    const int row0 = prm.row_base + blockIdx.y * BM, col0 = prm.row_base + blockIdx.x * BN;
+    const int row0 = prm.row_base + blockIdx.y * BM;
+    const int col0 = (prm.cols_from_zero ? 0 : prm.row_base) + blockIdx.x * BN;
     const int rows_lim = prm.ext ? prm.ext[z] : prm.rows;
     const int cols_lim = prm.ext_c ? prm.ext_c[z] : (prm.ext ? prm.ext[z] : prm.cols);
     if (row0 >= rows_lim || col0 >= cols_lim) return;              // tile outside this window
@@ -347,6 +385,20 @@ cudaError_t launch_oz_split(const double *src, int64_t rows, int64_t cols, int64
     return cudaGetLastError();
 }
 
+cudaError_t launch_oz_split_win(const double *src, int64_t src_z, int64_t ld, int64_t row0, int64_t col0,
+                                const int32_t *ext, int ext_off, int rows_fixed, int max_rows, int nb,
+                                const SliceBuf &dst, int64_t dst_zrow, int64_t dst_row0, int32_t *exps,
+                                cudaStream_t st)
+{
+    if (max_rows <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((max_rows + 1) / 2), (unsigned)nb);
+    k_oz_split_win<<<grid, 64, 0, st>>>(src, src_z, ld, row0, col0, ext, ext_off, rows_fixed, dst.ld,
+                                        reinterpret_cast<__nv_bfloat16 *>(dst.ptr), dst_zrow, dst_row0, dst.ld,
+                                        dst.ld * dst.rows, exps);
+    g_launches++;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_oz_split_f32(const float *src, int64_t rows, int64_t cols, int64_t ld, const SliceBuf &dst,
                                 int32_t *exps, cudaStream_t st)
 {
@@ -371,7 +423,7 @@ cudaError_t launch_gemm_oz(const SliceBuf &P, const int32_t *ep, const SliceBuf 
     prm.ep = ep;
     prm.eq = eq;
     // batched: prm.rows / prm.cols give the grid extent from row_base (the largest window)
-    const int ext_r = prm.rows - prm.row_base, ext_c = prm.cols - prm.row_base;
+    const int ext_r = prm.rows - prm.row_base, ext_c = prm.cols - (prm.cols_from_zero ? 0 : prm.row_base);
     if (ext_r <= 0 || ext_c <= 0) return cudaSuccess;
     dim3 grid((unsigned)((ext_c + oz::BN - 1) / oz::BN), (unsigned)((ext_r + oz::BM - 1) / oz::BM), (unsigned)batch);
     k_gemm_oz<<<grid, 192, oz_smem_bytes(), st>>>(mp, mq, prm);

@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cfloat>
 
+#include "fp64_util.cuh"
 #include "pfsm_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -58,31 +59,6 @@ __device__ __forceinline__ double block_sum(double v, double *red)
         for (int i = 0; i < nw; i++) t += red[i];
     }
     return t;
-}
-
-// 1/p and 1/sqrt(d) for d, p > 0 of any FP64 magnitude without the IEEE FP64 divide / square
-// root sequences (each ~10 dependent FP64 instructions of ~64 cycles on B300): the exponent is
-// split off (so the FP32 seed never under- or overflows), then an FP32 estimate and two Newton
-// steps, y <- y (2 - p y) and y <- y (3 - d y^2) / 2, give about 1 ulp.
-__device__ __forceinline__ double scaled_rcp(double p)
-{
-    int e;
-    const double m = frexp(p, &e);                     // p = m 2^e, m in [0.5, 1)
-    double y = (double)__frcp_rn((float)m);
-    y = y * fma(-m, y, 2.0);
-    y = y * fma(-m, y, 2.0);
-    return ldexp(y, -e);
-}
-
-__device__ __forceinline__ double scaled_rsqrt(double d)
-{
-    int e;
-    double m = frexp(d, &e);
-    if (e & 1) { m *= 2.0; e -= 1; }                  // d = m 2^e, e even, m in [0.5, 2)
-    double y = (double)rsqrtf((float)m);
-    y = y * fma(-0.5 * m, y * y, 1.5);
-    y = y * fma(-0.5 * m, y * y, 1.5);
-    return ldexp(y, -e / 2);
 }
 
 // Householder scalars of the column c (entries kk+1 .. M-1) that step kk reduces, by one warp:
@@ -1581,8 +1557,11 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
     // reduction's launch so that the reduction's clusters are placed first
     const bool side_e = h->side && h->prm.precision != PFSM_FP64 && !h->prm.fs_adaptive && h->prm.fs_iters > 0;
     if (side_e && (e0 = cudaEventRecord(h->fork_ev, st)) != cudaSuccess) return e0;
-    // 1. tridiagonalisation, one cluster per window
-    if (h->tri_blocked) {
+    // 1. tridiagonalisation: two stages (mixed forms, wide windows: k_band.cu), or one cluster
+    //    per window
+    if (h->tri_two_stage) {
+        if ((e0 = launch_band_reduction(h, A, st)) != cudaSuccess) return e0;
+    } else if (h->tri_blocked) {
         // blocked: one panel launch per kPanel columns, the trailing update as a batched digit
         // product A_ps[k1:, k1:] -= [V W] [W V]^T per window (FP64-accurate, tensor cores)
         const size_t smem = tri_panel_smem(Mmax, CL, h->tri_mcap);
@@ -1692,8 +1671,9 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
     }
     if (h->timing && (e0 = cudaEventRecord(h->sub_ev[2], st)) != cudaSuccess) return e0;
     // 4. back-transform + start vectors: the mixed forms apply the reflectors in compact-WY form
-    //    with digit products on the tensor cores (k_bt_wy.cu); the FP64 form one by one on the FP64
-    //    pipe
+    //    with digit products on the tensor cores (k_bt_wy.cu), after the bulge-chasing reflectors
+    //    when the reduction had two stages; the FP64 form one by one on the FP64 pipe
+    if (h->tri_two_stage && (e0 = launch_band_backtransform(h, st)) != cudaSuccess) return e0;
     if (h->prm.precision != PFSM_FP64 && w.btG) return launch_backtransform_wy(h, st, side_bt);
     {
         // vectors per CTA: the fewest for which sum_b ceil(m_b / vpc) <= N / vpc + nb CTAs fit

@@ -71,6 +71,14 @@ struct Workspace {
     double *btG = nullptr, *btRT = nullptr, *btW1 = nullptr, *btW2T = nullptr, *btY = nullptr;
     void *btDA = nullptr, *btDB = nullptr;
     int32_t *btEA = nullptr, *btEB = nullptr, *btExt = nullptr;
+    // mixed-form two-stage reduction (k_band.cu): digits of the trailing matrices and of the
+    // panel reflectors with their row exponents, Y = A22 V (then W = Y T; nb * Mmax x 32), T and
+    // U (nb x 32 x 32), the chunk partials of V^T W, the per-panel window extents, the band
+    // storage of stage 2 and its reflectors (per window, sweep and task: 32 entries and beta)
+    void *bdA = nullptr, *bdV = nullptr;
+    int32_t *bdeA = nullptr, *bdeV = nullptr, *bExt = nullptr;
+    double *bY = nullptr, *bT = nullptr, *bU = nullptr, *bXp = nullptr, *bBw = nullptr, *bR2 = nullptr,
+           *bT2 = nullptr;
 };
 
 }  // namespace pfsm
@@ -104,6 +112,7 @@ struct pfsm_handle_s {
     bool tri_blocked = false;      // mixed forms: blocked reduction (k_tridiag_panel)
     int32_t tri_rpw = 8;           // its rows-per-warp register capacity (8 or 24)
     int32_t tri_mcap = 0;          // largest window kept in shared memory by it
+    bool tri_two_stage = false;    // mixed forms: two-stage reduction (k_band.cu)
     int32_t *h_slices = nullptr;   // host copy of explicit slice sizes (or null)
     pfsm::Workspace ws;
     cudaStream_t last_stream = nullptr;
@@ -225,6 +234,7 @@ struct OzParams {
     int64_t zrow, zc;
     int row_base;
     const int32_t *ext;
+    int cols_from_zero;             // output columns start at 0 instead of row_base
     int64_t zrow_q;                 // Q's operand rows per window (0: zrow)
     const int32_t *ext_c;           // output column extents per window (null: ext)
     const double *Vp; int64_t ldv;  // with dcol: C[r, c] += Vp[r, c] dcol[c] (exact diagonal term)
@@ -269,6 +279,12 @@ cudaError_t run_gen_to_std_sym(int64_t N, const double *A, const double *B, doub
                                double tol, cudaStream_t st, Gen2StdResult &res);
 cudaError_t launch_oz_split(const double *src, int64_t rows, int64_t cols, int64_t ld, const SliceBuf &dst,
                             int32_t *exps, cudaStream_t st, bool zero_diag = false, double *d = nullptr);
+// batched over nb windows: ext[z] - ext_off rows (or rows_fixed rows) x (ext[z] - ext_off) columns
+// of the block at src + z * src_z + row0 * ld + col0, digits zero-filled to dst.ld (see k_gemm_oz.cu)
+cudaError_t launch_oz_split_win(const double *src, int64_t src_z, int64_t ld, int64_t row0, int64_t col0,
+                                const int32_t *ext, int ext_off, int rows_fixed, int max_rows, int nb,
+                                const SliceBuf &dst, int64_t dst_zrow, int64_t dst_row0, int32_t *exps,
+                                cudaStream_t st);
 cudaError_t launch_oz_split_f32(const float *src, int64_t rows, int64_t cols, int64_t ld, const SliceBuf &dst,
                                 int32_t *exps, cudaStream_t st);
 cudaError_t launch_gemm_oz(const SliceBuf &P, const int32_t *ep, const SliceBuf &Q, const int32_t *eq,
@@ -292,6 +308,20 @@ inline size_t tri_panel_smem(int Mmax, int CL, int Mcap)
     if (Mcap > 0) b += (size_t)((Mcap + CL - 1) / CL) * Mcap * sizeof(double);
     return b;
 }
+
+// two-stage reduction of the mixed forms (k_band.cu): band half-width, CTAs per window of the
+// panel and bulge-chasing kernels, warps per bulge-chasing CTA
+constexpr int kBand = 32;
+constexpr int kPanelCL = 8;
+constexpr int kChaseCL = 4;
+constexpr int kChaseWarps = 8;
+__host__ __device__ int band_panels(int M);
+size_t band_panel_smem(int Mmax);
+bool band_reduction_fits(int Mmax, size_t smem_cap);
+int band_tasks_per_sweep(int Mmax);
+cudaError_t configure_band_kernels();
+cudaError_t launch_band_reduction(pfsm_handle_s *h, const double *A, cudaStream_t st);
+cudaError_t launch_band_backtransform(pfsm_handle_s *h, cudaStream_t st);
 
 cudaError_t configure_dense_kernels();   // shared-memory attributes of k_dense.cu
 cudaError_t launch_gram_schmidt_f64(pfsm_handle_s *h, cudaStream_t st);
