@@ -310,6 +310,11 @@ typedef struct {
                              only); 0 otherwise */
     double gs_precond_residual; /* max |M S M^T - I| after the series, measured by eager solves
                                    (0 for solves captured into a CUDA graph) */
+    float band_ms[4];     /* two-stage reduction (mixed forms, wide windows), with timing: inside
+                             phase 6, 0 dense to band (panels), 1 band to tridiagonal (bulge
+                             chasing); inside phase 9, 2 the bulge reflectors applied to the
+                             eigenvectors, 3 the panel reflectors and the start vectors; zeros
+                             otherwise */
 } pfsm_profile_t;
 
 /* Enables (enable != 0) or disables CUDA-event phase timing on h. Timing adds one event record

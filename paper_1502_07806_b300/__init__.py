@@ -28,6 +28,8 @@ EXPORTED = ("pfsm_default_params", "pfsm_init", "pfsm_solve", "pfsm_backward", "
             "pfsm_gen_to_std_sym", "pfsm_scf_step")
 PHASES = ("plan", "submatrix", "fs_iterations", "gram_schmidt", "rayleigh", "backward")
 SUB_PHASES = ("tridiag", "bisect", "inverse_iter", "backtransform", "overlap", "cholesky")
+# two-stage reduction (mixed forms, wide windows): inside "tridiag" and "backtransform"
+BAND_PHASES = ("band_panels", "band_chase", "band_bt_chase", "band_bt_panels")
 
 
 class PFSMError(RuntimeError):
@@ -50,7 +52,8 @@ class Profile(ctypes.Structure):
                 ("phase_ms", ctypes.c_float * 12), ("gemm_tile_n", ctypes.c_int32),
                 ("path", ctypes.c_int32), ("guard_value", ctypes.c_double),
                 ("fs_steps", ctypes.c_int32), ("fs_residual", ctypes.c_double),
-                ("gs_precond", ctypes.c_int32), ("gs_precond_residual", ctypes.c_double)]
+                ("gs_precond", ctypes.c_int32), ("gs_precond_residual", ctypes.c_double),
+                ("band_ms", ctypes.c_float * 4)]
 
 
 _lib = None
@@ -198,6 +201,7 @@ class Handle:
         if pr.timed:
             out.update({name: float(pr.phase_ms[i]) for i, name in enumerate(PHASES)})
             out.update({name: float(pr.phase_ms[6 + i]) for i, name in enumerate(SUB_PHASES)})
+            out.update({name: float(pr.band_ms[i]) for i, name in enumerate(BAND_PHASES)})
         return out
 
     def diagnostic(self, which: int) -> torch.Tensor:

@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "pfsm_internal.cuh"
 
@@ -52,8 +53,8 @@ void free_ws(pfsm_handle_s *h)
                     w.sel_val, w.sel_vec, w.iiwork, w.slices, w.slE, w.slX, w.slY, w.slZ,
                     w.Z, w.dA, w.Linv, w.ozP, w.ozQ, w.ozeP, w.ozeQ, w.L32, w.R32, w.M32, w.F, w.VW, w.WV, w.tdP, w.tdQ, w.tdeP, w.tdeQ,
                     w.btG, w.btRT, w.btW1, w.btW2T, w.btY, w.btDA, w.btDB, w.btEA, w.btEB, w.btExt,
-                    w.ozA, w.ozeA, w.bdA, w.bdV, w.bdeA, w.bdeV, w.bExt, w.bY, w.bT, w.bU, w.bXp, w.bBw,
-                    w.bR2, w.bT2};
+                    w.ozA, w.ozeA, w.bdA, w.bdV, w.bdeA, w.bdeV, w.bExt, w.bKB, w.bV, w.bY, w.bT, w.bU, w.bXp,
+                    w.bBw, w.bR2, w.bT2, w.bD};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     w = Workspace{};
@@ -166,7 +167,7 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
     // the mixed forms' two-stage reduction: chosen for wide windows (automatic) or on request,
     // when its kernels' shared memory and schedule allow the window width
     if (prm.precision != PFSM_FP64 && prm.reduction != 1 && band_reduction_fits(Mx, kSmemCap) &&
-        backtransform_wy_fits(Mx) && (prm.reduction == 2 || Mx >= kTwoStageMinWidth)) {
+        (prm.reduction == 2 || Mx >= kTwoStageMinWidth)) {
         h->tri_two_stage = true;
         h->tri_blocked = false;
     }
@@ -248,7 +249,7 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
             PFSM_ALLOC(w.tdeP, nbM);
             PFSM_ALLOC(w.tdeQ, nbM);
         }
-        if (backtransform_wy_fits(h->Mmax)) {
+        if (backtransform_wy_fits(h->Mmax) && !h->tri_two_stage) {
             const size_t Mx = (size_t)h->Mmax, mx = (size_t)h->mmax, nbx = (size_t)nblocks;
             const size_t ldk = (size_t)padded_ld(h->Mmax);
             PFSM_ALLOC(w.btG, nbx * Mx * Mx);
@@ -271,19 +272,30 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
             const size_t Mx = (size_t)h->Mmax, nbx = (size_t)nblocks, KBx = (size_t)kBand;
             const size_t ldk = (size_t)padded_ld(h->Mmax);
             const size_t nt = (size_t)band_tasks_per_sweep(h->Mmax), nch = (Mx + 63) / 64;
+            const size_t np = (size_t)std::max(1, band_panels(h->Mmax));
             uint8_t *d1 = nullptr, *d2 = nullptr;
             PFSM_ALLOC(d1, (size_t)OZ_SLICES * nbx * Mx * ldk * 2);
             PFSM_ALLOC(d2, (size_t)OZ_SLICES * nbx * KBx * ldk * 2);
             w.bdA = d1; w.bdV = d2;
             PFSM_ALLOC(w.bdeA, nbx * Mx);
             PFSM_ALLOC(w.bdeV, nbx * KBx);
-            PFSM_ALLOC(w.bExt, nbx);
+            PFSM_ALLOC(w.bExt, np * nbx);
+            PFSM_ALLOC(w.bKB, nbx);
             PFSM_ALLOC(w.bY, nbx * Mx * KBx);
-            PFSM_ALLOC(w.bT, nbx * KBx * KBx);
+            PFSM_ALLOC(w.bT, np * nbx * KBx * KBx);
+            PFSM_ALLOC(w.bV, np * nbx * Mx * KBx);
+            // a window without some panel keeps that panel's T and reflector rows zero
+            if (e == cudaSuccess) e = cudaMemset(w.bT, 0, np * nbx * KBx * KBx * sizeof(double));
+            if (e == cudaSuccess) e = cudaMemset(w.bV, 0, np * nbx * Mx * KBx * sizeof(double));
+            if (e == cudaSuccess) {
+                std::vector<int32_t> kbv(nbx, kBand);
+                e = cudaMemcpy(w.bKB, kbv.data(), nbx * sizeof(int32_t), cudaMemcpyHostToDevice);
+            }
             PFSM_ALLOC(w.bU, nbx * KBx * KBx);
             PFSM_ALLOC(w.bXp, nbx * nch * KBx * KBx);
             PFSM_ALLOC(w.bBw, nbx * (Mx + 2 * KBx) * 2 * KBx);
             PFSM_ALLOC(w.bR2, nbx * Mx * nt * KBx);
+            PFSM_ALLOC(w.bD, nbx * Mx);
             PFSM_ALLOC(w.bT2, nbx * Mx * nt);
             if (e == cudaSuccess) e = configure_band_kernels();
         }
@@ -306,6 +318,7 @@ int pfsm_init(int64_t N, int32_t nblocks, const pfsm_params_t *p, pfsm_handle_t 
     for (int i = 0; i < 8 && e == cudaSuccess; i++) e = cudaEventCreate(&h->ev[i]);
     for (int i = 0; i < 4 && e == cudaSuccess; i++) e = cudaEventCreate(&h->sub_ev[i]);
     for (int i = 0; i < 2 && e == cudaSuccess; i++) e = cudaEventCreate(&h->gs_ev[i]);
+    for (int i = 0; i < 3 && e == cudaSuccess; i++) e = cudaEventCreate(&h->band_ev[i]);
     if (prm.precision != PFSM_FP64) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming);
@@ -360,22 +373,35 @@ static cudaError_t fs_mixed(pfsm_handle_s *h, const double *A, cudaStream_t st)
     if (K == 0) return cudaSuccess;
     const int ns = slices_for(h->prm.precision), kind = slice_kind(h->prm.precision);
     const int64_t ld = padded_ld(N);
-    SliceBuf sE{w.slE, N, ld, ns, kind}, sX{w.slX, N, ld, ns, kind}, sY{w.slY, N, ld, ns, kind},
-        sZ{w.slZ, N, ld, ns, kind};
+    SliceBuf sE{w.slE, N, ld, ns, kind}, sY{w.slY, N, ld, ns, kind}, sZ{w.slZ, N, ld, ns, kind};
     cudaError_t e;
     // the slices of E = A - diag(A) (and diag(A)) were split on the side stream during the window
     // eigensolves when the handle has one (launch_subeig)
     if (!h->side && (e = launch_split(A, N, N, N, sE, true, w.dA, st)) != cudaSuccess) return e;
     if ((e = join_side(h, st)) != cudaSuccess) return e;
-    if ((e = launch_split(w.X, N, N, N, sX, false, nullptr, st)) != cudaSuccess) return e;
+    // Y_0 = (A - eps I) X_0 is the window eigenvectors' residual E x outside each window (zero
+    // inside). It is the largest operand of the recurrence (the method's residual, 5e-3 on the
+    // vacancy-like matrix) and a split product loses about sqrt(N) 2^-24 of it to cancellation in
+    // dense couplings, so this one product is the FP64-accurate digit product (rows of X_0 against
+    // the digits of E split beside the window eigensolves), then split for the next products.
+    {
+        const SliceBuf dX{w.ozP, N, ld, OZ_SLICES, 0};
+        const bool presplit = h->a_split;
+        const SliceBuf dE{presplit ? w.ozA : w.ozQ, N, ld, OZ_SLICES, 0};
+        int32_t *eE = presplit ? w.ozeA : w.ozeQ;
+        if (!presplit && (e = launch_oz_split(A, N, N, N, dE, eE, st, true, w.dA)) != cudaSuccess) return e;
+        if ((e = launch_oz_split(w.X, N, N, N, dX, w.ozeP, st)) != cudaSuccess) return e;
+        OzParams o{};
+        o.rows = (int)N; o.cols = (int)N; o.C = w.Y; o.ldc = N; o.status = w.status;
+        o.krange64 = w.tile_krange; o.nrowtiles64 = (int)((N + kFsTileRows - 1) / kFsTileRows);
+        o.win_plan = w.plan; o.win_nb = h->nb;
+        if ((e = launch_gemm_oz(dX, w.ozeP, dE, eE, o, st)) != cudaSuccess) return e;
+        if ((e = launch_split(w.Y, N, N, N, sY, false, nullptr, st)) != cudaSuccess) return e;
+    }
     TcParams p{};
     p.rows = (int)N; p.cols = (int)N; p.ldo = N; p.bn = h->tc_bn;
     p.d = w.dA; p.eps = w.eps; p.alpha = w.alpha; p.status = w.status;
     p.plan = w.plan; p.nb = h->nb;
-    p.krange = w.tile_krange; p.nrowtiles64 = (int)((N + kFsTileRows - 1) / kFsTileRows);
-    p.epi = TC_EPI_Y0; p.out = w.Y;
-    if ((e = launch_gemm_tc(sX, sE, p, &sY, st)) != cudaSuccess) return e;
-    p.krange = nullptr;
     for (int j = 0; j < K; j++) {
         TcParams z = p;
         z.epi = TC_EPI_Z; z.out = w.Z; z.V = w.Y; z.X = w.X;
@@ -767,6 +793,12 @@ int pfsm_get_profile(pfsm_handle_t h, pfsm_profile_t *out)
         for (int i = 0; i < 4; i++) PFSM_CUDA(cudaEventElapsedTime(&out->phase_ms[6 + i], seq[i], seq[i + 1]));
         PFSM_CUDA(cudaEventElapsedTime(&out->phase_ms[10], h->ev[3], h->gs_ev[0]));
         PFSM_CUDA(cudaEventElapsedTime(&out->phase_ms[11], h->gs_ev[0], h->gs_ev[1]));
+        if (h->tri_two_stage && h->last_path == 0 && !h->last_was_backward) {
+            PFSM_CUDA(cudaEventElapsedTime(&out->band_ms[0], h->ev[1], h->band_ev[0]));
+            PFSM_CUDA(cudaEventElapsedTime(&out->band_ms[1], h->band_ev[0], h->band_ev[1]));
+            PFSM_CUDA(cudaEventElapsedTime(&out->band_ms[2], h->sub_ev[2], h->band_ev[2]));
+            PFSM_CUDA(cudaEventElapsedTime(&out->band_ms[3], h->band_ev[2], h->ev[2]));
+        }
     }
     if (h->last_was_backward) PFSM_CUDA(span(6, 7, &out->phase_ms[5]));
     out->timed = 1;
@@ -783,6 +815,8 @@ int pfsm_destroy(pfsm_handle_t h)
         if (h->sub_ev[i]) cudaEventDestroy(h->sub_ev[i]);
     for (int i = 0; i < 2; i++)
         if (h->gs_ev[i]) cudaEventDestroy(h->gs_ev[i]);
+    for (int i = 0; i < 3; i++)
+        if (h->band_ev[i]) cudaEventDestroy(h->band_ev[i]);
     if (h->side) cudaStreamDestroy(h->side);
     if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     if (h->join_ev) cudaEventDestroy(h->join_ev);

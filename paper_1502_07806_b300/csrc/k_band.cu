@@ -13,7 +13,8 @@
 //                      CTAs (rows in shared memory, partial sums exchanged through distributed
 //                      shared memory), unit reflectors v_t (beta = 2) with T of the compact-WY
 //                      form I - V T V^T (LAPACK's larft recurrence), R written into the band;
-//       Y = A22 V      FP64-accurate digit product on the tensor cores (k_gemm_oz.cu);
+//       Y = A22 V      FP64-accurate digit product on the tensor cores (k_gemm_oz.cu) of the
+//                      off-diagonal part, the diagonal part added exactly in FP64;
 //       k_band_w/u/z   W = Y T, U = T^T (V^T W), Z = W - V U / 2 on the FP64 pipe;
 //       A22 -= V Z^T + Z V^T   digit product, subtracted into the window.
 //     The O(M^3) work of this stage runs on the tensor cores at FP64 accuracy.
@@ -25,9 +26,8 @@
 //     band columns; one cluster per window, one warp per task, a cluster barrier per time step.
 //  3. the tridiagonal's eigenpairs as before (k_bisect, k_inverse_iter);
 //  4. y = Q1 Q2 z: Q2's reflectors applied to the eigenvectors z on the FP64 pipe (k_band_bt2),
-//     Q1's through the compact-WY back-transformation of k_bt_wy.cu (stage 1 stores its
-//     reflectors in the same row layout as the one-stage reduction: row k = c + t holds v_t on
-//     rows r0 + t .. M-1, tau[k] = beta_t).
+//     then Q1 panel by panel, Yr <- Yr - (Yr V T^T) V^T with two digit products per panel
+//     (k_band_bt1_u forms X T^T), and the start-vector rules (k_bt_wy.cu).
 // The FP64 form keeps the one-stage reduction (no tensor cores).
 #include <cooperative_groups.h>
 #include <algorithm>
@@ -345,10 +345,12 @@ k_band_u(const int32_t *__restrict__ extp, int c, const double *__restrict__ Tb,
 }
 
 // Z = W - V U / 2 and the operands of the trailing update: row r0 + i of window b in VW = [v z],
-// WV = [z v] (rows b * Mmax + r0 + i, 2 KB entries). Grid (ceil((Mmax - r0) / kChunk), nb), 256.
+// WV = [z v] (rows b * Mmax + r0 + i, 2 KB entries); the reflectors' row r0 + i also into Vrows
+// (kept for the back-transformation). Grid (ceil((Mmax - r0) / kChunk), nb), 256.
 __global__ void __launch_bounds__(256)
 k_band_z(const int32_t *__restrict__ extp, int Mmax, int c, const double *__restrict__ refl,
-         const double *__restrict__ Y, const double *__restrict__ U, double *__restrict__ VW, double *__restrict__ WV)
+         const double *__restrict__ Y, const double *__restrict__ U, double *__restrict__ VW, double *__restrict__ WV,
+         double *__restrict__ Vrows)
 {
     const int b = blockIdx.y, bx = blockIdx.x;
     const int r0 = c + KB;
@@ -376,6 +378,7 @@ k_band_z(const int32_t *__restrict__ extp, int Mmax, int c, const double *__rest
         VW[row * 2 * KB + KB + q] = z;
         WV[row * 2 * KB + q] = z;
         WV[row * 2 * KB + KB + q] = Vs[il][q];
+        Vrows[row * KB + q] = Vs[il][q];
     }
 }
 
@@ -400,11 +403,12 @@ k_band_extract(const int32_t *__restrict__ plan, int nb, int Mmax, const double 
 // One task (s, i) by one warp (see the file comment). Rows R = [a, a + L), a = s + 1 + i KB,
 // L = min(KB, M - a); the column it annihilates, col = s (i = 0) or a - KB; the blocks it touches:
 // left (rows R, columns col+1 .. a-1, only for i >= 1), diagonal (R x R, lower triangle stored) and
-// below (rows a + L .. a + L + KB - 1, columns R). Lane l: entry l of the reflector, column
-// col + 1 + l of the left block, column a + l of the diagonal block, row a + L + l of the block
-// below. The reflector goes to refl2 (KB entries, zero past L) and tau2.
+// below (rows a + L .. a + L + KB - 1, columns R). Every block is loaded with all its loads in
+// flight (registers first, then the warp's shared-memory tile S where a transpose is needed),
+// updated, and stored back. The reflector goes to refl2 (KB entries, zero past L) and tau2.
 __device__ __forceinline__ void chase_task(double *__restrict__ B, int M, int s, int i, double *__restrict__ r2,
-                                           double *__restrict__ t2, double *vsh, double *wsh, int lane)
+                                           double *__restrict__ t2, double *vsh, double *wsh, double (*S)[KB + 1],
+                                           int lane)
 {
     auto at = [&](int r, int cc) -> double & { return B[(size_t)cc * (2 * KB) + (r - cc)]; };
     const int a = s + 1 + i * KB;
@@ -427,47 +431,87 @@ __device__ __forceinline__ void chase_task(double *__restrict__ B, int M, int s,
     if (beta == 0.0) return;
     if (lane < L) at(a + lane, col) = (lane == 0) ? alpha : 0.0;
     vsh[lane] = v;
-    __syncwarp();
-    // left block: H from the left on columns col+1 .. a-1 (the rest of the previous bulge)
-    if (i >= 1 && lane < KB - 1) {
-        const int cc = col + 1 + lane;
-        double w = 0.0;
-        for (int r = 0; r < L; r++) w = fma(vsh[r], at(a + r, cc), w);
-        w *= beta;
-        for (int r = 0; r < L; r++) at(a + r, cc) = fma(-w, vsh[r], at(a + r, cc));
-    }
-    // diagonal block: D <- H D H = D - v w^T - w v^T, p = beta D v, w = p - (beta / 2)(v.p) v
-    double p = 0.0;
-    if (lane < L) {
-        for (int q = 0; q < L; q++) {
-            const double d = (q <= lane) ? at(a + lane, a + q) : at(a + q, a + lane);
-            p = fma(d, vsh[q], p);
+    double tmp[KB];
+    // left block: H from the left on columns col+1 .. a-1 (the rest of the previous bulge); lane =
+    // row for the loads and stores, lane = column for the arithmetic
+    if (i >= 1) {
+#pragma unroll
+        for (int q = 0; q < KB - 1; q++) tmp[q] = (lane < L) ? at(a + lane, col + 1 + q) : 0.0;
+#pragma unroll
+        for (int q = 0; q < KB - 1; q++) S[q][lane] = tmp[q];
+        __syncwarp();
+        if (lane < KB - 1) {
+            double w0 = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;     // four chains of dependent FMAs
+#pragma unroll
+            for (int r = 0; r < KB; r += 4) {
+                w0 = fma(vsh[r], S[lane][r], w0);
+                w1 = fma(vsh[r + 1], S[lane][r + 1], w1);
+                w2 = fma(vsh[r + 2], S[lane][r + 2], w2);
+                w3 = fma(vsh[r + 3], S[lane][r + 3], w3);
+            }
+            const double w = beta * ((w0 + w1) + (w2 + w3));
+#pragma unroll
+            for (int r = 0; r < KB; r++) S[lane][r] = fma(-w, vsh[r], S[lane][r]);
         }
-        p *= beta;
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < KB - 1; q++) tmp[q] = S[q][lane];
+#pragma unroll
+        for (int q = 0; q < KB - 1; q++)
+            if (lane < L) at(a + lane, col + 1 + q) = tmp[q];
+        __syncwarp();
     }
+    // diagonal block: D <- H D H = D - v w^T - w v^T, p = beta D v, w = p - (beta / 2)(v.p) v; column
+    // c of the lower triangle in S[c][r], r >= c (lane = row)
+#pragma unroll
+    for (int c = 0; c < KB; c++) tmp[c] = (c <= lane && lane < L) ? at(a + lane, a + c) : 0.0;
+#pragma unroll
+    for (int c = 0; c < KB; c++) S[c][lane] = tmp[c];
+    __syncwarp();
+    double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+#pragma unroll
+    for (int c = 0; c < KB; c += 4) {
+        p0 = fma((c <= lane) ? S[c][lane] : S[lane][c], vsh[c], p0);
+        p1 = fma((c + 1 <= lane) ? S[c + 1][lane] : S[lane][c + 1], vsh[c + 1], p1);
+        p2 = fma((c + 2 <= lane) ? S[c + 2][lane] : S[lane][c + 2], vsh[c + 2], p2);
+        p3 = fma((c + 3 <= lane) ? S[c + 3][lane] : S[lane][c + 3], vsh[c + 3], p3);
+    }
+    const double p = beta * ((p0 + p1) + (p2 + p3));
     const double vp = warp_sum(v * p);
     const double w = fma(-0.5 * beta * vp, v, p);
     wsh[lane] = w;
     __syncwarp();
-    if (lane < L)
-        for (int r = lane; r < L; r++)
-            at(a + r, a + lane) = fma(-vsh[r], w, fma(-wsh[r], v, at(a + r, a + lane)));
-    // below: rows e .. e + LB - 1, H from the right (this creates the next bulge)
+#pragma unroll
+    for (int c = 0; c < KB; c++)
+        if (c <= lane) tmp[c] = fma(-v, wsh[c], fma(-w, vsh[c], S[c][lane]));
+#pragma unroll
+    for (int c = 0; c < KB; c++)
+        if (c <= lane && lane < L) at(a + lane, a + c) = tmp[c];
+    // below: rows e .. e + LB - 1 (lane = row, in registers), H from the right (the next bulge)
     const int e = a + L;
     const int LB = min(KB, M - e);
-    if (lane < LB) {
-        double u = 0.0;
-        for (int q = 0; q < L; q++) u = fma(at(e + lane, a + q), vsh[q], u);
-        u *= beta;
-        for (int q = 0; q < L; q++) at(e + lane, a + q) = fma(-u, vsh[q], at(e + lane, a + q));
+#pragma unroll
+    for (int c = 0; c < KB; c++) tmp[c] = (lane < LB && c < L) ? at(e + lane, a + c) : 0.0;
+    double u0 = 0.0, u1 = 0.0, u2 = 0.0, u3 = 0.0;
+#pragma unroll
+    for (int c = 0; c < KB; c += 4) {
+        u0 = fma(tmp[c], vsh[c], u0);
+        u1 = fma(tmp[c + 1], vsh[c + 1], u1);
+        u2 = fma(tmp[c + 2], vsh[c + 2], u2);
+        u3 = fma(tmp[c + 3], vsh[c + 3], u3);
     }
+    const double u = beta * ((u0 + u1) + (u2 + u3));
+#pragma unroll
+    for (int c = 0; c < KB; c++)
+        if (lane < LB && c < L) at(e + lane, a + c) = fma(-u, vsh[c], tmp[c]);
     __syncwarp();
 }
 
 // Cluster of CL CTAs per window (grid nb * CL), NW warps each; warp g of the window runs the
-// sweeps s = g (mod CL NW), task (s, i) at time step 3 s + i; a cluster barrier (with a fence for
-// the band's global-memory writes) ends every time step. Needs 3 CL NW > the tasks of sweep 0 so
+// sweeps s = g (mod CL NW), task (s, i) at time step 3 s + i; a cluster barrier ends every time
+// step. Needs 3 CL NW > the tasks of sweep 0 so
 // that a warp's consecutive sweeps never overlap in time. Finally td/te of the tridiagonal.
+// Dynamic shared memory: per warp a KB x (KB + 1) tile and the reflector and w vectors.
 __global__ void __launch_bounds__(32 * kChaseWarps, 1)
 k_band_chase(const int32_t *__restrict__ plan, int nb, int Mmax, int NT, double *__restrict__ Bw,
              double *__restrict__ refl2, double *__restrict__ tau2, double *__restrict__ td, double *__restrict__ te)
@@ -478,24 +522,29 @@ k_band_chase(const int32_t *__restrict__ plan, int nb, int Mmax, int NT, double 
     const int b = blockIdx.x / CL;
     const int M = plan[3 * nb + b];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int W = CL * kChaseWarps, g = rank * kChaseWarps + warp;
-    __shared__ double vsh[kChaseWarps][KB], wsh[kChaseWarps][KB];
+    // consecutive sweeps (active together) go to different CTAs and sub-partitions
+    const int W = CL * kChaseWarps, g = warp * CL + rank;
+    extern __shared__ double csm[];
+    double(*S)[KB + 1] = reinterpret_cast<double(*)[KB + 1]>(csm + (size_t)warp * (KB * (KB + 1) + 2 * KB));
+    double *vsh = csm + (size_t)warp * (KB * (KB + 1) + 2 * KB) + KB * (KB + 1);
+    double *wsh = vsh + KB;
     double *B = Bw + (size_t)b * (Mmax + 2 * KB) * 2 * KB;
-    const int S = M - 2;                               // sweeps 0 .. M-3
-    if (S > 0) {
+    const int Sw = M - 2;                              // sweeps 0 .. M-3
+    if (Sw > 0) {
         const int nt0 = (M - 2 + KB - 1) / KB;         // tasks of sweep 0
-        const int tend = 3 * (S - 1) + nt0;
+        const int tend = 3 * (Sw - 1) + nt0;
         for (int t = 0; t < tend; t++) {
             const int smax = t / 3;
             if (smax >= g) {
                 const int s = g + ((smax - g) / W) * W;
                 const int i = t - 3 * s;
-                if (s < S && i < (M - 2 - s + KB - 1) / KB) {
+                if (s < Sw && i < (M - 2 - s + KB - 1) / KB) {
                     const size_t slot = ((size_t)b * Mmax + s) * NT + i;
-                    chase_task(B, M, s, i, refl2 + slot * KB, tau2 + slot, vsh[warp], wsh[warp], lane);
+                    chase_task(B, M, s, i, refl2 + slot * KB, tau2 + slot, vsh, wsh, S, lane);
                 }
             }
-            __threadfence();
+            // the barrier's release / acquire at cluster scope orders this step's band writes
+            // (global memory) before the next step's reads by every CTA of the cluster
             cluster.sync();
         }
     }
@@ -527,18 +576,26 @@ k_band_bt2(const int32_t *__restrict__ plan, int nb, int Mmax, int mmax, int NT,
             const size_t slot = ((size_t)b * Mmax + s) * NT + i;
             const double beta = tau2[slot];
             if (beta == 0.0) continue;
-            const double vl = refl2[slot * KB + lane];
+            const double vl = refl2[slot * KB + lane];    // zero past the reflector's length
             const int a = s + 1 + i * KB;
             const int L = min(KB, M - a);
-            double d = 0.0;
-            for (int r = 0; r < L; r++) {
-                const double vr = __shfl_sync(0xffffffffu, vl, r);
-                if (act) d = fma(vr, Y[(size_t)(a + r) * mmax], d);
+            // the lane's L entries loaded together, four partial dot products
+            double yv[KB];
+#pragma unroll
+            for (int r = 0; r < KB; r++) yv[r] = (act && r < L) ? Y[(size_t)(a + r) * mmax] : 0.0;
+            double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+#pragma unroll
+            for (int r = 0; r < KB; r += 4) {
+                d0 = fma(__shfl_sync(0xffffffffu, vl, r), yv[r], d0);
+                d1 = fma(__shfl_sync(0xffffffffu, vl, r + 1), yv[r + 1], d1);
+                d2 = fma(__shfl_sync(0xffffffffu, vl, r + 2), yv[r + 2], d2);
+                d3 = fma(__shfl_sync(0xffffffffu, vl, r + 3), yv[r + 3], d3);
             }
-            d *= beta;
-            for (int r = 0; r < L; r++) {
+            const double d = beta * ((d0 + d1) + (d2 + d3));
+#pragma unroll
+            for (int r = 0; r < KB; r++) {
                 const double vr = __shfl_sync(0xffffffffu, vl, r);
-                if (act) Y[(size_t)(a + r) * mmax] = fma(-d, vr, Y[(size_t)(a + r) * mmax]);
+                if (act && r < L) Y[(size_t)(a + r) * mmax] = fma(-d, vr, yv[r]);
             }
         }
         __syncthreads();
@@ -582,7 +639,43 @@ k_band_transpose(const int32_t *__restrict__ plan, int nb, int Mmax, int mmax, b
     }
 }
 
+// ---- back-transformation of stage 1: y = Q1 y', panel by panel ----------------------------------
+// Panel p's reflectors are I - V T V^T; for the eigenvector rows Yr (rows t, entries j) that is
+// Yr <- Yr - (Yr V T^T) V^T, applied for p = last .. 0. X = Yr V and Yr -= U V^T are digit
+// products; this kernel forms U = X T^T (rows t < m_b of window b, in place). Grid
+// (ceil(mmax / 64), nb), 256 threads.
+__global__ void __launch_bounds__(256)
+k_band_bt1_u(const int32_t *__restrict__ plan, int nb, int mmax, const double *__restrict__ Tp, double *__restrict__ X)
+{
+    const int b = blockIdx.y;
+    const int mb = plan[nb + b];
+    const int t0 = blockIdx.x * 64;
+    if (t0 >= mb) return;
+    const int rows = min(64, mb - t0);
+    __shared__ double T[KB][KB + 1], Xs[64][KB + 1];
+    const int tid = threadIdx.x;
+    const double *Tb = Tp + (size_t)b * KB * KB;
+    for (int e = tid; e < KB * KB; e += 256) T[e / KB][e % KB] = Tb[e];
+    double *Xb = X + ((size_t)b * mmax + t0) * KB;
+    for (int e = tid; e < 64 * KB; e += 256) Xs[e / KB][e % KB] = (e / KB < rows) ? Xb[e] : 0.0;
+    __syncthreads();
+    const int il = tid >> 2, q0 = tid & 3;
+    double u[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const int q = q0 + 4 * j;
+        double s = 0.0;
+        for (int r = q; r < KB; r++) s = fma(Xs[il][r], T[q][r], s);    // T upper triangular
+        u[j] = s;
+    }
+    if (il < rows)
+#pragma unroll
+        for (int j = 0; j < 8; j++) Xb[(size_t)il * KB + q0 + 4 * j] = u[j];
+}
+
 // ---- host side ------------------------------------------------------------------------------------
+
+size_t chase_smem() { return (size_t)kChaseWarps * (KB * (KB + 1) + 2 * KB) * sizeof(double); }
 
 size_t band_panel_smem(int Mmax)
 {
@@ -605,6 +698,9 @@ cudaError_t configure_band_kernels()
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_band_chase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chase_smem())) !=
+        cudaSuccess)
+        return e;
     return cudaFuncSetAttribute(k_band_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
 }
 
@@ -625,6 +721,10 @@ cudaError_t launch_band_reduction(pfsm_handle_s *h, const double *A, cudaStream_
     const size_t psmem = band_panel_smem(Mmax);
     for (int p = 0; p < np; p++) {
         const int c = p * KB, r0 = c + KB;
+        // this panel's extents (M, or 0 for a window without it), T factors and reflector rows
+        int32_t *extp = w.bExt + (size_t)p * nb;
+        double *Tp = w.bT + (size_t)p * nb * KB * KB;
+        double *Vrows = w.bV + (size_t)p * nb * Mmax * KB;
         {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3((unsigned)(nb * kPanelCL));
@@ -639,30 +739,33 @@ cudaError_t launch_band_reduction(pfsm_handle_s *h, const double *A, cudaStream_
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             if ((e = counted(cudaLaunchKernelEx(&cfg, k_band_panel, plan, nb, Mmax, c, rpc_cap, w.iiwork, w.refl,
-                                                w.tau, w.bT, w.bExt))) != cudaSuccess)
+                                                w.tau, Tp, extp))) != cudaSuccess)
                 return e;
         }
         // Y = A22 V: digits of A22 (rows r0 .. M-1, entries r0 .. M-1) and of V^T (reflector rows)
         const int64_t ldk = padded_ld(Mmax - r0);
         const SliceBuf dA{w.bdA, (int64_t)nb * Mmax, ldk, OZ_SLICES, 0};
         const SliceBuf dV{w.bdV, (int64_t)nb * KB, ldk, OZ_SLICES, 0};
-        if ((e = launch_oz_split_win(w.iiwork, MM, Mmax, r0, r0, w.bExt, r0, 0, Mmax - r0, nb, dA, Mmax, r0, w.bdeA,
-                                     st)) != cudaSuccess)
+        // A22 = D22 + E22: digits of E22 only (its entries are small against the diagonal, which
+        // would otherwise set each row's digit scale), D22 V added exactly in FP64
+        if ((e = launch_oz_split_win(w.iiwork, MM, Mmax, r0, r0, extp, r0, 0, nullptr, Mmax - r0, nb, dA, Mmax, r0,
+                                     w.bdeA, st, w.bD)) != cudaSuccess)
             return e;
-        if ((e = launch_oz_split_win(w.refl, MM, Mmax, c, r0, w.bExt, r0, KB, KB, nb, dV, KB, 0, w.bdeV, st)) !=
+        if ((e = launch_oz_split_win(w.refl, MM, Mmax, c, r0, extp, r0, KB, nullptr, KB, nb, dV, KB, 0, w.bdeV, st)) !=
             cudaSuccess)
             return e;
         OzParams o{};
         o.rows = Mmax; o.cols = KB; o.cols_from_zero = 1; o.C = w.bY; o.ldc = KB; o.status = w.status;
-        o.zrow = Mmax; o.zrow_q = KB; o.zc = (int64_t)Mmax * KB; o.row_base = r0; o.ext = w.bExt;
+        o.zrow = Mmax; o.zrow_q = KB; o.zc = (int64_t)Mmax * KB; o.row_base = r0; o.ext = extp;
+        o.Vp = w.refl + (size_t)c * Mmax; o.ldv = 1; o.vcs = Mmax; o.zv = MM; o.drow = w.bD; o.zd = Mmax;
         if ((e = launch_gemm_oz(dA, w.bdeA, dV, w.bdeV, o, st, nb)) != cudaSuccess) return e;
         // W = Y T, U = T^T V^T W, Z = W - V U / 2 -> [V Z], [Z V]
         const dim3 gch((unsigned)((Mmax - r0 + kChunk - 1) / kChunk), (unsigned)nb);
-        k_band_w<<<gch, 256, 0, st>>>(w.bExt, Mmax, c, w.refl, w.bT, w.bY, w.bXp, nchunk);
+        k_band_w<<<gch, 256, 0, st>>>(extp, Mmax, c, w.refl, Tp, w.bY, w.bXp, nchunk);
         g_launches++;
-        k_band_u<<<nb, 256, 0, st>>>(w.bExt, c, w.bT, w.bXp, nchunk, w.bU);
+        k_band_u<<<nb, 256, 0, st>>>(extp, c, Tp, w.bXp, nchunk, w.bU);
         g_launches++;
-        k_band_z<<<gch, 256, 0, st>>>(w.bExt, Mmax, c, w.refl, w.bY, w.bU, w.VW, w.WV);
+        k_band_z<<<gch, 256, 0, st>>>(extp, Mmax, c, w.refl, w.bY, w.bU, w.VW, w.WV, Vrows);
         g_launches++;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // A22 -= [V Z] [Z V]^T (rows and columns r0 .. M-1 of every window that had this panel)
@@ -672,9 +775,10 @@ cudaError_t launch_band_reduction(pfsm_handle_s *h, const double *A, cudaStream_
         if ((e = launch_oz_split(w.WV, srows, 2 * KB, 2 * KB, dQ, w.tdeQ, st)) != cudaSuccess) return e;
         OzParams u{};
         u.rows = Mmax; u.cols = Mmax; u.C = w.iiwork; u.ldc = Mmax; u.sub = 1; u.status = w.status;
-        u.zrow = Mmax; u.zc = MM; u.row_base = r0; u.ext = w.bExt;
+        u.zrow = Mmax; u.zc = MM; u.row_base = r0; u.ext = extp;
         if ((e = launch_gemm_oz(dP, w.tdeP, dQ, w.tdeQ, u, st, nb)) != cudaSuccess) return e;
     }
+    if (h->timing && (e = cudaEventRecord(h->band_ev[0], st)) != cudaSuccess) return e;
     k_band_extract<<<dim3((unsigned)((Mmax + 2 * KB + 7) / 8), (unsigned)nb), 256, 0, st>>>(plan, nb, Mmax, w.iiwork,
                                                                                          w.bBw);
     g_launches++;
@@ -682,7 +786,7 @@ cudaError_t launch_band_reduction(pfsm_handle_s *h, const double *A, cudaStream_
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nb * kChaseCL));
     cfg.blockDim = dim3(32 * kChaseWarps);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = chase_smem();
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -691,24 +795,65 @@ cudaError_t launch_band_reduction(pfsm_handle_s *h, const double *A, cudaStream_
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return counted(cudaLaunchKernelEx(&cfg, k_band_chase, plan, nb, Mmax, band_tasks_per_sweep(Mmax), w.bBw, w.bR2,
-                                      w.bT2, w.td, w.te));
+    if ((e = counted(cudaLaunchKernelEx(&cfg, k_band_chase, plan, nb, Mmax, band_tasks_per_sweep(Mmax), w.bBw, w.bR2,
+                                        w.bT2, w.td, w.te))) != cudaSuccess)
+        return e;
+    return h->timing ? cudaEventRecord(h->band_ev[1], st) : cudaSuccess;
 }
 
 cudaError_t launch_band_backtransform(pfsm_handle_s *h, cudaStream_t st)
 {
     Workspace &w = h->ws;
     const int nb = h->nb, Mmax = h->Mmax, mmax = h->mmax;
+    const int32_t *plan = w.plan;
+    cudaError_t e;
+    // stage 2: y' = Q2 z on the transposed eigenvectors
     double *Yt = w.iiwork;                             // free again after the inverse iteration
     const dim3 gt((unsigned)((Mmax + 31) / 32), (unsigned)((mmax + 31) / 32), (unsigned)nb);
-    k_band_transpose<<<gt, 256, 0, st>>>(w.plan, nb, Mmax, mmax, false, w.sel_vec, Yt);
+    k_band_transpose<<<gt, 256, 0, st>>>(plan, nb, Mmax, mmax, false, w.sel_vec, Yt);
     g_launches++;
     k_band_bt2<<<dim3((unsigned)((mmax + 31) / 32), (unsigned)nb), 32 * kBtWarps, 0, st>>>(
-        w.plan, nb, Mmax, mmax, band_tasks_per_sweep(Mmax), w.bR2, w.bT2, Yt);
+        plan, nb, Mmax, mmax, band_tasks_per_sweep(Mmax), w.bR2, w.bT2, Yt);
     g_launches++;
-    k_band_transpose<<<gt, 256, 0, st>>>(w.plan, nb, Mmax, mmax, true, w.sel_vec, Yt);
+    k_band_transpose<<<gt, 256, 0, st>>>(plan, nb, Mmax, mmax, true, w.sel_vec, Yt);
     g_launches++;
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (h->timing && (e = cudaEventRecord(h->band_ev[2], st)) != cudaSuccess) return e;
+    // stage 1: y = Q1 y', panels last .. first, on the rows of sel_vec (vector t, entries j)
+    const int np = band_panels(Mmax);
+    const int64_t nbm = (int64_t)nb * mmax, nbM = (int64_t)nb * Mmax;
+    for (int p = np - 1; p >= 0; p--) {
+        const int c = p * KB, r0 = c + KB;
+        const int32_t *extp = w.bExt + (size_t)p * nb;
+        const int64_t ldk = padded_ld(Mmax - r0);
+        const SliceBuf dY{w.bdA, nbm, ldk, OZ_SLICES, 0}, dV{w.bdV, (int64_t)nb * KB, ldk, OZ_SLICES, 0};
+        // X = Yr V: the rows' entries r0 .. M-1 against the reflector rows (zero digits for a window
+        // without this panel, so its X, U and update vanish)
+        if ((e = launch_oz_split_win(w.sel_vec, (int64_t)mmax * Mmax, Mmax, 0, r0, extp, r0, 0, plan + nb, mmax, nb, dY,
+                                     mmax, 0, w.bdeA, st)) != cudaSuccess)
+            return e;
+        if ((e = launch_oz_split_win(w.refl, (int64_t)Mmax * Mmax, Mmax, c, r0, extp, r0, KB, nullptr, KB, nb, dV, KB, 0,
+                                     w.bdeV, st)) != cudaSuccess)
+            return e;
+        OzParams o{};
+        o.rows = mmax; o.cols = KB; o.cols_from_zero = 1; o.C = w.bY; o.ldc = KB; o.status = w.status;
+        o.zrow = mmax; o.zrow_q = KB; o.zc = (int64_t)mmax * KB; o.ext = plan + nb; o.ext_c = w.bKB;
+        if ((e = launch_gemm_oz(dY, w.bdeA, dV, w.bdeV, o, st, nb)) != cudaSuccess) return e;
+        // U = X T^T
+        k_band_bt1_u<<<dim3((unsigned)((mmax + 63) / 64), (unsigned)nb), 256, 0, st>>>(
+            plan, nb, mmax, w.bT + (size_t)p * nb * KB * KB, w.bY);
+        g_launches++;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // Yr[:, r0:M] -= U V^T
+        const SliceBuf dU{w.tdP, nbm, KB, OZ_SLICES, 0}, dW{w.tdQ, nbM, KB, OZ_SLICES, 0};
+        if ((e = launch_oz_split(w.bY, nbm, KB, KB, dU, w.tdeP, st)) != cudaSuccess) return e;
+        if ((e = launch_oz_split(w.bV + (size_t)p * nbM * KB, nbM, KB, KB, dW, w.tdeQ, st)) != cudaSuccess) return e;
+        OzParams u{};
+        u.rows = mmax; u.cols = Mmax; u.col_off = r0; u.C = w.sel_vec; u.ldc = Mmax; u.sub = 1; u.status = w.status;
+        u.zrow = mmax; u.zrow_q = Mmax; u.zc = (int64_t)mmax * Mmax; u.ext = plan + nb; u.ext_c = plan + 3 * nb;
+        if ((e = launch_gemm_oz(dU, w.tdeP, dW, w.tdeQ, u, st, nb)) != cudaSuccess) return e;
+    }
+    return launch_bt_finish(h, w.sel_vec, st);
 }
 
 }  // namespace pfsm

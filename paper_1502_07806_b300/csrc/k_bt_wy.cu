@@ -376,6 +376,16 @@ cudaError_t launch_backtransform_wy(pfsm_handle_s *h, cudaStream_t st, bool refl
     return cudaGetLastError();
 }
 
+cudaError_t launch_bt_finish(pfsm_handle_s *h, const double *Y, cudaStream_t st)
+{
+    Workspace &w = h->ws;
+    const int64_t warps = (int64_t)h->nb * h->mmax;
+    k_bt_finish<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(w.plan, h->nb, h->N, h->Mmax, h->mmax, Y, w.sel_val,
+                                                             w.gersh, h->prm.alpha_theta, w.X, w.eps, w.alpha);
+    g_launches++;
+    return cudaGetLastError();
+}
+
 cudaError_t join_side(pfsm_handle_s *h, cudaStream_t st)
 {
     if (!h->side_pending) return cudaSuccess;

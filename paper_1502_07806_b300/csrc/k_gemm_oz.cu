@@ -151,12 +151,16 @@ __global__ void k_oz_split(const T *__restrict__ src, int64_t rows, int64_t cols
 }
 
 // Batched over windows (blockIdx.y = window z): with n = ext[z] - ext_off, rows i in [0, n) (or
-// [0, rows_fixed) when rows_fixed > 0) of the n-column block whose first entry is
+// [0, rows_fixed) when rows_fixed > 0, or [0, rext[z]) when rext is given) of the n-column block
+// whose first entry is
 // src + z * src_z + row0 * ld + col0 (ld the row stride), into digit rows
 // z * dst_zrow + dst_row0 + i with K index = column - col0; columns n .. fill_to - 1 of each row
-// get zero digits (the K padding the products read).
+// get zero digits (the K padding the products read). zero_diag: entry (i, i) of the block is taken
+// as 0 and its value stored in dout[digit row].
 __global__ void k_oz_split_win(const double *__restrict__ src, int64_t src_z, int64_t ld, int64_t row0, int64_t col0,
-                               const int32_t *__restrict__ ext, int ext_off, int rows_fixed, int64_t fill_to,
+                               const int32_t *__restrict__ ext, int ext_off, int rows_fixed,
+                               const int32_t *__restrict__ rext, int zero_diag, double *__restrict__ dout,
+                               int64_t fill_to,
                                __nv_bfloat16 *__restrict__ dst, int64_t dst_zrow, int64_t dst_row0, int64_t sl_ld,
                                int64_t sstride, int32_t *__restrict__ exps)
 {
@@ -164,12 +168,12 @@ __global__ void k_oz_split_win(const double *__restrict__ src, int64_t src_z, in
     const int lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int64_t n = max(0, ext[z] - ext_off);                      // the window's extent
-    const int64_t nrows = rows_fixed > 0 ? rows_fixed : n;
+    const int64_t nrows = rows_fixed > 0 ? rows_fixed : (rext ? rext[z] : n);
     if (i >= nrows) return;
     const double *x = src + (int64_t)z * src_z + (row0 + i) * ld + col0;
     const int64_t drow = (int64_t)z * dst_zrow + dst_row0 + i;
-    oz_split_row<double>(x, n, fill_to, -1, nullptr, reinterpret_cast<unsigned short *>(dst + drow * sl_ld), sstride,
-                         exps + drow, lane);
+    oz_split_row<double>(x, n, fill_to, zero_diag ? i : -1, zero_diag ? dout + drow : nullptr,
+                         reinterpret_cast<unsigned short *>(dst + drow * sl_ld), sstride, exps + drow, lane);
 }
 
 // ---- product ---------------------------------------------------------------------------------
@@ -181,7 +185,7 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
     using namespace oz;
     const int z = blockIdx.z;
     const int row0 = prm.row_base + blockIdx.y * BM;
-    const int col0 = (prm.cols_from_zero ? 0 : prm.row_base) + blockIdx.x * BN;
+    const int col0 = (prm.cols_from_zero ? 0 : prm.row_base) + prm.col_off + blockIdx.x * BN;
     const int rows_lim = prm.ext ? prm.ext[z] : prm.rows;
     const int cols_lim = prm.ext_c ? prm.ext_c[z] : (prm.ext ? prm.ext[z] : prm.cols);
     if (row0 >= rows_lim || col0 >= cols_lim) return;              // tile outside this window
@@ -210,8 +214,18 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
     const uint32_t done_bar = bar_base + 8u * (2 * STAGES + 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    // 32-element K blocks; a lower-triangular P has no entries beyond column row0 + BM - 1
-    const int nkb = prm.p_lower ? min(prm.kblocks, (row0 + BM + KB - 1) / KB) : prm.kblocks;
+    // 32-element K blocks kb_lo .. kb_lo + nkb - 1: a lower-triangular P has no entries beyond
+    // column row0 + BM - 1; with krange64 only the K range of the tile's rows (union of the ranges
+    // of its two 64-row tiles) is read
+    int kb_lo = 0, kb_hi = prm.p_lower ? min(prm.kblocks, (row0 + BM + KB - 1) / KB) : prm.kblocks;
+    if (prm.krange64) {
+        const int t0 = row0 / 64, t1 = min(t0 + 1, prm.nrowtiles64 - 1);
+        const int kbeg = min(prm.krange64[2 * t0], prm.krange64[2 * t1]);
+        const int kend = max(prm.krange64[2 * t0 + 1], prm.krange64[2 * t1 + 1]);
+        kb_lo = min(kbeg / KB, kb_hi);
+        kb_hi = max(kb_lo, min(kb_hi, (kend + KB - 1) / KB));
+    }
+    const int nkb = kb_hi - kb_lo;
     const int kb_per_chunk = KCHUNK / KB;
     const int nch = (nkb + kb_per_chunk - 1) / kb_per_chunk;
 
@@ -256,8 +270,8 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
                 }
                 if (*abort_flag) break;
                 mbar_expect_tx(full_bar(s), stage_bytes);
-                tma_load_3d(stageP(s, 0), &mapP, full_bar(s), kb * KB, (int)(zr + row0), 0);
-                tma_load_3d(stageQ(s, 0), &mapQ, full_bar(s), kb * KB, (int)(zq + col0), 0);
+                tma_load_3d(stageP(s, 0), &mapP, full_bar(s), (kb_lo + kb) * KB, (int)(zr + row0), 0);
+                tma_load_3d(stageQ(s, 0), &mapQ, full_bar(s), (kb_lo + kb) * KB, (int)(zq + col0), 0);
                 issued = kb + 1;
             }
             for (int i = (issued > STAGES ? issued - STAGES : 0); i < issued; i++)
@@ -342,16 +356,42 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
         for (int j = 0; j < BN; j++) eb[lane][j] = ldexp((double)hi[j] + (double)lo[j], er + ecol[j]);
         __syncwarp();
         if (ok) {
+            // every global load of the lane's 32 rows (C for a subtracting product, V for the
+            // diagonal term) issued before the first store, so they are in flight together instead
+            // of one dependent round trip per row
             const int c = col0 + lane;
+            const bool cok = c < cols_lim;
+            const int64_t zvo = (int64_t)z * prm.zv, zdo = (int64_t)z * prm.zd;
+            const int64_t vcs = prm.vcs ? prm.vcs : 1;
+            const bool dterm = prm.dcol || prm.drow;
+            const double dc = (prm.dcol && cok) ? prm.dcol[zdo + c] : 0.0;
+            double cv[32], dv[32];
+#pragma unroll
             for (int rr = 0; rr < 32; rr++) {
                 const int gr = R0 + rr;
-                if (gr >= rows_lim) break;
-                if (c < cols_lim && !(prm.lower_only && c > gr)) {
+                const bool v = gr < rows_lim && cok && !(prm.lower_only && c > gr);
+                cv[rr] = (v && prm.sub) ? Cz[(int64_t)gr * prm.ldc + c] : 0.0;
+                dv[rr] = (v && dterm) ? prm.Vp[zvo + (int64_t)gr * prm.ldv + c * vcs] : 0.0;
+            }
+#pragma unroll
+            for (int rr = 0; rr < 32; rr++) {
+                const int gr = R0 + rr;
+                if (gr < rows_lim && cok && !(prm.lower_only && c > gr)) {
                     double res = eb[rr][lane];
-                    if (prm.dcol) res = fma(prm.Vp[(int64_t)gr * prm.ldv + c], prm.dcol[c], res);
+                    if (prm.win_plan) {
+                        // zero inside the window of the slice owning row gr (largest b, k0[b] <= gr)
+                        int lo = 0, hi = prm.win_nb - 1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (prm.win_plan[mid] <= gr) lo = mid; else hi = mid - 1;
+                        }
+                        const int ws = prm.win_plan[2 * prm.win_nb + lo];
+                        if (c >= ws && c < ws + prm.win_plan[3 * prm.win_nb + lo]) res = 0.0;
+                    }
+                    if (prm.dcol) res = fma(dv[rr], dc, res);
+                    if (prm.drow) res = fma(dv[rr], prm.drow[zdo + gr], res);
                     const int64_t o = (int64_t)gr * prm.ldc + c;
-                    if (prm.sub) Cz[o] -= res;
-                    else Cz[o] = res;
+                    Cz[o] = prm.sub ? cv[rr] - res : res;
                 }
             }
         }
@@ -386,13 +426,14 @@ cudaError_t launch_oz_split(const double *src, int64_t rows, int64_t cols, int64
 }
 
 cudaError_t launch_oz_split_win(const double *src, int64_t src_z, int64_t ld, int64_t row0, int64_t col0,
-                                const int32_t *ext, int ext_off, int rows_fixed, int max_rows, int nb,
-                                const SliceBuf &dst, int64_t dst_zrow, int64_t dst_row0, int32_t *exps,
-                                cudaStream_t st)
+                                const int32_t *ext, int ext_off, int rows_fixed, const int32_t *rext, int max_rows,
+                                int nb, const SliceBuf &dst, int64_t dst_zrow, int64_t dst_row0, int32_t *exps,
+                                cudaStream_t st, double *diag_out)
 {
     if (max_rows <= 0) return cudaSuccess;
     dim3 grid((unsigned)((max_rows + 1) / 2), (unsigned)nb);
-    k_oz_split_win<<<grid, 64, 0, st>>>(src, src_z, ld, row0, col0, ext, ext_off, rows_fixed, dst.ld,
+    k_oz_split_win<<<grid, 64, 0, st>>>(src, src_z, ld, row0, col0, ext, ext_off, rows_fixed, rext,
+                                        diag_out ? 1 : 0, diag_out, dst.ld,
                                         reinterpret_cast<__nv_bfloat16 *>(dst.ptr), dst_zrow, dst_row0, dst.ld,
                                         dst.ld * dst.rows, exps);
     g_launches++;
@@ -423,7 +464,8 @@ cudaError_t launch_gemm_oz(const SliceBuf &P, const int32_t *ep, const SliceBuf 
     prm.ep = ep;
     prm.eq = eq;
     // batched: prm.rows / prm.cols give the grid extent from row_base (the largest window)
-    const int ext_r = prm.rows - prm.row_base, ext_c = prm.cols - (prm.cols_from_zero ? 0 : prm.row_base);
+    const int ext_r = prm.rows - prm.row_base;
+    const int ext_c = prm.cols - (prm.cols_from_zero ? 0 : prm.row_base) - prm.col_off;
     if (ext_r <= 0 || ext_c <= 0) return cudaSuccess;
     dim3 grid((unsigned)((ext_c + oz::BN - 1) / oz::BN), (unsigned)((ext_r + oz::BM - 1) / oz::BM), (unsigned)batch);
     k_gemm_oz<<<grid, 192, oz_smem_bytes(), st>>>(mp, mq, prm);

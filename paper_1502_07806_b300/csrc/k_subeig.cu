@@ -1632,7 +1632,7 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
     }
     // mixed forms: the back-transform's steps that need only the reflectors run on the side
     // stream beside the eigenvalue and inverse-iteration kernels (one warp per SM)
-    const bool side_bt = h->prm.precision != PFSM_FP64 && w.btG && h->side;
+    const bool side_bt = h->prm.precision != PFSM_FP64 && w.btG && h->side && !h->tri_two_stage;
     if (side_bt) {
         if ((e0 = cudaEventRecord(h->fork_ev, st)) != cudaSuccess) return e0;
         if ((e0 = cudaStreamWaitEvent(h->side, h->fork_ev, 0)) != cudaSuccess) return e0;
@@ -1673,7 +1673,7 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
     // 4. back-transform + start vectors: the mixed forms apply the reflectors in compact-WY form
     //    with digit products on the tensor cores (k_bt_wy.cu), after the bulge-chasing reflectors
     //    when the reduction had two stages; the FP64 form one by one on the FP64 pipe
-    if (h->tri_two_stage && (e0 = launch_band_backtransform(h, st)) != cudaSuccess) return e0;
+    if (h->tri_two_stage) return launch_band_backtransform(h, st);
     if (h->prm.precision != PFSM_FP64 && w.btG) return launch_backtransform_wy(h, st, side_bt);
     {
         // vectors per CTA: the fewest for which sum_b ceil(m_b / vpc) <= N / vpc + nb CTAs fit

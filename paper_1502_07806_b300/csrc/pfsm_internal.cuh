@@ -76,9 +76,10 @@ struct Workspace {
     // U (nb x 32 x 32), the chunk partials of V^T W, the per-panel window extents, the band
     // storage of stage 2 and its reflectors (per window, sweep and task: 32 entries and beta)
     void *bdA = nullptr, *bdV = nullptr;
-    int32_t *bdeA = nullptr, *bdeV = nullptr, *bExt = nullptr;
+    int32_t *bdeA = nullptr, *bdeV = nullptr, *bExt = nullptr, *bKB = nullptr;
+    double *bV = nullptr;          // every panel's reflectors as rows j (panels x nb * Mmax x 32)
     double *bY = nullptr, *bT = nullptr, *bU = nullptr, *bXp = nullptr, *bBw = nullptr, *bR2 = nullptr,
-           *bT2 = nullptr;
+           *bT2 = nullptr, *bD = nullptr;   // bD: the trailing matrices' diagonals (nb * Mmax)
 };
 
 }  // namespace pfsm
@@ -124,6 +125,8 @@ struct pfsm_handle_s {
     cudaEvent_t ev[8] = {};
     cudaEvent_t sub_ev[4] = {};   // inside the submatrix phase (timing only)
     cudaEvent_t gs_ev[2] = {};    // inside Gram-Schmidt: after the overlap, after Cholesky
+    cudaEvent_t band_ev[3] = {};  // two-stage reduction: after the panels, after the bulge chase,
+                                  // after the bulge reflectors' back-transformation
     // mixed forms: a second stream for work that depends only on A or on the window reduction
     // (the Eq. 11 operand split of A, the back-transform's reflector preparation and V^T V), run
     // beside the window kernels that leave SMs idle; forked and joined through events
@@ -235,10 +238,18 @@ struct OzParams {
     int row_base;
     const int32_t *ext;
     int cols_from_zero;             // output columns start at 0 instead of row_base
+    int col_off;                    // ... and col_off further on
+    const int32_t *krange64;        // per 64-row tile K range (kbeg, kend) of P's rows, or null
+    int nrowtiles64;
+    const int32_t *win_plan;        // with win_nb: output (r, c) zero for c inside the window of
+    int win_nb;                     // the slice owning row r (the first Eq. 11 product)
     int64_t zrow_q;                 // Q's operand rows per window (0: zrow)
     const int32_t *ext_c;           // output column extents per window (null: ext)
     const double *Vp; int64_t ldv;  // with dcol: C[r, c] += Vp[r, c] dcol[c] (exact diagonal term)
     const double *dcol;
+    const double *drow;             // with drow instead: C[r, c] += Vp[r, c] drow[r]
+    int64_t vcs;                    // column stride of Vp (0: 1); Vp[r, c] = Vp[r ldv + c vcs]
+    int64_t zv, zd;                 // batched: window z's Vp and dcol / drow start z zv and z zd further
     int32_t *status;
 };
 cudaError_t configure_oz_kernels();
@@ -280,11 +291,12 @@ cudaError_t run_gen_to_std_sym(int64_t N, const double *A, const double *B, doub
 cudaError_t launch_oz_split(const double *src, int64_t rows, int64_t cols, int64_t ld, const SliceBuf &dst,
                             int32_t *exps, cudaStream_t st, bool zero_diag = false, double *d = nullptr);
 // batched over nb windows: ext[z] - ext_off rows (or rows_fixed rows) x (ext[z] - ext_off) columns
-// of the block at src + z * src_z + row0 * ld + col0, digits zero-filled to dst.ld (see k_gemm_oz.cu)
+// of the block at src + z * src_z + row0 * ld + col0, digits zero-filled to dst.ld (see k_gemm_oz.cu);
+// with diag_out, the block's diagonal is split off (digits of zero) and stored there
 cudaError_t launch_oz_split_win(const double *src, int64_t src_z, int64_t ld, int64_t row0, int64_t col0,
-                                const int32_t *ext, int ext_off, int rows_fixed, int max_rows, int nb,
-                                const SliceBuf &dst, int64_t dst_zrow, int64_t dst_row0, int32_t *exps,
-                                cudaStream_t st);
+                                const int32_t *ext, int ext_off, int rows_fixed, const int32_t *rext, int max_rows,
+                                int nb, const SliceBuf &dst, int64_t dst_zrow, int64_t dst_row0, int32_t *exps,
+                                cudaStream_t st, double *diag_out = nullptr);
 cudaError_t launch_oz_split_f32(const float *src, int64_t rows, int64_t cols, int64_t ld, const SliceBuf &dst,
                                 int32_t *exps, cudaStream_t st);
 cudaError_t launch_gemm_oz(const SliceBuf &P, const int32_t *ep, const SliceBuf &Q, const int32_t *eq,
@@ -313,7 +325,7 @@ inline size_t tri_panel_smem(int Mmax, int CL, int Mcap)
 // panel and bulge-chasing kernels, warps per bulge-chasing CTA
 constexpr int kBand = 32;
 constexpr int kPanelCL = 8;
-constexpr int kChaseCL = 4;
+constexpr int kChaseCL = 3;
 constexpr int kChaseWarps = 8;
 __host__ __device__ int band_panels(int M);
 size_t band_panel_smem(int Mmax);
@@ -322,6 +334,8 @@ int band_tasks_per_sweep(int Mmax);
 cudaError_t configure_band_kernels();
 cudaError_t launch_band_reduction(pfsm_handle_s *h, const double *A, cudaStream_t st);
 cudaError_t launch_band_backtransform(pfsm_handle_s *h, cudaStream_t st);
+// the start-vector rules on back-transformed window eigenvectors Y (rows t, entries j; k_bt_wy.cu)
+cudaError_t launch_bt_finish(pfsm_handle_s *h, const double *Y, cudaStream_t st);
 
 cudaError_t configure_dense_kernels();   // shared-memory attributes of k_dense.cu
 cudaError_t launch_gram_schmidt_f64(pfsm_handle_s *h, cudaStream_t st);

@@ -11,17 +11,23 @@ keyed by the SHA-256 of the input bytes (A and prev, row-major float64).
 Stored per workload (``tests/golden/<name>.npz``):
   sha256_A, sha256_prev, n, nblocks, halo, fs_iters   input identity and method parameters
   plan (4 x nblocks), lam, res, eps, alpha           every eigenvalue, residual, shift and step
+  sketch_seed, Sq                                    the sketch Omega V of EVERY eigenvector
+                                                     (Omega: SKETCH x n seeded N(0, 1)), quantised
   cols, Vq                                           sampled eigenvector columns, quantised
   xcols, Xq                                          sampled vectors after Eq. 11, quantised
+The sketch lets a test check every vector and every cluster of close eigenvalues without storing
+V: for unit vectors u, v, ||Omega (u - v)|| / sqrt(SKETCH) estimates ||u - v|| (a chi variable
+with SKETCH degrees of freedom), and Omega P Omega^T = (Omega V_C)(Omega V_C)^T sketches the
+projector P of a cluster C.
 Metal workload only:
   dA_rows, dA_cols, dA_vals     sampled entries of the oracle gradient dA (FP64)
   dA_diag                       its whole diagonal
   dir_seeds, dA_dot_dir         <dA, D_d> for 32 unit-Frobenius symmetric directions D_d
 
-Quantisation: a column entry v is stored as the integer rint(v * 2^40), byte planes split so the
-(mostly constant) high bytes deflate well. The absolute error per entry is <= 2^-41 (4.5e-13),
-so a stored unit column differs from the oracle's by < 2^-41 sqrt(N) = 4.3e-11 in norm, far below
-the 1e-8 projector bar the tests apply.
+Quantisation (fullsize_ref.py): a column entry v is stored as the integer rint(v * 2^40), byte
+planes split so the (mostly constant) high bytes deflate well. The absolute error per entry is
+<= 2^-41 (4.5e-13), so a stored unit column differs from the oracle's by < 2^-41 sqrt(N) = 4.3e-11
+in norm, far below the 1e-8 projector bar the tests apply.
 
 Usage: python tests/golden/make_fullsize.py [vacancy] [metal] [--threads T]
 A raw dump of the full oracle outputs goes to gpurun_out/oracle_cache/ (git-ignored) so that the
@@ -30,7 +36,6 @@ sample can be re-packed without re-running the oracle (--repack).
 from __future__ import annotations
 
 import argparse
-import hashlib
 import os
 import sys
 import time
@@ -40,11 +45,12 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
+sys.path.insert(0, HERE)
 
 import oracle  # noqa: E402
 import workloads as wl  # noqa: E402
+from fullsize_ref import quantise, sha256, sketch_matrix  # noqa: E402
 
-QSCALE = 2.0 ** 40
 CACHE = os.path.join(ROOT, "gpurun_out", "oracle_cache")
 
 # the <V, W> term of the metal loss and the directions of the directional-derivative check
@@ -54,38 +60,14 @@ DIR_SEED0 = 0x5EED0000
 N_DIRS = 32
 
 
-def sha256(a: np.ndarray) -> str:
-    return hashlib.sha256(np.ascontiguousarray(a, dtype=np.float64).tobytes()).hexdigest()
-
-
-def quantise(cols: np.ndarray) -> np.ndarray:
-    """(n, c) float64 -> (8, n * c) uint8 byte planes of rint(v * 2^40) as little-endian int64."""
-    q = np.rint(np.ascontiguousarray(cols) * QSCALE).astype("<i8")
-    return q.reshape(-1).view(np.uint8).reshape(-1, 8).T.copy()
-
-
-def dequantise(planes: np.ndarray, n: int) -> np.ndarray:
-    """Inverse of quantise: (8, n * c) byte planes -> (n, c) float64."""
-    q = np.ascontiguousarray(planes.T).reshape(-1).view("<i8")
-    return (q.astype(np.float64) / QSCALE).reshape(n, -1)
-
-
-def load(name: str) -> dict:
-    """The stored reference of workload ``name`` ("vacancy9072" or "metal7200") with the
-    sampled columns dequantised (keys V_cols, X_cols)."""
-    with np.load(os.path.join(HERE, f"{name}.npz")) as z:
-        d = {k: z[k] for k in z.files}
-    n = int(d["n"])
-    d["V_cols"] = dequantise(d["Vq"], n)
-    d["X_cols"] = dequantise(d["Xq"], n)
-    return d
-
-
-def sample_columns(p, count: int, seed: int) -> np.ndarray:
-    """Every member of a near-degenerate pair of previous eigenvalues (gap < 1e-5), then seeded
-    distinct indices up to ``count`` columns, ascending."""
-    prev = p.prev
-    close = np.nonzero(np.diff(prev) < 1e-5)[0]
+def sample_columns(p, count: int, seed: int, pair_gap: float, max_pairs: int) -> np.ndarray:
+    """Both members of up to max_pairs near-degenerate pairs of previous eigenvalues (gap <
+    pair_gap; a seeded choice when there are more), then seeded distinct indices up to ``count``
+    columns, ascending."""
+    close = np.nonzero(np.diff(p.prev) < pair_gap)[0]
+    if close.size > max_pairs:
+        order = np.argsort(wl.raw_u64(seed + 1, 0, close.size), kind="stable")
+        close = np.sort(close[order[:max_pairs]])
     pick = set(close.tolist()) | set((close + 1).tolist())
     u = wl.raw_u64(seed, 0, 8 * count)
     for v in u:
@@ -123,13 +105,16 @@ def metal_gradient(p, r: dict, threads: int):
     return dA
 
 
-def pack(p, r: dict, ncols: int, nx: int, seed: int, extra: dict | None = None) -> str:
-    cols = sample_columns(p, ncols, seed)
+def pack(p, r: dict, ncols: int, nx: int, seed: int, pair_gap: float, max_pairs: int,
+         extra: dict | None = None) -> str:
+    cols = sample_columns(p, ncols, seed, pair_gap, max_pairs)
     xcols = cols[np.linspace(0, cols.size - 1, nx).round().astype(np.int64)]
+    sketch_seed = seed + 7
+    Om = sketch_matrix(p.n, sketch_seed)
     out = dict(sha256_A=sha256(p.A), sha256_prev=sha256(p.prev), n=p.n, nblocks=p.nblocks,
                halo=p.halo, fs_iters=p.fs_iters, plan=r["plan"], lam=r["lam"], res=r["res"],
-               eps=r["eps"], alpha=r["alpha"], cols=cols, Vq=quantise(r["V"][:, cols]),
-               xcols=xcols, Xq=quantise(r["xfs"][:, xcols]))
+               eps=r["eps"], alpha=r["alpha"], sketch_seed=sketch_seed, Sq=quantise(Om @ r["V"]),
+               cols=cols, Vq=quantise(r["V"][:, cols]), xcols=xcols, Xq=quantise(r["xfs"][:, xcols]))
     if extra:
         out.update(extra)
     path = os.path.join(HERE, f"{p.name}.npz")
@@ -147,7 +132,9 @@ def main():
     if "vacancy" in args.which:
         p = wl.vacancy_like()
         r = run_oracle(p, args.threads)
-        pack(p, r, ncols=256, nx=32, seed=wl.seed_for(3, 900))
+        # 24 of the 122 pairs of previous eigenvalues 1e-6 apart or closer (90 planted, 32 natural)
+        # in full, every vector and pair through the sketch
+        pack(p, r, ncols=64, nx=16, seed=wl.seed_for(3, 900), pair_gap=1.01e-6, max_pairs=24)
     if "metal" in args.which:
         p = wl.metal_like()
         r = run_oracle(p, args.threads)
@@ -163,7 +150,7 @@ def main():
         cols = (u[1::2] % np.uint64(n)).astype(np.int64)
         seeds = np.array([DIR_SEED0 + d for d in range(N_DIRS)], dtype=np.int64)
         dots = np.array([float(np.sum(dA * wl.symmetric_direction(n, int(s)))) for s in seeds])
-        pack(p, r, ncols=128, nx=16, seed=wl.seed_for(5, 901),
+        pack(p, r, ncols=48, nx=16, seed=wl.seed_for(5, 901), pair_gap=1e-7, max_pairs=8,
              extra=dict(dA_rows=rows, dA_cols=cols, dA_vals=dA[rows, cols], dA_diag=np.diag(dA).copy(),
                         dir_seeds=seeds, dA_dot_dir=dots, w_seed=W_SEED, occupied=OCCUPIED))
 
