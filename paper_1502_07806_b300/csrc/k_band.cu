@@ -16,7 +16,8 @@
 //       Y = A22 V      FP64-accurate digit product on the tensor cores (k_gemm_oz.cu) of the
 //                      off-diagonal part, the diagonal part added exactly in FP64;
 //       k_band_w/u/z   W = Y T, U = T^T (V^T W), Z = W - V U / 2 on the FP64 pipe;
-//       A22 -= V Z^T + Z V^T   digit product, subtracted into the window.
+//       A22 -= V Z^T + Z V^T   digit product (K = 64: the strip kernel, a CTA keeping its rows'
+//                      digits and walking a strip of column tiles), subtracted into the window.
 //     The O(M^3) work of this stage runs on the tensor cores at FP64 accuracy.
 //  2. band -> tridiagonal by bulge chasing (k_band_chase, FP64): sweep s annihilates column s below
 //     its subdiagonal with one reflector on rows s+1 .. s+KB and then chases the bulge down the
@@ -25,7 +26,8 @@
 //     following sweeps. Tasks (s, i) run at time 3 s + i, so every time step's tasks touch disjoint
 //     band columns; one cluster per window, one warp per task, a cluster barrier per time step.
 //  3. the tridiagonal's eigenpairs as before (k_bisect, k_inverse_iter);
-//  4. y = Q1 Q2 z: Q2's reflectors applied to the eigenvectors z on the FP64 pipe (k_band_bt2),
+//  4. y = Q1 Q2 z: Q2's reflectors applied to the eigenvectors z in float-float arithmetic on the
+//     FP32 pipe (k_band_bt2),
 //     then Q1 panel by panel, Yr <- Yr - (Yr V T^T) V^T with two digit products per panel
 //     (k_band_bt1_u forms X T^T), and the start-vector rules (k_bt_wy.cu).
 // The FP64 form keeps the one-stage reduction (no tensor cores).
@@ -45,6 +47,7 @@ constexpr int KB = kBand;
 constexpr int kPanelThreads = 256;
 constexpr int kChunk = 64;                 // rows per CTA of the W / Z kernels
 constexpr int kBtWarps = 8;                // k_band_bt2: warps per CTA (32 vectors per CTA)
+constexpr int kStrip = 8;                  // column tiles per CTA of the small-K digit products
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -556,19 +559,50 @@ k_band_chase(const int32_t *__restrict__ plan, int nb, int Mmax, int NT, double 
 }
 
 // ---- back-transformation of stage 2: y = Q2 z ----------------------------------------------------
-// Yt[b] holds the window's eigenvectors transposed (row j, column t; ld = mmax). Grid
-// (ceil(mmax / 32), nb), 256 threads: lane = vector t0 + lane, the reflectors of a sweep (disjoint
-// rows) spread over the 8 warps, sweeps in reverse order with a CTA barrier between them.
+// About 2.4e6 reflectors of 32 entries per solve touch the 252 eigenvectors of each window: 2 M^2 m
+// FMAs per window, 65 ms on the FP64 pipe at its peak. They are applied in float-float arithmetic
+// on the FP32 pipe (64 times the FP64 rate): a value is the unevaluated sum hi + lo of two floats
+// (48 significant bits), products split exactly by FMA (Dekker / Knuth two-product and two-sum,
+// as in the double-float arithmetic of Hida, Li and Bailey), which keeps the vectors to ~1e-15
+// relative per reflector (about 1e-13 after the ~2000 reflectors an entry meets). The vectors are
+// held transposed (row j, column t) as float2 pairs; the reflector v and beta v are converted per
+// task (one entry per lane).
+struct ff { float h, l; };
+
+__device__ __forceinline__ ff ff_from(double x)
+{
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+
+__device__ __forceinline__ double ff_to(ff a) { return (double)a.h + (double)a.l; }
+
+// (s_h + s_l) += (a_h + a_l)(b_h + b_l): exact product of the high parts, cross terms by FMA. The
+// rounded operations are written as intrinsics so that the compiler cannot contract them into
+// FMAs (which would break the exact two-sum).
+__device__ __forceinline__ void ff_fma_acc(float &sh, float &sl, float ah, float al, float bh, float bl)
+{
+    const float p = __fmul_rn(ah, bh);
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, fmaf(al, bh, e));
+    const float t = __fadd_rn(sh, p), bv = __fsub_rn(t, sh);
+    sl = __fadd_rn(sl, __fadd_rn(__fadd_rn(__fsub_rn(sh, __fsub_rn(t, bv)), __fsub_rn(p, bv)), e));
+    sh = t;
+}
+
+// Yt[b] holds the window's eigenvectors transposed as float-float (row j, column t; ld = mmax).
+// Grid (ceil(mmax / 32), nb), 256 threads: lane = vector t0 + lane, the reflectors of a sweep
+// (disjoint rows) spread over the 8 warps, sweeps in reverse order with a CTA barrier between them.
 __global__ void __launch_bounds__(32 * kBtWarps)
 k_band_bt2(const int32_t *__restrict__ plan, int nb, int Mmax, int mmax, int NT, const double *__restrict__ refl2,
-           const double *__restrict__ tau2, double *__restrict__ Yt)
+           const double *__restrict__ tau2, float2 *__restrict__ Yt)
 {
     const int b = blockIdx.y;
     const int mb = plan[nb + b], M = plan[3 * nb + b];
     const int t0 = blockIdx.x * 32;
     if (t0 >= mb) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double *Y = Yt + (size_t)b * Mmax * mmax + t0 + lane;
+    float2 *Y = Yt + (size_t)b * Mmax * mmax + t0 + lane;
     const bool act = t0 + lane < mb;
     for (int s = M - 3; s >= 0; s--) {
         const int ntask = (M - 2 - s + KB - 1) / KB;
@@ -576,37 +610,47 @@ k_band_bt2(const int32_t *__restrict__ plan, int nb, int Mmax, int mmax, int NT,
             const size_t slot = ((size_t)b * Mmax + s) * NT + i;
             const double beta = tau2[slot];
             if (beta == 0.0) continue;
-            const double vl = refl2[slot * KB + lane];    // zero past the reflector's length
+            const double vd = refl2[slot * KB + lane];     // zero past the reflector's length
+            const ff v = ff_from(vd), wv = ff_from(beta * vd);
             const int a = s + 1 + i * KB;
             const int L = min(KB, M - a);
-            // the lane's L entries loaded together, four partial dot products
-            double yv[KB];
+            float2 yv[KB];
 #pragma unroll
-            for (int r = 0; r < KB; r++) yv[r] = (act && r < L) ? Y[(size_t)(a + r) * mmax] : 0.0;
-            double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+            for (int r = 0; r < KB; r++) yv[r] = (act && r < L) ? Y[(size_t)(a + r) * mmax] : make_float2(0.f, 0.f);
+            // d = v . y in float-float, two accumulators
+            float dh0 = 0.f, dl0 = 0.f, dh1 = 0.f, dl1 = 0.f;
 #pragma unroll
-            for (int r = 0; r < KB; r += 4) {
-                d0 = fma(__shfl_sync(0xffffffffu, vl, r), yv[r], d0);
-                d1 = fma(__shfl_sync(0xffffffffu, vl, r + 1), yv[r + 1], d1);
-                d2 = fma(__shfl_sync(0xffffffffu, vl, r + 2), yv[r + 2], d2);
-                d3 = fma(__shfl_sync(0xffffffffu, vl, r + 3), yv[r + 3], d3);
+            for (int r = 0; r < KB; r += 2) {
+                ff_fma_acc(dh0, dl0, __shfl_sync(0xffffffffu, v.h, r), __shfl_sync(0xffffffffu, v.l, r), yv[r].x,
+                           yv[r].y);
+                ff_fma_acc(dh1, dl1, __shfl_sync(0xffffffffu, v.h, r + 1), __shfl_sync(0xffffffffu, v.l, r + 1),
+                           yv[r + 1].x, yv[r + 1].y);
             }
-            const double d = beta * ((d0 + d1) + (d2 + d3));
+            float dh = dh0, dl = dl0;
+            {
+                const float t = __fadd_rn(dh, dh1), bv = __fsub_rn(t, dh);
+                dl = __fadd_rn(__fadd_rn(dl, dl1), __fadd_rn(__fsub_rn(dh, __fsub_rn(t, bv)), __fsub_rn(dh1, bv)));
+                dh = t;
+            }
+            // y_r -= d (beta v_r), then renormalised
 #pragma unroll
             for (int r = 0; r < KB; r++) {
-                const double vr = __shfl_sync(0xffffffffu, vl, r);
-                if (act && r < L) Y[(size_t)(a + r) * mmax] = fma(-d, vr, yv[r]);
+                const float bh = __shfl_sync(0xffffffffu, wv.h, r), bl = __shfl_sync(0xffffffffu, wv.l, r);
+                float sh = yv[r].x, sl = yv[r].y;
+                ff_fma_acc(sh, sl, -dh, -dl, bh, bl);
+                const float h = __fadd_rn(sh, sl);
+                if (act && r < L) Y[(size_t)(a + r) * mmax] = make_float2(h, __fsub_rn(sl, __fsub_rn(h, sh)));
             }
         }
         __syncthreads();
     }
 }
 
-// sel_vec (rows t, entries j) <-> Yt (rows j, columns t), 32 x 32 tiles. Grid
+// sel_vec (rows t, entries j, FP64) <-> Yt (rows j, columns t, float-float), 32 x 32 tiles. Grid
 // (ceil(Mmax / 32), ceil(mmax / 32), nb), 256 threads.
 __global__ void __launch_bounds__(256)
 k_band_transpose(const int32_t *__restrict__ plan, int nb, int Mmax, int mmax, bool to_rows,
-                 double *__restrict__ sel_vec, double *__restrict__ Yt)
+                 double *__restrict__ sel_vec, float2 *__restrict__ Yt)
 {
     __shared__ double tile[32][33];
     const int b = blockIdx.z;
@@ -615,7 +659,7 @@ k_band_transpose(const int32_t *__restrict__ plan, int nb, int Mmax, int mmax, b
     if (j0 >= M || t0 >= mb) return;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     double *sv = sel_vec + (size_t)b * mmax * Mmax;
-    double *yt = Yt + (size_t)b * Mmax * mmax;
+    float2 *yt = Yt + (size_t)b * Mmax * mmax;
     if (!to_rows) {
         for (int q = ty; q < 32; q += 8) {
             const int t = t0 + q, j = j0 + tx;
@@ -624,12 +668,20 @@ k_band_transpose(const int32_t *__restrict__ plan, int nb, int Mmax, int mmax, b
         __syncthreads();
         for (int q = ty; q < 32; q += 8) {
             const int j = j0 + q, t = t0 + tx;
-            if (j < M && t < mb) yt[(size_t)j * mmax + t] = tile[tx][q];
+            if (j < M && t < mb) {
+                const ff f = ff_from(tile[tx][q]);
+                yt[(size_t)j * mmax + t] = make_float2(f.h, f.l);
+            }
         }
     } else {
         for (int q = ty; q < 32; q += 8) {
             const int j = j0 + q, t = t0 + tx;
-            tile[q][tx] = (j < M && t < mb) ? yt[(size_t)j * mmax + t] : 0.0;
+            if (j < M && t < mb) {
+                const float2 f = yt[(size_t)j * mmax + t];
+                tile[q][tx] = ff_to({f.x, f.y});
+            } else {
+                tile[q][tx] = 0.0;
+            }
         }
         __syncthreads();
         for (int q = ty; q < 32; q += 8) {
@@ -776,7 +828,7 @@ cudaError_t launch_band_reduction(pfsm_handle_s *h, const double *A, cudaStream_
         OzParams u{};
         u.rows = Mmax; u.cols = Mmax; u.C = w.iiwork; u.ldc = Mmax; u.sub = 1; u.status = w.status;
         u.zrow = Mmax; u.zc = MM; u.row_base = r0; u.ext = extp;
-        if ((e = launch_gemm_oz(dP, w.tdeP, dQ, w.tdeQ, u, st, nb)) != cudaSuccess) return e;
+        if ((e = launch_gemm_oz_strip(dP, w.tdeP, dQ, w.tdeQ, u, st, nb, kStrip)) != cudaSuccess) return e;
     }
     if (h->timing && (e = cudaEventRecord(h->band_ev[0], st)) != cudaSuccess) return e;
     k_band_extract<<<dim3((unsigned)((Mmax + 2 * KB + 7) / 8), (unsigned)nb), 256, 0, st>>>(plan, nb, Mmax, w.iiwork,
@@ -808,7 +860,7 @@ cudaError_t launch_band_backtransform(pfsm_handle_s *h, cudaStream_t st)
     const int32_t *plan = w.plan;
     cudaError_t e;
     // stage 2: y' = Q2 z on the transposed eigenvectors
-    double *Yt = w.iiwork;                             // free again after the inverse iteration
+    float2 *Yt = reinterpret_cast<float2 *>(w.iiwork);   // free again after the inverse iteration
     const dim3 gt((unsigned)((Mmax + 31) / 32), (unsigned)((mmax + 31) / 32), (unsigned)nb);
     k_band_transpose<<<gt, 256, 0, st>>>(plan, nb, Mmax, mmax, false, w.sel_vec, Yt);
     g_launches++;
@@ -851,7 +903,7 @@ cudaError_t launch_band_backtransform(pfsm_handle_s *h, cudaStream_t st)
         OzParams u{};
         u.rows = mmax; u.cols = Mmax; u.col_off = r0; u.C = w.sel_vec; u.ldc = Mmax; u.sub = 1; u.status = w.status;
         u.zrow = mmax; u.zrow_q = Mmax; u.zc = (int64_t)mmax * Mmax; u.ext = plan + nb; u.ext_c = plan + 3 * nb;
-        if ((e = launch_gemm_oz(dU, w.tdeP, dW, w.tdeQ, u, st, nb)) != cudaSuccess) return e;
+        if ((e = launch_gemm_oz_strip(dU, w.tdeP, dW, w.tdeQ, u, st, nb, kStrip)) != cudaSuccess) return e;
     }
     return launch_bt_finish(h, w.sel_vec, st);
 }

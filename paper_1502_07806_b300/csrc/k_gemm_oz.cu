@@ -79,6 +79,21 @@ __device__ __forceinline__ unsigned short oz_digit_bf16(uint32_t field)
 // largest |entry| into *eout and the S digit slices of entry c at out[c + s * sstride]; columns
 // cols .. fill_to - 1 get zero digits. diag_col >= 0: that entry is taken as 0 (its value stored
 // in *dval when dval is given).
+// f 2^e as a double for a float f: sign, exponent and significand moved by integer operations
+// (B300's FP64 pipe retires one warp instruction per 16 cycles per SM, and the float-to-double
+// conversion and ldexp run on it); zeros directly, the rare subnormal, infinite or out-of-range
+// cases by the conversion and ldexp. Equal to ldexp((double)f, e) for every input.
+__device__ __forceinline__ double oz_f2d_scaled(float f, int e)
+{
+    const uint32_t u = __float_as_uint(f);
+    if ((u << 1) == 0u) return __longlong_as_double((long long)(u >> 31) << 63);
+    const int ex = (int)((u >> 23) & 0xFFu);
+    const int dex = ex - 127 + 1023 + e;
+    if (ex == 0 || ex == 255 || dex <= 0 || dex >= 2047) return ldexp((double)f, e);
+    return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) | ((unsigned long long)dex << 52) |
+                                            ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+
 template <typename T>
 __device__ __forceinline__ void oz_split_row(const T *__restrict__ x, int64_t cols, int64_t fill_to, int64_t diag_col,
                                              double *dval, unsigned short *__restrict__ out, int64_t sstride,
@@ -353,7 +368,7 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
         const int R0 = row0 + 32 * gq;
         const int er = (ok && r < rows_lim) ? prm.ep[zr + r] : 0;
 #pragma unroll
-        for (int j = 0; j < BN; j++) eb[lane][j] = ldexp((double)hi[j] + (double)lo[j], er + ecol[j]);
+        for (int j = 0; j < BN; j++) eb[lane][j] = oz_f2d_scaled(hi[j], er + ecol[j]) + oz_f2d_scaled(lo[j], er + ecol[j]);
         __syncwarp();
         if (ok) {
             // every global load of the lane's 32 rows (C for a subtracting product, V for the
@@ -404,15 +419,225 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
     }
 }
 
+// ---- small-K products over column strips --------------------------------------------------------
+// The same digit product for K <= 64 (the rank-64 trailing updates of the two-stage reduction and
+// its panel back-transformation), where k_gemm_oz's per-tile costs dominate: every 128 x 32 tile
+// would reload 112 KB of P digits for 28 KB of Q digits and allocate its own tensor memory. Here a
+// CTA keeps its 128-row tile of P digits (all K blocks) in shared memory and walks a strip of up to
+// `strip` column tiles: Q digits through a two-stage ring, the level sums of tile t in TMEM buffer
+// t & 1 (levels at columns 32 L), so the drain and the C update of a tile overlap the MMAs of the
+// next. K <= 64 < one exact 512-term chunk, so every tile is one exact level sum. Warp roles as in
+// k_gemm_oz (0: TMA, 1: TMEM owner and MMA issuer, 2-5: drain and epilogue); every wait bounded.
+namespace ozs {
+constexpr int MAXKB = 2;                                  // K <= 64
+constexpr int QST = 2;                                    // Q ring stages
+constexpr int P_BYTES = MAXKB * OZ_SLICES * oz::P_TILE;   // 112 KB
+constexpr int QSTAGE = MAXKB * OZ_SLICES * oz::Q_TILE;    // 28 KB
+constexpr int EB_BYTES = 4 * 32 * (oz::BN + 1) * 8;       // per-warp epilogue staging
+}  // namespace ozs
+
+__global__ void __launch_bounds__(192, 1)
+k_gemm_oz_strip(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUtensorMap mapQ, OzParams prm,
+                int strip)
+{
+    using namespace tc;
+    using namespace oz;
+    const int z = blockIdx.z;
+    const int row0 = prm.row_base + blockIdx.y * BM;
+    const int cbase = (prm.cols_from_zero ? 0 : prm.row_base) + prm.col_off;
+    const int rows_lim = prm.ext ? prm.ext[z] : prm.rows;
+    const int cols_lim = prm.ext_c ? prm.ext_c[z] : (prm.ext ? prm.ext[z] : prm.rows);
+    const int ct0 = blockIdx.x * strip;
+    if (row0 >= rows_lim) return;
+    // column tiles of this strip inside the window
+    int nt = 0;
+    while (nt < strip && cbase + (ct0 + nt) * BN < cols_lim) nt++;
+    if (nt == 0) return;
+    const int64_t zr = (int64_t)z * prm.zrow;
+    const int64_t zq = (int64_t)z * (prm.zrow_q ? prm.zrow_q : prm.zrow);
+    double *Cz = prm.C + (int64_t)z * prm.zc;
+    const int LV = (prm.levels > 0 && prm.levels < OZ_LEVELS) ? prm.levels : OZ_LEVELS;
+    const int NSL = LV;
+    const int nkb = prm.kblocks;                                  // 1 or 2
+    extern __shared__ __align__(1024) uint8_t smraw[];
+    const uint32_t raw = smem_u32(smraw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *gbase = smraw + (base - raw);
+    const uint32_t pbase = base, qbase = base + ozs::P_BYTES;
+    double *ebuf = reinterpret_cast<double *>(gbase + ozs::P_BYTES + ozs::QST * ozs::QSTAGE);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + ozs::P_BYTES + ozs::QST * ozs::QSTAGE + ozs::EB_BYTES);
+    // bars: pfull, qfull[2], qempty[2], accf[2], acce[2], done
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 10);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    const uint32_t bb = smem_u32(bars);
+    const uint32_t pfull = bb;
+    auto qfull = [&](int s) { return bb + 8u * (1 + s); };
+    auto qempty = [&](int s) { return bb + 8u * (3 + s); };
+    auto accf = [&](int b) { return bb + 8u * (5 + b); };
+    auto acce = [&](int b) { return bb + 8u * (7 + b); };
+    const uint32_t done_bar = bb + 8u * 9;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        mbar_init(pfull, 1);
+        for (int q = 0; q < ozs::QST; q++) {
+            mbar_init(qfull(q), 1);
+            mbar_init(qempty(q), 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(accf(b), 1);
+            mbar_init(acce(b), 128);
+        }
+        mbar_init(done_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapP) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapQ) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem_acc = *tmem_slot;
+    auto pslice = [&](int kb, int sl) { return pbase + (uint32_t)((kb * NSL + sl) * P_TILE); };
+    auto qslice = [&](int st, int kb, int sl) {
+        return qbase + (uint32_t)(st * ozs::QSTAGE + (kb * NSL + sl) * Q_TILE);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            mbar_expect_tx(pfull, nkb * NSL * P_TILE);
+            for (int kb = 0; kb < nkb; kb++) tma_load_3d(pslice(kb, 0), &mapP, pfull, kb * KB, (int)(zr + row0), 0);
+            int issued = 0;
+            for (int t = 0; t < nt; t++) {
+                const int st = t % ozs::QST, round = t / ozs::QST;
+                if (round > 0 && !mbar_wait(qempty(st), (round - 1) & 1)) {
+                    set_status(prm.status, PFSM_ERR_TIMEOUT);
+                    *abort_flag = 1;
+                    break;
+                }
+                if (*abort_flag) break;
+                const int col0 = cbase + (ct0 + t) * BN;
+                mbar_expect_tx(qfull(st), nkb * NSL * Q_TILE);
+                for (int kb = 0; kb < nkb; kb++)
+                    tma_load_3d(qslice(st, kb, 0), &mapQ, qfull(st), kb * KB, (int)(zq + col0), 0);
+                issued = t + 1;
+            }
+            // every copy this warp issued has landed before the CTA can exit
+            mbar_wait(pfull, 0);
+            for (int i = (issued > ozs::QST ? issued - ozs::QST : 0); i < issued; i++)
+                mbar_wait(qfull(i % ozs::QST), (i / ozs::QST) & 1);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            bool ok = mbar_wait(pfull, 0);
+            for (int t = 0; t < nt && ok; t++) {
+                const int buf = t & 1, st = t % ozs::QST;
+                if (t >= 2 && !mbar_wait(acce(buf), ((t >> 1) - 1) & 1)) { ok = false; break; }
+                if (!mbar_wait(qfull(st), (t / ozs::QST) & 1) || *abort_flag) { ok = false; break; }
+                fence_after();
+                const uint32_t dbuf = tmem_acc + BUF_COLS * buf;
+                for (int kb = 0; kb < nkb; kb++)
+                    for (int h = 0; h < 2; h++)
+                        for (int sa = 0; sa < NSL; sa++) {
+                            const uint32_t acc = (kb == 0 && h == 0 && sa == 0) ? 0u : 1u;
+                            umma_bf16_n(dbuf + 32u * sa, sw64_desc(pslice(kb, sa)) + 2 * h,
+                                        sw64_desc(qslice(st, kb, 0)) + 2 * h, BN * (LV - sa), acc);
+                        }
+                umma_commit(qempty(st));
+                umma_commit(accf(buf));
+            }
+            if (!ok) {
+                set_status(prm.status, PFSM_ERR_TIMEOUT);
+                *abort_flag = 1;
+            }
+            umma_commit(done_bar);
+            mbar_wait(done_bar, 0);
+        }
+        __syncwarp();
+    } else {
+        const int gq = warp & 3;
+        const int r = row0 + 32 * gq + lane;
+        const int er = (r < rows_lim) ? prm.ep[zr + r] : 0;
+        double(*eb)[BN + 1] = reinterpret_cast<double(*)[BN + 1]>(ebuf) + 32 * gq;
+        const int R0 = row0 + 32 * gq;
+        for (int t = 0; t < nt; t++) {
+            const int buf = t & 1;
+            bool got = mbar_wait(accf(buf), (t >> 1) & 1);
+            got = __all_sync(0xffffffffu, got) && !*abort_flag;
+            if (!got) {
+                set_status(prm.status, PFSM_ERR_TIMEOUT);
+                *abort_flag = 1;
+                break;
+            }
+            fence_after();
+            float hi[BN], lo[BN];
+#pragma unroll
+            for (int j = 0; j < BN; j++) { hi[j] = 0.0f; lo[j] = 0.0f; }
+            for (int L = 0; L < LV; L++) {
+                const float scale = __int_as_float((127 - 12 - BETA * L) << 23);   // 2^-(12 + 7 L)
+                uint32_t v[32];
+                tmem_ld32(tmem_acc + ((uint32_t)(32 * gq) << 16) + BUF_COLS * buf + 32u * L, v);
+#pragma unroll
+                for (int j = 0; j < 32; j++) {
+                    const float x = __uint_as_float(v[j]) * scale;
+                    const float sum = hi[j] + x, bp = sum - hi[j];
+                    lo[j] += (hi[j] - (sum - bp)) + (x - bp);
+                    hi[j] = sum;
+                }
+            }
+            fence_before();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce(buf)) : "memory");
+            const int col0 = cbase + (ct0 + t) * BN;
+            const int c = col0 + lane;
+            const bool cok = c < cols_lim;
+            const int ec = cok ? prm.eq[zq + c] : 0;
+#pragma unroll
+            for (int j = 0; j < BN; j++) {
+                const int es = er + __shfl_sync(0xffffffffu, ec, j);
+                eb[lane][j] = oz_f2d_scaled(hi[j], es) + oz_f2d_scaled(lo[j], es);
+            }
+            __syncwarp();
+            double cv[32];
+#pragma unroll
+            for (int rr = 0; rr < 32; rr++) {
+                const int gr = R0 + rr;
+                cv[rr] = (prm.sub && gr < rows_lim && cok) ? Cz[(int64_t)gr * prm.ldc + c] : 0.0;
+            }
+#pragma unroll
+            for (int rr = 0; rr < 32; rr++) {
+                const int gr = R0 + rr;
+                if (gr < rows_lim && cok) Cz[(int64_t)gr * prm.ldc + c] = prm.sub ? cv[rr] - eb[rr][lane] : eb[rr][lane];
+            }
+            __syncwarp();
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_acc), "r"(oz::TMEM_COLS) : "memory");
+    }
+}
+
 // ---- host side -------------------------------------------------------------------------------
 
 namespace {
 size_t oz_smem_bytes() { return (size_t)oz::STAGES * oz::MAX_STAGE_BYTES + 1024 + 512; }
 }
 
+size_t oz_strip_smem_bytes() { return (size_t)ozs::P_BYTES + ozs::QST * ozs::QSTAGE + ozs::EB_BYTES + 1024 + 256; }
+
 cudaError_t configure_oz_kernels()
 {
-    return cudaFuncSetAttribute(k_gemm_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_gemm_oz_strip, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)oz_strip_smem_bytes());
 }
 
 cudaError_t launch_oz_split(const double *src, int64_t rows, int64_t cols, int64_t ld, const SliceBuf &dst,
@@ -469,6 +694,31 @@ cudaError_t launch_gemm_oz(const SliceBuf &P, const int32_t *ep, const SliceBuf 
     if (ext_r <= 0 || ext_c <= 0) return cudaSuccess;
     dim3 grid((unsigned)((ext_c + oz::BN - 1) / oz::BN), (unsigned)((ext_r + oz::BM - 1) / oz::BM), (unsigned)batch);
     k_gemm_oz<<<grid, 192, oz_smem_bytes(), st>>>(mp, mq, prm);
+    g_launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_oz_strip(const SliceBuf &P, const int32_t *ep, const SliceBuf &Q, const int32_t *eq,
+                                 OzParams prm, cudaStream_t st, int batch, int strip)
+{
+    CUtensorMap mp, mq;
+    cudaError_t e;
+    const int nsl = (prm.levels > 0 && prm.levels < OZ_LEVELS) ? prm.levels : OZ_LEVELS;
+    if (P.ns != OZ_SLICES || Q.ns != OZ_SLICES || P.kind != 0 || Q.kind != 0 || P.ld != Q.ld || P.ld % oz::KB ||
+        P.ld > ozs::MAXKB * oz::KB || prm.lower_only || prm.p_lower || prm.dcol || prm.drow || prm.win_plan ||
+        prm.krange64 || strip < 1)
+        return cudaErrorInvalidValue;
+    if ((e = make_slice_map64(&mp, P, oz::BM, nsl)) != cudaSuccess) return e;
+    if ((e = make_slice_map64(&mq, Q, oz::BN, nsl)) != cudaSuccess) return e;
+    prm.kblocks = (int)(P.ld / oz::KB);
+    prm.ep = ep;
+    prm.eq = eq;
+    const int ext_r = prm.rows - prm.row_base;
+    const int ext_c = prm.cols - (prm.cols_from_zero ? 0 : prm.row_base) - prm.col_off;
+    if (ext_r <= 0 || ext_c <= 0) return cudaSuccess;
+    const int nct = (ext_c + oz::BN - 1) / oz::BN;
+    dim3 grid((unsigned)((nct + strip - 1) / strip), (unsigned)((ext_r + oz::BM - 1) / oz::BM), (unsigned)batch);
+    k_gemm_oz_strip<<<grid, 192, oz_strip_smem_bytes(), st>>>(mp, mq, prm, strip);
     g_launches++;
     return cudaGetLastError();
 }

@@ -301,6 +301,10 @@ cudaError_t launch_oz_split_f32(const float *src, int64_t rows, int64_t cols, in
                                 int32_t *exps, cudaStream_t st);
 cudaError_t launch_gemm_oz(const SliceBuf &P, const int32_t *ep, const SliceBuf &Q, const int32_t *eq,
                            OzParams prm, cudaStream_t st, int batch = 1);
+// the same for K <= 64 (P.ld <= 64), a CTA per 128-row tile and strip of `strip` column tiles
+// (no lower_only / p_lower / diagonal terms / window mask / K ranges)
+cudaError_t launch_gemm_oz_strip(const SliceBuf &P, const int32_t *ep, const SliceBuf &Q, const int32_t *eq,
+                                 OzParams prm, cudaStream_t st, int batch, int strip);
 
 inline int slices_for(int precision) { return precision == PFSM_BF16_SPLIT ? 3 : 2; }
 inline int slice_kind(int precision) { return precision == PFSM_BF16_SPLIT ? 0 : 1; }
