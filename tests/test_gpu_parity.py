@@ -306,6 +306,23 @@ def test_mixed_ragged_and_edge_sizes(pf, orc, n, nb, halo, K, prec):
 
 
 @pytest.mark.parametrize("prec", [2, 1], ids=["bf16", "tf32"])
+@pytest.mark.parametrize("n,nb,halo,K", [
+    (120, 1, -1, 3), (200, 3, 40, 3), (333, 4, 50, 2), (513, 1, -1, 3), (700, 5, -1, 3), (450, 7, 90, 0),
+    (301, 2, 150, 1),
+])
+def test_two_stage_reduction_matches_oracle(pf, orc, n, nb, halo, K, prec):
+    """The two-stage window reduction (dense -> band of half-width 32 by digit products, float-float
+    bulge chasing, both back-transformations) forced on windows from 66 to 700 rows: ragged
+    windows and slices, one window covering the matrix, a window whose width is not a multiple of
+    32, K = 0. Same FP64 bars as every other form."""
+    p = wl.random_nearly_diagonal(n, seed=2000 + n + nb, sigma=1e-3, decay=24.0, nblocks=nb, halo=halo)
+    r = orc.pfsm(p.A, p.prev, nb, halo=halo, fs_iters=K)
+    g = _run(pf, p, fs_iters=K, precision=prec, reduction=2)
+    _check(r, g)
+    np.testing.assert_allclose(g["eps"], r.eps, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("prec", [2, 1], ids=["bf16", "tf32"])
 def test_mixed_explicit_slices_cluster_snap_and_zero_coupling(pf, orc, prec):
     """Explicit uneven slices, near-degenerate previous eigenvalues on slice boundaries (the plan
     moves them), and a diagonal A (start vectors are unit vectors, V = I) in the mixed forms."""
