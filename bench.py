@@ -49,7 +49,13 @@ DTYPES = {"fp64": "f64", "bf16": "bf16x3-split, f32 accumulate, f64 epilogue",
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, bytes per launch) of the roofline
 # kernel from an ncu capture of the current build, keyed by (kernel, workload); a kernel changed
 # since its capture has no entry (the line then reports null). Captures and commands: profiles/.
-TRAFFIC = {}
+TRAFFIC = {
+    # one 2200-row window captured whole (1.18 MB read + 0.22 MB written)
+    ("k_band_chase", "window2200"): 1.40e6,
+    # the same capture scaled by window rows to the N = 9072 solve's 36 windows of 2068 rows
+    # (the chase reads the band once and writes its reflectors: traffic grows with the rows)
+    ("k_band_chase", "vacancy"): 1.40e6 * 36 * 2068 / 2200,
+}
 
 
 def measured_peaks():
@@ -63,6 +69,12 @@ def measured_peaks():
 def workload(name: str = "vacancy", n=None, nblocks=None, halo=None):
     """The benchmarked workload; size overrides exist for profiling captures only."""
     import workloads as wl
+    if name == "window2200":
+        # profiling size: the two-stage reduction's kernels on one window of 2200 rows (one slice,
+        # no halo; vacancy-like spectrum and dense couplings)
+        p = wl.random_nearly_diagonal(2200, seed=11, sigma=1e-4, decay=None, lo=-0.5, hi=3.0, nblocks=1, halo=0)
+        return p, {"workload": "one 2200-row window (N=2200, 1 slice, halo 0, U[-0.5, 3] diagonal, dense couplings 1e-4; "
+                               "profiling size)", "N": p.n, "nblocks": 1, "halo": 0, "fs_iters": p.fs_iters}
     if name == "vacancy" and n is None:
         p = wl.vacancy_like()
         h = (p.n + 9) // 10
@@ -385,10 +397,11 @@ def run_extras(args, pf, torch, np, flush, precs, peaks, pv):
 
     # ---- context: torch.linalg.eigh (cuSOLVER, FP64) on the vacancy-like matrix ------------------
     Av = torch.from_numpy(pv.A).cuda()
-    ms, (w_e, _) = timed(lambda: torch.linalg.eigh(Av), 1)
+    torch.linalg.eigh(Av)                                     # warm-up (cuSOLVER workspace)
+    ms, (w_e, _) = timed(lambda: torch.linalg.eigh(Av), 2)
     out["eigh_context"] = {"what": "torch.linalg.eigh FP64 (cuSOLVER) full diagonalisation of the same N = 9072 "
                                    "matrix: the analogue of the paper's MAGMA column (context, not the target)",
-                           "ms": ms, "solves_per_s": 1000.0 / ms}
+                           "ms": ms, "solves_per_s": 1000.0 / ms, "timing": "best of 2 after a warm-up, L2 flushed"}
     del Av, w_e
     torch.cuda.empty_cache()
 
@@ -480,7 +493,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--precision", choices=("bf16", "tf32", "fp64"), default="bf16")
-    ap.add_argument("--workload", choices=("vacancy", "diamond"), default="vacancy")
+    ap.add_argument("--workload", choices=("vacancy", "diamond", "window2200"), default="vacancy")
+    ap.add_argument("--only-headline", action="store_true",
+                    help="time the headline precision form only (profiler captures)")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (ncu --profile-from-start off)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-oracle", action="store_true", help="skip the accuracy checks and the CPU baseline")
     ap.add_argument("--no-extras", action="store_true",
@@ -544,6 +561,8 @@ def main():
         sampler = ClockSampler(local) if clocks else None
         if sampler:
             sampler.__enter__()
+        if clocks and args.profile_range:
+            torch.cuda.cudart().cudaProfilerStart()
         for i in range(steps):
             flush.zero_()
             ev[i][0].record()
@@ -552,6 +571,8 @@ def main():
             prof = h.profile()          # synchronises; outside the events
             phases.append(prof)
             launches += prof["launches"]
+        if clocks and args.profile_range:
+            torch.cuda.cudart().cudaProfilerStop()
         barrier()
         if sampler:
             sampler.__exit__(None, None, None)
@@ -658,7 +679,7 @@ def main():
     # ---- the other forms of the same workload, fewer steps (the FP64 form takes seconds) ------------
     other_steps = {"bf16": (3, 1), "tf32": (3, 1), "fp64": (2, 1)}
     for prec in ("bf16", "tf32", "fp64"):
-        if prec == headline_prec:
+        if prec == headline_prec or args.only_headline:
             continue
         st_, wu = other_steps[prec]
         r = measure(p, prec, st_, wu, clocks=False)
@@ -669,7 +690,7 @@ def main():
         r["h"].close()
         del r
         torch.cuda.empty_cache()
-    fp64_value = forms["fp64"]["solves_per_s"]
+    fp64_value = forms["fp64"]["solves_per_s"] if "fp64" in forms else None
 
     # ---- roofline: the dominant kernel of the headline solve -----------------------------------
     local_peaks = measure_peaks_local(torch)
@@ -745,7 +766,7 @@ def main():
            "config": dict(cfg, precision=headline_prec, l2="flushed between steps (256 MiB write)",
                           parallelism=f"replicas x{world}"),
            "tflops": fl["total"] * value / world / 1e12,
-           "fp64_solves_per_s": fp64_value, "speedup_vs_fp64": value / fp64_value,
+           "fp64_solves_per_s": fp64_value, "speedup_vs_fp64": (value / fp64_value) if fp64_value else None,
            "forms": forms, "phases_ms": ph, "roofline": roofline, "roofline_other": other,
            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h},
