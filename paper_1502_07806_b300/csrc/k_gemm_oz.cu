@@ -94,6 +94,58 @@ __device__ __forceinline__ double oz_f2d_scaled(float f, int e)
                                             ((unsigned long long)(u & 0x7FFFFFu) << 29)));
 }
 
+// An exact FP32 integer |v| < 2^22 (a level sum of at most 64-term digit products) as an int32:
+// adding 1.5 2^23 leaves it, exactly, in the low significand bits.
+__device__ __forceinline__ int oz_lvl_i32(uint32_t raw)
+{
+    return __float_as_int(__uint_as_float(raw) + 12582912.0f) - 0x4B400000;
+}
+
+// T = sum_L v_L 128^(LV-1-L) over the raw level sums of column j: with K <= 64, |v_L| <=
+// (L + 1) 64^2 K = (L + 1) 2^18, so |T| < 2^61 and the sum is exact in 64-bit integers. Seven
+// levels go in int32 pairs (v_{L+1} + 128 v_L stays below 2^28) before the 64-bit adds.
+template <int N>
+__device__ __forceinline__ long long oz_levels_i64(const uint32_t (&v)[OZ_LEVELS][N], int j, int LV)
+{
+    if (LV == 7 && OZ_LEVELS == 7) {
+        const int i0 = oz_lvl_i32(v[0][j]), i1 = oz_lvl_i32(v[1][j]), i2 = oz_lvl_i32(v[2][j]);
+        const int i3 = oz_lvl_i32(v[3][j]), i4 = oz_lvl_i32(v[4][j]), i5 = oz_lvl_i32(v[5][j]);
+        const int i6 = oz_lvl_i32(v[6][j]);
+        const int p = i6 + i5 * 128, q = i4 + i3 * 128, r = i2 + i1 * 128;
+        return (long long)i0 * (1ll << 42) + (long long)r * (1ll << 28) + (long long)q * (1ll << 14) + (long long)p;
+    }
+    long long t = 0;
+#pragma unroll
+    for (int L = 0; L < OZ_LEVELS; L++)
+        if (L < LV) t = t * 128 + oz_lvl_i32(v[L][j]);
+    return t;
+}
+
+// t 2^e rounded to FP64 (to nearest, ties to even) by integer operations: the FP64 pipe, which
+// the C update needs, is 1/64 of the integer rate.
+__device__ __forceinline__ double oz_i64_to_f64_scaled(long long t, int e)
+{
+    if (t == 0) return 0.0;
+    const unsigned long long sgn = (unsigned long long)t & 0x8000000000000000ull;
+    unsigned long long m = sgn ? 0ull - (unsigned long long)t : (unsigned long long)t;
+    const int lz = __clzll((long long)m);
+    m <<= lz;                                                     // leading one at bit 63
+    const unsigned long long rr = m + (0x3FFull + ((m >> 11) & 1ull));
+    const int carry = rr < m ? 1 : 0;                             // rounded up to 2^64
+    const int ex = 1023 + 63 - lz + e + carry;
+    if (ex <= 0 || ex >= 2047) {                                  // subnormal or overflowing result:
+        double x = (double)t;                                     // exact powers of two, no call
+        for (int k = 0; k < 3; k++) {
+            const int ek = max(-1022, min(1023, e));
+            x *= __longlong_as_double((long long)(ek + 1023) << 52);
+            e -= ek;
+        }
+        return x;
+    }
+    const unsigned long long mant = carry ? 0ull : ((rr >> 11) & 0xFFFFFFFFFFFFFull);
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)ex << 52) | mant));
+}
+
 template <typename T>
 __device__ __forceinline__ void oz_split_row(const T *__restrict__ x, int64_t cols, int64_t fill_to, int64_t diag_col,
                                              double *dval, unsigned short *__restrict__ out, int64_t sstride,
@@ -427,16 +479,18 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
 // `strip` column tiles: Q digits through a two-stage ring, the level sums of tile t in TMEM buffer
 // t & 1 (levels at columns 32 L), so the drain and the C update of a tile overlap the MMAs of the
 // next. K <= 64 < one exact 512-term chunk, so every tile is one exact level sum. Warp roles as in
-// k_gemm_oz (0: TMA, 1: TMEM owner and MMA issuer, 2-5: drain and epilogue); every wait bounded.
+// k_gemm_oz (0: TMA, 1: TMEM owner and MMA issuer), eight drain warps (2-9); every wait bounded.
 namespace ozs {
 constexpr int MAXKB = 2;                                  // K <= 64
 constexpr int QST = 2;                                    // Q ring stages
 constexpr int P_BYTES = MAXKB * OZ_SLICES * oz::P_TILE;   // 112 KB
 constexpr int QSTAGE = MAXKB * OZ_SLICES * oz::Q_TILE;    // 28 KB
-constexpr int EB_BYTES = 4 * 32 * (oz::BN + 1) * 8;       // per-warp epilogue staging
+constexpr int EPI_WARPS = 8;                             // drain warps: 2 per TMEM lane quarter
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
+constexpr int EB_BYTES = EPI_WARPS * 32 * 17 * 8;        // per-warp 32 x 16 staging block
 }  // namespace ozs
 
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(ozs::THREADS, 1)
 k_gemm_oz_strip(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUtensorMap mapQ, OzParams prm,
                 int strip)
 {
@@ -485,7 +539,7 @@ k_gemm_oz_strip(const __grid_constant__ CUtensorMap mapP, const __grid_constant_
         }
         for (int b = 0; b < 2; b++) {
             mbar_init(accf(b), 1);
-            mbar_init(acce(b), 128);
+            mbar_init(acce(b), 32 * ozs::EPI_WARPS);
         }
         mbar_init(done_bar, 1);
         *abort_flag = 0;
@@ -560,13 +614,30 @@ k_gemm_oz_strip(const __grid_constant__ CUtensorMap mapP, const __grid_constant_
         }
         __syncwarp();
     } else {
-        const int gq = warp & 3;
+        // drain warps 2 .. 9: TMEM lane quarter gq = warp & 3 (the quarter a warp may read) and
+        // column half hc (16 of the tile's 32 columns), two warps per SM sub-partition so that one
+        // drains while the other waits on memory. Each entry's level sums are combined exactly in
+        // 64-bit integers and rounded once to FP64; the C update is the only FP64 operation.
+        const int gq = warp & 3, hc = (warp - 2) >> 2;
         const int r = row0 + 32 * gq + lane;
         const int er = (r < rows_lim) ? prm.ep[zr + r] : 0;
-        double(*eb)[BN + 1] = reinterpret_cast<double(*)[BN + 1]>(ebuf) + 32 * gq;
+        const int escale = -12 - BETA * (LV - 1);                 // scale of T's unit
+        double(*eb)[17] = reinterpret_cast<double(*)[17]>(ebuf) + 32 * (warp - 2);
         const int R0 = row0 + 32 * gq;
+        const int rsub = lane >> 4, cl = lane & 15;               // C update: rows 2 i + rsub, column cl
         for (int t = 0; t < nt; t++) {
             const int buf = t & 1;
+            const int c = cbase + (ct0 + t) * BN + 16 * hc + cl;
+            const bool cok = c < cols_lim;
+            const int ec = cok ? prm.eq[zq + c] : 0;
+            // this warp alone updates its 32 x 16 block of C: its loads go out before the wait for
+            // the tile's MMAs, so their latency overlaps it
+            double cv[16];
+#pragma unroll
+            for (int q = 0; q < 16; q++) {
+                const int gr = R0 + 2 * q + rsub;
+                cv[q] = (prm.sub && gr < rows_lim && cok) ? Cz[(int64_t)gr * prm.ldc + c] : 0.0;
+            }
             bool got = mbar_wait(accf(buf), (t >> 1) & 1);
             got = __all_sync(0xffffffffu, got) && !*abort_flag;
             if (!got) {
@@ -575,43 +646,33 @@ k_gemm_oz_strip(const __grid_constant__ CUtensorMap mapP, const __grid_constant_
                 break;
             }
             fence_after();
-            float hi[BN], lo[BN];
+            const uint32_t ta = tmem_acc + ((uint32_t)(32 * gq) << 16) + BUF_COLS * buf + 16u * hc;
 #pragma unroll
-            for (int j = 0; j < BN; j++) { hi[j] = 0.0f; lo[j] = 0.0f; }
-            for (int L = 0; L < LV; L++) {
-                const float scale = __int_as_float((127 - 12 - BETA * L) << 23);   // 2^-(12 + 7 L)
-                uint32_t v[32];
-                tmem_ld32(tmem_acc + ((uint32_t)(32 * gq) << 16) + BUF_COLS * buf + 32u * L, v);
+            for (int g = 0; g < 2; g++) {                         // two groups of 8 columns
+                uint32_t v[OZ_LEVELS][8];
 #pragma unroll
-                for (int j = 0; j < 32; j++) {
-                    const float x = __uint_as_float(v[j]) * scale;
-                    const float sum = hi[j] + x, bp = sum - hi[j];
-                    lo[j] += (hi[j] - (sum - bp)) + (x - bp);
-                    hi[j] = sum;
+                for (int L = 0; L < OZ_LEVELS; L++)
+                    if (L < LV) tmem_ld8_nowait(ta + 32u * L + 8u * g, v[L]);
+                tmem_wait_ld();
+#pragma unroll
+                for (int L = 0; L < OZ_LEVELS; L++)
+                    if (L < LV) tmem_regs_after_wait(v[L]);
+                if (g == 1) {                                     // every TMEM read of the tile done
+                    fence_before();
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce(buf)) : "memory");
+                }
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    const int es = er + __shfl_sync(0xffffffffu, ec, 8 * g + j) + escale;
+                    eb[lane][8 * g + j] = oz_i64_to_f64_scaled(oz_levels_i64(v, j, LV), es);
                 }
             }
-            fence_before();
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce(buf)) : "memory");
-            const int col0 = cbase + (ct0 + t) * BN;
-            const int c = col0 + lane;
-            const bool cok = c < cols_lim;
-            const int ec = cok ? prm.eq[zq + c] : 0;
-#pragma unroll
-            for (int j = 0; j < BN; j++) {
-                const int es = er + __shfl_sync(0xffffffffu, ec, j);
-                eb[lane][j] = oz_f2d_scaled(hi[j], es) + oz_f2d_scaled(lo[j], es);
-            }
             __syncwarp();
-            double cv[32];
 #pragma unroll
-            for (int rr = 0; rr < 32; rr++) {
-                const int gr = R0 + rr;
-                cv[rr] = (prm.sub && gr < rows_lim && cok) ? Cz[(int64_t)gr * prm.ldc + c] : 0.0;
-            }
-#pragma unroll
-            for (int rr = 0; rr < 32; rr++) {
-                const int gr = R0 + rr;
-                if (gr < rows_lim && cok) Cz[(int64_t)gr * prm.ldc + c] = prm.sub ? cv[rr] - eb[rr][lane] : eb[rr][lane];
+            for (int q = 0; q < 16; q++) {
+                const int gr = R0 + 2 * q + rsub;
+                const double res = eb[2 * q + rsub][cl];
+                if (gr < rows_lim && cok) Cz[(int64_t)gr * prm.ldc + c] = prm.sub ? cv[q] - res : res;
             }
             __syncwarp();
         }
@@ -718,7 +779,7 @@ cudaError_t launch_gemm_oz_strip(const SliceBuf &P, const int32_t *ep, const Sli
     if (ext_r <= 0 || ext_c <= 0) return cudaSuccess;
     const int nct = (ext_c + oz::BN - 1) / oz::BN;
     dim3 grid((unsigned)((nct + strip - 1) / strip), (unsigned)((ext_r + oz::BM - 1) / oz::BM), (unsigned)batch);
-    k_gemm_oz_strip<<<grid, 192, oz_strip_smem_bytes(), st>>>(mp, mq, prm, strip);
+    k_gemm_oz_strip<<<grid, ozs::THREADS, oz_strip_smem_bytes(), st>>>(mp, mq, prm, strip);
     g_launches++;
     return cudaGetLastError();
 }
