@@ -56,19 +56,6 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// CTA-wide sum in a fixed order (the same result in every CTA of a cluster)
-__device__ __forceinline__ double cta_sum(double v, double *red)
-{
-    v = warp_sum(v);
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[w] = v;
-    __syncthreads();
-    double t = 0.0;
-    for (int i = 0; i < nw; i++) t += red[i];
-    return t;
-}
-
 }  // namespace
 
 // Stage-1 panels of a window of width M: panel p (columns p KB .. p KB + KB - 1) exists while its
@@ -103,10 +90,13 @@ k_band_copy(const double *__restrict__ A, int64_t N, const int32_t *__restrict__
 // ---- stage 1: panel QR --------------------------------------------------------------------------
 // Cluster of CL CTAs per window (grid nb * CL), 256 threads. The panel's n = M - r0 rows are split
 // into CL contiguous chunks held in shared memory (rows x (KB + 1) doubles). Per column t: (A)
-// partial sums of the column's tail and its head entry, pulled by every CTA after a cluster
-// barrier; (B) partial dot products of the unit reflector with the later columns, pulled after a
-// second barrier, then the rank-1 update of the owned rows. Every CTA forms the same scalars from
-// the same partial sums in the same order. Outputs: reflector rows refl[c + t] (zero outside
+// partial sums of the column's tail and its head entry, pulled by warp 0 of every CTA after a
+// cluster barrier, which forms the reflector's scalars once for its CTA; (B) partial dot products
+// of the unit reflector with the later columns, pulled after a second barrier, then the rank-1
+// update of the owned rows. Every CTA forms the same scalars from the same partial sums in the same
+// order. The dot products and the update touch only the 31 - t later columns: a warp instruction
+// covers 32 / g rows of g >= 31 - t columns (g = 32, 16, 8 or 4), so the FP64 pipe, the kernel's
+// bound, does not issue for idle columns. Outputs: reflector rows refl[c + t] (zero outside
 // rows r0 + t .. M-1), tau = 2 (0 for a column whose tail is already zero), T (KB x KB, upper),
 // R into the band of G (rows r0 .. r0 + KB - 1, columns c .. c + KB - 1), and extp[b] = M when the
 // window has this panel, else 0 (the later kernels of this panel read their extent from it).
@@ -121,6 +111,7 @@ k_band_panel(const int32_t *__restrict__ plan, int nb, int Mmax, int c, int rpc_
     const int M = plan[3 * nb + b];
     const int r0 = c + KB;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = kPanelThreads / 32;
     if (r0 > M - 2) {                                  // no panel here (uniform over the cluster)
         if (rank == 0 && tid == 0) extp[b] = 0;
         return;
@@ -131,18 +122,20 @@ k_band_panel(const int32_t *__restrict__ plan, int nb, int Mmax, int c, int rpc_
     constexpr int LD = KB + 1;
     extern __shared__ double sm[];
     double *P = sm;                                    // rpc_cap x LD: owned rows of the panel
-    double *red = P + (size_t)rpc_cap * LD;            // 32: cta_sum scratch
+    double *red = P + (size_t)rpc_cap * LD;            // 32: per-warp partial sums
     double *hx = red + 32;                             // [0] partial tail^2, [1] head entry (owner)
     double *wp = hx + 2;                               // KB partial dots of the current column step
-    double *wr = wp + KB;                              // 8 x KB per-warp partial dots
-    double *alph = wr + 8 * KB;                        // KB: R's diagonal (alpha_t)
+    double *wr = wp + KB;                              // NW x KB per-warp partial dots
+    double *alph = wr + NW * KB;                       // KB: R's diagonal (alpha_t)
     double *bet = alph + KB;                           // KB: beta_t (2 or 0)
-    double *Gp = bet + KB;                             // KB x KB partial V^T V (own rows)
+    double *Gp = bet + KB;                             // KB x KB partial V^T V (own rows, p < q)
     double *Tm = Gp + KB * KB;                         // KB x KB: T (rank 0)
     double *Gs = Tm + KB * KB;                         // KB x KB: V^T V (rank 0)
+    double *sc = Gs + KB * KB;                         // 4: the column's 1/||v||, v_0, beta
+    double *wsum = sc + 4;                             // KB: -2 w_j of the column step
     double *Gb = G + (size_t)b * Mmax * Mmax;
 
-    for (int il = warp; il < nown; il += 8) P[il * LD + lane] = Gb[(size_t)(r0 + i0 + il) * Mmax + c + lane];
+    for (int il = warp; il < nown; il += NW) P[il * LD + lane] = Gb[(size_t)(r0 + i0 + il) * Mmax + c + lane];
     const int tmax = min(KB, n);
     for (int t = tid; t < KB; t += blockDim.x) { alph[t] = 0.0; bet[t] = 0.0; }
     __syncthreads();
@@ -153,91 +146,132 @@ k_band_panel(const int32_t *__restrict__ plan, int nb, int Mmax, int c, int rpc_
         double part = 0.0;
         for (int il = tid; il < nown; il += blockDim.x)
             if (i0 + il > t) part = fma(P[il * LD + t], P[il * LD + t], part);
-        part = cta_sum(part, red);
+        part = warp_sum(part);
+        if (lane == 0) red[warp] = part;
         const int owner = t / rpc;
+        __syncthreads();
         if (tid == 0) {
-            hx[0] = part;
+            double s2 = 0.0;
+            for (int q = 0; q < NW; q++) s2 += red[q];
+            hx[0] = s2;
             hx[1] = (owner == rank) ? P[(t - i0) * LD + t] : 0.0;
         }
         cluster.sync();
-        double tail2 = 0.0;
-        for (int r = 0; r < CL; r++) tail2 += cluster.map_shared_rank(hx, r)[0];
-        const double x0 = cluster.map_shared_rank(hx, owner)[1];
-        double inv = 0.0, v0 = 0.0, alpha = x0, beta = 0.0;
-        if (tail2 != 0.0) {
-            const double nn = fma(x0, x0, tail2);
-            const double xn = nn * scaled_rsqrt(nn);
-            alpha = (x0 >= 0.0) ? -xn : xn;
-            v0 = x0 - alpha;
-            inv = scaled_rsqrt(fma(v0, v0, tail2));
-            beta = 2.0;
+        if (warp == 0) {                               // the reflector's scalars, once per CTA
+            double tail2 = (lane < CL) ? cluster.map_shared_rank(hx, lane)[0] : 0.0;
+            tail2 = warp_sum(tail2);                   // the same order in every CTA
+            if (lane == 0) {
+                const double x0 = cluster.map_shared_rank(hx, owner)[1];
+                double inv = 0.0, v0 = 0.0, alpha = x0, beta = 0.0;
+                if (tail2 != 0.0) {
+                    const double nn = fma(x0, x0, tail2);
+                    const double xn = nn * scaled_rsqrt(nn);
+                    alpha = (x0 >= 0.0) ? -xn : xn;
+                    v0 = x0 - alpha;
+                    inv = scaled_rsqrt(fma(v0, v0, tail2));
+                    beta = 2.0;
+                }
+                sc[0] = inv;
+                sc[1] = v0;
+                sc[2] = beta;
+                alph[t] = alpha;
+                bet[t] = beta;
+            }
         }
+        __syncthreads();
+        const double inv = sc[0], v0 = sc[1], beta = sc[2];
         // the unit reflector into column t of the owned rows >= t (all zero when beta = 0)
         for (int il = tid; il < nown; il += blockDim.x) {
             const int i = i0 + il;
             if (i == t) P[il * LD + t] = v0 * inv;
             else if (i > t) P[il * LD + t] *= inv;
         }
-        if (tid == 0) { alph[t] = alpha; bet[t] = beta; }
         __syncthreads();
-        // (B) partial w_j = v . column j over the owned rows >= t, j > t (lane j, rows by warp)
+        // (B) partial w_j = v . column j over the owned rows >= t, for the nc = KB - 1 - t later
+        // columns: lane -> column t + 1 + (lane mod g), row offset lane / g within the warp's rows
+        const int nc = KB - 1 - t;
+        const int lg = nc > 16 ? 5 : nc > 8 ? 4 : nc > 4 ? 3 : 2;
+        const int g = 1 << lg, rp = 32 >> lg;
+        const int j = t + 1 + (lane & (g - 1)), ro = lane >> lg;
+        const bool jok = j < KB;
         if (beta != 0.0) {
             double acc = 0.0;
-            if (lane > t)
-                for (int il = warp; il < nown; il += 8)
-                    if (i0 + il >= t) acc = fma(P[il * LD + t], P[il * LD + lane], acc);
-            wr[warp * KB + lane] = acc;
+            if (jok)
+                for (int il = warp * rp + ro; il < nown; il += NW * rp)
+                    if (i0 + il >= t) acc = fma(P[il * LD + t], P[il * LD + j], acc);
+            for (int o = g; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (ro == 0 && jok) wr[warp * KB + j] = acc;
             __syncthreads();
             if (warp == 0) {
-                double s = 0.0;
-                for (int q = 0; q < 8; q++) s += wr[q * KB + lane];
-                wp[lane] = s;
+                double s2 = 0.0;
+                if (lane > t)
+                    for (int q = 0; q < NW; q++) s2 += wr[q * KB + lane];
+                wp[lane] = s2;
             }
         }
         cluster.sync();
         if (beta != 0.0) {
-            double wj = 0.0;
-            if (lane > t)
-                for (int r = 0; r < CL; r++) wj += cluster.map_shared_rank(wp, r)[lane];
-            if (lane > t)
-                for (int il = warp; il < nown; il += 8)
-                    if (i0 + il >= t) P[il * LD + lane] = fma(-2.0 * wj, P[il * LD + t], P[il * LD + lane]);
+            if (warp == 0) {
+                double wj = 0.0;
+                if (lane > t)
+                    for (int r = 0; r < CL; r++) wj += cluster.map_shared_rank(wp, r)[lane];
+                wsum[lane] = -2.0 * wj;
+            }
+            __syncthreads();
+            if (jok) {
+                const double m2w = wsum[j];
+                for (int il = warp * rp + ro; il < nown; il += NW * rp)
+                    if (i0 + il >= t) P[il * LD + j] = fma(m2w, P[il * LD + t], P[il * LD + j]);
+            }
         }
         __syncthreads();
     }
     // reflector columns: V[i][t] = P[i][t] for i >= t (the entries above are R's)
     auto vij = [&](int il, int t) -> double { return (t < tmax && i0 + il >= t) ? P[il * LD + t] : 0.0; };
-    // partial V^T V over the owned rows: thread (warp, lane) -> entries (p = warp + 8 q, lane)
+    // partial V^T V over the owned rows, strictly upper entries only (T needs no others): the
+    // 496 pairs p < q, two per thread
     {
-        double g[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int il = 0; il < nown; il++) {
-            const double vq = vij(il, lane);
+        constexpr int NPAIR = KB * (KB - 1) / 2;
+        int pp[2], qq[2];
 #pragma unroll
-            for (int q = 0; q < 4; q++) g[q] = fma(vij(il, warp + 8 * q), vq, g[q]);
+        for (int k = 0; k < 2; k++) {
+            int e = tid + k * kPanelThreads, pr = 0;
+            if (e >= NPAIR) e = 0;
+            while (e >= KB - 1 - pr) { e -= KB - 1 - pr; pr++; }
+            pp[k] = pr;
+            qq[k] = pr + 1 + e;
         }
-#pragma unroll
-        for (int q = 0; q < 4; q++) Gp[(warp + 8 * q) * KB + lane] = g[q];
+        const bool ok1 = tid + kPanelThreads < NPAIR;
+        double g0 = 0.0, g1 = 0.0;
+        for (int il = 0; il < nown; il++) {
+            g0 = fma(vij(il, pp[0]), vij(il, qq[0]), g0);
+            if (ok1) g1 = fma(vij(il, pp[1]), vij(il, qq[1]), g1);
+        }
+        if (tid < NPAIR) Gp[pp[0] * KB + qq[0]] = g0;
+        if (ok1) Gp[pp[1] * KB + qq[1]] = g1;
     }
     // outputs that need only this CTA's rows: reflector rows (zero above row t), R's rows
     double *bref = refl + (size_t)b * Mmax * Mmax;
     for (int t = 0; t < KB; t++)
         for (int il = tid; il < nown; il += blockDim.x)
             bref[(size_t)(c + t) * Mmax + r0 + i0 + il] = vij(il, t);
-    for (int il = warp; il < nown; il += 8) {
+    for (int il = warp; il < nown; il += NW) {
         const int i = i0 + il;                         // R row i < KB: entries j >= i of row r0 + i
         if (i < KB && lane >= i) Gb[(size_t)(r0 + i) * Mmax + c + lane] = (lane == i) ? alph[i] : P[il * LD + lane];
     }
     cluster.sync();
     if (rank == 0) {
         for (int e = tid; e < KB * KB; e += blockDim.x) {
-            double s = 0.0;
-            for (int r = 0; r < CL; r++) s += cluster.map_shared_rank(Gp, r)[e];
-            Gs[e] = s;
+            const int pr = e / KB, q = e % KB;
+            double s2 = 0.0;
+            if (pr < q)
+                for (int r = 0; r < CL; r++) s2 += cluster.map_shared_rank(Gp, r)[e];
+            Gs[e] = s2;
         }
         // reflector rows' entries between the row index and the reflector's first row are zero
-        for (int t = warp; t < KB; t += 8) {
+        for (int t = warp; t < KB; t += NW) {
             double *rr = bref + (size_t)(c + t) * Mmax;
-            for (int j = c + t + 1 + lane; j < r0; j += 32) rr[j] = 0.0;
+            for (int jj = c + t + 1 + lane; jj < r0; jj += 32) rr[jj] = 0.0;
             if (lane == 0) tau[(size_t)b * Mmax + c + t] = bet[t];
         }
         if (tid == 0) extp[b] = M;
@@ -247,11 +281,11 @@ k_band_panel(const int32_t *__restrict__ plan, int nb, int Mmax, int c, int rpc_
             for (int q = 0; q < KB; q++) Tm[q * KB + lane] = 0.0;
             __syncwarp();
             for (int t = 0; t < KB; t++) {
-                double s = 0.0;
+                double s2 = 0.0;
                 if (lane < t)
-                    for (int p = lane; p < t; p++) s = fma(Tm[lane * KB + p], Gs[p * KB + t], s);
+                    for (int pq = lane; pq < t; pq++) s2 = fma(Tm[lane * KB + pq], Gs[pq * KB + t], s2);
                 __syncwarp();
-                if (lane < t) Tm[lane * KB + t] = -bet[t] * s;
+                if (lane < t) Tm[lane * KB + t] = -bet[t] * s2;
                 if (lane == t) Tm[t * KB + t] = bet[t];
                 __syncwarp();
             }
@@ -732,7 +766,7 @@ size_t chase_smem() { return (size_t)kChaseWarps * (KB * (KB + 1) + 2 * KB) * si
 size_t band_panel_smem(int Mmax)
 {
     const int rpc = (Mmax - KB + kPanelCL - 1) / kPanelCL;
-    return ((size_t)rpc * (KB + 1) + 32 + 2 + KB + 8 * KB + 2 * KB + 3 * KB * KB) * sizeof(double);
+    return ((size_t)rpc * (KB + 1) + 32 + 2 + KB + 8 * KB + 2 * KB + 3 * KB * KB + 4 + KB) * sizeof(double);
 }
 
 bool band_reduction_fits(int Mmax, size_t smem_cap)
