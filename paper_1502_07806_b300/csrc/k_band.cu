@@ -518,12 +518,24 @@ __device__ __forceinline__ void chase_task(double *__restrict__ B, int M, int s,
     const double w = fma(-0.5 * beta * vp, v, p);
     wsh[lane] = w;
     __syncwarp();
+    // the 528 lower-triangle entries, 17 per lane: lanes l and l + 16 share rows p = l mod 16 and
+    // 31 - p (p + 1 and 32 - p entries), so no FP64 instruction issues for an empty row slot
+    {
+        const int pr = lane & 15, k0 = 17 * (lane >> 4);
+#pragma unroll
+        for (int jj = 0; jj < 17; jj++) {
+            const int k = k0 + jj;
+            if (k <= KB) {
+                const int r = (k <= pr) ? pr : KB - 1 - pr;
+                const int c = (k <= pr) ? k : k - pr - 1;
+                S[c][r] = fma(-vsh[r], wsh[c], fma(-wsh[r], vsh[c], S[c][r]));
+            }
+        }
+    }
+    __syncwarp();
 #pragma unroll
     for (int c = 0; c < KB; c++)
-        if (c <= lane) tmp[c] = fma(-v, wsh[c], fma(-w, vsh[c], S[c][lane]));
-#pragma unroll
-    for (int c = 0; c < KB; c++)
-        if (c <= lane && lane < L) at(a + lane, a + c) = tmp[c];
+        if (c <= lane && lane < L) at(a + lane, a + c) = S[c][lane];
     // below: rows e .. e + LB - 1 (lane = row, in registers), H from the right (the next bulge)
     const int e = a + L;
     const int LB = min(KB, M - e);
