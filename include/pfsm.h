@@ -324,6 +324,27 @@ int pfsm_set_timing(pfsm_handle_t h, int32_t enable);
 /* Synchronises the stream of the last call on h and fills *out (host pointer). */
 int pfsm_get_profile(pfsm_handle_t h, pfsm_profile_t *out);
 
+/* ---- test entry points: the hand-written FP64 helpers ------------------------------------------
+ * The serial FP64 paths (window eigensolves, bulge chasing, panel QR) avoid the IEEE FP64 divide
+ * and square-root sequences, and the digit products' epilogues avoid FP64 conversions: reciprocals
+ * and inverse square roots are FP32 seeds refined by two Newton steps, and an exact 64-bit integer
+ * sum is rounded to FP64 by integer operations. These calls evaluate those helpers elementwise on
+ * caller-given device arrays so that tests can compare them with CUDA's correctly rounded 1/x,
+ * 1/sqrt(x) and integer conversion. They have no counterpart in the paper and play no part in a
+ * solve. All pointers are device pointers; launches go to `stream`; nothing is synchronised.
+ *
+ * pfsm_selftest_fp64_helpers: for i < n, rcp_scaled[i] = 1/x[i] and rsqrt_scaled[i] = 1/sqrt(x[i])
+ * by the exponent-splitting Newton helpers (0 where x[i] <= 0, outside their domain), rcp_fast[i]
+ * = 1/x[i] by the bit-pattern Newton helper (either sign; |x| outside [2^-125, 2^126) takes
+ * CUDA's division).
+ * pfsm_selftest_i64_to_f64: out[i] = t[i] * 2^e[i] rounded to nearest, ties to even (the digit
+ * products' exact level-sum conversion).
+ * Both return PFSM_ERR_INVALID_ARG for n < 0 or a null pointer with n > 0, PFSM_ERR_CUDA if the
+ * launch fails. */
+int pfsm_selftest_fp64_helpers(const double *x, int64_t n, double *rcp_scaled, double *rsqrt_scaled,
+                               double *rcp_fast, void *stream);
+int pfsm_selftest_i64_to_f64(const int64_t *t, const int32_t *e, int64_t n, double *out, void *stream);
+
 /* Thread-local text of the last error raised on this thread ("" if none). */
 const char *pfsm_last_error(void);
 

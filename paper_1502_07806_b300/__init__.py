@@ -25,7 +25,7 @@ EXPORTED = ("pfsm_default_params", "pfsm_init", "pfsm_solve", "pfsm_backward", "
             "pfsm_get_diagnostic", "pfsm_set_timing", "pfsm_get_profile", "pfsm_last_error",
             "pfsm_destroy", "pfsm_fs_iterate_noalloc", "pfsm_split_gemm", "pfsm_split_gemm_ex", "pfsm_batch_init",
             "pfsm_solve_batched", "pfsm_batch_get_status", "pfsm_batch_destroy", "pfsm_gen_to_std",
-            "pfsm_gen_to_std_sym", "pfsm_scf_step")
+            "pfsm_gen_to_std_sym", "pfsm_scf_step", "pfsm_selftest_fp64_helpers", "pfsm_selftest_i64_to_f64")
 PHASES = ("plan", "submatrix", "fs_iterations", "gram_schmidt", "rayleigh", "backward")
 SUB_PHASES = ("tridiag", "bisect", "inverse_iter", "backtransform", "overlap", "cholesky")
 # two-stage reduction (mixed forms, wide windows): inside "tridiag" and "backtransform"
@@ -89,6 +89,8 @@ def load_library():
     lib.pfsm_set_timing.argtypes = [P, i32]
     lib.pfsm_get_profile.argtypes = [P, ctypes.POINTER(Profile)]
     lib.pfsm_last_error.argtypes = []
+    lib.pfsm_selftest_fp64_helpers.argtypes = [P, i64, P, P, P, P]
+    lib.pfsm_selftest_i64_to_f64.argtypes = [P, P, i64, P, P]
     lib.pfsm_last_error.restype = ctypes.c_char_p
     lib.pfsm_destroy.argtypes = [P]
     _lib = lib

@@ -30,6 +30,7 @@
 // scales; finally one FP64 conversion per entry and row-contiguous stores through shared memory.
 // The epilogue can add an exact FP64 diagonal term C[r, c] += V[r, c] d[c] (for products with
 // A = diag(d) + E whose digits cover E only). All mbarrier waits are bounded.
+#include "fp64_util.cuh"
 #include "tc_common.cuh"
 
 namespace pfsm {
@@ -119,31 +120,6 @@ __device__ __forceinline__ long long oz_levels_i64(const uint32_t (&v)[OZ_LEVELS
     for (int L = 0; L < OZ_LEVELS; L++)
         if (L < LV) t = t * 128 + oz_lvl_i32(v[L][j]);
     return t;
-}
-
-// t 2^e rounded to FP64 (to nearest, ties to even) by integer operations: the FP64 pipe, which
-// the C update needs, is 1/64 of the integer rate.
-__device__ __forceinline__ double oz_i64_to_f64_scaled(long long t, int e)
-{
-    if (t == 0) return 0.0;
-    const unsigned long long sgn = (unsigned long long)t & 0x8000000000000000ull;
-    unsigned long long m = sgn ? 0ull - (unsigned long long)t : (unsigned long long)t;
-    const int lz = __clzll((long long)m);
-    m <<= lz;                                                     // leading one at bit 63
-    const unsigned long long rr = m + (0x3FFull + ((m >> 11) & 1ull));
-    const int carry = rr < m ? 1 : 0;                             // rounded up to 2^64
-    const int ex = 1023 + 63 - lz + e + carry;
-    if (ex <= 0 || ex >= 2047) {                                  // subnormal or overflowing result:
-        double x = (double)t;                                     // exact powers of two, no call
-        for (int k = 0; k < 3; k++) {
-            const int ek = max(-1022, min(1023, e));
-            x *= __longlong_as_double((long long)(ek + 1023) << 52);
-            e -= ek;
-        }
-        return x;
-    }
-    const unsigned long long mant = carry ? 0ull : ((rr >> 11) & 0xFFFFFFFFFFFFFull);
-    return __longlong_as_double((long long)(sgn | ((unsigned long long)ex << 52) | mant));
 }
 
 template <typename T>

@@ -1032,30 +1032,6 @@ k_bisect(const int32_t *__restrict__ plan, int32_t nb, int32_t Mmax, int32_t mma
     if (valid) sel_val[(size_t)b * mmax + t] = x * s_isc;
 }
 
-// Reciprocal without an IEEE FP64 division (~640 cycles dependent on B300) and without F2F
-// conversions (they run on the FP64 pipe): the FP32 approximate reciprocal of p's leading 24 bits,
-// both conversions done by integer operations on the bit patterns, then two Newton steps
-// y <- y (2 - p y) (relative error 2^-22 -> 2^-44 -> rounding), about 1 ulp. |p| outside
-// [2^-125, 2^126) takes the FP64 division.
-__device__ __forceinline__ double fast_rcp(double p)
-{
-    const int hi = __double2hiint(p);
-    const unsigned lo = (unsigned)__double2loint(p);
-    const int ev = (hi >> 20) & 0x7FF;
-    if ((unsigned)(ev - 898) > 250u) return 1.0 / p;
-    const float pf = __uint_as_float(((unsigned)hi & 0x80000000u) | ((unsigned)(ev - 896) << 23) |
-                                     ((unsigned)(hi & 0xFFFFF) << 3) | (lo >> 29));
-    float rf;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(pf));
-    const unsigned rb = __float_as_uint(rf);
-    double y = __hiloint2double((int)((rb & 0x80000000u) | ((((rb >> 23) & 0xFFu) + 896u) << 20) |
-                                      ((rb & 0x7FFFFFu) >> 3)),
-                                (int)(rb << 29));
-    y = y * fma(-p, y, 2.0);
-    y = y * fma(-p, y, 2.0);
-    return y;
-}
-
 __device__ __forceinline__ double hash_unit(uint32_t a, uint32_t b, uint32_t c)
 {
     uint64_t z = ((uint64_t)a << 42) ^ ((uint64_t)b << 21) ^ (uint64_t)c;
