@@ -636,11 +636,32 @@ __device__ __forceinline__ void ff_fma_acc(float &sh, float &sl, float ah, float
     sh = t;
 }
 
+// The chase's reflectors (v, beta) as float-float w = sqrt(beta) v, written in place over the FP64
+// reflector rows (a float2 has the size of a double), so that H = I - w w^T and the kernels below
+// convert nothing per use. Grid (ceil(Mmax NT / 8), nb), 256 threads: one warp per (sweep, task).
+__global__ void __launch_bounds__(256)
+k_band_refl_ff(const int32_t *__restrict__ plan, int nb, int Mmax, int NT, double *__restrict__ refl2,
+               const double *__restrict__ tau2)
+{
+    const int b = blockIdx.y;
+    const int M = plan[3 * nb + b];
+    const int lane = threadIdx.x & 31;
+    const int q = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int s = q / NT, i = q % NT;
+    if (s >= M - 2 || i >= (M - 2 - s + KB - 1) / KB) return;
+    const size_t slot = ((size_t)b * Mmax + s) * NT + i;
+    const double w = refl2[slot * KB + lane] * sqrt(tau2[slot]);
+    const float h = (float)w;
+    __syncwarp();
+    reinterpret_cast<float2 *>(refl2)[slot * KB + lane] = make_float2(h, (float)(w - (double)h));
+}
+
+
 // Yt[b] holds the window's eigenvectors transposed as float-float (row j, column t; ld = mmax).
 // Grid (ceil(mmax / 32), nb), 256 threads: lane = vector t0 + lane, the reflectors of a sweep
 // (disjoint rows) spread over the 8 warps, sweeps in reverse order with a CTA barrier between them.
 __global__ void __launch_bounds__(32 * kBtWarps)
-k_band_bt2(const int32_t *__restrict__ plan, int nb, int Mmax, int mmax, int NT, const double *__restrict__ refl2,
+k_band_bt2(const int32_t *__restrict__ plan, int nb, int Mmax, int mmax, int NT, const float2 *__restrict__ rf,
            const double *__restrict__ tau2, float2 *__restrict__ Yt)
 {
     const int b = blockIdx.y;
@@ -656,8 +677,8 @@ k_band_bt2(const int32_t *__restrict__ plan, int nb, int Mmax, int mmax, int NT,
             const size_t slot = ((size_t)b * Mmax + s) * NT + i;
             const double beta = tau2[slot];
             if (beta == 0.0) continue;
-            const double vd = refl2[slot * KB + lane];     // zero past the reflector's length
-            const ff v = ff_from(vd), wv = ff_from(beta * vd);
+            const float2 wl = rf[slot * KB + lane];        // zero past the reflector's length
+            const ff v = {wl.x, wl.y}, wv = v;
             const int a = s + 1 + i * KB;
             const int L = min(KB, M - a);
             float2 yv[KB];
@@ -910,8 +931,13 @@ cudaError_t launch_band_backtransform(pfsm_handle_s *h, cudaStream_t st)
     const dim3 gt((unsigned)((Mmax + 31) / 32), (unsigned)((mmax + 31) / 32), (unsigned)nb);
     k_band_transpose<<<gt, 256, 0, st>>>(plan, nb, Mmax, mmax, false, w.sel_vec, Yt);
     g_launches++;
-    k_band_bt2<<<dim3((unsigned)((mmax + 31) / 32), (unsigned)nb), 32 * kBtWarps, 0, st>>>(
-        plan, nb, Mmax, mmax, band_tasks_per_sweep(Mmax), w.bR2, w.bT2, Yt);
+    const int NT = band_tasks_per_sweep(Mmax);
+    k_band_refl_ff<<<dim3((unsigned)(((size_t)Mmax * NT + 7) / 8), (unsigned)nb), 256, 0, st>>>(plan, nb, Mmax, NT,
+                                                                                              w.bR2, w.bT2);
+    g_launches++;
+    const float2 *rf = reinterpret_cast<const float2 *>(w.bR2);
+    k_band_bt2<<<dim3((unsigned)((mmax + 31) / 32), (unsigned)nb), 32 * kBtWarps, 0, st>>>(plan, nb, Mmax, mmax, NT, rf,
+                                                                                           w.bT2, Yt);
     g_launches++;
     k_band_transpose<<<gt, 256, 0, st>>>(plan, nb, Mmax, mmax, true, w.sel_vec, Yt);
     g_launches++;

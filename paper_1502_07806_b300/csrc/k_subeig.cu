@@ -1051,10 +1051,10 @@ __device__ __forceinline__ unsigned long long abs_bits(double x)
 }
 
 // Largest |z_i| exponent field of a lane's vector (element i at z[i * zst]), by integer max.
-__device__ __forceinline__ int max_exponent(const double *z, int zst, int M)
+__device__ __forceinline__ int max_exponent(const double *z, size_t zst, int M)
 {
     unsigned long long m = 0ull;
-    for (int i = 0; i < M; i++) m = max(m, abs_bits(z[i * zst]));
+    for (int i = 0; i < M; i++) m = max(m, abs_bits(z[(size_t)i * zst]));
     return (int)(m >> 52);
 }
 
@@ -1067,12 +1067,17 @@ __device__ __forceinline__ int max_exponent(const double *z, int zst, int M)
 // into global work arrays interleaved across lanes (element i of lane t at i * stride + t:
 // coalesced), and only read by the solves; the vector z, which every sweep reads and rewrites,
 // lives in shared memory (element i of lane t at i * L + t), so no load of z waits behind an L2
-// round trip of the store before it.
+// round trip of the store before it. Windows too wide for 32 lanes' vectors in shared memory (ZG)
+// keep z in a fifth global work array, interleaved like the factors, and every sweep over it loads
+// a block of PB entries before it stores any, so a lane waits one L2 round trip per block instead
+// of one per entry; the CTA then holds 32 lanes and the grid fits the GPU in one wave (with z in
+// shared memory such windows ran 8 lanes per CTA, one CTA per SM, in eight waves).
 // A lane's time is its count of FP64 instructions (~64 cycles each on its sub-partition), so: the
 // first solve's forward elimination runs inside the factorisation, pivot tests compare bit
 // patterns, a step computes only the taken branch, every lane starts from one random vector of the
 // window (cluster members after the first from their own), and the vector is normalised once,
 // after the second solve, with power-of-two rescaling by integer exponent tests guarding the range.
+template <bool ZG>
 __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int32_t Mmax,
                                int32_t mmax, const double *__restrict__ td,
                                const double *__restrict__ te, const double *__restrict__ sel_val,
@@ -1083,9 +1088,12 @@ __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int
     const int mb = plan[nb + b], M = plan[3 * nb + b];
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     extern __shared__ double zsm[];
-    const int zst = blockDim.x;
-    double *z = zsm + threadIdx.x;                          // element i at z[i * zst]
-    double *d = zsm + (size_t)zst * Mmax;                   // the window's T, shared by the lanes
+    const size_t stride = (size_t)nb * mmax;
+    const size_t me = (size_t)b * mmax + t;
+    // element i of the lane's vector at z[i * zst]: shared memory, or the fifth work array
+    const size_t zst = ZG ? stride : (size_t)blockDim.x;
+    double *z = ZG ? work + 4 * stride * Mmax + me : zsm + threadIdx.x;
+    double *d = zsm + (ZG ? 0 : (size_t)blockDim.x * Mmax); // the window's T, shared by the lanes
     double *e = d + Mmax;
     double *rv = e + Mmax;                                  // the window's start vector
     __shared__ double tn_part[32];
@@ -1108,8 +1116,6 @@ __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int
     const double *lam = sel_val + (size_t)b * mmax;
     const double gaptol = 1e-9 * fmax(tnorm, DBL_MIN);
     if (t > 0 && lam[t] - lam[t - 1] < gaptol) return;     // handled by the cluster's first lane
-    const size_t stride = (size_t)nb * mmax;
-    const size_t me = (size_t)b * mmax + t;
     double *__restrict__ u0 = work + me;                    // reciprocal pivots
     double *__restrict__ u1 = work + stride * Mmax + me;
     double *__restrict__ u2 = work + 2 * stride * Mmax + me;
@@ -1130,24 +1136,31 @@ __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int
             for (int i = 0; i < M; i++) z[i * zst] *= f;
         }
     };
+    // dst[i] = z[i] * f for i < M (dst = z allowed), a block of PB loads before its stores
+    auto scale_to = [&](double *dst, size_t dst_st, double f) {
+        for (int i0 = 0; i0 < M; i0 += PB) {
+            double zb[PB];
+#pragma unroll
+            for (int q2 = 0; q2 < PB; q2++) zb[q2] = (i0 + q2 < M) ? z[(size_t)(i0 + q2) * zst] : 0.0;
+#pragma unroll
+            for (int q2 = 0; q2 < PB; q2++)
+                if (i0 + q2 < M) dst[(size_t)(i0 + q2) * dst_st] = zb[q2] * f;
+        }
+    };
     int last = t;
     while (last + 1 < mb && lam[last + 1] - lam[last] < gaptol) last++;
     for (int j = t; j <= last; j++) {
         const double x = lam[j];
-        // start vector: the window's, or a cluster member's own
-        if (j == t) {
-            for (int i = 0; i < M; i++) z[i * zst] = rv[i];
-        } else {
-            for (int i = 0; i < M; i++) z[i * zst] = hash_unit(b, j, i);
-        }
+        // start vector: the window's, or a cluster member's own (read by the elimination below)
+        auto start = [&](int i) { return (j == t) ? rv[i] : hash_unit(b, j, i); };
         // pivoted LU of T - x I with the first solve's forward elimination: rows (p, q) = entries
         // at columns (i, i+1) of the pivot candidate, zi its right-hand side. The row-swap flag is
         // kept in the lowest mantissa bit of the stored multiplier (a 1-ulp change).
-        double p = d[0] - x, q = (M > 1) ? e[0] : 0.0, zi = z[0];
+        double p = d[0] - x, q = (M > 1) ? e[0] : 0.0, zi = start(0);
 #pragma unroll 4
         for (int i = 0; i + 1 < M; i++) {
             const double ei = e[i], an = d[i + 1] - x, en = (i + 2 < M) ? e[i + 1] : 0.0;
-            const double zn = z[(i + 1) * zst];
+            const double zn = start(i + 1);
             const bool swp = abs_bits(p) < abs_bits(ei);
             const double rp = fast_rcp(clamp_pivot(swp ? ei : p));
             const double l = (swp ? p : ei) * rp;
@@ -1172,16 +1185,20 @@ __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int
                 // block of PB rows are loaded together (one L2 round trip per block)
                 double zf = z[0];
                 for (int i0 = 0; i0 + 1 < M; i0 += PB) {
-                    double lr[PB];
+                    double lr[PB], zb[PB];
 #pragma unroll
-                    for (int q2 = 0; q2 < PB; q2++) lr[q2] = (i0 + q2 + 1 < M) ? lm[(size_t)(i0 + q2) * stride] : 0.0;
+                    for (int q2 = 0; q2 < PB; q2++) {
+                        const bool ok = i0 + q2 + 1 < M;
+                        lr[q2] = ok ? lm[(size_t)(i0 + q2) * stride] : 0.0;
+                        zb[q2] = ok ? z[(size_t)(i0 + q2 + 1) * zst] : 0.0;    // before this block's stores
+                    }
 #pragma unroll
                     for (int q2 = 0; q2 < PB; q2++) {
                         const int i = i0 + q2;
                         if (i + 1 < M) {
                             const double lraw = lr[q2];
                             const bool swp = (__double_as_longlong(lraw) & 1ll) != 0;
-                            const double zn = z[(i + 1) * zst];
+                            const double zn = zb[q2];
                             z[i * zst] = swp ? zn : zf;
                             zf = fma(-lraw, swp ? zn : zf, swp ? zf : zn);   // flag bit: <= 1 ulp of l
                         }
@@ -1192,7 +1209,7 @@ __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int
             // back substitution with the three upper diagonals, factors loaded a block at a time
             double z1 = 0.0, z2 = 0.0;
             for (int i0 = M - 1; i0 >= 0; i0 -= PB) {
-                double a0[PB], a1[PB], a2[PB];
+                double a0[PB], a1[PB], a2[PB], zb[PB];
 #pragma unroll
                 for (int q2 = 0; q2 < PB; q2++) {
                     const int i = i0 - q2;
@@ -1200,12 +1217,13 @@ __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int
                     a0[q2] = ok ? u0[(size_t)i * stride] : 0.0;
                     a1[q2] = ok ? u1[(size_t)i * stride] : 0.0;
                     a2[q2] = ok ? u2[(size_t)i * stride] : 0.0;
+                    zb[q2] = ok ? z[(size_t)i * zst] : 0.0;
                 }
 #pragma unroll
                 for (int q2 = 0; q2 < PB; q2++) {
                     const int i = i0 - q2;
                     if (i >= 0) {
-                        const double acc = fma(-a2[q2], z2, fma(-a1[q2], z1, z[i * zst]));
+                        const double acc = fma(-a2[q2], z2, fma(-a1[q2], z1, zb[q2]));
                         const double zi2 = acc * a0[q2];
                         z[i * zst] = zi2;
                         z2 = z1;
@@ -1236,13 +1254,16 @@ __global__ void k_inverse_iter(const int32_t *__restrict__ plan, int32_t nb, int
             const double nn = (n0 + n1) + (n2 + n3);
             if (!(nn > 0.0) || !(nn < INFINITY)) {
                 for (int i = 0; i < M; i++) z[i * zst] = hash_unit(b, j + 7919, i + it);
+                if (it == 1) scale_to(sel_vec + ((size_t)b * mmax + j) * Mmax, 1, 1.0);
                 continue;
             }
             const double inr = rsqrt(nn);
-            for (int i = 0; i < M; i++) z[i * zst] *= inr;
+            if (it == 1) {
+                scale_to(sel_vec + ((size_t)b * mmax + j) * Mmax, 1, inr);    // the unit vector out
+            } else {
+                scale_to(z, zst, inr);                                        // a member's next solve
+            }
         }
-        double *out = sel_vec + ((size_t)b * mmax + j) * Mmax;
-        for (int i = 0; i < M; i++) out[i] = z[i * zst];
     }
 }
 
@@ -1517,7 +1538,8 @@ cudaError_t configure_kernels(pfsm_handle_s *h)
     if ((e = set_max((const void *)k_tridiag_panel<24>)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_tridiag_panel<24>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
     if ((e = set_max((const void *)k_bisect)) != cudaSuccess) return e;
-    if ((e = set_max((const void *)k_inverse_iter)) != cudaSuccess) return e;
+    if ((e = set_max((const void *)k_inverse_iter<false>)) != cudaSuccess) return e;
+    if ((e = set_max((const void *)k_inverse_iter<true>)) != cudaSuccess) return e;
     if ((e = set_max((const void *)k_backtransform<1, 4>)) != cudaSuccess) return e;
     if ((e = set_max((const void *)k_backtransform<2, 4>)) != cudaSuccess) return e;
     return set_max((const void *)k_backtransform<2, 8>);
@@ -1635,12 +1657,17 @@ cudaError_t launch_subeig(pfsm_handle_s *h, const double *A, cudaStream_t st)
     if (h->timing && (e0 = cudaEventRecord(h->sub_ev[1], st)) != cudaSuccess) return e0;
     // 3. inverse iteration
     {
-        int lanes = tpb;
-        while (lanes > 1 && (size_t)(lanes + 3) * Mmax * sizeof(double) > kInvSmemCap) lanes >>= 1;
+        // the lanes' vectors in shared memory when 32 lanes' fit, else in the fifth work array
+        const bool zg = (size_t)(tpb + 3) * Mmax * sizeof(double) > kInvSmemCap;
+        const int lanes = tpb;
+        const size_t smem = (size_t)(zg ? 3 : lanes + 3) * Mmax * sizeof(double);
         dim3 grid((unsigned)((mmax + lanes - 1) / lanes), (unsigned)nb);
-        k_inverse_iter<<<grid, lanes, (size_t)(lanes + 3) * Mmax * sizeof(double), st>>>(w.plan, nb, Mmax, mmax, w.td,
-                                                                                       w.te, w.sel_val, w.sel_vec,
-                                                                                       w.iiwork);
+        if (zg)
+            k_inverse_iter<true><<<grid, lanes, smem, st>>>(w.plan, nb, Mmax, mmax, w.td, w.te, w.sel_val, w.sel_vec,
+                                                           w.iiwork);
+        else
+            k_inverse_iter<false><<<grid, lanes, smem, st>>>(w.plan, nb, Mmax, mmax, w.td, w.te, w.sel_val, w.sel_vec,
+                                                            w.iiwork);
         g_launches++;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
