@@ -464,7 +464,11 @@ def run_extras(args, pf, torch, np, flush, precs, peaks, pv):
 
     total_flops = sum(nominal_flops(q) for q in probs)
     bres, lam_out = {}, {}
-    for name, pr, reps in (("mixed", precs[prec], 3), ("fp64", pf.FP64, 1)):
+    forms_b = [("mixed", precs[prec], 3)]
+    if prec != "tf32":
+        forms_b.append(("tf32", pf.TF32_SPLIT, 3))
+    forms_b.append(("fp64", pf.FP64, 1))
+    for name, pr, reps in forms_b:
         b = pf.Batch([q.n for q in probs], [q.nblocks for q in probs], precision=pr)
         lams = [torch.empty(q.n, dtype=torch.float64, device="cuda") for q in probs]
         Vs = [torch.empty(q.n, q.n, dtype=torch.float64, device="cuda") for q in probs]
@@ -478,8 +482,9 @@ def run_extras(args, pf, torch, np, flush, precs, peaks, pv):
         del lams, Vs
         torch.cuda.empty_cache()
     bres["speedup_vs_fp64"] = bres["mixed"]["solves_per_s"] / bres["fp64"]["solves_per_s"]
-    bres["max_abs_dlambda_over_norm_mixed_vs_fp64"] = float(max(
-        np.max(np.abs(a - c)) / np.max(np.abs(c)) for a, c in zip(lam_out["mixed"], lam_out["fp64"])))
+    for name in [f for f, _, _ in forms_b if f != "fp64"]:
+        bres[f"max_abs_dlambda_over_norm_{name}_vs_fp64"] = float(max(
+            np.max(np.abs(a - c)) / np.max(np.abs(c)) for a, c in zip(lam_out[name], lam_out["fp64"])))
     out["batch"] = {"workload": "64 problems, N uniform in 200..3000 (seeded), slices clamp(N/10, 64, 256), K = 3, "
                                 "one captured CUDA graph per form", "total_N": int(sum(int(n) for n in sizes)),
                     "timing": "CUDA events around a graph replay, L2 flushed", **bres}

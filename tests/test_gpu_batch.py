@@ -2,7 +2,7 @@
 200..3000, slices clamp(N/10, 64, 256) wide) solved by one captured CUDA graph.
 
 Checks: every problem of the batch equals the same problem solved alone through pfsm_solve
-(bit-exact: same kernels, same inputs, deterministic arithmetic); a replay of the captured graph
+(bit-exact: same kernels, same inputs, deterministic arithmetic; BF16, TF32 and FP64 forms); a replay of the captured graph
 and a re-capture for new buffers reproduce it; the smallest problems match the FP64 oracle at the
 FP64 bar; all device status words are clear."""
 import numpy as np
@@ -36,9 +36,9 @@ def _dev(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
 
-@pytest.mark.parametrize("name,prec", [("bf16", 2), ("fp64", 0)])
+@pytest.mark.parametrize("name,prec", [("bf16", 2), ("tf32", 1), ("fp64", 0)])
 def test_batch_equals_individual_solves(pf, problems, name, prec):
-    probs = problems if name == "bf16" else problems[:12]
+    probs = problems if name != "fp64" else problems[:12]
     As = [_dev(p.A) for p in probs]
     prevs = [_dev(p.prev) for p in probs]
     b = pf.Batch([p.n for p in probs], [p.nblocks for p in probs], precision=prec)
@@ -59,10 +59,11 @@ def test_batch_equals_individual_solves(pf, problems, name, prec):
     b.close()
 
 
-def test_batch_small_problems_match_oracle(pf, orc, problems):
+@pytest.mark.parametrize("prec", [2, 1])
+def test_batch_small_problems_match_oracle(pf, orc, problems, prec):
     order = np.argsort([p.n for p in problems])[:4]
     probs = [problems[i] for i in order]
-    b = pf.Batch([p.n for p in probs], [p.nblocks for p in probs], precision=pf.BF16_SPLIT)
+    b = pf.Batch([p.n for p in probs], [p.nblocks for p in probs], precision=prec)
     lams, Vs = b.solve([_dev(p.A) for p in probs], [_dev(p.prev) for p in probs])
     assert b.status() == [0] * len(probs)
     for p, lam, V in zip(probs, lams, Vs):
