@@ -46,7 +46,7 @@ namespace {
 constexpr int KB = kBand;
 constexpr int kPanelThreads = 256;
 constexpr int kChunk = 64;                 // rows per CTA of the W / Z kernels
-constexpr int kBtWarps = 8;                // k_band_bt2: warps per CTA (32 vectors per CTA)
+constexpr int kBtWarps = 8;                // k_band_bt2: warps per CTA (16 vectors per CTA)
 constexpr int kStrip = 8;                  // column tiles per CTA of the small-K digit products
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -657,56 +657,76 @@ k_band_refl_ff(const int32_t *__restrict__ plan, int nb, int Mmax, int NT, doubl
 }
 
 
+// (s_h + s_l) += (b_h + b_l) by two-sum of the high parts (not renormalised)
+__device__ __forceinline__ void ff_add(float &sh, float &sl, float bh, float bl)
+{
+    const float t = __fadd_rn(sh, bh), bv = __fsub_rn(t, sh);
+    sl = __fadd_rn(__fadd_rn(sl, bl), __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bv)), __fsub_rn(bh, bv)));
+    sh = t;
+}
+
 // Yt[b] holds the window's eigenvectors transposed as float-float (row j, column t; ld = mmax).
-// Grid (ceil(mmax / 32), nb), 256 threads: lane = vector t0 + lane, the reflectors of a sweep
-// (disjoint rows) spread over the 8 warps, sweeps in reverse order with a CTA barrier between them.
-__global__ void __launch_bounds__(32 * kBtWarps)
+// Grid (ceil(mmax / 16), nb), 256 threads, two CTAs per SM: lanes l and l + 16 share vector
+// t0 + (l mod 16), each holding 16 of a reflector's 32 rows (half the registers of a lane per
+// vector, so twice the warps hide the latency of the float-float chains); the reflectors of a
+// sweep (disjoint rows) spread over the 8 warps, sweeps in reverse order with a CTA barrier
+// between them.
+__global__ void __launch_bounds__(32 * kBtWarps, 2)
 k_band_bt2(const int32_t *__restrict__ plan, int nb, int Mmax, int mmax, int NT, const float2 *__restrict__ rf,
            const double *__restrict__ tau2, float2 *__restrict__ Yt)
 {
+    constexpr int HR = KB / 2;                             // rows per lane
     const int b = blockIdx.y;
     const int mb = plan[nb + b], M = plan[3 * nb + b];
-    const int t0 = blockIdx.x * 32;
+    const int t0 = blockIdx.x * 16;
     if (t0 >= mb) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float2 *Y = Yt + (size_t)b * Mmax * mmax + t0 + lane;
-    const bool act = t0 + lane < mb;
+    const int vi = lane & 15, hh = lane >> 4;
+    float2 *Y = Yt + (size_t)b * Mmax * mmax + t0 + vi;
+    const bool act = t0 + vi < mb;
     for (int s = M - 3; s >= 0; s--) {
         const int ntask = (M - 2 - s + KB - 1) / KB;
         for (int i = warp; i < ntask; i += kBtWarps) {
             const size_t slot = ((size_t)b * Mmax + s) * NT + i;
-            const double beta = tau2[slot];
-            if (beta == 0.0) continue;
-            const float2 wl = rf[slot * KB + lane];        // zero past the reflector's length
-            const ff v = {wl.x, wl.y}, wv = v;
+            if (tau2[slot] == 0.0) continue;
+            const float2 wl = rf[slot * KB + lane];        // w = sqrt(beta) v, zero past the length
             const int a = s + 1 + i * KB;
             const int L = min(KB, M - a);
-            float2 yv[KB];
+            const int r0 = HR * hh;
+            float2 yv[HR];
 #pragma unroll
-            for (int r = 0; r < KB; r++) yv[r] = (act && r < L) ? Y[(size_t)(a + r) * mmax] : make_float2(0.f, 0.f);
-            // d = v . y in float-float, two accumulators
+            for (int k = 0; k < HR; k++)
+                yv[k] = (act && r0 + k < L) ? Y[(size_t)(a + r0 + k) * mmax] : make_float2(0.f, 0.f);
+            // d = w . y in float-float: this lane's 16 rows in two accumulators, then the two halves
             float dh0 = 0.f, dl0 = 0.f, dh1 = 0.f, dl1 = 0.f;
 #pragma unroll
-            for (int r = 0; r < KB; r += 2) {
-                ff_fma_acc(dh0, dl0, __shfl_sync(0xffffffffu, v.h, r), __shfl_sync(0xffffffffu, v.l, r), yv[r].x,
-                           yv[r].y);
-                ff_fma_acc(dh1, dl1, __shfl_sync(0xffffffffu, v.h, r + 1), __shfl_sync(0xffffffffu, v.l, r + 1),
-                           yv[r + 1].x, yv[r + 1].y);
+            for (int k = 0; k < HR; k += 2) {
+                ff_fma_acc(dh0, dl0, __shfl_sync(0xffffffffu, wl.x, r0 + k), __shfl_sync(0xffffffffu, wl.y, r0 + k),
+                           yv[k].x, yv[k].y);
+                ff_fma_acc(dh1, dl1, __shfl_sync(0xffffffffu, wl.x, r0 + k + 1),
+                           __shfl_sync(0xffffffffu, wl.y, r0 + k + 1), yv[k + 1].x, yv[k + 1].y);
             }
-            float dh = dh0, dl = dl0;
+            ff_add(dh0, dl0, dh1, dl1);
             {
-                const float t = __fadd_rn(dh, dh1), bv = __fsub_rn(t, dh);
-                dl = __fadd_rn(__fadd_rn(dl, dl1), __fadd_rn(__fsub_rn(dh, __fsub_rn(t, bv)), __fsub_rn(dh1, bv)));
-                dh = t;
+                // lower half's sum plus upper half's, the same operation order in both lanes
+                const float ph = __shfl_xor_sync(0xffffffffu, dh0, 16), pl = __shfl_xor_sync(0xffffffffu, dl0, 16);
+                if (hh) {
+                    float xh = ph, xl = pl;
+                    ff_add(xh, xl, dh0, dl0);
+                    dh0 = xh;
+                    dl0 = xl;
+                } else {
+                    ff_add(dh0, dl0, ph, pl);
+                }
             }
-            // y_r -= d (beta v_r), then renormalised
+            // y_r -= d w_r, then renormalised
 #pragma unroll
-            for (int r = 0; r < KB; r++) {
-                const float bh = __shfl_sync(0xffffffffu, wv.h, r), bl = __shfl_sync(0xffffffffu, wv.l, r);
-                float sh = yv[r].x, sl = yv[r].y;
-                ff_fma_acc(sh, sl, -dh, -dl, bh, bl);
+            for (int k = 0; k < HR; k++) {
+                const float bh = __shfl_sync(0xffffffffu, wl.x, r0 + k), bl = __shfl_sync(0xffffffffu, wl.y, r0 + k);
+                float sh = yv[k].x, sl = yv[k].y;
+                ff_fma_acc(sh, sl, -dh0, -dl0, bh, bl);
                 const float h = __fadd_rn(sh, sl);
-                if (act && r < L) Y[(size_t)(a + r) * mmax] = make_float2(h, __fsub_rn(sl, __fsub_rn(h, sh)));
+                if (act && r0 + k < L) Y[(size_t)(a + r0 + k) * mmax] = make_float2(h, __fsub_rn(sl, __fsub_rn(h, sh)));
             }
         }
         __syncthreads();
@@ -936,7 +956,7 @@ cudaError_t launch_band_backtransform(pfsm_handle_s *h, cudaStream_t st)
                                                                                               w.bR2, w.bT2);
     g_launches++;
     const float2 *rf = reinterpret_cast<const float2 *>(w.bR2);
-    k_band_bt2<<<dim3((unsigned)((mmax + 31) / 32), (unsigned)nb), 32 * kBtWarps, 0, st>>>(plan, nb, Mmax, mmax, NT, rf,
+    k_band_bt2<<<dim3((unsigned)((mmax + 15) / 16), (unsigned)nb), 32 * kBtWarps, 0, st>>>(plan, nb, Mmax, mmax, NT, rf,
                                                                                            w.bT2, Yt);
     g_launches++;
     k_band_transpose<<<gt, 256, 0, st>>>(plan, nb, Mmax, mmax, true, w.sel_vec, Yt);
