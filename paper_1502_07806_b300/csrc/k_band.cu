@@ -46,7 +46,8 @@ namespace {
 constexpr int KB = kBand;
 constexpr int kPanelThreads = 256;
 constexpr int kChunk = 64;                 // rows per CTA of the W / Z kernels
-constexpr int kBtWarps = 8;                // k_band_bt2: warps per CTA (16 vectors per CTA)
+constexpr int kBtWarps = 8;                // k_band_bt2: warps per CTA
+constexpr int kBtVpw = 16;                 // k_band_bt2: vectors per warp (2 lanes each; 4 measured slower)
 constexpr int kStrip = 8;                  // column tiles per CTA of the small-K digit products
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -666,22 +667,23 @@ __device__ __forceinline__ void ff_add(float &sh, float &sl, float bh, float bl)
 }
 
 // Yt[b] holds the window's eigenvectors transposed as float-float (row j, column t; ld = mmax).
-// Grid (ceil(mmax / 16), nb), 256 threads, two CTAs per SM: lanes l and l + 16 share vector
-// t0 + (l mod 16), each holding 16 of a reflector's 32 rows (half the registers of a lane per
-// vector, so twice the warps hide the latency of the float-float chains); the reflectors of a
-// sweep (disjoint rows) spread over the 8 warps, sweeps in reverse order with a CTA barrier
+// Grid (ceil(mmax / VPW), nb), 256 threads, 32 / VPW CTAs per SM: the LPV = 32 / VPW lanes
+// l, l + VPW, ... share vector t0 + (l mod VPW), each holding KB / LPV of a reflector's rows (fewer
+// registers per lane, so more warps hide the latency of the float-float chains); the reflectors of
+// a sweep (disjoint rows) spread over the 8 warps, sweeps in reverse order with a CTA barrier
 // between them.
-__global__ void __launch_bounds__(32 * kBtWarps, 2)
+template <int VPW>
+__global__ void __launch_bounds__(32 * kBtWarps, 32 / VPW)
 k_band_bt2(const int32_t *__restrict__ plan, int nb, int Mmax, int mmax, int NT, const float2 *__restrict__ rf,
            const double *__restrict__ tau2, float2 *__restrict__ Yt)
 {
-    constexpr int HR = KB / 2;                             // rows per lane
+    constexpr int LPV = 32 / VPW, HR = KB / LPV;           // lanes per vector, rows per lane
     const int b = blockIdx.y;
     const int mb = plan[nb + b], M = plan[3 * nb + b];
-    const int t0 = blockIdx.x * 16;
+    const int t0 = blockIdx.x * VPW;
     if (t0 >= mb) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int vi = lane & 15, hh = lane >> 4;
+    const int vi = lane % VPW, hh = lane / VPW;
     float2 *Y = Yt + (size_t)b * Mmax * mmax + t0 + vi;
     const bool act = t0 + vi < mb;
     for (int s = M - 3; s >= 0; s--) {
@@ -697,7 +699,8 @@ k_band_bt2(const int32_t *__restrict__ plan, int nb, int Mmax, int mmax, int NT,
 #pragma unroll
             for (int k = 0; k < HR; k++)
                 yv[k] = (act && r0 + k < L) ? Y[(size_t)(a + r0 + k) * mmax] : make_float2(0.f, 0.f);
-            // d = w . y in float-float: this lane's 16 rows in two accumulators, then the two halves
+            // d = w . y in float-float: this lane's rows in two accumulators, then the LPV lanes of
+            // the vector by a butterfly that adds lower + upper in every lane (identical results)
             float dh0 = 0.f, dl0 = 0.f, dh1 = 0.f, dl1 = 0.f;
 #pragma unroll
             for (int k = 0; k < HR; k += 2) {
@@ -707,10 +710,10 @@ k_band_bt2(const int32_t *__restrict__ plan, int nb, int Mmax, int mmax, int NT,
                            __shfl_sync(0xffffffffu, wl.y, r0 + k + 1), yv[k + 1].x, yv[k + 1].y);
             }
             ff_add(dh0, dl0, dh1, dl1);
-            {
-                // lower half's sum plus upper half's, the same operation order in both lanes
-                const float ph = __shfl_xor_sync(0xffffffffu, dh0, 16), pl = __shfl_xor_sync(0xffffffffu, dl0, 16);
-                if (hh) {
+#pragma unroll
+            for (int o = VPW; o < 32; o <<= 1) {
+                const float ph = __shfl_xor_sync(0xffffffffu, dh0, o), pl = __shfl_xor_sync(0xffffffffu, dl0, o);
+                if (lane & o) {
                     float xh = ph, xl = pl;
                     ff_add(xh, xl, dh0, dl0);
                     dh0 = xh;
@@ -956,8 +959,8 @@ cudaError_t launch_band_backtransform(pfsm_handle_s *h, cudaStream_t st)
                                                                                               w.bR2, w.bT2);
     g_launches++;
     const float2 *rf = reinterpret_cast<const float2 *>(w.bR2);
-    k_band_bt2<<<dim3((unsigned)((mmax + 15) / 16), (unsigned)nb), 32 * kBtWarps, 0, st>>>(plan, nb, Mmax, mmax, NT, rf,
-                                                                                           w.bT2, Yt);
+    k_band_bt2<kBtVpw><<<dim3((unsigned)((mmax + kBtVpw - 1) / kBtVpw), (unsigned)nb), 32 * kBtWarps, 0, st>>>(
+        plan, nb, Mmax, mmax, NT, rf, w.bT2, Yt);
     g_launches++;
     k_band_transpose<<<gt, 256, 0, st>>>(plan, nb, Mmax, mmax, true, w.sel_vec, Yt);
     g_launches++;
