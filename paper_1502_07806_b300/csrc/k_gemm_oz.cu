@@ -44,6 +44,7 @@ constexpr int MAX_STAGE_BYTES = OZ_SLICES * (P_TILE + Q_TILE);
 constexpr uint32_t TMEM_COLS = 512;               // two buffers of 256 columns, level L at 32 L
 constexpr uint32_t BUF_COLS = 256;
 constexpr int KCHUNK = 512;                       // K terms per exact level sum
+constexpr int kGroupRows = 8;                     // row tiles per group of the tile walk
 constexpr int BETA = 7;                           // bits per digit
 constexpr int QBITS = BETA * OZ_SLICES - 1;       // fixed-point bits of q (48)
 static_assert(OZ_LEVELS <= OZ_SLICES && OZ_LEVELS <= 8, "the s = 0 MMA must span every level");
@@ -227,8 +228,20 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
     using namespace tc;
     using namespace oz;
     const int z = blockIdx.z;
-    const int row0 = prm.row_base + blockIdx.y * BM;
-    const int col0 = (prm.cols_from_zero ? 0 : prm.row_base) + prm.col_off + blockIdx.x * BN;
+    // CTAs start in blockIdx order; the tiles are walked in groups of kGroupRows tile rows, the
+    // group's rows innermost, so the CTAs resident together share a few row tiles of P and each
+    // column tile of Q is read from DRAM once per group instead of once per row tile
+    int ty, tx;
+    {
+        const int gx = gridDim.x, lin = blockIdx.y * gx + blockIdx.x;
+        const int grp = lin / (kGroupRows * gx), r_first = grp * kGroupRows;
+        const int nr = min(kGroupRows, (int)gridDim.y - r_first);
+        const int loc = lin - grp * kGroupRows * gx;
+        ty = r_first + loc % nr;
+        tx = loc / nr;
+    }
+    const int row0 = prm.row_base + ty * BM;
+    const int col0 = (prm.cols_from_zero ? 0 : prm.row_base) + prm.col_off + tx * BN;
     const int rows_lim = prm.ext ? prm.ext[z] : prm.rows;
     const int cols_lim = prm.ext_c ? prm.ext_c[z] : (prm.ext ? prm.ext[z] : prm.cols);
     if (row0 >= rows_lim || col0 >= cols_lim) return;              // tile outside this window

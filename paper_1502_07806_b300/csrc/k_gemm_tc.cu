@@ -47,13 +47,21 @@ template <int KIND, int BN> struct Cfg {
     static constexpr int NPAIRS = NS * (NS + 1) / 2;
 };
 
-// Output tile t -> (tile row, tile column): row-major over the tile grid, or over its lower
-// triangle (column tile <= row tile) for lower-only products of square outputs.
-__device__ __forceinline__ void tile_coords(int t, int ncolt, int lower, int &tr, int &tcl)
+// Output tile t -> (tile row, tile column). Full products walk the tile grid in groups of
+// kGroupRows tile rows, the group's rows innermost: the ~148 tiles in flight at a time then share
+// a few tile rows of P and each tile column of Q is read from DRAM once per group, not once per
+// tile row (at N = 9072 the operands' slices, ~0.5 GB each, are four times L2). Lower-only
+// products of square outputs walk the lower triangle (column tile <= row tile) row by row.
+constexpr int kGroupRows = 8;
+
+__device__ __forceinline__ void tile_coords(int t, int nrowt, int ncolt, int lower, int &tr, int &tcl)
 {
     if (!lower) {
-        tr = t / ncolt;
-        tcl = t % ncolt;
+        const int grp = t / (kGroupRows * ncolt), r_first = grp * kGroupRows;
+        const int nr = min(kGroupRows, nrowt - r_first);
+        const int loc = t - grp * kGroupRows * ncolt;
+        tr = r_first + loc % nr;
+        tcl = loc / nr;
         return;
     }
     int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
@@ -139,7 +147,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
             bool stop = false;
             for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
                 int tr, tcl, kb0, kb1;
-                tile_coords(t, ncolt, prm.lower_only, tr, tcl);
+                tile_coords(t, nrowt, ncolt, prm.lower_only, tr, tcl);
                 krange(tr, kb0, kb1);
                 for (int kb = kb0; kb < kb1; kb++, it++) {
                     const int s = it % C::STAGES, round = it / C::STAGES;
@@ -172,7 +180,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
             bool ok = true;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, lt++) {
                 int tr, tcl, kb0, kb1;
-                tile_coords(t, ncolt, prm.lower_only, tr, tcl);
+                tile_coords(t, nrowt, ncolt, prm.lower_only, tr, tcl);
                 krange(tr, kb0, kb1);
                 const int buf = lt & 1;
                 if (lt >= 2 && !mbar_wait(acce_bar(buf), ((lt >> 1) - 1) & 1)) { ok = false; break; }
@@ -216,7 +224,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
         int lt = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, lt++) {
             int tr, tcl, kb0, kb1;
-            tile_coords(t, ncolt, prm.lower_only, tr, tcl);
+            tile_coords(t, nrowt, ncolt, prm.lower_only, tr, tcl);
             krange(tr, kb0, kb1);
             const int buf = lt & 1;
             const int row0 = tr * BM, col0 = tcl * BN;
