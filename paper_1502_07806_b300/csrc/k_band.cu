@@ -444,9 +444,14 @@ k_band_extract(const int32_t *__restrict__ plan, int nb, int Mmax, const double 
 // below (rows a + L .. a + L + KB - 1, columns R). Every block is loaded with all its loads in
 // flight (registers first, then the warp's shared-memory tile S where a transpose is needed),
 // updated, and stored back. The reflector goes to refl2 (KB entries, zero past L) and tau2.
+// part: 2 = the whole task; 0 = the reflector, the annihilated column and the diagonal block; 1 =
+// the left and below blocks. Parts 0 and 1 of one task run on two warps of one CTA (different
+// sub-partitions, so their FP64 instruction streams issue side by side), each forming the same
+// reflector from the same column; they meet at named barrier bar_id once both have read the column,
+// after which part 0 overwrites it.
 __device__ __forceinline__ void chase_task(double *__restrict__ B, int M, int s, int i, double *__restrict__ r2,
                                            double *__restrict__ t2, double *vsh, double *wsh, double (*S)[KB + 1],
-                                           int lane)
+                                           int lane, int part, int bar_id)
 {
     auto at = [&](int r, int cc) -> double & { return B[(size_t)cc * (2 * KB) + (r - cc)]; };
     const int a = s + 1 + i * KB;
@@ -464,15 +469,19 @@ __device__ __forceinline__ void chase_task(double *__restrict__ B, int M, int s,
         beta = 2.0 * scaled_rcp(fma(v0, v0, tail2));
         v = (lane == 0) ? v0 : x;
     }
-    r2[lane] = v;
-    if (lane == 0) *t2 = beta;
+    if (part != 1) {
+        r2[lane] = v;
+        if (lane == 0) *t2 = beta;
+    }
+    if (part != 2) asm volatile("bar.sync %0, 64;" ::"r"(bar_id) : "memory");
     if (beta == 0.0) return;
-    if (lane < L) at(a + lane, col) = (lane == 0) ? alpha : 0.0;
+    if (part != 1 && lane < L) at(a + lane, col) = (lane == 0) ? alpha : 0.0;
     vsh[lane] = v;
+    __syncwarp();
     double tmp[KB];
     // left block: H from the left on columns col+1 .. a-1 (the rest of the previous bulge); lane =
     // row for the loads and stores, lane = column for the arithmetic
-    if (i >= 1) {
+    if (part != 0 && i >= 1) {
 #pragma unroll
         for (int q = 0; q < KB - 1; q++) tmp[q] = (lane < L) ? at(a + lane, col + 1 + q) : 0.0;
 #pragma unroll
@@ -501,6 +510,7 @@ __device__ __forceinline__ void chase_task(double *__restrict__ B, int M, int s,
     }
     // diagonal block: D <- H D H = D - v w^T - w v^T, p = beta D v, w = p - (beta / 2)(v.p) v; column
     // c of the lower triangle in S[c][r], r >= c (lane = row)
+    if (part != 1) {
 #pragma unroll
     for (int c = 0; c < KB; c++) tmp[c] = (c <= lane && lane < L) ? at(a + lane, a + c) : 0.0;
 #pragma unroll
@@ -537,6 +547,8 @@ __device__ __forceinline__ void chase_task(double *__restrict__ B, int M, int s,
 #pragma unroll
     for (int c = 0; c < KB; c++)
         if (c <= lane && lane < L) at(a + lane, a + c) = S[c][lane];
+    }
+    if (part == 0) return;
     // below: rows e .. e + LB - 1 (lane = row, in registers), H from the right (the next bulge)
     const int e = a + L;
     const int LB = min(KB, M - e);
@@ -557,10 +569,14 @@ __device__ __forceinline__ void chase_task(double *__restrict__ B, int M, int s,
     __syncwarp();
 }
 
-// Cluster of CL CTAs per window (grid nb * CL), NW warps each; warp g of the window runs the
-// sweeps s = g (mod CL NW), task (s, i) at time step 3 s + i; a cluster barrier ends every time
-// step. Needs 3 CL NW > the tasks of sweep 0 so
-// that a warp's consecutive sweeps never overlap in time. Finally td/te of the tridiagonal.
+// Cluster of CL CTAs per window (grid nb * CL), NW warps each; task (s, i) at time step 3 s + i; a
+// cluster barrier ends every time step. Sweeps before s_pair: warp g of the window runs the
+// sweeps s = g (mod CL NW), one warp per task (needs 3 CL NW > the tasks of sweep 0 so that a
+// warp's consecutive sweeps never overlap in time). From s_pair on (at most 3 P tasks per sweep,
+// P = CL NW / 2) warp pair q (warps 2j, 2j + 1 of CTA r, q = r + CL j) runs the sweeps s_pair + q
+// (mod P), one task split over the pair: a task's time is its warp's FP64 instruction count (one
+// per 64 cycles per sub-partition), and in these later steps half the warps had no task. Finally
+// td/te of the tridiagonal.
 // Dynamic shared memory: per warp a KB x (KB + 1) tile and the reflector and w vectors.
 __global__ void __launch_bounds__(32 * kChaseWarps, 1)
 k_band_chase(const int32_t *__restrict__ plan, int nb, int Mmax, int NT, double *__restrict__ Bw,
@@ -583,14 +599,28 @@ k_band_chase(const int32_t *__restrict__ plan, int nb, int Mmax, int NT, double 
     if (Sw > 0) {
         const int nt0 = (M - 2 + KB - 1) / KB;         // tasks of sweep 0
         const int tend = 3 * (Sw - 1) + nt0;
+        // sweeps from s_pair on have at most 3 P tasks (P = CL NW / 2 warp pairs), so each can go
+        // to a pair of warps with a pair's consecutive sweeps still apart in time; earlier sweeps
+        // take one warp per task (the first steps have more tasks than warp pairs)
+        const int P = W / 2;
+        const int s_pair = max(0, M - 2 - 3 * P * KB);
+        const int q = rank + CL * (warp >> 1), part = warp & 1, bar_id = 1 + (warp >> 1);
         for (int t = 0; t < tend; t++) {
             const int smax = t / 3;
             if (smax >= g) {
                 const int s = g + ((smax - g) / W) * W;
                 const int i = t - 3 * s;
+                if (s < min(Sw, s_pair) && i < (M - 2 - s + KB - 1) / KB) {
+                    const size_t slot = ((size_t)b * Mmax + s) * NT + i;
+                    chase_task(B, M, s, i, refl2 + slot * KB, tau2 + slot, vsh, wsh, S, lane, 2, 0);
+                }
+            }
+            if (smax - s_pair >= q) {
+                const int s = s_pair + q + ((smax - s_pair - q) / P) * P;
+                const int i = t - 3 * s;
                 if (s < Sw && i < (M - 2 - s + KB - 1) / KB) {
                     const size_t slot = ((size_t)b * Mmax + s) * NT + i;
-                    chase_task(B, M, s, i, refl2 + slot * KB, tau2 + slot, vsh, wsh, S, lane);
+                    chase_task(B, M, s, i, refl2 + slot * KB, tau2 + slot, vsh, wsh, S, lane, part, bar_id);
                 }
             }
             // the barrier's release / acquire at cluster scope orders this step's band writes
