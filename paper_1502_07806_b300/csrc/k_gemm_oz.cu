@@ -468,15 +468,17 @@ k_gemm_oz(const __grid_constant__ CUtensorMap mapP, const __grid_constant__ CUte
 // `strip` column tiles: Q digits through a two-stage ring, the level sums of tile t in TMEM buffer
 // t & 1 (levels at columns 32 L), so the drain and the C update of a tile overlap the MMAs of the
 // next. K <= 64 < one exact 512-term chunk, so every tile is one exact level sum. Warp roles as in
-// k_gemm_oz (0: TMA, 1: TMEM owner and MMA issuer), eight drain warps (2-9); every wait bounded.
+// k_gemm_oz (0: TMA, 1: TMEM owner and MMA issuer), sixteen drain warps (2-17); every wait bounded.
 namespace ozs {
 constexpr int MAXKB = 2;                                  // K <= 64
 constexpr int QST = 2;                                    // Q ring stages
 constexpr int P_BYTES = MAXKB * OZ_SLICES * oz::P_TILE;   // 112 KB
 constexpr int QSTAGE = MAXKB * OZ_SLICES * oz::Q_TILE;    // 28 KB
-constexpr int EPI_WARPS = 8;                             // drain warps: 2 per TMEM lane quarter
+constexpr int EPI_WARPS = 16;                            // drain warps: 4 per TMEM lane quarter
+constexpr int CW = oz::BN * 4 / EPI_WARPS;                // columns per drain warp (8)
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
-constexpr int EB_BYTES = EPI_WARPS * 32 * 17 * 8;        // per-warp 32 x 16 staging block
+constexpr int EB_BYTES = EPI_WARPS * 32 * (CW + 1) * 8;  // per-warp 32 x CW staging block
+static_assert(CW == 8, "the drain loads one 8-column TMEM group per level");
 }  // namespace ozs
 
 __global__ void __launch_bounds__(ozs::THREADS, 1)
@@ -603,28 +605,30 @@ k_gemm_oz_strip(const __grid_constant__ CUtensorMap mapP, const __grid_constant_
         }
         __syncwarp();
     } else {
-        // drain warps 2 .. 9: TMEM lane quarter gq = warp & 3 (the quarter a warp may read) and
-        // column half hc (16 of the tile's 32 columns), two warps per SM sub-partition so that one
-        // drains while the other waits on memory. Each entry's level sums are combined exactly in
+        // drain warps 2 .. 17: TMEM lane quarter gq = warp & 3 (the quarter a warp may read) and
+        // column slice hc (8 of the tile's 32 columns), four warps per SM sub-partition so that
+        // some drain while others wait on memory. Each entry's level sums are combined exactly in
         // 64-bit integers and rounded once to FP64; the C update is the only FP64 operation.
+        using ozs::CW;
         const int gq = warp & 3, hc = (warp - 2) >> 2;
         const int r = row0 + 32 * gq + lane;
         const int er = (r < rows_lim) ? prm.ep[zr + r] : 0;
         const int escale = -12 - BETA * (LV - 1);                 // scale of T's unit
-        double(*eb)[17] = reinterpret_cast<double(*)[17]>(ebuf) + 32 * (warp - 2);
+        double(*eb)[CW + 1] = reinterpret_cast<double(*)[CW + 1]>(ebuf) + 32 * (warp - 2);
         const int R0 = row0 + 32 * gq;
-        const int rsub = lane >> 4, cl = lane & 15;               // C update: rows 2 i + rsub, column cl
+        constexpr int RP = 32 / CW;                               // rows per C instruction (4)
+        const int rsub = lane / CW, cl = lane % CW;               // C update: rows RP q + rsub, column cl
         for (int t = 0; t < nt; t++) {
             const int buf = t & 1;
-            const int c = cbase + (ct0 + t) * BN + 16 * hc + cl;
+            const int c = cbase + (ct0 + t) * BN + CW * hc + cl;
             const bool cok = c < cols_lim;
             const int ec = cok ? prm.eq[zq + c] : 0;
-            // this warp alone updates its 32 x 16 block of C: its loads go out before the wait for
+            // this warp alone updates its 32 x CW block of C: its loads go out before the wait for
             // the tile's MMAs, so their latency overlaps it
-            double cv[16];
+            double cv[32 / RP];
 #pragma unroll
-            for (int q = 0; q < 16; q++) {
-                const int gr = R0 + 2 * q + rsub;
+            for (int q = 0; q < 32 / RP; q++) {
+                const int gr = R0 + RP * q + rsub;
                 cv[q] = (prm.sub && gr < rows_lim && cok) ? Cz[(int64_t)gr * prm.ldc + c] : 0.0;
             }
             bool got = mbar_wait(accf(buf), (t >> 1) & 1);
@@ -635,32 +639,27 @@ k_gemm_oz_strip(const __grid_constant__ CUtensorMap mapP, const __grid_constant_
                 break;
             }
             fence_after();
-            const uint32_t ta = tmem_acc + ((uint32_t)(32 * gq) << 16) + BUF_COLS * buf + 16u * hc;
+            const uint32_t ta = tmem_acc + ((uint32_t)(32 * gq) << 16) + BUF_COLS * buf + (uint32_t)(CW * hc);
+            uint32_t v[OZ_LEVELS][8];
 #pragma unroll
-            for (int g = 0; g < 2; g++) {                         // two groups of 8 columns
-                uint32_t v[OZ_LEVELS][8];
+            for (int L = 0; L < OZ_LEVELS; L++)
+                if (L < LV) tmem_ld8_nowait(ta + 32u * L, v[L]);
+            tmem_wait_ld();
 #pragma unroll
-                for (int L = 0; L < OZ_LEVELS; L++)
-                    if (L < LV) tmem_ld8_nowait(ta + 32u * L + 8u * g, v[L]);
-                tmem_wait_ld();
+            for (int L = 0; L < OZ_LEVELS; L++)
+                if (L < LV) tmem_regs_after_wait(v[L]);
+            fence_before();                                       // every TMEM read of the tile done
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce(buf)) : "memory");
 #pragma unroll
-                for (int L = 0; L < OZ_LEVELS; L++)
-                    if (L < LV) tmem_regs_after_wait(v[L]);
-                if (g == 1) {                                     // every TMEM read of the tile done
-                    fence_before();
-                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce(buf)) : "memory");
-                }
-#pragma unroll
-                for (int j = 0; j < 8; j++) {
-                    const int es = er + __shfl_sync(0xffffffffu, ec, 8 * g + j) + escale;
-                    eb[lane][8 * g + j] = oz_i64_to_f64_scaled(oz_levels_i64(v, j, LV), es);
-                }
+            for (int j = 0; j < CW; j++) {
+                const int es = er + __shfl_sync(0xffffffffu, ec, j) + escale;
+                eb[lane][j] = oz_i64_to_f64_scaled(oz_levels_i64(v, j, LV), es);
             }
             __syncwarp();
 #pragma unroll
-            for (int q = 0; q < 16; q++) {
-                const int gr = R0 + 2 * q + rsub;
-                const double res = eb[2 * q + rsub][cl];
+            for (int q = 0; q < 32 / RP; q++) {
+                const int gr = R0 + RP * q + rsub;
+                const double res = eb[RP * q + rsub][cl];
                 if (gr < rows_lim && cok) Cz[(int64_t)gr * prm.ldc + c] = prm.sub ? cv[q] - res : res;
             }
             __syncwarp();
