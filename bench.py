@@ -590,7 +590,9 @@ def main():
         plan = h.diagnostic(pf.DIAG_PLAN).cpu().numpy()
         out = dict(total=total, steps=steps, warmup=warmup, value=job_rate(steps, world, total), phases=ph,
                    launches=launches, clocks=sampler.summary() if sampler else None, plan=plan,
-                   gemm_tile_n=phases[-1].get("gemm_tile_n") if phases else None, A=A, prev=prev)
+                   gemm_tile_n=phases[-1].get("gemm_tile_n") if phases else None, A=A, prev=prev,
+                   gs={"preconditioner": phases[-1].get("gs_precond"),
+                       "series_residual": phases[-1].get("gs_precond_residual")} if phases else None)
         if keep:
             out.update(h=h, lam=lam, V=V)
         else:
@@ -675,7 +677,8 @@ def main():
         return 0
 
     forms = {headline_prec: {"solves_per_s": value, "ms_per_solve": ms_per_step, "steps": args.steps,
-                             "warmup": args.warmup, "phases_ms": main_run["phases"]}}
+                             "warmup": args.warmup, "phases_ms": main_run["phases"],
+                             "gram_schmidt_path": main_run["gs"]}}
     if not args.no_oracle:
         forms[headline_prec]["accuracy"] = accuracy_vs_golden(p, lam, V, cfg.get("golden", ""))
     h.close()
@@ -689,7 +692,7 @@ def main():
         st_, wu = other_steps[prec]
         r = measure(p, prec, st_, wu, clocks=False)
         forms[prec] = {"solves_per_s": r["value"], "ms_per_solve": 1000.0 * r["total"] / st_, "steps": st_,
-                       "warmup": wu, "phases_ms": r["phases"]}
+                       "warmup": wu, "phases_ms": r["phases"], "gram_schmidt_path": r["gs"]}
         if not args.no_oracle:
             forms[prec]["accuracy"] = accuracy_vs_golden(p, r["lam"], r["V"], cfg.get("golden", ""))
         r["h"].close()
