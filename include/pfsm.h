@@ -336,13 +336,14 @@ int pfsm_get_profile(pfsm_handle_t h, pfsm_profile_t *out);
  * pfsm_selftest_fp64_helpers: for i < n, rcp_scaled[i] = 1/x[i] and rsqrt_scaled[i] = 1/sqrt(x[i])
  * by the exponent-splitting Newton helpers (0 where x[i] <= 0, outside their domain), rcp_fast[i]
  * = 1/x[i] by the bit-pattern Newton helper (either sign; |x| outside [2^-125, 2^126) takes
- * CUDA's division).
+ * CUDA's division), rsqrt_fast[i] = 1/sqrt(x[i]) by the bit-pattern Newton helper (0 where
+ * x[i] <= 0; x outside [2^-125, 2^124) takes the exponent-splitting helper).
  * pfsm_selftest_i64_to_f64: out[i] = t[i] * 2^e[i] rounded to nearest, ties to even (the digit
  * products' exact level-sum conversion).
  * Both return PFSM_ERR_INVALID_ARG for n < 0 or a null pointer with n > 0, PFSM_ERR_CUDA if the
  * launch fails. */
 int pfsm_selftest_fp64_helpers(const double *x, int64_t n, double *rcp_scaled, double *rsqrt_scaled,
-                               double *rcp_fast, void *stream);
+                               double *rcp_fast, double *rsqrt_fast, void *stream);
 int pfsm_selftest_i64_to_f64(const int64_t *t, const int32_t *e, int64_t n, double *out, void *stream);
 
 /* Thread-local text of the last error raised on this thread ("" if none). */

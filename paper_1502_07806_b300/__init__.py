@@ -89,7 +89,7 @@ def load_library():
     lib.pfsm_set_timing.argtypes = [P, i32]
     lib.pfsm_get_profile.argtypes = [P, ctypes.POINTER(Profile)]
     lib.pfsm_last_error.argtypes = []
-    lib.pfsm_selftest_fp64_helpers.argtypes = [P, i64, P, P, P, P]
+    lib.pfsm_selftest_fp64_helpers.argtypes = [P, i64, P, P, P, P, P]
     lib.pfsm_selftest_i64_to_f64.argtypes = [P, P, i64, P, P]
     lib.pfsm_last_error.restype = ctypes.c_char_p
     lib.pfsm_destroy.argtypes = [P]

@@ -56,6 +56,27 @@ __device__ __forceinline__ double fast_rcp(double p)
     return y;
 }
 
+// 1/sqrt(d) for d > 0 without F2F conversions or exponent splitting (both take FP64-pipe
+// instructions): the FP32 approximate inverse square root of d's leading 24 bits, conversions from
+// and to FP64 by integer operations on the bit patterns, then two Newton steps y <- y (3/2 - d y^2 / 2)
+// (relative error 2^-22 -> 2^-43 -> rounding). d outside [2^-125, 2^124) takes scaled_rsqrt.
+__device__ __forceinline__ double fast_rsqrt(double d)
+{
+    const int hi = __double2hiint(d);
+    const unsigned lo = (unsigned)__double2loint(d);
+    const int ev = (hi >> 20) & 0x7FF;
+    if ((unsigned)(ev - 898) > 248u || hi < 0) return scaled_rsqrt(d);
+    const float df = __uint_as_float(((unsigned)(ev - 896) << 23) | ((unsigned)(hi & 0xFFFFF) << 3) | (lo >> 29));
+    float rf;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(df));
+    const unsigned rb = __float_as_uint(rf);
+    double y = __hiloint2double((int)(((((rb >> 23) & 0xFFu) + 896u) << 20) | ((rb & 0x7FFFFFu) >> 3)), (int)(rb << 29));
+    const double hd = 0.5 * d;
+    y = y * fma(-hd, y * y, 1.5);
+    y = y * fma(-hd, y * y, 1.5);
+    return y;
+}
+
 // t 2^e rounded to FP64 (to nearest, ties to even) by integer operations: the FP64 pipe, which
 // the C update needs, is 1/64 of the integer rate.
 __device__ __forceinline__ double oz_i64_to_f64_scaled(long long t, int e)

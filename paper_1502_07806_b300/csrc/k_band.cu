@@ -166,10 +166,10 @@ k_band_panel(const int32_t *__restrict__ plan, int nb, int Mmax, int c, int rpc_
                 double inv = 0.0, v0 = 0.0, alpha = x0, beta = 0.0;
                 if (tail2 != 0.0) {
                     const double nn = fma(x0, x0, tail2);
-                    const double xn = nn * scaled_rsqrt(nn);
+                    const double xn = nn * fast_rsqrt(nn);
                     alpha = (x0 >= 0.0) ? -xn : xn;
                     v0 = x0 - alpha;
-                    inv = scaled_rsqrt(fma(v0, v0, tail2));
+                    inv = fast_rsqrt(fma(v0, v0, tail2));
                     beta = 2.0;
                 }
                 sc[0] = inv;
@@ -463,10 +463,10 @@ __device__ __forceinline__ void chase_task(double *__restrict__ B, int M, int s,
     double beta = 0.0, alpha = x0, v = 0.0;
     if (tail2 != 0.0) {
         const double nn = fma(x0, x0, tail2);
-        const double xn = nn * scaled_rsqrt(nn);
+        const double xn = nn * fast_rsqrt(nn);
         alpha = (x0 >= 0.0) ? -xn : xn;
         const double v0 = x0 - alpha;
-        beta = 2.0 * scaled_rcp(fma(v0, v0, tail2));
+        beta = 2.0 * fast_rcp(fma(v0, v0, tail2));
         v = (lane == 0) ? v0 : x;
     }
     if (part != 1) {

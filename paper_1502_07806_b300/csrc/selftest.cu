@@ -10,7 +10,8 @@ namespace pfsm {
 namespace {
 
 __global__ void k_selftest_fp64(const double *__restrict__ x, int64_t n, double *__restrict__ rcp_scaled,
-                                double *__restrict__ rsqrt_scaled, double *__restrict__ rcp_fast)
+                                double *__restrict__ rsqrt_scaled, double *__restrict__ rcp_fast,
+                                double *__restrict__ rsqrt_fast)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -18,6 +19,7 @@ __global__ void k_selftest_fp64(const double *__restrict__ x, int64_t n, double 
     rcp_scaled[i] = (v > 0.0) ? scaled_rcp(v) : 0.0;          // defined for positive arguments
     rsqrt_scaled[i] = (v > 0.0) ? scaled_rsqrt(v) : 0.0;
     rcp_fast[i] = fast_rcp(v);
+    rsqrt_fast[i] = (v > 0.0) ? fast_rsqrt(v) : 0.0;
 }
 
 __global__ void k_selftest_i64(const long long *__restrict__ t, const int32_t *__restrict__ e, int64_t n,
@@ -31,12 +33,14 @@ __global__ void k_selftest_i64(const long long *__restrict__ t, const int32_t *_
 }  // namespace pfsm
 
 extern "C" int pfsm_selftest_fp64_helpers(const double *x, int64_t n, double *rcp_scaled, double *rsqrt_scaled,
-                                          double *rcp_fast, void *stream)
+                                          double *rcp_fast, double *rsqrt_fast, void *stream)
 {
-    if (n < 0 || (n > 0 && (!x || !rcp_scaled || !rsqrt_scaled || !rcp_fast))) return PFSM_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!x || !rcp_scaled || !rsqrt_scaled || !rcp_fast || !rsqrt_fast)))
+        return PFSM_ERR_INVALID_ARG;
     if (n == 0) return PFSM_OK;
     pfsm::k_selftest_fp64<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, n, rcp_scaled,
-                                                                                         rsqrt_scaled, rcp_fast);
+                                                                                         rsqrt_scaled, rcp_fast,
+                                                                                         rsqrt_fast);
     return cudaGetLastError() == cudaSuccess ? PFSM_OK : PFSM_ERR_CUDA;
 }
 

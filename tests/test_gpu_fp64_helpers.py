@@ -8,7 +8,8 @@ the mantissa interval [1, 2) (its ends included), against:
   1/x           IEEE division (numpy's and CUDA's are both correctly rounded);
   1/sqrt(x)     the correctly rounded value, from 60-digit decimal arithmetic;
   t 2^e         the exact rational rounded once (Python's Fraction -> float is correctly rounded).
-Bounds: the Newton helpers within 2 ulp of the correctly rounded result (two steps from a 2^-22
+The bit-pattern inverse square root is the one the panel QR and the bulge chase use. Bounds: the
+Newton helpers within 2 ulp of the correctly rounded result (two steps from a 2^-22
 seed leave ~2^-88 of approximation error, so only the last steps' roundings remain); the integer
 conversion bit for bit."""
 import ctypes
@@ -54,8 +55,8 @@ def test_newton_reciprocal_and_rsqrt_within_two_ulp():
     pf, lib = _lib()
     x = _inputs(-1020, 1020, 3)                      # positive, results normal
     xd = torch.from_numpy(x).cuda()
-    r1, r2, r3 = (torch.empty_like(xd) for _ in range(3))
-    assert lib.pfsm_selftest_fp64_helpers(_ptr(xd), x.size, _ptr(r1), _ptr(r2), _ptr(r3), None) == pf.OK
+    r1, r2, r3, r4 = (torch.empty_like(xd) for _ in range(4))
+    assert lib.pfsm_selftest_fp64_helpers(_ptr(xd), x.size, _ptr(r1), _ptr(r2), _ptr(r3), _ptr(r4), None) == pf.OK
     torch.cuda.synchronize()
     rcp_ref = 1.0 / x
     decimal.getcontext().prec = 60
@@ -63,26 +64,35 @@ def test_newton_reciprocal_and_rsqrt_within_two_ulp():
     e_rcp = _ulps(r1.cpu().numpy(), rcp_ref)
     e_rsq = _ulps(r2.cpu().numpy(), rsq_ref)
     e_fast = _ulps(r3.cpu().numpy(), rcp_ref)
-    print(f"max ulp: scaled_rcp {e_rcp.max():.2f}, scaled_rsqrt {e_rsq.max():.2f}, fast_rcp {e_fast.max():.2f}")
+    e_frsq = _ulps(r4.cpu().numpy(), rsq_ref)
+    print(f"max ulp: scaled_rcp {e_rcp.max():.2f}, scaled_rsqrt {e_rsq.max():.2f}, fast_rcp {e_fast.max():.2f}, "
+          f"fast_rsqrt {e_frsq.max():.2f}")
     assert e_rcp.max() <= 2.0
     assert e_rsq.max() <= 2.0
     assert e_fast.max() <= 2.0
+    assert e_frsq.max() <= 2.0
 
 
 def test_fast_reciprocal_negative_and_outside_its_fast_range():
     pf, lib = _lib()
     x = np.concatenate([-_inputs(-1020, 1020, 5), _inputs(-1020, -126, 6), _inputs(126, 1020, 7)])
     xd = torch.from_numpy(x).cuda()
-    r1, r2, r3 = (torch.empty_like(xd) for _ in range(3))
-    assert lib.pfsm_selftest_fp64_helpers(_ptr(xd), x.size, _ptr(r1), _ptr(r2), _ptr(r3), None) == pf.OK
+    r1, r2, r3, r4 = (torch.empty_like(xd) for _ in range(4))
+    assert lib.pfsm_selftest_fp64_helpers(_ptr(xd), x.size, _ptr(r1), _ptr(r2), _ptr(r3), _ptr(r4), None) == pf.OK
     torch.cuda.synchronize()
     got = r3.cpu().numpy()
     assert _ulps(got, 1.0 / x).max() <= 2.0
     outside = np.abs(x) < 2.0 ** -125
     outside |= np.abs(x) >= 2.0 ** 126
     np.testing.assert_array_equal(got[outside], 1.0 / x[outside])      # CUDA's own division there
-    # the scaled helpers are defined for positive arguments only: zero elsewhere
-    assert np.all(r1.cpu().numpy()[x <= 0] == 0.0) and np.all(r2.cpu().numpy()[x <= 0] == 0.0)
+    # the inverse square roots outside the bit-pattern range fall back to the scaled helper
+    pos = x > 0
+    decimal.getcontext().prec = 60
+    rsq_ref = np.array([float(1 / decimal.Decimal(v).sqrt()) for v in x[pos]])
+    assert _ulps(r4.cpu().numpy()[pos], rsq_ref).max() <= 2.0
+    # the square-root and scaled helpers are defined for positive arguments only: zero elsewhere
+    for r in (r1, r2, r4):
+        assert np.all(r.cpu().numpy()[x <= 0] == 0.0)
 
 
 def test_integer_sum_to_fp64_is_correctly_rounded():
@@ -106,7 +116,7 @@ def test_integer_sum_to_fp64_is_correctly_rounded():
 
 def test_selftest_entry_points_reject_bad_arguments():
     pf, lib = _lib()
-    assert lib.pfsm_selftest_fp64_helpers(None, 4, None, None, None, None) == pf.INVALID_ARG
-    assert lib.pfsm_selftest_fp64_helpers(None, -1, None, None, None, None) == pf.INVALID_ARG
+    assert lib.pfsm_selftest_fp64_helpers(None, 4, None, None, None, None, None) == pf.INVALID_ARG
+    assert lib.pfsm_selftest_fp64_helpers(None, -1, None, None, None, None, None) == pf.INVALID_ARG
     assert lib.pfsm_selftest_i64_to_f64(None, None, 3, None, None) == pf.INVALID_ARG
-    assert lib.pfsm_selftest_fp64_helpers(None, 0, None, None, None, None) == pf.OK
+    assert lib.pfsm_selftest_fp64_helpers(None, 0, None, None, None, None, None) == pf.OK
