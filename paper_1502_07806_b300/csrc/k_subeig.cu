@@ -74,10 +74,10 @@ __device__ __forceinline__ void householder_scalars(const double *c, int kk, int
     double beta = 0.0, alpha = x0, v0 = 0.0;
     if (t2 != 0.0) {
         const double nn = fma(x0, x0, t2);
-        const double xn = nn * scaled_rsqrt(nn);
+        const double xn = nn * fast_rsqrt(nn);
         alpha = (x0 >= 0.0) ? -xn : xn;
         v0 = x0 - alpha;
-        beta = 2.0 * scaled_rcp(fma(v0, v0, t2));
+        beta = 2.0 * fast_rcp(fma(v0, v0, t2));
     }
     if (lane == 0) { sc[0] = beta; sc[1] = alpha; sc[2] = v0; }
 }
@@ -508,10 +508,10 @@ k_tridiag_panel(const double *__restrict__ A, int64_t N, const int32_t *__restri
         double beta = 0.0, alpha = x0;
         if (tail2 != 0.0) {
             const double nn = fma(x0, x0, tail2);
-            const double xn = nn * scaled_rsqrt(nn);
+            const double xn = nn * fast_rsqrt(nn);
             alpha = (x0 >= 0.0) ? -xn : xn;
             const double v0 = x0 - alpha;
-            beta = 2.0 * scaled_rcp(fma(v0, v0, tail2));
+            beta = 2.0 * fast_rcp(fma(v0, v0, tail2));
         }
         for (int i = k + 1 + tid; i < M; i += blockDim.x)
             hv[i] = (beta != 0.0) ? ((i == k + 1) ? x0 - alpha : vbuf[i]) : 0.0;
