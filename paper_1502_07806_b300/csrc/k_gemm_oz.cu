@@ -157,25 +157,38 @@ __device__ __forceinline__ void oz_split_row(const T *__restrict__ x, int64_t co
     // the sum is rounded to an integer held in the low significand bits)
     constexpr double kMagic = 6755399441055744.0;                     // 1.5 2^52
     constexpr long long kBias = 64ll * (((1ll << 42) - 1) / 127);     // sum_{i < 6} 64 128^i
-    auto emit = [&](int64_t c, double t) {
+    // the seven BF16 digits of t (low half: slice 6 .. high: slice 0), as 16-bit patterns
+    auto digits = [&](double t, uint32_t (&d)[OZ_SLICES]) {
         const long long q = (long long)(oz_bits(t) - oz_bits(kMagic)) + kBias;
         const uint32_t lo = (uint32_t)q, hi = (uint32_t)((unsigned long long)q >> 32);
-        unsigned short *o = out + c;
-        o[6 * sstride] = oz_digit_bf16(lo & 127u);
-        o[5 * sstride] = oz_digit_bf16((lo >> 7) & 127u);
-        o[4 * sstride] = oz_digit_bf16((lo >> 14) & 127u);
-        o[3 * sstride] = oz_digit_bf16((lo >> 21) & 127u);
-        o[2 * sstride] = oz_digit_bf16(__funnelshift_r(lo, hi, 28) & 127u);
-        o[1 * sstride] = oz_digit_bf16((hi >> 3) & 127u);
-        o[0] = oz_digit_bf16((uint32_t)(((int)hi >> 10) + 64));      // top digit q' >> 42, |n_0| <= 64
+        d[6] = oz_digit_bf16(lo & 127u);
+        d[5] = oz_digit_bf16((lo >> 7) & 127u);
+        d[4] = oz_digit_bf16((lo >> 14) & 127u);
+        d[3] = oz_digit_bf16((lo >> 21) & 127u);
+        d[2] = oz_digit_bf16(__funnelshift_r(lo, hi, 28) & 127u);
+        d[1] = oz_digit_bf16((hi >> 3) & 127u);
+        d[0] = oz_digit_bf16((uint32_t)(((int)hi >> 10) + 64));      // top digit q' >> 42, |n_0| <= 64
+    };
+    // two adjacent entries per lane, their digits stored as one 32-bit word per slice (row starts
+    // and slice strides are even); past the row's end the pair's second entry is zero, whose zero
+    // digits land in the row's padding, which the products read as zero K terms anyway
+    auto emit2 = [&](int64_t c, double t0, double t1) {
+        uint32_t d0[OZ_SLICES], d1[OZ_SLICES];
+        digits(t0, d0);
+        digits(t1, d1);
+#pragma unroll
+        for (int sl = 0; sl < OZ_SLICES; sl++)
+            *reinterpret_cast<uint32_t *>(out + c + sl * sstride) = d0[sl] | (d1[sl] << 16);
     };
     const int sh = oz::QBITS - e;
     if (sh <= 1000) {                                                 // 2^sh is a double: one FMA
         const double sc = ldexp(1.0, sh);
-        for (int64_t c = lane; c < cols; c += 32) emit(c, fma(val(c), sc, kMagic));
+        for (int64_t c = 2 * lane; c < cols; c += 64)
+            emit2(c, fma(val(c), sc, kMagic), (c + 1 < cols) ? fma(val(c + 1), sc, kMagic) : kMagic);
     } else {                                                          // rows below 2^-952: two factors
         const double sc1 = ldexp(1.0, sh / 2), sc2 = ldexp(1.0, sh - sh / 2);
-        for (int64_t c = lane; c < cols; c += 32) emit(c, fma(val(c) * sc1, sc2, kMagic));
+        for (int64_t c = 2 * lane; c < cols; c += 64)
+            emit2(c, fma(val(c) * sc1, sc2, kMagic), (c + 1 < cols) ? fma(val(c + 1) * sc1, sc2, kMagic) : kMagic);
     }
     for (int64_t c = cols + lane; c < fill_to; c += 32)
 #pragma unroll
