@@ -311,8 +311,9 @@ def test_mixed_ragged_and_edge_sizes(pf, orc, n, nb, halo, K, prec):
     (301, 2, 150, 1),
 ])
 def test_two_stage_reduction_matches_oracle(pf, orc, n, nb, halo, K, prec):
-    """The two-stage window reduction (dense -> band of half-width 32 by digit products, float-float
-    bulge chasing, both back-transformations) forced on windows from 66 to 700 rows: ragged
+    """The two-stage window reduction (dense -> band of half-width 32 by digit products, FP64 bulge
+    chasing with every task split over a warp pair, the bulge reflectors applied in float-float, the
+    panel back-transformation by digit products) forced on windows from 66 to 700 rows: ragged
     windows and slices, one window covering the matrix, a window whose width is not a multiple of
     32, K = 0. Same FP64 bars as every other form."""
     p = wl.random_nearly_diagonal(n, seed=2000 + n + nb, sigma=1e-3, decay=24.0, nblocks=nb, halo=halo)
@@ -320,6 +321,24 @@ def test_two_stage_reduction_matches_oracle(pf, orc, n, nb, halo, K, prec):
     g = _run(pf, p, fs_iters=K, precision=prec, reduction=2)
     _check(r, g)
     np.testing.assert_allclose(g["eps"], r.eps, rtol=0, atol=1e-12)
+
+
+@pytest.fixture(scope="module")
+def wide(orc):
+    p = wl.random_nearly_diagonal(1800, seed=4242, sigma=1e-3, decay=24.0, nblocks=2)
+    return p, orc.pfsm(p.A, p.prev, 2, fs_iters=p.fs_iters)       # ~20 s of CPU, once
+
+
+@pytest.mark.parametrize("prec", [0, 2, 1], ids=["fp64", "bf16", "tf32"])
+def test_wide_windows_match_oracle(pf, wide, prec):
+    """Windows of 1260 rows (N = 1800, two slices, default halo): in the mixed forms the two-stage
+    reduction by default, with bulge-chasing sweeps of both kinds (the first 106 with more tasks
+    than warp pairs, one warp per task; the rest split over warp pairs), and in every form the
+    inverse iteration that keeps its iterates in global memory (windows wider than 731 rows)."""
+    p, r = wide
+    g = _run(pf, p, precision=prec)
+    assert int(np.max(g["plan"][3])) == 1260
+    _check(r, g)
 
 
 @pytest.mark.parametrize("prec", [2, 1], ids=["bf16", "tf32"])
