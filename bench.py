@@ -50,11 +50,11 @@ DTYPES = {"fp64": "f64", "bf16": "bf16x3-split, f32 accumulate, f64 epilogue",
 # kernel from an ncu capture of the current build, keyed by (kernel, workload); a kernel changed
 # since its capture has no entry (the line then reports null). Captures and commands: profiles/.
 TRAFFIC = {
-    # one 2200-row window captured whole (1.23 MB read + 0.21 MB written)
-    ("k_band_chase", "window2200"): 1.44e6,
+    # one 2200-row window captured whole (1.24 MB read + 0.37 MB written)
+    ("k_band_chase", "window2200"): 1.61e6,
     # the same capture scaled by window rows to the N = 9072 solve's 36 windows of 2068 rows
     # (the chase reads the band once and writes its reflectors: traffic grows with the rows)
-    ("k_band_chase", "vacancy"): 1.44e6 * 36 * 2068 / 2200,
+    ("k_band_chase", "vacancy"): 1.61e6 * 36 * 2068 / 2200,
 }
 
 
