@@ -30,14 +30,16 @@ planes split so the (mostly constant) high bytes deflate well. The absolute erro
 in norm, far below the 1e-8 projector bar the tests apply.
 
 Usage: python tests/golden/make_fullsize.py [vacancy] [metal] [--threads T]
-A raw dump of the full oracle outputs goes to gpurun_out/oracle_cache/ (git-ignored) so that the
-sample can be re-packed without re-running the oracle (--repack).
+A raw dump of the full oracle outputs (several GB) goes to a cache directory outside the repository
+($PFSM_ORACLE_CACHE, default <system temp dir>/pfsm_oracle_cache) so that the sample can be re-packed
+without re-running the oracle.
 """
 from __future__ import annotations
 
 import argparse
 import os
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -51,7 +53,7 @@ import oracle  # noqa: E402
 import workloads as wl  # noqa: E402
 from fullsize_ref import quantise, sha256, sketch_matrix  # noqa: E402
 
-CACHE = os.path.join(ROOT, "gpurun_out", "oracle_cache")
+CACHE = os.environ.get("PFSM_ORACLE_CACHE", os.path.join(tempfile.gettempdir(), "pfsm_oracle_cache"))
 
 # the <V, W> term of the metal loss and the directions of the directional-derivative check
 W_SEED = 55
